@@ -1,0 +1,185 @@
+"""FP64 CPU oracle of one Ito-KMC time step (arXiv 2307.01797).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``; never by the product package.
+It shares no code with the CUDA library.  The particle, KMC and photon steps
+are plain C (``itokmc_oracle.c``, built without FMA contraction); the field
+solve is numpy (``poisson.py``); the step composition is ``step.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "itokmc_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+TAG_INIT, TAG_PUSH, TAG_KMC, TAG_PRODUCT, TAG_PHOTON = 1, 2, 3, 4, 5
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (no FMA contraction, no fast-math)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``ora_params`` in itokmc_oracle.c."""
+    _fields_ = [
+        ("n", ctypes.c_int32), ("ppc", ctypes.c_int32), ("n_new", ctypes.c_int32),
+        ("n_crit", ctypes.c_int32), ("n_ssa", ctypes.c_int32), ("frac_bits", ctypes.c_int32),
+        ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+        ("dt", ctypes.c_double), ("mu", ctypes.c_double), ("D", ctypes.c_double),
+        ("alpha_A", ctypes.c_double), ("alpha_B", ctypes.c_double), ("eta", ctypes.c_double),
+        ("photon_ratio", ctypes.c_double), ("kappa_lo", ctypes.c_double), ("kappa_hi", ctypes.c_double),
+        ("eps", ctypes.c_double), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
+    ]
+
+
+def make_params(phys: dict, seed: int, step: int = 0) -> Params:
+    """Build oracle parameters from a physics dict (see the package's
+    ``synth.physics_*`` helpers for the keys)."""
+    p = Params()
+    p.n = int(phys["n"])
+    p.ppc = int(phys.get("ppc", 8))
+    p.n_new = int(phys.get("n_new", 64))
+    p.n_crit = int(phys.get("n_crit", 5))
+    p.n_ssa = int(phys.get("n_ssa", 10))
+    p.frac_bits = int(phys.get("frac_bits", 10))
+    for a in range(3):
+        p.lo[a] = float(phys["lo"][a])
+        p.hi[a] = float(phys["hi"][a])
+    p.dt = float(phys["dt"])
+    p.mu = float(phys["mu"])
+    p.D = float(phys["D"])
+    p.alpha_A = float(phys["alpha_A"])
+    p.alpha_B = float(phys["alpha_B"])
+    p.eta = float(phys["eta"])
+    p.photon_ratio = float(phys.get("photon_ratio", 0.0))
+    p.kappa_lo = float(phys.get("kappa_lo", 520.0))
+    p.kappa_hi = float(phys.get("kappa_hi", 3.0e4))
+    p.eps = float(phys.get("eps", float("inf")))
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.step = int(step) & 0xFFFFFFFF
+    return p
+
+
+def _P(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            d, i64, u32, u64, i32 = (ctypes.c_double, ctypes.c_int64, ctypes.c_uint32,
+                                     ctypes.c_uint64, ctypes.c_int32)
+            pd, pi64, pu32, pu64 = (ctypes.POINTER(d), ctypes.POINTER(i64), ctypes.POINTER(u32),
+                                    ctypes.POINTER(u64))
+            pp = ctypes.POINTER(Params)
+            L.ora_philox4x32_10.argtypes = [pu32, pu32, pu32]
+            L.ora_log.argtypes = [d]; L.ora_log.restype = d
+            L.ora_exp.argtypes = [d]; L.ora_exp.restype = d
+            L.ora_sincos2pi.argtypes = [d, pd, pd]
+            L.ora_poisson_draws.argtypes = [u64, u32, u32, u32, u32, d, i64, pi64]
+            L.ora_uniform_draws.argtypes = [u64, u32, u32, u32, u32, i64, pd]
+            L.ora_push.argtypes = [pp, i64, pd, pd, pd, pd, pd, pd, pd, pd, pd, pi64]
+            L.ora_sort_by_cell.argtypes = [i64, i64, pi64, pi64]; L.ora_sort_by_cell.restype = i64
+            L.ora_deposit.argtypes = [pp, i64, pd, pd, pd, pu32, pi64, pi64, pi64]
+            L.ora_kmc.argtypes = [pp, pi64, pd, pd, pd, pi64, pi64, pi64]; L.ora_kmc.restype = ctypes.c_int
+            L.ora_kmc_single.argtypes = [pp, i64, d, d, d, u32, pi64]; L.ora_kmc_single.restype = i64
+            L.ora_products_photons.argtypes = [pp, i64, pd, pd, pd, pu32, pi64, pi64, pi64, pi64, pi64,
+                                               pi64, pi64, pd, pd, pd, pu32, pi64, i64, pi64]
+            L.ora_products_photons.restype = i64
+            L.ora_merge.argtypes = [pp, pd, pd, pd, pu32, pi64, pd, pd, pd, pu32, pi64, i64]
+            L.ora_merge.restype = i64
+            L.ora_merge_list.argtypes = [i64, pd, pd, pd, pu64, i32, pd, pd, pd, pu64]
+            L.ora_merge_list.restype = i64
+            L.ora_photon_samples.argtypes = [pp, i32, i32, i32, i64, pd, pd, pd, pd]
+            _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- primitives
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().ora_philox4x32_10(_P(c, ctypes.c_uint32), _P(k, ctypes.c_uint32), _P(out, ctypes.c_uint32))
+    return out
+
+
+def log(x: float) -> float:
+    return lib().ora_log(float(x))
+
+
+def exp(x: float) -> float:
+    return lib().ora_exp(float(x))
+
+
+def sincos2pi(u: float):
+    s = ctypes.c_double()
+    c = ctypes.c_double()
+    lib().ora_sincos2pi(float(u), ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
+
+
+def uniform_draws(seed, index, step, tag, sub, n):
+    out = np.zeros(n, dtype=np.float64)
+    lib().ora_uniform_draws(seed, index, step, tag, sub, n, _P(out, ctypes.c_double))
+    return out
+
+
+def poisson_draws(seed, index, step, tag, sub, mu, n):
+    out = np.zeros(n, dtype=np.int64)
+    lib().ora_poisson_draws(seed, index, step, tag, sub, float(mu), n, _P(out, ctypes.c_int64))
+    return out
+
+
+def kmc_single(params: Params, X0: int, k_ion: float, k_att: float, k_ph: float, index: int):
+    fired = np.zeros(3, dtype=np.int64)
+    X = lib().ora_kmc_single(ctypes.byref(params), int(X0), float(k_ion), float(k_att), float(k_ph),
+                             int(index), _P(fired, ctypes.c_int64))
+    return int(X), fired
+
+
+def photon_samples(params: Params, i: int, j: int, k: int, m: int):
+    """Photon draws of cell (i,j,k), slots 0..m-1: (Y0[m,3], kappa[m], r[m], dir[m,3])."""
+    Y0 = np.zeros((m, 3)); kap = np.zeros(m); r = np.zeros(m); d = np.zeros((m, 3))
+    lib().ora_photon_samples(ctypes.byref(params), i, j, k, m, _P(Y0, ctypes.c_double),
+                             _P(kap, ctypes.c_double), _P(r, ctypes.c_double), _P(d, ctypes.c_double))
+    return Y0, kap, r, d
+
+
+def merge_list(x, y, z, w, T):
+    x = np.ascontiguousarray(x, np.float64); y = np.ascontiguousarray(y, np.float64)
+    z = np.ascontiguousarray(z, np.float64); w = np.ascontiguousarray(w, np.uint64)
+    M = len(w)
+    ox = np.zeros(T, np.float64); oy = np.zeros(T, np.float64); oz = np.zeros(T, np.float64)
+    ow = np.zeros(T, np.uint64)
+    n = lib().ora_merge_list(M, _P(x, ctypes.c_double), _P(y, ctypes.c_double), _P(z, ctypes.c_double),
+                             _P(w, ctypes.c_uint64), int(T), _P(ox, ctypes.c_double),
+                             _P(oy, ctypes.c_double), _P(oz, ctypes.c_double), _P(ow, ctypes.c_uint64))
+    return ox[:n], oy[:n], oz[:n], ow[:n]
+
+
+from . import stages  # noqa: E402  (stage wrappers and the step composition)
+from .stages import (push, sort_by_cell, deposit, kmc, products_photons, merge, step,  # noqa: E402,F401
+                     rho_fixed)
+from .poisson import solve as solve_field  # noqa: E402,F401

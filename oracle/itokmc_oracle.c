@@ -1,0 +1,991 @@
+/*
+ * itokmc_oracle.c -- slow, plain FP64 CPU oracle of one Ito-KMC time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only the tests, the package's smoke check and the CPU
+ * baseline leg of the benchmark use it.  It shares no code, header, table or
+ * constant generator with the CUDA library; both are written independently
+ * from the same written specification (R. Marskar, "Stochastic and
+ * self-consistent 3D modeling of streamer discharge trees with Kinetic Monte
+ * Carlo", arXiv 2307.01797).
+ *
+ * Every function below follows the paper in the paper's order.  Where the
+ * paper leaves a detail open (cell-centred indexing, tie-breaks, random-number
+ * layout, particle boundary conditions ...) the reading adopted is stated at
+ * the function.  Compile with -O2 -ffp-contract=off (no fused multiply-add,
+ * no fast-math) so that every floating-point operation is a single IEEE-754
+ * round-to-nearest operation performed in the order written.
+ *
+ * Contents
+ *   Philox4x32-10 counter RNG      (Salmon et al., SC'11)
+ *   ora_log / ora_exp / sincos2pi  (argument reduction + series, own code)
+ *   Poisson sampler                (inversion; PTRS of Hoermann 1993)
+ *   push      a1+a2  -- Sec. 4.2 (CIC interpolation), Sec. 4.3 (explicit
+ *                       Euler-Maruyama, first equation), Eq. ito_kernel
+ *   sort      a3     -- stable sort by cell ("spatial binning", Sec. 5.6)
+ *   deposit   a4     -- Sec. 4.2 CIC deposition in int64 fixed point
+ *   kmc       a6     -- Sec. 3.2.3 steps 1-8 (Cao et al. hybrid, eps = inf)
+ *   products  a7     -- Sec. 4.4, Eq. w
+ *   photons   a8     -- Sec. 4.5, Eq. photon_transport; Sec. 5.1 kappa(f)
+ *   merge     a9     -- Sec. 4.6, Eq. weight_median
+ * The field solve (a5) is oracle/poisson.py (numpy, exact separable solve).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Parameters of one realization (single cubic grid).                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t n;            /* cells per axis                                 */
+    int32_t ppc;          /* target particles per cell after merge (2^k)    */
+    int32_t n_new;        /* max new computational particles per cell (64)  */
+    int32_t n_crit;       /* critical-reaction threshold N_c (5)            */
+    int32_t n_ssa;        /* max SSA steps per substep N_SSA (10)           */
+    int32_t frac_bits;    /* fixed-point bits s per axis (10)               */
+    double lo[3], hi[3];  /* domain corners, m                              */
+    double dt;            /* time step, s                                   */
+    double mu, D;         /* electron mobility m^2/Vs, diffusion m^2/s      */
+    double alpha_A, alpha_B, eta; /* alpha(E)=A exp(-B/|E|) 1/m; eta 1/m    */
+    double photon_ratio;  /* k_gamma / k_alpha (0 disables photons)         */
+    double kappa_lo, kappa_hi; /* absorption coefficient range 1/m         */
+    double eps;           /* Cao accuracy factor (INFINITY in the paper)    */
+    uint64_t seed;        /* Philox key of this realization                 */
+    uint32_t step;        /* step counter k (part of every Philox counter)  */
+    uint32_t pad;
+} ora_params;
+
+enum { TAG_INIT = 1, TAG_PUSH = 2, TAG_KMC = 3, TAG_PRODUCT = 4, TAG_PHOTON = 5 };
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC'11).  One round maps (c0,c1,c2,c3) with key        */
+/* (k0,k1) to (hi(M1 c2)^c1^k0, lo(M1 c2), hi(M0 c0)^c3^k1, lo(M0 c0)); the */
+/* key is bumped by the Weyl constants between rounds.                      */
+/* ------------------------------------------------------------------------ */
+void ora_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* A draw stream: key = seed, counter = (index, step, tag<<24|sub, block).   */
+/* Words are consumed in order; a new block is generated when the previous  */
+/* four words are used up.                                                  */
+typedef struct {
+    uint32_t key[2];
+    uint32_t ctr[4];
+    uint32_t buf[4];
+    int pos;
+} ora_stream;
+
+static void stream_init(ora_stream* s, uint64_t seed, uint32_t index, uint32_t step,
+                        uint32_t tag, uint32_t sub)
+{
+    s->key[0] = (uint32_t)seed;
+    s->key[1] = (uint32_t)(seed >> 32);
+    s->ctr[0] = index;
+    s->ctr[1] = step;
+    s->ctr[2] = (tag << 24) | sub;
+    s->ctr[3] = 0;
+    s->pos = 4;
+}
+
+static uint32_t stream_u32(ora_stream* s)
+{
+    if (s->pos == 4) {
+        ora_philox4x32_10(s->ctr, s->key, s->buf);
+        s->ctr[3] += 1;
+        s->pos = 0;
+    }
+    return s->buf[s->pos++];
+}
+
+/* Uniform in (0,1): 52 random bits k from two words, u = (2k+1) 2^-53,     */
+/* exact in double, never 0 or 1.                                           */
+static double stream_uniform(ora_stream* s)
+{
+    uint32_t a = stream_u32(s);
+    uint32_t b = stream_u32(s);
+    uint64_t k = ((uint64_t)a << 20) | (uint64_t)(b >> 12);
+    return (double)(2u * k + 1u) * 0x1p-53;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Elementary functions, written here so that CPU and GPU agree bit for bit */
+/* (libm implementations differ in the last place).                         */
+/*                                                                          */
+/* log: x = 2^e m with m in [sqrt(1/2), sqrt(2)); s = (m-1)/(m+1);          */
+/*      ln m = 2 atanh(s) = 2s + 2s z P(z), z = s^2, P = sum z^j/(2j+3)     */
+/*      (series through s^21, |s| <= 0.1716); ln x = e ln2_hi + (e ln2_lo + */
+/*      ln m), ln2 split Cody-Waite style so that e*ln2_hi is exact.        */
+/* exp: n = rint(x/ln2), r = (x - n ln2_hi) - n ln2_lo, |r| <= 0.35;        */
+/*      e^r by its Taylor series through r^13 (Horner), scaled by 2^n.      */
+/* sincos2pi(u): angle 2 pi u = (q + f) pi/2 with q = rint(4u) and          */
+/*      f = 4u - q in [-1/2, 1/2] exact; a = f pi/2, |a| <= pi/4; sin a and */
+/*      cos a by Taylor series through a^17 / a^18; quadrant swap by q.     */
+/* Only +, -, *, / and exact bit manipulation are used.                     */
+/* ------------------------------------------------------------------------ */
+/* ln2 split: HI = double(ln2) with its low 21 mantissa bits cleared (so    */
+/* e*HI is exact for |e| < 2^21); LO = ln2 - HI rounded to double.          */
+static const double ORA_LN2_HI = 6.93147180369123816490e-01;
+static const double ORA_LN2_LO = 1.90821492927058770002e-10;
+
+static double bits_to_double(uint64_t b) { double d; memcpy(&d, &b, 8); return d; }
+static uint64_t double_to_bits(double d) { uint64_t b; memcpy(&b, &d, 8); return b; }
+
+double ora_log(double x)
+{
+    if (!(x > 0.0)) return (x == 0.0) ? -INFINITY : NAN;
+    if (isinf(x)) return x;
+    int e = 0;
+    uint64_t b = double_to_bits(x);
+    int bexp = (int)((b >> 52) & 0x7ff);
+    if (bexp == 0) {                 /* subnormal: scale into normal range */
+        x = x * 0x1p54;
+        e = -54;
+        b = double_to_bits(x);
+        bexp = (int)((b >> 52) & 0x7ff);
+    }
+    e += bexp - 1023;
+    double m = bits_to_double((b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL); /* [1,2) */
+    if (m > 1.41421356237309504880) { m = m * 0.5; e += 1; }
+    double f = m - 1.0;              /* exact (Sterbenz) */
+    double s = f / (2.0 + f);
+    double z = s * s;
+    double p = 1.0 / 21.0;
+    p = p * z + 1.0 / 19.0;
+    p = p * z + 1.0 / 17.0;
+    p = p * z + 1.0 / 15.0;
+    p = p * z + 1.0 / 13.0;
+    p = p * z + 1.0 / 11.0;
+    p = p * z + 1.0 / 9.0;
+    p = p * z + 1.0 / 7.0;
+    p = p * z + 1.0 / 5.0;
+    p = p * z + 1.0 / 3.0;
+    double two_s = 2.0 * s;
+    double lnm = two_s + two_s * (z * p);
+    double de = (double)e;
+    return de * ORA_LN2_HI + (de * ORA_LN2_LO + lnm);
+}
+
+double ora_exp(double x)
+{
+    if (x != x) return x;
+    if (x > 709.78) return INFINITY;
+    if (x < -745.2) return 0.0;
+    double nd = rint(x * 1.44269504088896340736);   /* x / ln2 */
+    double r = (x - nd * ORA_LN2_HI) - nd * ORA_LN2_LO;
+    double p = 1.0 / 6227020800.0;                  /* 1/13! */
+    p = p * r + 1.0 / 479001600.0;                  /* 1/12! */
+    p = p * r + 1.0 / 39916800.0;                   /* 1/11! */
+    p = p * r + 1.0 / 3628800.0;                    /* 1/10! */
+    p = p * r + 1.0 / 362880.0;                     /* 1/9!  */
+    p = p * r + 1.0 / 40320.0;
+    p = p * r + 1.0 / 5040.0;
+    p = p * r + 1.0 / 720.0;
+    p = p * r + 1.0 / 120.0;
+    p = p * r + 1.0 / 24.0;
+    p = p * r + 1.0 / 6.0;
+    p = p * r + 0.5;
+    p = p * r + 1.0;
+    p = p * r + 1.0;
+    int n = (int)nd;
+    if (n > 1023) {                                 /* 2^n overflows alone */
+        return (p * 2.0) * bits_to_double((uint64_t)(n - 1 + 1023) << 52);
+    }
+    if (n < -1020) {                                /* subnormal result    */
+        double scaled = p * bits_to_double((uint64_t)(n + 600 + 1023) << 52);
+        return scaled * 0x1p-600;
+    }
+    return p * bits_to_double((uint64_t)(n + 1023) << 52);
+}
+
+void ora_sincos2pi(double u, double* s_out, double* c_out)
+{
+    double t = 4.0 * u;
+    double q = rint(t);
+    double f = t - q;
+    double a = f * 1.57079632679489661923;          /* pi/2 */
+    double z = a * a;
+    double sp = -1.0 / 355687428096000.0;           /* -1/17! */
+    sp = sp * z + 1.0 / 1307674368000.0;            /* 1/15!  */
+    sp = sp * z - 1.0 / 6227020800.0;               /* 1/13!  */
+    sp = sp * z + 1.0 / 39916800.0;                 /* 1/11!  */
+    sp = sp * z - 1.0 / 362880.0;
+    sp = sp * z + 1.0 / 5040.0;
+    sp = sp * z - 1.0 / 120.0;
+    sp = sp * z + 1.0 / 6.0;
+    double sa = a - a * (z * sp);
+    double cp = 1.0 / 6402373705728000.0;           /* 1/18! */
+    cp = cp * z - 1.0 / 20922789888000.0;           /* 1/16! */
+    cp = cp * z + 1.0 / 87178291200.0;              /* 1/14! */
+    cp = cp * z - 1.0 / 479001600.0;                /* 1/12! */
+    cp = cp * z + 1.0 / 3628800.0;
+    cp = cp * z - 1.0 / 40320.0;
+    cp = cp * z + 1.0 / 720.0;
+    cp = cp * z - 1.0 / 24.0;
+    cp = cp * z + 0.5;
+    double ca = 1.0 - z * cp;
+    int qi = ((int)q) & 3;
+    double s, c;
+    switch (qi) {
+    case 0: s = sa; c = ca; break;
+    case 1: s = ca; c = -sa; break;
+    case 2: s = -sa; c = -ca; break;
+    default: s = -ca; c = sa; break;
+    }
+    *s_out = s;
+    *c_out = c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Poisson sampler P(mu) used by tau-leaping (Eq. tau_leaping).             */
+/* mu <= 0: 0 with no draw.  mu < 10: inversion by sequential search (one   */
+/* uniform).  mu >= 10: PTRS, transformed rejection with squeeze (W.        */
+/* Hoermann, "The transformed rejection method for generating Poisson       */
+/* random variables", Insurance: Math. & Econ. 12, 1993), two uniforms per  */
+/* trial; log k! exact below 10, Stirling series through k^-7 above.        */
+/* ------------------------------------------------------------------------ */
+static double ora_logfact(int64_t k)
+{
+    if (k < 10) {
+        double f = 1.0;
+        for (int64_t i = 2; i <= k; ++i) f = f * (double)i;
+        return ora_log(f);
+    }
+    double x = (double)k;
+    double r = 1.0 / x;
+    double r2 = r * r;
+    double ser = 1.0 / 1680.0;
+    ser = 1.0 / 1260.0 - r2 * ser;
+    ser = 1.0 / 360.0 - r2 * ser;
+    ser = 1.0 / 12.0 - r2 * ser;
+    ser = r * ser;
+    return (((x + 0.5) * ora_log(x) - x) + 0.91893853320467274178) + ser;
+}
+
+static int64_t ora_poisson(ora_stream* s, double mu)
+{
+    if (!(mu > 0.0)) return 0;
+    if (mu < 10.0) {
+        double u = stream_uniform(s);
+        double p = ora_exp(-mu);
+        double F = p;
+        int64_t k = 0;
+        while (u > F && k < 200) {
+            k += 1;
+            p = (p * mu) / (double)k;
+            F = F + p;
+        }
+        return k;
+    }
+    double slam = sqrt(mu);
+    double loglam = ora_log(mu);
+    double b = 0.931 + 2.53 * slam;
+    double a = -0.059 + 0.02483 * b;
+    double invalpha = 1.1239 + 1.1328 / (b - 3.4);
+    double vr = 0.9277 - 3.6224 / (b - 2.0);
+    for (int it = 0; it < 1000000; ++it) {
+        double U = stream_uniform(s) - 0.5;
+        double V = stream_uniform(s);
+        double us = 0.5 - fabs(U);
+        double kd = floor(((((2.0 * a) / us) + b) * U + mu) + 0.43);
+        if (us >= 0.07 && V <= vr) return (int64_t)kd;
+        if (kd < 0.0 || (us < 0.013 && V > us)) continue;
+        double lhs = (ora_log(V) + ora_log(invalpha)) - ora_log((a / (us * us)) + b);
+        double rhs = ((-mu) + kd * loglam) - ora_logfact((int64_t)kd);
+        if (lhs <= rhs) return (int64_t)kd;
+    }
+    return -1;
+}
+
+/* Exported for the oracle's own pins: n Poisson draws from one stream.     */
+void ora_poisson_draws(uint64_t seed, uint32_t index, uint32_t step, uint32_t tag, uint32_t sub,
+                       double mu, int64_t n, int64_t* out)
+{
+    ora_stream s;
+    stream_init(&s, seed, index, step, tag, sub);
+    for (int64_t i = 0; i < n; ++i) out[i] = ora_poisson(&s, mu);
+}
+
+/* Exported: n uniforms from one stream (pins of the uniform map).          */
+void ora_uniform_draws(uint64_t seed, uint32_t index, uint32_t step, uint32_t tag, uint32_t sub,
+                       int64_t n, double* out)
+{
+    ora_stream s;
+    stream_init(&s, seed, index, step, tag, sub);
+    for (int64_t i = 0; i < n; ++i) out[i] = stream_uniform(&s);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid helpers.  Cell-centred mesh: cell i spans [lo+i h, lo+(i+1) h], its  */
+/* centre is lo+(i+1/2) h (the paper's x_i = i dx read as the centre index). */
+/* Linear index (k n + j) n + i, x fastest.                                 */
+/* ------------------------------------------------------------------------ */
+static double cell_h(const ora_params* p, int ax) { return (p->hi[ax] - p->lo[ax]) / (double)p->n; }
+
+static int64_t lin(const ora_params* p, int i, int j, int k)
+{
+    return ((int64_t)k * p->n + j) * p->n + i;
+}
+
+static int clampi(int i, int n) { return i < 0 ? 0 : (i > n - 1 ? n - 1 : i); }
+
+/* CIC stencil along one axis: u = (x-lo)/h - 1/2, i0 = floor(u), f = u-i0; */
+/* weights (1-f, f) on cells (i0, i0+1), indices folded onto [0, n-1].      */
+static void cic_axis(const ora_params* p, int ax, double x, int* ia, int* ib, double* f_out)
+{
+    double h = cell_h(p, ax);
+    double u = (x - p->lo[ax]) / h - 0.5;
+    double fl = floor(u);
+    int i0 = (int)fl;
+    *f_out = u - fl;
+    *ia = clampi(i0, p->n);
+    *ib = clampi(i0 + 1, p->n);
+}
+
+/* Cell of a position known to lie in [lo, hi): floor((x-lo)/h), top-clamped. */
+static int cell_axis(const ora_params* p, int ax, double x)
+{
+    double h = cell_h(p, ax);
+    int i = (int)floor((x - p->lo[ax]) / h);
+    return i > p->n - 1 ? p->n - 1 : (i < 0 ? 0 : i);
+}
+
+static int inside(const ora_params* p, const double X[3])
+{
+    for (int ax = 0; ax < 3; ++ax)
+        if (!(X[ax] >= p->lo[ax] && X[ax] < p->hi[ax])) return 0;
+    return 1;
+}
+
+/* Trilinear (CIC) interpolation of a cell-centred field at X (Sec. 4.2,     */
+/* V_p = v(X_p), Sec. 3.1).  Sum order: z outer, y, x inner; weight product  */
+/* (wx*wy)*wz.                                                               */
+static double interp(const ora_params* p, const double* F, const int ia[3], const int ib[3],
+                     const double f[3])
+{
+    double wx[2] = { 1.0 - f[0], f[0] };
+    double wy[2] = { 1.0 - f[1], f[1] };
+    double wz[2] = { 1.0 - f[2], f[2] };
+    int ix[2] = { ia[0], ib[0] }, iy[2] = { ia[1], ib[1] }, iz[2] = { ia[2], ib[2] };
+    double acc = 0.0;
+    for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a)
+                acc = acc + ((wx[a] * wy[b]) * wz[c]) * F[lin(p, ix[a], iy[b], iz[c])];
+    return acc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* a1+a2: interpolate E and push (explicit Euler-Maruyama, Sec. 4.3 first   */
+/* equation; Eq. ito_kernel; V_p = sgn(Z) mu E(X_p) with sgn = -1 for       */
+/* electrons, Eq. Vk1).  Normals by Box-Muller from the stream               */
+/* (index = i, step, PUSH): pairs (u1,u2), (u3,u4); N = (r1 cos, r1 sin,     */
+/* r2 cos).  x' = (x + ((-mu) E_x) dt) + sqrt(2 D dt) N_x.  A particle with  */
+/* x' outside [lo, hi) on any axis leaves through the electrode / side face  */
+/* and is removed; its weight is tallied (particle boundary condition: the   */
+/* paper states removal for photons only; electrons are absorbed likewise).  */
+/* cell_out[i] = new linear cell, or -1 if removed.                          */
+/* ------------------------------------------------------------------------ */
+void ora_push(const ora_params* p, int64_t np, const double* x, const double* y, const double* z,
+              const double* Ex, const double* Ey, const double* Ez,
+              double* xo, double* yo, double* zo, int64_t* cell_out)
+{
+    double sdt = sqrt((2.0 * p->D) * p->dt);
+    double nmu = -p->mu;
+    for (int64_t i = 0; i < np; ++i) {
+        double X[3] = { x[i], y[i], z[i] };
+        int ia[3], ib[3];
+        double f[3];
+        for (int ax = 0; ax < 3; ++ax) cic_axis(p, ax, X[ax], &ia[ax], &ib[ax], &f[ax]);
+        double Ep[3] = { interp(p, Ex, ia, ib, f), interp(p, Ey, ia, ib, f), interp(p, Ez, ia, ib, f) };
+        ora_stream s;
+        stream_init(&s, p->seed, (uint32_t)i, p->step, TAG_PUSH, 0);
+        double u1 = stream_uniform(&s), u2 = stream_uniform(&s);
+        double u3 = stream_uniform(&s), u4 = stream_uniform(&s);
+        double r1 = sqrt(-2.0 * ora_log(u1)), r2 = sqrt(-2.0 * ora_log(u3));
+        double s1, c1, s2, c2;
+        ora_sincos2pi(u2, &s1, &c1);
+        ora_sincos2pi(u4, &s2, &c2);
+        double N[3] = { r1 * c1, r1 * s1, r2 * c2 };
+        double Xn[3];
+        for (int ax = 0; ax < 3; ++ax) Xn[ax] = (X[ax] + (nmu * Ep[ax]) * p->dt) + sdt * N[ax];
+        xo[i] = Xn[0]; yo[i] = Xn[1]; zo[i] = Xn[2];
+        if (inside(p, Xn))
+            cell_out[i] = lin(p, cell_axis(p, 0, Xn[0]), cell_axis(p, 1, Xn[1]), cell_axis(p, 2, Xn[2]));
+        else
+            cell_out[i] = -1;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* a3: stable sort by cell; removed particles (cell -1) dropped.  The        */
+/* canonical order is (cell, previous array index).  Writes the permutation  */
+/* and returns the number kept.  Written as a counting sort (a stable sort). */
+/* ------------------------------------------------------------------------ */
+int64_t ora_sort_by_cell(int64_t np, int64_t ncell, const int64_t* cell, int64_t* perm)
+{
+    int64_t* cnt = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < np; ++i)
+        if (cell[i] >= 0) cnt[cell[i] + 1] += 1;
+    for (int64_t c = 0; c < ncell; ++c) cnt[c + 1] += cnt[c];
+    int64_t kept = cnt[ncell];
+    for (int64_t i = 0; i < np; ++i)
+        if (cell[i] >= 0) perm[cnt[cell[i]]++] = i;
+    free(cnt);
+    return kept;
+}
+
+/* ------------------------------------------------------------------------ */
+/* a4: CIC deposition (Sec. 4.2, W_cic(x) = 1-|x|) in int64 fixed point.     */
+/* Per axis a = floor(f 2^s) with f from cic_axis; axis weights (2^s - a, a) */
+/* so the 8 contributions w*Ax*Ay*Az sum to w 2^(3s) exactly.  ne_fix is in  */
+/* units of 2^-3s electrons per cell.  Xe[c] = sum of w over the particles   */
+/* whose cell is c (the KMC state X_e of Sec. 3.2).                          */
+/* ------------------------------------------------------------------------ */
+void ora_deposit(const ora_params* p, int64_t np, const double* x, const double* y, const double* z,
+                 const uint32_t* w, const int64_t* cell, int64_t* ne_fix, int64_t* Xe)
+{
+    int s = p->frac_bits;
+    int64_t one = (int64_t)1 << s;
+    double scale = (double)one;
+    for (int64_t i = 0; i < np; ++i) {
+        double X[3] = { x[i], y[i], z[i] };
+        int ia[3], ib[3];
+        int64_t A[3][2];
+        for (int ax = 0; ax < 3; ++ax) {
+            double f;
+            cic_axis(p, ax, X[ax], &ia[ax], &ib[ax], &f);
+            int64_t a = (int64_t)floor(f * scale);
+            A[ax][0] = one - a;
+            A[ax][1] = a;
+        }
+        int ix[2] = { ia[0], ib[0] }, iy[2] = { ia[1], ib[1] }, iz[2] = { ia[2], ib[2] };
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a)
+                    ne_fix[lin(p, ix[a], iy[b], iz[c])] += (int64_t)w[i] * A[0][a] * A[1][b] * A[2][c];
+        Xe[cell[i]] += (int64_t)w[i];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* a6: per-cell KMC, Sec. 3.2.3 steps 1-8 (Cao, Gillespie, Petzold 2005,     */
+/* 2006) for the first-order network of Table air_reactions restricted to    */
+/*   r=0 ionization  e -> 2e + M+   a0 = k_alpha X   nu_e = +1               */
+/*   r=1 attachment  e -> M-        a1 = k_eta X     nu_e = -1               */
+/*   r=2 photon      e -> e + gamma a2 = k_gamma X   nu_e =  0               */
+/* with k_alpha = alpha(|E|) mu |E|, k_eta = eta mu |E|, k_gamma =           */
+/* photon_ratio k_alpha (Sec. 5.1 structure).  Readings: critical set =     */
+/* reactions within N_c firings of exhausting a reactant (only attachment,   */
+/* when X < N_c); dt_c = -ln(u)/A_c; dt_nc from the eps formula (infinite    */
+/* for eps = inf); the SSA switch (A dtau <= 1, dtau = min(dt - tau, dt_nc)) */
+/* is tested before the critical time is drawn, as in the cited Cao et al.   */
+/* (2006) procedure -- testing it after a critical draw that did not fire    */
+/* would count critical firings twice; a rejected substep sets dt_nc =       */
+/* dtau/2 and redoes step 5 with fresh draws (the critical time is kept);    */
+/* the SSA branch runs at most N_SSA events and advances tau by the full     */
+/* dtau if the next event falls beyond it, else by the time of the last      */
+/* event.  Draws come from the stream (index = cell, step, KMC).             */
+/* Outputs per cell: firings of each reaction.                               */
+/* ------------------------------------------------------------------------ */
+static int kmc_cell(const ora_params* p, ora_stream* s, int64_t X0, double kr[3],
+                    int64_t fired[3])
+{
+    static const int nu[3] = { +1, -1, 0 };
+    int64_t X = X0;
+    double dt = p->dt;
+    double tau = 0.0;
+    fired[0] = fired[1] = fired[2] = 0;
+    for (int guard = 0; guard < 100000; ++guard) {
+        if (!(tau < dt)) return 0;
+        double xd = (double)X;
+        double a[3] = { kr[0] * xd, kr[1] * xd, kr[2] * xd };
+        double A = (a[0] + a[1]) + a[2];
+        if (!(A > 0.0)) return 0;
+        /* step 1: partition (only attachment can exhaust its reactant) */
+        int crit[3] = { 0, X < (int64_t)p->n_crit, 0 };
+        /* step 2 */
+        double Ac = 0.0;
+        for (int r = 0; r < 3; ++r) if (crit[r]) Ac = Ac + a[r];
+        /* step 4: non-critical step bound from eps (infinite for eps = inf) */
+        double dtnc = INFINITY;
+        if (!isinf(p->eps)) {
+            double xi = 0.0, sig2 = 0.0;
+            int any = 0;
+            for (int r = 0; r < 3; ++r) {
+                if (crit[r]) continue;
+                any = 1;
+                xi = xi + (double)nu[r] * a[r];
+                sig2 = sig2 + (double)(nu[r] * nu[r]) * a[r];
+            }
+            if (any) {
+                double num = p->eps * xd;
+                if (num < 1.0) num = 1.0;
+                double t1 = (xi != 0.0) ? num / fabs(xi) : INFINITY;
+                double t2 = (sig2 != 0.0) ? (num * num) / sig2 : INFINITY;
+                dtnc = t1 < t2 ? t1 : t2;
+            }
+        }
+        /* step 3 is drawn lazily (only when a leap is taken) and kept across */
+        /* rejections ("return to step 5").                                   */
+        double dtc = -1.0;
+        for (int rej = 0; rej < 10000; ++rej) {
+            double rem = dt - tau;
+            double dtau = dtnc < rem ? dtnc : rem;
+            int64_t k[3] = { 0, 0, 0 };
+            double adv;
+            if (A * dtau <= 1.0) {
+                /* step 6b exception, checked before the critical draw as in  */
+                /* Cao et al. (2006): SSA on the whole network, at most N_SSA */
+                /* events within dtau; tau advances by dtau if the next event */
+                /* falls beyond it, else by the time of the last event.       */
+                int64_t Xs = X;
+                double t = 0.0;
+                for (int ev = 0; ev < p->n_ssa; ++ev) {
+                    double xs = (double)Xs;
+                    double as[3] = { kr[0] * xs, kr[1] * xs, kr[2] * xs };
+                    double As = (as[0] + as[1]) + as[2];
+                    if (!(As > 0.0)) { t = dtau; break; }
+                    double dte = (-ora_log(stream_uniform(s))) / As;
+                    if (t + dte > dtau) { t = dtau; break; }
+                    t = t + dte;
+                    double target = stream_uniform(s) * As, cum = 0.0;
+                    int j = 2;
+                    for (int r = 0; r < 3; ++r) {
+                        cum = cum + as[r];
+                        if (cum > target) { j = r; break; }
+                    }
+                    k[j] += 1;
+                    Xs += nu[j];
+                }
+                adv = t;
+            } else {
+                /* step 3: time to the next critical reaction */
+                if (dtc < 0.0)
+                    dtc = (Ac > 0.0) ? (-ora_log(stream_uniform(s))) / Ac : INFINITY;
+                if (dtc < dtnc && dtc < rem) {
+                    /* step 6a: one critical reaction fires, non-critical leap */
+                    dtau = dtc;
+                    double target = stream_uniform(s) * Ac, cum = 0.0;
+                    int rc = -1, last = -1;
+                    for (int r = 0; r < 3; ++r) {
+                        if (!crit[r]) continue;
+                        last = r;
+                        cum = cum + a[r];
+                        if (cum > target) { rc = r; break; }
+                    }
+                    if (rc < 0) rc = last;
+                    k[rc] += 1;
+                }
+                /* step 6a/6b: non-critical tau-leap over dtau (Eq. tau_leaping) */
+                for (int r = 0; r < 3; ++r)
+                    if (!crit[r]) k[r] += ora_poisson(s, a[r] * dtau);
+                adv = dtau;
+            }
+            int64_t Xn = X + k[0] - k[1];
+            if (Xn < 0) {                 /* step 7a: reject, halve, redo step 5 */
+                dtnc = dtau * 0.5;
+                continue;
+            }
+            /* step 7b: accept */
+            X = Xn;
+            fired[0] += k[0]; fired[1] += k[1]; fired[2] += k[2];
+            if (adv >= rem) tau = dt; else tau = tau + adv;
+            goto next_substep;
+        }
+        return -1;
+    next_substep:;
+    }
+    return -1;
+}
+
+/* Reaction frequencies from the cell-centred field (Sec. 5.1, LFA). */
+static void rates_at(const ora_params* p, double ex, double ey, double ez, double kr[3])
+{
+    double Em = sqrt((ex * ex + ey * ey) + ez * ez);
+    double ve = p->mu * Em;
+    double alpha = (Em > 0.0) ? p->alpha_A * ora_exp(-(p->alpha_B / Em)) : 0.0;
+    kr[0] = alpha * ve;
+    kr[1] = p->eta * ve;
+    kr[2] = p->photon_ratio * kr[0];
+}
+
+/* Returns 0, or -1 if some cell did not finish (iteration guard). */
+int ora_kmc(const ora_params* p, const int64_t* Xe, const double* Ex, const double* Ey,
+            const double* Ez, int64_t* n_ion, int64_t* n_att, int64_t* n_ph)
+{
+    int64_t ncell = (int64_t)p->n * p->n * p->n;
+    int status = 0;
+    for (int64_t c = 0; c < ncell; ++c) {
+        n_ion[c] = n_att[c] = n_ph[c] = 0;
+        if (Xe[c] <= 0) continue;
+        double kr[3];
+        rates_at(p, Ex[c], Ey[c], Ez[c], kr);
+        ora_stream s;
+        stream_init(&s, p->seed, (uint32_t)c, p->step, TAG_KMC, 0);
+        int64_t fired[3];
+        if (kmc_cell(p, &s, Xe[c], kr, fired) != 0) status = -1;
+        n_ion[c] = fired[0]; n_att[c] = fired[1]; n_ph[c] = fired[2];
+    }
+    return status;
+}
+
+/* Exported for the oracle's pins: a single cell, given rates, X0 and a     */
+/* stream index; returns the final X, firings in fired[3].                  */
+int64_t ora_kmc_single(const ora_params* p, int64_t X0, double k_ion, double k_att, double k_ph,
+                       uint32_t index, int64_t* fired)
+{
+    double kr[3] = { k_ion, k_att, k_ph };
+    ora_stream s;
+    stream_init(&s, p->seed, index, p->step, TAG_KMC, 0);
+    if (kmc_cell(p, &s, X0, kr, fired) != 0) return -1;
+    return X0 + fired[0] - fired[1];
+}
+
+/* ------------------------------------------------------------------------ */
+/* a7 + a8: KMC-particle coupling (Sec. 4.4) and photons (Sec. 4.5).         */
+/* Gain dN > 0 in cell c: m = min(dN, N_new) new particles, weight           */
+/* dN div m (Eq. w), the remainder on the first; positions uniform in the    */
+/* cell, x = lo + (i + u) h, stream (c, step, PRODUCT, slot j).  Loss L > 0: */
+/* removed from the cell's existing particles by systematic integer          */
+/* sampling over cumulative weights C_p (W = sum w): particle p loses        */
+/* floor((C_p L + R)/W) - floor((C_{p-1} L + R)/W), R = (64-bit draw) mod W  */
+/* from stream (c, step, PRODUCT, N_new) -- exact, unbiased (each physical   */
+/* electron removed with probability L/W).  Photons: m = min(N_gamma, N_new) */
+/* superphotons with the same weight rule; stream (c, step, PHOTON, j):     */
+/* emission point (3 uniforms), kappa = K1 (K2/K1)^U (Sec. 5.1), r =         */
+/* -ln(u)/kappa (exponential with parameter kappa), c_z = 2u-1, phi = 2 pi u,*/
+/* c_xy = sqrt((1-c_z)(1+c_z)) (cos, sin); Y = Y0 + r c (Eq.                 */
+/* photon_transport).  Y inside [lo,hi)^3: photoionization creates an        */
+/* electron of the photon's weight at Y and an M+ in Y's cell; otherwise the */
+/* photon is lost.  New particles are listed by (source cell, products then  */
+/* photoelectrons, slot).                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double* x; double* y; double* z; uint32_t* w; int64_t* cell;
+    int64_t n, cap;
+} ora_plist;
+
+static int plist_push(ora_plist* L, double x, double y, double z, uint64_t w, int64_t cell)
+{
+    if (L->n >= L->cap) return -1;
+    if (w > 0xffffffffull) return -2;
+    L->x[L->n] = x; L->y[L->n] = y; L->z[L->n] = z; L->w[L->n] = (uint32_t)w; L->cell[L->n] = cell;
+    L->n += 1;
+    return 0;
+}
+
+/* One superphoton of cell c, slot j (stream (c, step, PHOTON, j)):          */
+/* emission point Y0 uniform in the cell, absorption coefficient kappa,      */
+/* absorption distance r and unit direction dir.                             */
+static void photon_sample(const ora_params* p, int64_t c, uint32_t j, const int ijk[3], double lnK,
+                          double Y0[3], double* kappa_out, double* r_out, double dir[3])
+{
+    ora_stream s;
+    stream_init(&s, p->seed, (uint32_t)c, p->step, TAG_PHOTON, j);
+    for (int ax = 0; ax < 3; ++ax) {
+        double u = stream_uniform(&s);
+        Y0[ax] = p->lo[ax] + ((double)ijk[ax] + u) * cell_h(p, ax);
+    }
+    double kappa = p->kappa_lo * ora_exp(stream_uniform(&s) * lnK);
+    double r = (-ora_log(stream_uniform(&s))) / kappa;
+    double cz = 2.0 * stream_uniform(&s) - 1.0;
+    double sphi, cphi;
+    ora_sincos2pi(stream_uniform(&s), &sphi, &cphi);
+    double st = sqrt((1.0 - cz) * (1.0 + cz));
+    dir[0] = st * cphi;
+    dir[1] = st * sphi;
+    dir[2] = cz;
+    *kappa_out = kappa;
+    *r_out = r;
+}
+
+/* Exported for the pins: the photon draws of cells c (given as i,j,k) for  */
+/* slots 0..m-1: Y0 (3m), kappa (m), r (m), dir (3m).                       */
+void ora_photon_samples(const ora_params* p, int32_t i, int32_t j, int32_t k, int64_t m,
+                        double* Y0, double* kappa, double* r, double* dir)
+{
+    int ijk[3] = { i, j, k };
+    int64_t c = lin(p, i, j, k);
+    double lnK = ora_log(p->kappa_hi / p->kappa_lo);
+    for (int64_t q = 0; q < m; ++q)
+        photon_sample(p, c, (uint32_t)q, ijk, lnK, Y0 + 3 * q, kappa + q, r + q, dir + 3 * q);
+}
+
+/* Particles: sorted canonical arrays (x,y,z,w,cell) of length np with       */
+/* cell_start[ncell+1].  Weights w are updated in place for losses.          */
+/* New particles are written to (nx..ncell_new) up to cap_new; returns their */
+/* count, -1 if capacity is exceeded, -2 on weight overflow.                 */
+/* Npos/Nneg are updated (+ionizations, +attachments, +photoionizations).    */
+int64_t ora_products_photons(const ora_params* p, int64_t np, const double* x, const double* y,
+                             const double* z, uint32_t* w, const int64_t* cell_start,
+                             const int64_t* Xe, const int64_t* n_ion, const int64_t* n_att,
+                             const int64_t* n_ph, int64_t* Npos, int64_t* Nneg,
+                             double* nx, double* ny, double* nz, uint32_t* nw, int64_t* ncell_new,
+                             int64_t cap_new, int64_t* lost_photon_weight)
+{
+    (void)np; (void)x; (void)y; (void)z;
+    int64_t ncell = (int64_t)p->n * p->n * p->n;
+    ora_plist L = { nx, ny, nz, nw, ncell_new, 0, cap_new };
+    int64_t lost = 0;
+    double h[3] = { cell_h(p, 0), cell_h(p, 1), cell_h(p, 2) };
+    double lnK = ora_log(p->kappa_hi / p->kappa_lo);
+    for (int64_t c = 0; c < ncell; ++c) {
+        int ci = (int)(c % p->n), cj = (int)((c / p->n) % p->n), ck = (int)(c / ((int64_t)p->n * p->n));
+        int ijk[3] = { ci, cj, ck };
+        int64_t dN = n_ion[c] - n_att[c];
+        Npos[c] += n_ion[c];
+        Nneg[c] += n_att[c];
+        if (dN > 0) {
+            int64_t m = dN < p->n_new ? dN : p->n_new;
+            int64_t wq = dN / m, rem = dN % m;
+            for (int64_t j = 0; j < m; ++j) {
+                ora_stream s;
+                stream_init(&s, p->seed, (uint32_t)c, p->step, TAG_PRODUCT, (uint32_t)j);
+                double P[3];
+                for (int ax = 0; ax < 3; ++ax) {
+                    double u = stream_uniform(&s);
+                    P[ax] = p->lo[ax] + ((double)ijk[ax] + u) * h[ax];
+                }
+                int rc = plist_push(&L, P[0], P[1], P[2], (uint64_t)(wq + (j == 0 ? rem : 0)), c);
+                if (rc) return rc;
+            }
+        } else if (dN < 0) {
+            uint64_t Ls = (uint64_t)(-dN);
+            uint64_t W = (uint64_t)Xe[c];
+            ora_stream s;
+            stream_init(&s, p->seed, (uint32_t)c, p->step, TAG_PRODUCT, (uint32_t)p->n_new);
+            uint32_t a = stream_u32(&s), b = stream_u32(&s);
+            uint64_t R = (((uint64_t)a << 32) | b) % W;
+            unsigned __int128 C = 0;
+            for (int64_t q = cell_start[c]; q < cell_start[c + 1]; ++q) {
+                unsigned __int128 before = (C * Ls + R) / W;
+                C += w[q];
+                unsigned __int128 after = (C * Ls + R) / W;
+                w[q] = (uint32_t)(w[q] - (uint64_t)(after - before));
+            }
+        }
+        if (n_ph[c] > 0) {
+            int64_t G = n_ph[c];
+            int64_t m = G < p->n_new ? G : p->n_new;
+            int64_t wq = G / m, rem = G % m;
+            for (int64_t j = 0; j < m; ++j) {
+                int64_t wj = wq + (j == 0 ? rem : 0);
+                double Y0[3], kappa, r, dir[3], Ya[3];
+                photon_sample(p, c, (uint32_t)j, ijk, lnK, Y0, &kappa, &r, dir);
+                for (int ax = 0; ax < 3; ++ax) Ya[ax] = Y0[ax] + r * dir[ax];
+                if (inside(p, Ya)) {
+                    int64_t dc = lin(p, cell_axis(p, 0, Ya[0]), cell_axis(p, 1, Ya[1]), cell_axis(p, 2, Ya[2]));
+                    Npos[dc] += wj;
+                    int rc = plist_push(&L, Ya[0], Ya[1], Ya[2], (uint64_t)wj, dc);
+                    if (rc) return rc;
+                } else {
+                    lost += wj;
+                }
+            }
+        }
+    }
+    *lost_photon_weight = lost;
+    return L.n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* a9: superparticle merge/split per cell (Sec. 4.6).  The cell's list (its  */
+/* surviving particles in canonical order, then its new particles in list    */
+/* order) is split level by level, T = ppc leaves: a node of weight >= 2 is  */
+/* split; the axis is that of the largest bounding-box extent (ties: lowest  */
+/* axis); the node is stably sorted by that coordinate; the median p' is the */
+/* first index with sum_{<p'} w + w_p' > sum_{>p'} w (Eq. weight_median,     */
+/* read with p' >= 1); a physical median (w = 1) joins the lighter side      */
+/* (tie: left); a superparticle median is split into left weight             */
+/* ceil(W/2) - W_left and the rest, zero-weight parts dropped.  Each leaf    */
+/* becomes one particle: weight sum, weight-averaged position summed in list */
+/* order.  Leaves are emitted left to right.                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct { double X[3]; uint64_t w; int64_t ord; } ora_mp;
+
+static int cmp_axis;
+static int cmp_mp(const void* A, const void* B)
+{
+    const ora_mp* a = (const ora_mp*)A;
+    const ora_mp* b = (const ora_mp*)B;
+    double xa = a->X[cmp_axis], xb = b->X[cmp_axis];
+    if (xa < xb) return -1;
+    if (xa > xb) return 1;
+    return (a->ord < b->ord) ? -1 : (a->ord > b->ord);
+}
+
+/* Splits node [P, P+M) (array of M particles) into left/right arrays.      */
+static void split_node(ora_mp* P, int64_t M, ora_mp* left, int64_t* nl, ora_mp* right, int64_t* nr)
+{
+    double lo[3], hi[3];
+    for (int ax = 0; ax < 3; ++ax) { lo[ax] = P[0].X[ax]; hi[ax] = P[0].X[ax]; }
+    for (int64_t q = 1; q < M; ++q)
+        for (int ax = 0; ax < 3; ++ax) {
+            if (P[q].X[ax] < lo[ax]) lo[ax] = P[q].X[ax];
+            if (P[q].X[ax] > hi[ax]) hi[ax] = P[q].X[ax];
+        }
+    int axis = 0;
+    double ext[3] = { hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2] };
+    if (ext[1] > ext[axis]) axis = 1;
+    if (ext[2] > ext[axis]) axis = 2;
+    for (int64_t q = 0; q < M; ++q) P[q].ord = q;       /* stability key */
+    cmp_axis = axis;
+    qsort(P, (size_t)M, sizeof(ora_mp), cmp_mp);
+    uint64_t W = 0;
+    for (int64_t q = 0; q < M; ++q) W += P[q].w;
+    uint64_t C = 0;
+    int64_t pm = M - 1;
+    for (int64_t q = 0; q < M; ++q) {
+        C += P[q].w;
+        if (2 * C > W) { pm = q; break; }
+    }
+    uint64_t WL = C - P[pm].w;
+    uint64_t WR = W - C;
+    *nl = 0; *nr = 0;
+    for (int64_t q = 0; q < pm; ++q) left[(*nl)++] = P[q];
+    if (P[pm].w == 1) {
+        if (WL <= WR) left[(*nl)++] = P[pm];
+        else right[(*nr)++] = P[pm];
+    } else {
+        uint64_t a = (W + 1) / 2 - WL;
+        uint64_t b = P[pm].w - a;
+        if (a > 0) { ora_mp m = P[pm]; m.w = a; left[(*nl)++] = m; }
+        if (b > 0) { ora_mp m = P[pm]; m.w = b; right[(*nr)++] = m; }
+    }
+    for (int64_t q = pm + 1; q < M; ++q) right[(*nr)++] = P[q];
+}
+
+/* Merge one cell's list in[0..M) into at most T leaves written to out.     */
+/* Returns the number of leaves.                                             */
+static int64_t merge_cell(const ora_mp* in, int64_t M, int T, ora_mp* out)
+{
+    /* nodes stored as consecutive ranges in a work buffer; each split may   */
+    /* add one particle, so capacity M + T suffices.                         */
+    int64_t cap = M + T + 1;
+    ora_mp* cur = (ora_mp*)malloc(sizeof(ora_mp) * (size_t)cap);
+    ora_mp* nxt = (ora_mp*)malloc(sizeof(ora_mp) * (size_t)cap);
+    ora_mp* tl = (ora_mp*)malloc(sizeof(ora_mp) * (size_t)cap);
+    ora_mp* tr = (ora_mp*)malloc(sizeof(ora_mp) * (size_t)cap);
+    int64_t* nb = (int64_t*)malloc(sizeof(int64_t) * (size_t)(T + 1));
+    int64_t* nb2 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(T + 1));
+    memcpy(cur, in, sizeof(ora_mp) * (size_t)M);
+    int nnodes = 1;
+    nb[0] = 0; nb[1] = M;
+    for (int level = 1; level < T; level *= 2) {
+        int64_t fill = 0;
+        int nn = 0;
+        nb2[0] = 0;
+        for (int d = 0; d < nnodes; ++d) {
+            ora_mp* node = cur + nb[d];
+            int64_t m = nb[d + 1] - nb[d];
+            uint64_t W = 0;
+            for (int64_t q = 0; q < m; ++q) W += node[q].w;
+            if (W >= 2) {
+                int64_t nl, nr;
+                split_node(node, m, tl, &nl, tr, &nr);
+                memcpy(nxt + fill, tl, sizeof(ora_mp) * (size_t)nl); fill += nl; nb2[++nn] = fill;
+                memcpy(nxt + fill, tr, sizeof(ora_mp) * (size_t)nr); fill += nr; nb2[++nn] = fill;
+            } else {
+                memcpy(nxt + fill, node, sizeof(ora_mp) * (size_t)m); fill += m; nb2[++nn] = fill;
+            }
+        }
+        ora_mp* t = cur; cur = nxt; nxt = t;
+        int64_t* tb = nb; nb = nb2; nb2 = tb;
+        nnodes = nn;
+    }
+    for (int d = 0; d < nnodes; ++d) {
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        uint64_t W = 0;
+        for (int64_t q = nb[d]; q < nb[d + 1]; ++q) {
+            double wd = (double)cur[q].w;
+            sx = sx + wd * cur[q].X[0];
+            sy = sy + wd * cur[q].X[1];
+            sz = sz + wd * cur[q].X[2];
+            W += cur[q].w;
+        }
+        double Wd = (double)W;
+        out[d].X[0] = sx / Wd; out[d].X[1] = sy / Wd; out[d].X[2] = sz / Wd;
+        out[d].w = W;
+        out[d].ord = d;
+    }
+    free(cur); free(nxt); free(tl); free(tr); free(nb); free(nb2);
+    return nnodes;
+}
+
+/* Merge/split every cell.  Input: canonical sorted list (existing then new  */
+/* per cell, already grouped by cell: in_start[ncell+1]).  Zero-weight       */
+/* particles are skipped.  Output arrays need capacity sum min(W_c, ppc).    */
+/* Returns the count, or -1 on capacity, -2 on weight overflow.             */
+int64_t ora_merge(const ora_params* p, const double* x, const double* y, const double* z,
+                  const uint32_t* w, const int64_t* in_start,
+                  double* ox, double* oy, double* oz, uint32_t* ow, int64_t* ocell, int64_t cap)
+{
+    int64_t ncell = (int64_t)p->n * p->n * p->n;
+    int T = p->ppc;
+    int64_t nout = 0;
+    int64_t maxm = 0;
+    for (int64_t c = 0; c < ncell; ++c) {
+        int64_t m = in_start[c + 1] - in_start[c];
+        if (m > maxm) maxm = m;
+    }
+    ora_mp* buf = (ora_mp*)malloc(sizeof(ora_mp) * (size_t)(maxm + 1));
+    ora_mp* leaves = (ora_mp*)malloc(sizeof(ora_mp) * (size_t)(T + 1));
+    for (int64_t c = 0; c < ncell; ++c) {
+        int64_t M = 0;
+        for (int64_t q = in_start[c]; q < in_start[c + 1]; ++q) {
+            if (w[q] == 0) continue;
+            buf[M].X[0] = x[q]; buf[M].X[1] = y[q]; buf[M].X[2] = z[q];
+            buf[M].w = w[q]; buf[M].ord = M;
+            M += 1;
+        }
+        if (M == 0) continue;
+        int64_t nl = merge_cell(buf, M, T, leaves);
+        for (int64_t d = 0; d < nl; ++d) {
+            if (nout >= cap) { free(buf); free(leaves); return -1; }
+            if (leaves[d].w > 0xffffffffull) { free(buf); free(leaves); return -2; }
+            ox[nout] = leaves[d].X[0]; oy[nout] = leaves[d].X[1]; oz[nout] = leaves[d].X[2];
+            ow[nout] = (uint32_t)leaves[d].w; ocell[nout] = c;
+            nout += 1;
+        }
+    }
+    free(buf); free(leaves);
+    return nout;
+}
+
+/* Exported for the pins: merge one list (positions x,y,z, weights w) into  */
+/* at most T leaves.  Returns the leaf count.                               */
+int64_t ora_merge_list(int64_t M, const double* x, const double* y, const double* z,
+                       const uint64_t* w, int32_t T, double* ox, double* oy, double* oz, uint64_t* ow)
+{
+    ora_mp* in = (ora_mp*)malloc(sizeof(ora_mp) * (size_t)(M + 1));
+    ora_mp* out = (ora_mp*)malloc(sizeof(ora_mp) * (size_t)(T + 1));
+    int64_t K = 0;
+    for (int64_t q = 0; q < M; ++q) {
+        if (w[q] == 0) continue;
+        in[K].X[0] = x[q]; in[K].X[1] = y[q]; in[K].X[2] = z[q]; in[K].w = w[q]; in[K].ord = K;
+        K += 1;
+    }
+    int64_t nl = (K > 0) ? merge_cell(in, K, T, out) : 0;
+    for (int64_t d = 0; d < nl; ++d) {
+        ox[d] = out[d].X[0]; oy[d] = out[d].X[1]; oz[d] = out[d].X[2]; ow[d] = out[d].w;
+    }
+    free(in); free(out);
+    return nl;
+}

@@ -1,0 +1,167 @@
+"""Stage wrappers and the full-step composition of the oracle.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  The arithmetic of every
+stage is in ``itokmc_oracle.c``; this module marshals numpy arrays and chains the
+stages in the order of one time step:
+
+  push (a1+a2) -> stable sort by cell (a3) -> deposit ne_fix, X_e (a4)
+  -> rho snapshot -> KMC (a6) -> products and photons (a7, a8)
+  -> merge/split (a9)
+
+with the field for the next step solved from the rho snapshot (a5,
+``poisson.py``).  The order is the Godunov split of the paper's final algorithm
+(Sec. 4.7: transport, then chemistry, then superparticle management) with the
+explicit Euler-Maruyama push of Sec. 4.3.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import Params, _P, lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def push(p: Params, x, y, z, E):
+    """a1+a2.  E = (Ex, Ey, Ez) cell-centred arrays of n^3 (x fastest).
+    Returns (xo, yo, zo, cell) with cell = -1 for removed particles."""
+    x, y, z = _d(x), _d(y), _d(z)
+    Ex, Ey, Ez = (_d(np.asarray(e).ravel()) for e in E)
+    n = len(x)
+    xo, yo, zo = np.empty(n), np.empty(n), np.empty(n)
+    cell = np.empty(n, dtype=np.int64)
+    lib().ora_push(ctypes.byref(p), n, _P(x, ctypes.c_double), _P(y, ctypes.c_double),
+                   _P(z, ctypes.c_double), _P(Ex, ctypes.c_double), _P(Ey, ctypes.c_double),
+                   _P(Ez, ctypes.c_double), _P(xo, ctypes.c_double), _P(yo, ctypes.c_double),
+                   _P(zo, ctypes.c_double), _P(cell, ctypes.c_int64))
+    return xo, yo, zo, cell
+
+
+def sort_by_cell(cell, ncell: int):
+    """a3.  Stable permutation by cell; removed (-1) dropped."""
+    cell = np.ascontiguousarray(cell, dtype=np.int64)
+    perm = np.empty(len(cell), dtype=np.int64)
+    k = lib().ora_sort_by_cell(len(cell), int(ncell), _P(cell, ctypes.c_int64), _P(perm, ctypes.c_int64))
+    return perm[:k]
+
+
+def deposit(p: Params, x, y, z, w, cell):
+    """a4.  Returns (ne_fix, Xe), int64 arrays of n^3."""
+    ncell = p.n ** 3
+    x, y, z = _d(x), _d(y), _d(z)
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    cell = np.ascontiguousarray(cell, dtype=np.int64)
+    ne = np.zeros(ncell, dtype=np.int64)
+    Xe = np.zeros(ncell, dtype=np.int64)
+    lib().ora_deposit(ctypes.byref(p), len(x), _P(x, ctypes.c_double), _P(y, ctypes.c_double),
+                      _P(z, ctypes.c_double), _P(w, ctypes.c_uint32), _P(cell, ctypes.c_int64),
+                      _P(ne, ctypes.c_int64), _P(Xe, ctypes.c_int64))
+    return ne, Xe
+
+
+def kmc(p: Params, Xe, E):
+    """a6.  Returns (n_ion, n_att, n_ph) firings per cell."""
+    ncell = p.n ** 3
+    Xe = np.ascontiguousarray(Xe, dtype=np.int64)
+    Ex, Ey, Ez = (_d(np.asarray(e).ravel()) for e in E)
+    a, b, c = (np.zeros(ncell, dtype=np.int64) for _ in range(3))
+    st = lib().ora_kmc(ctypes.byref(p), _P(Xe, ctypes.c_int64), _P(Ex, ctypes.c_double),
+                       _P(Ey, ctypes.c_double), _P(Ez, ctypes.c_double), _P(a, ctypes.c_int64),
+                       _P(b, ctypes.c_int64), _P(c, ctypes.c_int64))
+    if st != 0:
+        raise RuntimeError("oracle KMC iteration guard hit")
+    return a, b, c
+
+
+def cell_start_of(cell, ncell):
+    return np.searchsorted(cell, np.arange(ncell + 1), side="left").astype(np.int64)
+
+
+def products_photons(p: Params, x, y, z, w, cell, Xe, fired, Npos, Nneg):
+    """a7 + a8.  w (uint32) is updated in place for losses; Npos/Nneg in place.
+    Returns (new particle arrays (x, y, z, w, cell), lost photon weight)."""
+    ncell = p.n ** 3
+    cs = cell_start_of(cell, ncell)
+    n_ion, n_att, n_ph = (np.ascontiguousarray(f, dtype=np.int64) for f in fired)
+    cap = int(np.minimum(n_ion + n_ph, 2 * p.n_new).sum()) + 16
+    nx, ny, nz = np.empty(cap), np.empty(cap), np.empty(cap)
+    nw = np.empty(cap, dtype=np.uint32)
+    nc = np.empty(cap, dtype=np.int64)
+    lost = ctypes.c_int64(0)
+    x, y, z = _d(x), _d(y), _d(z)
+    Xe = np.ascontiguousarray(Xe, dtype=np.int64)
+    assert w.dtype == np.uint32 and w.flags.c_contiguous
+    assert Npos.dtype == np.int64 and Nneg.dtype == np.int64
+    k = lib().ora_products_photons(ctypes.byref(p), len(x), _P(x, ctypes.c_double), _P(y, ctypes.c_double),
+                                   _P(z, ctypes.c_double), _P(w, ctypes.c_uint32), _P(cs, ctypes.c_int64),
+                                   _P(Xe, ctypes.c_int64), _P(n_ion, ctypes.c_int64),
+                                   _P(n_att, ctypes.c_int64), _P(n_ph, ctypes.c_int64),
+                                   _P(Npos, ctypes.c_int64), _P(Nneg, ctypes.c_int64),
+                                   _P(nx, ctypes.c_double), _P(ny, ctypes.c_double), _P(nz, ctypes.c_double),
+                                   _P(nw, ctypes.c_uint32), _P(nc, ctypes.c_int64), cap, ctypes.byref(lost))
+    if k < 0:
+        raise RuntimeError(f"oracle products/photons failed ({k})")
+    return (nx[:k], ny[:k], nz[:k], nw[:k], nc[:k]), int(lost.value)
+
+
+def merge(p: Params, x, y, z, w, cell):
+    """a9 on a list grouped by cell (canonical order).  Returns the merged
+    particle arrays (x, y, z, w, cell)."""
+    ncell = p.n ** 3
+    cs = cell_start_of(cell, ncell)
+    x, y, z = _d(x), _d(y), _d(z)
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    W = np.add.reduceat(w.astype(np.int64), cs[:-1]) if len(w) else np.zeros(ncell, np.int64)
+    W = np.where(np.diff(cs) > 0, W, 0)
+    cap = int(np.minimum(W, p.ppc).sum()) + 1
+    ox, oy, oz = np.empty(cap), np.empty(cap), np.empty(cap)
+    ow = np.empty(cap, dtype=np.uint32)
+    oc = np.empty(cap, dtype=np.int64)
+    k = lib().ora_merge(ctypes.byref(p), _P(x, ctypes.c_double), _P(y, ctypes.c_double),
+                        _P(z, ctypes.c_double), _P(w, ctypes.c_uint32), _P(cs, ctypes.c_int64),
+                        _P(ox, ctypes.c_double), _P(oy, ctypes.c_double), _P(oz, ctypes.c_double),
+                        _P(ow, ctypes.c_uint32), _P(oc, ctypes.c_int64), cap)
+    if k < 0:
+        raise RuntimeError(f"oracle merge failed ({k})")
+    return ox[:k], oy[:k], oz[:k], ow[:k], oc[:k]
+
+
+def rho_fixed(p: Params, ne_fix, Npos, Nneg):
+    """Space charge per cell in units of q_e 2^-3s: 2^3s (N+ - N-) - ne_fix."""
+    return (np.asarray(Npos, np.int64) - np.asarray(Nneg, np.int64)) * (1 << (3 * p.frac_bits)) - ne_fix
+
+
+def step(p: Params, state: dict, E):
+    """One full step (a1-a4, a6-a9) from ``state`` with field E = (Ex,Ey,Ez).
+
+    state: x, y, z (float64), w (uint32), cell (int64), canonical order;
+    Npos, Nneg (int64 n^3).  Returns (new_state, info) where info holds the
+    intermediate results: sorted particles, ne_fix, Xe, rho_fixed (for the
+    next field solve), firings, outflow and lost-photon weights."""
+    ncell = p.n ** 3
+    xo, yo, zo, cnew = push(p, state["x"], state["y"], state["z"], E)
+    w0 = np.asarray(state["w"], np.uint32)
+    outflow = int(w0[cnew < 0].astype(np.int64).sum())
+    perm = sort_by_cell(cnew, ncell)
+    sx, sy, sz, sw, sc = xo[perm], yo[perm], zo[perm], w0[perm].copy(), cnew[perm]
+    ne, Xe = deposit(p, sx, sy, sz, sw, sc)
+    Npos = np.array(state["Npos"], dtype=np.int64, copy=True)
+    Nneg = np.array(state["Nneg"], dtype=np.int64, copy=True)
+    rho = rho_fixed(p, ne, Npos, Nneg)
+    fired = kmc(p, Xe, E)
+    sorted_state = dict(x=sx.copy(), y=sy.copy(), z=sz.copy(), w=sw.copy(), cell=sc.copy())
+    new, lost = products_photons(p, sx, sy, sz, sw, sc, Xe, fired, Npos, Nneg)
+    ax = np.concatenate([sx, new[0]]); ay = np.concatenate([sy, new[1]])
+    az = np.concatenate([sz, new[2]]); aw = np.concatenate([sw, new[3]])
+    ac = np.concatenate([sc, new[4]])
+    order = np.argsort(ac, kind="stable")
+    mx, my, mz, mw, mc = merge(p, ax[order], ay[order], az[order], aw[order], ac[order])
+    new_state = dict(x=mx, y=my, z=mz, w=mw, cell=mc, Npos=Npos, Nneg=Nneg)
+    info = dict(sorted=sorted_state, ne_fix=ne, Xe=Xe, rho_fixed=rho, n_ion=fired[0], n_att=fired[1],
+                n_ph=fired[2], outflow=outflow, lost_photon=lost, weights_after_loss=sw,
+                new_particles=new)
+    return new_state, info
