@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Ito-KMC step (one JSON line on rank 0).
+
+Workload: the single-positive-streamer configuration -- 256^3 cells over a
+2 cm cube, 1.5 MV/m applied, dt = 5 ps, ppc = 32, photoionization on -- with
+a synthetic developed discharge tree (4 channels, Gaussian radial profile,
+peak 1e19 m^-3) sampled to ``--particles`` superparticles and quasi-neutral
+ion counts with a positive head charge at each channel tip.  A step is one
+full pass of the hot path: interpolate, push, sort, deposit (a1-a4), KMC
+(a6), products, photons and merge/split (a7-a9) and the multigrid field
+solve (a5).  The particle records (GBs) exceed the 129 MB L2, so no flush is
+needed between steps.
+
+--impl reference times the FP64 CPU oracle (single thread, as it stands) on a
+bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (push+sort+deposit+KMC), HBM roofline %; FP32 vs FP64 at stated err"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ workload
+def workload(args):
+    from paper_2307_01797_gb300 import synth
+    ph = synth.physics_streamer(args.n)
+    st = synth.streamer_tree_state(ph, int(args.particles), seed=7)
+    ions = synth.streamer_ions(ph, st, seed=8)
+    return ph, st, ions
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(ph, st, ions, max_particles, seed):
+    """A bounded sample of the workload for the oracle: the particles of a
+    contiguous run of cells (canonical order) holding about max_particles."""
+    import oracle
+    p = oracle.make_params(ph, seed=seed)
+    S = oracle.canonical(p, st)
+    N = len(S["w"])
+    start = N // 2 - max_particles // 2 if N > max_particles else 0
+    sl = slice(max(start, 0), max(start, 0) + max_particles)
+    sub = {k: v[sl] for k, v in S.items()}
+    n3 = ph["n"] ** 3
+    sub["Npos"] = np.asarray(ions[0], np.int64)
+    sub["Nneg"] = np.asarray(ions[1], np.int64)
+    return sub
+
+
+def time_oracle_step(ph, sub, E, step, seed):
+    """push + sort + deposit + KMC of the oracle on the sample (the metric's
+    scope); returns (seconds, particles)."""
+    import oracle
+    p = oracle.make_params(ph, seed=seed, step=step)
+    t0 = time.perf_counter()
+    xo, yo, zo, cell = oracle.push(p, sub["x"], sub["y"], sub["z"], E)
+    perm = oracle.sort_by_cell(cell, ph["n"] ** 3)
+    ne, Xe = oracle.deposit(p, xo[perm], yo[perm], zo[perm], sub["w"][perm], cell[perm])
+    oracle.kmc(p, Xe, E)
+    return time.perf_counter() - t0, len(sub["w"])
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2307_01797_gb300 import synth
+    ph, st, ions = workload(args)
+    E = synth.random_field(ph, seed=3, amp=1e6, base=ph["E0"])
+    sub = oracle_sample(ph, st, ions, args.ref_particles, seed=1)
+    for w in range(args.warmup):
+        time_oracle_step(ph, sub, E, w, 1)
+    tot_t, tot_n = 0.0, 0
+    for k in range(args.steps):
+        t, n = time_oracle_step(ph, sub, E, args.warmup + k, 1)
+        tot_t += t
+        tot_n += n
+    v = tot_n / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args, len(st["w"])),
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(sub['w'])} particles of a contiguous cell run of the workload, "
+                                       "push+sort+deposit+KMC per step on the full grid"},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, nparticles):
+    return {"workload": f"single positive streamer, {args.n}^3 cells over a 2 cm cube, 1.5 MV/m, dt 5 ps, ppc 32, "
+                        f"photoionization on, synthetic 4-channel discharge tree",
+            "grid": args.n, "particles": int(nparticles), "ppc": 32, "form": args.form,
+            "l2": "inputs > L2 (particle records of several GB; no flush)"}
+
+
+# ------------------------------------------------------------------ our arm
+def our_arm(args, rank, world):
+    import torch
+    from paper_2307_01797_gb300 import itokmc
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ph, st, ions = workload(args)
+    N0 = len(st["w"])
+    form = itokmc.MIXED if args.form == "mixed" else itokmc.FP64
+    cap = int(N0 * 1.6) + 1_000_000
+    H = itokmc.Handle(itokmc.make_config(ph, cap, seed0=1 + rank, precision=form))
+    H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+    H.itokmc_set_ions(*ions)
+    H.itokmc_solve_field()
+    for _ in range(args.warmup):
+        H.itokmc_step(1)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = H.itokmc_get_stats()["kernel_launches"]
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage = {"transport": 0.0, "kmc": 0.0, "particles": 0.0, "field": 0.0}
+    processed = 0
+    movers = 0
+    mg_cycles = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        processed += H.itokmc_num_particles()
+        H.itokmc_step(1)
+        s = H.itokmc_get_stats()
+        stage["transport"] += s["ms_transport"]; stage["kmc"] += s["ms_kmc"]
+        stage["particles"] += s["ms_particles"]; stage["field"] += s["ms_field"]
+        movers += s["n_movers"]
+        mg_cycles.append(s["mg_cycles"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = H.itokmc_get_stats()["kernel_launches"] - l0
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        p = torch.tensor([float(processed)], device="cuda")
+        dist.all_reduce(p)
+        processed_all = float(p.item())
+    else:
+        processed_all = float(processed)
+    value = processed_all / (ms / 1e3)
+    # headline scope: push+sort+deposit+KMC
+    core_ms = stage["transport"] + stage["kmc"]
+    core_rate = processed / (core_ms / 1e3)
+    # roofline of the transport stage (push + sort + deposit, the metric's
+    # particle stream): algorithmic bytes = read + write of every record plus
+    # the per-cell mesh terms amortised over ppc
+    R = 32 if form == itokmc.FP64 else 20
+    mesh = (24 + 8 + 8) if form == itokmc.FP64 else (12 + 8 + 8)
+    alg_bytes = processed * (2 * R + mesh / 32)
+    ach = alg_bytes / (stage["transport"] / 1e3) / 1e9
+    pk, pk_kind = peaks()
+    # e2e: host arrays in pinned memory, uploaded every step; density read back
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in st.items()}
+        ne_host = torch.empty(args.n ** 3, dtype=torch.int64).pin_memory()
+        K2 = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = 0
+        lib = itokmc.lib()
+        for _ in range(K2):
+            H.itokmc_set_particles(pin["x"], pin["y"], pin["z"], pin["w"], mem=itokmc.HOST)
+            done += N0
+            H.itokmc_step(1)
+            itokmc._check(lib.itokmc_read_densities(H.h, 0, itokmc.NE_FIX, itokmc._ptr(ne_host),
+                                                    ne_host.numel() * 8), H.h)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": done / te, "unit": "particle-steps/s", "h2d_bytes_per_step": N0 * (3 * 8 + 4),
+               "d2h_bytes_per_step": args.n ** 3 * 8, "steps": K2}
+    if rank != 0:
+        H.close()
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        from paper_2307_01797_gb300 import synth
+        E = tuple(np.asarray(b).reshape(args.n, args.n, args.n) for b in H.itokmc_read_densities(itokmc.E))
+        sub = oracle_sample(ph, st, ions, args.ref_particles, seed=1)
+        t_tot, n_tot, k = 0.0, 0, 0
+        while t_tot < args.cpu_seconds and k < 20:
+            t, n = time_oracle_step(ph, sub, E, k, 1)
+            t_tot += t; n_tot += n; k += 1
+        cpu = {"value": n_tot / t_tot, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(sub['w'])} particles (a contiguous cell run of the workload) x {k} steps of "
+                         "push+sort+deposit+KMC on the full grid, single-threaded C oracle"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if form == itokmc.FP64 else "f32",
+        "data": "synthetic (seeded discharge-tree state; no dataset)",
+        "config": config_of(args, N0),
+        "push_sort_deposit_kmc_rate": core_rate,
+        "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
+        "movers_per_step": movers / args.steps, "mg_cycles": mg_cycles,
+        "roofline": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)", "achieved": ach,
+                     "peak": pk, "peak_kind": pk_kind, "unit": "GB/s", "frac": ach / pk, "traffic": None,
+                     "bytes_per_particle": 2 * R + mesh / 32},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    H.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--particles", type=float, default=2e7)
+    ap.add_argument("--ref-particles", type=int, default=2000000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+    else:
+        our_arm(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * itokmc.h -- C ABI of the GB300 Ito-KMC streamer step (libitokmc.so).
+ *
+ * One time step of the Ito-Kinetic-Monte-Carlo model of R. Marskar,
+ * "Stochastic and self-consistent 3D modeling of streamer discharge trees
+ * with Kinetic Monte Carlo" (arXiv 2307.01797), on a uniform cubic grid with
+ * plane electrodes at z = lo_z (phi = 0) and z = hi_z (phi = E0 (hi_z-lo_z))
+ * and homogeneous Neumann side faces.  The system solved is Eq. ito_poisson
+ * (Sec. 4): particle transport Eq. ito_kernel, per-cell chemistry Eq. kmc,
+ * field Eq. poisson with E = -grad phi.
+ *
+ * A step (itokmc_step) runs, on the handle's CUDA stream:
+ *   a1  trilinear (CIC) interpolation of E to the particles      Sec. 4.2
+ *   a2  explicit Euler-Maruyama push, v = -mu E                   Sec. 4.3
+ *   a3  stable sort of the particles by cell
+ *   a4  CIC deposition in int64 fixed point; X_e per cell         Sec. 4.2
+ *   a6  per-cell KMC, Cao et al. hybrid tau-leap/SSA              Sec. 3.2.3
+ *   a7  product particles (N_new = 64, Eq. w), loss removal       Sec. 4.4
+ *   a8  photon emission and absorption (photoionization)          Sec. 4.5
+ *   a9  kd-tree merge/split to ppc particles per cell             Sec. 4.6
+ *   a5  geometric-multigrid Poisson solve for the next step's E   Sec. 4.3
+ * The field is solved from the charge deposited in a4 together with the ion
+ * counts before a6 (every reaction is charge neutral).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns 0 (ITOKMC_OK) or a negative ITOKMC_ERR_* code; no
+ *     C++ exception crosses the ABI.  itokmc_last_error() gives the message.
+ *     After ITOKMC_ERR_CUDA or ITOKMC_ERR_TIMEOUT the handle is poisoned:
+ *     every later call except itokmc_last_error/itokmc_destroy returns
+ *     ITOKMC_ERR_POISONED.
+ *   - Units are SI.  Grid index (i, j, k) has linear cell index
+ *     (k n + j) n + i (x fastest); cell i spans [lo + i h, lo + (i+1) h].
+ *   - Realization r of an ensemble uses Philox key seed0 + r and owns cells
+ *     r n^3 ... (r+1) n^3 - 1 of every per-cell array.
+ *   - Host buffers are owned by the caller and are only read or written
+ *     during the call.  Device memory is owned by the handle (allocated in
+ *     itokmc_init through the caller's allocator, or cudaMallocAsync when
+ *     none is given, and released by itokmc_destroy).
+ *   - Calls are asynchronous on the handle's stream unless they return data
+ *     to the host, in which case they synchronise that stream.
+ */
+#ifndef ITOKMC_H
+#define ITOKMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define ITOKMC_OK 0
+#define ITOKMC_ERR_ARG (-1)        /* invalid argument or configuration     */
+#define ITOKMC_ERR_OOM (-2)        /* device allocation failed              */
+#define ITOKMC_ERR_CUDA (-3)       /* a CUDA runtime call failed            */
+#define ITOKMC_ERR_CAPACITY (-4)   /* particle capacity exceeded            */
+#define ITOKMC_ERR_OVERFLOW (-5)   /* weight or fixed-point overflow        */
+#define ITOKMC_ERR_NOCONV (-6)     /* multigrid did not reach its tolerance */
+#define ITOKMC_ERR_TIMEOUT (-7)    /* a bounded device wait gave up         */
+#define ITOKMC_ERR_POISONED (-8)   /* handle unusable after an earlier error */
+#define ITOKMC_ERR_KMC (-9)        /* KMC iteration guard hit in some cell  */
+
+/* ---- precision forms --------------------------------------------------- */
+#define ITOKMC_FP64 0   /* FP64 positions/push/KMC, FP64 multigrid (parity) */
+#define ITOKMC_MIXED 1  /* FP32 cell-relative positions and push, int64     */
+                        /* fixed-point deposit, FP32 V-cycles inside FP64   */
+                        /* residual iterative refinement                    */
+
+/* ---- memory kinds for host/device pointers ----------------------------- */
+#define ITOKMC_HOST 0
+#define ITOKMC_DEVICE 1
+
+/* ---- fields readable with itokmc_read_densities ------------------------ */
+#define ITOKMC_NE_FIX 0   /* int64 n^3: CIC electron density in units of     */
+                          /* 2^-3s electrons per cell (as of the last a4)   */
+#define ITOKMC_XE 1       /* int64 n^3: electrons per cell (NGP), last a4   */
+#define ITOKMC_NPOS 2     /* int64 n^3: positive-ion count per cell         */
+#define ITOKMC_NNEG 3     /* int64 n^3: negative-ion count per cell         */
+#define ITOKMC_PHI 4      /* double n^3: potential, V                       */
+#define ITOKMC_E 5        /* double 3 n^3: Ex block, Ey block, Ez block V/m */
+#define ITOKMC_RHO 6      /* int64 n^3: space charge 2^3s (N+ - N-) - ne_fix*/
+                          /* in units of q_e 2^-3s, as of the last a4       */
+#define ITOKMC_FIRINGS 7  /* int64 3 n^3: ionizations, attachments, photon  */
+                          /* emissions of the last a6 (blocks of n^3)       */
+
+/* ---- stages runnable one at a time (itokmc_run_stage) ------------------ */
+#define ITOKMC_STAGE_TRANSPORT 0  /* a1-a4: push, sort, deposit, X_e, rho   */
+#define ITOKMC_STAGE_KMC 1        /* a6 with the current E                  */
+#define ITOKMC_STAGE_PARTICLES 2  /* a7-a9: products, photons, merge/split  */
+#define ITOKMC_STAGE_FIELD 3      /* a5 from the rho of the last a4          */
+
+typedef void* (*itokmc_alloc_fn)(size_t bytes, void* ctx);   /* device memory */
+typedef void (*itokmc_free_fn)(void* ptr, void* ctx);
+
+typedef struct itokmc_config {
+    int32_t n[3];              /* cells per axis: equal powers of two >= 8   */
+    int32_t n_realizations;    /* ensemble size R >= 1                       */
+    double lo[3], hi[3];       /* domain corners (m); cells must be cubes    */
+    double dt;                 /* time step (s)                              */
+    uint64_t seed0;            /* realization r uses Philox key seed0 + r    */
+    double mu, D;              /* electron mobility (m^2/Vs), diffusion m^2/s*/
+    double alpha_A, alpha_B;   /* ionization alpha(E) = A exp(-B/|E|) (1/m)  */
+    double eta;                /* attachment coefficient (1/m)               */
+    double E0;                 /* applied field (V/m): phi(hi_z)=E0 L_z      */
+    double photon_ratio;       /* k_gamma = photon_ratio k_alpha; 0 = off    */
+    double kappa_lo, kappa_hi; /* absorption coefficient range (1/m)         */
+    double eps;                /* Cao accuracy factor; INFINITY as in paper  */
+    int32_t ppc;               /* particles per cell after merge (2^k <= 256)*/
+    int32_t n_new;             /* max new particles per cell (64, <= 64)     */
+    int32_t n_crit;            /* critical threshold N_c (5)                 */
+    int32_t n_ssa;             /* max SSA events per substep N_SSA (10)      */
+    int32_t frac_bits;         /* fixed-point bits s per axis (10, <= 10)    */
+    int32_t precision;         /* ITOKMC_FP64 or ITOKMC_MIXED                */
+    double mg_rtol;            /* stop when ||r||_2 <= mg_rtol ||b||_2       */
+    int32_t mg_nu1, mg_nu2;    /* red-black Gauss-Seidel pre/post sweeps     */
+    int32_t mg_max_cycles;     /* V-cycle limit (ITOKMC_ERR_NOCONV beyond)   */
+    int32_t field_precision;   /* -1: as precision; else ITOKMC_FP64/MIXED   */
+    int64_t particle_capacity; /* particles storable (all realizations)      */
+    void* stream;              /* cudaStream_t to run on, or NULL (default)  */
+    itokmc_alloc_fn alloc;     /* device allocator, or NULL: cudaMallocAsync */
+    itokmc_free_fn free_fn;    /* matching free                              */
+    void* alloc_ctx;           /* passed to alloc/free_fn                    */
+} itokmc_config;
+
+typedef struct itokmc_stats {
+    int64_t n_particles;       /* particles now (all realizations)           */
+    int64_t step;              /* steps taken                                */
+    int64_t n_movers;          /* particles that changed cell in the last a2 */
+    int64_t outflow_weight;    /* electrons absorbed at faces, last step     */
+    int64_t ionizations, attachments, photon_emissions; /* last a6          */
+    int64_t photons_absorbed_weight, photons_lost_weight; /* last a8        */
+    int64_t n_new_particles;   /* products + photoelectrons, last a7/a8      */
+    int32_t mg_cycles;         /* V-cycles of the last field solve           */
+    int32_t kmc_status;        /* 0, or ITOKMC_ERR_KMC                       */
+    double mg_rel_residual;    /* ||r||/||b|| after the last field solve      */
+    double ms_transport, ms_kmc, ms_particles, ms_field; /* last step (events)*/
+    int64_t kernel_launches;   /* kernels launched by the library so far     */
+} itokmc_stats;
+
+typedef struct itokmc_handle itokmc_handle;
+
+/* Fills *cfg with the defaults of the paper's method (N_new 64, N_c 5,
+ * N_SSA 10, eps = INFINITY, s = 10, rtol 1e-10, nu1 = nu2 = 2, 64 cycles,
+ * FP64).  Grid, physics and capacity must still be set by the caller. */
+int itokmc_config_defaults(itokmc_config* cfg);
+
+/* Validates *cfg, allocates all device state for n_realizations x n^3 cells
+ * and particle_capacity particles, zeroes it, and returns the handle in
+ * *out.  No particles exist yet.  Errors: ERR_ARG (bad config), ERR_OOM. */
+int itokmc_init(const itokmc_config* cfg, itokmc_handle** out);
+
+/* Releases all device memory of the handle.  Always safe on a poisoned
+ * handle; NULL is a no-op. */
+int itokmc_destroy(itokmc_handle* h);
+
+/* Replaces all particles.  x, y, z (double), w (uint32 weights = physical
+ * electrons, >= 1) and realization (int32, may be NULL when R = 1) hold n
+ * particles in any order, in host (mem = ITOKMC_HOST) or device memory.
+ * Particles are stably sorted by (realization, cell); particles outside
+ * [lo, hi) are rejected with ERR_ARG.  ERR_CAPACITY if n > capacity. */
+int itokmc_set_particles(itokmc_handle* h, const double* x, const double* y, const double* z,
+                         const uint32_t* w, const int32_t* realization, int64_t n, int32_t mem);
+
+/* Copies the particles (canonical order: by realization, cell, then the
+ * order of the last sort/merge) into caller buffers of capacity cap.  Any
+ * pointer may be NULL.  cell receives the linear cell index within the
+ * realization.  *n_out receives the particle count; ERR_CAPACITY if it
+ * exceeds cap (nothing copied).  Synchronises the stream. */
+int itokmc_read_particles(itokmc_handle* h, double* x, double* y, double* z, uint32_t* w,
+                          int32_t* realization, int64_t* cell, int64_t cap, int64_t* n_out,
+                          int32_t mem);
+
+/* Sets the ion counts (int64, R n^3 each; host or device). */
+int itokmc_set_ions(itokmc_handle* h, const int64_t* npos, const int64_t* nneg, int32_t mem);
+
+/* Sets E directly (double, three blocks Ex, Ey, Ez of R n^3 each), bypassing
+ * the field solve: used to feed a given field to the next step or stage. */
+int itokmc_set_field(itokmc_handle* h, const double* E, int32_t mem);
+
+/* Re-deposits the current particles (a4) and solves the field (a5) from
+ * them and the current ions: the initial field of a run.  ERR_NOCONV if the
+ * multigrid stops at mg_max_cycles above tolerance. */
+int itokmc_solve_field(itokmc_handle* h);
+
+/* Advances nsteps full steps (a1-a9 then a5).  Errors: ERR_CAPACITY,
+ * ERR_OVERFLOW, ERR_NOCONV, ERR_KMC, ERR_CUDA. */
+int itokmc_step(itokmc_handle* h, int32_t nsteps);
+
+/* Runs one stage (ITOKMC_STAGE_*) on the current state without advancing
+ * the step counter; a full step is TRANSPORT, KMC, PARTICLES, FIELD and then
+ * the counter advance (itokmc_advance_counter). */
+int itokmc_run_stage(itokmc_handle* h, int32_t stage);
+
+/* Advances the step counter used in every Philox counter by one. */
+int itokmc_advance_counter(itokmc_handle* h);
+
+/* Copies one field (ITOKMC_NE_FIX ...) of realization r (or all
+ * realizations when r = -1) into host_out of the given size in bytes.
+ * ERR_ARG if bytes is too small.  Synchronises the stream. */
+int itokmc_read_densities(itokmc_handle* h, int32_t realization, int32_t which, void* host_out,
+                          size_t bytes);
+
+/* Fills *st with counters of the last step.  Synchronises the stream. */
+int itokmc_get_stats(itokmc_handle* h, itokmc_stats* st);
+
+/* Current particle count (all realizations).  Synchronises the stream. */
+int itokmc_num_particles(itokmc_handle* h, int64_t* n_out);
+
+/* Message of the last error on this handle ("" if none).  h may be NULL
+ * for errors of itokmc_init. */
+const char* itokmc_last_error(const itokmc_handle* h);
+
+/* Library version string. */
+const char* itokmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ITOKMC_H */

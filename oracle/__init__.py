@@ -112,6 +112,7 @@ def lib():
             L.ora_merge_list.argtypes = [i64, pd, pd, pd, pu64, i32, pd, pd, pd, pu64]
             L.ora_merge_list.restype = i64
             L.ora_photon_samples.argtypes = [pp, i32, i32, i32, i64, pd, pd, pd, pd]
+            L.ora_cells.argtypes = [pp, i64, pd, pd, pd, pi64]
             _lib = L
     return _lib
 
@@ -165,6 +166,24 @@ def photon_samples(params: Params, i: int, j: int, k: int, m: int):
     lib().ora_photon_samples(ctypes.byref(params), i, j, k, m, _P(Y0, ctypes.c_double),
                              _P(kap, ctypes.c_double), _P(r, ctypes.c_double), _P(d, ctypes.c_double))
     return Y0, kap, r, d
+
+
+def cells(params: Params, x, y, z):
+    x = np.ascontiguousarray(x, np.float64); y = np.ascontiguousarray(y, np.float64)
+    z = np.ascontiguousarray(z, np.float64)
+    out = np.empty(len(x), np.int64)
+    lib().ora_cells(ctypes.byref(params), len(x), _P(x, ctypes.c_double), _P(y, ctypes.c_double),
+                    _P(z, ctypes.c_double), _P(out, ctypes.c_int64))
+    return out
+
+
+def canonical(params: Params, st: dict) -> dict:
+    """Particles of ``st`` (x, y, z, w; any order) in canonical order (cell,
+    input order) with their cells; particles outside the box are dropped."""
+    c = cells(params, st["x"], st["y"], st["z"])
+    perm = stages.sort_by_cell(c, params.n ** 3)
+    return dict(x=np.asarray(st["x"], np.float64)[perm], y=np.asarray(st["y"], np.float64)[perm],
+                z=np.asarray(st["z"], np.float64)[perm], w=np.asarray(st["w"], np.uint32)[perm], cell=c[perm])
 
 
 def merge_list(x, y, z, w, T):

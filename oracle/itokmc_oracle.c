@@ -989,3 +989,15 @@ int64_t ora_merge_list(int64_t M, const double* x, const double* y, const double
     free(in); free(out);
     return nl;
 }
+
+/* Cell of each position (floor((x-lo)/h), top-clamped), or -1 outside       */
+/* [lo, hi): the key by which an arbitrary particle list is put in canonical */
+/* order (a stable sort by this key, ora_sort_by_cell).                      */
+void ora_cells(const ora_params* p, int64_t np, const double* x, const double* y, const double* z,
+               int64_t* cell)
+{
+    for (int64_t i = 0; i < np; ++i) {
+        double X[3] = { x[i], y[i], z[i] };
+        cell[i] = inside(p, X) ? lin(p, cell_axis(p, 0, X[0]), cell_axis(p, 1, X[1]), cell_axis(p, 2, X[2])) : -1;
+    }
+}

@@ -1,0 +1,561 @@
+// ik_api.cu -- the C ABI of libitokmc (declared in include/itokmc.h): handle
+// life cycle, device memory, state upload/readback and the step driver.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/itokmc.h"
+#include "ik_common.cuh"
+#include "ik_state.h"
+
+namespace ik {
+unsigned long long g_launches = 0;
+}
+
+struct itokmc_handle {
+    itokmc_config cfg;
+    ik::Params P;
+    ik::Dev d;
+    cudaStream_t s = nullptr;
+    uint64_t G = 0;
+    uint32_t N = 0;           // particle count (host copy)
+    uint32_t cap = 0;
+    int64_t step = 0;
+    int field_prec = 0;
+    bool poisoned = false;
+    std::string err;
+    std::vector<void*> allocs;
+    itokmc_stats st{};
+    cudaEvent_t ev[8]{};
+    struct Readback { uint32_t N; uint32_t pad; ik::Counters ctr; }* rb = nullptr;  // pinned
+};
+
+namespace {
+
+thread_local std::string g_init_err;
+
+int fail(itokmc_handle* h, int code, const std::string& msg)
+{
+    if (h) {
+        h->err = msg;
+        if (code == ITOKMC_ERR_CUDA || code == ITOKMC_ERR_TIMEOUT) h->poisoned = true;
+    } else {
+        g_init_err = msg;
+    }
+    return code;
+}
+
+int cuda_check(itokmc_handle* h, cudaError_t e, const char* where)
+{
+    if (e == cudaSuccess) return ITOKMC_OK;
+    return fail(h, ITOKMC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define IK_CHECK(h, call)                                        \
+    do {                                                         \
+        int _rc = cuda_check((h), (call), #call);                \
+        if (_rc) return _rc;                                     \
+    } while (0)
+
+#define IK_GUARD(h)                                              \
+    do {                                                         \
+        if (!(h)) return ITOKMC_ERR_ARG;                         \
+        if ((h)->poisoned) return ITOKMC_ERR_POISONED;           \
+    } while (0)
+
+void* dalloc(itokmc_handle* h, size_t bytes, int* rc)
+{
+    if (*rc) return nullptr;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (h->cfg.alloc) {
+        p = h->cfg.alloc(bytes, h->cfg.alloc_ctx);
+        if (!p) { *rc = fail(h, ITOKMC_ERR_OOM, "allocator returned NULL"); return nullptr; }
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, h->s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *rc = fail(h, ITOKMC_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+            return nullptr;
+        }
+    }
+    h->allocs.push_back(p);
+    if (cudaMemsetAsync(p, 0, bytes, h->s) != cudaSuccess) *rc = fail(h, ITOKMC_ERR_CUDA, "memset");
+    return p;
+}
+
+template <class T>
+T* dalloc_n(itokmc_handle* h, size_t n, int* rc) { return reinterpret_cast<T*>(dalloc(h, n * sizeof(T), rc)); }
+
+int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+
+int status_of_err(itokmc_handle* h, unsigned err)
+{
+    if (!err) return ITOKMC_OK;
+    if (err & ik::DERR_CAPACITY) return fail(h, ITOKMC_ERR_CAPACITY, "particle, mover, photon or merge capacity exceeded");
+    if (err & ik::DERR_OVERFLOW) return fail(h, ITOKMC_ERR_OVERFLOW, "weight or fixed-point overflow");
+    if (err & ik::DERR_KMC) return fail(h, ITOKMC_ERR_KMC, "KMC iteration guard hit");
+    if (err & ik::DERR_TIMEOUT) return fail(h, ITOKMC_ERR_TIMEOUT, "device wait timed out");
+    return fail(h, ITOKMC_ERR_ARG, "invalid particle data (outside the domain, zero weight or bad realization)");
+}
+
+// Copies N (from cell_start[G]) and the counters to the pinned mirror and waits.
+int readback(itokmc_handle* h)
+{
+    IK_CHECK(h, cudaMemcpyAsync(&h->rb->N, h->d.cell_start + h->G, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->s));
+    IK_CHECK(h, cudaMemcpyAsync(&h->rb->ctr, h->d.ctr, sizeof(ik::Counters), cudaMemcpyDeviceToHost, h->s));
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    IK_CHECK(h, cudaGetLastError());
+    h->N = h->rb->N;
+    return ITOKMC_OK;
+}
+
+float elapsed(itokmc_handle* h, int a, int b)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]) != cudaSuccess) { cudaGetLastError(); return -1.f; }
+    return ms;
+}
+
+int stage_transport(itokmc_handle* h)
+{
+    IK_CHECK(h, cudaEventRecord(h->ev[0], h->s));
+    ik::launch_transport_f64(h->P, h->d, h->N, h->s);
+    ik::launch_transport_finish_f64(h->P, h->d, h->N, h->G, h->s);
+    ik::launch_rho(h->P, h->d, h->G, h->s);
+    IK_CHECK(h, cudaEventRecord(h->ev[1], h->s));
+    int rc = readback(h);
+    if (rc) return rc;
+    const ik::Counters& c = h->rb->ctr;
+    h->st.n_movers = (int64_t)c.n_movers;
+    int64_t out = 0;
+    for (int r = 0; r < h->P.R; ++r) out += (int64_t)c.outflow[r];
+    h->st.outflow_weight = out;
+    h->st.ms_transport = elapsed(h, 0, 1);
+    return status_of_err(h, c.err);
+}
+
+int stage_kmc(itokmc_handle* h)
+{
+    IK_CHECK(h, cudaEventRecord(h->ev[2], h->s));
+    ik::launch_kmc(h->P, h->d, h->G, h->s);
+    IK_CHECK(h, cudaEventRecord(h->ev[3], h->s));
+    return cuda_check(h, cudaGetLastError(), "kmc launch");
+}
+
+int stage_particles(itokmc_handle* h)
+{
+    IK_CHECK(h, cudaEventRecord(h->ev[4], h->s));
+    ik::launch_particles_f64(h->P, h->d, h->N, h->G, h->s);
+    IK_CHECK(h, cudaEventRecord(h->ev[5], h->s));
+    int rc = readback(h);
+    if (rc) return rc;
+    const ik::Counters& c = h->rb->ctr;
+    h->st.ionizations = (int64_t)c.ion;
+    h->st.attachments = (int64_t)c.att;
+    h->st.photon_emissions = (int64_t)c.phot;
+    h->st.photons_absorbed_weight = (int64_t)c.absorbed_w;
+    int64_t lost = 0;
+    for (int r = 0; r < h->P.R; ++r) lost += (int64_t)c.lost[r];
+    h->st.photons_lost_weight = lost;
+    h->st.n_new_particles = (int64_t)c.n_photo;
+    h->st.kmc_status = (c.err & ik::DERR_KMC) ? ITOKMC_ERR_KMC : 0;
+    h->st.ms_kmc = elapsed(h, 2, 3);
+    h->st.ms_particles = elapsed(h, 4, 5);
+    if (h->N > h->cap) return fail(h, ITOKMC_ERR_CAPACITY, "particle capacity exceeded after merge");
+    return status_of_err(h, c.err);
+}
+
+int stage_field(itokmc_handle* h)
+{
+    IK_CHECK(h, cudaEventRecord(h->ev[6], h->s));
+    int cycles = 0;
+    double rel = 0.0;
+    const int st = ik::field_solve(h->P, h->d, h->field_prec, h->cfg.mg_rtol, h->cfg.mg_nu1, h->cfg.mg_nu2,
+                                   h->cfg.mg_max_cycles, h->s, &cycles, &rel);
+    if (st == -3) return cuda_check(h, cudaGetLastError(), "field solve");
+    ik::launch_efield(h->P, h->d, h->s);
+    IK_CHECK(h, cudaEventRecord(h->ev[7], h->s));
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    IK_CHECK(h, cudaGetLastError());
+    h->st.mg_cycles = cycles;
+    h->st.mg_rel_residual = rel;
+    h->st.ms_field = elapsed(h, 6, 7);
+    if (st != 0) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "multigrid stopped at %d cycles, relative residual %.3e", cycles, rel);
+        return fail(h, ITOKMC_ERR_NOCONV, buf);
+    }
+    return ITOKMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int itokmc_config_defaults(itokmc_config* c)
+{
+    if (!c) return ITOKMC_ERR_ARG;
+    memset(c, 0, sizeof(*c));
+    c->n_realizations = 1;
+    c->eps = INFINITY;
+    c->ppc = 8;
+    c->n_new = 64;
+    c->n_crit = 5;
+    c->n_ssa = 10;
+    c->frac_bits = 10;
+    c->precision = ITOKMC_FP64;
+    c->field_precision = -1;
+    c->mg_rtol = 1e-10;
+    c->mg_nu1 = 2;
+    c->mg_nu2 = 2;
+    c->mg_max_cycles = 64;
+    c->kappa_lo = 520.0;
+    c->kappa_hi = 3.0e4;
+    return ITOKMC_OK;
+}
+
+int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
+{
+    if (!cfg || !out) return fail(nullptr, ITOKMC_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    const int n = cfg->n[0];
+    if (n < 8 || (n & (n - 1)) || cfg->n[1] != n || cfg->n[2] != n || n > 1024)
+        return fail(nullptr, ITOKMC_ERR_ARG, "grid must be n^3 with n a power of two in [8, 1024]");
+    const int R = cfg->n_realizations;
+    if (R < 1 || R > ik::MAX_R) return fail(nullptr, ITOKMC_ERR_ARG, "n_realizations out of range");
+    const uint64_t G = (uint64_t)R * n * n * n;
+    if (G > ik::KEY_MASK) return fail(nullptr, ITOKMC_ERR_ARG, "too many cells (R n^3 must be < 2^30)");
+    const double h0 = (cfg->hi[0] - cfg->lo[0]) / n;
+    for (int a = 0; a < 3; ++a) {
+        if (!(cfg->hi[a] > cfg->lo[a])) return fail(nullptr, ITOKMC_ERR_ARG, "hi must exceed lo");
+        if ((cfg->hi[a] - cfg->lo[a]) / n != h0) return fail(nullptr, ITOKMC_ERR_ARG, "cells must be cubes");
+    }
+    if (!(cfg->dt > 0) || cfg->D < 0 || cfg->mu < 0) return fail(nullptr, ITOKMC_ERR_ARG, "dt, mu, D");
+    if (cfg->ppc < 1 || cfg->ppc > 256 || (cfg->ppc & (cfg->ppc - 1)))
+        return fail(nullptr, ITOKMC_ERR_ARG, "ppc must be a power of two <= 256");
+    if (cfg->n_new < 1 || cfg->n_new > 64) return fail(nullptr, ITOKMC_ERR_ARG, "n_new in [1, 64]");
+    if (cfg->frac_bits < 1 || cfg->frac_bits > 10) return fail(nullptr, ITOKMC_ERR_ARG, "frac_bits in [1, 10]");
+    if (cfg->n_ssa < 1 || cfg->n_crit < 0) return fail(nullptr, ITOKMC_ERR_ARG, "n_ssa, n_crit");
+    if (cfg->precision != ITOKMC_FP64 && cfg->precision != ITOKMC_MIXED)
+        return fail(nullptr, ITOKMC_ERR_ARG, "precision");
+    if (cfg->particle_capacity < 1 || cfg->particle_capacity > 0x7fff0000ll)
+        return fail(nullptr, ITOKMC_ERR_ARG, "particle_capacity in [1, 2^31)");
+    if (cfg->photon_ratio > 0 && !(cfg->kappa_hi >= cfg->kappa_lo && cfg->kappa_lo > 0))
+        return fail(nullptr, ITOKMC_ERR_ARG, "kappa range");
+    if (!(cfg->alloc == nullptr) != !(cfg->free_fn == nullptr))
+        return fail(nullptr, ITOKMC_ERR_ARG, "alloc and free_fn must be given together");
+
+    itokmc_handle* h = new itokmc_handle();
+    h->cfg = *cfg;
+    h->s = (cudaStream_t)cfg->stream;
+    h->G = G;
+    h->cap = (uint32_t)cfg->particle_capacity;
+    h->field_prec = cfg->field_precision < 0 ? cfg->precision : cfg->field_precision;
+    ik::Params& P = h->P;
+    P.n = n; P.n3 = n * n * n; P.R = R; P.log2n = ilog2(n);
+    P.ppc = cfg->ppc; P.n_new = cfg->n_new; P.n_crit = cfg->n_crit; P.n_ssa = cfg->n_ssa; P.frac_bits = cfg->frac_bits;
+    for (int a = 0; a < 3; ++a) { P.lo[a] = cfg->lo[a]; P.hi[a] = cfg->hi[a]; P.h[a] = (cfg->hi[a] - cfg->lo[a]) / n; }
+    P.dt = cfg->dt; P.mu = cfg->mu; P.D = cfg->D; P.alpha_A = cfg->alpha_A; P.alpha_B = cfg->alpha_B; P.eta = cfg->eta;
+    P.photon_ratio = cfg->photon_ratio; P.kappa_lo = cfg->kappa_lo; P.kappa_hi = cfg->kappa_hi; P.eps = cfg->eps;
+    P.sdt = sqrt((2.0 * cfg->D) * cfg->dt);
+    P.E0 = cfg->E0;
+    P.seed0 = cfg->seed0;
+    P.step = 0;
+    P.f_drift = (float)(-cfg->mu * cfg->dt / P.h[0]);
+    P.f_diff = (float)(P.sdt / P.h[0]);
+
+    int rc = 0;
+    ik::Dev& d = h->d;
+    const size_t cap = h->cap;
+    d.mover_cap = h->cap;
+    d.photo_cap = (uint32_t)std::max<size_t>(1u << 16, cap / 4);
+    d.work_cap = 3 * std::max<uint64_t>(1ull << 20, cap / 2);
+    d.recA = dalloc_n<ik::P64>(h, cap, &rc);
+    d.recB = dalloc_n<ik::P64>(h, cap, &rc);
+    d.keyB = dalloc_n<uint32_t>(h, cap, &rc);
+    d.cell_start = dalloc_n<uint32_t>(h, G + 1, &rc);
+    d.cell_start_B = dalloc_n<uint32_t>(h, G + 1, &rc);
+    d.out_start = dalloc_n<uint32_t>(h, G + 1, &rc);
+    d.cnt_new = dalloc_n<int32_t>(h, G, &rc);
+    d.in_cnt = dalloc_n<int32_t>(h, G, &rc);
+    d.in_before = dalloc_n<int32_t>(h, G, &rc);
+    d.cursor = dalloc_n<int32_t>(h, G, &rc);
+    d.delta = dalloc_n<int64_t>(h, G, &rc);
+    d.in_off = dalloc_n<uint32_t>(h, G + 1, &rc);
+    const size_t nblk = (cap + ik::TPB - 1) / ik::TPB + 1;
+    d.blk_stay = dalloc_n<uint32_t>(h, nblk, &rc);
+    d.blk_prefix = dalloc_n<uint32_t>(h, nblk, &rc);
+    d.movers = dalloc_n<ik::Mover>(h, cap, &rc);
+    d.mover_sorted = dalloc_n<uint32_t>(h, cap, &rc);
+    d.ne_fix = dalloc_n<unsigned long long>(h, G, &rc);
+    d.Xe = dalloc_n<unsigned long long>(h, G, &rc);
+    d.Npos = dalloc_n<int64_t>(h, G, &rc);
+    d.Nneg = dalloc_n<int64_t>(h, G, &rc);
+    d.rho = dalloc_n<int64_t>(h, G, &rc);
+    d.E = dalloc_n<ik::E64>(h, G, &rc);
+    d.E32 = dalloc_n<float4>(h, G, &rc);
+    d.fired = dalloc_n<int64_t>(h, 3 * G, &rc);
+    d.stage = dalloc_n<double>(h, 3 * G, &rc);
+    d.photos = dalloc_n<ik::Photo>(h, d.photo_cap, &rc);
+    d.photo_sorted = dalloc_n<uint32_t>(h, d.photo_cap, &rc);
+    d.photo_cnt = dalloc_n<int32_t>(h, G, &rc);
+    d.photo_cursor = dalloc_n<int32_t>(h, G, &rc);
+    d.photo_w = dalloc_n<unsigned long long>(h, G, &rc);
+    d.photo_off = dalloc_n<uint32_t>(h, G + 1, &rc);
+    d.work_off = dalloc_n<uint64_t>(h, G + 1, &rc);
+    d.work = reinterpret_cast<unsigned char*>(dalloc(h, d.work_cap * 32, &rc));
+    d.work_bytes = d.work_cap * 32;
+    const size_t se = 2 * std::max(std::max(ik::scan_scratch_elems(G, 3), ik::scan_scratch_elems(nblk, 3)),
+                                   ik::radix_scratch_elems(h->cap));
+    d.scan_blk = dalloc_n<long long>(h, se, &rc);
+    d.scan_blk_elems = se;
+    d.ctr = dalloc_n<ik::Counters>(h, 1, &rc);
+    d.sort_tmp = dalloc_n<uint32_t>(h, 4 * cap, &rc);
+    // multigrid hierarchy down to 4^3
+    int l = 0;
+    for (int m = n; m >= 4 && l < ik::MAX_LEVELS; m >>= 1, ++l) {
+        ik::MGLevel& L = d.lev[l];
+        const size_t cells = (size_t)R * m * m * m;
+        L.n = m;
+        L.h = P.h[0] * (double)(n / m);
+        L.phi = dalloc_n<double>(h, cells, &rc);
+        L.rhs = dalloc_n<double>(h, cells, &rc);
+        L.res = nullptr;
+        L.phi32 = dalloc_n<float>(h, cells, &rc);
+        L.rhs32 = dalloc_n<float>(h, cells, &rc);
+    }
+    d.nlev = l;
+    const size_t nb = (size_t)R * n * n * n / 256 + 16;
+    d.norm_part = dalloc_n<double>(h, 2 * nb, &rc);
+    d.norm_out = dalloc_n<double>(h, 2 * R, &rc);
+    if (!rc && cudaMallocHost(reinterpret_cast<void**>(&h->rb), sizeof(*h->rb)) != cudaSuccess)
+        rc = fail(h, ITOKMC_ERR_OOM, "pinned host buffer");
+    for (int e = 0; e < 8 && !rc; ++e)
+        if (cudaEventCreate(&h->ev[e]) != cudaSuccess) rc = fail(h, ITOKMC_ERR_CUDA, "event create");
+    if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->s), "init sync");
+    if (rc) {
+        g_init_err = h->err;
+        itokmc_destroy(h);
+        return rc;
+    }
+    // linear potential as the first guess of the first solve
+    *out = h;
+    return ITOKMC_OK;
+}
+
+int itokmc_destroy(itokmc_handle* h)
+{
+    if (!h) return ITOKMC_OK;
+    cudaStreamSynchronize(h->s);
+    cudaGetLastError();
+    for (void* p : h->allocs) {
+        if (h->cfg.free_fn) h->cfg.free_fn(p, h->cfg.alloc_ctx);
+        else cudaFreeAsync(p, h->s);
+    }
+    cudaStreamSynchronize(h->s);
+    for (auto& e : h->ev) if (e) cudaEventDestroy(e);
+    if (h->rb) cudaFreeHost(h->rb);
+    cudaGetLastError();
+    delete h;
+    return ITOKMC_OK;
+}
+
+int itokmc_set_particles(itokmc_handle* h, const double* x, const double* y, const double* z, const uint32_t* w,
+                         const int32_t* realization, int64_t n, int32_t mem)
+{
+    IK_GUARD(h);
+    if (n < 0 || (n > 0 && (!x || !y || !z || !w))) return fail(h, ITOKMC_ERR_ARG, "bad particle arrays");
+    if (n > (int64_t)h->cap) return fail(h, ITOKMC_ERR_CAPACITY, "more particles than particle_capacity");
+    if (h->P.R > 1 && n > 0 && !realization) return fail(h, ITOKMC_ERR_ARG, "realization array required when R > 1");
+    // stage the SoA arrays in the (about to be overwritten) record buffer A
+    unsigned char* st = reinterpret_cast<unsigned char*>(h->d.recA);
+    double* dx = reinterpret_cast<double*>(st);
+    double* dy = dx + n;
+    double* dz = dy + n;
+    uint32_t* dw = reinterpret_cast<uint32_t*>(dz + n);
+    int32_t* dr = realization ? reinterpret_cast<int32_t*>(dw + n) : nullptr;
+    const cudaMemcpyKind k = mem == ITOKMC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (n > 0) {
+        IK_CHECK(h, cudaMemcpyAsync(dx, x, n * sizeof(double), k, h->s));
+        IK_CHECK(h, cudaMemcpyAsync(dy, y, n * sizeof(double), k, h->s));
+        IK_CHECK(h, cudaMemcpyAsync(dz, z, n * sizeof(double), k, h->s));
+        IK_CHECK(h, cudaMemcpyAsync(dw, w, n * sizeof(uint32_t), k, h->s));
+        if (dr) IK_CHECK(h, cudaMemcpyAsync(dr, realization, n * sizeof(int32_t), k, h->s));
+    }
+    ik::launch_set_particles_f64(h->P, h->d, dx, dy, dz, dw, dr, (uint32_t)n, h->G, h->s);
+    int rc = readback(h);
+    if (rc) return rc;
+    if (h->rb->ctr.err) {
+        h->N = 0;
+        cudaMemsetAsync(h->d.cell_start, 0, (h->G + 1) * sizeof(uint32_t), h->s);
+        cudaStreamSynchronize(h->s);
+        return fail(h, ITOKMC_ERR_ARG, "particle outside the domain, zero weight or bad realization");
+    }
+    h->N = (uint32_t)n;
+    h->st.n_particles = n;
+    return ITOKMC_OK;
+}
+
+int itokmc_read_particles(itokmc_handle* h, double* x, double* y, double* z, uint32_t* w, int32_t* realization,
+                          int64_t* cell, int64_t cap, int64_t* n_out, int32_t mem)
+{
+    IK_GUARD(h);
+    if (mem != ITOKMC_HOST) return fail(h, ITOKMC_ERR_ARG, "read_particles copies to host memory");
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    const uint32_t N = h->N;
+    if (n_out) *n_out = N;
+    if ((int64_t)N > cap) return fail(h, ITOKMC_ERR_CAPACITY, "output buffer smaller than the particle count");
+    std::vector<ik::P64> buf(N);
+    if (N) IK_CHECK(h, cudaMemcpyAsync(buf.data(), h->d.recA, N * sizeof(ik::P64), cudaMemcpyDeviceToHost, h->s));
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    const uint32_t n3 = (uint32_t)h->P.n3;
+    for (uint32_t i = 0; i < N; ++i) {
+        if (x) x[i] = buf[i].x;
+        if (y) y[i] = buf[i].y;
+        if (z) z[i] = buf[i].z;
+        if (w) w[i] = buf[i].w;
+        if (realization) realization[i] = (int32_t)(buf[i].cell / n3);
+        if (cell) cell[i] = (int64_t)(buf[i].cell % n3);
+    }
+    return ITOKMC_OK;
+}
+
+int itokmc_set_ions(itokmc_handle* h, const int64_t* npos, const int64_t* nneg, int32_t mem)
+{
+    IK_GUARD(h);
+    const cudaMemcpyKind k = mem == ITOKMC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (npos) IK_CHECK(h, cudaMemcpyAsync(h->d.Npos, npos, h->G * sizeof(int64_t), k, h->s));
+    if (nneg) IK_CHECK(h, cudaMemcpyAsync(h->d.Nneg, nneg, h->G * sizeof(int64_t), k, h->s));
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    return ITOKMC_OK;
+}
+
+int itokmc_set_field(itokmc_handle* h, const double* E, int32_t mem)
+{
+    IK_GUARD(h);
+    if (!E) return fail(h, ITOKMC_ERR_ARG, "NULL field");
+    const cudaMemcpyKind k = mem == ITOKMC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    IK_CHECK(h, cudaMemcpyAsync(h->d.stage, E, 3 * h->G * sizeof(double), k, h->s));
+    ik::launch_pack_field(h->P, h->d, h->d.stage, h->s);
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    return cuda_check(h, cudaGetLastError(), "set_field");
+}
+
+int itokmc_solve_field(itokmc_handle* h)
+{
+    IK_GUARD(h);
+    cudaMemsetAsync(h->d.ctr, 0, sizeof(ik::Counters), h->s);
+    ik::launch_deposit_only_f64(h->P, h->d, h->N, h->s);
+    ik::launch_rho(h->P, h->d, h->G, h->s);
+    int rc = readback(h);
+    if (rc) return rc;
+    rc = status_of_err(h, h->rb->ctr.err);
+    if (rc) return rc;
+    return stage_field(h);
+}
+
+int itokmc_run_stage(itokmc_handle* h, int32_t stage)
+{
+    IK_GUARD(h);
+    switch (stage) {
+    case ITOKMC_STAGE_TRANSPORT: return stage_transport(h);
+    case ITOKMC_STAGE_KMC: {
+        int rc = stage_kmc(h);
+        if (rc) return rc;
+        IK_CHECK(h, cudaMemcpyAsync(&h->rb->ctr, h->d.ctr, sizeof(ik::Counters), cudaMemcpyDeviceToHost, h->s));
+        IK_CHECK(h, cudaStreamSynchronize(h->s));
+        return status_of_err(h, h->rb->ctr.err & ik::DERR_KMC);
+    }
+    case ITOKMC_STAGE_PARTICLES: return stage_particles(h);
+    case ITOKMC_STAGE_FIELD: return stage_field(h);
+    default: return fail(h, ITOKMC_ERR_ARG, "unknown stage");
+    }
+}
+
+int itokmc_advance_counter(itokmc_handle* h)
+{
+    IK_GUARD(h);
+    h->step += 1;
+    h->P.step = (uint32_t)h->step;
+    h->st.step = h->step;
+    return ITOKMC_OK;
+}
+
+int itokmc_step(itokmc_handle* h, int32_t nsteps)
+{
+    IK_GUARD(h);
+    if (nsteps < 0) return fail(h, ITOKMC_ERR_ARG, "nsteps < 0");
+    for (int k = 0; k < nsteps; ++k) {
+        int rc = stage_transport(h);
+        if (!rc) rc = stage_kmc(h);
+        if (!rc) rc = stage_particles(h);
+        if (!rc) rc = stage_field(h);
+        if (rc) return rc;
+        itokmc_advance_counter(h);
+    }
+    h->st.n_particles = h->N;
+    return ITOKMC_OK;
+}
+
+int itokmc_read_densities(itokmc_handle* h, int32_t r, int32_t which, void* host_out, size_t bytes)
+{
+    IK_GUARD(h);
+    if (!host_out) return fail(h, ITOKMC_ERR_ARG, "NULL output");
+    if (r < -1 || r >= h->P.R) return fail(h, ITOKMC_ERR_ARG, "realization out of range");
+    const size_t n3 = (size_t)h->P.n3;
+    const size_t cnt = r < 0 ? h->G : n3;
+    const size_t off = r < 0 ? 0 : (size_t)r * n3;
+    const void* src = nullptr;
+    int blocks = 1;
+    switch (which) {
+    case ITOKMC_NE_FIX: src = h->d.ne_fix; break;
+    case ITOKMC_XE: src = h->d.Xe; break;
+    case ITOKMC_NPOS: src = h->d.Npos; break;
+    case ITOKMC_NNEG: src = h->d.Nneg; break;
+    case ITOKMC_PHI: src = h->d.lev[0].phi; break;
+    case ITOKMC_RHO: src = h->d.rho; break;
+    case ITOKMC_E:
+        ik::launch_unpack_field(h->P, h->d, h->d.stage, h->s);
+        src = h->d.stage; blocks = 3; break;
+    case ITOKMC_FIRINGS: src = h->d.fired; blocks = 3; break;
+    default: return fail(h, ITOKMC_ERR_ARG, "unknown field");
+    }
+    if (bytes < blocks * cnt * 8) return fail(h, ITOKMC_ERR_ARG, "output buffer too small");
+    for (int b = 0; b < blocks; ++b)
+        IK_CHECK(h, cudaMemcpyAsync(static_cast<char*>(host_out) + b * cnt * 8,
+                                    static_cast<const char*>(src) + (b * h->G + off) * 8, cnt * 8,
+                                    cudaMemcpyDeviceToHost, h->s));
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    return cuda_check(h, cudaGetLastError(), "read_densities");
+}
+
+int itokmc_get_stats(itokmc_handle* h, itokmc_stats* st)
+{
+    IK_GUARD(h);
+    if (!st) return ITOKMC_ERR_ARG;
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    h->st.n_particles = h->N;
+    h->st.kernel_launches = (int64_t)ik::g_launches;
+    *st = h->st;
+    return ITOKMC_OK;
+}
+
+int itokmc_num_particles(itokmc_handle* h, int64_t* n_out)
+{
+    IK_GUARD(h);
+    if (!n_out) return ITOKMC_ERR_ARG;
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    *n_out = h->N;
+    return ITOKMC_OK;
+}
+
+const char* itokmc_last_error(const itokmc_handle* h) { return h ? h->err.c_str() : g_init_err.c_str(); }
+
+const char* itokmc_version(void) { return "itokmc 0.1 (sm_103a)"; }
+
+}  // extern "C"

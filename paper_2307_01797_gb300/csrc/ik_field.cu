@@ -1,0 +1,404 @@
+// ik_field.cu -- field solve (a5): lap(phi) = -rho/eps0, E = -grad(phi).
+//
+// Sec. 4.3: finite-volume discretisation (the 3D standard stencil is the
+// 7-point one) solved by geometric multigrid V-cycles with red-black
+// Gauss-Seidel smoothing, exit at a relative residual of 1e-10.  Boundary
+// conditions of Sec. 5.1: plane electrodes (Dirichlet, phi = 0 at z = lo,
+// E0 L at z = hi; ghost 2 phi_b - phi_1) and homogeneous Neumann side faces
+// (ghost = phi_1).  Cell-centred hierarchy down to 4^3: averaging
+// restriction, trilinear cell-centred prolongation, and a one-block
+// red-black solve at the bottom (the paper uses BiCGSTAB there).
+//
+// Two forms: FP64 V-cycles on the FP64 system, or FP32 V-cycles on the
+// correction equation inside FP64 residual iterative refinement
+// (phi += V32(b - A phi) until the FP64 residual meets the tolerance).
+// Realizations are stacked (slowest index) and solved together; each has
+// its own convergence test.  Norms are reduced in a fixed order.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "ik_common.cuh"
+#include "ik_state.h"
+
+namespace ik {
+
+namespace {
+
+struct Geo {      // one level, all realizations
+    int n, log2n, R;
+    uint64_t cells;   // R n^3
+};
+
+__device__ __forceinline__ void decode(uint64_t t, int log2n, int& r, int& k, int& j, int& i)
+{
+    const int n = 1 << log2n;
+    i = (int)(t & (uint64_t)(n - 1));
+    j = (int)((t >> log2n) & (uint64_t)(n - 1));
+    k = (int)((t >> (2 * log2n)) & (uint64_t)(n - 1));
+    r = (int)(t >> (3 * log2n));
+}
+
+// Sum of interior neighbours and the diagonal count n_int + 2 n_D of the
+// homogeneous operator at (k, j, i).
+template <class T>
+__device__ __forceinline__ T nbr_sum(const T* __restrict__ phi, uint64_t idx, int n, int i, int j, int k,
+                                     int& diag)
+{
+    const uint64_t sy = (uint64_t)n, sz = (uint64_t)n * n;
+    T s = 0;
+    diag = 0;
+    if (i > 0) { s += phi[idx - 1]; ++diag; }
+    if (i < n - 1) { s += phi[idx + 1]; ++diag; }
+    if (j > 0) { s += phi[idx - sy]; ++diag; }
+    if (j < n - 1) { s += phi[idx + sy]; ++diag; }
+    if (k > 0) { s += phi[idx - sz]; ++diag; } else diag += 2;
+    if (k < n - 1) { s += phi[idx + sz]; ++diag; } else diag += 2;
+    return s;
+}
+
+template <class T>
+__global__ void k_smooth(T* __restrict__ phi, const T* __restrict__ rhs, Geo G, T h2, int color)
+{
+    const uint64_t half = G.cells >> 1;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < half; t += (uint64_t)gridDim.x * blockDim.x) {
+        // t enumerates (r, k, j, ih); i = 2 ih + parity
+        const int n = G.n;
+        const int ih = (int)(t & (uint64_t)(n / 2 - 1));
+        const int j = (int)((t >> (G.log2n - 1)) & (uint64_t)(n - 1));
+        const int k = (int)((t >> (2 * G.log2n - 1)) & (uint64_t)(n - 1));
+        const uint64_t r = t >> (3 * G.log2n - 1);
+        const int i = 2 * ih + ((j + k + color) & 1);
+        const uint64_t idx = ((r * n + k) * n + j) * n + i;
+        int diag;
+        const T s = nbr_sum(phi, idx, n, i, j, k, diag);
+        phi[idx] = (s - h2 * rhs[idx]) / (T)diag;
+    }
+}
+
+// Residual r = b - A phi at fine cells, averaged over the 8 children of each
+// coarse cell into the coarse right-hand side.
+template <class T, class TC>
+__global__ void k_resid_restrict(const T* __restrict__ phi, const T* __restrict__ rhs, TC* __restrict__ rhs_c,
+                                 Geo Gc, int nf, T inv_h2)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < Gc.cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        int r, K, J, I;
+        decode(t, Gc.log2n, r, K, J, I);
+        T acc = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
+            const uint64_t idx = (((uint64_t)r * nf + k) * nf + j) * nf + i;
+            int diag;
+            const T s = nbr_sum(phi, idx, nf, i, j, k, diag);
+            acc += rhs[idx] - (s - (T)diag * phi[idx]) * inv_h2;
+        }
+        rhs_c[t] = (TC)(acc * (T)0.125);
+    }
+}
+
+// phi_f += trilinear cell-centred interpolation of the coarse correction
+// (weights 3/4, 1/4 per axis; ghosts: Neumann e, Dirichlet -e).
+template <class T>
+__global__ void k_prolong(T* __restrict__ phi_f, const T* __restrict__ e_c, Geo Gf)
+{
+    const int nc = Gf.n / 2;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < Gf.cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        int r, k, j, i;
+        decode(t, Gf.log2n, r, k, j, i);
+        const int I = i >> 1, J = j >> 1, K = k >> 1;
+        const int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1), K2 = K + ((k & 1) ? 1 : -1);
+        const T* ec = e_c + (uint64_t)r * nc * nc * nc;
+        int ix[2] = { I, I2 }, iy[2] = { J, J2 }, iz[2] = { K, K2 };
+        T wx[2] = { (T)0.75, (T)0.25 }, wy[2] = { (T)0.75, (T)0.25 }, wz[2] = { (T)0.75, (T)0.25 };
+        if (I2 < 0 || I2 >= nc) { ix[1] = I; }
+        if (J2 < 0 || J2 >= nc) { iy[1] = J; }
+        if (K2 < 0 || K2 >= nc) { iz[1] = K; wz[1] = (T)-0.25; }
+        T acc = 0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+                    acc += wx[a] * wy[b] * wz[c] * ec[((uint64_t)iz[c] * nc + iy[b]) * nc + ix[a]];
+        phi_f[t] += acc;
+    }
+}
+
+// Bottom solve: one block per realization, red-black sweeps in shared memory.
+template <class T>
+__global__ void k_bottom(T* __restrict__ phi, const T* __restrict__ rhs, int n, T h2, int sweeps)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T* s = reinterpret_cast<T*>(smem_raw);
+    T* b = s + n * n * n;
+    const int cells = n * n * n;
+    const uint64_t base = (uint64_t)blockIdx.x * cells;
+    for (int c = threadIdx.x; c < cells; c += blockDim.x) { s[c] = phi[base + c]; b[c] = rhs[base + c]; }
+    __syncthreads();
+    for (int it = 0; it < sweeps; ++it) {
+        for (int color = 0; color < 2; ++color) {
+            for (int c = threadIdx.x; c < cells; c += blockDim.x) {
+                const int i = c % n, j = (c / n) % n, k = c / (n * n);
+                if (((i + j + k) & 1) != color) continue;
+                int diag;
+                const T sum = nbr_sum(s, (uint64_t)c, n, i, j, k, diag);
+                s[c] = (sum - h2 * b[c]) / (T)diag;
+            }
+            __syncthreads();
+        }
+    }
+    for (int c = threadIdx.x; c < cells; c += blockDim.x) phi[base + c] = s[c];
+}
+
+// FP64 residual, its squared norm per block (fixed order), and optionally
+// the FP32 copy for the inner V-cycle.  A block covers items*256 cells of
+// one realization.
+constexpr int NORM_TPB = 256;
+
+__global__ void __launch_bounds__(NORM_TPB) k_resid_norm(const double* __restrict__ phi, const double* __restrict__ rhs,
+                                                         float* __restrict__ r32, Geo G, double inv_h2,
+                                                         double* __restrict__ part, int with_b, int items)
+{
+    __shared__ double red[NORM_TPB / 32][2];
+    const uint64_t base = ((uint64_t)blockIdx.x * NORM_TPB) * items;
+    double acc = 0.0, bacc = 0.0;
+    for (int q = 0; q < items; ++q) {
+        const uint64_t t = base + (uint64_t)q * NORM_TPB + threadIdx.x;
+        if (t >= G.cells) break;
+        int r, k, j, i;
+        decode(t, G.log2n, r, k, j, i);
+        int diag;
+        const double s = nbr_sum(phi, t, G.n, i, j, k, diag);
+        const double res = rhs[t] - (s - (double)diag * phi[t]) * inv_h2;
+        if (r32) r32[t] = (float)res;
+        acc += res * res;
+        if (with_b) bacc += rhs[t] * rhs[t];
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, d);
+        bacc += __shfl_xor_sync(0xffffffffu, bacc, d);
+    }
+    if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5][0] = acc; red[threadIdx.x >> 5][1] = bacc; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < NORM_TPB / 32; ++w) { a += red[w][0]; b += red[w][1]; }
+        part[2 * (uint64_t)blockIdx.x] = a;
+        part[2 * (uint64_t)blockIdx.x + 1] = b;
+    }
+}
+
+// Per realization: sum its blocks' partials in order.
+__global__ void k_norm_final(const double* __restrict__ part, int blocks_per_real, int R, double* __restrict__ out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < blocks_per_real; ++q) {
+        a += part[2 * ((uint64_t)r * blocks_per_real + q)];
+        b += part[2 * ((uint64_t)r * blocks_per_real + q) + 1];
+    }
+    out[2 * r] = a;
+    out[2 * r + 1] = b;
+}
+
+__global__ void k_add_correction(double* __restrict__ phi, const float* __restrict__ e, uint64_t cells)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cells; t += (uint64_t)gridDim.x * blockDim.x)
+        phi[t] += (double)e[t];
+}
+
+template <class T>
+__global__ void k_zero(T* __restrict__ a, uint64_t cells)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cells; t += (uint64_t)gridDim.x * blockDim.x)
+        a[t] = (T)0;
+}
+
+// E = -grad(phi) by centred differences with the boundary ghosts, and |E|.
+__global__ void k_efield(const double* __restrict__ phi, E64* __restrict__ E, float4* __restrict__ E32, Geo G,
+                         double h, double phi_top)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G.cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        int r, k, j, i;
+        decode(t, G.log2n, r, k, j, i);
+        const int n = G.n;
+        const uint64_t sy = (uint64_t)n, sz = (uint64_t)n * n;
+        const double c = phi[t];
+        const double xm = i > 0 ? phi[t - 1] : c, xp = i < n - 1 ? phi[t + 1] : c;
+        const double ym = j > 0 ? phi[t - sy] : c, yp = j < n - 1 ? phi[t + sy] : c;
+        const double zm = k > 0 ? phi[t - sz] : -c, zp = k < n - 1 ? phi[t + sz] : 2.0 * phi_top - c;
+        const double ex = (xm - xp) / (2.0 * h), ey = (ym - yp) / (2.0 * h), ez = (zm - zp) / (2.0 * h);
+        const double m = sqrt((ex * ex + ey * ey) + ez * ez);
+        reinterpret_cast<double2*>(E + t)[0] = make_double2(ex, ey);
+        reinterpret_cast<double2*>(E + t)[1] = make_double2(ez, m);
+        if (E32) E32[t] = make_float4((float)ex, (float)ey, (float)ez, (float)m);
+    }
+}
+
+int gridsz(uint64_t n, int tpb) {
+    uint64_t b = (n + tpb - 1) / tpb;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+Geo geo(const Dev& d, int l, int R)
+{
+    Geo g;
+    g.n = d.lev[l].n;
+    g.log2n = 0;
+    while ((1 << g.log2n) < g.n) ++g.log2n;
+    g.R = R;
+    g.cells = (uint64_t)R * g.n * g.n * g.n;
+    return g;
+}
+
+template <class T>
+T* lphi(MGLevel& L);
+template <>
+double* lphi<double>(MGLevel& L) { return L.phi; }
+template <>
+float* lphi<float>(MGLevel& L) { return L.phi32; }
+template <class T>
+T* lrhs(MGLevel& L);
+template <>
+double* lrhs<double>(MGLevel& L) { return L.rhs; }
+template <>
+float* lrhs<float>(MGLevel& L) { return L.rhs32; }
+
+template <class T>
+void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
+{
+    MGLevel& L = d.lev[l];
+    const Geo G = geo(d, l, R);
+    const T h2 = (T)(L.h * L.h);
+    T* phi = lphi<T>(L);
+    T* rhs = lrhs<T>(L);
+    if (l == d.nlev - 1) {
+        const int cells = G.n * G.n * G.n;
+        const size_t sm = 2 * sizeof(T) * cells;
+        ++g_launches;
+        k_bottom<T><<<R, 256, sm, s>>>(phi, rhs, G.n, h2, 4 * cells);
+        return;
+    }
+    const int tpb = 256;
+    for (int it = 0; it < nu1; ++it) {
+        ++g_launches;
+        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, h2, 0);
+        ++g_launches;
+        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, h2, 1);
+    }
+    MGLevel& C = d.lev[l + 1];
+    const Geo Gc = geo(d, l + 1, R);
+    ++g_launches;
+    k_resid_restrict<T, T><<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(phi, rhs, lrhs<T>(C), Gc, G.n, (T)(1.0 / (L.h * L.h)));
+    ++g_launches;
+    k_zero<T><<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(lphi<T>(C), Gc.cells);
+    vcycle<T>(d, l + 1, R, nu1, nu2, s);
+    ++g_launches;
+    k_prolong<T><<<gridsz(G.cells, tpb), tpb, 0, s>>>(phi, lphi<T>(C), G);
+    for (int it = 0; it < nu2; ++it) {
+        ++g_launches;
+        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, h2, 1);
+        ++g_launches;
+        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, h2, 0);
+    }
+}
+
+}  // namespace
+
+// Returns 0 on convergence, ITOKMC_ERR_NOCONV (-6) if max_cycles is reached.
+int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2, int max_cycles,
+                cudaStream_t s, int* cycles_out, double* rel_out)
+{
+    const int R = P.R;
+    MGLevel& L0 = d.lev[0];
+    const Geo G0 = geo(d, 0, R);
+    const double inv_h2 = 1.0 / (L0.h * L0.h);
+    const uint64_t per_real = G0.cells / R;
+    const int items = (int)(per_real / NORM_TPB < 8 ? per_real / NORM_TPB : 8);
+    const int nblk = (int)(G0.cells / ((uint64_t)NORM_TPB * items));
+    const int bpr = nblk / R;
+    std::vector<double> h_norm(2 * R);
+    double worst = 0.0;
+    int cyc = 0;
+    int status = -6;
+    for (cyc = 0; cyc <= max_cycles; ++cyc) {
+        ++g_launches;
+        k_resid_norm<<<nblk, NORM_TPB, 0, s>>>(L0.phi, L0.rhs, precision == 1 ? L0.rhs32 : nullptr, G0, inv_h2,
+                                               d.norm_part, 1, items);
+        ++g_launches;
+        k_norm_final<<<(R + 127) / 128, 128, 0, s>>>(d.norm_part, bpr, R, d.norm_out);
+        cudaMemcpyAsync(h_norm.data(), d.norm_out, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
+        worst = 0.0;
+        bool done = true;
+        for (int r = 0; r < R; ++r) {
+            const double rn = std::sqrt(h_norm[2 * r]), bn = std::sqrt(h_norm[2 * r + 1]);
+            const double rel = bn > 0.0 ? rn / bn : rn;
+            if (rel > worst) worst = rel;
+            if (!(rn <= rtol * bn)) done = false;
+        }
+        if (done) { status = 0; break; }
+        if (cyc == max_cycles) break;
+        if (precision == 1) {
+            ++g_launches;
+            k_zero<float><<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi32, G0.cells);
+            vcycle<float>(d, 0, R, nu1, nu2, s);
+            ++g_launches;
+            k_add_correction<<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi, L0.phi32, G0.cells);
+        } else {
+            vcycle<double>(d, 0, R, nu1, nu2, s);
+        }
+    }
+    if (cycles_out) *cycles_out = cyc;
+    if (rel_out) *rel_out = worst;
+    return status;
+}
+
+__global__ void k_pack_field(const double* __restrict__ E3, E64* __restrict__ E, float4* __restrict__ E32, uint64_t G)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G; t += (uint64_t)gridDim.x * blockDim.x) {
+        const double ex = E3[t], ey = E3[G + t], ez = E3[2 * G + t];
+        const double m = sqrt((ex * ex + ey * ey) + ez * ez);
+        reinterpret_cast<double2*>(E + t)[0] = make_double2(ex, ey);
+        reinterpret_cast<double2*>(E + t)[1] = make_double2(ez, m);
+        if (E32) E32[t] = make_float4((float)ex, (float)ey, (float)ez, (float)m);
+    }
+}
+
+__global__ void k_unpack_field(const E64* __restrict__ E, double* __restrict__ E3, uint64_t G)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G; t += (uint64_t)gridDim.x * blockDim.x) {
+        const E64 e = E[t];
+        E3[t] = e.x; E3[G + t] = e.y; E3[2 * G + t] = e.z;
+    }
+}
+
+void launch_pack_field(const Params& P, Dev& d, const double* E3, cudaStream_t s)
+{
+    const uint64_t G = (uint64_t)P.R * P.n3;
+    ++g_launches;
+    k_pack_field<<<gridsz(G, 256), 256, 0, s>>>(E3, d.E, d.E32, G);
+}
+
+void launch_unpack_field(const Params& P, Dev& d, double* E3, cudaStream_t s)
+{
+    const uint64_t G = (uint64_t)P.R * P.n3;
+    ++g_launches;
+    k_unpack_field<<<gridsz(G, 256), 256, 0, s>>>(d.E, E3, G);
+}
+
+void launch_efield(const Params& P, Dev& d, cudaStream_t s)
+{
+    const Geo G0 = geo(d, 0, P.R);
+    ++g_launches;
+    k_efield<<<gridsz(G0.cells, 256), 256, 0, s>>>(d.lev[0].phi, d.E, d.E32, G0, d.lev[0].h,
+                                                  P.E0 * (P.hi[2] - P.lo[2]));
+}
+
+}  // namespace ik

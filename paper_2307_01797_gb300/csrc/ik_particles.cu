@@ -1,0 +1,1004 @@
+// ik_particles.cu -- particle stages of the Ito-KMC step, FP64 form.
+//
+//   transport (a1-a4): pass 1 interpolates E (Sec. 4.2), pushes every
+//     particle by explicit Euler-Maruyama (Sec. 4.3; v = -mu E, Eq. Vk1),
+//     computes its new cell, deposits its CIC charge in int64 fixed point
+//     (Sec. 4.2) and X_e, and counts per cell; a 3-channel cell scan gives
+//     the new cell offsets; pass 2 moves every particle that stayed in its
+//     cell straight to its final slot and a small kernel places the few that
+//     changed cell.  The result is the stable order (cell, previous index).
+//   rho: space charge snapshot and multigrid right-hand side.
+//   KMC (a6): one thread per occupied cell, Sec. 3.2.3.
+//   particles (a7-a9): loss removal and products (Sec. 4.4, Eq. w), photons
+//     (Sec. 4.5, Eq. photon_transport), kd-tree merge/split (Sec. 4.6).
+#include <cstdio>
+
+#include "ik_common.cuh"
+#include "ik_scan.cuh"
+#include "ik_state.h"
+
+namespace ik {
+
+namespace {
+
+__device__ __forceinline__ P64 ld_p64(const P64* p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    P64 r;
+    r.x = a.x; r.y = a.y; r.z = b.x;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(b.y);
+    r.cell = (uint32_t)bits;
+    r.w = (uint32_t)(bits >> 32);
+    return r;
+}
+
+__device__ __forceinline__ void st_p64(P64* p, const P64& v)
+{
+    const unsigned long long bits = (unsigned long long)v.cell | ((unsigned long long)v.w << 32);
+    reinterpret_cast<double2*>(p)[0] = make_double2(v.x, v.y);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v.z, __longlong_as_double((long long)bits));
+}
+
+__device__ __forceinline__ E64 ld_e64(const E64* p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return E64{ a.x, a.y, b.x, b.y };
+}
+
+// Trilinear interpolation of the cell-centred field at (x,y,z); sum order z
+// outer, y, x inner; weight (wx*wy)*wz.
+__device__ __forceinline__ void interp_f64(const Params& P, const E64* __restrict__ E, const double X[3],
+                                           double Ep[3])
+{
+    int ia[3], ib[3];
+    double f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cic_axis(X[a], P.lo[a], P.h[a], P.n, ia[a], ib[a], f[a]);
+    const double wx[2] = { 1.0 - f[0], f[0] }, wy[2] = { 1.0 - f[1], f[1] }, wz[2] = { 1.0 - f[2], f[2] };
+    const int ix[2] = { ia[0], ib[0] }, iy[2] = { ia[1], ib[1] }, iz[2] = { ia[2], ib[2] };
+    double ax = 0.0, ay = 0.0, az = 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const double wgt = (wx[a] * wy[b]) * wz[c];
+                const E64 e = ld_e64(E + ((size_t)iz[c] * P.n + iy[b]) * P.n + ix[a]);
+                ax = ax + wgt * e.x;
+                ay = ay + wgt * e.y;
+                az = az + wgt * e.z;
+            }
+    Ep[0] = ax; Ep[1] = ay; Ep[2] = az;
+}
+
+// Int64 CIC deposition of weight w at X into ne (one realization's block).
+__device__ __forceinline__ void deposit_f64(const Params& P, unsigned long long* __restrict__ ne,
+                                            const double X[3], uint32_t w)
+{
+    const long long one = 1ll << P.frac_bits;
+    const double scale = (double)one;
+    int ia[3], ib[3];
+    long long A[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double f;
+        cic_axis(X[a], P.lo[a], P.h[a], P.n, ia[a], ib[a], f);
+        const long long q = (long long)floor(f * scale);
+        A[a][0] = one - q;
+        A[a][1] = q;
+    }
+    const int ix[2] = { ia[0], ib[0] }, iy[2] = { ia[1], ib[1] }, iz[2] = { ia[2], ib[2] };
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const long long v = (long long)w * A[0][a] * A[1][b] * A[2][c];
+                if (v) atomicAdd(ne + ((size_t)iz[c] * P.n + iy[b]) * P.n + ix[a], (unsigned long long)v);
+            }
+}
+
+__device__ __forceinline__ int real_of(const Params& P, uint32_t g) { return (int)(g >> (3 * P.log2n)); }
+
+// ------------------------------------------------------------------ pass 1
+__global__ void __launch_bounds__(TPB) k_push_f64(
+    Params P, const P64* __restrict__ A, P64* __restrict__ B, uint32_t* __restrict__ keyB, uint32_t N,
+    const uint32_t* __restrict__ cell_start, const E64* __restrict__ E, int32_t* __restrict__ cnt_new,
+    int32_t* __restrict__ in_cnt, int32_t* __restrict__ in_before, unsigned long long* __restrict__ Xe,
+    unsigned long long* __restrict__ ne_fix, Mover* __restrict__ movers, uint32_t mover_cap,
+    Counters* __restrict__ ctr, uint32_t* __restrict__ blk_stay)
+{
+    const uint32_t i = blockIdx.x * TPB + threadIdx.x;
+    bool alive = false, mover = false;
+    uint32_t gnew = 0, w = 0;
+    if (i < N) {
+        const P64 p = ld_p64(A + i);
+        const uint32_t gold = p.cell;
+        const int r = real_of(P, gold);
+        const uint32_t idx = i - cell_start[(size_t)r * P.n3];
+        const size_t ebase = (size_t)r * P.n3;
+        w = p.w;
+        const double X[3] = { p.x, p.y, p.z };
+        double Ep[3];
+        interp_f64(P, E + ebase, X, Ep);
+        Stream s(seed_of(P, r), idx, P.step, TAG_PUSH, 0);
+        const double u1 = s.uniform(), u2 = s.uniform(), u3 = s.uniform(), u4 = s.uniform();
+        const double r1 = sqrt(-2.0 * dlog(u1)), r2 = sqrt(-2.0 * dlog(u3));
+        double s1, c1, s2, c2;
+        dsincos2pi(u2, &s1, &c1);
+        dsincos2pi(u4, &s2, &c2);
+        const double Nn[3] = { r1 * c1, r1 * s1, r2 * c2 };
+        const double nmu = -P.mu;
+        double Xn[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Xn[a] = (X[a] + (nmu * Ep[a]) * P.dt) + P.sdt * Nn[a];
+            inside = inside && (Xn[a] >= P.lo[a]) && (Xn[a] < P.hi[a]);
+        }
+        P64 q;
+        q.x = Xn[0]; q.y = Xn[1]; q.z = Xn[2]; q.w = w;
+        if (inside) {
+            const int ix = cell_axis(Xn[0], P.lo[0], P.h[0], P.n);
+            const int iy = cell_axis(Xn[1], P.lo[1], P.h[1], P.n);
+            const int iz = cell_axis(Xn[2], P.lo[2], P.h[2], P.n);
+            gnew = (uint32_t)(ebase + ((size_t)iz * P.n + iy) * P.n + ix);
+            alive = true;
+            mover = gnew != gold;
+            q.cell = gnew;
+            keyB[i] = gnew | (mover ? KEY_MOVER : 0u);
+            deposit_f64(P, ne_fix + ebase, Xn, w);
+            if (mover) {
+                atomicAdd(in_cnt + gnew, 1);
+                if (gold < gnew) atomicAdd(in_before + gnew, 1);
+                const unsigned long long slot = atomicAdd(&ctr->n_movers, 1ull);
+                if (slot < mover_cap) movers[slot] = Mover{ gnew, i };
+                else atomicOr(&ctr->err, DERR_CAPACITY);
+            }
+        } else {
+            q.cell = gold;
+            keyB[i] = KEY_DEAD;
+            atomicAdd(&ctr->outflow[r], (unsigned long long)w);
+        }
+        st_p64(B + i, q);
+    }
+    unsigned long long v = alive ? (unsigned long long)w : 0ull;
+    unsigned c = alive ? 1u : 0u;
+    if (warp_run_sum(gnew, alive, v, c)) {
+        atomicAdd(cnt_new + gnew, (int)c);
+        atomicAdd(Xe + gnew, v);
+    }
+    const int nstay = __syncthreads_count(alive && !mover);
+    if (threadIdx.x == 0) blk_stay[blockIdx.x] = (uint32_t)nstay;
+}
+
+// Exclusive scan over the pass-1 blocks of their stayer counts.
+struct BlockScanOp {
+    const uint32_t* blk;
+    uint32_t* prefix;
+    __device__ void load(uint64_t g, long long v[1]) const { v[0] = blk[g]; }
+    __device__ void store(uint64_t g, const long long ex[1], const long long*) const { prefix[g] = (uint32_t)ex[0]; }
+    __device__ void total(const long long*) const {}
+};
+
+// Cell scan: new offsets, stayer offsets, mover offsets.
+struct TransportScanOp {
+    const int32_t* cnt_new;
+    const int32_t* in_cnt;
+    const int32_t* in_before;
+    uint32_t* new_start;
+    int64_t* delta;
+    uint32_t* in_off;
+    uint64_t G;
+    __device__ void load(uint64_t g, long long v[3]) const
+    {
+        const int cn = cnt_new[g], ic = in_cnt[g];
+        v[0] = cn; v[1] = cn - ic; v[2] = ic;
+    }
+    __device__ void store(uint64_t g, const long long ex[3], const long long*) const
+    {
+        new_start[g] = (uint32_t)ex[0];
+        delta[g] = ex[0] + in_before[g] - ex[1];
+        in_off[g] = (uint32_t)ex[2];
+    }
+    __device__ void total(const long long t[3]) const
+    {
+        new_start[G] = (uint32_t)t[0];
+        in_off[G] = (uint32_t)t[2];
+    }
+};
+
+// ------------------------------------------------------------------ pass 2
+__device__ __forceinline__ uint32_t block_excl_count(bool flag, uint32_t* total)
+{
+    __shared__ uint32_t wcnt[TPB / 32];
+    const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    const uint32_t within = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) wcnt[wid] = __popc(bal);
+    __syncthreads();
+    uint32_t pre = 0, tot = 0;
+#pragma unroll
+    for (int k = 0; k < TPB / 32; ++k) {
+        if (k < (int)wid) pre += wcnt[k];
+        tot += wcnt[k];
+    }
+    if (total) *total = tot;
+    return pre + within;
+}
+
+__global__ void __launch_bounds__(TPB) k_scatter_f64(const P64* __restrict__ B, P64* __restrict__ A,
+                                                     const uint32_t* __restrict__ keyB, uint32_t N,
+                                                     const uint32_t* __restrict__ blk_prefix,
+                                                     const int64_t* __restrict__ delta, uint32_t cap,
+                                                     Counters* __restrict__ ctr)
+{
+    const uint32_t i = blockIdx.x * TPB + threadIdx.x;
+    uint32_t k = KEY_DEAD;
+    if (i < N) k = keyB[i];
+    const bool stay = !(k & (KEY_DEAD | KEY_MOVER));
+    const uint32_t rank = block_excl_count(stay, nullptr);
+    if (stay) {
+        const uint32_t g = k & KEY_MASK;
+        const long long pos = (long long)blk_prefix[blockIdx.x] + rank + delta[g];
+        if (pos >= 0 && pos < (long long)cap) st_p64(A + pos, ld_p64(B + i));
+        else atomicOr(&ctr->err, DERR_INTERNAL);
+    }
+}
+
+__global__ void k_mover_place(const Mover* __restrict__ movers, const Counters* __restrict__ ctr,
+                              uint32_t mover_cap, const uint32_t* __restrict__ in_off,
+                              int32_t* __restrict__ cursor, uint32_t* __restrict__ sorted)
+{
+    const uint32_t n = (uint32_t)min(ctr->n_movers, (unsigned long long)mover_cap);
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        const uint32_t g = movers[m].g;
+        const uint32_t slot = in_off[g] + (uint32_t)atomicAdd(cursor + g, 1);
+        if (slot < mover_cap) sorted[slot] = m;
+    }
+}
+
+__global__ void k_mover_write_f64(const Mover* __restrict__ movers, const Counters* __restrict__ ctr,
+                                  uint32_t mover_cap, const uint32_t* __restrict__ sorted,
+                                  const uint32_t* __restrict__ in_off, const int32_t* __restrict__ in_cnt,
+                                  const int32_t* __restrict__ in_before, const int32_t* __restrict__ cnt_new,
+                                  const uint32_t* __restrict__ new_start, int32_t* __restrict__ cursor,
+                                  const P64* __restrict__ B, P64* __restrict__ A)
+{
+    const uint32_t n = (uint32_t)min(ctr->n_movers, (unsigned long long)mover_cap);
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const Mover mv = movers[sorted[s]];
+        const uint32_t g = mv.g;
+        const uint32_t b = in_off[g], e = b + (uint32_t)in_cnt[g];
+        uint32_t rank = 0;
+        for (uint32_t t = b; t < e && t < mover_cap; ++t) rank += movers[sorted[t]].i < mv.i;
+        const uint32_t stay = (uint32_t)(cnt_new[g] - in_cnt[g]);
+        const uint32_t pos = new_start[g] + rank + (rank >= (uint32_t)in_before[g] ? stay : 0u);
+        if (pos < mover_cap && e <= mover_cap) st_p64(A + pos, ld_p64(B + mv.i));
+        cursor[g] = 0;
+    }
+}
+
+// ------------------------------------------------------------------ deposit only
+__global__ void __launch_bounds__(TPB) k_deposit_f64(Params P, const P64* __restrict__ A, uint32_t N,
+                                                     unsigned long long* __restrict__ Xe,
+                                                     unsigned long long* __restrict__ ne_fix)
+{
+    const uint32_t i = blockIdx.x * TPB + threadIdx.x;
+    bool alive = i < N;
+    uint32_t g = 0, w = 0;
+    if (alive) {
+        const P64 p = ld_p64(A + i);
+        g = p.cell;
+        w = p.w;
+        const double X[3] = { p.x, p.y, p.z };
+        deposit_f64(P, ne_fix + (size_t)real_of(P, g) * P.n3, X, w);
+    }
+    unsigned long long v = alive ? (unsigned long long)w : 0ull;
+    unsigned c = alive ? 1u : 0u;
+    if (warp_run_sum(g, alive, v, c)) atomicAdd(Xe + g, v);
+}
+
+// ------------------------------------------------------------------ rho
+// rho_fixed = 2^3s (N+ - N-) - ne_fix (units q_e 2^-3s per cell) and the
+// multigrid right-hand side b = -rho/eps0 with the electrode potentials
+// folded in (ghost 2 phi_b - phi_1 at z faces: -2 phi_b / h^2).
+__global__ void k_rho(Params P, const int64_t* __restrict__ Npos, const int64_t* __restrict__ Nneg,
+                      const unsigned long long* __restrict__ ne_fix, int64_t* __restrict__ rho,
+                      double* __restrict__ rhs, uint64_t G, double qscale, double phi_top,
+                      Counters* __restrict__ ctr)
+{
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
+        const long long dq = Npos[g] - Nneg[g];
+        const unsigned long long ne = ne_fix[g];
+        const long long lim = 1ll << (62 - 3 * P.frac_bits);
+        if (dq >= lim || dq <= -lim || ne >= (1ull << 62)) atomicOr(&ctr->err, DERR_OVERFLOW);
+        const long long rf = dq * (1ll << (3 * P.frac_bits)) - (long long)ne;
+        rho[g] = rf;
+        const int k = (int)((g >> (2 * P.log2n)) & (uint64_t)(P.n - 1));
+        double b = -((double)rf * qscale) / 8.8541878128e-12;
+        if (k == P.n - 1) b = b - 2.0 * phi_top / (P.h[2] * P.h[2]);
+        rhs[g] = b;
+    }
+}
+
+// ------------------------------------------------------------------ KMC
+// Sec. 3.2.3 for the network {e -> 2e + M+, e -> M-, e -> e + gamma}; the
+// SSA switch is tested before the critical draw (Cao et al. 2006).
+__device__ int kmc_cell(const Params& P, Stream& s, long long X0, const double kr[3], long long fired[3])
+{
+    const int nu[3] = { +1, -1, 0 };
+    long long X = X0;
+    const double dt = P.dt;
+    double tau = 0.0;
+    fired[0] = fired[1] = fired[2] = 0;
+    for (int guard = 0; guard < 100000; ++guard) {
+        if (!(tau < dt)) return 0;
+        const double xd = (double)X;
+        const double a[3] = { kr[0] * xd, kr[1] * xd, kr[2] * xd };
+        const double A = (a[0] + a[1]) + a[2];
+        if (!(A > 0.0)) return 0;
+        const bool crit[3] = { false, X < (long long)P.n_crit, false };
+        double Ac = 0.0;
+        for (int r = 0; r < 3; ++r) if (crit[r]) Ac = Ac + a[r];
+        double dtnc = __longlong_as_double(0x7ff0000000000000ll);
+        if (!isinf(P.eps)) {
+            double xi = 0.0, sig2 = 0.0;
+            bool any = false;
+            for (int r = 0; r < 3; ++r) {
+                if (crit[r]) continue;
+                any = true;
+                xi = xi + (double)nu[r] * a[r];
+                sig2 = sig2 + (double)(nu[r] * nu[r]) * a[r];
+            }
+            if (any) {
+                double num = P.eps * xd;
+                if (num < 1.0) num = 1.0;
+                const double inf = __longlong_as_double(0x7ff0000000000000ll);
+                const double t1 = (xi != 0.0) ? num / fabs(xi) : inf;
+                const double t2 = (sig2 != 0.0) ? (num * num) / sig2 : inf;
+                dtnc = t1 < t2 ? t1 : t2;
+            }
+        }
+        double dtc = -1.0;
+        bool accepted = false;
+        for (int rej = 0; rej < 10000 && !accepted; ++rej) {
+            const double rem = dt - tau;
+            double dtau = dtnc < rem ? dtnc : rem;
+            long long k[3] = { 0, 0, 0 };
+            double adv;
+            if (A * dtau <= 1.0) {
+                long long Xs = X;
+                double t = 0.0;
+                for (int ev = 0; ev < P.n_ssa; ++ev) {
+                    const double xs = (double)Xs;
+                    const double as[3] = { kr[0] * xs, kr[1] * xs, kr[2] * xs };
+                    const double As = (as[0] + as[1]) + as[2];
+                    if (!(As > 0.0)) { t = dtau; break; }
+                    const double dte = (-dlog(s.uniform())) / As;
+                    if (t + dte > dtau) { t = dtau; break; }
+                    t = t + dte;
+                    const double target = s.uniform() * As;
+                    double cum = 0.0;
+                    int j = 2;
+                    for (int r = 0; r < 3; ++r) {
+                        cum = cum + as[r];
+                        if (cum > target) { j = r; break; }
+                    }
+                    k[j] += 1;
+                    Xs += nu[j];
+                }
+                adv = t;
+            } else {
+                if (dtc < 0.0)
+                    dtc = (Ac > 0.0) ? (-dlog(s.uniform())) / Ac : __longlong_as_double(0x7ff0000000000000ll);
+                if (dtc < dtnc && dtc < rem) {
+                    dtau = dtc;
+                    const double target = s.uniform() * Ac;
+                    double cum = 0.0;
+                    int rc = -1, last = -1;
+                    for (int r = 0; r < 3; ++r) {
+                        if (!crit[r]) continue;
+                        last = r;
+                        cum = cum + a[r];
+                        if (cum > target) { rc = r; break; }
+                    }
+                    if (rc < 0) rc = last;
+                    k[rc] += 1;
+                }
+                for (int r = 0; r < 3; ++r) {
+                    if (crit[r]) continue;
+                    const long long kk = dpoisson(s, a[r] * dtau);
+                    if (kk < 0) return -1;
+                    k[r] += kk;
+                }
+                adv = dtau;
+            }
+            const long long Xn = X + k[0] - k[1];
+            if (Xn < 0) {
+                dtnc = dtau * 0.5;
+                continue;
+            }
+            X = Xn;
+            fired[0] += k[0]; fired[1] += k[1]; fired[2] += k[2];
+            if (adv >= rem) tau = dt; else tau = tau + adv;
+            accepted = true;
+        }
+        if (!accepted) return -1;
+    }
+    return -1;
+}
+
+__global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const E64* __restrict__ E,
+                      int64_t* __restrict__ fired, int64_t* __restrict__ Npos, int64_t* __restrict__ Nneg,
+                      uint64_t G, Counters* __restrict__ ctr)
+{
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
+        long long f[3] = { 0, 0, 0 };
+        const long long X0 = (long long)Xe[g];
+        if (X0 > 0) {
+            const E64 e = ld_e64(E + g);
+            const double Em = e.m;
+            const double ve = P.mu * Em;
+            const double alpha = (Em > 0.0) ? P.alpha_A * dexp(-(P.alpha_B / Em)) : 0.0;
+            double kr[3];
+            kr[0] = alpha * ve;
+            kr[1] = P.eta * ve;
+            kr[2] = P.photon_ratio * kr[0];
+            const int r = real_of(P, (uint32_t)g);
+            const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
+            Stream s(seed_of(P, r), c, P.step, TAG_KMC, 0);
+            if (kmc_cell(P, s, X0, kr, f) != 0) {
+                atomicOr(&ctr->err, DERR_KMC);
+                ctr->kmc_fail_cell = (unsigned)g;
+            }
+            Npos[g] += f[0];
+            Nneg[g] += f[1];
+            atomicAdd(&ctr->ion, (unsigned long long)f[0]);
+            atomicAdd(&ctr->att, (unsigned long long)f[1]);
+            atomicAdd(&ctr->phot, (unsigned long long)f[2]);
+        }
+        fired[g] = f[0];
+        fired[G + g] = f[1];
+        fired[2 * G + g] = f[2];
+    }
+}
+
+// ------------------------------------------------------------------ loss
+// Systematic integer removal of L = -dN electrons from the cell's particles
+// in canonical order: particle p loses floor((C_p L + R)/W) -
+// floor((C_{p-1} L + R)/W), R = (64-bit draw) mod W.
+__global__ void k_loss_f64(Params P, P64* __restrict__ A, const uint32_t* __restrict__ cs,
+                           const unsigned long long* __restrict__ Xe, const int64_t* __restrict__ fired,
+                           uint64_t G)
+{
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
+        const long long dN = fired[g] - fired[G + g];
+        if (dN >= 0) continue;
+        const unsigned long long L = (unsigned long long)(-dN);
+        const unsigned long long W = Xe[g];
+        const int r = real_of(P, (uint32_t)g);
+        const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
+        Stream s(seed_of(P, r), c, P.step, TAG_PRODUCT, (uint32_t)P.n_new);
+        const uint32_t a = s.u32(), b = s.u32();
+        const unsigned long long R = (((unsigned long long)a << 32) | b) % W;
+        unsigned __int128 C = 0;
+        for (uint32_t q = cs[g]; q < cs[g + 1]; ++q) {
+            const unsigned __int128 before = (C * L + R) / W;
+            const uint32_t w = A[q].w;
+            C += w;
+            const unsigned __int128 after = (C * L + R) / W;
+            A[q].w = (uint32_t)(w - (unsigned long long)(after - before));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ photons
+// One superphoton (cell c, slot j): emission point, kappa, distance, direction.
+__device__ __forceinline__ void photon_sample(const Params& P, uint64_t seed, uint32_t c, uint32_t j,
+                                              const int ijk[3], double lnK, double Y0[3], double& r,
+                                              double dir[3])
+{
+    Stream s(seed, c, P.step, TAG_PHOTON, j);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double u = s.uniform();
+        Y0[a] = P.lo[a] + ((double)ijk[a] + u) * P.h[a];
+    }
+    const double kappa = P.kappa_lo * dexp(s.uniform() * lnK);
+    r = (-dlog(s.uniform())) / kappa;
+    const double cz = 2.0 * s.uniform() - 1.0;
+    double sphi, cphi;
+    dsincos2pi(s.uniform(), &sphi, &cphi);
+    const double st = sqrt((1.0 - cz) * (1.0 + cz));
+    dir[0] = st * cphi;
+    dir[1] = st * sphi;
+    dir[2] = cz;
+}
+
+__global__ void k_photons(Params P, const int64_t* __restrict__ fired, uint64_t G,
+                          Photo* __restrict__ photos, uint32_t photo_cap, int32_t* __restrict__ photo_cnt,
+                          unsigned long long* __restrict__ photo_w, int64_t* __restrict__ Npos,
+                          Counters* __restrict__ ctr)
+{
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
+        const long long Gm = fired[2 * G + g];
+        if (Gm <= 0) continue;
+        const double lnK = dlog(P.kappa_hi / P.kappa_lo);
+        const int r = real_of(P, (uint32_t)g);
+        const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
+        const int ijk[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
+                             (int)(c >> (2 * P.log2n)) };
+        const long long m = Gm < P.n_new ? Gm : P.n_new;
+        const long long wq = Gm / m, rem = Gm % m;
+        const uint64_t seed = seed_of(P, r);
+        for (long long j = 0; j < m; ++j) {
+            const long long wj = wq + (j == 0 ? rem : 0);
+            double Y0[3], rr, dir[3], Ya[3];
+            photon_sample(P, seed, c, (uint32_t)j, ijk, lnK, Y0, rr, dir);
+            bool inside = true;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                Ya[a] = Y0[a] + rr * dir[a];
+                inside = inside && (Ya[a] >= P.lo[a]) && (Ya[a] < P.hi[a]);
+            }
+            if (!inside) {
+                atomicAdd(&ctr->lost[r], (unsigned long long)wj);
+                continue;
+            }
+            if (wj > 0xffffffffll) atomicOr(&ctr->err, DERR_OVERFLOW);
+            const int ix = cell_axis(Ya[0], P.lo[0], P.h[0], P.n);
+            const int iy = cell_axis(Ya[1], P.lo[1], P.h[1], P.n);
+            const int iz = cell_axis(Ya[2], P.lo[2], P.h[2], P.n);
+            const uint32_t gd = (uint32_t)((size_t)r * P.n3 + ((size_t)iz * P.n + iy) * P.n + ix);
+            atomicAdd((unsigned long long*)(Npos + gd), (unsigned long long)wj);
+            atomicAdd(photo_cnt + gd, 1);
+            atomicAdd(photo_w + gd, (unsigned long long)wj);
+            atomicAdd(&ctr->absorbed_w, (unsigned long long)wj);
+            const unsigned long long slot = atomicAdd(&ctr->n_photo, 1ull);
+            if (slot < photo_cap) {
+                Photo ph;
+                ph.x = Ya[0]; ph.y = Ya[1]; ph.z = Ya[2];
+                ph.g = gd; ph.src = c; ph.slot = (uint32_t)j; ph.w = (uint32_t)wj;
+                photos[slot] = ph;
+            } else {
+                atomicOr(&ctr->err, DERR_CAPACITY);
+            }
+        }
+    }
+}
+
+__global__ void k_photo_place(const Photo* __restrict__ photos, const Counters* __restrict__ ctr,
+                              uint32_t photo_cap, const uint32_t* __restrict__ photo_off,
+                              int32_t* __restrict__ cursor, uint32_t* __restrict__ sorted)
+{
+    const uint32_t n = (uint32_t)min(ctr->n_photo, (unsigned long long)photo_cap);
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        const uint32_t g = photos[m].g;
+        const uint32_t slot = photo_off[g] + (uint32_t)atomicAdd(cursor + g, 1);
+        if (slot < photo_cap) sorted[slot] = m;
+    }
+}
+
+// ------------------------------------------------------------------ merge scan
+// Per cell: W = X_e + dN + photo weight -> min(W, ppc) leaves; photo offsets;
+// work elements M + ppc (global scratch only for lists too long for the
+// warp's shared-memory buffers).
+constexpr int MERGE_SMEM = 160;   // elements per shared buffer (x3 per warp)
+constexpr int MERGE_WARPS = 4;
+
+struct MergeScanOp {
+    const unsigned long long* Xe;
+    const int64_t* fired;
+    const unsigned long long* photo_w;
+    const int32_t* photo_cnt;
+    const uint32_t* cs;
+    uint32_t* out_start;
+    uint32_t* photo_off;
+    uint64_t* work_off;
+    uint64_t G;
+    int ppc, n_new;
+    __device__ void load(uint64_t g, long long v[3]) const
+    {
+        const long long dN = fired[g] - fired[G + g];
+        const long long W = (long long)Xe[g] + dN + (long long)photo_w[g];
+        v[0] = W < ppc ? W : ppc;
+        v[1] = photo_cnt[g];
+        const long long M = (long long)(cs[g + 1] - cs[g]) + (dN > 0 ? (dN < n_new ? dN : n_new) : 0) + photo_cnt[g];
+        v[2] = (M > 0 && M + ppc > MERGE_SMEM) ? (M + ppc) : 0;
+    }
+    __device__ void store(uint64_t g, const long long ex[3], const long long*) const
+    {
+        out_start[g] = (uint32_t)ex[0];
+        photo_off[g] = (uint32_t)ex[1];
+        work_off[g] = (uint64_t)ex[2];
+    }
+    __device__ void total(const long long t[3]) const
+    {
+        out_start[G] = (uint32_t)t[0];
+        photo_off[G] = (uint32_t)t[1];
+        work_off[G] = (uint64_t)t[2];
+    }
+};
+
+// ------------------------------------------------------------------ merge
+struct MP {           // merge work element (FP64 form)
+    double x, y, z;
+    uint32_t w;
+    uint32_t pad;
+};
+
+__device__ __forceinline__ double mp_coord(const MP& p, int a) { return a == 0 ? p.x : (a == 1 ? p.y : p.z); }
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, d));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, d));
+    return v;
+}
+
+// Splits node src[0..m) of weight W (>= 2) into dst: left part then right
+// part.  tmp holds the node sorted along the split axis.  Returns nl.
+__device__ uint32_t split_node(const MP* src, uint32_t m, unsigned long long W, MP* tmp, MP* dst,
+                               uint32_t* nr_out)
+{
+    const unsigned lane = lane_id();
+    // bounding box and axis (largest extent, ties to the lowest axis)
+    double lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { lo[a] = 1e300; hi[a] = -1e300; }
+    for (uint32_t j = lane; j < m; j += 32) {
+        const MP p = src[j];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double v = mp_coord(p, a);
+            lo[a] = fmin(lo[a], v);
+            hi[a] = fmax(hi[a], v);
+        }
+    }
+    double ext[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ext[a] = warp_max(hi[a]) - warp_min(lo[a]);
+    int axis = 0;
+    if (ext[1] > ext[axis]) axis = 1;
+    if (ext[2] > ext[axis]) axis = 2;
+    // stable rank sort by (coordinate, list position)
+    for (uint32_t j = lane; j < m; j += 32) {
+        const MP pj = src[j];
+        const double cj = mp_coord(pj, axis);
+        uint32_t rank = 0;
+        for (uint32_t k = 0; k < m; ++k) {
+            const double ck = mp_coord(src[k], axis);
+            rank += (ck < cj) || (ck == cj && k < j);
+        }
+        tmp[rank] = pj;
+    }
+    __syncwarp();
+    // weighted median p': first index with 2 C_p > W
+    unsigned long long carry = 0, Cpm = 0;
+    uint32_t pm = m - 1;
+    for (uint32_t base = 0; base < m; base += 32) {
+        const uint32_t j = base + lane;
+        unsigned long long v = j < m ? tmp[j].w : 0ull;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, v, d);
+            if ((int)lane >= d) v += y;
+        }
+        const unsigned long long Cj = carry + v;
+        const unsigned bal = __ballot_sync(0xffffffffu, j < m && 2ull * Cj > W);
+        if (bal) {
+            const int src_lane = __ffs(bal) - 1;
+            pm = base + src_lane;
+            Cpm = __shfl_sync(0xffffffffu, Cj, src_lane);
+            break;
+        }
+        carry = __shfl_sync(0xffffffffu, Cj, 31);
+    }
+    const MP med = tmp[pm];
+    const unsigned long long WL = Cpm - med.w;
+    const unsigned long long WR = W - Cpm;
+    bool left_med, right_med;
+    MP ml = med, mr = med;
+    if (med.w == 1) {
+        left_med = WL <= WR;
+        right_med = !left_med;
+    } else {
+        const unsigned long long a = (W + 1) / 2 - WL;
+        const unsigned long long b = med.w - a;
+        ml.w = (uint32_t)a;
+        mr.w = (uint32_t)b;
+        left_med = a > 0;
+        right_med = b > 0;
+    }
+    const uint32_t nl = pm + (left_med ? 1u : 0u);
+    for (uint32_t j = lane; j < pm; j += 32) dst[j] = tmp[j];
+    if (lane == 0 && left_med) dst[pm] = ml;
+    const uint32_t roff = nl;
+    const uint32_t rstart = right_med ? 1u : 0u;
+    if (lane == 0 && right_med) dst[roff] = mr;
+    for (uint32_t j = pm + 1 + lane; j < m; j += 32) dst[roff + rstart + (j - pm - 1)] = tmp[j];
+    __syncwarp();
+    *nr_out = rstart + (m - pm - 1);
+    return nl;
+}
+
+__global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge_f64(
+    Params P, const P64* __restrict__ A, const uint32_t* __restrict__ cs, const int64_t* __restrict__ fired,
+    const Photo* __restrict__ photos, const uint32_t* __restrict__ photo_sorted,
+    const uint32_t* __restrict__ photo_off, const uint32_t* __restrict__ out_start,
+    const uint64_t* __restrict__ work_off, MP* __restrict__ work, uint64_t work_cap, P64* __restrict__ out,
+    uint64_t G, uint32_t cap, uint32_t photo_cap, Counters* __restrict__ ctr)
+{
+    __shared__ MP sbuf[MERGE_WARPS][3][MERGE_SMEM];
+    __shared__ uint32_t sb[MERGE_WARPS][2][257];
+    const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
+    const uint64_t nchunks = (G + 31) / 32;
+    const uint64_t gw = (uint64_t)blockIdx.x * MERGE_WARPS + wid;
+    const uint64_t nwarps = (uint64_t)gridDim.x * MERGE_WARPS;
+    const int T = P.ppc;
+    for (uint64_t chunk = gw; chunk < nchunks; chunk += nwarps) {
+        const uint64_t g0 = chunk * 32 + lane;
+        const bool has = g0 < G && out_start[g0 + 1] > out_start[g0];
+        unsigned todo = __ballot_sync(0xffffffffu, has);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint64_t g = chunk * 32 + l;
+            const int r = real_of(P, (uint32_t)g);
+            const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
+            const long long dN = fired[g] - fired[G + g];
+            const uint32_t e0 = cs[g], e1 = cs[g + 1];
+            const uint32_t mprod = dN > 0 ? (uint32_t)(dN < P.n_new ? dN : P.n_new) : 0u;
+            const uint32_t p0 = photo_off[g], np = photo_off[g + 1] - p0;
+            const uint32_t Mmax = (e1 - e0) + mprod + np;
+            if ((uint64_t)p0 + np > photo_cap || out_start[g + 1] > cap) {
+                if (lane == 0) atomicOr(&ctr->err, DERR_CAPACITY);
+                continue;
+            }
+            MP *cur, *nxt, *tmp;
+            if (Mmax + T <= MERGE_SMEM) {
+                cur = sbuf[wid][0]; nxt = sbuf[wid][1]; tmp = sbuf[wid][2];
+            } else {
+                const uint64_t S = (uint64_t)Mmax + T;
+                if (work_off[g] + S > work_cap) {
+                    if (lane == 0) atomicOr(&ctr->err, DERR_CAPACITY);
+                    continue;
+                }
+                MP* base = work + 3 * work_off[g];
+                cur = base; nxt = base + S; tmp = base + 2 * S;
+            }
+            // gather: existing (w > 0, canonical order), then new particles in
+            // (source cell, products before photoelectrons, slot) order
+            uint32_t M = 0;
+            for (uint32_t b = e0; b < e1; b += 32) {
+                const uint32_t q = b + lane;
+                P64 p;
+                const bool ok = q < e1 && (p = ld_p64(A + q), p.w > 0);
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                if (ok) {
+                    MP e; e.x = p.x; e.y = p.y; e.z = p.z; e.w = p.w; e.pad = 0;
+                    cur[M + __popc(bal & ((1u << lane) - 1u))] = e;
+                }
+                M += __popc(bal);
+            }
+            // photoelectrons: rank by (source, slot)
+            uint32_t n_lt = 0;
+            for (uint32_t j = lane; j < np; j += 32) {
+                const Photo pj = photos[photo_sorted[p0 + j]];
+                n_lt += pj.src < c;
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) n_lt += __shfl_xor_sync(0xffffffffu, n_lt, d);
+            for (uint32_t j = lane; j < np; j += 32) {
+                const Photo pj = photos[photo_sorted[p0 + j]];
+                uint32_t rank = 0;
+                for (uint32_t k = 0; k < np; ++k) {
+                    const Photo pk = photos[photo_sorted[p0 + k]];
+                    rank += (pk.src < pj.src) || (pk.src == pj.src && pk.slot < pj.slot);
+                }
+                MP e; e.x = pj.x; e.y = pj.y; e.z = pj.z; e.w = pj.w; e.pad = 0;
+                cur[M + (rank < n_lt ? rank : rank + mprod)] = e;
+            }
+            if (mprod) {
+                const long long wq = dN / (long long)mprod, rem = dN % (long long)mprod;
+                const int ijk[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
+                                     (int)(c >> (2 * P.log2n)) };
+                for (uint32_t j = lane; j < mprod; j += 32) {
+                    Stream s(seed_of(P, r), c, P.step, TAG_PRODUCT, j);
+                    MP e;
+                    double X[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) X[a] = P.lo[a] + ((double)ijk[a] + s.uniform()) * P.h[a];
+                    e.x = X[0]; e.y = X[1]; e.z = X[2];
+                    const long long wj = wq + (j == 0 ? rem : 0);
+                    if (wj > 0xffffffffll) atomicOr(&ctr->err, DERR_OVERFLOW);
+                    e.w = (uint32_t)wj; e.pad = 0;
+                    cur[M + n_lt + j] = e;
+                }
+            }
+            M += mprod + np;
+            __syncwarp();
+            // level-synchronous median splits up to T leaves
+            uint32_t* bnd = sb[wid][0];
+            uint32_t* bnd2 = sb[wid][1];
+            if (lane == 0) { bnd[0] = 0; bnd[1] = M; }
+            __syncwarp();
+            int nnodes = 1;
+            for (int level = 1; level < T; level *= 2) {
+                uint32_t fill = 0;
+                int nn = 0;
+                if (lane == 0) bnd2[0] = 0;
+                for (int d = 0; d < nnodes; ++d) {
+                    const uint32_t s0 = bnd[d], s1 = bnd[d + 1], m = s1 - s0;
+                    unsigned long long W = 0;
+                    for (uint32_t j = lane; j < m; j += 32) W += cur[s0 + j].w;
+                    W = warp_sum_u64(W);
+                    if (W >= 2) {
+                        uint32_t nr;
+                        const uint32_t nl = split_node(cur + s0, m, W, tmp, nxt + fill, &nr);
+                        fill += nl;
+                        if (lane == 0) bnd2[nn + 1] = fill;
+                        fill += nr;
+                        if (lane == 0) bnd2[nn + 2] = fill;
+                        nn += 2;
+                    } else {
+                        for (uint32_t j = lane; j < m; j += 32) nxt[fill + j] = cur[s0 + j];
+                        fill += m;
+                        if (lane == 0) bnd2[nn + 1] = fill;
+                        nn += 1;
+                    }
+                    __syncwarp();
+                }
+                MP* t = cur; cur = nxt; nxt = t;
+                uint32_t* tb = bnd; bnd = bnd2; bnd2 = tb;
+                nnodes = nn;
+                __syncwarp();
+            }
+            // leaves: weight sum, weight-averaged position (list order)
+            const uint32_t o0 = out_start[g];
+            if ((uint32_t)nnodes != out_start[g + 1] - o0) {
+                if (lane == 0) atomicOr(&ctr->err, DERR_INTERNAL);
+            } else {
+                for (int d = lane; d < nnodes; d += 32) {
+                    double sx = 0.0, sy = 0.0, sz = 0.0;
+                    unsigned long long Wl = 0;
+                    for (uint32_t q = bnd[d]; q < bnd[d + 1]; ++q) {
+                        const MP e = cur[q];
+                        const double wd = (double)e.w;
+                        sx = sx + wd * e.x;
+                        sy = sy + wd * e.y;
+                        sz = sz + wd * e.z;
+                        Wl += e.w;
+                    }
+                    if (Wl > 0xffffffffull) atomicOr(&ctr->err, DERR_OVERFLOW);
+                    const double Wd = (double)Wl;
+                    P64 o;
+                    o.x = sx / Wd; o.y = sy / Wd; o.z = sz / Wd;
+                    o.cell = (uint32_t)g;
+                    o.w = (uint32_t)Wl;
+                    st_p64(out + o0 + d, o);
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+int grid_for(uint64_t n, int tpb, int maxb = 152 * 16)
+{
+    const uint64_t b = (n + tpb - 1) / tpb;
+    return (int)(b < 1 ? 1 : (b > (uint64_t)maxb ? (uint64_t)maxb : b));
+}
+
+}  // namespace
+
+size_t scan_scratch_elems(uint64_t G, int C) { return (size_t)(scan_nblk(G) + 1) * C + C; }
+
+// ---------------------------------------------------------------- launchers
+void launch_transport_f64(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
+{
+    const uint64_t G = (uint64_t)P.R * P.n3;
+    cudaMemsetAsync(d.cnt_new, 0, G * sizeof(int32_t), s);
+    cudaMemsetAsync(d.in_cnt, 0, G * sizeof(int32_t), s);
+    cudaMemsetAsync(d.in_before, 0, G * sizeof(int32_t), s);
+    cudaMemsetAsync(d.Xe, 0, G * sizeof(unsigned long long), s);
+    cudaMemsetAsync(d.ne_fix, 0, G * sizeof(unsigned long long), s);
+    cudaMemsetAsync(d.ctr, 0, sizeof(Counters), s);
+    const uint32_t nblk = (N + TPB - 1) / TPB;
+    if (N > 0)
+        ++g_launches;
+        k_push_f64<<<nblk, TPB, 0, s>>>(P, d.recA, d.recB, d.keyB, N, d.cell_start, d.E, d.cnt_new, d.in_cnt,
+                                         d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr, d.blk_stay);
+}
+
+void launch_transport_finish_f64(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s)
+{
+    TransportScanOp op{ d.cnt_new, d.in_cnt, d.in_before, d.cell_start_B, d.delta, d.in_off, G };
+    run_scan<3>(op, G, d.scan_blk, s);
+    const uint32_t nblk = (N + TPB - 1) / TPB;
+    if (N > 0) {
+        BlockScanOp bop{ d.blk_stay, d.blk_prefix };
+        run_scan<1>(bop, nblk, d.scan_blk + scan_scratch_elems(G, 3), s);
+        ++g_launches;
+        k_scatter_f64<<<nblk, TPB, 0, s>>>(d.recB, d.recA, d.keyB, N, d.blk_prefix, d.delta, d.mover_cap, d.ctr);
+        const int mg = grid_for(N / 8 + 1, 256, 1024);
+        ++g_launches;
+        k_mover_place<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.in_off, d.cursor, d.mover_sorted);
+        ++g_launches;
+        k_mover_write_f64<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.mover_sorted, d.in_off, d.in_cnt, d.in_before,
+                                             d.cnt_new, d.cell_start_B, d.cursor, d.recB, d.recA);
+    }
+    uint32_t* t = d.cell_start; d.cell_start = d.cell_start_B; d.cell_start_B = t;
+}
+
+void launch_deposit_only_f64(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
+{
+    const uint64_t G = (uint64_t)P.R * P.n3;
+    cudaMemsetAsync(d.Xe, 0, G * sizeof(unsigned long long), s);
+    cudaMemsetAsync(d.ne_fix, 0, G * sizeof(unsigned long long), s);
+    // counted below
+    if (N > 0) g_launches++, k_deposit_f64<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.recA, N, d.Xe, d.ne_fix);
+}
+
+void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
+{
+    const double dV = P.h[0] * P.h[1] * P.h[2];
+    const double qscale = 1.602176634e-19 * ldexp(1.0, -3 * P.frac_bits) / dV;
+    const double phi_top = P.E0 * (P.hi[2] - P.lo[2]);
+    ++g_launches;
+    k_rho<<<grid_for(G, 256), 256, 0, s>>>(P, d.Npos, d.Nneg, d.ne_fix, d.rho, d.lev[0].rhs, G, qscale, phi_top,
+                                          d.ctr);
+}
+
+void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
+{
+    ++g_launches;
+    k_kmc<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.fired, d.Npos, d.Nneg, G, d.ctr);
+}
+
+void launch_particles_f64(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s)
+{
+    (void)N;
+    cudaMemsetAsync(d.photo_cnt, 0, G * sizeof(int32_t), s);
+    cudaMemsetAsync(d.photo_cursor, 0, G * sizeof(int32_t), s);
+    cudaMemsetAsync(d.photo_w, 0, G * sizeof(unsigned long long), s);
+    ++g_launches;
+    k_loss_f64<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.recA, d.cell_start, d.Xe, d.fired, G);
+    if (P.photon_ratio > 0.0)
+        ++g_launches;
+        k_photons<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.fired, G, d.photos, d.photo_cap, d.photo_cnt,
+                                                            d.photo_w, d.Npos, d.ctr);
+    MergeScanOp op{ d.Xe, d.fired, d.photo_w, d.photo_cnt, d.cell_start, d.out_start, d.photo_off, d.work_off,
+                    G, P.ppc, P.n_new };
+    run_scan<3>(op, G, d.scan_blk, s);
+    if (P.photon_ratio > 0.0)
+        ++g_launches;
+        k_photo_place<<<grid_for(d.photo_cap, 256, 1024), 256, 0, s>>>(d.photos, d.ctr, d.photo_cap, d.photo_off,
+                                                                      d.photo_cursor, d.photo_sorted);
+    ++g_launches;
+    k_merge_f64<<<152 * 8, MERGE_WARPS * 32, 0, s>>>(P, d.recA, d.cell_start, d.fired, d.photos, d.photo_sorted,
+                                                      d.photo_off, d.out_start, d.work_off,
+                                                      reinterpret_cast<MP*>(d.work), d.work_cap / 3, d.recB, G,
+                                                      d.mover_cap, d.photo_cap, d.ctr);
+    P64* t = d.recA; d.recA = d.recB; d.recB = t;
+    uint32_t* u = d.cell_start; d.cell_start = d.out_start; d.out_start = u;
+}
+
+}  // namespace ik

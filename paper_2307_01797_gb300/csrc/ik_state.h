@@ -1,0 +1,147 @@
+// ik_state.h -- device state of one itokmc handle and the host-side launchers
+// shared by the translation units of libitokmc.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ik_common.cuh"
+
+namespace ik {
+
+// FP64-form particle record: absolute position, global cell (r n^3 + c),
+// weight (physical electrons).  32 bytes, loaded as two 16-byte vectors.
+struct alignas(16) P64 {
+    double x, y, z;
+    uint32_t cell;
+    uint32_t w;
+};
+
+// Mixed-form particle record: position inside the cell in cell units
+// [0, 1), weight.  16 bytes; the global cell lives in a separate array.
+struct alignas(16) P32 {
+    float ox, oy, oz;
+    uint32_t w;
+};
+
+// Cell-centred field: E components and |E| = sqrt((Ex^2 + Ey^2) + Ez^2).
+struct alignas(16) E64 {
+    double x, y, z, m;
+};
+
+struct Mover {       // a particle that changed cell in the push
+    uint32_t g;      // new global cell
+    uint32_t i;      // index in the pre-push array
+};
+
+struct Photo {       // an absorbed superphoton (photoelectron)
+    double x, y, z;  // absorption point (FP64 form) / cell offsets (mixed)
+    uint32_t g;      // global absorption cell
+    uint32_t src;    // source cell within the realization
+    uint32_t slot;   // superphoton slot in the source cell
+    uint32_t w;      // weight
+};
+
+// Flags in the push key word.
+constexpr uint32_t KEY_DEAD = 0x80000000u;
+constexpr uint32_t KEY_MOVER = 0x40000000u;
+constexpr uint32_t KEY_MASK = 0x3fffffffu;
+
+constexpr int TPB = 256;        // threads per block of the particle passes
+constexpr int MAX_R = 1024;     // realizations per handle
+
+// Device counters of one step (zeroed at the start of each stage).
+struct Counters {
+    unsigned long long n_movers;
+    unsigned long long n_photo;
+    unsigned long long n_new;          // product + photo particles
+    unsigned long long ion, att, phot; // firings
+    unsigned long long absorbed_w;
+    unsigned int err;                  // DERR_* bits
+    unsigned int kmc_fail_cell;
+    unsigned long long outflow[MAX_R];
+    unsigned long long lost[MAX_R];
+};
+
+struct MGLevel {
+    int n;                 // cells per axis on this level
+    double h;              // cell size
+    double* phi;  double* rhs;  double* res;   // FP64 (size R n^3)
+    float* phi32; float* rhs32;                 // FP32 inner V-cycles
+};
+
+constexpr int MAX_LEVELS = 12;
+
+struct Dev {
+    // particles (ping-pong)
+    P64* recA = nullptr;  P64* recB = nullptr;
+    P32* rA32 = nullptr;  P32* rB32 = nullptr;
+    uint32_t* cellA32 = nullptr;  uint32_t* cellB32 = nullptr;
+    uint32_t* keyB = nullptr;
+    uint32_t* cell_start = nullptr;     // G + 1, current array
+    uint32_t* cell_start_B = nullptr;   // G + 1, scratch
+    // per-cell transport counters
+    int32_t* cnt_new = nullptr;  int32_t* in_cnt = nullptr;  int32_t* in_before = nullptr;
+    int32_t* cursor = nullptr;   int64_t* delta = nullptr;   uint32_t* in_off = nullptr;
+    uint32_t* blk_stay = nullptr;  uint32_t* blk_prefix = nullptr;
+    Mover* movers = nullptr;  uint32_t* mover_sorted = nullptr;
+    // mesh
+    unsigned long long* ne_fix = nullptr;  unsigned long long* Xe = nullptr;
+    int64_t* Npos = nullptr;  int64_t* Nneg = nullptr;  int64_t* rho = nullptr;
+    E64* E = nullptr;  float4* E32 = nullptr;
+    // chemistry
+    int64_t* fired = nullptr;          // 3 G: ion, att, photon
+    // photons
+    Photo* photos = nullptr;  uint32_t* photo_sorted = nullptr;
+    int32_t* photo_cnt = nullptr;  int32_t* photo_cursor = nullptr;
+    unsigned long long* photo_w = nullptr;  uint32_t* photo_off = nullptr;
+    // merge
+    uint32_t* out_start = nullptr;     // G + 1
+    uint64_t* work_off = nullptr;      // G + 1
+    unsigned char* work = nullptr;  size_t work_bytes = 0;
+    // scans
+    long long* scan_blk = nullptr;  size_t scan_blk_elems = 0;
+    // multigrid
+    MGLevel lev[MAX_LEVELS];
+    int nlev = 0;
+    double* norm_part = nullptr;  double* norm_out = nullptr;  size_t norm_blocks = 0;
+    // counters
+    Counters* ctr = nullptr;
+    Counters* ctr_host = nullptr;      // pinned mirror
+    uint32_t* sort_tmp = nullptr;      // radix-sort scratch (4 x capacity u32)
+    uint32_t mover_cap = 0, photo_cap = 0;
+    uint64_t work_cap = 0;             // merge work elements (all 3 buffers)
+    double* stage = nullptr;           // 3 G doubles: field upload/readback
+};
+
+// ------------------------------------------------------------- launchers
+// ik_particles.cu
+void launch_transport_f64(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
+void launch_transport_finish_f64(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s);
+void launch_deposit_only_f64(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
+void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
+void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
+void launch_particles_f64(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s);
+// ik_sort.cu
+void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
+                      uint32_t n, int key_bits, cudaStream_t s, long long* blk_scratch,
+                      size_t blk_scratch_elems);
+size_t radix_scratch_elems(uint32_t cap);
+void launch_set_particles_f64(const Params& P, Dev& d, const double* x, const double* y,
+                              const double* z, const uint32_t* w, const int32_t* real, uint32_t n,
+                              uint64_t G, cudaStream_t s);
+// ik_field.cu
+int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2,
+                int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out);
+void launch_efield(const Params& P, Dev& d, cudaStream_t s);
+void launch_pack_field(const Params& P, Dev& d, const double* E3, cudaStream_t s);
+void launch_unpack_field(const Params& P, Dev& d, double* E3, cudaStream_t s);
+
+// Kernel launches issued by this library (all handles), for the benchmark's
+// launch count.
+extern unsigned long long g_launches;
+
+// generic 3-phase exclusive scan over G cells with C channels (ik_particles.cu)
+size_t scan_scratch_elems(uint64_t G, int C);
+
+}  // namespace ik

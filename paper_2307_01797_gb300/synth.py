@@ -140,19 +140,18 @@ def blob_state(phys, seed=1, sigma=5e-4, peak=1e18, zfrac=0.8, centers=None):
     return sample_density(phys, gaussian_blobs(centers, sigma, peak), seed, cells=cells)
 
 
-def streamer_tree_state(phys, target_particles, seed=7, n_ch=1e19, sigma_r=5e-4, branches=4):
-    """A developed streamer tree: ``branches`` channels from the anode side
-    (z = 0.9 L) downward, fanning out, each a line segment with Gaussian
-    radial profile n_ch exp(-r^2/2 sigma_r^2); channel length scaled so the
-    particle count approaches ``target_particles``."""
-    n = phys["n"]
+def streamer_tree_geometry(phys, target_particles, seed=7, n_ch=1e19, sigma_r=5e-4, branches=4):
+    """Channel segments of a synthetic discharge tree: ``branches`` line
+    segments from the anode side (z = 0.9 L) downward and outward, their
+    length chosen so that ~``target_particles`` superparticles fill them."""
     L = phys["hi"][0] - phys["lo"][0]
     h = cell_size(phys)
     lo = np.asarray(phys["lo"])
     ppc = phys["ppc"]
     r_occ = sigma_r * math.sqrt(2.0 * math.log(max(n_ch * h ** 3, 2.0)))
     cells_per_len = math.pi * (r_occ / h) ** 2
-    length = min(0.85 * L, target_particles / (ppc * branches * cells_per_len) * h)
+    # about 55% of the cells within r_occ reach ppc particles (Gaussian tail)
+    length = min(0.85 * L, target_particles / (0.55 * ppc * branches * cells_per_len) * h)
     rng = np.random.Generator(np.random.PCG64(seed + 1))
     top = np.array([lo[0] + L / 2, lo[1] + L / 2, lo[2] + 0.9 * L])
     segs = []
@@ -162,6 +161,17 @@ def streamer_tree_state(phys, target_particles, seed=7, n_ch=1e19, sigma_r=5e-4,
         d = np.array([tilt * math.cos(ang), tilt * math.sin(ang), -1.0])
         d /= np.linalg.norm(d)
         segs.append((top, top + length * d))
+    return segs, r_occ
+
+
+def streamer_tree_state(phys, target_particles, seed=7, n_ch=1e19, sigma_r=5e-4, branches=4):
+    """A developed streamer tree: the channels of ``streamer_tree_geometry``
+    with Gaussian radial profile n_ch exp(-r^2/2 sigma_r^2), sampled to at
+    most ppc particles per cell."""
+    n = phys["n"]
+    h = cell_size(phys)
+    lo = np.asarray(phys["lo"])
+    segs, r_occ = streamer_tree_geometry(phys, target_particles, seed, n_ch, sigma_r, branches)
 
     def fn(x, y, z):
         out = np.zeros_like(x)
@@ -184,13 +194,48 @@ def streamer_tree_state(phys, target_particles, seed=7, n_ch=1e19, sigma_r=5e-4,
                                  np.arange(rmin[2], rmax[2] + 1), indexing="ij")
         sel.append(((kk * n + jj) * n + ii).ravel())
     cells = np.unique(np.concatenate(sel)).astype(np.int64)
-    # evaluate the density in chunks to bound memory
     out = {k: [] for k in ("x", "y", "z", "w")}
     for c0 in range(0, cells.size, 1 << 22):
         part = sample_density(phys, fn, seed + 17 * c0, cells=cells[c0:c0 + (1 << 22)])
         for k in out:
             out[k].append(part[k])
     return {k: np.concatenate(v) for k, v in out.items()}
+
+
+def cell_counts(phys, st):
+    """Electrons per cell of a particle state (NGP by floor of the position)."""
+    n = phys["n"]
+    h = cell_size(phys)
+    lo = np.asarray(phys["lo"])
+    ijk = [np.clip(np.floor((np.asarray(st[a]) - lo[q]) / h).astype(np.int64), 0, n - 1)
+           for q, a in enumerate(("x", "y", "z"))]
+    c = (ijk[2] * n + ijk[1]) * n + ijk[0]
+    return np.bincount(c, weights=np.asarray(st["w"], np.float64), minlength=n ** 3)
+
+
+def streamer_ions(phys, st, seed=8, head_density=3e18, target_particles=None, sigma_r=5e-4, branches=4):
+    """Ion counts for a streamer-tree state: a quasi-neutral channel (N+ =
+    electrons per cell) plus a net positive head charge (Gaussian ball of
+    density ``head_density``) at each channel tip; N- = 0."""
+    n = phys["n"]
+    h = cell_size(phys)
+    lo = np.asarray(phys["lo"])
+    Np = np.rint(cell_counts(phys, st)).astype(np.int64)
+    if target_particles is None:
+        target_particles = len(st["w"])
+    segs, _ = streamer_tree_geometry(phys, target_particles, seed - 1, sigma_r=sigma_r, branches=branches)
+    c = lo[0] + (np.arange(n) + 0.5) * h
+    rng = np.random.Generator(np.random.PCG64(seed))
+    for _, tip in segs:
+        r = int(math.ceil(4 * sigma_r / h))
+        ic = np.clip(np.floor((tip - lo) / h).astype(int), r, n - 1 - r)
+        sl = [slice(ic[q] - r, ic[q] + r + 1) for q in range(3)]
+        Z, Y, X = np.meshgrid(c[sl[2]], c[sl[1]], c[sl[0]], indexing="ij")
+        d2 = (X - tip[0]) ** 2 + (Y - tip[1]) ** 2 + (Z - tip[2]) ** 2
+        add = rng.poisson(head_density * np.exp(-d2 / (2 * sigma_r ** 2)) * h ** 3)
+        V = Np.reshape(n, n, n)
+        V[sl[2], sl[1], sl[0]] += add
+    return Np, np.zeros(n ** 3, np.int64)
 
 
 def uniform_slab_state(phys, count, seed=1, z0=0.4, z1=0.6, weight=100):

@@ -1,0 +1,73 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads without a GPU
+and exports every entry point that include/itokmc.h declares; the binding's
+struct layouts match the header's (compiled with gcc)."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2307_01797_gb300 import build, itokmc
+
+
+def test_library_exports_every_header_symbol():
+    L = itokmc.lib()
+    names = itokmc.header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert b"sm_103a" in L.itokmc_version()
+
+
+def test_config_defaults_without_gpu():
+    c = itokmc.Config()
+    assert itokmc.lib().itokmc_config_defaults(ctypes.byref(c)) == 0
+    assert c.n_new == 64 and c.n_crit == 5 and c.n_ssa == 10 and c.frac_bits == 10
+    assert c.mg_rtol == 1e-10 and c.eps == float("inf")
+
+
+def test_init_rejects_bad_config_without_touching_the_gpu():
+    c = itokmc.Config()
+    itokmc.lib().itokmc_config_defaults(ctypes.byref(c))
+    c.n[0] = c.n[1] = c.n[2] = 12          # not a power of two
+    c.particle_capacity = 10
+    h = ctypes.c_void_p()
+    assert itokmc.lib().itokmc_init(ctypes.byref(c), ctypes.byref(h)) == -1
+    assert b"power of two" in itokmc.lib().itokmc_last_error(None)
+
+
+def test_struct_layout_matches_header():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "itokmc.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(itokmc_config), offsetof(itokmc_config, particle_capacity),
+         offsetof(itokmc_config, alloc_ctx), offsetof(itokmc_config, field_precision),
+         sizeof(itokmc_stats), offsetof(itokmc_stats, ms_field));
+  return 0;
+}'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "s.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "s")
+        subprocess.run(["gcc", "-I", os.path.join(build.ROOT, "include"), c, "-o", exe], check=True)
+        got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    C, S = itokmc.Config, itokmc.Stats
+    assert got == [ctypes.sizeof(C), C.particle_capacity.offset, C.alloc_ctx.offset, C.field_precision.offset,
+                   ctypes.sizeof(S), S.ms_field.offset]
+
+
+def test_oracle_and_library_share_no_source():
+    """The oracle and the CUDA path are independent: no include or import
+    crosses between them."""
+    csrc = os.path.join(build.HERE, "csrc")
+    for f in os.listdir(csrc):
+        txt = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in txt.lower(), f
+    odir = os.path.join(build.ROOT, "oracle")
+    for f in os.listdir(odir):
+        if f.endswith((".c", ".py")):
+            txt = open(os.path.join(odir, f)).read()
+            assert "csrc" not in txt and "itokmc.h" not in txt and "paper_2307_01797_gb300" not in txt, f
