@@ -115,8 +115,8 @@ def merge(p: Params, x, y, z, w, cell):
     cs = cell_start_of(cell, ncell)
     x, y, z = _d(x), _d(y), _d(z)
     w = np.ascontiguousarray(w, dtype=np.uint32)
-    W = np.add.reduceat(w.astype(np.int64), cs[:-1]) if len(w) else np.zeros(ncell, np.int64)
-    W = np.where(np.diff(cs) > 0, W, 0)
+    W = np.zeros(ncell, np.int64)
+    np.add.at(W, np.asarray(cell, np.int64), w.astype(np.int64))
     cap = int(np.minimum(W, p.ppc).sum()) + 1
     ox, oy, oz = np.empty(cap), np.empty(cap), np.empty(cap)
     ow = np.empty(cap, dtype=np.uint32)

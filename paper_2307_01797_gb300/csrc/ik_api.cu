@@ -91,6 +91,48 @@ void* dalloc(itokmc_handle* h, size_t bytes, int* rc)
 template <class T>
 T* dalloc_n(itokmc_handle* h, size_t n, int* rc) { return reinterpret_cast<T*>(dalloc(h, n * sizeof(T), rc)); }
 
+void dfree(itokmc_handle* h, void* p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < h->allocs.size(); ++i)
+        if (h->allocs[i] == p) { h->allocs.erase(h->allocs.begin() + i); break; }
+    if (h->cfg.free_fn) h->cfg.free_fn(p, h->cfg.alloc_ctx);
+    else cudaFreeAsync(p, h->s);
+}
+
+// Grows the photon list to hold at least `need` superphotons (geometric).
+int ensure_photo_cap(itokmc_handle* h, uint64_t need)
+{
+    if (need <= h->d.photo_cap) return ITOKMC_OK;
+    if (need > 0xfff00000ull) return ITOKMC_ERR_CAPACITY;
+    uint64_t cap = std::max<uint64_t>(need + need / 4, 2ull * h->d.photo_cap);
+    if (cap > 0xfff00000ull) cap = 0xfff00000ull;
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    dfree(h, h->d.photos);
+    dfree(h, h->d.photo_sorted);
+    int rc = 0;
+    h->d.photos = dalloc_n<ik::Photo>(h, cap, &rc);
+    h->d.photo_sorted = dalloc_n<uint32_t>(h, cap, &rc);
+    if (rc) return rc;
+    h->d.photo_cap = (uint32_t)cap;
+    return ITOKMC_OK;
+}
+
+// Grows the merge work buffer to `need` elements per buffer (x3).
+int ensure_work_cap(itokmc_handle* h, uint64_t need)
+{
+    if (3 * need <= h->d.work_cap) return ITOKMC_OK;
+    const uint64_t cap = 3 * std::max<uint64_t>(need + need / 4, h->d.work_cap / 3 * 2);
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    dfree(h, h->d.work);
+    int rc = 0;
+    h->d.work = reinterpret_cast<unsigned char*>(dalloc(h, cap * 32, &rc));
+    if (rc) return rc;
+    h->d.work_cap = cap;
+    h->d.work_bytes = cap * 32;
+    return ITOKMC_OK;
+}
+
 int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
 int status_of_err(itokmc_handle* h, unsigned err)
@@ -124,8 +166,8 @@ float elapsed(itokmc_handle* h, int a, int b)
 int stage_transport(itokmc_handle* h)
 {
     IK_CHECK(h, cudaEventRecord(h->ev[0], h->s));
-    ik::launch_transport_f64(h->P, h->d, h->N, h->s);
-    ik::launch_transport_finish_f64(h->P, h->d, h->N, h->G, h->s);
+    ik::launch_transport(h->P, h->d, h->N, h->s);
+    ik::launch_transport_finish(h->P, h->d, h->N, h->G, h->s);
     ik::launch_rho(h->P, h->d, h->G, h->s);
     IK_CHECK(h, cudaEventRecord(h->ev[1], h->s));
     int rc = readback(h);
@@ -150,9 +192,25 @@ int stage_kmc(itokmc_handle* h)
 int stage_particles(itokmc_handle* h)
 {
     IK_CHECK(h, cudaEventRecord(h->ev[4], h->s));
-    ik::launch_particles_f64(h->P, h->d, h->N, h->G, h->s);
+    // the photon list must hold every superphoton this step can emit
+    IK_CHECK(h, cudaMemcpyAsync(&h->rb->ctr, h->d.ctr, sizeof(ik::Counters), cudaMemcpyDeviceToHost, h->s));
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    int rc = ensure_photo_cap(h, h->rb->ctr.photo_slots);
+    if (rc) return rc;
+    ik::launch_particles_a(h->P, h->d, h->G, h->s);
+    // output count and big-cell work size are known after the merge scan
+    uint64_t tail[2];
+    uint32_t outn = 0;
+    IK_CHECK(h, cudaMemcpyAsync(&tail[0], h->d.work_off + h->G, sizeof(uint64_t), cudaMemcpyDeviceToHost, h->s));
+    IK_CHECK(h, cudaMemcpyAsync(&outn, h->d.out_start + h->G, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->s));
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    (void)tail[1];
+    if (outn > h->cap) return fail(h, ITOKMC_ERR_CAPACITY, "particle capacity exceeded by the merge output");
+    rc = ensure_work_cap(h, tail[0]);
+    if (rc) return rc;
+    ik::launch_particles_b(h->P, h->d, h->G, h->s);
     IK_CHECK(h, cudaEventRecord(h->ev[5], h->s));
-    int rc = readback(h);
+    rc = readback(h);
     if (rc) return rc;
     const ik::Counters& c = h->rb->ctr;
     h->st.ionizations = (int64_t)c.ion;
@@ -166,7 +224,6 @@ int stage_particles(itokmc_handle* h)
     h->st.kmc_status = (c.err & ik::DERR_KMC) ? ITOKMC_ERR_KMC : 0;
     h->st.ms_kmc = elapsed(h, 2, 3);
     h->st.ms_particles = elapsed(h, 4, 5);
-    if (h->N > h->cap) return fail(h, ITOKMC_ERR_CAPACITY, "particle capacity exceeded after merge");
     return status_of_err(h, c.err);
 }
 
@@ -274,9 +331,17 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     const size_t cap = h->cap;
     d.mover_cap = h->cap;
     d.photo_cap = (uint32_t)std::max<size_t>(1u << 16, cap / 4);
-    d.work_cap = 3 * std::max<uint64_t>(1ull << 20, cap / 2);
-    d.recA = dalloc_n<ik::P64>(h, cap, &rc);
-    d.recB = dalloc_n<ik::P64>(h, cap, &rc);
+    d.work_cap = std::max<uint64_t>(3ull << 20, 2 * (uint64_t)cap + 16);
+    d.mixed = cfg->precision == ITOKMC_MIXED;
+    if (d.mixed) {
+        d.rA32 = dalloc_n<ik::P32>(h, cap, &rc);
+        d.rB32 = dalloc_n<ik::P32>(h, cap, &rc);
+        d.cellA32 = dalloc_n<uint32_t>(h, cap, &rc);
+        d.cellB32 = dalloc_n<uint32_t>(h, cap, &rc);
+    } else {
+        d.recA = dalloc_n<ik::P64>(h, cap, &rc);
+        d.recB = dalloc_n<ik::P64>(h, cap, &rc);
+    }
     d.keyB = dalloc_n<uint32_t>(h, cap, &rc);
     d.cell_start = dalloc_n<uint32_t>(h, G + 1, &rc);
     d.cell_start_B = dalloc_n<uint32_t>(h, G + 1, &rc);
@@ -372,8 +437,9 @@ int itokmc_set_particles(itokmc_handle* h, const double* x, const double* y, con
     if (n < 0 || (n > 0 && (!x || !y || !z || !w))) return fail(h, ITOKMC_ERR_ARG, "bad particle arrays");
     if (n > (int64_t)h->cap) return fail(h, ITOKMC_ERR_CAPACITY, "more particles than particle_capacity");
     if (h->P.R > 1 && n > 0 && !realization) return fail(h, ITOKMC_ERR_ARG, "realization array required when R > 1");
-    // stage the SoA arrays in the (about to be overwritten) record buffer A
-    unsigned char* st = reinterpret_cast<unsigned char*>(h->d.recA);
+    // stage the SoA arrays in scratch: the (about to be overwritten) record
+    // buffer A of the FP64 form, the merge work buffer of the mixed form
+    unsigned char* st = h->d.mixed ? h->d.work : reinterpret_cast<unsigned char*>(h->d.recA);
     double* dx = reinterpret_cast<double*>(st);
     double* dy = dx + n;
     double* dz = dy + n;
@@ -387,7 +453,7 @@ int itokmc_set_particles(itokmc_handle* h, const double* x, const double* y, con
         IK_CHECK(h, cudaMemcpyAsync(dw, w, n * sizeof(uint32_t), k, h->s));
         if (dr) IK_CHECK(h, cudaMemcpyAsync(dr, realization, n * sizeof(int32_t), k, h->s));
     }
-    ik::launch_set_particles_f64(h->P, h->d, dx, dy, dz, dw, dr, (uint32_t)n, h->G, h->s);
+    ik::launch_set_particles(h->P, h->d, dx, dy, dz, dw, dr, (uint32_t)n, h->G, h->s);
     int rc = readback(h);
     if (rc) return rc;
     if (h->rb->ctr.err) {
@@ -410,17 +476,42 @@ int itokmc_read_particles(itokmc_handle* h, double* x, double* y, double* z, uin
     const uint32_t N = h->N;
     if (n_out) *n_out = N;
     if ((int64_t)N > cap) return fail(h, ITOKMC_ERR_CAPACITY, "output buffer smaller than the particle count");
-    std::vector<ik::P64> buf(N);
-    if (N) IK_CHECK(h, cudaMemcpyAsync(buf.data(), h->d.recA, N * sizeof(ik::P64), cudaMemcpyDeviceToHost, h->s));
-    IK_CHECK(h, cudaStreamSynchronize(h->s));
     const uint32_t n3 = (uint32_t)h->P.n3;
+    if (!h->d.mixed) {
+        std::vector<ik::P64> buf(N);
+        if (N) IK_CHECK(h, cudaMemcpyAsync(buf.data(), h->d.recA, N * sizeof(ik::P64), cudaMemcpyDeviceToHost, h->s));
+        IK_CHECK(h, cudaStreamSynchronize(h->s));
+        for (uint32_t i = 0; i < N; ++i) {
+            if (x) x[i] = buf[i].x;
+            if (y) y[i] = buf[i].y;
+            if (z) z[i] = buf[i].z;
+            if (w) w[i] = buf[i].w;
+            if (realization) realization[i] = (int32_t)(buf[i].cell / n3);
+            if (cell) cell[i] = (int64_t)(buf[i].cell % n3);
+        }
+        return ITOKMC_OK;
+    }
+    // mixed form: absolute position lo + (i + offset) h
+    std::vector<ik::P32> buf(N);
+    std::vector<uint32_t> cb(N);
+    if (N) {
+        IK_CHECK(h, cudaMemcpyAsync(buf.data(), h->d.rA32, N * sizeof(ik::P32), cudaMemcpyDeviceToHost, h->s));
+        IK_CHECK(h, cudaMemcpyAsync(cb.data(), h->d.cellA32, N * sizeof(uint32_t), cudaMemcpyDeviceToHost, h->s));
+    }
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    const uint32_t n = (uint32_t)h->P.n;
     for (uint32_t i = 0; i < N; ++i) {
-        if (x) x[i] = buf[i].x;
-        if (y) y[i] = buf[i].y;
-        if (z) z[i] = buf[i].z;
+        const uint32_t c = cb[i] % n3;
+        const uint32_t id[3] = { c % n, (c / n) % n, c / (n * n) };
+        const float o[3] = { buf[i].ox, buf[i].oy, buf[i].oz };
+        double X[3];
+        for (int a = 0; a < 3; ++a) X[a] = h->P.lo[a] + ((double)id[a] + (double)o[a]) * h->P.h[a];
+        if (x) x[i] = X[0];
+        if (y) y[i] = X[1];
+        if (z) z[i] = X[2];
         if (w) w[i] = buf[i].w;
-        if (realization) realization[i] = (int32_t)(buf[i].cell / n3);
-        if (cell) cell[i] = (int64_t)(buf[i].cell % n3);
+        if (realization) realization[i] = (int32_t)(cb[i] / n3);
+        if (cell) cell[i] = (int64_t)c;
     }
     return ITOKMC_OK;
 }
@@ -450,7 +541,7 @@ int itokmc_solve_field(itokmc_handle* h)
 {
     IK_GUARD(h);
     cudaMemsetAsync(h->d.ctr, 0, sizeof(ik::Counters), h->s);
-    ik::launch_deposit_only_f64(h->P, h->d, h->N, h->s);
+    ik::launch_deposit_only(h->P, h->d, h->N, h->s);
     ik::launch_rho(h->P, h->d, h->G, h->s);
     int rc = readback(h);
     if (rc) return rc;

@@ -84,7 +84,9 @@ struct Stream {
     }
 };
 
-// FP32 uniform on (0,1) from one word: (2k+1) 2^-24 with k = top 23 bits.
+// FP32 uniform on (0,1) from the high word of an FP64 uniform: its top 23
+// bits k give (2k+1) 2^-24 (exact in FP32), the FP64 uniform to within an
+// FP32 ulp.
 __device__ __forceinline__ float uniform_f32(uint32_t v)
 {
     return (float)(2u * (v >> 9) + 1u) * 0x1p-24f;

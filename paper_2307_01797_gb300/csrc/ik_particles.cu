@@ -458,6 +458,7 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
             }
             Npos[g] += f[0];
             Nneg[g] += f[1];
+            if (f[2] > 0) atomicAdd(&ctr->photo_slots, (unsigned long long)(f[2] < P.n_new ? f[2] : P.n_new));
             atomicAdd(&ctr->ion, (unsigned long long)f[0]);
             atomicAdd(&ctr->att, (unsigned long long)f[1]);
             atomicAdd(&ctr->phot, (unsigned long long)f[2]);
@@ -472,9 +473,8 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
 // Systematic integer removal of L = -dN electrons from the cell's particles
 // in canonical order: particle p loses floor((C_p L + R)/W) -
 // floor((C_{p-1} L + R)/W), R = (64-bit draw) mod W.
-__global__ void k_loss_f64(Params P, P64* __restrict__ A, const uint32_t* __restrict__ cs,
-                           const unsigned long long* __restrict__ Xe, const int64_t* __restrict__ fired,
-                           uint64_t G)
+__global__ void k_loss(Params P, uint32_t* __restrict__ wbase, int wstride, const uint32_t* __restrict__ cs,
+                       const unsigned long long* __restrict__ Xe, const int64_t* __restrict__ fired, uint64_t G)
 {
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
         const long long dN = fired[g] - fired[G + g];
@@ -489,12 +489,22 @@ __global__ void k_loss_f64(Params P, P64* __restrict__ A, const uint32_t* __rest
         unsigned __int128 C = 0;
         for (uint32_t q = cs[g]; q < cs[g + 1]; ++q) {
             const unsigned __int128 before = (C * L + R) / W;
-            const uint32_t w = A[q].w;
+            uint32_t* wq = wbase + (size_t)q * wstride;
+            const uint32_t w = *wq;
             C += w;
             const unsigned __int128 after = (C * L + R) / W;
-            A[q].w = (uint32_t)(w - (unsigned long long)(after - before));
+            *wq = (uint32_t)(w - (unsigned long long)(after - before));
         }
     }
+}
+
+// Offset in cell units, rounded to FP32 and kept in [0, 1).
+__device__ __forceinline__ float clamp_off(double v)
+{
+    float f = (float)v;
+    if (!(f >= 0.0f)) f = 0.0f;
+    if (f >= 1.0f) f = 0x1.fffffep-1f;
+    return f;
 }
 
 // ------------------------------------------------------------------ photons
@@ -520,7 +530,7 @@ __device__ __forceinline__ void photon_sample(const Params& P, uint64_t seed, ui
     dir[2] = cz;
 }
 
-__global__ void k_photons(Params P, const int64_t* __restrict__ fired, uint64_t G,
+__global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired, uint64_t G,
                           Photo* __restrict__ photos, uint32_t photo_cap, int32_t* __restrict__ photo_cnt,
                           unsigned long long* __restrict__ photo_w, int64_t* __restrict__ Npos,
                           Counters* __restrict__ ctr)
@@ -562,7 +572,15 @@ __global__ void k_photons(Params P, const int64_t* __restrict__ fired, uint64_t 
             const unsigned long long slot = atomicAdd(&ctr->n_photo, 1ull);
             if (slot < photo_cap) {
                 Photo ph;
-                ph.x = Ya[0]; ph.y = Ya[1]; ph.z = Ya[2];
+                if (mixed) {
+                    const int id[3] = { ix, iy, iz };
+                    double o[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) o[a] = (double)clamp_off((Ya[a] - P.lo[a]) / P.h[a] - (double)id[a]);
+                    ph.x = o[0]; ph.y = o[1]; ph.z = o[2];
+                } else {
+                    ph.x = Ya[0]; ph.y = Ya[1]; ph.z = Ya[2];
+                }
                 ph.g = gd; ph.src = c; ph.slot = (uint32_t)j; ph.w = (uint32_t)wj;
                 photos[slot] = ph;
             } else {
@@ -739,12 +757,17 @@ __device__ uint32_t split_node(const MP* src, uint32_t m, unsigned long long W, 
     return nl;
 }
 
-__global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge_f64(
-    Params P, const P64* __restrict__ A, const uint32_t* __restrict__ cs, const int64_t* __restrict__ fired,
-    const Photo* __restrict__ photos, const uint32_t* __restrict__ photo_sorted,
+// MX = false: FP64 records with absolute positions; MX = true: FP32 cell
+// offsets plus a cell array.  The tree itself works on FP64 coordinates
+// (FP32 offsets convert exactly).
+template <bool MX>
+__global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
+    Params P, const P64* __restrict__ A, const P32* __restrict__ A32, const uint32_t* __restrict__ cs,
+    const int64_t* __restrict__ fired, const Photo* __restrict__ photos, const uint32_t* __restrict__ photo_sorted,
     const uint32_t* __restrict__ photo_off, const uint32_t* __restrict__ out_start,
     const uint64_t* __restrict__ work_off, MP* __restrict__ work, uint64_t work_cap, P64* __restrict__ out,
-    uint64_t G, uint32_t cap, uint32_t photo_cap, Counters* __restrict__ ctr)
+    P32* __restrict__ out32, uint32_t* __restrict__ cout, uint64_t G, uint32_t cap, uint32_t photo_cap,
+    Counters* __restrict__ ctr)
 {
     __shared__ MP sbuf[MERGE_WARPS][3][MERGE_SMEM];
     __shared__ uint32_t sb[MERGE_WARPS][2][257];
@@ -789,13 +812,21 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge_f64(
             uint32_t M = 0;
             for (uint32_t b = e0; b < e1; b += 32) {
                 const uint32_t q = b + lane;
-                P64 p;
-                const bool ok = q < e1 && (p = ld_p64(A + q), p.w > 0);
-                const unsigned bal = __ballot_sync(0xffffffffu, ok);
-                if (ok) {
-                    MP e; e.x = p.x; e.y = p.y; e.z = p.z; e.w = p.w; e.pad = 0;
-                    cur[M + __popc(bal & ((1u << lane) - 1u))] = e;
+                MP e;
+                bool ok = false;
+                if (q < e1) {
+                    if constexpr (MX) {
+                        const P32 p = A32[q];
+                        e.x = p.ox; e.y = p.oy; e.z = p.oz; e.w = p.w;
+                    } else {
+                        const P64 p = ld_p64(A + q);
+                        e.x = p.x; e.y = p.y; e.z = p.z; e.w = p.w;
+                    }
+                    e.pad = 0;
+                    ok = e.w > 0;
                 }
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                if (ok) cur[M + __popc(bal & ((1u << lane) - 1u))] = e;
                 M += __popc(bal);
             }
             // photoelectrons: rank by (source, slot)
@@ -825,7 +856,11 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge_f64(
                     MP e;
                     double X[3];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) X[a] = P.lo[a] + ((double)ijk[a] + s.uniform()) * P.h[a];
+                    for (int a = 0; a < 3; ++a) {
+                        const double u = s.uniform();
+                        if constexpr (MX) X[a] = (double)clamp_off(u);
+                        else X[a] = P.lo[a] + ((double)ijk[a] + u) * P.h[a];
+                    }
                     e.x = X[0]; e.y = X[1]; e.z = X[2];
                     const long long wj = wq + (j == 0 ? rem : 0);
                     if (wj > 0xffffffffll) atomicOr(&ctr->err, DERR_OVERFLOW);
@@ -889,16 +924,233 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge_f64(
                     }
                     if (Wl > 0xffffffffull) atomicOr(&ctr->err, DERR_OVERFLOW);
                     const double Wd = (double)Wl;
-                    P64 o;
-                    o.x = sx / Wd; o.y = sy / Wd; o.z = sz / Wd;
-                    o.cell = (uint32_t)g;
-                    o.w = (uint32_t)Wl;
-                    st_p64(out + o0 + d, o);
+                    if constexpr (MX) {
+                        P32 o;
+                        o.ox = clamp_off(sx / Wd); o.oy = clamp_off(sy / Wd); o.oz = clamp_off(sz / Wd);
+                        o.w = (uint32_t)Wl;
+                        out32[o0 + d] = o;
+                        cout[o0 + d] = (uint32_t)g;
+                    } else {
+                        P64 o;
+                        o.x = sx / Wd; o.y = sy / Wd; o.z = sz / Wd;
+                        o.cell = (uint32_t)g;
+                        o.w = (uint32_t)Wl;
+                        st_p64(out + o0 + d, o);
+                    }
                 }
             }
             __syncwarp();
         }
     }
+}
+
+// ------------------------------------------------------------------ mixed form
+// Positions are (cell, FP32 offset in cell units); the push, interpolation
+// and normals run in FP32; the deposit stays exact int64 fixed point.
+__device__ __forceinline__ void cic32(float o, int idx, int n, int& ia, int& ib, float& f)
+{
+    const bool up = o >= 0.5f;
+    const int i0 = idx - 1 + (up ? 1 : 0);
+    f = up ? o - 0.5f : o + 0.5f;
+    ia = clampi(i0, n);
+    ib = clampi(i0 + 1, n);
+}
+
+__device__ __forceinline__ void deposit32(const Params& P, unsigned long long* __restrict__ ne, const int id[3],
+                                          const float o[3], uint32_t w)
+{
+    const int one = 1 << P.frac_bits, half = one >> 1;
+    int ia[3], ib[3];
+    long long A[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int q = (int)floorf(o[a] * (float)one);   // exact: o in [0,1), power-of-two scale
+        const int aa = (q + half) & (one - 1);
+        const int i0 = id[a] - 1 + (q >= half ? 1 : 0);
+        ia[a] = clampi(i0, P.n);
+        ib[a] = clampi(i0 + 1, P.n);
+        A[a][0] = one - aa;
+        A[a][1] = aa;
+    }
+    const int ix[2] = { ia[0], ib[0] }, iy[2] = { ia[1], ib[1] }, iz[2] = { ia[2], ib[2] };
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const long long v = (long long)w * A[0][a] * A[1][b] * A[2][c];
+                if (v) atomicAdd(ne + ((size_t)iz[c] * P.n + iy[b]) * P.n + ix[a], (unsigned long long)v);
+            }
+}
+
+__global__ void __launch_bounds__(TPB) k_push_f32(
+    Params P, const P32* __restrict__ A, const uint32_t* __restrict__ cA, P32* __restrict__ B,
+    uint32_t* __restrict__ keyB, uint32_t N, const uint32_t* __restrict__ cell_start,
+    const float4* __restrict__ E32, int32_t* __restrict__ cnt_new, int32_t* __restrict__ in_cnt,
+    int32_t* __restrict__ in_before, unsigned long long* __restrict__ Xe, unsigned long long* __restrict__ ne_fix,
+    Mover* __restrict__ movers, uint32_t mover_cap, Counters* __restrict__ ctr, uint32_t* __restrict__ blk_stay)
+{
+    const uint32_t i = blockIdx.x * TPB + threadIdx.x;
+    bool alive = false, mover = false;
+    uint32_t gnew = 0, w = 0;
+    if (i < N) {
+        const P32 p = A[i];
+        const uint32_t gold = __ldg(cA + i);
+        const int r = real_of(P, gold);
+        const uint32_t c = gold & (uint32_t)(P.n3 - 1);
+        const int id[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
+                            (int)(c >> (2 * P.log2n)) };
+        const uint32_t idx = i - cell_start[(size_t)r * P.n3];
+        const size_t ebase = (size_t)r * P.n3;
+        w = p.w;
+        const float o[3] = { p.ox, p.oy, p.oz };
+        int ia[3], ib[3];
+        float f[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) cic32(o[a], id[a], P.n, ia[a], ib[a], f[a]);
+        const float wx[2] = { 1.f - f[0], f[0] }, wy[2] = { 1.f - f[1], f[1] }, wz[2] = { 1.f - f[2], f[2] };
+        const int ix[2] = { ia[0], ib[0] }, iy[2] = { ia[1], ib[1] }, iz[2] = { ia[2], ib[2] };
+        float ex = 0.f, ey = 0.f, ez = 0.f;
+#pragma unroll
+        for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+            for (int by = 0; by < 2; ++by)
+#pragma unroll
+                for (int ax = 0; ax < 2; ++ax) {
+                    const float wgt = __fmul_rn(__fmul_rn(wx[ax], wy[by]), wz[cz]);
+                    const float4 e = __ldg(E32 + ebase + ((size_t)iz[cz] * P.n + iy[by]) * P.n + ix[ax]);
+                    ex = __fmaf_rn(wgt, e.x, ex);
+                    ey = __fmaf_rn(wgt, e.y, ey);
+                    ez = __fmaf_rn(wgt, e.z, ez);
+                }
+        // the FP64 form's stream (blocks 0 and 1): uniform j takes the top 24
+        // of its 52 bits, so both forms draw common random numbers (equal to
+        // FP32 rounding) -> FP32 Box-Muller, three normals
+        const uint64_t key = seed_of(P, r);
+        const u32x4 b0 = philox10(u32x4{ idx, P.step, TAG_PUSH << 24, 0u }, (uint32_t)key, (uint32_t)(key >> 32));
+        const u32x4 b1 = philox10(u32x4{ idx, P.step, TAG_PUSH << 24, 1u }, (uint32_t)key, (uint32_t)(key >> 32));
+        const float u1 = uniform_f32(b0.x), u2 = uniform_f32(b0.z), u3 = uniform_f32(b1.x), u4 = uniform_f32(b1.z);
+        const float r1 = sqrtf(-2.0f * logf(u1)), r2 = sqrtf(-2.0f * logf(u3));
+        float s1, c1, s2, c2;
+        sincospif(2.0f * u2, &s1, &c1);
+        sincospif(2.0f * u4, &s2, &c2);
+        const float nrm[3] = { r1 * c1, r1 * s1, r2 * c2 };
+        const float Ep[3] = { ex, ey, ez };
+        float on[3];
+        int idn[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float d = __fmaf_rn(P.f_drift, Ep[a], P.f_diff * nrm[a]);
+            float x = o[a] + d;
+            const float fl = floorf(x);
+            x -= fl;
+            if (x >= 1.0f) x = 0x1.fffffep-1f;
+            if (!(x >= 0.0f)) x = 0.0f;
+            on[a] = x;
+            idn[a] = id[a] + (int)fl;
+            inside = inside && idn[a] >= 0 && idn[a] < P.n;
+        }
+        P32 q;
+        q.ox = on[0]; q.oy = on[1]; q.oz = on[2]; q.w = w;
+        B[i] = q;
+        if (inside) {
+            gnew = (uint32_t)(ebase + ((size_t)idn[2] * P.n + idn[1]) * P.n + idn[0]);
+            alive = true;
+            mover = gnew != gold;
+            keyB[i] = gnew | (mover ? KEY_MOVER : 0u);
+            deposit32(P, ne_fix + ebase, idn, on, w);
+            if (mover) {
+                atomicAdd(in_cnt + gnew, 1);
+                if (gold < gnew) atomicAdd(in_before + gnew, 1);
+                const unsigned long long slot = atomicAdd(&ctr->n_movers, 1ull);
+                if (slot < mover_cap) movers[slot] = Mover{ gnew, i };
+                else atomicOr(&ctr->err, DERR_CAPACITY);
+            }
+        } else {
+            keyB[i] = KEY_DEAD;
+            atomicAdd(&ctr->outflow[r], (unsigned long long)w);
+        }
+    }
+    unsigned long long v = alive ? (unsigned long long)w : 0ull;
+    unsigned cc = alive ? 1u : 0u;
+    if (warp_run_sum(gnew, alive, v, cc)) {
+        atomicAdd(cnt_new + gnew, (int)cc);
+        atomicAdd(Xe + gnew, v);
+    }
+    const int nstay = __syncthreads_count(alive && !mover);
+    if (threadIdx.x == 0) blk_stay[blockIdx.x] = (uint32_t)nstay;
+}
+
+__global__ void __launch_bounds__(TPB) k_scatter_f32(const P32* __restrict__ B, P32* __restrict__ A,
+                                                     uint32_t* __restrict__ cA, const uint32_t* __restrict__ keyB,
+                                                     uint32_t N, const uint32_t* __restrict__ blk_prefix,
+                                                     const int64_t* __restrict__ delta, uint32_t cap,
+                                                     Counters* __restrict__ ctr)
+{
+    const uint32_t i = blockIdx.x * TPB + threadIdx.x;
+    uint32_t k = KEY_DEAD;
+    if (i < N) k = keyB[i];
+    const bool stay = !(k & (KEY_DEAD | KEY_MOVER));
+    const uint32_t rank = block_excl_count(stay, nullptr);
+    if (stay) {
+        const uint32_t g = k & KEY_MASK;
+        const long long pos = (long long)blk_prefix[blockIdx.x] + rank + delta[g];
+        if (pos >= 0 && pos < (long long)cap) {
+            A[pos] = B[i];
+            cA[pos] = g;
+        } else {
+            atomicOr(&ctr->err, DERR_INTERNAL);
+        }
+    }
+}
+
+__global__ void k_mover_write_f32(const Mover* __restrict__ movers, const Counters* __restrict__ ctr,
+                                  uint32_t mover_cap, const uint32_t* __restrict__ sorted,
+                                  const uint32_t* __restrict__ in_off, const int32_t* __restrict__ in_cnt,
+                                  const int32_t* __restrict__ in_before, const int32_t* __restrict__ cnt_new,
+                                  const uint32_t* __restrict__ new_start, int32_t* __restrict__ cursor,
+                                  const P32* __restrict__ B, P32* __restrict__ A, uint32_t* __restrict__ cA)
+{
+    const uint32_t n = (uint32_t)min(ctr->n_movers, (unsigned long long)mover_cap);
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const Mover mv = movers[sorted[s]];
+        const uint32_t g = mv.g;
+        const uint32_t b = in_off[g], e = b + (uint32_t)in_cnt[g];
+        uint32_t rank = 0;
+        for (uint32_t t = b; t < e && t < mover_cap; ++t) rank += movers[sorted[t]].i < mv.i;
+        const uint32_t stay = (uint32_t)(cnt_new[g] - in_cnt[g]);
+        const uint32_t pos = new_start[g] + rank + (rank >= (uint32_t)in_before[g] ? stay : 0u);
+        if (pos < mover_cap && e <= mover_cap) {
+            A[pos] = B[mv.i];
+            cA[pos] = g;
+        }
+        cursor[g] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_deposit_f32(Params P, const P32* __restrict__ A,
+                                                     const uint32_t* __restrict__ cA, uint32_t N,
+                                                     unsigned long long* __restrict__ Xe,
+                                                     unsigned long long* __restrict__ ne_fix)
+{
+    const uint32_t i = blockIdx.x * TPB + threadIdx.x;
+    bool alive = i < N;
+    uint32_t g = 0, w = 0;
+    if (alive) {
+        const P32 p = A[i];
+        g = cA[i];
+        w = p.w;
+        const uint32_t c = g & (uint32_t)(P.n3 - 1);
+        const int id[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
+                            (int)(c >> (2 * P.log2n)) };
+        const float o[3] = { p.ox, p.oy, p.oz };
+        deposit32(P, ne_fix + (size_t)real_of(P, g) * P.n3, id, o, w);
+    }
+    unsigned long long v = alive ? (unsigned long long)w : 0ull;
+    unsigned c = alive ? 1u : 0u;
+    if (warp_run_sum(g, alive, v, c)) atomicAdd(Xe + g, v);
 }
 
 int grid_for(uint64_t n, int tpb, int maxb = 152 * 16)
@@ -912,7 +1164,7 @@ int grid_for(uint64_t n, int tpb, int maxb = 152 * 16)
 size_t scan_scratch_elems(uint64_t G, int C) { return (size_t)(scan_nblk(G) + 1) * C + C; }
 
 // ---------------------------------------------------------------- launchers
-void launch_transport_f64(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
+void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
 {
     const uint64_t G = (uint64_t)P.R * P.n3;
     cudaMemsetAsync(d.cnt_new, 0, G * sizeof(int32_t), s);
@@ -922,13 +1174,18 @@ void launch_transport_f64(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
     cudaMemsetAsync(d.ne_fix, 0, G * sizeof(unsigned long long), s);
     cudaMemsetAsync(d.ctr, 0, sizeof(Counters), s);
     const uint32_t nblk = (N + TPB - 1) / TPB;
-    if (N > 0)
-        ++g_launches;
+    if (N == 0) return;
+    ++g_launches;
+    if (d.mixed)
+        k_push_f32<<<nblk, TPB, 0, s>>>(P, d.rA32, d.cellA32, d.rB32, d.keyB, N, d.cell_start, d.E32, d.cnt_new,
+                                         d.in_cnt, d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr,
+                                         d.blk_stay);
+    else
         k_push_f64<<<nblk, TPB, 0, s>>>(P, d.recA, d.recB, d.keyB, N, d.cell_start, d.E, d.cnt_new, d.in_cnt,
                                          d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr, d.blk_stay);
 }
 
-void launch_transport_finish_f64(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s)
+void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s)
 {
     TransportScanOp op{ d.cnt_new, d.in_cnt, d.in_before, d.cell_start_B, d.delta, d.in_off, G };
     run_scan<3>(op, G, d.scan_blk, s);
@@ -936,25 +1193,35 @@ void launch_transport_finish_f64(const Params& P, Dev& d, uint32_t N, uint64_t G
     if (N > 0) {
         BlockScanOp bop{ d.blk_stay, d.blk_prefix };
         run_scan<1>(bop, nblk, d.scan_blk + scan_scratch_elems(G, 3), s);
-        ++g_launches;
-        k_scatter_f64<<<nblk, TPB, 0, s>>>(d.recB, d.recA, d.keyB, N, d.blk_prefix, d.delta, d.mover_cap, d.ctr);
         const int mg = grid_for(N / 8 + 1, 256, 1024);
-        ++g_launches;
-        k_mover_place<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.in_off, d.cursor, d.mover_sorted);
-        ++g_launches;
-        k_mover_write_f64<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.mover_sorted, d.in_off, d.in_cnt, d.in_before,
-                                             d.cnt_new, d.cell_start_B, d.cursor, d.recB, d.recA);
+        g_launches += 3;
+        if (d.mixed) {
+            k_scatter_f32<<<nblk, TPB, 0, s>>>(d.rB32, d.rA32, d.cellA32, d.keyB, N, d.blk_prefix, d.delta,
+                                               d.mover_cap, d.ctr);
+            k_mover_place<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.in_off, d.cursor, d.mover_sorted);
+            k_mover_write_f32<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.mover_sorted, d.in_off, d.in_cnt,
+                                                 d.in_before, d.cnt_new, d.cell_start_B, d.cursor, d.rB32, d.rA32,
+                                                 d.cellA32);
+        } else {
+            k_scatter_f64<<<nblk, TPB, 0, s>>>(d.recB, d.recA, d.keyB, N, d.blk_prefix, d.delta, d.mover_cap,
+                                               d.ctr);
+            k_mover_place<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.in_off, d.cursor, d.mover_sorted);
+            k_mover_write_f64<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.mover_sorted, d.in_off, d.in_cnt,
+                                                 d.in_before, d.cnt_new, d.cell_start_B, d.cursor, d.recB, d.recA);
+        }
     }
     uint32_t* t = d.cell_start; d.cell_start = d.cell_start_B; d.cell_start_B = t;
 }
 
-void launch_deposit_only_f64(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
+void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
 {
     const uint64_t G = (uint64_t)P.R * P.n3;
     cudaMemsetAsync(d.Xe, 0, G * sizeof(unsigned long long), s);
     cudaMemsetAsync(d.ne_fix, 0, G * sizeof(unsigned long long), s);
-    // counted below
-    if (N > 0) g_launches++, k_deposit_f64<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.recA, N, d.Xe, d.ne_fix);
+    if (N == 0) return;
+    ++g_launches;
+    if (d.mixed) k_deposit_f32<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.rA32, d.cellA32, N, d.Xe, d.ne_fix);
+    else k_deposit_f64<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.recA, N, d.Xe, d.ne_fix);
 }
 
 void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
@@ -973,31 +1240,50 @@ void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
     k_kmc<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.fired, d.Npos, d.Nneg, G, d.ctr);
 }
 
-void launch_particles_f64(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s)
+// Part a: loss removal, photons, merge scan (offsets, output count, work).
+void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 {
-    (void)N;
     cudaMemsetAsync(d.photo_cnt, 0, G * sizeof(int32_t), s);
     cudaMemsetAsync(d.photo_cursor, 0, G * sizeof(int32_t), s);
     cudaMemsetAsync(d.photo_w, 0, G * sizeof(unsigned long long), s);
+    uint32_t* wbase = d.mixed ? reinterpret_cast<uint32_t*>(d.rA32) + 3 : reinterpret_cast<uint32_t*>(d.recA) + 7;
+    const int wstride = d.mixed ? 4 : 8;
     ++g_launches;
-    k_loss_f64<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.recA, d.cell_start, d.Xe, d.fired, G);
-    if (P.photon_ratio > 0.0)
+    k_loss<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, wbase, wstride, d.cell_start, d.Xe, d.fired, G);
+    if (P.photon_ratio > 0.0) {
         ++g_launches;
-        k_photons<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.fired, G, d.photos, d.photo_cap, d.photo_cnt,
-                                                            d.photo_w, d.Npos, d.ctr);
+        k_photons<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.mixed ? 1 : 0, d.fired, G, d.photos, d.photo_cap,
+                                                            d.photo_cnt, d.photo_w, d.Npos, d.ctr);
+    }
     MergeScanOp op{ d.Xe, d.fired, d.photo_w, d.photo_cnt, d.cell_start, d.out_start, d.photo_off, d.work_off,
                     G, P.ppc, P.n_new };
     run_scan<3>(op, G, d.scan_blk, s);
-    if (P.photon_ratio > 0.0)
+}
+
+// Part b (after the host has checked the output count and work size):
+// photoelectron grouping and the merge/split itself.
+void launch_particles_b(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
+{
+    if (P.photon_ratio > 0.0) {
         ++g_launches;
         k_photo_place<<<grid_for(d.photo_cap, 256, 1024), 256, 0, s>>>(d.photos, d.ctr, d.photo_cap, d.photo_off,
                                                                       d.photo_cursor, d.photo_sorted);
+    }
     ++g_launches;
-    k_merge_f64<<<152 * 8, MERGE_WARPS * 32, 0, s>>>(P, d.recA, d.cell_start, d.fired, d.photos, d.photo_sorted,
-                                                      d.photo_off, d.out_start, d.work_off,
-                                                      reinterpret_cast<MP*>(d.work), d.work_cap / 3, d.recB, G,
-                                                      d.mover_cap, d.photo_cap, d.ctr);
-    P64* t = d.recA; d.recA = d.recB; d.recB = t;
+    if (d.mixed) {
+        k_merge<true><<<152 * 8, MERGE_WARPS * 32, 0, s>>>(
+            P, nullptr, d.rA32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
+            d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
+            d.photo_cap, d.ctr);
+        P32* t = d.rA32; d.rA32 = d.rB32; d.rB32 = t;
+        uint32_t* tc = d.cellA32; d.cellA32 = d.cellB32; d.cellB32 = tc;
+    } else {
+        k_merge<false><<<152 * 8, MERGE_WARPS * 32, 0, s>>>(
+            P, d.recA, nullptr, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
+            d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, d.recB, nullptr, nullptr, G, d.mover_cap,
+            d.photo_cap, d.ctr);
+        P64* t = d.recA; d.recA = d.recB; d.recB = t;
+    }
     uint32_t* u = d.cell_start; d.cell_start = d.out_start; d.out_start = u;
 }
 

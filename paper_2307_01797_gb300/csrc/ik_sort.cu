@@ -108,6 +108,30 @@ __global__ void k_gather(const P64* __restrict__ in, const uint32_t* __restrict_
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) out[j] = in[perm[j]];
 }
 
+// Mixed form: (cell, FP32 offset in cell units) from the sorted FP64 records.
+__global__ void k_gather32(Params P, const P64* __restrict__ in, const uint32_t* __restrict__ perm, uint32_t n,
+                           P32* __restrict__ out, uint32_t* __restrict__ cout)
+{
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const P64 p = in[perm[j]];
+        const uint32_t c = p.cell & (uint32_t)(P.n3 - 1);
+        const int id[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
+                            (int)(c >> (2 * P.log2n)) };
+        const double X[3] = { p.x, p.y, p.z };
+        float o[3];
+        for (int a = 0; a < 3; ++a) {
+            float f = (float)((X[a] - P.lo[a]) / P.h[a] - (double)id[a]);
+            if (!(f >= 0.0f)) f = 0.0f;
+            if (f >= 1.0f) f = 0x1.fffffep-1f;
+            o[a] = f;
+        }
+        P32 q;
+        q.ox = o[0]; q.oy = o[1]; q.oz = o[2]; q.w = p.w;
+        out[j] = q;
+        cout[j] = p.cell;
+    }
+}
+
 // cell_start from sorted keys: cells (key[j-1], key[j]] start at j.
 __global__ void k_cell_start(const uint32_t* __restrict__ keys, uint32_t n, uint64_t G, uint32_t* __restrict__ cs)
 {
@@ -158,9 +182,10 @@ size_t radix_scratch_elems(uint32_t cap)
     return scan_scratch_elems((uint64_t)RS_BINS * nblk, 1) + (size_t)RS_BINS * nblk + 16;
 }
 
-// x, y, z, w, real are device pointers (already staged).
-void launch_set_particles_f64(const Params& P, Dev& d, const double* x, const double* y, const double* z,
-                              const uint32_t* w, const int32_t* real, uint32_t n, uint64_t G, cudaStream_t s)
+// x, y, z, w, real are device pointers (already staged).  `tmp64` holds n
+// FP64 records during the sort.
+void launch_set_particles(const Params& P, Dev& d, const double* x, const double* y, const double* z,
+                          const uint32_t* w, const int32_t* real, uint32_t n, uint64_t G, cudaStream_t s)
 {
     uint32_t* keys = d.sort_tmp;
     uint32_t* vals = keys + d.mover_cap;
@@ -169,12 +194,14 @@ void launch_set_particles_f64(const Params& P, Dev& d, const double* x, const do
     cudaMemsetAsync(d.ctr, 0, sizeof(Counters), s);
     if (n > 0) {
         ++g_launches;
-        k_pack<<<gsz(n, 256), 256, 0, s>>>(P, x, y, z, w, real, n, d.recB, keys, vals, d.ctr);
+        P64* tmp64 = d.mixed ? reinterpret_cast<P64*>(d.work) + n : d.recB;   // staging sits at the start
+        k_pack<<<gsz(n, 256), 256, 0, s>>>(P, x, y, z, w, real, n, tmp64, keys, vals, d.ctr);
         int bits = 1;
         while (bits < 32 && (1ull << bits) < G) ++bits;
         radix_sort_pairs(keys, vals, kt, vt, n, bits, s, d.scan_blk, 0);
         ++g_launches;
-        k_gather<<<gsz(n, 256), 256, 0, s>>>(d.recB, vals, n, d.recA);
+        if (d.mixed) k_gather32<<<gsz(n, 256), 256, 0, s>>>(P, tmp64, vals, n, d.rA32, d.cellA32);
+        else k_gather<<<gsz(n, 256), 256, 0, s>>>(tmp64, vals, n, d.recA);
     }
     ++g_launches;
     k_cell_start<<<gsz((uint64_t)n + 1, 256), 256, 0, s>>>(keys, n, G, d.cell_start);

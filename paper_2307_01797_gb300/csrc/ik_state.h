@@ -57,6 +57,7 @@ struct Counters {
     unsigned long long n_new;          // product + photo particles
     unsigned long long ion, att, phot; // firings
     unsigned long long absorbed_w;
+    unsigned long long photo_slots;    // sum over cells of min(N_gamma, N_new)
     unsigned int err;                  // DERR_* bits
     unsigned int kmc_fail_cell;
     unsigned long long outflow[MAX_R];
@@ -112,24 +113,26 @@ struct Dev {
     uint32_t mover_cap = 0, photo_cap = 0;
     uint64_t work_cap = 0;             // merge work elements (all 3 buffers)
     double* stage = nullptr;           // 3 G doubles: field upload/readback
+    bool mixed = false;                // FP32 particle form
 };
 
 // ------------------------------------------------------------- launchers
 // ik_particles.cu
-void launch_transport_f64(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
-void launch_transport_finish_f64(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s);
-void launch_deposit_only_f64(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
+void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
+void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s);
+void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
 void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
-void launch_particles_f64(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s);
+void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
+void launch_particles_b(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
 // ik_sort.cu
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
                       uint32_t n, int key_bits, cudaStream_t s, long long* blk_scratch,
                       size_t blk_scratch_elems);
 size_t radix_scratch_elems(uint32_t cap);
-void launch_set_particles_f64(const Params& P, Dev& d, const double* x, const double* y,
-                              const double* z, const uint32_t* w, const int32_t* real, uint32_t n,
-                              uint64_t G, cudaStream_t s);
+void launch_set_particles(const Params& P, Dev& d, const double* x, const double* y,
+                          const double* z, const uint32_t* w, const int32_t* real, uint32_t n,
+                          uint64_t G, cudaStream_t s);
 // ik_field.cu
 int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2,
                 int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out);

@@ -233,3 +233,76 @@ def test_edge_cases():
         H2.itokmc_set_particles(np.zeros(2000) + L / 2, np.zeros(2000) + L / 2, np.zeros(2000) + L / 2,
                                 np.ones(2000, np.uint32))
     assert e.value.code == -4
+
+
+# ---------------------------------------------------------------- mixed form
+def _mixed_handle(ph, st, E, ions, seed0, cap):
+    H = gpu_handle(ph, cap, seed0=seed0, precision=itokmc.MIXED)
+    H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+    if E is not None:
+        H.itokmc_set_field(*E)
+    if ions is not None:
+        H.itokmc_set_ions(*ions)
+    return H
+
+
+def test_mixed_transport_against_fp64_oracle():
+    """FP32 positions/push with common random numbers: positions within
+    1e-5 cell of the FP64 oracle for all but a few particles whose cell
+    membership flips at a face; exact charge conservation of the int64
+    deposit; densities within 1e-3 (relative L2)."""
+    ph = small_phys(32, dt=2e-10)
+    st = mixed_state(ph, seed=17)
+    E = synth.random_field(ph, seed=5, amp=4e6)
+    ions = synth.random_ions(ph, seed=6)
+    seed0 = 12
+    S = oracle_state(ph, st, seed0, *ions)
+    T, ne, Xe, rho, out = _transport_oracle(ph, S, E, seed0, 0)
+    H = _mixed_handle(ph, st, E, ions, seed0, 4 * len(st["w"]))
+    # the upload itself rounds positions to FP32 offsets: same cells, same order
+    G0 = H.itokmc_read_particles()
+    assert np.array_equal(G0["cell"], S["cell"]) and np.array_equal(G0["w"], S["w"])
+    H.itokmc_run_stage(itokmc.STAGE_TRANSPORT)
+    G = H.itokmc_read_particles()
+    assert abs(len(G["w"]) - len(T["w"])) <= 2
+    h = synth.cell_size(ph)
+    W = int(G["w"].astype(np.int64).sum())
+    neg = H.itokmc_read_densities(itokmc.NE_FIX)
+    assert sum(int(v) for v in neg) == W << (3 * ph["frac_bits"])
+    if len(G["w"]) == len(T["w"]):
+        d = np.max(np.abs(np.stack([G["x"] - T["x"], G["y"] - T["y"], G["z"] - T["z"]])), axis=0) / h
+        assert (d > 1e-5).mean() < 2e-3, (d > 1e-5).mean()
+    rel = np.linalg.norm((neg - ne).astype(np.float64)) / np.linalg.norm(ne.astype(np.float64))
+    assert rel < 1e-3, rel
+    assert np.abs(H.itokmc_read_densities(itokmc.XE) - Xe).sum() <= 0.001 * Xe.sum()
+
+
+def test_mixed_steps_against_fp64_oracle_chain():
+    """Three full steps of the mixed form (FP32 particles, FP32 V-cycles in
+    FP64 refinement) against the FP64 oracle chain: electron density and E
+    within the stated tolerance, charge conservation exact."""
+    ph = small_phys(16, dt=5e-12, photon_ratio=0.06)
+    st = mixed_state(ph, seed=31, peak=1e19, n_random=500)
+    seed0 = 9
+    p0 = oracle.make_params(ph, seed=seed0)
+    S = oracle_state(ph, st, seed0)
+    ne, _ = oracle.deposit(p0, S["x"], S["y"], S["z"], S["w"], S["cell"])
+    phi, E = poisson.solve(oracle.rho_fixed(p0, ne, S["Npos"], S["Nneg"]), ph)
+    H = _mixed_handle(ph, st, E, None, seed0, 200000)
+    Q0 = -int(st["w"].astype(np.int64).sum())
+    out = 0
+    for k in range(3):
+        S, info = oracle.step(oracle.make_params(ph, seed=seed0, step=k), S, E)
+        phi, E = poisson.solve(info["rho_fixed"], ph)
+        H.itokmc_step(1)
+        out += H.itokmc_get_stats()["outflow_weight"]
+        neg = H.itokmc_read_densities(itokmc.NE_FIX).astype(np.float64)
+        rel = np.linalg.norm(neg - info["ne_fix"]) / np.linalg.norm(info["ne_fix"].astype(np.float64))
+        assert rel < 2e-2, (k, rel)
+        Eg = H.itokmc_read_densities(itokmc.E)
+        Eo = np.stack([e.ravel() for e in E])
+        assert np.max(np.abs(Eg - Eo)) / np.max(np.abs(Eo)) < 1e-3
+        G = H.itokmc_read_particles()
+        Np, Nn = H.itokmc_read_densities(itokmc.NPOS), H.itokmc_read_densities(itokmc.NNEG)
+        assert int(Np.sum() - Nn.sum()) - int(G["w"].astype(np.int64).sum()) == Q0 + out
+        assert np.bincount(G["cell"], minlength=16 ** 3).max() <= ph["ppc"]
