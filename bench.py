@@ -179,7 +179,9 @@ def our_arm(args, rank, world):
     ph, st, ions = workload(args)
     N0 = len(st["w"])
     form = itokmc.MIXED if args.form == "mixed" else itokmc.FP64
-    cap = int(N0 * 1.6) + 1_000_000
+    # photoelectrons landing in empty cells are split up to ppc particles each,
+    # so the count grows from step to step
+    cap = int(N0 * args.cap_factor) + 20_000_000
     H = itokmc.Handle(itokmc.make_config(ph, cap, seed0=1 + rank, precision=form))
     H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
     H.itokmc_set_ions(*ions)
@@ -198,9 +200,12 @@ def our_arm(args, rank, world):
     processed = 0
     movers = 0
     mg_cycles = []
+    counts = []
     e0.record(stream)
     for _ in range(args.steps):
-        processed += H.itokmc_num_particles()
+        nk = H.itokmc_num_particles()
+        counts.append(nk)
+        processed += nk
         H.itokmc_step(1)
         s = H.itokmc_get_stats()
         stage["transport"] += s["ms_transport"]; stage["kmc"] += s["ms_kmc"]
@@ -278,7 +283,7 @@ def our_arm(args, rank, world):
         "config": config_of(args, N0),
         "push_sort_deposit_kmc_rate": core_rate,
         "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
-        "movers_per_step": movers / args.steps, "mg_cycles": mg_cycles,
+        "movers_per_step": movers / args.steps, "mg_cycles": mg_cycles, "particles_per_step": counts,
         "roofline": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)", "achieved": ach,
                      "peak": pk, "peak_kind": pk_kind, "unit": "GB/s", "frac": ach / pk, "traffic": None,
                      "bytes_per_particle": 2 * R + mesh / 32},
@@ -301,6 +306,7 @@ def main():
     ap.add_argument("--particles", type=float, default=2e7)
     ap.add_argument("--ref-particles", type=int, default=2000000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cap-factor", type=float, default=4.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -190,7 +190,7 @@ def test_ensemble_members_equal_single_runs():
 
 def test_deterministic_rerun():
     ph = small_phys(16, dt=5e-12, photon_ratio=0.06)
-    st = mixed_state(ph, seed=8, peak=1e19)
+    st = mixed_state(ph, seed=8, peak=3e16)
     out = []
     for _ in range(2):
         H = gpu_handle(ph, 100000, seed0=3)
