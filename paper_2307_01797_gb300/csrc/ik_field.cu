@@ -57,6 +57,21 @@ __device__ __forceinline__ T nbr_sum(const T* __restrict__ phi, uint64_t idx, in
     return s;
 }
 
+// 1/diag for the diagonal counts 1..8 (a multiply instead of a divide).
+template <class T>
+__device__ __forceinline__ T inv_diag(int d)
+{
+    switch (d) {
+    case 4: return (T)(1.0 / 4.0);
+    case 5: return (T)(1.0 / 5.0);
+    case 6: return (T)(1.0 / 6.0);
+    case 7: return (T)(1.0 / 7.0);
+    case 8: return (T)(1.0 / 8.0);
+    case 9: return (T)(1.0 / 9.0);
+    default: return (T)1 / (T)d;
+    }
+}
+
 template <class T>
 __global__ void k_smooth(T* __restrict__ phi, const T* __restrict__ rhs, Geo G, T h2, int color)
 {
@@ -72,7 +87,7 @@ __global__ void k_smooth(T* __restrict__ phi, const T* __restrict__ rhs, Geo G, 
         const uint64_t idx = ((r * n + k) * n + j) * n + i;
         int diag;
         const T s = nbr_sum(phi, idx, n, i, j, k, diag);
-        phi[idx] = (s - h2 * rhs[idx]) / (T)diag;
+        phi[idx] = (s - h2 * rhs[idx]) * inv_diag<T>(diag);
     }
 }
 
@@ -192,18 +207,32 @@ __global__ void __launch_bounds__(NORM_TPB) k_resid_norm(const double* __restric
     }
 }
 
-// Per realization: sum its blocks' partials in order.
-__global__ void k_norm_final(const double* __restrict__ part, int blocks_per_real, int R, double* __restrict__ out)
+// Per realization (one block each): fixed-order strided sums, then a fixed
+// tree in shared memory -- the same result on every run.
+__global__ void __launch_bounds__(256) k_norm_final(const double* __restrict__ part, int blocks_per_real, int R,
+                                                    double* __restrict__ out)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
+    __shared__ double sa[256], sb[256];
+    const int r = blockIdx.x;
     double a = 0.0, b = 0.0;
-    for (int q = 0; q < blocks_per_real; ++q) {
+    for (int q = threadIdx.x; q < blocks_per_real; q += 256) {
         a += part[2 * ((uint64_t)r * blocks_per_real + q)];
         b += part[2 * ((uint64_t)r * blocks_per_real + q) + 1];
     }
-    out[2 * r] = a;
-    out[2 * r + 1] = b;
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sa[threadIdx.x] += sa[threadIdx.x + w];
+            sb[threadIdx.x] += sb[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * r] = sa[0];
+        out[2 * r + 1] = sb[0];
+    }
 }
 
 __global__ void k_add_correction(double* __restrict__ phi, const float* __restrict__ e, uint64_t cells)
@@ -282,7 +311,7 @@ void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
         const int cells = G.n * G.n * G.n;
         const size_t sm = 2 * sizeof(T) * cells;
         ++g_launches;
-        k_bottom<T><<<R, 256, sm, s>>>(phi, rhs, G.n, h2, 4 * cells);
+        k_bottom<T><<<R, 256, sm, s>>>(phi, rhs, G.n, h2, 48);
         return;
     }
     const int tpb = 256;
@@ -332,7 +361,7 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
         k_resid_norm<<<nblk, NORM_TPB, 0, s>>>(L0.phi, L0.rhs, precision == 1 ? L0.rhs32 : nullptr, G0, inv_h2,
                                                d.norm_part, 1, items);
         ++g_launches;
-        k_norm_final<<<(R + 127) / 128, 128, 0, s>>>(d.norm_part, bpr, R, d.norm_out);
+        k_norm_final<<<R, 256, 0, s>>>(d.norm_part, bpr, R, d.norm_out);
         cudaMemcpyAsync(h_norm.data(), d.norm_out, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
         worst = 0.0;

@@ -435,7 +435,7 @@ __device__ int kmc_cell(const Params& P, Stream& s, long long X0, const double k
 
 __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const E64* __restrict__ E,
                       int64_t* __restrict__ fired, int64_t* __restrict__ Npos, int64_t* __restrict__ Nneg,
-                      uint64_t G, Counters* __restrict__ ctr)
+                      uint64_t G, uint32_t* __restrict__ pc_list, Counters* __restrict__ ctr)
 {
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
         long long f[3] = { 0, 0, 0 };
@@ -458,7 +458,10 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
             }
             Npos[g] += f[0];
             Nneg[g] += f[1];
-            if (f[2] > 0) atomicAdd(&ctr->photo_slots, (unsigned long long)(f[2] < P.n_new ? f[2] : P.n_new));
+            if (f[2] > 0) {
+                atomicAdd(&ctr->photo_slots, (unsigned long long)(f[2] < P.n_new ? f[2] : P.n_new));
+                pc_list[atomicAdd(&ctr->n_photo_cells, 1u)] = (uint32_t)g;
+            }
             atomicAdd(&ctr->ion, (unsigned long long)f[0]);
             atomicAdd(&ctr->att, (unsigned long long)f[1]);
             atomicAdd(&ctr->phot, (unsigned long long)f[2]);
@@ -530,15 +533,18 @@ __device__ __forceinline__ void photon_sample(const Params& P, uint64_t seed, ui
     dir[2] = cz;
 }
 
+// One warp per photon-emitting cell, one lane per superphoton slot.
 __global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired, uint64_t G,
-                          Photo* __restrict__ photos, uint32_t photo_cap, int32_t* __restrict__ photo_cnt,
-                          unsigned long long* __restrict__ photo_w, int64_t* __restrict__ Npos,
-                          Counters* __restrict__ ctr)
+                          const uint32_t* __restrict__ pc_list, Photo* __restrict__ photos, uint32_t photo_cap,
+                          int32_t* __restrict__ photo_cnt, unsigned long long* __restrict__ photo_w,
+                          int64_t* __restrict__ Npos, Counters* __restrict__ ctr)
 {
-    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned lane = lane_id();
+    const uint32_t ncells = ctr->n_photo_cells;
+    const double lnK = dlog(P.kappa_hi / P.kappa_lo);
+    for (uint32_t e = (blockIdx.x * blockDim.x + threadIdx.x) / 32; e < ncells; e += (gridDim.x * blockDim.x) / 32) {
+        const uint64_t g = pc_list[e];
         const long long Gm = fired[2 * G + g];
-        if (Gm <= 0) continue;
-        const double lnK = dlog(P.kappa_hi / P.kappa_lo);
         const int r = real_of(P, (uint32_t)g);
         const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
         const int ijk[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
@@ -546,7 +552,7 @@ __global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired
         const long long m = Gm < P.n_new ? Gm : P.n_new;
         const long long wq = Gm / m, rem = Gm % m;
         const uint64_t seed = seed_of(P, r);
-        for (long long j = 0; j < m; ++j) {
+        for (long long j = lane; j < m; j += 32) {
             const long long wj = wq + (j == 0 ? rem : 0);
             double Y0[3], rr, dir[3], Ya[3];
             photon_sample(P, seed, c, (uint32_t)j, ijk, lnK, Y0, rr, dir);
@@ -603,11 +609,13 @@ __global__ void k_photo_place(const Photo* __restrict__ photos, const Counters* 
 }
 
 // ------------------------------------------------------------------ merge scan
+constexpr int MERGE_SMEM = 128;      // elements per shared buffer (x3 per warp)
+constexpr int MERGE_WARPS = 8;
+constexpr int MERGE_LANE_NODES = 8;  // levels with at least this many nodes split one node per lane
 // Per cell: W = X_e + dN + photo weight -> min(W, ppc) leaves; photo offsets;
 // work elements M + ppc (global scratch only for lists too long for the
 // warp's shared-memory buffers).
-constexpr int MERGE_SMEM = 160;   // elements per shared buffer (x3 per warp)
-constexpr int MERGE_WARPS = 4;
+
 
 struct MergeScanOp {
     const unsigned long long* Xe;
@@ -618,28 +626,38 @@ struct MergeScanOp {
     uint32_t* out_start;
     uint32_t* photo_off;
     uint64_t* work_off;
+    uint32_t* small_list;     // non-empty cells whose list fits shared memory
+    uint32_t* big_list;       // the others
+    uint32_t* list_n;         // [2]: lengths
     uint64_t G;
     int ppc, n_new;
-    __device__ void load(uint64_t g, long long v[3]) const
+    __device__ void load(uint64_t g, long long v[5]) const
     {
         const long long dN = fired[g] - fired[G + g];
         const long long W = (long long)Xe[g] + dN + (long long)photo_w[g];
         v[0] = W < ppc ? W : ppc;
         v[1] = photo_cnt[g];
         const long long M = (long long)(cs[g + 1] - cs[g]) + (dN > 0 ? (dN < n_new ? dN : n_new) : 0) + photo_cnt[g];
-        v[2] = (M > 0 && M + ppc > MERGE_SMEM) ? (M + ppc) : 0;
+        const bool big = M > 0 && M + ppc > MERGE_SMEM;
+        v[2] = big ? (M + ppc) : 0;
+        v[3] = (v[0] > 0 && !big) ? 1 : 0;
+        v[4] = (v[0] > 0 && big) ? 1 : 0;
     }
-    __device__ void store(uint64_t g, const long long ex[3], const long long*) const
+    __device__ void store(uint64_t g, const long long ex[5], const long long* v) const
     {
         out_start[g] = (uint32_t)ex[0];
         photo_off[g] = (uint32_t)ex[1];
         work_off[g] = (uint64_t)ex[2];
+        if (v[3]) small_list[ex[3]] = (uint32_t)g;
+        if (v[4]) big_list[ex[4]] = (uint32_t)g;
     }
-    __device__ void total(const long long t[3]) const
+    __device__ void total(const long long t[5]) const
     {
         out_start[G] = (uint32_t)t[0];
         photo_off[G] = (uint32_t)t[1];
         work_off[G] = (uint64_t)t[2];
+        list_n[0] = (uint32_t)t[3];
+        list_n[1] = (uint32_t)t[4];
     }
 };
 
@@ -760,30 +778,82 @@ __device__ uint32_t split_node(const MP* src, uint32_t m, unsigned long long W, 
 // MX = false: FP64 records with absolute positions; MX = true: FP32 cell
 // offsets plus a cell array.  The tree itself works on FP64 coordinates
 // (FP32 offsets convert exactly).
-template <bool MX>
+// One node per lane: stable insertion sort of the node's slice along its
+// widest axis (in place), weighted median, child sizes.  Returns the number
+// of output elements; nl_out receives the left child's size (0 = unsplit).
+__device__ __forceinline__ uint32_t lane_split_prepare(MP* node, uint32_t m, unsigned long long W, uint32_t& pm_out,
+                                                       MP& ml, MP& mr, uint32_t& nl_out, bool& lmed, bool& rmed)
+{
+    double lo[3] = { node[0].x, node[0].y, node[0].z }, hi[3] = { node[0].x, node[0].y, node[0].z };
+    for (uint32_t q = 1; q < m; ++q) {
+        const MP e = node[q];
+        const double v[3] = { e.x, e.y, e.z };
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = v[a] < lo[a] ? v[a] : lo[a];
+            hi[a] = v[a] > hi[a] ? v[a] : hi[a];
+        }
+    }
+    const double ext[3] = { hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2] };
+    int axis = 0;
+    if (ext[1] > ext[axis]) axis = 1;
+    if (ext[2] > ext[axis]) axis = 2;
+    for (uint32_t q = 1; q < m; ++q) {
+        const MP key = node[q];
+        const double c = mp_coord(key, axis);
+        int p = (int)q - 1;
+        while (p >= 0 && mp_coord(node[p], axis) > c) {
+            node[p + 1] = node[p];
+            --p;
+        }
+        node[p + 1] = key;
+    }
+    unsigned long long C = 0;
+    uint32_t pm = m - 1;
+    for (uint32_t q = 0; q < m; ++q) {
+        C += node[q].w;
+        if (2ull * C > W) { pm = q; break; }
+    }
+    const MP med = node[pm];
+    const unsigned long long WL = C - med.w, WR = W - C;
+    ml = med; mr = med;
+    if (med.w == 1) {
+        lmed = WL <= WR;
+        rmed = !lmed;
+    } else {
+        const unsigned long long a = (W + 1) / 2 - WL, b = med.w - a;
+        ml.w = (uint32_t)a;
+        mr.w = (uint32_t)b;
+        lmed = a > 0;
+        rmed = b > 0;
+    }
+    pm_out = pm;
+    nl_out = pm + (lmed ? 1u : 0u);
+    return nl_out + (rmed ? 1u : 0u) + (m - pm - 1);
+}
+
+// SMALL: cells whose list fits the warp's shared buffers; otherwise the
+// cells that do not, with their buffers in the global work area.
+template <bool MX, bool SMALL>
 __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
     Params P, const P64* __restrict__ A, const P32* __restrict__ A32, const uint32_t* __restrict__ cs,
     const int64_t* __restrict__ fired, const Photo* __restrict__ photos, const uint32_t* __restrict__ photo_sorted,
     const uint32_t* __restrict__ photo_off, const uint32_t* __restrict__ out_start,
     const uint64_t* __restrict__ work_off, MP* __restrict__ work, uint64_t work_cap, P64* __restrict__ out,
     P32* __restrict__ out32, uint32_t* __restrict__ cout, uint64_t G, uint32_t cap, uint32_t photo_cap,
-    Counters* __restrict__ ctr)
+    const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_n, Counters* __restrict__ ctr)
 {
-    __shared__ MP sbuf[MERGE_WARPS][3][MERGE_SMEM];
+    extern __shared__ unsigned char merge_smem[];
+    MP(*sbuf)[3][MERGE_SMEM] = reinterpret_cast<MP(*)[3][MERGE_SMEM]>(merge_smem);
     __shared__ uint32_t sb[MERGE_WARPS][2][257];
     const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
-    const uint64_t nchunks = (G + 31) / 32;
     const uint64_t gw = (uint64_t)blockIdx.x * MERGE_WARPS + wid;
     const uint64_t nwarps = (uint64_t)gridDim.x * MERGE_WARPS;
     const int T = P.ppc;
-    for (uint64_t chunk = gw; chunk < nchunks; chunk += nwarps) {
-        const uint64_t g0 = chunk * 32 + lane;
-        const bool has = g0 < G && out_start[g0 + 1] > out_start[g0];
-        unsigned todo = __ballot_sync(0xffffffffu, has);
-        while (todo) {
-            const int l = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint64_t g = chunk * 32 + l;
+    const uint32_t ncells = list_n[SMALL ? 0 : 1];
+    for (uint64_t li = gw; li < ncells; li += nwarps) {
+        {
+            const uint64_t g = list[li];
             const int r = real_of(P, (uint32_t)g);
             const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
             const long long dN = fired[g] - fired[G + g];
@@ -796,7 +866,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                 continue;
             }
             MP *cur, *nxt, *tmp;
-            if (Mmax + T <= MERGE_SMEM) {
+            if (SMALL) {
                 cur = sbuf[wid][0]; nxt = sbuf[wid][1]; tmp = sbuf[wid][2];
             } else {
                 const uint64_t S = (uint64_t)Mmax + T;
@@ -877,9 +947,61 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
             __syncwarp();
             int nnodes = 1;
             for (int level = 1; level < T; level *= 2) {
+                if (lane == 0) bnd2[0] = 0;
+                if (nnodes >= MERGE_LANE_NODES) {
+                    // one node per lane; nodes in rounds of 32
+                    uint32_t fill = 0;
+                    int nn = 0;
+                    for (int d0 = 0; d0 < nnodes; d0 += 32) {
+                        const int d = d0 + (int)lane;
+                        uint32_t s0 = 0, m = 0, outn = 0, pm = 0, nl = 0;
+                        unsigned long long W = 0;
+                        bool split = false, lmed = false, rmed = false;
+                        MP ml, mr;
+                        if (d < nnodes) {
+                            s0 = bnd[d];
+                            m = bnd[d + 1] - s0;
+                            for (uint32_t q = 0; q < m; ++q) W += cur[s0 + q].w;
+                            split = W >= 2;
+                            outn = split ? lane_split_prepare(cur + s0, m, W, pm, ml, mr, nl, lmed, rmed) : m;
+                        }
+                        // exclusive scans over the round: output elements, child nodes
+                        uint32_t o = outn, ch = d < nnodes ? (split ? 2u : 1u) : 0u;
+#pragma unroll
+                        for (int k = 1; k < 32; k <<= 1) {
+                            const uint32_t yo = __shfl_up_sync(0xffffffffu, o, k);
+                            const uint32_t yc = __shfl_up_sync(0xffffffffu, ch, k);
+                            if ((int)lane >= k) { o += yo; ch += yc; }
+                        }
+                        const uint32_t off = fill + o - outn;
+                        const int cidx = nn + (int)(ch - (d < nnodes ? (split ? 2u : 1u) : 0u));
+                        if (d < nnodes) {
+                            MP* dst = nxt + off;
+                            if (split) {
+                                for (uint32_t q = 0; q < pm; ++q) dst[q] = cur[s0 + q];
+                                if (lmed) dst[pm] = ml;
+                                uint32_t r0 = nl;
+                                if (rmed) dst[r0++] = mr;
+                                for (uint32_t q = pm + 1; q < m; ++q) dst[r0++] = cur[s0 + q];
+                                bnd2[cidx + 1] = off + nl;
+                                bnd2[cidx + 2] = off + outn;
+                            } else {
+                                for (uint32_t q = 0; q < m; ++q) dst[q] = cur[s0 + q];
+                                bnd2[cidx + 1] = off + m;
+                            }
+                        }
+                        fill += __shfl_sync(0xffffffffu, o, 31);
+                        nn += (int)__shfl_sync(0xffffffffu, ch, 31);
+                    }
+                    __syncwarp();
+                    MP* t = cur; cur = nxt; nxt = t;
+                    uint32_t* tb = bnd; bnd = bnd2; bnd2 = tb;
+                    nnodes = nn;
+                    __syncwarp();
+                    continue;
+                }
                 uint32_t fill = 0;
                 int nn = 0;
-                if (lane == 0) bnd2[0] = 0;
                 for (int d = 0; d < nnodes; ++d) {
                     const uint32_t s0 = bnd[d], s1 = bnd[d + 1], m = s1 - s0;
                     unsigned long long W = 0;
@@ -1237,7 +1359,7 @@ void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 {
     ++g_launches;
-    k_kmc<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.fired, d.Npos, d.Nneg, G, d.ctr);
+    k_kmc<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.fired, d.Npos, d.Nneg, G, d.pc_list, d.ctr);
 }
 
 // Part a: loss removal, photons, merge scan (offsets, output count, work).
@@ -1252,12 +1374,12 @@ void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
     k_loss<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, wbase, wstride, d.cell_start, d.Xe, d.fired, G);
     if (P.photon_ratio > 0.0) {
         ++g_launches;
-        k_photons<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.mixed ? 1 : 0, d.fired, G, d.photos, d.photo_cap,
-                                                            d.photo_cnt, d.photo_w, d.Npos, d.ctr);
+        k_photons<<<152 * 16, 256, 0, s>>>(P, d.mixed ? 1 : 0, d.fired, G, d.pc_list, d.photos, d.photo_cap,
+                                            d.photo_cnt, d.photo_w, d.Npos, d.ctr);
     }
     MergeScanOp op{ d.Xe, d.fired, d.photo_w, d.photo_cnt, d.cell_start, d.out_start, d.photo_off, d.work_off,
-                    G, P.ppc, P.n_new };
-    run_scan<3>(op, G, d.scan_blk, s);
+                    d.small_list, d.big_list, d.list_n, G, P.ppc, P.n_new };
+    run_scan<5>(op, G, d.scan_blk, s);
 }
 
 // Part b (after the host has checked the output count and work size):
@@ -1269,19 +1391,34 @@ void launch_particles_b(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
         k_photo_place<<<grid_for(d.photo_cap, 256, 1024), 256, 0, s>>>(d.photos, d.ctr, d.photo_cap, d.photo_off,
                                                                       d.photo_cursor, d.photo_sorted);
     }
-    ++g_launches;
+    const size_t smem = sizeof(MP) * 3 * MERGE_SMEM * MERGE_WARPS;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_merge<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_merge<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    g_launches += 2;
     if (d.mixed) {
-        k_merge<true><<<152 * 8, MERGE_WARPS * 32, 0, s>>>(
+        k_merge<true, true><<<152 * 2, MERGE_WARPS * 32, smem, s>>>(
             P, nullptr, d.rA32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
             d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
-            d.photo_cap, d.ctr);
+            d.photo_cap, d.small_list, d.list_n, d.ctr);
+        k_merge<true, false><<<152 * 4, MERGE_WARPS * 32, 0, s>>>(
+            P, nullptr, d.rA32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
+            d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
+            d.photo_cap, d.big_list, d.list_n, d.ctr);
         P32* t = d.rA32; d.rA32 = d.rB32; d.rB32 = t;
         uint32_t* tc = d.cellA32; d.cellA32 = d.cellB32; d.cellB32 = tc;
     } else {
-        k_merge<false><<<152 * 8, MERGE_WARPS * 32, 0, s>>>(
+        k_merge<false, true><<<152 * 2, MERGE_WARPS * 32, smem, s>>>(
             P, d.recA, nullptr, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
             d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, d.recB, nullptr, nullptr, G, d.mover_cap,
-            d.photo_cap, d.ctr);
+            d.photo_cap, d.small_list, d.list_n, d.ctr);
+        k_merge<false, false><<<152 * 4, MERGE_WARPS * 32, 0, s>>>(
+            P, d.recA, nullptr, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
+            d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, d.recB, nullptr, nullptr, G, d.mover_cap,
+            d.photo_cap, d.big_list, d.list_n, d.ctr);
         P64* t = d.recA; d.recA = d.recB; d.recB = t;
     }
     uint32_t* u = d.cell_start; d.cell_start = d.out_start; d.out_start = u;

@@ -132,15 +132,21 @@ __global__ void k_gather32(Params P, const P64* __restrict__ in, const uint32_t*
     }
 }
 
-// cell_start from sorted keys: cells (key[j-1], key[j]] start at j.
-__global__ void k_cell_start(const uint32_t* __restrict__ keys, uint32_t n, uint64_t G, uint32_t* __restrict__ cs)
+// Particles per cell (keys are cells), for the offsets.
+__global__ void k_count_keys(const uint32_t* __restrict__ keys, uint32_t n, int32_t* __restrict__ cnt)
 {
-    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j <= n; j += (uint64_t)gridDim.x * blockDim.x) {
-        const long long lo = j == 0 ? -1 : (long long)keys[j - 1];
-        const long long hi = j == n ? (long long)G : (long long)keys[j];
-        for (long long g = lo + 1; g <= hi; ++g) cs[g] = (uint32_t)j;
-    }
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        atomicAdd(cnt + keys[j], 1);
 }
+
+struct CountScanOp {
+    const int32_t* cnt;
+    uint32_t* cs;
+    uint64_t G;
+    __device__ void load(uint64_t g, long long v[1]) const { v[0] = cnt[g]; }
+    __device__ void store(uint64_t g, const long long ex[1], const long long*) const { cs[g] = (uint32_t)ex[0]; }
+    __device__ void total(const long long t[1]) const { cs[G] = (uint32_t)t[0]; }
+};
 
 int gsz(uint64_t n, int tpb)
 {
@@ -203,8 +209,12 @@ void launch_set_particles(const Params& P, Dev& d, const double* x, const double
         if (d.mixed) k_gather32<<<gsz(n, 256), 256, 0, s>>>(P, tmp64, vals, n, d.rA32, d.cellA32);
         else k_gather<<<gsz(n, 256), 256, 0, s>>>(tmp64, vals, n, d.recA);
     }
-    ++g_launches;
-    k_cell_start<<<gsz((uint64_t)n + 1, 256), 256, 0, s>>>(keys, n, G, d.cell_start);
+    cudaMemsetAsync(d.cnt_new, 0, G * sizeof(int32_t), s);
+    if (n > 0) {
+        ++g_launches;
+        k_count_keys<<<gsz(n, 256), 256, 0, s>>>(keys, n, d.cnt_new);
+    }
+    run_scan<1>(CountScanOp{ d.cnt_new, d.cell_start, G }, G, d.scan_blk, s);
 }
 
 }  // namespace ik

@@ -58,6 +58,7 @@ struct Counters {
     unsigned long long ion, att, phot; // firings
     unsigned long long absorbed_w;
     unsigned long long photo_slots;    // sum over cells of min(N_gamma, N_new)
+    unsigned int n_photo_cells;        // photon-emitting cells listed by the KMC
     unsigned int err;                  // DERR_* bits
     unsigned int kmc_fail_cell;
     unsigned long long outflow[MAX_R];
@@ -99,6 +100,10 @@ struct Dev {
     // merge
     uint32_t* out_start = nullptr;     // G + 1
     uint64_t* work_off = nullptr;      // G + 1
+    uint32_t* small_list = nullptr;    // G: non-empty cells merged in shared memory
+    uint32_t* big_list = nullptr;      // G: non-empty cells merged in the work buffer
+    uint32_t* list_n = nullptr;        // 2 counts
+    uint32_t* pc_list = nullptr;       // G: photon-emitting cells
     unsigned char* work = nullptr;  size_t work_bytes = 0;
     // scans
     long long* scan_blk = nullptr;  size_t scan_blk_elems = 0;
