@@ -214,6 +214,38 @@ const char* itokmc_last_error(const itokmc_handle* h);
 /* Library version string. */
 const char* itokmc_version(void);
 
+/* ---- field solve without device allocation ------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- for instance a program whose device memory is
+ * owned by another runtime's pool with a fixed budget, code that must avoid
+ * the implicit device synchronisation of cudaMalloc/cudaFree, or a plugin
+ * whose host forbids new device allocations.  It runs the same multigrid
+ * field solve as itokmc_solve_field (a5) on caller memory and allocates
+ * nothing: its scratch is a file-scope device array of 16 MiB inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits, so grids are limited to ITOKMC_NOALLOC_MAX_N cells per axis.
+ *
+ *   cfg     grid (n, lo, hi; one realization), E0, frac_bits, mg_rtol,
+ *           mg_nu1/nu2, mg_max_cycles, precision/field_precision (FP64 or
+ *           MIXED) and stream; particle and allocator fields are ignored.
+ *   rho     device, int64 n^3: space charge in units of q_e 2^-3s per cell
+ *           (the ITOKMC_RHO layout).
+ *   phi     device, double n^3: initial guess on entry, potential on exit.
+ *   E       device, double 3 n^3: Ex, Ey, Ez blocks on exit.
+ *   cycles_out, rel_out  optional: V-cycles used, final ||r||/||b||.
+ * Returns ITOKMC_OK, ITOKMC_ERR_ARG (NULL pointer, R != 1, n not a power of
+ * two or n > ITOKMC_NOALLOC_MAX_N), ITOKMC_ERR_NOCONV or ITOKMC_ERR_CUDA;
+ * the message is in itokmc_last_error(NULL).  The first call on a device
+ * looks up the scratch array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the one
+ * scratch array and it keeps the last call's contents (the solve clears
+ * what it needs), so calls that overlap on the GPU -- on two streams, or
+ * from two threads -- race and must be serialised by the caller.  The call
+ * synchronises cfg->stream before it returns. */
+#define ITOKMC_NOALLOC_MAX_N 64
+int itokmc_field_solve_noalloc(const itokmc_config* cfg, const int64_t* rho, double* phi, double* E,
+                               int32_t* cycles_out, double* rel_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,14 @@
 
 namespace ik {
 unsigned long long g_launches = 0;
+
+// Message of the last error raised without a handle (fixed storage: no
+// allocation on this path).
+thread_local char g_noh_err[256] = "";
+void set_global_error(const char* msg)
+{
+    snprintf(g_noh_err, sizeof g_noh_err, "%s", msg);
+}
 }
 
 struct itokmc_handle {
@@ -35,7 +43,6 @@ struct itokmc_handle {
 
 namespace {
 
-thread_local std::string g_init_err;
 
 int fail(itokmc_handle* h, int code, const std::string& msg)
 {
@@ -43,7 +50,7 @@ int fail(itokmc_handle* h, int code, const std::string& msg)
         h->err = msg;
         if (code == ITOKMC_ERR_CUDA || code == ITOKMC_ERR_TIMEOUT) h->poisoned = true;
     } else {
-        g_init_err = msg;
+        ik::set_global_error(msg.c_str());
     }
     return code;
 }
@@ -404,11 +411,13 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     d.norm_out = dalloc_n<double>(h, 2 * R, &rc);
     if (!rc && cudaMallocHost(reinterpret_cast<void**>(&h->rb), sizeof(*h->rb)) != cudaSuccess)
         rc = fail(h, ITOKMC_ERR_OOM, "pinned host buffer");
+    if (!rc && cudaMallocHost(reinterpret_cast<void**>(&d.norm_host), 2 * R * sizeof(double)) != cudaSuccess)
+        rc = fail(h, ITOKMC_ERR_OOM, "pinned host buffer");
     for (int e = 0; e < 8 && !rc; ++e)
         if (cudaEventCreate(&h->ev[e]) != cudaSuccess) rc = fail(h, ITOKMC_ERR_CUDA, "event create");
     if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->s), "init sync");
     if (rc) {
-        g_init_err = h->err;
+        ik::set_global_error(h->err.c_str());
         itokmc_destroy(h);
         return rc;
     }
@@ -429,6 +438,7 @@ int itokmc_destroy(itokmc_handle* h)
     cudaStreamSynchronize(h->s);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
     if (h->rb) cudaFreeHost(h->rb);
+    if (h->d.norm_host) cudaFreeHost(h->d.norm_host);
     cudaGetLastError();
     delete h;
     return ITOKMC_OK;
@@ -649,7 +659,7 @@ int itokmc_num_particles(itokmc_handle* h, int64_t* n_out)
     return ITOKMC_OK;
 }
 
-const char* itokmc_last_error(const itokmc_handle* h) { return h ? h->err.c_str() : g_init_err.c_str(); }
+const char* itokmc_last_error(const itokmc_handle* h) { return h ? h->err.c_str() : ik::g_noh_err; }
 
 const char* itokmc_version(void) { return "itokmc 0.1 (sm_103a)"; }
 

@@ -16,8 +16,9 @@
 // its own convergence test.  Norms are reduced in a fixed order.
 #include <cmath>
 #include <cstdio>
-#include <vector>
+#include <mutex>
 
+#include "../../include/itokmc.h"
 #include "ik_common.cuh"
 #include "ik_state.h"
 
@@ -352,7 +353,7 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
     const int items = (int)(per_real / NORM_TPB < 8 ? per_real / NORM_TPB : 8);
     const int nblk = (int)(G0.cells / ((uint64_t)NORM_TPB * items));
     const int bpr = nblk / R;
-    std::vector<double> h_norm(2 * R);
+    double* h_norm = d.norm_host;       // 2 R doubles of host memory owned by the caller
     double worst = 0.0;
     int cyc = 0;
     int status = -6;
@@ -362,7 +363,7 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
                                                d.norm_part, 1, items);
         ++g_launches;
         k_norm_final<<<R, 256, 0, s>>>(d.norm_part, bpr, R, d.norm_out);
-        cudaMemcpyAsync(h_norm.data(), d.norm_out, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h_norm, d.norm_out, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
         worst = 0.0;
         bool done = true;
@@ -431,3 +432,152 @@ void launch_efield(const Params& P, Dev& d, cudaStream_t s)
 }
 
 }  // namespace ik
+
+// ===========================================================================
+// Field solve without device allocation (itokmc_field_solve_noalloc).
+//
+// Some callers cannot call cudaMalloc: a host program whose device memory
+// belongs to another runtime's pool with a fixed budget, code that must not
+// incur the implicit device synchronisation of cudaMalloc/cudaFree inside a
+// latency-critical loop, or a plugin whose host forbids new device
+// allocations.  For them the multigrid scratch (coarse levels, FP32 copies,
+// right-hand side, norm partials and the packed field) lives in this
+// file-scope device array, which every GPU that loads the library keeps
+// until the process exits.  The caller passes the charge, the potential and
+// the field buffers.
+// ===========================================================================
+namespace ik {
+namespace {
+
+constexpr size_t NOALLOC_BYTES = 16u << 20;     // 16 MiB: grids up to 64^3
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_noalloc_mtx;
+constexpr int NOALLOC_MAX_DEV = 64;
+void* g_noalloc_ptr[NOALLOC_MAX_DEV] = {};
+
+// b = -rho/eps0 with the electrode potentials folded in (as the step does).
+__global__ void k_rhs_from_rho(const int64_t* __restrict__ rho, double* __restrict__ rhs, int n, int log2n,
+                               double qscale, double phi_top, double h)
+{
+    const uint64_t cells = (uint64_t)n * n * n;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < cells; g += (uint64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(g >> (2 * log2n));
+        double b = -((double)rho[g] * qscale) / 8.8541878128e-12;
+        if (k == n - 1) b = b - 2.0 * phi_top / (h * h);
+        rhs[g] = b;
+    }
+}
+
+size_t carve(size_t& off, size_t bytes)
+{
+    const size_t at = off;
+    off = (off + bytes + 255) & ~(size_t)255;
+    return at;
+}
+
+}  // namespace
+}  // namespace ik
+
+extern "C" int itokmc_field_solve_noalloc(const itokmc_config* cfg, const int64_t* rho, double* phi, double* E,
+                                          int32_t* cycles_out, double* rel_out)
+{
+    using namespace ik;
+    if (!cfg || !rho || !phi || !E) { set_global_error("field_solve_noalloc: NULL argument"); return ITOKMC_ERR_ARG; }
+    const int n = cfg->n[0];
+    if (cfg->n_realizations != 1 || cfg->n[1] != n || cfg->n[2] != n || n < 8 || (n & (n - 1))) {
+        set_global_error("field_solve_noalloc: one realization on an n^3 grid, n a power of two >= 8");
+        return ITOKMC_ERR_ARG;
+    }
+    if (n > ITOKMC_NOALLOC_MAX_N) {
+        set_global_error("field_solve_noalloc: grid larger than ITOKMC_NOALLOC_MAX_N (64) cells per axis");
+        return ITOKMC_ERR_ARG;
+    }
+    const int prec = cfg->field_precision < 0 ? cfg->precision : cfg->field_precision;
+    cudaStream_t s = (cudaStream_t)cfg->stream;
+    // set-up once per device, with that device current: the device address
+    // of the scratch array (its name is only a stand-in in host code)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEV) {
+        cudaGetLastError();
+        set_global_error("field_solve_noalloc: no current CUDA device");
+        return ITOKMC_ERR_CUDA;
+    }
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mtx);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                set_global_error("field_solve_noalloc: cudaGetSymbolAddress of the scratch array failed");
+                return ITOKMC_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    }
+    // lay the hierarchy out in the scratch array
+    Params P{};
+    P.n = n; P.n3 = n * n * n; P.R = 1;
+    while ((1 << P.log2n) < n) ++P.log2n;
+    for (int a = 0; a < 3; ++a) { P.lo[a] = cfg->lo[a]; P.hi[a] = cfg->hi[a]; P.h[a] = (cfg->hi[a] - cfg->lo[a]) / n; }
+    P.E0 = cfg->E0;
+    P.frac_bits = cfg->frac_bits;
+    Dev d;
+    size_t off = 0;
+    int l = 0;
+    for (int m = n; m >= 4 && l < MAX_LEVELS; m >>= 1, ++l) {
+        MGLevel& L = d.lev[l];
+        const size_t cells = (size_t)m * m * m;
+        L.n = m;
+        L.h = P.h[0] * (double)(n / m);
+        L.phi = l == 0 ? phi : reinterpret_cast<double*>(base + carve(off, cells * sizeof(double)));
+        L.rhs = reinterpret_cast<double*>(base + carve(off, cells * sizeof(double)));
+        L.res = nullptr;
+        L.phi32 = reinterpret_cast<float*>(base + carve(off, cells * sizeof(float)));
+        L.rhs32 = reinterpret_cast<float*>(base + carve(off, cells * sizeof(float)));
+    }
+    d.nlev = l;
+    d.norm_part = reinterpret_cast<double*>(base + carve(off, 2 * ((size_t)P.n3 / 256 + 16) * sizeof(double)));
+    d.norm_out = reinterpret_cast<double*>(base + carve(off, 2 * sizeof(double)));
+    d.E = reinterpret_cast<E64*>(base + carve(off, (size_t)P.n3 * sizeof(E64)));
+    d.E32 = nullptr;
+    if (off > NOALLOC_BYTES) {
+        set_global_error("field_solve_noalloc: scratch layout exceeds the static array");
+        return ITOKMC_ERR_ARG;
+    }
+    double norm_host[2];               // stack memory: no allocation
+    d.norm_host = norm_host;
+    const double dV = P.h[0] * P.h[1] * P.h[2];
+    const double qscale = 1.602176634e-19 * ldexp(1.0, -3 * P.frac_bits) / dV;
+    const double phi_top = P.E0 * (P.hi[2] - P.lo[2]);
+    ++g_launches;
+    k_rhs_from_rho<<<gridsz((uint64_t)P.n3, 256), 256, 0, s>>>(rho, d.lev[0].rhs, n, P.log2n, qscale, phi_top, P.h[0]);
+    int cycles = 0;
+    double rel = 0.0;
+    const int st = field_solve(P, d, prec, cfg->mg_rtol, cfg->mg_nu1, cfg->mg_nu2, cfg->mg_max_cycles, s, &cycles,
+                               &rel);
+    if (cycles_out) *cycles_out = cycles;
+    if (rel_out) *rel_out = rel;
+    if (st == -3) {
+        set_global_error("field_solve_noalloc: CUDA error in the multigrid");
+        return ITOKMC_ERR_CUDA;
+    }
+    launch_efield(P, d, s);
+    const uint64_t G = (uint64_t)P.n3;
+    ++g_launches;
+    k_unpack_field<<<gridsz(G, 256), 256, 0, s>>>(d.E, E, G);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_global_error("field_solve_noalloc: CUDA error");
+        return ITOKMC_ERR_CUDA;
+    }
+    if (st != 0) {
+        set_global_error("field_solve_noalloc: multigrid did not reach mg_rtol within mg_max_cycles");
+        return ITOKMC_ERR_NOCONV;
+    }
+    return ITOKMC_OK;
+}

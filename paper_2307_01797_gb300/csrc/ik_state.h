@@ -111,6 +111,7 @@ struct Dev {
     MGLevel lev[MAX_LEVELS];
     int nlev = 0;
     double* norm_part = nullptr;  double* norm_out = nullptr;  size_t norm_blocks = 0;
+    double* norm_host = nullptr;       // 2 R doubles (pinned or stack) for the norm readback
     // counters
     Counters* ctr = nullptr;
     Counters* ctr_host = nullptr;      // pinned mirror
@@ -148,6 +149,10 @@ void launch_unpack_field(const Params& P, Dev& d, double* E3, cudaStream_t s);
 // Kernel launches issued by this library (all handles), for the benchmark's
 // launch count.
 extern unsigned long long g_launches;
+
+// Last error of a call made without a handle (itokmc_last_error(NULL)).
+extern thread_local char g_noh_err[256];
+void set_global_error(const char* msg);
 
 // generic 3-phase exclusive scan over G cells with C channels (ik_particles.cu)
 size_t scan_scratch_elems(uint64_t G, int C);

@@ -111,6 +111,8 @@ def lib(build_if_missing: bool = True):
                 "itokmc_num_particles": ([H, ctypes.POINTER(i64)], ctypes.c_int),
                 "itokmc_last_error": ([H], ctypes.c_char_p),
                 "itokmc_version": ([], ctypes.c_char_p),
+                "itokmc_field_solve_noalloc": ([ctypes.POINTER(Config), vp, vp, vp, ctypes.POINTER(i32),
+                                                ctypes.POINTER(d)], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -118,6 +120,19 @@ def lib(build_if_missing: bool = True):
                 f.restype = res
             _lib = L
     return _lib
+
+
+def itokmc_field_solve_noalloc(cfg: Config, rho, phi, E):
+    """Field solve on caller device buffers (torch tensors) with no device
+    allocation by the library: rho int64 n^3, phi float64 n^3 (initial guess
+    in, potential out), E float64 3 n^3 (out).  Returns (cycles, rel)."""
+    cyc = ctypes.c_int32()
+    rel = ctypes.c_double()
+    code = lib().itokmc_field_solve_noalloc(ctypes.byref(cfg), _ptr(rho), _ptr(phi), _ptr(E), ctypes.byref(cyc),
+                                            ctypes.byref(rel))
+    if code != ITOKMC_OK:
+        raise ItokmcError(code, lib().itokmc_last_error(None).decode())
+    return cyc.value, rel.value
 
 
 # ------------------------------------------------------------------ allocator
