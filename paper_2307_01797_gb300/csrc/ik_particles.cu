@@ -104,6 +104,127 @@ __device__ __forceinline__ void deposit_f64(const Params& P, unsigned long long*
 
 __device__ __forceinline__ int real_of(const Params& P, uint32_t g) { return (int)(g >> (3 * P.log2n)); }
 
+// CIC stencil of one particle in fixed point: folded indices and axis
+// weights (2^s - a, a).
+struct Stencil {
+    int ia[3], ib[3];
+    long long A[3][2];
+};
+
+__device__ __forceinline__ void stencil_f64(const Params& P, const double X[3], Stencil& S)
+{
+    const long long one = 1ll << P.frac_bits;
+    const double scale = (double)one;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double f;
+        cic_axis(X[a], P.lo[a], P.h[a], P.n, S.ia[a], S.ib[a], f);
+        const long long q = (long long)floor(f * scale);
+        S.A[a][0] = one - q;
+        S.A[a][1] = q;
+    }
+}
+
+__device__ __forceinline__ void stencil_f32(const Params& P, const int id[3], const float o[3], Stencil& S)
+{
+    const int one = 1 << P.frac_bits, half = one >> 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int q = (int)floorf(o[a] * (float)one);   // exact: o in [0,1), power-of-two scale
+        const int aa = (q + half) & (one - 1);
+        const int i0 = id[a] - 1 + (q >= half ? 1 : 0);
+        S.ia[a] = clampi(i0, P.n);
+        S.ib[a] = clampi(i0 + 1, P.n);
+        S.A[a][0] = one - aa;
+        S.A[a][1] = aa;
+    }
+}
+
+constexpr int DEP_WIN = 2048;   // cells of the block's shared deposit window (16 KB)
+
+// Deposits the 8 fixed-point CIC contributions of every alive particle of the
+// block.  The cells the block touches usually form a small box (particles are
+// sorted by cell), so the contributions are first summed in a shared-memory
+// window over that box and flushed with one global atomic per touched cell;
+// blocks whose box is too large or spans realizations add directly.  Integer
+// sums: the result does not depend on the order.  All threads of the block
+// must call this.
+__device__ __forceinline__ void block_deposit(const Params& P, unsigned long long* __restrict__ ne, bool alive, int r,
+                                              const Stencil& S, uint32_t w)
+{
+    __shared__ unsigned long long win[DEP_WIN];
+    __shared__ int wred[TPB / 32][8];
+    __shared__ int wfin[8];
+    const int BIG = 0x7fffffff;
+    int v[8];
+    if (alive) {
+        v[0] = S.ia[0]; v[1] = S.ia[1]; v[2] = S.ia[2];
+        v[3] = -S.ib[0]; v[4] = -S.ib[1]; v[5] = -S.ib[2];
+        v[6] = r; v[7] = -r;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = BIG;
+    }
+    const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __reduce_min_sync(0xffffffffu, v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) wred[wid][k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        int m = BIG;
+        for (int q = 0; q < TPB / 32; ++q) m = min(m, wred[q][threadIdx.x]);
+        wfin[threadIdx.x] = m;
+    }
+    __syncthreads();
+    if (wfin[0] == BIG) return;                       // no alive particle in the block
+    const int lo0 = wfin[0], lo1 = wfin[1], lo2 = wfin[2];
+    const int e0 = -wfin[3] - lo0 + 1, e1 = -wfin[4] - lo1 + 1, e2 = -wfin[5] - lo2 + 1;
+    const long long V = (long long)e0 * e1 * e2;
+    const bool use = wfin[6] == -wfin[7] && V <= DEP_WIN;
+    const int ix[2] = { S.ia[0], S.ib[0] }, iy[2] = { S.ia[1], S.ib[1] }, iz[2] = { S.ia[2], S.ib[2] };
+    if (!use) {
+        if (alive) {
+            unsigned long long* base = ne + (size_t)r * P.n3;
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
+                        const long long val = (long long)w * S.A[0][a] * S.A[1][b] * S.A[2][c];
+                        if (val) atomicAdd(base + ((size_t)iz[c] * P.n + iy[b]) * P.n + ix[a], (unsigned long long)val);
+                    }
+        }
+        return;
+    }
+    for (int t = threadIdx.x; t < (int)V; t += TPB) win[t] = 0ull;
+    __syncthreads();
+    if (alive) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const long long val = (long long)w * S.A[0][a] * S.A[1][b] * S.A[2][c];
+                    if (val) atomicAdd(&win[((iz[c] - lo2) * e1 + (iy[b] - lo1)) * e0 + (ix[a] - lo0)],
+                                       (unsigned long long)val);
+                }
+    }
+    __syncthreads();
+    unsigned long long* base = ne + (size_t)wfin[6] * P.n3;
+    for (int t = threadIdx.x; t < (int)V; t += TPB) {
+        const unsigned long long val = win[t];
+        if (val) {
+            const int x = t % e0, y = (t / e0) % e1, z = t / (e0 * e1);
+            atomicAdd(base + ((size_t)(z + lo2) * P.n + (y + lo1)) * P.n + (x + lo0), val);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ pass 1
 __global__ void __launch_bounds__(TPB) k_push_f64(
     Params P, const P64* __restrict__ A, P64* __restrict__ B, uint32_t* __restrict__ keyB, uint32_t N,
@@ -115,10 +236,13 @@ __global__ void __launch_bounds__(TPB) k_push_f64(
     const uint32_t i = blockIdx.x * TPB + threadIdx.x;
     bool alive = false, mover = false;
     uint32_t gnew = 0, w = 0;
+    int rr = 0;
+    Stencil S;
     if (i < N) {
         const P64 p = ld_p64(A + i);
         const uint32_t gold = p.cell;
         const int r = real_of(P, gold);
+        rr = r;
         const uint32_t idx = i - cell_start[(size_t)r * P.n3];
         const size_t ebase = (size_t)r * P.n3;
         w = p.w;
@@ -151,7 +275,7 @@ __global__ void __launch_bounds__(TPB) k_push_f64(
             mover = gnew != gold;
             q.cell = gnew;
             keyB[i] = gnew | (mover ? KEY_MOVER : 0u);
-            deposit_f64(P, ne_fix + ebase, Xn, w);
+            stencil_f64(P, Xn, S);
             if (mover) {
                 atomicAdd(in_cnt + gnew, 1);
                 if (gold < gnew) atomicAdd(in_before + gnew, 1);
@@ -166,6 +290,7 @@ __global__ void __launch_bounds__(TPB) k_push_f64(
         }
         st_p64(B + i, q);
     }
+    block_deposit(P, ne_fix, alive, rr, S, w);
     unsigned long long v = alive ? (unsigned long long)w : 0ull;
     unsigned c = alive ? 1u : 0u;
     if (warp_run_sum(gnew, alive, v, c)) {
@@ -328,62 +453,123 @@ __global__ void k_rho(Params P, const int64_t* __restrict__ Npos, const int64_t*
 
 // ------------------------------------------------------------------ KMC
 // Sec. 3.2.3 for the network {e -> 2e + M+, e -> M-, e -> e + gamma}; the
-// SSA switch is tested before the critical draw (Cao et al. 2006).
-__device__ int kmc_cell(const Params& P, Stream& s, long long X0, const double kr[3], long long fired[3])
+// SSA switch is tested before the critical draw (Cao et al. 2006).  T is the
+// arithmetic of the propensities, times and leaps: double (FP64 form, the
+// oracle's operations) or float (mixed form; a float uniform is the top 23
+// bits of the same stream's FP64 uniform, so both forms draw common random
+// numbers; Poisson means at or above 2^22 are drawn in FP64).
+template <class T> struct KT;
+template <> struct KT<double> {
+    static __device__ __forceinline__ double uni(Stream& s) { return s.uniform(); }
+    static __device__ __forceinline__ double lg(double x) { return dlog(x); }
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+    static __device__ __forceinline__ long long poisson(Stream& s, double mu) { return dpoisson(s, mu); }
+};
+template <> struct KT<float> {
+    static __device__ __forceinline__ float uni(Stream& s)
+    {
+        const uint32_t a = s.u32();
+        (void)s.u32();
+        return uniform_f32(a);
+    }
+    static __device__ __forceinline__ float lg(float x) { return logf(x); }
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+    static __device__ long long poisson(Stream& s, float mu);
+};
+
+// FP32 Poisson: inversion below 10, PTRS (Hoermann 1993) up to 2^22, FP64 above.
+__device__ long long KT<float>::poisson(Stream& s, float mu)
 {
+    if (!(mu > 0.0f)) return 0;
+    if (mu >= 4194304.0f) return dpoisson(s, (double)mu);
+    if (mu < 10.0f) {
+        const float u = uni(s);
+        float p = expf(-mu);
+        float F = p;
+        long long k = 0;
+        while (u > F && k < 200) {
+            k += 1;
+            p = (p * mu) / (float)k;
+            F = F + p;
+        }
+        return k;
+    }
+    const float slam = sqrtf(mu);
+    const float loglam = logf(mu);
+    const float b = 0.931f + 2.53f * slam;
+    const float a = -0.059f + 0.02483f * b;
+    const float invalpha = 1.1239f + 1.1328f / (b - 3.4f);
+    const float vr = 0.9277f - 3.6224f / (b - 2.0f);
+    for (int it = 0; it < 1000000; ++it) {
+        const float U = uni(s) - 0.5f;
+        const float V = uni(s);
+        const float us = 0.5f - fabsf(U);
+        const float kd = floorf(((((2.0f * a) / us) + b) * U + mu) + 0.43f);
+        if (us >= 0.07f && V <= vr) return (long long)kd;
+        if (kd < 0.0f || (us < 0.013f && V > us)) continue;
+        const float lhs = (logf(V) + logf(invalpha)) - logf((a / (us * us)) + b);
+        const float rhs = ((-mu) + kd * loglam) - lgammaf(kd + 1.0f);
+        if (lhs <= rhs) return (long long)kd;
+    }
+    return -1;
+}
+
+template <class T>
+__device__ int kmc_cell(const Params& P, Stream& s, long long X0, const T kr[3], long long fired[3])
+{
+    using K = KT<T>;
     const int nu[3] = { +1, -1, 0 };
     long long X = X0;
-    const double dt = P.dt;
-    double tau = 0.0;
+    const T dt = (T)P.dt;
+    T tau = (T)0;
     fired[0] = fired[1] = fired[2] = 0;
     for (int guard = 0; guard < 100000; ++guard) {
         if (!(tau < dt)) return 0;
-        const double xd = (double)X;
-        const double a[3] = { kr[0] * xd, kr[1] * xd, kr[2] * xd };
-        const double A = (a[0] + a[1]) + a[2];
-        if (!(A > 0.0)) return 0;
+        const T xd = (T)X;
+        const T a[3] = { kr[0] * xd, kr[1] * xd, kr[2] * xd };
+        const T A = (a[0] + a[1]) + a[2];
+        if (!(A > (T)0)) return 0;
         const bool crit[3] = { false, X < (long long)P.n_crit, false };
-        double Ac = 0.0;
+        T Ac = (T)0;
         for (int r = 0; r < 3; ++r) if (crit[r]) Ac = Ac + a[r];
-        double dtnc = __longlong_as_double(0x7ff0000000000000ll);
+        T dtnc = K::inf();
         if (!isinf(P.eps)) {
-            double xi = 0.0, sig2 = 0.0;
+            T xi = (T)0, sig2 = (T)0;
             bool any = false;
             for (int r = 0; r < 3; ++r) {
                 if (crit[r]) continue;
                 any = true;
-                xi = xi + (double)nu[r] * a[r];
-                sig2 = sig2 + (double)(nu[r] * nu[r]) * a[r];
+                xi = xi + (T)nu[r] * a[r];
+                sig2 = sig2 + (T)(nu[r] * nu[r]) * a[r];
             }
             if (any) {
-                double num = P.eps * xd;
-                if (num < 1.0) num = 1.0;
-                const double inf = __longlong_as_double(0x7ff0000000000000ll);
-                const double t1 = (xi != 0.0) ? num / fabs(xi) : inf;
-                const double t2 = (sig2 != 0.0) ? (num * num) / sig2 : inf;
+                T num = (T)P.eps * xd;
+                if (num < (T)1) num = (T)1;
+                const T t1 = (xi != (T)0) ? num / (xi < (T)0 ? -xi : xi) : K::inf();
+                const T t2 = (sig2 != (T)0) ? (num * num) / sig2 : K::inf();
                 dtnc = t1 < t2 ? t1 : t2;
             }
         }
-        double dtc = -1.0;
+        T dtc = (T)-1;
         bool accepted = false;
         for (int rej = 0; rej < 10000 && !accepted; ++rej) {
-            const double rem = dt - tau;
-            double dtau = dtnc < rem ? dtnc : rem;
+            const T rem = dt - tau;
+            T dtau = dtnc < rem ? dtnc : rem;
             long long k[3] = { 0, 0, 0 };
-            double adv;
-            if (A * dtau <= 1.0) {
+            T adv;
+            if (A * dtau <= (T)1) {
                 long long Xs = X;
-                double t = 0.0;
+                T t = (T)0;
                 for (int ev = 0; ev < P.n_ssa; ++ev) {
-                    const double xs = (double)Xs;
-                    const double as[3] = { kr[0] * xs, kr[1] * xs, kr[2] * xs };
-                    const double As = (as[0] + as[1]) + as[2];
-                    if (!(As > 0.0)) { t = dtau; break; }
-                    const double dte = (-dlog(s.uniform())) / As;
+                    const T xs = (T)Xs;
+                    const T as[3] = { kr[0] * xs, kr[1] * xs, kr[2] * xs };
+                    const T As = (as[0] + as[1]) + as[2];
+                    if (!(As > (T)0)) { t = dtau; break; }
+                    const T dte = (-K::lg(K::uni(s))) / As;
                     if (t + dte > dtau) { t = dtau; break; }
                     t = t + dte;
-                    const double target = s.uniform() * As;
-                    double cum = 0.0;
+                    const T target = K::uni(s) * As;
+                    T cum = (T)0;
                     int j = 2;
                     for (int r = 0; r < 3; ++r) {
                         cum = cum + as[r];
@@ -394,12 +580,11 @@ __device__ int kmc_cell(const Params& P, Stream& s, long long X0, const double k
                 }
                 adv = t;
             } else {
-                if (dtc < 0.0)
-                    dtc = (Ac > 0.0) ? (-dlog(s.uniform())) / Ac : __longlong_as_double(0x7ff0000000000000ll);
+                if (dtc < (T)0) dtc = (Ac > (T)0) ? (-K::lg(K::uni(s))) / Ac : K::inf();
                 if (dtc < dtnc && dtc < rem) {
                     dtau = dtc;
-                    const double target = s.uniform() * Ac;
-                    double cum = 0.0;
+                    const T target = K::uni(s) * Ac;
+                    T cum = (T)0;
                     int rc = -1, last = -1;
                     for (int r = 0; r < 3; ++r) {
                         if (!crit[r]) continue;
@@ -412,7 +597,7 @@ __device__ int kmc_cell(const Params& P, Stream& s, long long X0, const double k
                 }
                 for (int r = 0; r < 3; ++r) {
                     if (crit[r]) continue;
-                    const long long kk = dpoisson(s, a[r] * dtau);
+                    const long long kk = K::poisson(s, a[r] * dtau);
                     if (kk < 0) return -1;
                     k[r] += kk;
                 }
@@ -420,7 +605,7 @@ __device__ int kmc_cell(const Params& P, Stream& s, long long X0, const double k
             }
             const long long Xn = X + k[0] - k[1];
             if (Xn < 0) {
-                dtnc = dtau * 0.5;
+                dtnc = dtau * (T)0.5;
                 continue;
             }
             X = Xn;
@@ -433,26 +618,37 @@ __device__ int kmc_cell(const Params& P, Stream& s, long long X0, const double k
     return -1;
 }
 
+template <class T>
 __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const E64* __restrict__ E,
-                      int64_t* __restrict__ fired, int64_t* __restrict__ Npos, int64_t* __restrict__ Nneg,
-                      uint64_t G, uint32_t* __restrict__ pc_list, Counters* __restrict__ ctr)
+                      const float4* __restrict__ E32, int64_t* __restrict__ fired, int64_t* __restrict__ Npos,
+                      int64_t* __restrict__ Nneg, uint64_t G, uint32_t* __restrict__ pc_list,
+                      Counters* __restrict__ ctr)
 {
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
         long long f[3] = { 0, 0, 0 };
         const long long X0 = (long long)Xe[g];
         if (X0 > 0) {
-            const E64 e = ld_e64(E + g);
-            const double Em = e.m;
-            const double ve = P.mu * Em;
-            const double alpha = (Em > 0.0) ? P.alpha_A * dexp(-(P.alpha_B / Em)) : 0.0;
-            double kr[3];
-            kr[0] = alpha * ve;
-            kr[1] = P.eta * ve;
-            kr[2] = P.photon_ratio * kr[0];
+            T kr[3];
+            if constexpr (sizeof(T) == 8) {
+                const E64 e = ld_e64(E + g);
+                const double Em = e.m;
+                const double ve = P.mu * Em;
+                const double alpha = (Em > 0.0) ? P.alpha_A * dexp(-(P.alpha_B / Em)) : 0.0;
+                kr[0] = alpha * ve;
+                kr[1] = P.eta * ve;
+                kr[2] = P.photon_ratio * kr[0];
+            } else {
+                const float Em = __ldg(E32 + g).w;
+                const float ve = (float)P.mu * Em;
+                const float alpha = (Em > 0.0f) ? (float)P.alpha_A * expf(-((float)P.alpha_B / Em)) : 0.0f;
+                kr[0] = alpha * ve;
+                kr[1] = (float)P.eta * ve;
+                kr[2] = (float)P.photon_ratio * kr[0];
+            }
             const int r = real_of(P, (uint32_t)g);
             const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
             Stream s(seed_of(P, r), c, P.step, TAG_KMC, 0);
-            if (kmc_cell(P, s, X0, kr, f) != 0) {
+            if (kmc_cell<T>(P, s, X0, kr, f) != 0) {
                 atomicOr(&ctr->err, DERR_KMC);
                 ctr->kmc_fail_cell = (unsigned)g;
             }
@@ -630,7 +826,7 @@ struct MergeScanOp {
     uint32_t* big_list;       // the others
     uint32_t* list_n;         // [2]: lengths
     uint64_t G;
-    int ppc, n_new;
+    int ppc, n_new, cap;
     __device__ void load(uint64_t g, long long v[5]) const
     {
         const long long dN = fired[g] - fired[G + g];
@@ -638,7 +834,7 @@ struct MergeScanOp {
         v[0] = W < ppc ? W : ppc;
         v[1] = photo_cnt[g];
         const long long M = (long long)(cs[g + 1] - cs[g]) + (dN > 0 ? (dN < n_new ? dN : n_new) : 0) + photo_cnt[g];
-        const bool big = M > 0 && M + ppc > MERGE_SMEM;
+        const bool big = M > 0 && M + ppc > cap;
         v[2] = big ? (M + ppc) : 0;
         v[3] = (v[0] > 0 && !big) ? 1 : 0;
         v[4] = (v[0] > 0 && big) ? 1 : 0;
@@ -662,6 +858,11 @@ struct MergeScanOp {
 };
 
 // ------------------------------------------------------------------ merge
+struct MP32 {         // merge work element (mixed form: cell offsets)
+    float x, y, z;
+    uint32_t w;
+};
+
 struct MP {           // merge work element (FP64 form)
     double x, y, z;
     uint32_t w;
@@ -669,6 +870,13 @@ struct MP {           // merge work element (FP64 form)
 };
 
 __device__ __forceinline__ double mp_coord(const MP& p, int a) { return a == 0 ? p.x : (a == 1 ? p.y : p.z); }
+__device__ __forceinline__ double mp_coord(const MP32& p, int a)
+{
+    return (double)(a == 0 ? p.x : (a == 1 ? p.y : p.z));
+}
+
+template <bool MX> struct MergeElem { using T = MP; static constexpr int CAP = 128; };
+template <> struct MergeElem<true> { using T = MP32; static constexpr int CAP = 256; };
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 {
@@ -691,8 +899,8 @@ __device__ __forceinline__ double warp_max(double v)
 
 // Splits node src[0..m) of weight W (>= 2) into dst: left part then right
 // part.  tmp holds the node sorted along the split axis.  Returns nl.
-__device__ uint32_t split_node(const MP* src, uint32_t m, unsigned long long W, MP* tmp, MP* dst,
-                               uint32_t* nr_out)
+template <class E>
+__device__ uint32_t split_node(const E* src, uint32_t m, unsigned long long W, E* tmp, E* dst, uint32_t* nr_out)
 {
     const unsigned lane = lane_id();
     // bounding box and axis (largest extent, ties to the lowest axis)
@@ -700,7 +908,7 @@ __device__ uint32_t split_node(const MP* src, uint32_t m, unsigned long long W, 
 #pragma unroll
     for (int a = 0; a < 3; ++a) { lo[a] = 1e300; hi[a] = -1e300; }
     for (uint32_t j = lane; j < m; j += 32) {
-        const MP p = src[j];
+        const E p = src[j];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const double v = mp_coord(p, a);
@@ -714,16 +922,42 @@ __device__ uint32_t split_node(const MP* src, uint32_t m, unsigned long long W, 
     int axis = 0;
     if (ext[1] > ext[axis]) axis = 1;
     if (ext[2] > ext[axis]) axis = 2;
-    // stable rank sort by (coordinate, list position)
-    for (uint32_t j = lane; j < m; j += 32) {
-        const MP pj = src[j];
-        const double cj = mp_coord(pj, axis);
-        uint32_t rank = 0;
+    // stable rank sort by (coordinate, list position): each lane keeps the
+    // keys of its elements j = lane + 32 q in registers and scans all k with
+    // broadcast loads
+    if (m <= 256) {
+        double cj[8];
+        uint32_t rk[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t j = lane + 32u * q;
+            cj[q] = j < m ? mp_coord(src[j], axis) : 0.0;
+            rk[q] = 0;
+        }
         for (uint32_t k = 0; k < m; ++k) {
             const double ck = mp_coord(src[k], axis);
-            rank += (ck < cj) || (ck == cj && k < j);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t j = lane + 32u * q;
+                rk[q] += (ck < cj[q]) || (ck == cj[q] && k < j);
+            }
         }
-        tmp[rank] = pj;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t j = lane + 32u * q;
+            if (j < m) tmp[rk[q]] = src[j];
+        }
+    } else {
+        for (uint32_t j = lane; j < m; j += 32) {
+            const E pj = src[j];
+            const double cj = mp_coord(pj, axis);
+            uint32_t rank = 0;
+            for (uint32_t k = 0; k < m; ++k) {
+                const double ck = mp_coord(src[k], axis);
+                rank += (ck < cj) || (ck == cj && k < j);
+            }
+            tmp[rank] = pj;
+        }
     }
     __syncwarp();
     // weighted median p': first index with 2 C_p > W
@@ -747,11 +981,11 @@ __device__ uint32_t split_node(const MP* src, uint32_t m, unsigned long long W, 
         }
         carry = __shfl_sync(0xffffffffu, Cj, 31);
     }
-    const MP med = tmp[pm];
+    const E med = tmp[pm];
     const unsigned long long WL = Cpm - med.w;
     const unsigned long long WR = W - Cpm;
     bool left_med, right_med;
-    MP ml = med, mr = med;
+    E ml = med, mr = med;
     if (med.w == 1) {
         left_med = WL <= WR;
         right_med = !left_med;
@@ -781,13 +1015,15 @@ __device__ uint32_t split_node(const MP* src, uint32_t m, unsigned long long W, 
 // One node per lane: stable insertion sort of the node's slice along its
 // widest axis (in place), weighted median, child sizes.  Returns the number
 // of output elements; nl_out receives the left child's size (0 = unsplit).
-__device__ __forceinline__ uint32_t lane_split_prepare(MP* node, uint32_t m, unsigned long long W, uint32_t& pm_out,
-                                                       MP& ml, MP& mr, uint32_t& nl_out, bool& lmed, bool& rmed)
+template <class E>
+__device__ __forceinline__ uint32_t lane_split_prepare(E* node, uint32_t m, unsigned long long W, uint32_t& pm_out,
+                                                       E& ml, E& mr, uint32_t& nl_out, bool& lmed, bool& rmed)
 {
-    double lo[3] = { node[0].x, node[0].y, node[0].z }, hi[3] = { node[0].x, node[0].y, node[0].z };
+    double lo[3] = { mp_coord(node[0], 0), mp_coord(node[0], 1), mp_coord(node[0], 2) };
+    double hi[3] = { lo[0], lo[1], lo[2] };
     for (uint32_t q = 1; q < m; ++q) {
-        const MP e = node[q];
-        const double v[3] = { e.x, e.y, e.z };
+        const E e = node[q];
+        const double v[3] = { mp_coord(e, 0), mp_coord(e, 1), mp_coord(e, 2) };
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             lo[a] = v[a] < lo[a] ? v[a] : lo[a];
@@ -799,7 +1035,7 @@ __device__ __forceinline__ uint32_t lane_split_prepare(MP* node, uint32_t m, uns
     if (ext[1] > ext[axis]) axis = 1;
     if (ext[2] > ext[axis]) axis = 2;
     for (uint32_t q = 1; q < m; ++q) {
-        const MP key = node[q];
+        const E key = node[q];
         const double c = mp_coord(key, axis);
         int p = (int)q - 1;
         while (p >= 0 && mp_coord(node[p], axis) > c) {
@@ -814,7 +1050,7 @@ __device__ __forceinline__ uint32_t lane_split_prepare(MP* node, uint32_t m, uns
         C += node[q].w;
         if (2ull * C > W) { pm = q; break; }
     }
-    const MP med = node[pm];
+    const E med = node[pm];
     const unsigned long long WL = C - med.w, WR = W - C;
     ml = med; mr = med;
     if (med.w == 1) {
@@ -839,12 +1075,15 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
     Params P, const P64* __restrict__ A, const P32* __restrict__ A32, const uint32_t* __restrict__ cs,
     const int64_t* __restrict__ fired, const Photo* __restrict__ photos, const uint32_t* __restrict__ photo_sorted,
     const uint32_t* __restrict__ photo_off, const uint32_t* __restrict__ out_start,
-    const uint64_t* __restrict__ work_off, MP* __restrict__ work, uint64_t work_cap, P64* __restrict__ out,
+    const uint64_t* __restrict__ work_off, typename MergeElem<MX>::T* __restrict__ work, uint64_t work_cap,
+    P64* __restrict__ out,
     P32* __restrict__ out32, uint32_t* __restrict__ cout, uint64_t G, uint32_t cap, uint32_t photo_cap,
     const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_n, Counters* __restrict__ ctr)
 {
+    using MPT = typename MergeElem<MX>::T;
+    constexpr int CAP = MergeElem<MX>::CAP;
     extern __shared__ unsigned char merge_smem[];
-    MP(*sbuf)[3][MERGE_SMEM] = reinterpret_cast<MP(*)[3][MERGE_SMEM]>(merge_smem);
+    MPT(*sbuf)[3][CAP] = reinterpret_cast<MPT(*)[3][CAP]>(merge_smem);
     __shared__ uint32_t sb[MERGE_WARPS][2][257];
     const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
     const uint64_t gw = (uint64_t)blockIdx.x * MERGE_WARPS + wid;
@@ -865,7 +1104,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                 if (lane == 0) atomicOr(&ctr->err, DERR_CAPACITY);
                 continue;
             }
-            MP *cur, *nxt, *tmp;
+            MPT *cur, *nxt, *tmp;
             if (SMALL) {
                 cur = sbuf[wid][0]; nxt = sbuf[wid][1]; tmp = sbuf[wid][2];
             } else {
@@ -874,7 +1113,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                     if (lane == 0) atomicOr(&ctr->err, DERR_CAPACITY);
                     continue;
                 }
-                MP* base = work + 3 * work_off[g];
+                MPT* base = work + 3 * work_off[g];
                 cur = base; nxt = base + S; tmp = base + 2 * S;
             }
             // gather: existing (w > 0, canonical order), then new particles in
@@ -882,7 +1121,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
             uint32_t M = 0;
             for (uint32_t b = e0; b < e1; b += 32) {
                 const uint32_t q = b + lane;
-                MP e;
+                MPT e;
                 bool ok = false;
                 if (q < e1) {
                     if constexpr (MX) {
@@ -890,9 +1129,8 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                         e.x = p.ox; e.y = p.oy; e.z = p.oz; e.w = p.w;
                     } else {
                         const P64 p = ld_p64(A + q);
-                        e.x = p.x; e.y = p.y; e.z = p.z; e.w = p.w;
+                        e.x = p.x; e.y = p.y; e.z = p.z; e.w = p.w; e.pad = 0;
                     }
-                    e.pad = 0;
                     ok = e.w > 0;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, ok);
@@ -914,7 +1152,9 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                     const Photo pk = photos[photo_sorted[p0 + k]];
                     rank += (pk.src < pj.src) || (pk.src == pj.src && pk.slot < pj.slot);
                 }
-                MP e; e.x = pj.x; e.y = pj.y; e.z = pj.z; e.w = pj.w; e.pad = 0;
+                MPT e;
+                e.x = pj.x; e.y = pj.y; e.z = pj.z; e.w = pj.w;
+                if constexpr (!MX) e.pad = 0;
                 cur[M + (rank < n_lt ? rank : rank + mprod)] = e;
             }
             if (mprod) {
@@ -923,7 +1163,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                                      (int)(c >> (2 * P.log2n)) };
                 for (uint32_t j = lane; j < mprod; j += 32) {
                     Stream s(seed_of(P, r), c, P.step, TAG_PRODUCT, j);
-                    MP e;
+                    MPT e;
                     double X[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
@@ -934,7 +1174,8 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                     e.x = X[0]; e.y = X[1]; e.z = X[2];
                     const long long wj = wq + (j == 0 ? rem : 0);
                     if (wj > 0xffffffffll) atomicOr(&ctr->err, DERR_OVERFLOW);
-                    e.w = (uint32_t)wj; e.pad = 0;
+                    e.w = (uint32_t)wj;
+                    if constexpr (!MX) e.pad = 0;
                     cur[M + n_lt + j] = e;
                 }
             }
@@ -957,7 +1198,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                         uint32_t s0 = 0, m = 0, outn = 0, pm = 0, nl = 0;
                         unsigned long long W = 0;
                         bool split = false, lmed = false, rmed = false;
-                        MP ml, mr;
+                        MPT ml, mr;
                         if (d < nnodes) {
                             s0 = bnd[d];
                             m = bnd[d + 1] - s0;
@@ -976,7 +1217,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                         const uint32_t off = fill + o - outn;
                         const int cidx = nn + (int)(ch - (d < nnodes ? (split ? 2u : 1u) : 0u));
                         if (d < nnodes) {
-                            MP* dst = nxt + off;
+                            MPT* dst = nxt + off;
                             if (split) {
                                 for (uint32_t q = 0; q < pm; ++q) dst[q] = cur[s0 + q];
                                 if (lmed) dst[pm] = ml;
@@ -994,7 +1235,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                         nn += (int)__shfl_sync(0xffffffffu, ch, 31);
                     }
                     __syncwarp();
-                    MP* t = cur; cur = nxt; nxt = t;
+                    MPT* t = cur; cur = nxt; nxt = t;
                     uint32_t* tb = bnd; bnd = bnd2; bnd2 = tb;
                     nnodes = nn;
                     __syncwarp();
@@ -1023,7 +1264,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                     }
                     __syncwarp();
                 }
-                MP* t = cur; cur = nxt; nxt = t;
+                MPT* t = cur; cur = nxt; nxt = t;
                 uint32_t* tb = bnd; bnd = bnd2; bnd2 = tb;
                 nnodes = nn;
                 __syncwarp();
@@ -1037,7 +1278,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                     double sx = 0.0, sy = 0.0, sz = 0.0;
                     unsigned long long Wl = 0;
                     for (uint32_t q = bnd[d]; q < bnd[d + 1]; ++q) {
-                        const MP e = cur[q];
+                        const MPT e = cur[q];
                         const double wd = (double)e.w;
                         sx = sx + wd * e.x;
                         sy = sy + wd * e.y;
@@ -1116,10 +1357,13 @@ __global__ void __launch_bounds__(TPB) k_push_f32(
     const uint32_t i = blockIdx.x * TPB + threadIdx.x;
     bool alive = false, mover = false;
     uint32_t gnew = 0, w = 0;
+    int rr = 0;
+    Stencil S;
     if (i < N) {
         const P32 p = A[i];
         const uint32_t gold = __ldg(cA + i);
         const int r = real_of(P, gold);
+        rr = r;
         const uint32_t c = gold & (uint32_t)(P.n3 - 1);
         const int id[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
                             (int)(c >> (2 * P.log2n)) };
@@ -1182,7 +1426,7 @@ __global__ void __launch_bounds__(TPB) k_push_f32(
             alive = true;
             mover = gnew != gold;
             keyB[i] = gnew | (mover ? KEY_MOVER : 0u);
-            deposit32(P, ne_fix + ebase, idn, on, w);
+            stencil_f32(P, idn, on, S);
             if (mover) {
                 atomicAdd(in_cnt + gnew, 1);
                 if (gold < gnew) atomicAdd(in_before + gnew, 1);
@@ -1195,6 +1439,7 @@ __global__ void __launch_bounds__(TPB) k_push_f32(
             atomicAdd(&ctr->outflow[r], (unsigned long long)w);
         }
     }
+    block_deposit(P, ne_fix, alive, rr, S, w);
     unsigned long long v = alive ? (unsigned long long)w : 0ull;
     unsigned cc = alive ? 1u : 0u;
     if (warp_run_sum(gnew, alive, v, cc)) {
@@ -1359,7 +1604,12 @@ void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 {
     ++g_launches;
-    k_kmc<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.fired, d.Npos, d.Nneg, G, d.pc_list, d.ctr);
+    if (d.mixed)
+        k_kmc<float><<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G,
+                                                              d.pc_list, d.ctr);
+    else
+        k_kmc<double><<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G,
+                                                               d.pc_list, d.ctr);
 }
 
 // Part a: loss removal, photons, merge scan (offsets, output count, work).
@@ -1378,7 +1628,8 @@ void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
                                             d.photo_cnt, d.photo_w, d.Npos, d.ctr);
     }
     MergeScanOp op{ d.Xe, d.fired, d.photo_w, d.photo_cnt, d.cell_start, d.out_start, d.photo_off, d.work_off,
-                    d.small_list, d.big_list, d.list_n, G, P.ppc, P.n_new };
+                    d.small_list, d.big_list, d.list_n, G, P.ppc, P.n_new,
+                    d.mixed ? MergeElem<true>::CAP : MergeElem<false>::CAP };
     run_scan<5>(op, G, d.scan_blk, s);
 }
 
@@ -1391,22 +1642,24 @@ void launch_particles_b(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
         k_photo_place<<<grid_for(d.photo_cap, 256, 1024), 256, 0, s>>>(d.photos, d.ctr, d.photo_cap, d.photo_off,
                                                                       d.photo_cursor, d.photo_sorted);
     }
-    const size_t smem = sizeof(MP) * 3 * MERGE_SMEM * MERGE_WARPS;
+    const size_t smem32 = sizeof(MP32) * 3 * MergeElem<true>::CAP * MERGE_WARPS;
+    const size_t smem64 = sizeof(MP) * 3 * MergeElem<false>::CAP * MERGE_WARPS;
+    const size_t smem = d.mixed ? smem32 : smem64;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_merge<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_merge<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_merge<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+        cudaFuncSetAttribute(k_merge<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
         attr_set = true;
     }
     g_launches += 2;
     if (d.mixed) {
         k_merge<true, true><<<152 * 2, MERGE_WARPS * 32, smem, s>>>(
             P, nullptr, d.rA32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
-            d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
+            d.work_off, reinterpret_cast<MP32*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
             d.photo_cap, d.small_list, d.list_n, d.ctr);
         k_merge<true, false><<<152 * 4, MERGE_WARPS * 32, 0, s>>>(
             P, nullptr, d.rA32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
-            d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
+            d.work_off, reinterpret_cast<MP32*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
             d.photo_cap, d.big_list, d.list_n, d.ctr);
         P32* t = d.rA32; d.rA32 = d.rB32; d.rB32 = t;
         uint32_t* tc = d.cellA32; d.cellA32 = d.cellB32; d.cellB32 = tc;
