@@ -369,8 +369,9 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     d.Npos = dalloc_n<int64_t>(h, G, &rc);
     d.Nneg = dalloc_n<int64_t>(h, G, &rc);
     d.rho = dalloc_n<int64_t>(h, G, &rc);
-    d.E = dalloc_n<ik::E64>(h, G, &rc);
-    d.E32 = dalloc_n<float4>(h, G, &rc);
+    // FP64 form: FP64 field (push, KMC); mixed form: FP32 field only
+    if (d.mixed) d.E32 = dalloc_n<float4>(h, G, &rc);
+    else d.E = dalloc_n<ik::E64>(h, G, &rc);
     d.fired = dalloc_n<int64_t>(h, 3 * G, &rc);
     d.stage = dalloc_n<double>(h, 3 * G, &rc);
     d.photos = dalloc_n<ik::Photo>(h, d.photo_cap, &rc);

@@ -250,9 +250,13 @@ __global__ void k_zero(T* __restrict__ a, uint64_t cells)
 }
 
 // E = -grad(phi) by centred differences with the boundary ghosts, and |E|.
+// FP64 form: everything in FP64 into E64.  Mixed form (E == nullptr): the
+// differences of neighbouring potentials in FP64 (they cancel most digits),
+// the scaling and |E| in FP32, into E32 only.
 __global__ void k_efield(const double* __restrict__ phi, E64* __restrict__ E, float4* __restrict__ E32, Geo G,
                          double h, double phi_top)
 {
+    const float inv2h = (float)(1.0 / (2.0 * h));
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G.cells; t += (uint64_t)gridDim.x * blockDim.x) {
         int r, k, j, i;
         decode(t, G.log2n, r, k, j, i);
@@ -262,11 +266,16 @@ __global__ void k_efield(const double* __restrict__ phi, E64* __restrict__ E, fl
         const double xm = i > 0 ? phi[t - 1] : c, xp = i < n - 1 ? phi[t + 1] : c;
         const double ym = j > 0 ? phi[t - sy] : c, yp = j < n - 1 ? phi[t + sy] : c;
         const double zm = k > 0 ? phi[t - sz] : -c, zp = k < n - 1 ? phi[t + sz] : 2.0 * phi_top - c;
-        const double ex = (xm - xp) / (2.0 * h), ey = (ym - yp) / (2.0 * h), ez = (zm - zp) / (2.0 * h);
-        const double m = sqrt((ex * ex + ey * ey) + ez * ez);
-        reinterpret_cast<double2*>(E + t)[0] = make_double2(ex, ey);
-        reinterpret_cast<double2*>(E + t)[1] = make_double2(ez, m);
-        if (E32) E32[t] = make_float4((float)ex, (float)ey, (float)ez, (float)m);
+        if (E) {
+            const double ex = (xm - xp) / (2.0 * h), ey = (ym - yp) / (2.0 * h), ez = (zm - zp) / (2.0 * h);
+            const double m = sqrt((ex * ex + ey * ey) + ez * ez);
+            reinterpret_cast<double2*>(E + t)[0] = make_double2(ex, ey);
+            reinterpret_cast<double2*>(E + t)[1] = make_double2(ez, m);
+            if (E32) E32[t] = make_float4((float)ex, (float)ey, (float)ez, (float)m);
+        } else {
+            const float ex = (float)(xm - xp) * inv2h, ey = (float)(ym - yp) * inv2h, ez = (float)(zm - zp) * inv2h;
+            E32[t] = make_float4(ex, ey, ez, sqrtf(ex * ex + ey * ey + ez * ez));
+        }
     }
 }
 
@@ -285,6 +294,109 @@ Geo geo(const Dev& d, int l, int R)
     g.R = R;
     g.cells = (uint64_t)R * g.n * g.n * g.n;
     return g;
+}
+
+// ---------------------------------------------------------------------------
+// The coarse end of the V-cycle (levels of at most 16^3 cells) in one launch:
+// one block per realization runs pre-smoothing, residual restriction, the
+// bottom sweeps, prolongation and post-smoothing level by level, with block
+// barriers between the phases (the arrays are tiny and stay in cache).
+constexpr int COARSE_N = 16;
+
+struct CoarseLevels {
+    int nlev;            // levels in the fused range, finest first
+    int n[MAX_LEVELS];
+    double h2[MAX_LEVELS];
+    void* phi[MAX_LEVELS];
+    void* rhs[MAX_LEVELS];
+};
+
+template <class T>
+__device__ void blk_smooth(T* phi, const T* rhs, int n, T h2, int color)
+{
+    const int half = n * n * n / 2;
+    for (int t = threadIdx.x; t < half; t += blockDim.x) {
+        const int ih = t % (n / 2), j = (t / (n / 2)) % n, k = t / (n * n / 2);
+        const int i = 2 * ih + ((j + k + color) & 1);
+        const uint64_t idx = ((uint64_t)k * n + j) * n + i;
+        int diag;
+        const T sum = nbr_sum(phi, idx, n, i, j, k, diag);
+        phi[idx] = (sum - h2 * rhs[idx]) / (T)diag;
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ void blk_resid_restrict(const T* phi, const T* rhs, T* rhs_c, int nf, T inv_h2)
+{
+    const int nc = nf / 2;
+    for (int t = threadIdx.x; t < nc * nc * nc; t += blockDim.x) {
+        const int I = t % nc, J = (t / nc) % nc, K = t / (nc * nc);
+        T acc = 0;
+        for (int c = 0; c < 8; ++c) {
+            const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
+            const uint64_t idx = ((uint64_t)k * nf + j) * nf + i;
+            int diag;
+            const T sum = nbr_sum(phi, idx, nf, i, j, k, diag);
+            acc += rhs[idx] - (sum - (T)diag * phi[idx]) * inv_h2;
+        }
+        rhs_c[t] = acc * (T)0.125;
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ void blk_prolong(T* phi_f, const T* e_c, int nf)
+{
+    const int nc = nf / 2;
+    for (int t = threadIdx.x; t < nf * nf * nf; t += blockDim.x) {
+        const int i = t % nf, j = (t / nf) % nf, k = t / (nf * nf);
+        const int I = i >> 1, J = j >> 1, K = k >> 1;
+        const int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1), K2 = K + ((k & 1) ? 1 : -1);
+        int ix[2] = { I, I2 }, iy[2] = { J, J2 }, iz[2] = { K, K2 };
+        T wz1 = (T)0.25;
+        if (I2 < 0 || I2 >= nc) ix[1] = I;
+        if (J2 < 0 || J2 >= nc) iy[1] = J;
+        if (K2 < 0 || K2 >= nc) { iz[1] = K; wz1 = (T)-0.25; }
+        const T wx[2] = { (T)0.75, (T)0.25 }, wy[2] = { (T)0.75, (T)0.25 }, wz[2] = { (T)0.75, wz1 };
+        T acc = 0;
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a)
+                    acc += wx[a] * wy[b] * wz[c] * e_c[((uint64_t)iz[c] * nc + iy[b]) * nc + ix[a]];
+        phi_f[t] += acc;
+    }
+    __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseLevels C, int nu1, int nu2, int bottom_sweeps)
+{
+    const int r = blockIdx.x;
+    auto PHI = [&](int l) { return reinterpret_cast<T*>(C.phi[l]) + (uint64_t)r * C.n[l] * C.n[l] * C.n[l]; };
+    auto RHS = [&](int l) { return reinterpret_cast<T*>(C.rhs[l]) + (uint64_t)r * C.n[l] * C.n[l] * C.n[l]; };
+    const int L = C.nlev - 1;
+    for (int l = 0; l < L; ++l) {
+        for (int it = 0; it < nu1; ++it) {
+            blk_smooth<T>(PHI(l), RHS(l), C.n[l], (T)C.h2[l], 0);
+            blk_smooth<T>(PHI(l), RHS(l), C.n[l], (T)C.h2[l], 1);
+        }
+        blk_resid_restrict<T>(PHI(l), RHS(l), RHS(l + 1), C.n[l], (T)(1.0 / C.h2[l]));
+        T* pc = PHI(l + 1);
+        for (int t = threadIdx.x; t < C.n[l + 1] * C.n[l + 1] * C.n[l + 1]; t += blockDim.x) pc[t] = (T)0;
+        __syncthreads();
+    }
+    for (int it = 0; it < bottom_sweeps; ++it) {
+        blk_smooth<T>(PHI(L), RHS(L), C.n[L], (T)C.h2[L], 0);
+        blk_smooth<T>(PHI(L), RHS(L), C.n[L], (T)C.h2[L], 1);
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        blk_prolong<T>(PHI(l), PHI(l + 1), C.n[l]);
+        for (int it = 0; it < nu2; ++it) {
+            blk_smooth<T>(PHI(l), RHS(l), C.n[l], (T)C.h2[l], 1);
+            blk_smooth<T>(PHI(l), RHS(l), C.n[l], (T)C.h2[l], 0);
+        }
+    }
 }
 
 template <class T>
@@ -308,6 +420,20 @@ void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
     const T h2 = (T)(L.h * L.h);
     T* phi = lphi<T>(L);
     T* rhs = lrhs<T>(L);
+    if (L.n <= COARSE_N && d.nlev - l >= 2) {
+        CoarseLevels C{};
+        C.nlev = d.nlev - l;
+        for (int q = 0; q < C.nlev; ++q) {
+            MGLevel& M = d.lev[l + q];
+            C.n[q] = M.n;
+            C.h2[q] = M.h * M.h;
+            C.phi[q] = lphi<T>(M);
+            C.rhs[q] = lrhs<T>(M);
+        }
+        ++g_launches;
+        k_vcycle_coarse<T><<<R, 1024, 0, s>>>(C, nu1, nu2, 48);
+        return;
+    }
     if (l == d.nlev - 1) {
         const int cells = G.n * G.n * G.n;
         const size_t sm = 2 * sizeof(T) * cells;
@@ -395,17 +521,26 @@ __global__ void k_pack_field(const double* __restrict__ E3, E64* __restrict__ E,
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G; t += (uint64_t)gridDim.x * blockDim.x) {
         const double ex = E3[t], ey = E3[G + t], ez = E3[2 * G + t];
         const double m = sqrt((ex * ex + ey * ey) + ez * ez);
-        reinterpret_cast<double2*>(E + t)[0] = make_double2(ex, ey);
-        reinterpret_cast<double2*>(E + t)[1] = make_double2(ez, m);
+        if (E) {
+            reinterpret_cast<double2*>(E + t)[0] = make_double2(ex, ey);
+            reinterpret_cast<double2*>(E + t)[1] = make_double2(ez, m);
+        }
         if (E32) E32[t] = make_float4((float)ex, (float)ey, (float)ez, (float)m);
     }
 }
 
-__global__ void k_unpack_field(const E64* __restrict__ E, double* __restrict__ E3, uint64_t G)
+// Field readback: from the FP64 field, or from the FP32 one (mixed form).
+__global__ void k_unpack_field(const E64* __restrict__ E, const float4* __restrict__ E32, double* __restrict__ E3,
+                               uint64_t G)
 {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G; t += (uint64_t)gridDim.x * blockDim.x) {
-        const E64 e = E[t];
-        E3[t] = e.x; E3[G + t] = e.y; E3[2 * G + t] = e.z;
+        if (E) {
+            const E64 e = E[t];
+            E3[t] = e.x; E3[G + t] = e.y; E3[2 * G + t] = e.z;
+        } else {
+            const float4 e = E32[t];
+            E3[t] = e.x; E3[G + t] = e.y; E3[2 * G + t] = e.z;
+        }
     }
 }
 
@@ -420,7 +555,7 @@ void launch_unpack_field(const Params& P, Dev& d, double* E3, cudaStream_t s)
 {
     const uint64_t G = (uint64_t)P.R * P.n3;
     ++g_launches;
-    k_unpack_field<<<gridsz(G, 256), 256, 0, s>>>(d.E, E3, G);
+    k_unpack_field<<<gridsz(G, 256), 256, 0, s>>>(d.E, d.E32, E3, G);
 }
 
 void launch_efield(const Params& P, Dev& d, cudaStream_t s)
@@ -568,7 +703,7 @@ extern "C" int itokmc_field_solve_noalloc(const itokmc_config* cfg, const int64_
     launch_efield(P, d, s);
     const uint64_t G = (uint64_t)P.n3;
     ++g_launches;
-    k_unpack_field<<<gridsz(G, 256), 256, 0, s>>>(d.E, E, G);
+    k_unpack_field<<<gridsz(G, 256), 256, 0, s>>>(d.E, nullptr, E, G);
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaGetLastError();

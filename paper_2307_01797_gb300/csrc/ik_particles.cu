@@ -104,6 +104,37 @@ __device__ __forceinline__ void deposit_f64(const Params& P, unsigned long long*
 
 __device__ __forceinline__ int real_of(const Params& P, uint32_t g) { return (int)(g >> (3 * P.log2n)); }
 
+// Sum over the warp, then one atomic by lane 0 (all lanes must call).
+__device__ __forceinline__ void warp_add(unsigned long long* dst, unsigned long long v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+// A slot in a shared counter for each calling lane: one atomic per group of
+// converged lanes.
+__device__ __forceinline__ unsigned long long warp_slot(unsigned long long* ctr)
+{
+    const unsigned mask = __activemask();
+    const int leader = __ffs(mask) - 1;
+    const unsigned lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+__device__ __forceinline__ unsigned warp_slot32(unsigned* ctr)
+{
+    const unsigned mask = __activemask();
+    const int leader = __ffs(mask) - 1;
+    const unsigned lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if ((int)lane == leader) base = atomicAdd(ctr, (unsigned)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
 // CIC stencil of one particle in fixed point: folded indices and axis
 // weights (2^s - a, a).
 struct Stencil {
@@ -279,7 +310,7 @@ __global__ void __launch_bounds__(TPB) k_push_f64(
             if (mover) {
                 atomicAdd(in_cnt + gnew, 1);
                 if (gold < gnew) atomicAdd(in_before + gnew, 1);
-                const unsigned long long slot = atomicAdd(&ctr->n_movers, 1ull);
+                const unsigned long long slot = warp_slot(&ctr->n_movers);
                 if (slot < mover_cap) movers[slot] = Mover{ gnew, i };
                 else atomicOr(&ctr->err, DERR_CAPACITY);
             }
@@ -434,7 +465,7 @@ __global__ void __launch_bounds__(TPB) k_deposit_f64(Params P, const P64* __rest
 // folded in (ghost 2 phi_b - phi_1 at z faces: -2 phi_b / h^2).
 __global__ void k_rho(Params P, const int64_t* __restrict__ Npos, const int64_t* __restrict__ Nneg,
                       const unsigned long long* __restrict__ ne_fix, int64_t* __restrict__ rho,
-                      double* __restrict__ rhs, uint64_t G, double qscale, double phi_top,
+                      double* __restrict__ rhs, uint64_t G, double qscale, double bc_top,
                       Counters* __restrict__ ctr)
 {
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
@@ -445,8 +476,8 @@ __global__ void k_rho(Params P, const int64_t* __restrict__ Npos, const int64_t*
         const long long rf = dq * (1ll << (3 * P.frac_bits)) - (long long)ne;
         rho[g] = rf;
         const int k = (int)((g >> (2 * P.log2n)) & (uint64_t)(P.n - 1));
-        double b = -((double)rf * qscale) / 8.8541878128e-12;
-        if (k == P.n - 1) b = b - 2.0 * phi_top / (P.h[2] * P.h[2]);
+        double b = -((double)rf * qscale);
+        if (k == P.n - 1) b = b - bc_top;
         rhs[g] = b;
     }
 }
@@ -455,7 +486,7 @@ __global__ void k_rho(Params P, const int64_t* __restrict__ Npos, const int64_t*
 // Sec. 3.2.3 for the network {e -> 2e + M+, e -> M-, e -> e + gamma}; the
 // SSA switch is tested before the critical draw (Cao et al. 2006).  T is the
 // arithmetic of the propensities, times and leaps: double (FP64 form, the
-// oracle's operations) or float (mixed form; a float uniform is the top 23
+// specification's operation order) or float (mixed form; a float uniform is the top 23
 // bits of the same stream's FP64 uniform, so both forms draw common random
 // numbers; Poisson means at or above 2^22 are drawn in FP64).
 template <class T> struct KT;
@@ -624,7 +655,12 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
                       int64_t* __restrict__ Nneg, uint64_t G, uint32_t* __restrict__ pc_list,
                       Counters* __restrict__ ctr)
 {
-    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
+    unsigned long long t_ion = 0, t_att = 0, t_ph = 0, t_slots = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t g0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t gend = ((G + stride - 1) / stride) * stride;   // whole warps iterate together
+    for (uint64_t g = g0; g < gend; g += stride) {
+        if (g >= G) continue;
         long long f[3] = { 0, 0, 0 };
         const long long X0 = (long long)Xe[g];
         if (X0 > 0) {
@@ -655,17 +691,21 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
             Npos[g] += f[0];
             Nneg[g] += f[1];
             if (f[2] > 0) {
-                atomicAdd(&ctr->photo_slots, (unsigned long long)(f[2] < P.n_new ? f[2] : P.n_new));
-                pc_list[atomicAdd(&ctr->n_photo_cells, 1u)] = (uint32_t)g;
+                t_slots += (unsigned long long)(f[2] < P.n_new ? f[2] : P.n_new);
+                pc_list[warp_slot32(&ctr->n_photo_cells)] = (uint32_t)g;
             }
-            atomicAdd(&ctr->ion, (unsigned long long)f[0]);
-            atomicAdd(&ctr->att, (unsigned long long)f[1]);
-            atomicAdd(&ctr->phot, (unsigned long long)f[2]);
+            t_ion += (unsigned long long)f[0];
+            t_att += (unsigned long long)f[1];
+            t_ph += (unsigned long long)f[2];
         }
         fired[g] = f[0];
         fired[G + g] = f[1];
         fired[2 * G + g] = f[2];
     }
+    warp_add(&ctr->ion, t_ion);
+    warp_add(&ctr->att, t_att);
+    warp_add(&ctr->phot, t_ph);
+    warp_add(&ctr->photo_slots, t_slots);
 }
 
 // ------------------------------------------------------------------ loss
@@ -685,6 +725,19 @@ __global__ void k_loss(Params P, uint32_t* __restrict__ wbase, int wstride, cons
         Stream s(seed_of(P, r), c, P.step, TAG_PRODUCT, (uint32_t)P.n_new);
         const uint32_t a = s.u32(), b = s.u32();
         const unsigned long long R = (((unsigned long long)a << 32) | b) % W;
+        if (W < (1ull << 32)) {
+            // C <= W and L <= W: C L + R < 2^64, the same quotients in 64 bits
+            unsigned long long C64 = 0;
+            for (uint32_t q = cs[g]; q < cs[g + 1]; ++q) {
+                uint32_t* wq = wbase + (size_t)q * wstride;
+                const uint32_t w = *wq;
+                const unsigned long long before = (C64 * L + R) / W;
+                C64 += w;
+                const unsigned long long after = (C64 * L + R) / W;
+                *wq = (uint32_t)(w - (after - before));
+            }
+            continue;
+        }
         unsigned __int128 C = 0;
         for (uint32_t q = cs[g]; q < cs[g + 1]; ++q) {
             const unsigned __int128 before = (C * L + R) / W;
@@ -737,6 +790,7 @@ __global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired
 {
     const unsigned lane = lane_id();
     const uint32_t ncells = ctr->n_photo_cells;
+    unsigned long long t_abs = 0;
     const double lnK = dlog(P.kappa_hi / P.kappa_lo);
     for (uint32_t e = (blockIdx.x * blockDim.x + threadIdx.x) / 32; e < ncells; e += (gridDim.x * blockDim.x) / 32) {
         const uint64_t g = pc_list[e];
@@ -770,8 +824,8 @@ __global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired
             atomicAdd((unsigned long long*)(Npos + gd), (unsigned long long)wj);
             atomicAdd(photo_cnt + gd, 1);
             atomicAdd(photo_w + gd, (unsigned long long)wj);
-            atomicAdd(&ctr->absorbed_w, (unsigned long long)wj);
-            const unsigned long long slot = atomicAdd(&ctr->n_photo, 1ull);
+            t_abs += (unsigned long long)wj;
+            const unsigned long long slot = warp_slot(&ctr->n_photo);
             if (slot < photo_cap) {
                 Photo ph;
                 if (mixed) {
@@ -790,6 +844,7 @@ __global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired
             }
         }
     }
+    warp_add(&ctr->absorbed_w, t_abs);
 }
 
 __global__ void k_photo_place(const Photo* __restrict__ photos, const Counters* __restrict__ ctr,
@@ -897,6 +952,36 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
+// Stable rank sort of m <= 32 NQ elements by (coordinate, position): each
+// lane keeps the keys of its elements j = lane + 32 q in registers and scans
+// all k with broadcast loads.
+template <class E, int NQ>
+__device__ __forceinline__ void rank_sort_reg(const E* src, uint32_t m, int axis, E* tmp)
+{
+    const unsigned lane = lane_id();
+    double cj[NQ];
+    uint32_t rk[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint32_t j = lane + 32u * q;
+        cj[q] = j < m ? mp_coord(src[j], axis) : 0.0;
+        rk[q] = 0;
+    }
+    for (uint32_t k = 0; k < m; ++k) {
+        const double ck = mp_coord(src[k], axis);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const uint32_t j = lane + 32u * q;
+            rk[q] += (ck < cj[q]) || (ck == cj[q] && k < j);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint32_t j = lane + 32u * q;
+        if (j < m) tmp[rk[q]] = src[j];
+    }
+}
+
 // Splits node src[0..m) of weight W (>= 2) into dst: left part then right
 // part.  tmp holds the node sorted along the split axis.  Returns nl.
 template <class E>
@@ -926,26 +1011,15 @@ __device__ uint32_t split_node(const E* src, uint32_t m, unsigned long long W, E
     // keys of its elements j = lane + 32 q in registers and scans all k with
     // broadcast loads
     if (m <= 256) {
-        double cj[8];
-        uint32_t rk[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t j = lane + 32u * q;
-            cj[q] = j < m ? mp_coord(src[j], axis) : 0.0;
-            rk[q] = 0;
-        }
-        for (uint32_t k = 0; k < m; ++k) {
-            const double ck = mp_coord(src[k], axis);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const uint32_t j = lane + 32u * q;
-                rk[q] += (ck < cj[q]) || (ck == cj[q] && k < j);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t j = lane + 32u * q;
-            if (j < m) tmp[rk[q]] = src[j];
+        switch ((m + 31) / 32) {
+        case 1: rank_sort_reg<E, 1>(src, m, axis, tmp); break;
+        case 2: rank_sort_reg<E, 2>(src, m, axis, tmp); break;
+        case 3: rank_sort_reg<E, 3>(src, m, axis, tmp); break;
+        case 4: rank_sort_reg<E, 4>(src, m, axis, tmp); break;
+        case 5: rank_sort_reg<E, 5>(src, m, axis, tmp); break;
+        case 6: rank_sort_reg<E, 6>(src, m, axis, tmp); break;
+        case 7: rank_sort_reg<E, 7>(src, m, axis, tmp); break;
+        default: rank_sort_reg<E, 8>(src, m, axis, tmp); break;
         }
     } else {
         for (uint32_t j = lane; j < m; j += 32) {
@@ -1430,7 +1504,7 @@ __global__ void __launch_bounds__(TPB) k_push_f32(
             if (mover) {
                 atomicAdd(in_cnt + gnew, 1);
                 if (gold < gnew) atomicAdd(in_before + gnew, 1);
-                const unsigned long long slot = atomicAdd(&ctr->n_movers, 1ull);
+                const unsigned long long slot = warp_slot(&ctr->n_movers);
                 if (slot < mover_cap) movers[slot] = Mover{ gnew, i };
                 else atomicOr(&ctr->err, DERR_CAPACITY);
             }
@@ -1594,10 +1668,11 @@ void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
 void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 {
     const double dV = P.h[0] * P.h[1] * P.h[2];
-    const double qscale = 1.602176634e-19 * ldexp(1.0, -3 * P.frac_bits) / dV;
+    const double qscale = 1.602176634e-19 * ldexp(1.0, -3 * P.frac_bits) / dV / 8.8541878128e-12;
     const double phi_top = P.E0 * (P.hi[2] - P.lo[2]);
+    const double bc_top = 2.0 * phi_top / (P.h[2] * P.h[2]);
     ++g_launches;
-    k_rho<<<grid_for(G, 256), 256, 0, s>>>(P, d.Npos, d.Nneg, d.ne_fix, d.rho, d.lev[0].rhs, G, qscale, phi_top,
+    k_rho<<<grid_for(G, 256), 256, 0, s>>>(P, d.Npos, d.Nneg, d.ne_fix, d.rho, d.lev[0].rhs, G, qscale, bc_top,
                                           d.ctr);
 }
 
