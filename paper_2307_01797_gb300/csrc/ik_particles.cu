@@ -804,22 +804,58 @@ __global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired
         const uint64_t seed = seed_of(P, r);
         for (long long j = lane; j < m; j += 32) {
             const long long wj = wq + (j == 0 ? rem : 0);
-            double Y0[3], rr, dir[3], Ya[3];
-            photon_sample(P, seed, c, (uint32_t)j, ijk, lnK, Y0, rr, dir);
             bool inside = true;
+            int ix, iy, iz;
+            double Ya[3];
+            if (mixed) {
+                // FP32 in cell units from the source cell's corner; the same
+                // draws as the FP64 form (top 23 bits of each uniform)
+                Stream st(seed, c, P.step, TAG_PHOTON, (uint32_t)j);
+                float Yc[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                Ya[a] = Y0[a] + rr * dir[a];
-                inside = inside && (Ya[a] >= P.lo[a]) && (Ya[a] < P.hi[a]);
+                for (int a = 0; a < 3; ++a) {
+                    const uint32_t hw = st.u32();
+                    (void)st.u32();
+                    Yc[a] = uniform_f32(hw);
+                }
+                const uint32_t h4 = st.u32(); (void)st.u32();
+                const uint32_t h5 = st.u32(); (void)st.u32();
+                const uint32_t h6 = st.u32(); (void)st.u32();
+                const uint32_t h7 = st.u32(); (void)st.u32();
+                const float kappa = (float)P.kappa_lo * expf(uniform_f32(h4) * (float)lnK);
+                const float rc = (-logf(uniform_f32(h5))) / kappa * (float)(1.0 / P.h[0]);
+                const float cz = 2.0f * uniform_f32(h6) - 1.0f;
+                float sphi, cphi;
+                sincospif(2.0f * uniform_f32(h7), &sphi, &cphi);
+                const float stt = sqrtf((1.0f - cz) * (1.0f + cz));
+                const float dir[3] = { stt * cphi, stt * sphi, cz };
+                int id[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float y = Yc[a] + rc * dir[a];
+                    const float fl = floorf(y);
+                    id[a] = ijk[a] + (int)fl;
+                    Ya[a] = (double)clamp_off((double)(y - fl));
+                    inside = inside && id[a] >= 0 && id[a] < P.n;
+                }
+                ix = id[0]; iy = id[1]; iz = id[2];
+            } else {
+                double Y0[3], rr, dir[3];
+                photon_sample(P, seed, c, (uint32_t)j, ijk, lnK, Y0, rr, dir);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    Ya[a] = Y0[a] + rr * dir[a];
+                    inside = inside && (Ya[a] >= P.lo[a]) && (Ya[a] < P.hi[a]);
+                }
+                ix = inside ? cell_axis(Ya[0], P.lo[0], P.h[0], P.n) : 0;
+                iy = inside ? cell_axis(Ya[1], P.lo[1], P.h[1], P.n) : 0;
+                iz = inside ? cell_axis(Ya[2], P.lo[2], P.h[2], P.n) : 0;
             }
             if (!inside) {
                 atomicAdd(&ctr->lost[r], (unsigned long long)wj);
                 continue;
             }
             if (wj > 0xffffffffll) atomicOr(&ctr->err, DERR_OVERFLOW);
-            const int ix = cell_axis(Ya[0], P.lo[0], P.h[0], P.n);
-            const int iy = cell_axis(Ya[1], P.lo[1], P.h[1], P.n);
-            const int iz = cell_axis(Ya[2], P.lo[2], P.h[2], P.n);
             const uint32_t gd = (uint32_t)((size_t)r * P.n3 + ((size_t)iz * P.n + iy) * P.n + ix);
             atomicAdd((unsigned long long*)(Npos + gd), (unsigned long long)wj);
             atomicAdd(photo_cnt + gd, 1);
@@ -828,15 +864,7 @@ __global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired
             const unsigned long long slot = warp_slot(&ctr->n_photo);
             if (slot < photo_cap) {
                 Photo ph;
-                if (mixed) {
-                    const int id[3] = { ix, iy, iz };
-                    double o[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) o[a] = (double)clamp_off((Ya[a] - P.lo[a]) / P.h[a] - (double)id[a]);
-                    ph.x = o[0]; ph.y = o[1]; ph.z = o[2];
-                } else {
-                    ph.x = Ya[0]; ph.y = Ya[1]; ph.z = Ya[2];
-                }
+                ph.x = Ya[0]; ph.y = Ya[1]; ph.z = Ya[2];   // offsets (mixed) or absolute (FP64)
                 ph.g = gd; ph.src = c; ph.slot = (uint32_t)j; ph.w = (uint32_t)wj;
                 photos[slot] = ph;
             } else {
@@ -1211,26 +1239,29 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                 if (ok) cur[M + __popc(bal & ((1u << lane) - 1u))] = e;
                 M += __popc(bal);
             }
-            // photoelectrons: rank by (source, slot)
+            // photoelectrons: rank by (source, slot); the keys are staged in
+            // the (still unused) tmp buffer so the ranking reads shared memory
             uint32_t n_lt = 0;
+            unsigned long long* keys = reinterpret_cast<unsigned long long*>(tmp);
             for (uint32_t j = lane; j < np; j += 32) {
                 const Photo pj = photos[photo_sorted[p0 + j]];
+                keys[j] = ((unsigned long long)pj.src << 8) | pj.slot;
                 n_lt += pj.src < c;
-            }
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) n_lt += __shfl_xor_sync(0xffffffffu, n_lt, d);
-            for (uint32_t j = lane; j < np; j += 32) {
-                const Photo pj = photos[photo_sorted[p0 + j]];
-                uint32_t rank = 0;
-                for (uint32_t k = 0; k < np; ++k) {
-                    const Photo pk = photos[photo_sorted[p0 + k]];
-                    rank += (pk.src < pj.src) || (pk.src == pj.src && pk.slot < pj.slot);
-                }
                 MPT e;
                 e.x = pj.x; e.y = pj.y; e.z = pj.z; e.w = pj.w;
                 if constexpr (!MX) e.pad = 0;
-                cur[M + (rank < n_lt ? rank : rank + mprod)] = e;
+                nxt[j] = e;                           // unranked, in slot order
             }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) n_lt += __shfl_xor_sync(0xffffffffu, n_lt, d);
+            __syncwarp();
+            for (uint32_t j = lane; j < np; j += 32) {
+                const unsigned long long kj = keys[j];
+                uint32_t rank = 0;
+                for (uint32_t k = 0; k < np; ++k) rank += keys[k] < kj;
+                cur[M + (rank < n_lt ? rank : rank + mprod)] = nxt[j];
+            }
+            __syncwarp();
             if (mprod) {
                 const long long wq = dN / (long long)mprod, rem = dN % (long long)mprod;
                 const int ijk[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
