@@ -212,6 +212,8 @@ def our_arm(args, rank, world):
         stage["particles"] += s["ms_particles"]; stage["field"] += s["ms_field"]
         movers += s["n_movers"]
         mg_cycles.append(s["mg_cycles"])
+        merge_stats = {k: s[k] for k in ("merge_cells", "merge_elements", "merge_elements_sq", "merge_max_list",
+                                         "n_new_particles", "photon_emissions", "ionizations", "attachments")}
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -284,6 +286,7 @@ def our_arm(args, rank, world):
         "push_sort_deposit_kmc_rate": core_rate,
         "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
         "movers_per_step": movers / args.steps, "mg_cycles": mg_cycles, "particles_per_step": counts,
+        "last_step_counters": merge_stats,
         "roofline": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)", "achieved": ach,
                      "peak": pk, "peak_kind": pk_kind, "unit": "GB/s", "frac": ach / pk, "traffic": None,
                      "bytes_per_particle": 2 * R + mesh / 32},

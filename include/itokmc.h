@@ -136,6 +136,7 @@ typedef struct itokmc_stats {
     double mg_rel_residual;    /* ||r||/||b|| after the last field solve      */
     double ms_transport, ms_kmc, ms_particles, ms_field; /* last step (events)*/
     int64_t kernel_launches;   /* kernels launched by the library so far     */
+    int64_t merge_cells, merge_elements, merge_elements_sq, merge_max_list; /* last a9 */
 } itokmc_stats;
 
 typedef struct itokmc_handle itokmc_handle;

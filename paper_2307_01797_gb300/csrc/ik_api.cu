@@ -231,6 +231,10 @@ int stage_particles(itokmc_handle* h)
     h->st.kmc_status = (c.err & ik::DERR_KMC) ? ITOKMC_ERR_KMC : 0;
     h->st.ms_kmc = elapsed(h, 2, 3);
     h->st.ms_particles = elapsed(h, 4, 5);
+    h->st.merge_cells = (int64_t)c.merge_cells;
+    h->st.merge_elements = (int64_t)c.merge_elems;
+    h->st.merge_elements_sq = (int64_t)c.merge_elems2;
+    h->st.merge_max_list = (int64_t)c.merge_maxm;
     return status_of_err(h, c.err);
 }
 

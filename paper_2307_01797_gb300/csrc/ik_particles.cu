@@ -967,36 +967,89 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
     return v;
 }
-__device__ __forceinline__ double warp_min(double v)
+
+// Order-preserving integer keys of coordinates: the tree compares keys with
+// integer instructions (FP64 comparisons run at a small fraction of the FP32
+// rate on GB300).  key(a) < key(b) iff a < b for all non-NaN values except
+// that -0 sorts below +0 (positions never hold -0).
+__device__ __forceinline__ uint32_t okey(float v)
 {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, d));
-    return v;
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
-__device__ __forceinline__ double warp_max(double v)
+__device__ __forceinline__ unsigned long long okey(double v)
 {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, d));
-    return v;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ float okey_val(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+__device__ __forceinline__ double okey_val(unsigned long long k)
+{
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
 }
 
-// Stable rank sort of m <= 32 NQ elements by (coordinate, position): each
-// lane keeps the keys of its elements j = lane + 32 q in registers and scans
-// all k with broadcast loads.
+template <class E> struct ET;
+template <> struct ET<MP> {
+    using K = unsigned long long;
+    using V = double;
+    static __device__ __forceinline__ K key(const MP& e, int a) { return okey(a == 0 ? e.x : (a == 1 ? e.y : e.z)); }
+    static __device__ __forceinline__ K wmin(K v)
+    {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) { const K o = __shfl_xor_sync(0xffffffffu, v, d); v = o < v ? o : v; }
+        return v;
+    }
+    static __device__ __forceinline__ K wmax(K v)
+    {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) { const K o = __shfl_xor_sync(0xffffffffu, v, d); v = o > v ? o : v; }
+        return v;
+    }
+};
+template <> struct ET<MP32> {
+    using K = uint32_t;
+    using V = float;
+    static __device__ __forceinline__ K key(const MP32& e, int a) { return okey(a == 0 ? e.x : (a == 1 ? e.y : e.z)); }
+    static __device__ __forceinline__ K wmin(K v) { return __reduce_min_sync(0xffffffffu, v); }
+    static __device__ __forceinline__ K wmax(K v) { return __reduce_max_sync(0xffffffffu, v); }
+};
+
+// Widest axis from key bounds (largest extent, ties to the lowest axis); the
+// extent hi - lo is taken in the element's own precision.
+template <class E>
+__device__ __forceinline__ int widest_axis(const typename ET<E>::K lo[3], const typename ET<E>::K hi[3])
+{
+    using V = typename ET<E>::V;
+    V ext[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ext[a] = okey_val(hi[a]) - okey_val(lo[a]);
+    int axis = 0;
+    if (ext[1] > ext[axis]) axis = 1;
+    if (ext[2] > ext[axis]) axis = 2;
+    return axis;
+}
+
+// Stable rank sort of m <= 32 NQ elements by (key, position): each lane
+// keeps the keys of its elements j = lane + 32 q in registers and scans all
+// k with broadcast loads.
 template <class E, int NQ>
 __device__ __forceinline__ void rank_sort_reg(const E* src, uint32_t m, int axis, E* tmp)
 {
+    using K = typename ET<E>::K;
     const unsigned lane = lane_id();
-    double cj[NQ];
+    K cj[NQ];
     uint32_t rk[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         const uint32_t j = lane + 32u * q;
-        cj[q] = j < m ? mp_coord(src[j], axis) : 0.0;
+        cj[q] = j < m ? ET<E>::key(src[j], axis) : (K)0;
         rk[q] = 0;
     }
     for (uint32_t k = 0; k < m; ++k) {
-        const double ck = mp_coord(src[k], axis);
+        const K ck = ET<E>::key(src[k], axis);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const uint32_t j = lane + 32u * q;
@@ -1015,29 +1068,23 @@ __device__ __forceinline__ void rank_sort_reg(const E* src, uint32_t m, int axis
 template <class E>
 __device__ uint32_t split_node(const E* src, uint32_t m, unsigned long long W, E* tmp, E* dst, uint32_t* nr_out)
 {
+    using K = typename ET<E>::K;
     const unsigned lane = lane_id();
-    // bounding box and axis (largest extent, ties to the lowest axis)
-    double lo[3], hi[3];
+    K lo[3], hi[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) { lo[a] = 1e300; hi[a] = -1e300; }
+    for (int a = 0; a < 3; ++a) { lo[a] = (K)~(K)0; hi[a] = (K)0; }
     for (uint32_t j = lane; j < m; j += 32) {
         const E p = src[j];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double v = mp_coord(p, a);
-            lo[a] = fmin(lo[a], v);
-            hi[a] = fmax(hi[a], v);
+            const K v = ET<E>::key(p, a);
+            lo[a] = v < lo[a] ? v : lo[a];
+            hi[a] = v > hi[a] ? v : hi[a];
         }
     }
-    double ext[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) ext[a] = warp_max(hi[a]) - warp_min(lo[a]);
-    int axis = 0;
-    if (ext[1] > ext[axis]) axis = 1;
-    if (ext[2] > ext[axis]) axis = 2;
-    // stable rank sort by (coordinate, list position): each lane keeps the
-    // keys of its elements j = lane + 32 q in registers and scans all k with
-    // broadcast loads
+    for (int a = 0; a < 3; ++a) { lo[a] = ET<E>::wmin(lo[a]); hi[a] = ET<E>::wmax(hi[a]); }
+    const int axis = widest_axis<E>(lo, hi);
     if (m <= 256) {
         switch ((m + 31) / 32) {
         case 1: rank_sort_reg<E, 1>(src, m, axis, tmp); break;
@@ -1052,10 +1099,10 @@ __device__ uint32_t split_node(const E* src, uint32_t m, unsigned long long W, E
     } else {
         for (uint32_t j = lane; j < m; j += 32) {
             const E pj = src[j];
-            const double cj = mp_coord(pj, axis);
+            const K cj = ET<E>::key(pj, axis);
             uint32_t rank = 0;
             for (uint32_t k = 0; k < m; ++k) {
-                const double ck = mp_coord(src[k], axis);
+                const K ck = ET<E>::key(src[k], axis);
                 rank += (ck < cj) || (ck == cj && k < j);
             }
             tmp[rank] = pj;
@@ -1111,40 +1158,36 @@ __device__ uint32_t split_node(const E* src, uint32_t m, unsigned long long W, E
     return nl;
 }
 
-// MX = false: FP64 records with absolute positions; MX = true: FP32 cell
-// offsets plus a cell array.  The tree itself works on FP64 coordinates
-// (FP32 offsets convert exactly).
 // One node per lane: stable insertion sort of the node's slice along its
 // widest axis (in place), weighted median, child sizes.  Returns the number
-// of output elements; nl_out receives the left child's size (0 = unsplit).
+// of output elements; nl_out receives the left child's size.
 template <class E>
 __device__ __forceinline__ uint32_t lane_split_prepare(E* node, uint32_t m, unsigned long long W, uint32_t& pm_out,
                                                        E& ml, E& mr, uint32_t& nl_out, bool& lmed, bool& rmed)
 {
-    double lo[3] = { mp_coord(node[0], 0), mp_coord(node[0], 1), mp_coord(node[0], 2) };
-    double hi[3] = { lo[0], lo[1], lo[2] };
+    using K = typename ET<E>::K;
+    K lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { lo[a] = ET<E>::key(node[0], a); hi[a] = lo[a]; }
     for (uint32_t q = 1; q < m; ++q) {
         const E e = node[q];
-        const double v[3] = { mp_coord(e, 0), mp_coord(e, 1), mp_coord(e, 2) };
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            lo[a] = v[a] < lo[a] ? v[a] : lo[a];
-            hi[a] = v[a] > hi[a] ? v[a] : hi[a];
+            const K v = ET<E>::key(e, a);
+            lo[a] = v < lo[a] ? v : lo[a];
+            hi[a] = v > hi[a] ? v : hi[a];
         }
     }
-    const double ext[3] = { hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2] };
-    int axis = 0;
-    if (ext[1] > ext[axis]) axis = 1;
-    if (ext[2] > ext[axis]) axis = 2;
+    const int axis = widest_axis<E>(lo, hi);
     for (uint32_t q = 1; q < m; ++q) {
-        const E key = node[q];
-        const double c = mp_coord(key, axis);
+        const E kv = node[q];
+        const K c = ET<E>::key(kv, axis);
         int p = (int)q - 1;
-        while (p >= 0 && mp_coord(node[p], axis) > c) {
+        while (p >= 0 && ET<E>::key(node[p], axis) > c) {
             node[p + 1] = node[p];
             --p;
         }
-        node[p + 1] = key;
+        node[p + 1] = kv;
     }
     unsigned long long C = 0;
     uint32_t pm = m - 1;
@@ -1286,6 +1329,12 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
             }
             M += mprod + np;
             __syncwarp();
+            if (lane == 0) {
+                atomicAdd(&ctr->merge_cells, 1ull);
+                atomicAdd(&ctr->merge_elems, (unsigned long long)M);
+                atomicAdd(&ctr->merge_elems2, (unsigned long long)M * M);
+                atomicMax(&ctr->merge_maxm, (unsigned long long)M);
+            }
             // level-synchronous median splits up to T leaves
             uint32_t* bnd = sb[wid][0];
             uint32_t* bnd2 = sb[wid][1];

@@ -59,6 +59,7 @@ struct Counters {
     unsigned long long absorbed_w;
     unsigned long long photo_slots;    // sum over cells of min(N_gamma, N_new)
     unsigned int n_photo_cells;        // photon-emitting cells listed by the KMC
+    unsigned long long merge_cells, merge_elems, merge_elems2, merge_maxm;   // merge workload
     unsigned int err;                  // DERR_* bits
     unsigned int kmc_fail_cell;
     unsigned long long outflow[MAX_R];

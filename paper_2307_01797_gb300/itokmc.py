@@ -57,7 +57,8 @@ class Stats(ctypes.Structure):
         ("n_new_particles", ctypes.c_int64), ("mg_cycles", ctypes.c_int32), ("kmc_status", ctypes.c_int32),
         ("mg_rel_residual", ctypes.c_double), ("ms_transport", ctypes.c_double), ("ms_kmc", ctypes.c_double),
         ("ms_particles", ctypes.c_double), ("ms_field", ctypes.c_double),
-        ("kernel_launches", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64), ("merge_cells", ctypes.c_int64), ("merge_elements", ctypes.c_int64),
+        ("merge_elements_sq", ctypes.c_int64), ("merge_max_list", ctypes.c_int64),
     ]
 
     def as_dict(self):
