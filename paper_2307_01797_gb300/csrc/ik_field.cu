@@ -504,6 +504,8 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
         if (precision == 1) {
             ++g_launches;
             k_zero<float><<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi32, G0.cells);
+            // inner solve of A e = r in FP32: two V-cycles per FP64 residual
+            vcycle<float>(d, 0, R, nu1, nu2, s);
             vcycle<float>(d, 0, R, nu1, nu2, s);
             ++g_launches;
             k_add_correction<<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi, L0.phi32, G0.cells);

@@ -959,7 +959,7 @@ __device__ __forceinline__ double mp_coord(const MP32& p, int a)
 }
 
 template <bool MX> struct MergeElem { using T = MP; static constexpr int CAP = 128; };
-template <> struct MergeElem<true> { using T = MP32; static constexpr int CAP = 256; };
+template <> struct MergeElem<true> { using T = MP32; static constexpr int CAP = 176; };
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 {
@@ -1229,7 +1229,8 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
     constexpr int CAP = MergeElem<MX>::CAP;
     extern __shared__ unsigned char merge_smem[];
     MPT(*sbuf)[3][CAP] = reinterpret_cast<MPT(*)[3][CAP]>(merge_smem);
-    __shared__ uint32_t sb[MERGE_WARPS][2][257];
+    // node boundaries: 2 x (ppc + 1) per warp after the element buffers
+    uint32_t* sbnd = reinterpret_cast<uint32_t*>(merge_smem + (SMALL ? sizeof(MPT) * 3 * CAP * MERGE_WARPS : 0));
     const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
     const uint64_t gw = (uint64_t)blockIdx.x * MERGE_WARPS + wid;
     const uint64_t nwarps = (uint64_t)gridDim.x * MERGE_WARPS;
@@ -1336,14 +1337,15 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
                 atomicMax(&ctr->merge_maxm, (unsigned long long)M);
             }
             // level-synchronous median splits up to T leaves
-            uint32_t* bnd = sb[wid][0];
-            uint32_t* bnd2 = sb[wid][1];
+            uint32_t* bnd = sbnd + (size_t)wid * 2 * (T + 1);
+            uint32_t* bnd2 = bnd + (T + 1);
             if (lane == 0) { bnd[0] = 0; bnd[1] = M; }
             __syncwarp();
             int nnodes = 1;
             for (int level = 1; level < T; level *= 2) {
                 if (lane == 0) bnd2[0] = 0;
-                if (nnodes >= MERGE_LANE_NODES) {
+                // one node per lane once the nodes are many or small
+                if (nnodes >= MERGE_LANE_NODES || (int)bnd[nnodes] <= 12 * nnodes) {
                     // one node per lane; nodes in rounds of 32
                     uint32_t fill = 0;
                     int nn = 0;
@@ -1797,22 +1799,27 @@ void launch_particles_b(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
         k_photo_place<<<grid_for(d.photo_cap, 256, 1024), 256, 0, s>>>(d.photos, d.ctr, d.photo_cap, d.photo_off,
                                                                       d.photo_cursor, d.photo_sorted);
     }
-    const size_t smem32 = sizeof(MP32) * 3 * MergeElem<true>::CAP * MERGE_WARPS;
-    const size_t smem64 = sizeof(MP) * 3 * MergeElem<false>::CAP * MERGE_WARPS;
+    const size_t bnd_bytes = sizeof(uint32_t) * 2 * (P.ppc + 1) * MERGE_WARPS;
+    const size_t smem32 = sizeof(MP32) * 3 * MergeElem<true>::CAP * MERGE_WARPS + bnd_bytes;
+    const size_t smem64 = sizeof(MP) * 3 * MergeElem<false>::CAP * MERGE_WARPS + bnd_bytes;
     const size_t smem = d.mixed ? smem32 : smem64;
-    static bool attr_set = false;
-    if (!attr_set) {
+    const size_t smem_big = bnd_bytes;
+    static size_t attr32 = 0, attr64 = 0;
+    if (smem32 > attr32) {
         cudaFuncSetAttribute(k_merge<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+        attr32 = smem32;
+    }
+    if (smem64 > attr64) {
         cudaFuncSetAttribute(k_merge<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
-        attr_set = true;
+        attr64 = smem64;
     }
     g_launches += 2;
     if (d.mixed) {
-        k_merge<true, true><<<152 * 2, MERGE_WARPS * 32, smem, s>>>(
+        k_merge<true, true><<<152 * 3, MERGE_WARPS * 32, smem, s>>>(
             P, nullptr, d.rA32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
             d.work_off, reinterpret_cast<MP32*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
             d.photo_cap, d.small_list, d.list_n, d.ctr);
-        k_merge<true, false><<<152 * 4, MERGE_WARPS * 32, 0, s>>>(
+        k_merge<true, false><<<152 * 4, MERGE_WARPS * 32, smem_big, s>>>(
             P, nullptr, d.rA32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
             d.work_off, reinterpret_cast<MP32*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
             d.photo_cap, d.big_list, d.list_n, d.ctr);
@@ -1823,7 +1830,7 @@ void launch_particles_b(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
             P, d.recA, nullptr, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
             d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, d.recB, nullptr, nullptr, G, d.mover_cap,
             d.photo_cap, d.small_list, d.list_n, d.ctr);
-        k_merge<false, false><<<152 * 4, MERGE_WARPS * 32, 0, s>>>(
+        k_merge<false, false><<<152 * 4, MERGE_WARPS * 32, smem_big, s>>>(
             P, d.recA, nullptr, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
             d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, d.recB, nullptr, nullptr, G, d.mover_cap,
             d.photo_cap, d.big_list, d.list_n, d.ctr);
