@@ -386,12 +386,13 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     d.photo_off = dalloc_n<uint32_t>(h, G + 1, &rc);
     d.work_off = dalloc_n<uint64_t>(h, G + 1, &rc);
     d.small_list = dalloc_n<uint32_t>(h, G, &rc);
+    d.mid_list = dalloc_n<uint32_t>(h, G, &rc);
     d.big_list = dalloc_n<uint32_t>(h, G, &rc);
     d.list_n = dalloc_n<uint32_t>(h, 4, &rc);
     d.pc_list = dalloc_n<uint32_t>(h, G, &rc);
     d.work = reinterpret_cast<unsigned char*>(dalloc(h, d.work_cap * 32, &rc));
     d.work_bytes = d.work_cap * 32;
-    const size_t se = 2 * std::max(std::max(ik::scan_scratch_elems(G, 5), ik::scan_scratch_elems(nblk, 3)),
+    const size_t se = 2 * std::max(std::max(ik::scan_scratch_elems(G, 6), ik::scan_scratch_elems(nblk, 3)),
                                    ik::radix_scratch_elems(h->cap));
     d.scan_blk = dalloc_n<long long>(h, se, &rc);
     d.scan_blk_elems = se;

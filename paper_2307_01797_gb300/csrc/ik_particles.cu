@@ -888,7 +888,6 @@ __global__ void k_photo_place(const Photo* __restrict__ photos, const Counters* 
 }
 
 // ------------------------------------------------------------------ merge scan
-constexpr int MERGE_SMEM = 128;      // elements per shared buffer (x3 per warp)
 constexpr int MERGE_WARPS = 8;
 constexpr int MERGE_LANE_NODES = 8;  // levels with at least this many nodes split one node per lane
 // Per cell: W = X_e + dN + photo weight -> min(W, ppc) leaves; photo offsets;
@@ -905,38 +904,42 @@ struct MergeScanOp {
     uint32_t* out_start;
     uint32_t* photo_off;
     uint64_t* work_off;
-    uint32_t* small_list;     // non-empty cells whose list fits shared memory
+    uint32_t* small_list;     // non-empty cells whose list fits the small shared buffers
+    uint32_t* mid_list;       // ... the large shared buffers
     uint32_t* big_list;       // the others
     uint32_t* list_n;         // [2]: lengths
     uint64_t G;
-    int ppc, n_new, cap;
-    __device__ void load(uint64_t g, long long v[5]) const
+    int ppc, n_new, cap, cap_mid;
+    __device__ void load(uint64_t g, long long v[6]) const
     {
         const long long dN = fired[g] - fired[G + g];
         const long long W = (long long)Xe[g] + dN + (long long)photo_w[g];
         v[0] = W < ppc ? W : ppc;
         v[1] = photo_cnt[g];
         const long long M = (long long)(cs[g + 1] - cs[g]) + (dN > 0 ? (dN < n_new ? dN : n_new) : 0) + photo_cnt[g];
-        const bool big = M > 0 && M + ppc > cap;
-        v[2] = big ? (M + ppc) : 0;
-        v[3] = (v[0] > 0 && !big) ? 1 : 0;
-        v[4] = (v[0] > 0 && big) ? 1 : 0;
+        const int tier = M + ppc <= cap ? 0 : (M + ppc <= cap_mid ? 1 : 2);
+        v[2] = (M > 0 && tier == 2) ? (M + ppc) : 0;
+        v[3] = (v[0] > 0 && tier == 0) ? 1 : 0;
+        v[4] = (v[0] > 0 && tier == 1) ? 1 : 0;
+        v[5] = (v[0] > 0 && tier == 2) ? 1 : 0;
     }
-    __device__ void store(uint64_t g, const long long ex[5], const long long* v) const
+    __device__ void store(uint64_t g, const long long ex[6], const long long* v) const
     {
         out_start[g] = (uint32_t)ex[0];
         photo_off[g] = (uint32_t)ex[1];
         work_off[g] = (uint64_t)ex[2];
         if (v[3]) small_list[ex[3]] = (uint32_t)g;
-        if (v[4]) big_list[ex[4]] = (uint32_t)g;
+        if (v[4]) mid_list[ex[4]] = (uint32_t)g;
+        if (v[5]) big_list[ex[5]] = (uint32_t)g;
     }
-    __device__ void total(const long long t[5]) const
+    __device__ void total(const long long t[6]) const
     {
         out_start[G] = (uint32_t)t[0];
         photo_off[G] = (uint32_t)t[1];
         work_off[G] = (uint64_t)t[2];
         list_n[0] = (uint32_t)t[3];
         list_n[1] = (uint32_t)t[4];
+        list_n[2] = (uint32_t)t[5];
     }
 };
 
@@ -958,8 +961,15 @@ __device__ __forceinline__ double mp_coord(const MP32& p, int a)
     return (double)(a == 0 ? p.x : (a == 1 ? p.y : p.z));
 }
 
-template <bool MX> struct MergeElem { using T = MP; static constexpr int CAP = 128; };
-template <> struct MergeElem<true> { using T = MP32; static constexpr int CAP = 176; };
+// Merge tiers: cells whose lists fit small shared buffers (8 warps per
+// block), larger shared buffers (2 warps per block), or global scratch.
+template <bool MX> struct MergeElem { using T = MP; static constexpr int CAP = 128; static constexpr int CAP_MID = 512; };
+template <> struct MergeElem<true> { using T = MP32; static constexpr int CAP = 176; static constexpr int CAP_MID = 1024; };
+constexpr int MERGE_WARPS_MID = 2;
+template <bool MX, int TIER> struct MergeTier {
+    static constexpr int CAP = TIER == 0 ? MergeElem<MX>::CAP : (TIER == 1 ? MergeElem<MX>::CAP_MID : 0);
+    static constexpr int NW = TIER == 1 ? MERGE_WARPS_MID : MERGE_WARPS;
+};
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 {
@@ -1085,7 +1095,7 @@ __device__ uint32_t split_node(const E* src, uint32_t m, unsigned long long W, E
 #pragma unroll
     for (int a = 0; a < 3; ++a) { lo[a] = ET<E>::wmin(lo[a]); hi[a] = ET<E>::wmax(hi[a]); }
     const int axis = widest_axis<E>(lo, hi);
-    if (m <= 256) {
+    if (m <= 512) {
         switch ((m + 31) / 32) {
         case 1: rank_sort_reg<E, 1>(src, m, axis, tmp); break;
         case 2: rank_sort_reg<E, 2>(src, m, axis, tmp); break;
@@ -1094,7 +1104,10 @@ __device__ uint32_t split_node(const E* src, uint32_t m, unsigned long long W, E
         case 5: rank_sort_reg<E, 5>(src, m, axis, tmp); break;
         case 6: rank_sort_reg<E, 6>(src, m, axis, tmp); break;
         case 7: rank_sort_reg<E, 7>(src, m, axis, tmp); break;
-        default: rank_sort_reg<E, 8>(src, m, axis, tmp); break;
+        case 8: rank_sort_reg<E, 8>(src, m, axis, tmp); break;
+        case 9: case 10: rank_sort_reg<E, 10>(src, m, axis, tmp); break;
+        case 11: case 12: rank_sort_reg<E, 12>(src, m, axis, tmp); break;
+        default: rank_sort_reg<E, 16>(src, m, axis, tmp); break;
         }
     } else {
         for (uint32_t j = lane; j < m; j += 32) {
@@ -1213,10 +1226,10 @@ __device__ __forceinline__ uint32_t lane_split_prepare(E* node, uint32_t m, unsi
     return nl_out + (rmed ? 1u : 0u) + (m - pm - 1);
 }
 
-// SMALL: cells whose list fits the warp's shared buffers; otherwise the
-// cells that do not, with their buffers in the global work area.
-template <bool MX, bool SMALL>
-__global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
+// TIER 0 / 1: cells whose list fits the warp's small / large shared
+// buffers; TIER 2: the others, with their buffers in the global work area.
+template <bool MX, int TIER>
+__global__ void __launch_bounds__(MergeTier<MX, TIER>::NW * 32) k_merge(
     Params P, const P64* __restrict__ A, const P32* __restrict__ A32, const uint32_t* __restrict__ cs,
     const int64_t* __restrict__ fired, const Photo* __restrict__ photos, const uint32_t* __restrict__ photo_sorted,
     const uint32_t* __restrict__ photo_off, const uint32_t* __restrict__ out_start,
@@ -1226,16 +1239,18 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
     const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_n, Counters* __restrict__ ctr)
 {
     using MPT = typename MergeElem<MX>::T;
-    constexpr int CAP = MergeElem<MX>::CAP;
+    constexpr bool SMALL = TIER < 2;
+    constexpr int CAP = MergeTier<MX, TIER>::CAP > 0 ? MergeTier<MX, TIER>::CAP : 1;
+    constexpr int NW = MergeTier<MX, TIER>::NW;
     extern __shared__ unsigned char merge_smem[];
-    MPT(*sbuf)[3][CAP] = reinterpret_cast<MPT(*)[3][CAP]>(merge_smem);
+    MPT* sbuf = reinterpret_cast<MPT*>(merge_smem);
     // node boundaries: 2 x (ppc + 1) per warp after the element buffers
-    uint32_t* sbnd = reinterpret_cast<uint32_t*>(merge_smem + (SMALL ? sizeof(MPT) * 3 * CAP * MERGE_WARPS : 0));
+    uint32_t* sbnd = reinterpret_cast<uint32_t*>(merge_smem + (SMALL ? sizeof(MPT) * 3 * CAP * NW : 0));
     const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
-    const uint64_t gw = (uint64_t)blockIdx.x * MERGE_WARPS + wid;
-    const uint64_t nwarps = (uint64_t)gridDim.x * MERGE_WARPS;
+    const uint64_t gw = (uint64_t)blockIdx.x * NW + wid;
+    const uint64_t nwarps = (uint64_t)gridDim.x * NW;
     const int T = P.ppc;
-    const uint32_t ncells = list_n[SMALL ? 0 : 1];
+    const uint32_t ncells = list_n[TIER];
     for (uint64_t li = gw; li < ncells; li += nwarps) {
         {
             const uint64_t g = list[li];
@@ -1252,7 +1267,9 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge(
             }
             MPT *cur, *nxt, *tmp;
             if (SMALL) {
-                cur = sbuf[wid][0]; nxt = sbuf[wid][1]; tmp = sbuf[wid][2];
+                cur = sbuf + (size_t)wid * 3 * CAP;
+                nxt = cur + CAP;
+                tmp = nxt + CAP;
             } else {
                 const uint64_t S = (uint64_t)Mmax + T;
                 if (work_off[g] + S > work_cap) {
@@ -1785,9 +1802,47 @@ void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
                                             d.photo_cnt, d.photo_w, d.Npos, d.ctr);
     }
     MergeScanOp op{ d.Xe, d.fired, d.photo_w, d.photo_cnt, d.cell_start, d.out_start, d.photo_off, d.work_off,
-                    d.small_list, d.big_list, d.list_n, G, P.ppc, P.n_new,
-                    d.mixed ? MergeElem<true>::CAP : MergeElem<false>::CAP };
-    run_scan<5>(op, G, d.scan_blk, s);
+                    d.small_list, d.mid_list, d.big_list, d.list_n, G, P.ppc, P.n_new,
+                    d.mixed ? MergeElem<true>::CAP : MergeElem<false>::CAP,
+                    d.mixed ? MergeElem<true>::CAP_MID : MergeElem<false>::CAP_MID };
+    run_scan<6>(op, G, d.scan_blk, s);
+}
+
+template <bool MX>
+void launch_merge_tiers(const Params& P, Dev& d, uint64_t G, cudaStream_t s, const P64* A, const P32* A32, P64* out,
+                        P32* out32, uint32_t* cout)
+{
+    using E = typename MergeElem<MX>::T;
+    const size_t bnd_w = sizeof(uint32_t) * 2 * (P.ppc + 1);
+    const size_t sm0 = (sizeof(E) * 3 * MergeTier<MX, 0>::CAP + bnd_w) * MergeTier<MX, 0>::NW;
+    const size_t sm1 = (sizeof(E) * 3 * MergeTier<MX, 1>::CAP + bnd_w) * MergeTier<MX, 1>::NW;
+    const size_t sm2 = bnd_w * MERGE_WARPS;
+    static size_t a0 = 0, a1 = 0;
+    if (sm0 > a0) { cudaFuncSetAttribute(k_merge<MX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0); a0 = sm0; }
+    if (sm1 > a1) { cudaFuncSetAttribute(k_merge<MX, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1); a1 = sm1; }
+    E* work = reinterpret_cast<E*>(d.work);
+    g_launches += 3;
+    k_merge<MX, 0><<<152 * 3, MergeTier<MX, 0>::NW * 32, sm0, s>>>(
+        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, work,
+        d.work_cap / 3, out, out32, cout, G, d.mover_cap, d.photo_cap, d.small_list, d.list_n, d.ctr);
+    k_merge<MX, 1><<<152 * 2, MergeTier<MX, 1>::NW * 32, sm1, s>>>(
+        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, work,
+        d.work_cap / 3, out, out32, cout, G, d.mover_cap, d.photo_cap, d.mid_list, d.list_n, d.ctr);
+    k_merge<MX, 2><<<152 * 4, MERGE_WARPS * 32, sm2, s>>>(
+        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, work,
+        d.work_cap / 3, out, out32, cout, G, d.mover_cap, d.photo_cap, d.big_list, d.list_n, d.ctr);
+}
+
+void launch_merges(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
+{
+    if (d.mixed) {
+        launch_merge_tiers<true>(P, d, G, s, nullptr, d.rA32, nullptr, d.rB32, d.cellB32);
+        P32* t = d.rA32; d.rA32 = d.rB32; d.rB32 = t;
+        uint32_t* tc = d.cellA32; d.cellA32 = d.cellB32; d.cellB32 = tc;
+    } else {
+        launch_merge_tiers<false>(P, d, G, s, d.recA, nullptr, d.recB, nullptr, nullptr);
+        P64* t = d.recA; d.recA = d.recB; d.recB = t;
+    }
 }
 
 // Part b (after the host has checked the output count and work size):
@@ -1799,43 +1854,7 @@ void launch_particles_b(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
         k_photo_place<<<grid_for(d.photo_cap, 256, 1024), 256, 0, s>>>(d.photos, d.ctr, d.photo_cap, d.photo_off,
                                                                       d.photo_cursor, d.photo_sorted);
     }
-    const size_t bnd_bytes = sizeof(uint32_t) * 2 * (P.ppc + 1) * MERGE_WARPS;
-    const size_t smem32 = sizeof(MP32) * 3 * MergeElem<true>::CAP * MERGE_WARPS + bnd_bytes;
-    const size_t smem64 = sizeof(MP) * 3 * MergeElem<false>::CAP * MERGE_WARPS + bnd_bytes;
-    const size_t smem = d.mixed ? smem32 : smem64;
-    const size_t smem_big = bnd_bytes;
-    static size_t attr32 = 0, attr64 = 0;
-    if (smem32 > attr32) {
-        cudaFuncSetAttribute(k_merge<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
-        attr32 = smem32;
-    }
-    if (smem64 > attr64) {
-        cudaFuncSetAttribute(k_merge<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
-        attr64 = smem64;
-    }
-    g_launches += 2;
-    if (d.mixed) {
-        k_merge<true, true><<<152 * 3, MERGE_WARPS * 32, smem, s>>>(
-            P, nullptr, d.rA32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
-            d.work_off, reinterpret_cast<MP32*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
-            d.photo_cap, d.small_list, d.list_n, d.ctr);
-        k_merge<true, false><<<152 * 4, MERGE_WARPS * 32, smem_big, s>>>(
-            P, nullptr, d.rA32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
-            d.work_off, reinterpret_cast<MP32*>(d.work), d.work_cap / 3, nullptr, d.rB32, d.cellB32, G, d.mover_cap,
-            d.photo_cap, d.big_list, d.list_n, d.ctr);
-        P32* t = d.rA32; d.rA32 = d.rB32; d.rB32 = t;
-        uint32_t* tc = d.cellA32; d.cellA32 = d.cellB32; d.cellB32 = tc;
-    } else {
-        k_merge<false, true><<<152 * 2, MERGE_WARPS * 32, smem, s>>>(
-            P, d.recA, nullptr, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
-            d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, d.recB, nullptr, nullptr, G, d.mover_cap,
-            d.photo_cap, d.small_list, d.list_n, d.ctr);
-        k_merge<false, false><<<152 * 4, MERGE_WARPS * 32, smem_big, s>>>(
-            P, d.recA, nullptr, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start,
-            d.work_off, reinterpret_cast<MP*>(d.work), d.work_cap / 3, d.recB, nullptr, nullptr, G, d.mover_cap,
-            d.photo_cap, d.big_list, d.list_n, d.ctr);
-        P64* t = d.recA; d.recA = d.recB; d.recB = t;
-    }
+    launch_merges(P, d, G, s);
     uint32_t* u = d.cell_start; d.cell_start = d.out_start; d.out_start = u;
 }
 

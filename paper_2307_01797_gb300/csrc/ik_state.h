@@ -102,6 +102,7 @@ struct Dev {
     uint32_t* out_start = nullptr;     // G + 1
     uint64_t* work_off = nullptr;      // G + 1
     uint32_t* small_list = nullptr;    // G: non-empty cells merged in shared memory
+    uint32_t* mid_list = nullptr;      // G: ... in large shared buffers
     uint32_t* big_list = nullptr;      // G: non-empty cells merged in the work buffer
     uint32_t* list_n = nullptr;        // 2 counts
     uint32_t* pc_list = nullptr;       // G: photon-emitting cells
