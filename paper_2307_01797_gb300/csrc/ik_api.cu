@@ -125,18 +125,26 @@ int ensure_photo_cap(itokmc_handle* h, uint64_t need)
     return ITOKMC_OK;
 }
 
-// Grows the merge work buffer to `need` elements per buffer (x3).
-int ensure_work_cap(itokmc_handle* h, uint64_t need)
+// Merge work area of `cap` 32-byte units.
+void set_work(itokmc_handle* h, unsigned char* p, uint64_t cap)
 {
-    if (3 * need <= h->d.work_cap) return ITOKMC_OK;
-    const uint64_t cap = 3 * std::max<uint64_t>(need + need / 4, h->d.work_cap / 3 * 2);
-    IK_CHECK(h, cudaStreamSynchronize(h->s));
-    dfree(h, h->d.work);
-    int rc = 0;
-    h->d.work = reinterpret_cast<unsigned char*>(dalloc(h, cap * 32, &rc));
-    if (rc) return rc;
+    h->d.work = p;
     h->d.work_cap = cap;
     h->d.work_bytes = cap * 32;
+}
+
+// Grows the merge work area to hold `need` 32-byte units.
+int ensure_work_cap(itokmc_handle* h, uint64_t need)
+{
+    if (need <= h->d.work_cap) return ITOKMC_OK;
+    const uint64_t cap = std::max<uint64_t>(need + need / 4, h->d.work_cap * 2);
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    dfree(h, h->d.work);
+    set_work(h, nullptr, 0);
+    int rc = 0;
+    unsigned char* p = reinterpret_cast<unsigned char*>(dalloc(h, cap * 32, &rc));
+    if (rc) return rc;
+    set_work(h, p, cap);
     return ITOKMC_OK;
 }
 
@@ -205,7 +213,7 @@ int stage_particles(itokmc_handle* h)
     int rc = ensure_photo_cap(h, h->rb->ctr.photo_slots);
     if (rc) return rc;
     ik::launch_particles_a(h->P, h->d, h->G, h->s);
-    // output count and big-cell work size are known after the merge scan
+    // output count and merge work size are known after the merge scan
     uint64_t tail[2];
     uint32_t outn = 0;
     IK_CHECK(h, cudaMemcpyAsync(&tail[0], h->d.work_off + h->G, sizeof(uint64_t), cudaMemcpyDeviceToHost, h->s));
@@ -243,7 +251,8 @@ int stage_field(itokmc_handle* h)
     IK_CHECK(h, cudaEventRecord(h->ev[6], h->s));
     int cycles = 0;
     double rel = 0.0;
-    const int st = ik::field_solve(h->P, h->d, h->field_prec, h->cfg.mg_rtol, h->cfg.mg_nu1, h->cfg.mg_nu2,
+    const int st = ik::field_solve(h->P, h->d, h->d.phi_F > 0 ? 2 : h->field_prec, h->cfg.mg_rtol, h->cfg.mg_nu1, h->cfg.mg_nu2,
+                                   h->rb->ctr.rho_absmax,
                                    h->cfg.mg_max_cycles, h->s, &cycles, &rel);
     if (st == -3) return cuda_check(h, cudaGetLastError(), "field solve");
     ik::launch_efield(h->P, h->d, h->s);
@@ -344,6 +353,8 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     d.photo_cap = (uint32_t)std::max<size_t>(1u << 16, cap / 4);
     d.work_cap = std::max<uint64_t>(3ull << 20, 2 * (uint64_t)cap + 16);
     d.mixed = cfg->precision == ITOKMC_MIXED;
+    // mixed field form: fixed-point potential and right-hand side
+    d.phi_F = h->field_prec == ITOKMC_MIXED ? ik::phi_fixed_bits(ik::phi_bound(P, 0)) : 0;
     if (d.mixed) {
         d.rA32 = dalloc_n<ik::P32>(h, cap, &rc);
         d.rB32 = dalloc_n<ik::P32>(h, cap, &rc);
@@ -390,8 +401,7 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     d.big_list = dalloc_n<uint32_t>(h, G, &rc);
     d.list_n = dalloc_n<uint32_t>(h, 4, &rc);
     d.pc_list = dalloc_n<uint32_t>(h, G, &rc);
-    d.work = reinterpret_cast<unsigned char*>(dalloc(h, d.work_cap * 32, &rc));
-    d.work_bytes = d.work_cap * 32;
+    set_work(h, reinterpret_cast<unsigned char*>(dalloc(h, d.work_cap * 32, &rc)), d.work_cap);
     const size_t se = 2 * std::max(std::max(ik::scan_scratch_elems(G, 6), ik::scan_scratch_elems(nblk, 3)),
                                    ik::radix_scratch_elems(h->cap));
     d.scan_blk = dalloc_n<long long>(h, se, &rc);
@@ -628,7 +638,14 @@ int itokmc_read_densities(itokmc_handle* h, int32_t r, int32_t which, void* host
     case ITOKMC_XE: src = h->d.Xe; break;
     case ITOKMC_NPOS: src = h->d.Npos; break;
     case ITOKMC_NNEG: src = h->d.Nneg; break;
-    case ITOKMC_PHI: src = h->d.lev[0].phi; break;
+    case ITOKMC_PHI:
+        if (h->d.phi_F > 0) {
+            ik::launch_phi_to_double(h->P, h->d, h->d.stage, h->s);
+            src = h->d.stage;
+        } else {
+            src = h->d.lev[0].phi;
+        }
+        break;
     case ITOKMC_RHO: src = h->d.rho; break;
     case ITOKMC_E:
         ik::launch_unpack_field(h->P, h->d, h->d.stage, h->s);

@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(NORM_TPB) k_resid_norm(const double* __restric
         const double s = nbr_sum(phi, t, G.n, i, j, k, diag);
         const double res = rhs[t] - (s - (double)diag * phi[t]) * inv_h2;
         if (r32) r32[t] = (float)res;
-        acc += res * res;
-        if (with_b) bacc += rhs[t] * rhs[t];
+        acc = __fma_rn(res, res, acc);
+        if (with_b) bacc = __fma_rn(rhs[t], rhs[t], bacc);
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -240,6 +240,120 @@ __global__ void k_add_correction(double* __restrict__ phi, const float* __restri
 {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cells; t += (uint64_t)gridDim.x * blockDim.x)
         phi[t] += (double)e[t];
+}
+
+// ---- fixed-point potential (mixed field form)
+// The potential is held as Phi = phi 2^F (int64) and the right-hand side as
+// B = round(h^2 2^F b), so the residual h^2 2^F (b - A phi) = B - (sum of
+// neighbours - diag Phi) is exact integer arithmetic (FP64 runs at a small
+// fraction of the integer rate on GB300).  The FP32 residual r = R 2^-F / h^2
+// feeds the FP32 correction V-cycles; squared norms are summed in FP32 per
+// thread and FP64 across the block in a fixed order.
+constexpr long long PHI_LIM = 1ll << 59;
+
+__global__ void __launch_bounds__(NORM_TPB) k_resid_fixed(const long long* __restrict__ Phi,
+                                                          const long long* __restrict__ B, float* __restrict__ r32,
+                                                          Geo G, float sc, double* __restrict__ part, int with_b,
+                                                          int items)
+{
+    __shared__ double red[NORM_TPB / 32][2];
+    const uint64_t base = ((uint64_t)blockIdx.x * NORM_TPB) * items;
+    float acc = 0.f, bacc = 0.f;
+    bool bad = false;
+    for (int q = 0; q < items; ++q) {
+        const uint64_t t = base + (uint64_t)q * NORM_TPB + threadIdx.x;
+        if (t >= G.cells) break;
+        int r, k, j, i;
+        decode(t, G.log2n, r, k, j, i);
+        int diag;
+        const long long s = nbr_sum(Phi, t, G.n, i, j, k, diag);
+        const long long pc = Phi[t];
+        bad |= pc >= PHI_LIM || pc <= -PHI_LIM;
+        const long long b = B[t];
+        const float res = __ll2float_rn(b - (s - (long long)diag * pc)) * sc;
+        r32[t] = res;
+        acc = __fmaf_rn(res, res, acc);
+        if (with_b) {
+            const float bf = __ll2float_rn(b) * sc;
+            bacc = __fmaf_rn(bf, bf, bacc);
+        }
+    }
+    double a = bad ? (double)INFINITY : (double)acc, bb = (double)bacc;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, d);
+        bb += __shfl_xor_sync(0xffffffffu, bb, d);
+    }
+    if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5][0] = a; red[threadIdx.x >> 5][1] = bb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < NORM_TPB / 32; ++w) { x += red[w][0]; y += red[w][1]; }
+        part[2 * (uint64_t)blockIdx.x] = x;
+        part[2 * (uint64_t)blockIdx.x + 1] = y;
+    }
+}
+
+// Phi += round(e 2^F) for the FP32 correction e (volts).
+__global__ void k_add_fixed(long long* __restrict__ Phi, const float* __restrict__ e, float scale, uint64_t cells)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cells; t += (uint64_t)gridDim.x * blockDim.x)
+        Phi[t] += __float2ll_rn(e[t] * scale);
+}
+
+// E = -grad(phi) from the fixed-point potential: the neighbour differences
+// are exact integers, scaled by 2^-F / 2h (FP64 into E64 and/or FP32 into E32).
+__global__ void k_efield_fixed(const long long* __restrict__ Phi, E64* __restrict__ E, float4* __restrict__ E32,
+                               Geo G, double sc, long long Phi_top)
+{
+    const float scf = (float)sc;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G.cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        int r, k, j, i;
+        decode(t, G.log2n, r, k, j, i);
+        const int n = G.n;
+        const uint64_t sy = (uint64_t)n, sz = (uint64_t)n * n;
+        const long long c = Phi[t];
+        const long long xm = i > 0 ? Phi[t - 1] : c, xp = i < n - 1 ? Phi[t + 1] : c;
+        const long long ym = j > 0 ? Phi[t - sy] : c, yp = j < n - 1 ? Phi[t + sy] : c;
+        const long long zm = k > 0 ? Phi[t - sz] : -c, zp = k < n - 1 ? Phi[t + sz] : 2 * Phi_top - c;
+        if (E) {
+            const double ex = (double)(xm - xp) * sc, ey = (double)(ym - yp) * sc, ez = (double)(zm - zp) * sc;
+            const double m = sqrt((ex * ex + ey * ey) + ez * ez);
+            reinterpret_cast<double2*>(E + t)[0] = make_double2(ex, ey);
+            reinterpret_cast<double2*>(E + t)[1] = make_double2(ez, m);
+            if (E32) E32[t] = make_float4((float)ex, (float)ey, (float)ez, (float)m);
+        } else {
+            const float ex = __ll2float_rn(xm - xp) * scf, ey = __ll2float_rn(ym - yp) * scf,
+                        ez = __ll2float_rn(zm - zp) * scf;
+            E32[t] = make_float4(ex, ey, ez, sqrtf(ex * ex + ey * ey + ez * ez));
+        }
+    }
+}
+
+// B = round(b h^2 2^F) with b formed exactly as the FP64 right-hand side.
+__global__ void k_rhs_fixed(const int64_t* __restrict__ rho, long long* __restrict__ B, Geo G, double qscale,
+                            double bc_top, double bfix)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G.cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        const int k = (int)((t >> (2 * G.log2n)) & (uint64_t)(G.n - 1));
+        double b = -((double)rho[t] * qscale);
+        if (k == G.n - 1) b = b - bc_top;
+        B[t] = __double2ll_rn(b * bfix);
+    }
+}
+
+// Phi <- round(Phi 2^-sh) when the fixed-point scale is lowered.
+__global__ void k_shift_fixed(long long* __restrict__ Phi, int sh, uint64_t cells)
+{
+    const long long half = 1ll << (sh - 1);
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cells; t += (uint64_t)gridDim.x * blockDim.x)
+        Phi[t] = (Phi[t] + half) >> sh;
+}
+
+__global__ void k_phi_to_double(const long long* __restrict__ Phi, double* __restrict__ out, double sc, uint64_t cells)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cells; t += (uint64_t)gridDim.x * blockDim.x)
+        out[t] = (double)Phi[t] * sc;
 }
 
 template <class T>
@@ -467,9 +581,15 @@ void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
 
 }  // namespace
 
-// Returns 0 on convergence, ITOKMC_ERR_NOCONV (-6) if max_cycles is reached.
-int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2, int max_cycles,
-                cudaStream_t s, int* cycles_out, double* rel_out)
+constexpr int MAX_REAL_NORM = 4096;
+
+// precision: 0 FP64 V-cycles; 1 FP32 V-cycles in FP64 residual refinement;
+// 2 FP32 V-cycles in fixed-point residual refinement (potential in units of
+// 2^-phi_F V, right-hand side prepared by the charge kernel).  Returns 0 on
+// convergence, ITOKMC_ERR_NOCONV (-6) if max_cycles is reached or the
+// potential leaves the fixed-point range.
+int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2, unsigned long long rho_absmax,
+                int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out)
 {
     const int R = P.R;
     MGLevel& L0 = d.lev[0];
@@ -480,13 +600,37 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
     const int nblk = (int)(G0.cells / ((uint64_t)NORM_TPB * items));
     const int bpr = nblk / R;
     double* h_norm = d.norm_host;       // 2 R doubles of host memory owned by the caller
+    double bnorm[MAX_REAL_NORM];
+    if (R > MAX_REAL_NORM) return -1;
     double worst = 0.0;
     int cyc = 0;
     int status = -6;
+    const bool fixed = precision == 2;
+    long long* Phi = reinterpret_cast<long long*>(L0.phi);
+    long long* Bfix = reinterpret_cast<long long*>(L0.rhs);
+    if (fixed) {
+        // scale from a bound on |phi| (lowered only: the warm start is shifted)
+        const int F = phi_fixed_bits(phi_bound(P, rho_absmax));
+        if (F < d.phi_F) {
+            ++g_launches;
+            k_shift_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(Phi, d.phi_F - F, G0.cells);
+            d.phi_F = F;
+        }
+        double qscale, bc_top;
+        rhs_consts(P, qscale, bc_top);
+        ++g_launches;
+        k_rhs_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(d.rho, Bfix, G0, qscale, bc_top,
+                                                         L0.h * L0.h * std::ldexp(1.0, d.phi_F));
+    }
+    const float rsc = (float)(std::ldexp(1.0, -d.phi_F) * inv_h2);
+    const float esc = (float)std::ldexp(1.0, d.phi_F);
     for (cyc = 0; cyc <= max_cycles; ++cyc) {
         ++g_launches;
-        k_resid_norm<<<nblk, NORM_TPB, 0, s>>>(L0.phi, L0.rhs, precision == 1 ? L0.rhs32 : nullptr, G0, inv_h2,
-                                               d.norm_part, 1, items);
+        if (fixed)
+            k_resid_fixed<<<nblk, NORM_TPB, 0, s>>>(Phi, Bfix, L0.rhs32, G0, rsc, d.norm_part, cyc == 0, items);
+        else
+            k_resid_norm<<<nblk, NORM_TPB, 0, s>>>(L0.phi, L0.rhs, precision == 1 ? L0.rhs32 : nullptr, G0, inv_h2,
+                                                   d.norm_part, cyc == 0, items);
         ++g_launches;
         k_norm_final<<<R, 256, 0, s>>>(d.norm_part, bpr, R, d.norm_out);
         cudaMemcpyAsync(h_norm, d.norm_out, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -494,21 +638,25 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
         worst = 0.0;
         bool done = true;
         for (int r = 0; r < R; ++r) {
-            const double rn = std::sqrt(h_norm[2 * r]), bn = std::sqrt(h_norm[2 * r + 1]);
+            if (cyc == 0) bnorm[r] = h_norm[2 * r + 1];
+            const double rn = std::sqrt(h_norm[2 * r]), bn = std::sqrt(bnorm[r]);
             const double rel = bn > 0.0 ? rn / bn : rn;
-            if (rel > worst) worst = rel;
+            if (rel > worst || !(rel == rel)) worst = rel;
             if (!(rn <= rtol * bn)) done = false;
         }
         if (done) { status = 0; break; }
-        if (cyc == max_cycles) break;
-        if (precision == 1) {
+        if (cyc == max_cycles || !std::isfinite(worst)) break;
+        if (precision >= 1) {
             ++g_launches;
             k_zero<float><<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi32, G0.cells);
-            // inner solve of A e = r in FP32: two V-cycles per FP64 residual
+            // inner solve of A e = r in FP32: two V-cycles per outer residual
             vcycle<float>(d, 0, R, nu1, nu2, s);
             vcycle<float>(d, 0, R, nu1, nu2, s);
             ++g_launches;
-            k_add_correction<<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi, L0.phi32, G0.cells);
+            if (fixed)
+                k_add_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(Phi, L0.phi32, esc, G0.cells);
+            else
+                k_add_correction<<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi, L0.phi32, G0.cells);
         } else {
             vcycle<double>(d, 0, R, nu1, nu2, s);
         }
@@ -563,9 +711,23 @@ void launch_unpack_field(const Params& P, Dev& d, double* E3, cudaStream_t s)
 void launch_efield(const Params& P, Dev& d, cudaStream_t s)
 {
     const Geo G0 = geo(d, 0, P.R);
+    const double phi_top = P.E0 * (P.hi[2] - P.lo[2]);
     ++g_launches;
-    k_efield<<<gridsz(G0.cells, 256), 256, 0, s>>>(d.lev[0].phi, d.E, d.E32, G0, d.lev[0].h,
-                                                  P.E0 * (P.hi[2] - P.lo[2]));
+    if (d.phi_F > 0)
+        k_efield_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(
+            reinterpret_cast<const long long*>(d.lev[0].phi), d.E, d.E32, G0,
+            std::ldexp(1.0, -d.phi_F) / (2.0 * d.lev[0].h), std::llrint(std::ldexp(phi_top, d.phi_F)));
+    else
+        k_efield<<<gridsz(G0.cells, 256), 256, 0, s>>>(d.lev[0].phi, d.E, d.E32, G0, d.lev[0].h, phi_top);
+}
+
+// The potential as FP64 volts into out (R n^3).
+void launch_phi_to_double(const Params& P, Dev& d, double* out, cudaStream_t s)
+{
+    const Geo G0 = geo(d, 0, P.R);
+    ++g_launches;
+    k_phi_to_double<<<gridsz(G0.cells, 256), 256, 0, s>>>(reinterpret_cast<const long long*>(d.lev[0].phi), out,
+                                                          std::ldexp(1.0, -d.phi_F), G0.cells);
 }
 
 }  // namespace ik
@@ -694,7 +856,7 @@ extern "C" int itokmc_field_solve_noalloc(const itokmc_config* cfg, const int64_
     k_rhs_from_rho<<<gridsz((uint64_t)P.n3, 256), 256, 0, s>>>(rho, d.lev[0].rhs, n, P.log2n, qscale, phi_top, P.h[0]);
     int cycles = 0;
     double rel = 0.0;
-    const int st = field_solve(P, d, prec, cfg->mg_rtol, cfg->mg_nu1, cfg->mg_nu2, cfg->mg_max_cycles, s, &cycles,
+    const int st = field_solve(P, d, prec, cfg->mg_rtol, cfg->mg_nu1, cfg->mg_nu2, 0ull, cfg->mg_max_cycles, s, &cycles,
                                &rel);
     if (cycles_out) *cycles_out = cycles;
     if (rel_out) *rel_out = rel;

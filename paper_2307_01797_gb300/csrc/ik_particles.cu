@@ -12,6 +12,7 @@
 //   particles (a7-a9): loss removal and products (Sec. 4.4, Eq. w), photons
 //     (Sec. 4.5, Eq. photon_transport), kd-tree merge/split (Sec. 4.6).
 #include <cstdio>
+#include <type_traits>
 
 #include "ik_common.cuh"
 #include "ik_scan.cuh"
@@ -460,14 +461,16 @@ __global__ void __launch_bounds__(TPB) k_deposit_f64(Params P, const P64* __rest
 }
 
 // ------------------------------------------------------------------ rho
-// rho_fixed = 2^3s (N+ - N-) - ne_fix (units q_e 2^-3s per cell) and the
-// multigrid right-hand side b = -rho/eps0 with the electrode potentials
-// folded in (ghost 2 phi_b - phi_1 at z faces: -2 phi_b / h^2).
+// rho_fixed = 2^3s (N+ - N-) - ne_fix (units q_e 2^-3s per cell), its
+// maximum modulus, and (rhs != nullptr) the FP64 multigrid right-hand side
+// b = -rho/eps0 with the electrode potentials folded in (ghost 2 phi_b -
+// phi_1 at z faces: -2 phi_b / h^2).
 __global__ void k_rho(Params P, const int64_t* __restrict__ Npos, const int64_t* __restrict__ Nneg,
                       const unsigned long long* __restrict__ ne_fix, int64_t* __restrict__ rho,
                       double* __restrict__ rhs, uint64_t G, double qscale, double bc_top,
                       Counters* __restrict__ ctr)
 {
+    unsigned long long amax = 0;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
         const long long dq = Npos[g] - Nneg[g];
         const unsigned long long ne = ne_fix[g];
@@ -475,11 +478,21 @@ __global__ void k_rho(Params P, const int64_t* __restrict__ Npos, const int64_t*
         if (dq >= lim || dq <= -lim || ne >= (1ull << 62)) atomicOr(&ctr->err, DERR_OVERFLOW);
         const long long rf = dq * (1ll << (3 * P.frac_bits)) - (long long)ne;
         rho[g] = rf;
-        const int k = (int)((g >> (2 * P.log2n)) & (uint64_t)(P.n - 1));
-        double b = -((double)rf * qscale);
-        if (k == P.n - 1) b = b - bc_top;
-        rhs[g] = b;
+        const unsigned long long a = (unsigned long long)(rf < 0 ? -rf : rf);
+        amax = a > amax ? a : amax;
+        if (rhs) {
+            const int k = (int)((g >> (2 * P.log2n)) & (uint64_t)(P.n - 1));
+            double b = -((double)rf * qscale);
+            if (k == P.n - 1) b = b - bc_top;
+            rhs[g] = b;
+        }
     }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, amax, d);
+        amax = o > amax ? o : amax;
+    }
+    if ((threadIdx.x & 31) == 0 && amax) atomicMax(&ctr->rho_absmax, amax);
 }
 
 // ------------------------------------------------------------------ KMC
@@ -758,6 +771,12 @@ __device__ __forceinline__ float clamp_off(double v)
     if (f >= 1.0f) f = 0x1.fffffep-1f;
     return f;
 }
+__device__ __forceinline__ float clamp_offf(float f)
+{
+    if (!(f >= 0.0f)) f = 0.0f;
+    if (f >= 1.0f) f = 0x1.fffffep-1f;
+    return f;
+}
 
 // ------------------------------------------------------------------ photons
 // One superphoton (cell c, slot j): emission point, kappa, distance, direction.
@@ -888,13 +907,51 @@ __global__ void k_photo_place(const Photo* __restrict__ photos, const Counters* 
 }
 
 // ------------------------------------------------------------------ merge scan
-constexpr int MERGE_WARPS = 8;
-constexpr int MERGE_LANE_NODES = 8;  // levels with at least this many nodes split one node per lane
+// Per-warp scratch of the merge of one cell (all node arrays for T = ppc
+// nodes, element lists for `cap` elements): byte offsets from the base.
+struct MLayout {
+    uint32_t cur, tmp, nW, nC, keys, nlo, nhi, nA, nB, nb, nb2, npm, nsh, nid, nid2, nnd, nax, nfl, bytes;
+};
+__host__ __device__ inline uint32_t ml_take(uint32_t& o, uint32_t bytes)
+{
+    const uint32_t r = o;
+    o += (bytes + 15u) & ~15u;
+    return r;
+}
+__host__ __device__ inline MLayout merge_layout(uint32_t cap, uint32_t T, uint32_t esize, uint32_t ksize)
+{
+    MLayout L;
+    uint32_t o = 0;
+    L.cur = ml_take(o, cap * esize);
+    L.tmp = ml_take(o, cap * esize);
+    L.nW = ml_take(o, T * 8);
+    L.nC = ml_take(o, T * 8);
+    L.keys = ml_take(o, cap * ksize);
+    L.nlo = ml_take(o, 3 * T * ksize);
+    L.nhi = ml_take(o, 3 * T * ksize);
+    L.nA = ml_take(o, T * 4);
+    L.nB = ml_take(o, T * 4);
+    L.nb = ml_take(o, (T + 1) * 4);
+    L.nb2 = ml_take(o, (T + 1) * 4);
+    L.npm = ml_take(o, T * 4);
+    L.nsh = ml_take(o, T * 4);
+    L.nid = ml_take(o, cap * 2);
+    L.nid2 = ml_take(o, cap * 2);
+    L.nnd = ml_take(o, T * 2);
+    L.nax = ml_take(o, T);
+    L.nfl = ml_take(o, T);
+    L.bytes = o;
+    return L;
+}
+
+// Merge tiers by list capacity M + ppc (a level adds at most one element
+// per node): tier 0 and 1 in shared memory (warps per block NW0 / NW1),
+// tier 2 in the global work area.
+constexpr uint32_t MERGE_CAP0 = 128, MERGE_CAP1 = 512;
+constexpr int MERGE_NW0 = 4, MERGE_NW1 = 2;
+
 // Per cell: W = X_e + dN + photo weight -> min(W, ppc) leaves; photo offsets;
-// work elements M + ppc (global scratch only for lists too long for the
-// warp's shared-memory buffers).
-
-
+// work-area units (32 B) for tier-2 cells; the tier lists.
 struct MergeScanOp {
     const unsigned long long* Xe;
     const int64_t* fired;
@@ -904,12 +961,12 @@ struct MergeScanOp {
     uint32_t* out_start;
     uint32_t* photo_off;
     uint64_t* work_off;
-    uint32_t* small_list;     // non-empty cells whose list fits the small shared buffers
-    uint32_t* mid_list;       // ... the large shared buffers
-    uint32_t* big_list;       // the others
-    uint32_t* list_n;         // [2]: lengths
+    uint32_t* small_list;     // non-empty cells of tier 0
+    uint32_t* mid_list;       // ... tier 1
+    uint32_t* big_list;       // ... tier 2
+    uint32_t* list_n;         // [3]: lengths
     uint64_t G;
-    int ppc, n_new, cap, cap_mid;
+    int ppc, n_new, esize, ksize;
     __device__ void load(uint64_t g, long long v[6]) const
     {
         const long long dN = fired[g] - fired[G + g];
@@ -917,8 +974,11 @@ struct MergeScanOp {
         v[0] = W < ppc ? W : ppc;
         v[1] = photo_cnt[g];
         const long long M = (long long)(cs[g + 1] - cs[g]) + (dN > 0 ? (dN < n_new ? dN : n_new) : 0) + photo_cnt[g];
-        const int tier = M + ppc <= cap ? 0 : (M + ppc <= cap_mid ? 1 : 2);
-        v[2] = (M > 0 && tier == 2) ? (M + ppc) : 0;
+        const long long S = M + ppc;
+        const int tier = S <= MERGE_CAP0 ? 0 : (S <= MERGE_CAP1 ? 1 : 2);
+        v[2] = (v[0] > 0 && tier == 2)
+                   ? ((long long)merge_layout((uint32_t)S, (uint32_t)ppc, (uint32_t)esize, (uint32_t)ksize).bytes + 31) / 32
+                   : 0;
         v[3] = (v[0] > 0 && tier == 0) ? 1 : 0;
         v[4] = (v[0] > 0 && tier == 1) ? 1 : 0;
         v[5] = (v[0] > 0 && tier == 2) ? 1 : 0;
@@ -955,28 +1015,8 @@ struct MP {           // merge work element (FP64 form)
     uint32_t pad;
 };
 
-__device__ __forceinline__ double mp_coord(const MP& p, int a) { return a == 0 ? p.x : (a == 1 ? p.y : p.z); }
-__device__ __forceinline__ double mp_coord(const MP32& p, int a)
-{
-    return (double)(a == 0 ? p.x : (a == 1 ? p.y : p.z));
-}
-
-// Merge tiers: cells whose lists fit small shared buffers (8 warps per
-// block), larger shared buffers (2 warps per block), or global scratch.
-template <bool MX> struct MergeElem { using T = MP; static constexpr int CAP = 128; static constexpr int CAP_MID = 512; };
-template <> struct MergeElem<true> { using T = MP32; static constexpr int CAP = 176; static constexpr int CAP_MID = 1024; };
-constexpr int MERGE_WARPS_MID = 2;
-template <bool MX, int TIER> struct MergeTier {
-    static constexpr int CAP = TIER == 0 ? MergeElem<MX>::CAP : (TIER == 1 ? MergeElem<MX>::CAP_MID : 0);
-    static constexpr int NW = TIER == 1 ? MERGE_WARPS_MID : MERGE_WARPS;
-};
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
-{
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    return v;
-}
+template <class E> struct EKey { using K = unsigned long long; };
+template <> struct EKey<MP32> { using K = uint32_t; };
 
 // Order-preserving integer keys of coordinates: the tree compares keys with
 // integer instructions (FP64 comparisons run at a small fraction of the FP32
@@ -1042,416 +1082,407 @@ __device__ __forceinline__ int widest_axis(const typename ET<E>::K lo[3], const 
     return axis;
 }
 
-// Stable rank sort of m <= 32 NQ elements by (key, position): each lane
-// keeps the keys of its elements j = lane + 32 q in registers and scans all
-// k with broadcast loads.
-template <class E, int NQ>
-__device__ __forceinline__ void rank_sort_reg(const E* src, uint32_t m, int axis, E* tmp)
+// Minimum / maximum over a group of contiguous lanes (a node's elements in
+// one chunk of 32); the result is valid at the group's last lane.
+__device__ __forceinline__ uint32_t grp_min(unsigned grp, uint32_t v, unsigned) { return __reduce_min_sync(grp, v); }
+__device__ __forceinline__ uint32_t grp_max(unsigned grp, uint32_t v, unsigned) { return __reduce_max_sync(grp, v); }
+__device__ __forceinline__ unsigned long long grp_min(unsigned grp, unsigned long long v, unsigned lane)
 {
-    using K = typename ET<E>::K;
-    const unsigned lane = lane_id();
-    K cj[NQ];
-    uint32_t rk[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const uint32_t j = lane + 32u * q;
-        cj[q] = j < m ? ET<E>::key(src[j], axis) : (K)0;
-        rk[q] = 0;
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long o = __shfl_up_sync(0xffffffffu, v, d);
+        if ((int)lane >= d && ((grp >> (lane - d)) & 1u)) v = o < v ? o : v;
     }
-    for (uint32_t k = 0; k < m; ++k) {
-        const K ck = ET<E>::key(src[k], axis);
+    return v;
+}
+__device__ __forceinline__ unsigned long long grp_max(unsigned grp, unsigned long long v, unsigned lane)
+{
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const uint32_t j = lane + 32u * q;
-            rk[q] += (ck < cj[q]) || (ck == cj[q] && k < j);
-        }
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long o = __shfl_up_sync(0xffffffffu, v, d);
+        if ((int)lane >= d && ((grp >> (lane - d)) & 1u)) v = o > v ? o : v;
     }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const uint32_t j = lane + 32u * q;
-        if (j < m) tmp[rk[q]] = src[j];
-    }
+    return v;
 }
 
-// Splits node src[0..m) of weight W (>= 2) into dst: left part then right
-// part.  tmp holds the node sorted along the split axis.  Returns nl.
-template <class E>
-__device__ uint32_t split_node(const E* src, uint32_t m, unsigned long long W, E* tmp, E* dst, uint32_t* nr_out)
-{
-    using K = typename ET<E>::K;
-    const unsigned lane = lane_id();
-    K lo[3], hi[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) { lo[a] = (K)~(K)0; hi[a] = (K)0; }
-    for (uint32_t j = lane; j < m; j += 32) {
-        const E p = src[j];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const K v = ET<E>::key(p, a);
-            lo[a] = v < lo[a] ? v : lo[a];
-            hi[a] = v > hi[a] ? v : hi[a];
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) { lo[a] = ET<E>::wmin(lo[a]); hi[a] = ET<E>::wmax(hi[a]); }
-    const int axis = widest_axis<E>(lo, hi);
-    if (m <= 512) {
-        switch ((m + 31) / 32) {
-        case 1: rank_sort_reg<E, 1>(src, m, axis, tmp); break;
-        case 2: rank_sort_reg<E, 2>(src, m, axis, tmp); break;
-        case 3: rank_sort_reg<E, 3>(src, m, axis, tmp); break;
-        case 4: rank_sort_reg<E, 4>(src, m, axis, tmp); break;
-        case 5: rank_sort_reg<E, 5>(src, m, axis, tmp); break;
-        case 6: rank_sort_reg<E, 6>(src, m, axis, tmp); break;
-        case 7: rank_sort_reg<E, 7>(src, m, axis, tmp); break;
-        case 8: rank_sort_reg<E, 8>(src, m, axis, tmp); break;
-        case 9: case 10: rank_sort_reg<E, 10>(src, m, axis, tmp); break;
-        case 11: case 12: rank_sort_reg<E, 12>(src, m, axis, tmp); break;
-        default: rank_sort_reg<E, 16>(src, m, axis, tmp); break;
-        }
-    } else {
-        for (uint32_t j = lane; j < m; j += 32) {
-            const E pj = src[j];
-            const K cj = ET<E>::key(pj, axis);
-            uint32_t rank = 0;
-            for (uint32_t k = 0; k < m; ++k) {
-                const K ck = ET<E>::key(src[k], axis);
-                rank += (ck < cj) || (ck == cj && k < j);
-            }
-            tmp[rank] = pj;
-        }
-    }
-    __syncwarp();
-    // weighted median p': first index with 2 C_p > W
-    unsigned long long carry = 0, Cpm = 0;
-    uint32_t pm = m - 1;
-    for (uint32_t base = 0; base < m; base += 32) {
-        const uint32_t j = base + lane;
-        unsigned long long v = j < m ? tmp[j].w : 0ull;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, v, d);
-            if ((int)lane >= d) v += y;
-        }
-        const unsigned long long Cj = carry + v;
-        const unsigned bal = __ballot_sync(0xffffffffu, j < m && 2ull * Cj > W);
-        if (bal) {
-            const int src_lane = __ffs(bal) - 1;
-            pm = base + src_lane;
-            Cpm = __shfl_sync(0xffffffffu, Cj, src_lane);
-            break;
-        }
-        carry = __shfl_sync(0xffffffffu, Cj, 31);
-    }
-    const E med = tmp[pm];
-    const unsigned long long WL = Cpm - med.w;
-    const unsigned long long WR = W - Cpm;
-    bool left_med, right_med;
-    E ml = med, mr = med;
-    if (med.w == 1) {
-        left_med = WL <= WR;
-        right_med = !left_med;
-    } else {
-        const unsigned long long a = (W + 1) / 2 - WL;
-        const unsigned long long b = med.w - a;
-        ml.w = (uint32_t)a;
-        mr.w = (uint32_t)b;
-        left_med = a > 0;
-        right_med = b > 0;
-    }
-    const uint32_t nl = pm + (left_med ? 1u : 0u);
-    for (uint32_t j = lane; j < pm; j += 32) dst[j] = tmp[j];
-    if (lane == 0 && left_med) dst[pm] = ml;
-    const uint32_t roff = nl;
-    const uint32_t rstart = right_med ? 1u : 0u;
-    if (lane == 0 && right_med) dst[roff] = mr;
-    for (uint32_t j = pm + 1 + lane; j < m; j += 32) dst[roff + rstart + (j - pm - 1)] = tmp[j];
-    __syncwarp();
-    *nr_out = rstart + (m - pm - 1);
-    return nl;
-}
+constexpr uint8_t NO_SPLIT = 0xff;
 
-// One node per lane: stable insertion sort of the node's slice along its
-// widest axis (in place), weighted median, child sizes.  Returns the number
-// of output elements; nl_out receives the left child's size.
-template <class E>
-__device__ __forceinline__ uint32_t lane_split_prepare(E* node, uint32_t m, unsigned long long W, uint32_t& pm_out,
-                                                       E& ml, E& mr, uint32_t& nl_out, bool& lmed, bool& rmed)
-{
-    using K = typename ET<E>::K;
-    K lo[3], hi[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) { lo[a] = ET<E>::key(node[0], a); hi[a] = lo[a]; }
-    for (uint32_t q = 1; q < m; ++q) {
-        const E e = node[q];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const K v = ET<E>::key(e, a);
-            lo[a] = v < lo[a] ? v : lo[a];
-            hi[a] = v > hi[a] ? v : hi[a];
-        }
-    }
-    const int axis = widest_axis<E>(lo, hi);
-    for (uint32_t q = 1; q < m; ++q) {
-        const E kv = node[q];
-        const K c = ET<E>::key(kv, axis);
-        int p = (int)q - 1;
-        while (p >= 0 && ET<E>::key(node[p], axis) > c) {
-            node[p + 1] = node[p];
-            --p;
-        }
-        node[p + 1] = kv;
-    }
-    unsigned long long C = 0;
-    uint32_t pm = m - 1;
-    for (uint32_t q = 0; q < m; ++q) {
-        C += node[q].w;
-        if (2ull * C > W) { pm = q; break; }
-    }
-    const E med = node[pm];
-    const unsigned long long WL = C - med.w, WR = W - C;
-    ml = med; mr = med;
-    if (med.w == 1) {
-        lmed = WL <= WR;
-        rmed = !lmed;
-    } else {
-        const unsigned long long a = (W + 1) / 2 - WL, b = med.w - a;
-        ml.w = (uint32_t)a;
-        mr.w = (uint32_t)b;
-        lmed = a > 0;
-        rmed = b > 0;
-    }
-    pm_out = pm;
-    nl_out = pm + (lmed ? 1u : 0u);
-    return nl_out + (rmed ? 1u : 0u) + (m - pm - 1);
-}
-
-// TIER 0 / 1: cells whose list fits the warp's small / large shared
-// buffers; TIER 2: the others, with their buffers in the global work area.
-template <bool MX, int TIER>
-__global__ void __launch_bounds__(MergeTier<MX, TIER>::NW * 32) k_merge(
+// Merge/split of whole cells, one warp per cell, all nodes of a tree level
+// at once.  The cell's list (existing particles with w > 0 in canonical
+// order, then new ones in (source cell, products before photoelectrons,
+// slot) order) is split level by level exactly as specified: every node of
+// weight >= 2 is sorted stably along the widest axis of its bounding box
+// (ties keep the node's current order), cut at the weighted median (first
+// element with 2 C > W), a unit-weight median joins the lighter side (left
+// on ties) and a heavier one is divided ceil(W/2) - W_L : rest.  Leaves are
+// the nodes after log2(ppc) levels.  Per level the warp runs element-
+// parallel passes (bounding boxes by group reductions, a rank sort, a
+// segmented weight scan, a scatter into the next level's list) and node-
+// parallel passes (axis, median bookkeeping).  GLOBAL: the scratch lives in
+// the work area (cells too long for shared memory).
+template <class E, bool GLOBAL>
+__global__ void __launch_bounds__(128) k_merge_lv(
     Params P, const P64* __restrict__ A, const P32* __restrict__ A32, const uint32_t* __restrict__ cs,
     const int64_t* __restrict__ fired, const Photo* __restrict__ photos, const uint32_t* __restrict__ photo_sorted,
     const uint32_t* __restrict__ photo_off, const uint32_t* __restrict__ out_start,
-    const uint64_t* __restrict__ work_off, typename MergeElem<MX>::T* __restrict__ work, uint64_t work_cap,
-    P64* __restrict__ out,
-    P32* __restrict__ out32, uint32_t* __restrict__ cout, uint64_t G, uint32_t cap, uint32_t photo_cap,
-    const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_n, Counters* __restrict__ ctr)
+    const uint64_t* __restrict__ work_off, unsigned char* __restrict__ work, uint64_t work_cap,
+    P64* __restrict__ out, P32* __restrict__ out32, uint32_t* __restrict__ cout, uint64_t G, uint32_t cap,
+    uint32_t photo_cap, const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_n, int tier,
+    uint32_t CAP, Counters* __restrict__ ctr)
 {
-    using MPT = typename MergeElem<MX>::T;
-    constexpr bool SMALL = TIER < 2;
-    constexpr int CAP = MergeTier<MX, TIER>::CAP > 0 ? MergeTier<MX, TIER>::CAP : 1;
-    constexpr int NW = MergeTier<MX, TIER>::NW;
-    extern __shared__ unsigned char merge_smem[];
-    MPT* sbuf = reinterpret_cast<MPT*>(merge_smem);
-    // node boundaries: 2 x (ppc + 1) per warp after the element buffers
-    uint32_t* sbnd = reinterpret_cast<uint32_t*>(merge_smem + (SMALL ? sizeof(MPT) * 3 * CAP * NW : 0));
-    const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
-    const uint64_t gw = (uint64_t)blockIdx.x * NW + wid;
-    const uint64_t nwarps = (uint64_t)gridDim.x * NW;
+    constexpr bool MX = std::is_same<E, MP32>::value;
+    using K = typename EKey<E>::K;
+    extern __shared__ __align__(16) unsigned char msm[];
+    const unsigned lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int T = P.ppc;
-    const uint32_t ncells = list_n[TIER];
-    for (uint64_t li = gw; li < ncells; li += nwarps) {
-        {
-            const uint64_t g = list[li];
-            const int r = real_of(P, (uint32_t)g);
-            const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
-            const long long dN = fired[g] - fired[G + g];
-            const uint32_t e0 = cs[g], e1 = cs[g + 1];
-            const uint32_t mprod = dN > 0 ? (uint32_t)(dN < P.n_new ? dN : P.n_new) : 0u;
-            const uint32_t p0 = photo_off[g], np = photo_off[g + 1] - p0;
-            const uint32_t Mmax = (e1 - e0) + mprod + np;
-            if ((uint64_t)p0 + np > photo_cap || out_start[g + 1] > cap) {
+    const uint32_t ncells = list_n[tier];
+    unsigned long long t_cells = 0, t_el = 0, t_sq = 0, t_max = 0;
+    for (uint32_t li = blockIdx.x * nw + wid; li < ncells; li += gridDim.x * nw) {
+        const uint64_t g = list[li];
+        const int r = real_of(P, (uint32_t)g);
+        const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
+        const long long dN = fired[g] - fired[G + g];
+        const uint32_t e0 = cs[g], e1 = cs[g + 1];
+        const uint32_t mprod = dN > 0 ? (uint32_t)(dN < P.n_new ? dN : P.n_new) : 0u;
+        const uint32_t p0 = photo_off[g], np = photo_off[g + 1] - p0;
+        const uint32_t Mmax = (e1 - e0) + mprod + np;
+        if ((uint64_t)p0 + np > photo_cap || out_start[g + 1] > cap) {
+            if (lane == 0) atomicOr(&ctr->err, DERR_CAPACITY);
+            continue;
+        }
+        MLayout L;
+        unsigned char* base;
+        if constexpr (GLOBAL) {
+            L = merge_layout(Mmax + T, T, sizeof(E), sizeof(K));
+            if (work_off[g] * 32 + L.bytes > work_cap * 32) {
                 if (lane == 0) atomicOr(&ctr->err, DERR_CAPACITY);
                 continue;
             }
-            MPT *cur, *nxt, *tmp;
-            if (SMALL) {
-                cur = sbuf + (size_t)wid * 3 * CAP;
-                nxt = cur + CAP;
-                tmp = nxt + CAP;
-            } else {
-                const uint64_t S = (uint64_t)Mmax + T;
-                if (work_off[g] + S > work_cap) {
-                    if (lane == 0) atomicOr(&ctr->err, DERR_CAPACITY);
-                    continue;
+            base = work + work_off[g] * 32;
+        } else {
+            if (Mmax + T > CAP) {
+                if (lane == 0) atomicOr(&ctr->err, DERR_INTERNAL);
+                continue;
+            }
+            L = merge_layout(CAP, T, sizeof(E), sizeof(K));
+            base = msm + (size_t)wid * L.bytes;
+        }
+        E* cur = reinterpret_cast<E*>(base + L.cur);
+        E* tmp = reinterpret_cast<E*>(base + L.tmp);
+        unsigned long long* nW = reinterpret_cast<unsigned long long*>(base + L.nW);
+        unsigned long long* nC = reinterpret_cast<unsigned long long*>(base + L.nC);
+        K* keys = reinterpret_cast<K*>(base + L.keys);
+        K* nlo = reinterpret_cast<K*>(base + L.nlo);
+        K* nhi = reinterpret_cast<K*>(base + L.nhi);
+        uint32_t* nA = reinterpret_cast<uint32_t*>(base + L.nA);
+        uint32_t* nB = reinterpret_cast<uint32_t*>(base + L.nB);
+        uint32_t* nb = reinterpret_cast<uint32_t*>(base + L.nb);
+        uint32_t* nb2 = reinterpret_cast<uint32_t*>(base + L.nb2);
+        uint32_t* npm = reinterpret_cast<uint32_t*>(base + L.npm);
+        uint32_t* nsh = reinterpret_cast<uint32_t*>(base + L.nsh);
+        uint16_t* nid = reinterpret_cast<uint16_t*>(base + L.nid);
+        uint16_t* nid2 = reinterpret_cast<uint16_t*>(base + L.nid2);
+        uint16_t* nnd = reinterpret_cast<uint16_t*>(base + L.nnd);
+        uint8_t* nax = reinterpret_cast<uint8_t*>(base + L.nax);
+        uint8_t* nfl = reinterpret_cast<uint8_t*>(base + L.nfl);
+
+        // ---- gather: existing particles with w > 0 (canonical order)
+        uint32_t M = 0;
+        for (uint32_t b = e0; b < e1; b += 32) {
+            const uint32_t q = b + lane;
+            E e;
+            bool ok = false;
+            if (q < e1) {
+                if constexpr (MX) {
+                    const P32 p = A32[q];
+                    e.x = p.ox; e.y = p.oy; e.z = p.oz; e.w = p.w;
+                } else {
+                    const P64 p = ld_p64(A + q);
+                    e.x = p.x; e.y = p.y; e.z = p.z; e.w = p.w; e.pad = 0;
                 }
-                MPT* base = work + 3 * work_off[g];
-                cur = base; nxt = base + S; tmp = base + 2 * S;
+                ok = e.w > 0;
             }
-            // gather: existing (w > 0, canonical order), then new particles in
-            // (source cell, products before photoelectrons, slot) order
-            uint32_t M = 0;
-            for (uint32_t b = e0; b < e1; b += 32) {
-                const uint32_t q = b + lane;
-                MPT e;
-                bool ok = false;
-                if (q < e1) {
-                    if constexpr (MX) {
-                        const P32 p = A32[q];
-                        e.x = p.ox; e.y = p.oy; e.z = p.oz; e.w = p.w;
-                    } else {
-                        const P64 p = ld_p64(A + q);
-                        e.x = p.x; e.y = p.y; e.z = p.z; e.w = p.w; e.pad = 0;
-                    }
-                    ok = e.w > 0;
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, ok);
-                if (ok) cur[M + __popc(bal & ((1u << lane) - 1u))] = e;
-                M += __popc(bal);
-            }
-            // photoelectrons: rank by (source, slot); the keys are staged in
-            // the (still unused) tmp buffer so the ranking reads shared memory
-            uint32_t n_lt = 0;
-            unsigned long long* keys = reinterpret_cast<unsigned long long*>(tmp);
-            for (uint32_t j = lane; j < np; j += 32) {
-                const Photo pj = photos[photo_sorted[p0 + j]];
-                keys[j] = ((unsigned long long)pj.src << 8) | pj.slot;
-                n_lt += pj.src < c;
-                MPT e;
-                e.x = pj.x; e.y = pj.y; e.z = pj.z; e.w = pj.w;
-                if constexpr (!MX) e.pad = 0;
-                nxt[j] = e;                           // unranked, in slot order
-            }
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) n_lt += __shfl_xor_sync(0xffffffffu, n_lt, d);
-            __syncwarp();
-            for (uint32_t j = lane; j < np; j += 32) {
-                const unsigned long long kj = keys[j];
-                uint32_t rank = 0;
-                for (uint32_t k = 0; k < np; ++k) rank += keys[k] < kj;
-                cur[M + (rank < n_lt ? rank : rank + mprod)] = nxt[j];
-            }
-            __syncwarp();
-            if (mprod) {
-                const long long wq = dN / (long long)mprod, rem = dN % (long long)mprod;
-                const int ijk[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
-                                     (int)(c >> (2 * P.log2n)) };
-                for (uint32_t j = lane; j < mprod; j += 32) {
-                    Stream s(seed_of(P, r), c, P.step, TAG_PRODUCT, j);
-                    MPT e;
-                    double X[3];
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (ok) cur[M + __popc(bal & ((1u << lane) - 1u))] = e;
+            M += __popc(bal);
+        }
+        // photoelectrons ranked by (source cell, slot): keys staged in tmp
+        unsigned long long* pkey = reinterpret_cast<unsigned long long*>(tmp);
+        uint32_t n_lt = 0;
+        for (uint32_t j = lane; j < np; j += 32) {
+            const Photo& pj = photos[photo_sorted[p0 + j]];
+            pkey[j] = ((unsigned long long)pj.src << 8) | pj.slot;
+            n_lt += pj.src < c;
+        }
+        n_lt = __reduce_add_sync(0xffffffffu, n_lt);
+        __syncwarp();
+        for (uint32_t j = lane; j < np; j += 32) {
+            const unsigned long long kj = pkey[j];
+            uint32_t rank = 0;
+            for (uint32_t k = 0; k < np; ++k) rank += pkey[k] < kj;
+            const Photo pj = photos[photo_sorted[p0 + j]];
+            E e;
+            e.x = pj.x; e.y = pj.y; e.z = pj.z; e.w = pj.w;
+            if constexpr (!MX) e.pad = 0;
+            cur[M + (rank < n_lt ? rank : rank + mprod)] = e;
+        }
+        // products: uniform in the cell, the remainder on the first
+        if (mprod) {
+            const long long wq = dN / (long long)mprod, rem = dN % (long long)mprod;
+            const int ijk[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
+                                 (int)(c >> (2 * P.log2n)) };
+            for (uint32_t j = lane; j < mprod; j += 32) {
+                Stream st(seed_of(P, r), c, P.step, TAG_PRODUCT, j);
+                E e;
+                if constexpr (MX) {
+                    // FP32 uniforms from the high words of the FP64 ones
+                    float X[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        const double u = s.uniform();
-                        if constexpr (MX) X[a] = (double)clamp_off(u);
-                        else X[a] = P.lo[a] + ((double)ijk[a] + u) * P.h[a];
+                        X[a] = uniform_f32(st.u32());
+                        (void)st.u32();
                     }
                     e.x = X[0]; e.y = X[1]; e.z = X[2];
-                    const long long wj = wq + (j == 0 ? rem : 0);
-                    if (wj > 0xffffffffll) atomicOr(&ctr->err, DERR_OVERFLOW);
-                    e.w = (uint32_t)wj;
-                    if constexpr (!MX) e.pad = 0;
-                    cur[M + n_lt + j] = e;
-                }
-            }
-            M += mprod + np;
-            __syncwarp();
-            if (lane == 0) {
-                atomicAdd(&ctr->merge_cells, 1ull);
-                atomicAdd(&ctr->merge_elems, (unsigned long long)M);
-                atomicAdd(&ctr->merge_elems2, (unsigned long long)M * M);
-                atomicMax(&ctr->merge_maxm, (unsigned long long)M);
-            }
-            // level-synchronous median splits up to T leaves
-            uint32_t* bnd = sbnd + (size_t)wid * 2 * (T + 1);
-            uint32_t* bnd2 = bnd + (T + 1);
-            if (lane == 0) { bnd[0] = 0; bnd[1] = M; }
-            __syncwarp();
-            int nnodes = 1;
-            for (int level = 1; level < T; level *= 2) {
-                if (lane == 0) bnd2[0] = 0;
-                // one node per lane once the nodes are many or small
-                if (nnodes >= MERGE_LANE_NODES || (int)bnd[nnodes] <= 12 * nnodes) {
-                    // one node per lane; nodes in rounds of 32
-                    uint32_t fill = 0;
-                    int nn = 0;
-                    for (int d0 = 0; d0 < nnodes; d0 += 32) {
-                        const int d = d0 + (int)lane;
-                        uint32_t s0 = 0, m = 0, outn = 0, pm = 0, nl = 0;
-                        unsigned long long W = 0;
-                        bool split = false, lmed = false, rmed = false;
-                        MPT ml, mr;
-                        if (d < nnodes) {
-                            s0 = bnd[d];
-                            m = bnd[d + 1] - s0;
-                            for (uint32_t q = 0; q < m; ++q) W += cur[s0 + q].w;
-                            split = W >= 2;
-                            outn = split ? lane_split_prepare(cur + s0, m, W, pm, ml, mr, nl, lmed, rmed) : m;
-                        }
-                        // exclusive scans over the round: output elements, child nodes
-                        uint32_t o = outn, ch = d < nnodes ? (split ? 2u : 1u) : 0u;
+                } else {
+                    double X[3];
 #pragma unroll
-                        for (int k = 1; k < 32; k <<= 1) {
-                            const uint32_t yo = __shfl_up_sync(0xffffffffu, o, k);
-                            const uint32_t yc = __shfl_up_sync(0xffffffffu, ch, k);
-                            if ((int)lane >= k) { o += yo; ch += yc; }
-                        }
-                        const uint32_t off = fill + o - outn;
-                        const int cidx = nn + (int)(ch - (d < nnodes ? (split ? 2u : 1u) : 0u));
-                        if (d < nnodes) {
-                            MPT* dst = nxt + off;
-                            if (split) {
-                                for (uint32_t q = 0; q < pm; ++q) dst[q] = cur[s0 + q];
-                                if (lmed) dst[pm] = ml;
-                                uint32_t r0 = nl;
-                                if (rmed) dst[r0++] = mr;
-                                for (uint32_t q = pm + 1; q < m; ++q) dst[r0++] = cur[s0 + q];
-                                bnd2[cidx + 1] = off + nl;
-                                bnd2[cidx + 2] = off + outn;
-                            } else {
-                                for (uint32_t q = 0; q < m; ++q) dst[q] = cur[s0 + q];
-                                bnd2[cidx + 1] = off + m;
-                            }
-                        }
-                        fill += __shfl_sync(0xffffffffu, o, 31);
-                        nn += (int)__shfl_sync(0xffffffffu, ch, 31);
+                    for (int a = 0; a < 3; ++a) X[a] = P.lo[a] + ((double)ijk[a] + st.uniform()) * P.h[a];
+                    e.x = X[0]; e.y = X[1]; e.z = X[2];
+                }
+                const long long wj = wq + (j == 0 ? rem : 0);
+                if (wj > 0xffffffffll) atomicOr(&ctr->err, DERR_OVERFLOW);
+                e.w = (uint32_t)wj;
+                if constexpr (!MX) e.pad = 0;
+                cur[M + n_lt + j] = e;
+            }
+        }
+        M += mprod + np;
+        if (lane == 0) {
+            t_cells += 1; t_el += M; t_sq += (unsigned long long)M * M; t_max = M > t_max ? M : t_max;
+            nb[0] = 0;
+            nb[1] = M;
+        }
+        for (uint32_t j = lane; j < M; j += 32) nid[j] = 0;
+        uint32_t n = M;
+        int nnodes = 1;
+        __syncwarp();
+
+        for (int level = 1; level < T; level *= 2) {
+            // ---- node weights and bounding boxes
+            for (int d = lane; d < nnodes; d += 32) {
+                nW[d] = 0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) { nlo[3 * d + a] = (K)~(K)0; nhi[3 * d + a] = (K)0; }
+            }
+            __syncwarp();
+            for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+                const uint32_t j = b0 + lane;
+                const bool ok = j < n;
+                const uint32_t d = ok ? nid[j] : 0xffffu;
+                const unsigned grp = __match_any_sync(0xffffffffu, d);
+                const bool last = (int)lane == 31 - __clz(grp);
+                E e;
+                if (ok) e = cur[j];
+                else { e.x = 0; e.y = 0; e.z = 0; e.w = 0; }
+                const uint32_t wlo = __reduce_add_sync(grp, e.w & 0xffffu);
+                const uint32_t whi = __reduce_add_sync(grp, e.w >> 16);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const K v = ET<E>::key(e, a);
+                    const K mn = grp_min(grp, v, lane), mx = grp_max(grp, v, lane);
+                    if (ok && last) {
+                        atomicMin(nlo + 3 * d + a, mn);
+                        atomicMax(nhi + 3 * d + a, mx);
                     }
-                    __syncwarp();
-                    MPT* t = cur; cur = nxt; nxt = t;
-                    uint32_t* tb = bnd; bnd = bnd2; bnd2 = tb;
-                    nnodes = nn;
-                    __syncwarp();
+                }
+                if (ok && last) atomicAdd(nW + d, ((unsigned long long)whi << 16) + wlo);
+            }
+            __syncwarp();
+            // ---- split axis per node (NO_SPLIT below weight 2)
+            bool any_split = false;
+            for (int d = lane; d < nnodes; d += 32) {
+                K lo[3], hi[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) { lo[a] = nlo[3 * d + a]; hi[a] = nhi[3 * d + a]; }
+                const bool sp = nW[d] >= 2;
+                nax[d] = sp ? (uint8_t)widest_axis<E>(lo, hi) : NO_SPLIT;
+                any_split |= sp;
+            }
+            // no node of weight >= 2: this and all further levels keep the list
+            if (!__any_sync(0xffffffffu, any_split)) break;
+            __syncwarp();
+            for (uint32_t j = lane; j < n; j += 32) {
+                const uint8_t a = nax[nid[j]];
+                keys[j] = a == NO_SPLIT ? (K)0 : ET<E>::key(cur[j], a);
+            }
+            __syncwarp();
+            // ---- stable rank sort within each node: cur -> tmp
+            for (uint32_t j = lane; j < n; j += 32) {
+                const uint32_t d = nid[j];
+                if (nax[d] == NO_SPLIT) { tmp[j] = cur[j]; continue; }
+                const uint32_t s0 = nb[d], s1 = nb[d + 1];
+                const K kj = keys[j];
+                uint32_t rk = 0;
+                for (uint32_t k = s0; k < j; ++k) rk += keys[k] <= kj;
+                for (uint32_t k = j + 1; k < s1; ++k) rk += keys[k] < kj;
+                tmp[s0 + rk] = cur[j];
+            }
+            __syncwarp();
+            // ---- weighted median: segmented inclusive weight scan in sorted order
+            unsigned long long carry = 0;
+            uint32_t carry_d = 0xffffffffu;
+            for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+                const uint32_t j = b0 + lane;
+                const bool ok = j < n;
+                const uint32_t d = ok ? nid[j] : 0xffffu;
+                const unsigned grp = __match_any_sync(0xffffffffu, d);
+                const unsigned long long w = ok ? tmp[j].w : 0ull;
+                unsigned long long v = w;
+#pragma unroll
+                for (int k = 1; k < 32; k <<= 1) {
+                    const unsigned long long o = __shfl_up_sync(0xffffffffu, v, k);
+                    if ((int)lane >= k && ((grp >> (lane - k)) & 1u)) v += o;
+                }
+                if (d == carry_d) v += carry;
+                if (ok && nax[d] != NO_SPLIT) {
+                    const unsigned long long W = nW[d];
+                    if (2ull * v > W && 2ull * (v - w) <= W) {
+                        npm[d] = j - nb[d];
+                        nC[d] = v;
+                    }
+                }
+                carry = __shfl_sync(0xffffffffu, v, 31);
+                carry_d = __shfl_sync(0xffffffffu, d, 31);
+            }
+            __syncwarp();
+            // ---- per node: median rule, child layout of the next level
+            uint32_t ex_c = 0, nd_c = 0;
+            for (int d0 = 0; d0 < nnodes; d0 += 32) {
+                const int d = d0 + (int)lane;
+                uint32_t extra = 0, cnt = 0, pm = 0, a = 0, b = 0;
+                bool lm = false, rm = false, split = false;
+                if (d < nnodes) {
+                    split = nax[d] != NO_SPLIT;
+                    cnt = split ? 2u : 1u;
+                    if (split) {
+                        pm = npm[d];
+                        const unsigned long long W = nW[d], C = nC[d];
+                        const uint32_t wm = tmp[nb[d] + pm].w;
+                        const unsigned long long WL = C - wm, WR = W - C;
+                        if (wm == 1) {
+                            lm = WL <= WR;
+                            rm = !lm;
+                        } else {
+                            const unsigned long long aa = (W + 1) / 2 - WL;
+                            a = (uint32_t)aa;
+                            b = (uint32_t)(wm - aa);
+                            lm = a > 0;
+                            rm = b > 0;
+                        }
+                        extra = (lm ? 1u : 0u) + (rm ? 1u : 0u) - 1u;
+                    }
+                }
+                uint32_t ie = extra, ic = cnt;
+#pragma unroll
+                for (int k = 1; k < 32; k <<= 1) {
+                    const uint32_t ye = __shfl_up_sync(0xffffffffu, ie, k);
+                    const uint32_t yc = __shfl_up_sync(0xffffffffu, ic, k);
+                    if ((int)lane >= k) { ie += ye; ic += yc; }
+                }
+                if (d < nnodes) {
+                    const uint32_t sh = ex_c + ie - extra, ndi = nd_c + ic - cnt;
+                    nsh[d] = sh;
+                    nnd[d] = (uint16_t)ndi;
+                    nA[d] = a;
+                    nB[d] = b;
+                    nfl[d] = (uint8_t)((lm ? 1 : 0) | (rm ? 2 : 0));
+                    const uint32_t start = nb[d] + sh;
+                    nb2[ndi] = start;
+                    if (split) nb2[ndi + 1] = start + pm + (lm ? 1u : 0u);
+                }
+                ex_c += __shfl_sync(0xffffffffu, ie, 31);
+                nd_c += __shfl_sync(0xffffffffu, ic, 31);
+            }
+            if (lane == 0) nb2[nd_c] = n + ex_c;
+            __syncwarp();
+            // ---- scatter into the next level's list
+            for (uint32_t j = lane; j < n; j += 32) {
+                const uint32_t d = nid[j];
+                const uint32_t p = j - nb[d], start = nb[d] + nsh[d];
+                const uint16_t nd = nnd[d];
+                const E e = tmp[j];
+                if (nax[d] == NO_SPLIT) {
+                    cur[start + p] = e;
+                    nid2[start + p] = nd;
                     continue;
                 }
-                uint32_t fill = 0;
-                int nn = 0;
-                for (int d = 0; d < nnodes; ++d) {
-                    const uint32_t s0 = bnd[d], s1 = bnd[d + 1], m = s1 - s0;
-                    unsigned long long W = 0;
-                    for (uint32_t j = lane; j < m; j += 32) W += cur[s0 + j].w;
-                    W = warp_sum_u64(W);
-                    if (W >= 2) {
-                        uint32_t nr;
-                        const uint32_t nl = split_node(cur + s0, m, W, tmp, nxt + fill, &nr);
-                        fill += nl;
-                        if (lane == 0) bnd2[nn + 1] = fill;
-                        fill += nr;
-                        if (lane == 0) bnd2[nn + 2] = fill;
-                        nn += 2;
-                    } else {
-                        for (uint32_t j = lane; j < m; j += 32) nxt[fill + j] = cur[s0 + j];
-                        fill += m;
-                        if (lane == 0) bnd2[nn + 1] = fill;
-                        nn += 1;
+                const uint32_t pm = npm[d];
+                const uint32_t lm = nfl[d] & 1u, rm = nfl[d] >> 1;
+                if (p < pm) {
+                    cur[start + p] = e;
+                    nid2[start + p] = nd;
+                } else if (p > pm) {
+                    const uint32_t q = start + p + lm + rm - 1u;
+                    cur[q] = e;
+                    nid2[q] = (uint16_t)(nd + 1);
+                } else {
+                    if (lm) {
+                        E l = e;
+                        if (e.w != 1) l.w = nA[d];
+                        cur[start + pm] = l;
+                        nid2[start + pm] = nd;
                     }
-                    __syncwarp();
+                    if (rm) {
+                        E rr = e;
+                        if (e.w != 1) rr.w = nB[d];
+                        cur[start + pm + lm] = rr;
+                        nid2[start + pm + lm] = (uint16_t)(nd + 1);
+                    }
                 }
-                MPT* t = cur; cur = nxt; nxt = t;
-                uint32_t* tb = bnd; bnd = bnd2; bnd2 = tb;
-                nnodes = nn;
-                __syncwarp();
             }
-            // leaves: weight sum, weight-averaged position (list order)
-            const uint32_t o0 = out_start[g];
-            if ((uint32_t)nnodes != out_start[g + 1] - o0) {
-                if (lane == 0) atomicOr(&ctr->err, DERR_INTERNAL);
-            } else {
-                for (int d = lane; d < nnodes; d += 32) {
+            n += ex_c;
+            nnodes = (int)nd_c;
+            { uint32_t* t = nb; nb = nb2; nb2 = t; }
+            { uint16_t* t = nid; nid = nid2; nid2 = t; }
+            __syncwarp();
+        }
+        // ---- leaves: weight sum, weight-averaged position (list order)
+        const uint32_t o0 = out_start[g];
+        if ((uint32_t)nnodes != out_start[g + 1] - o0) {
+            if (lane == 0) atomicOr(&ctr->err, DERR_INTERNAL);
+        } else {
+            for (int d = lane; d < nnodes; d += 32) {
+                if constexpr (MX) {
+                    // mixed form: a one-element leaf keeps its offsets; the
+                    // weighted mean of a larger leaf is taken in FP32
+                    const uint32_t q0 = nb[d], q1 = nb[d + 1];
+                    P32 o;
+                    if (q1 - q0 == 1) {
+                        const E e = cur[q0];
+                        o.ox = e.x; o.oy = e.y; o.oz = e.z; o.w = e.w;
+                    } else {
+                        float sx = 0.f, sy = 0.f, sz = 0.f;
+                        unsigned long long Wl = 0;
+                        for (uint32_t q = q0; q < q1; ++q) {
+                            const E e = cur[q];
+                            const float wf = (float)e.w;
+                            sx = sx + wf * e.x;
+                            sy = sy + wf * e.y;
+                            sz = sz + wf * e.z;
+                            Wl += e.w;
+                        }
+                        if (Wl > 0xffffffffull) atomicOr(&ctr->err, DERR_OVERFLOW);
+                        const float Wf = (float)Wl;
+                        o.ox = clamp_offf(sx / Wf); o.oy = clamp_offf(sy / Wf); o.oz = clamp_offf(sz / Wf);
+                        o.w = (uint32_t)Wl;
+                    }
+                    out32[o0 + d] = o;
+                    cout[o0 + d] = (uint32_t)g;
+                } else {
                     double sx = 0.0, sy = 0.0, sz = 0.0;
                     unsigned long long Wl = 0;
-                    for (uint32_t q = bnd[d]; q < bnd[d + 1]; ++q) {
-                        const MPT e = cur[q];
+                    for (uint32_t q = nb[d]; q < nb[d + 1]; ++q) {
+                        const E e = cur[q];
                         const double wd = (double)e.w;
                         sx = sx + wd * e.x;
                         sy = sy + wd * e.y;
@@ -1460,23 +1491,22 @@ __global__ void __launch_bounds__(MergeTier<MX, TIER>::NW * 32) k_merge(
                     }
                     if (Wl > 0xffffffffull) atomicOr(&ctr->err, DERR_OVERFLOW);
                     const double Wd = (double)Wl;
-                    if constexpr (MX) {
-                        P32 o;
-                        o.ox = clamp_off(sx / Wd); o.oy = clamp_off(sy / Wd); o.oz = clamp_off(sz / Wd);
-                        o.w = (uint32_t)Wl;
-                        out32[o0 + d] = o;
-                        cout[o0 + d] = (uint32_t)g;
-                    } else {
-                        P64 o;
-                        o.x = sx / Wd; o.y = sy / Wd; o.z = sz / Wd;
-                        o.cell = (uint32_t)g;
-                        o.w = (uint32_t)Wl;
-                        st_p64(out + o0 + d, o);
-                    }
+                    P64 o;
+                    o.x = sx / Wd; o.y = sy / Wd; o.z = sz / Wd;
+                    o.cell = (uint32_t)g;
+                    o.w = (uint32_t)Wl;
+                    st_p64(out + o0 + d, o);
                 }
             }
-            __syncwarp();
         }
+        __syncwarp();
+    }
+    // workload counters, one atomic each per warp
+    if (lane == 0 && t_cells) {
+        atomicAdd(&ctr->merge_cells, t_cells);
+        atomicAdd(&ctr->merge_elems, t_el);
+        atomicAdd(&ctr->merge_elems2, t_sq);
+        atomicMax(&ctr->merge_maxm, t_max);
     }
 }
 
@@ -1766,13 +1796,12 @@ void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
 
 void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 {
-    const double dV = P.h[0] * P.h[1] * P.h[2];
-    const double qscale = 1.602176634e-19 * ldexp(1.0, -3 * P.frac_bits) / dV / 8.8541878128e-12;
-    const double phi_top = P.E0 * (P.hi[2] - P.lo[2]);
-    const double bc_top = 2.0 * phi_top / (P.h[2] * P.h[2]);
+    double qscale, bc_top;
+    rhs_consts(P, qscale, bc_top);
     ++g_launches;
-    k_rho<<<grid_for(G, 256), 256, 0, s>>>(P, d.Npos, d.Nneg, d.ne_fix, d.rho, d.lev[0].rhs, G, qscale, bc_top,
-                                          d.ctr);
+    // the fixed-point field form builds its right-hand side in the solve
+    k_rho<<<grid_for(G, 256), 256, 0, s>>>(P, d.Npos, d.Nneg, d.ne_fix, d.rho, d.phi_F > 0 ? nullptr : d.lev[0].rhs,
+                                          G, qscale, bc_top, d.ctr);
 }
 
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
@@ -1803,34 +1832,35 @@ void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
     }
     MergeScanOp op{ d.Xe, d.fired, d.photo_w, d.photo_cnt, d.cell_start, d.out_start, d.photo_off, d.work_off,
                     d.small_list, d.mid_list, d.big_list, d.list_n, G, P.ppc, P.n_new,
-                    d.mixed ? MergeElem<true>::CAP : MergeElem<false>::CAP,
-                    d.mixed ? MergeElem<true>::CAP_MID : MergeElem<false>::CAP_MID };
+                    d.mixed ? (int)sizeof(MP32) : (int)sizeof(MP), d.mixed ? 4 : 8 };
     run_scan<6>(op, G, d.scan_blk, s);
 }
+
 
 template <bool MX>
 void launch_merge_tiers(const Params& P, Dev& d, uint64_t G, cudaStream_t s, const P64* A, const P32* A32, P64* out,
                         P32* out32, uint32_t* cout)
 {
-    using E = typename MergeElem<MX>::T;
-    const size_t bnd_w = sizeof(uint32_t) * 2 * (P.ppc + 1);
-    const size_t sm0 = (sizeof(E) * 3 * MergeTier<MX, 0>::CAP + bnd_w) * MergeTier<MX, 0>::NW;
-    const size_t sm1 = (sizeof(E) * 3 * MergeTier<MX, 1>::CAP + bnd_w) * MergeTier<MX, 1>::NW;
-    const size_t sm2 = bnd_w * MERGE_WARPS;
-    static size_t a0 = 0, a1 = 0;
-    if (sm0 > a0) { cudaFuncSetAttribute(k_merge<MX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0); a0 = sm0; }
-    if (sm1 > a1) { cudaFuncSetAttribute(k_merge<MX, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1); a1 = sm1; }
-    E* work = reinterpret_cast<E*>(d.work);
+    using E = typename std::conditional<MX, MP32, MP>::type;
+    using K = typename EKey<E>::K;
+    const MLayout L0 = merge_layout(MERGE_CAP0, P.ppc, sizeof(E), sizeof(K));
+    const MLayout L1 = merge_layout(MERGE_CAP1, P.ppc, sizeof(E), sizeof(K));
+    const size_t sm0 = (size_t)L0.bytes * MERGE_NW0, sm1 = (size_t)L1.bytes * MERGE_NW1;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_merge_lv<E, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
     g_launches += 3;
-    k_merge<MX, 0><<<152 * 3, MergeTier<MX, 0>::NW * 32, sm0, s>>>(
-        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, work,
-        d.work_cap / 3, out, out32, cout, G, d.mover_cap, d.photo_cap, d.small_list, d.list_n, d.ctr);
-    k_merge<MX, 1><<<152 * 2, MergeTier<MX, 1>::NW * 32, sm1, s>>>(
-        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, work,
-        d.work_cap / 3, out, out32, cout, G, d.mover_cap, d.photo_cap, d.mid_list, d.list_n, d.ctr);
-    k_merge<MX, 2><<<152 * 4, MERGE_WARPS * 32, sm2, s>>>(
-        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, work,
-        d.work_cap / 3, out, out32, cout, G, d.mover_cap, d.photo_cap, d.big_list, d.list_n, d.ctr);
+    k_merge_lv<E, false><<<152 * 16, MERGE_NW0 * 32, sm0, s>>>(
+        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
+        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.small_list, d.list_n, 0, MERGE_CAP0, d.ctr);
+    k_merge_lv<E, false><<<152 * 4, MERGE_NW1 * 32, sm1, s>>>(
+        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
+        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.mid_list, d.list_n, 1, MERGE_CAP1, d.ctr);
+    k_merge_lv<E, true><<<152 * 4, 128, 0, s>>>(
+        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
+        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.big_list, d.list_n, 2, 0, d.ctr);
 }
 
 void launch_merges(const Params& P, Dev& d, uint64_t G, cudaStream_t s)

@@ -3,6 +3,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <cmath>
 #include <cuda_runtime.h>
 
 #include "ik_common.cuh"
@@ -60,6 +61,7 @@ struct Counters {
     unsigned long long photo_slots;    // sum over cells of min(N_gamma, N_new)
     unsigned int n_photo_cells;        // photon-emitting cells listed by the KMC
     unsigned long long merge_cells, merge_elems, merge_elems2, merge_maxm;   // merge workload
+    unsigned long long rho_absmax;     // max |rho_fixed| of the last deposit
     unsigned int err;                  // DERR_* bits
     unsigned int kmc_fail_cell;
     unsigned long long outflow[MAX_R];
@@ -101,12 +103,12 @@ struct Dev {
     // merge
     uint32_t* out_start = nullptr;     // G + 1
     uint64_t* work_off = nullptr;      // G + 1
-    uint32_t* small_list = nullptr;    // G: non-empty cells merged in shared memory
-    uint32_t* mid_list = nullptr;      // G: ... in large shared buffers
-    uint32_t* big_list = nullptr;      // G: non-empty cells merged in the work buffer
+    uint32_t* small_list = nullptr;    // G: non-empty cells of merge tier 0 (small shared scratch)
+    uint32_t* mid_list = nullptr;      // G: ... tier 1 (large shared scratch)
+    uint32_t* big_list = nullptr;      // G: ... tier 2 (scratch in the work area)
     uint32_t* list_n = nullptr;        // 2 counts
     uint32_t* pc_list = nullptr;       // G: photon-emitting cells
-    unsigned char* work = nullptr;  size_t work_bytes = 0;
+    unsigned char* work = nullptr;  size_t work_bytes = 0;   // merge scratch of tier-2 cells
     // scans
     long long* scan_blk = nullptr;  size_t scan_blk_elems = 0;
     // multigrid
@@ -119,10 +121,42 @@ struct Dev {
     Counters* ctr_host = nullptr;      // pinned mirror
     uint32_t* sort_tmp = nullptr;      // radix-sort scratch (4 x capacity u32)
     uint32_t mover_cap = 0, photo_cap = 0;
-    uint64_t work_cap = 0;             // merge work elements (all 3 buffers)
+    uint64_t work_cap = 0;             // merge work area, 32-byte units
     double* stage = nullptr;           // 3 G doubles: field upload/readback
     bool mixed = false;                // FP32 particle form
+    int phi_F = 0;                     // potential in int64 units of 2^-phi_F V (0: FP64 potential)
 };
+
+// Right-hand side constants: b = -rho_fixed qscale, minus bc_top in the top
+// layer (electrode ghost 2 phi_b - phi_1).
+inline void rhs_consts(const Params& P, double& qscale, double& bc_top)
+{
+    const double dV = P.h[0] * P.h[1] * P.h[2];
+    qscale = 1.602176634e-19 * std::ldexp(1.0, -3 * P.frac_bits) / dV / 8.8541878128e-12;
+    const double phi_top = P.E0 * (P.hi[2] - P.lo[2]);
+    bc_top = 2.0 * phi_top / (P.h[2] * P.h[2]);
+}
+
+// Fixed-point bits F of the potential for a bound |phi| <= phi_max: keeps
+// |Phi| = |phi| 2^F at most 2^58, so sums of eight stay inside int64.
+inline int phi_fixed_bits(double phi_max)
+{
+    int e = 0;
+    std::frexp(phi_max > 1.0 ? phi_max : 1.0, &e);   // phi_max < 2^e
+    const int F = 58 - e;
+    return F < 8 ? 8 : (F > 52 ? 52 : F);
+}
+
+// Bound on |phi| of the discrete solution: the electrode potential plus the
+// 1D Dirichlet bound max|b| Lz^2 / 8 of the space charge, doubled for the
+// iterates.
+inline double phi_bound(const Params& P, unsigned long long rho_absmax)
+{
+    double qscale, bc_top;
+    rhs_consts(P, qscale, bc_top);
+    const double Lz = P.hi[2] - P.lo[2];
+    return 2.0 * (std::fabs(P.E0 * Lz) + (double)rho_absmax * qscale * Lz * Lz / 8.0) + 1.0;
+}
 
 // ------------------------------------------------------------- launchers
 // ik_particles.cu
@@ -142,9 +176,10 @@ void launch_set_particles(const Params& P, Dev& d, const double* x, const double
                           const double* z, const uint32_t* w, const int32_t* real, uint32_t n,
                           uint64_t G, cudaStream_t s);
 // ik_field.cu
-int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2,
+int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2, unsigned long long rho_absmax,
                 int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out);
 void launch_efield(const Params& P, Dev& d, cudaStream_t s);
+void launch_phi_to_double(const Params& P, Dev& d, double* out, cudaStream_t s);
 void launch_pack_field(const Params& P, Dev& d, const double* E3, cudaStream_t s);
 void launch_unpack_field(const Params& P, Dev& d, double* E3, cudaStream_t s);
 
