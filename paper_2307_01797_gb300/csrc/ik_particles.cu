@@ -947,8 +947,8 @@ __host__ __device__ inline MLayout merge_layout(uint32_t cap, uint32_t T, uint32
 // Merge tiers by list capacity M + ppc (a level adds at most one element
 // per node): tier 0 and 1 in shared memory (warps per block NW0 / NW1),
 // tier 2 in the global work area.
-constexpr uint32_t MERGE_CAP0 = 128, MERGE_CAP1 = 512;
-constexpr int MERGE_NW0 = 4, MERGE_NW1 = 2;
+constexpr uint32_t MERGE_CAP0 = 128, MERGE_CAP1 = 256;
+constexpr int MERGE_NW0 = 4, MERGE_NW1 = 4;
 
 // Per cell: W = X_e + dN + photo weight -> min(W, ppc) leaves; photo offsets;
 // work-area units (32 B) for tier-2 cells; the tier lists.
@@ -1855,7 +1855,7 @@ void launch_merge_tiers(const Params& P, Dev& d, uint64_t G, cudaStream_t s, con
     k_merge_lv<E, false><<<152 * 16, MERGE_NW0 * 32, sm0, s>>>(
         P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
         d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.small_list, d.list_n, 0, MERGE_CAP0, d.ctr);
-    k_merge_lv<E, false><<<152 * 4, MERGE_NW1 * 32, sm1, s>>>(
+    k_merge_lv<E, false><<<152 * 8, MERGE_NW1 * 32, sm1, s>>>(
         P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
         d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.mid_list, d.list_n, 1, MERGE_CAP1, d.ctr);
     k_merge_lv<E, true><<<152 * 4, 128, 0, s>>>(
