@@ -158,27 +158,20 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def config_of(args, nparticles):
+def config_of(args, nparticles, fp64=True):
     return {"workload": f"single positive streamer, {args.n}^3 cells over a 2 cm cube, 1.5 MV/m, dt 5 ps, ppc 32, "
                         f"photoionization on, synthetic 4-channel discharge tree",
-            "grid": args.n, "particles": int(nparticles), "ppc": 32, "form": args.form,
+            "grid": args.n, "particles": int(nparticles), "ppc": 32,
+            "form": "fp64 plain" if fp64 else "mixed (fp32 + fixed point)",
             "l2": "inputs > L2 (particle records of several GB; no flush)"}
 
 
 # ------------------------------------------------------------------ our arm
-def our_arm(args, rank, world):
+def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e):
+    """Warm up and time args.steps full steps of one form on the workload;
+    returns the measurements (rank-local) and the handle's stats."""
     import torch
-    from paper_2307_01797_gb300 import itokmc
-
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    ph, st, ions = workload(args)
     N0 = len(st["w"])
-    form = itokmc.MIXED if args.form == "mixed" else itokmc.FP64
     # photoelectrons landing in empty cells are split up to ppc particles each,
     # so the count grows from step to step
     cap = int(N0 * args.cap_factor) + 20_000_000
@@ -186,6 +179,7 @@ def our_arm(args, rank, world):
     H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
     H.itokmc_set_ions(*ions)
     H.itokmc_solve_field()
+    tune = None if args.no_tune else H.itokmc_autotune()
     for _ in range(args.warmup):
         H.itokmc_step(1)
     stream = torch.cuda.current_stream()
@@ -201,6 +195,7 @@ def our_arm(args, rank, world):
     movers = 0
     mg_cycles = []
     counts = []
+    last = {}
     e0.record(stream)
     for _ in range(args.steps):
         nk = H.itokmc_num_particles()
@@ -212,8 +207,9 @@ def our_arm(args, rank, world):
         stage["particles"] += s["ms_particles"]; stage["field"] += s["ms_field"]
         movers += s["n_movers"]
         mg_cycles.append(s["mg_cycles"])
-        merge_stats = {k: s[k] for k in ("merge_cells", "merge_elements", "merge_elements_sq", "merge_max_list",
-                                         "n_new_particles", "photon_emissions", "ionizations", "attachments")}
+        last = {k: s[k] for k in ("merge_cells", "merge_elements", "merge_elements_sq", "merge_max_list",
+                                  "n_new_particles", "photon_emissions", "ionizations", "attachments",
+                                  "mg_rel_residual")}
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -230,21 +226,27 @@ def our_arm(args, rank, world):
         processed_all = float(p.item())
     else:
         processed_all = float(processed)
-    value = processed_all / (ms / 1e3)
-    # headline scope: push+sort+deposit+KMC
+    # push+sort+deposit+KMC scope (stage times from CUDA events on the
+    # library's stream)
     core_ms = stage["transport"] + stage["kmc"]
-    core_rate = processed / (core_ms / 1e3)
     # roofline of the transport stage (push + sort + deposit, the metric's
     # particle stream): algorithmic bytes = read + write of every record plus
     # the per-cell mesh terms amortised over ppc
     R = 32 if form == itokmc.FP64 else 20
     mesh = (24 + 8 + 8) if form == itokmc.FP64 else (12 + 8 + 8)
-    alg_bytes = processed * (2 * R + mesh / 32)
-    ach = alg_bytes / (stage["transport"] / 1e3) / 1e9
-    pk, pk_kind = peaks()
-    # e2e: host arrays in pinned memory, uploaded every step; density read back
-    e2e = None
-    if not args.no_e2e:
+    bpp = 2 * R + mesh / 32
+    ach = processed * bpp / (stage["transport"] / 1e3) / 1e9
+    out = {"value": processed_all / (ms / 1e3), "ms_per_step": ms / args.steps,
+           "push_sort_deposit_kmc_rate": processed / (core_ms / 1e3),
+           "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
+           "movers_per_step": movers / args.steps, "mg_cycles": mg_cycles, "particles_per_step": counts,
+           "last_step_counters": last, "gpu_launches": int(launches), "clocks": clk,
+           "transport_achieved_gbs": ach, "bytes_per_particle": bpp,
+           "mg_smoothing": {"nu1": tune["mg_nu1"], "nu2": tune["mg_nu2"], "autotuned": True} if tune else
+           {"nu1": 2, "nu2": 2, "autotuned": False}}
+    if with_e2e:
+        # e2e through the public API: the state uploaded from pinned host
+        # memory, one step, the electron density read back, every step
         pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in st.items()}
         ne_host = torch.empty(args.n ** 3, dtype=torch.int64).pin_memory()
         K2 = max(1, min(args.steps, 5))
@@ -260,15 +262,42 @@ def our_arm(args, rank, world):
                                                     ne_host.numel() * 8), H.h)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        e2e = {"value": done / te, "unit": "particle-steps/s", "h2d_bytes_per_step": N0 * (3 * 8 + 4),
-               "d2h_bytes_per_step": args.n ** 3 * 8, "steps": K2}
+        out["e2e"] = {"value": done / te, "unit": "particle-steps/s", "h2d_bytes_per_step": N0 * (3 * 8 + 4),
+                      "d2h_bytes_per_step": args.n ** 3 * 8, "steps": K2}
+    E = None
+    if rank == 0 and not args.no_cpu_baseline and form == itokmc.FP64:
+        E = tuple(np.asarray(b).reshape(args.n, args.n, args.n) for b in H.itokmc_read_densities(itokmc.E))
+    H.close()
+    return out, E
+
+
+def our_arm(args, rank, world):
+    import torch
+    from paper_2307_01797_gb300 import itokmc
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ph, st, ions = workload(args)
+    N0 = len(st["w"])
+    forms = {"fp64": [itokmc.FP64], "mixed": [itokmc.MIXED], "both": [itokmc.FP64, itokmc.MIXED]}[args.form]
+    res = {}
+    E = None
+    for f in forms:
+        r, e = run_form(args, itokmc, f, ph, st, ions, rank, world, dist, dev, with_e2e=(f == forms[0]
+                                                                                        and not args.no_e2e))
+        res[f] = r
+        E = E if E is not None else e
     if rank != 0:
-        H.close()
         return
     cpu = None
     if not args.no_cpu_baseline:
-        from paper_2307_01797_gb300 import synth
-        E = tuple(np.asarray(b).reshape(args.n, args.n, args.n) for b in H.itokmc_read_densities(itokmc.E))
+        if E is None:
+            from paper_2307_01797_gb300 import synth
+            E = synth.random_field(ph, seed=3, amp=1e6, base=ph["E0"])
         sub = oracle_sample(ph, st, ions, args.ref_particles, seed=1)
         t_tot, n_tot, k = 0.0, 0, 0
         while t_tot < args.cpu_seconds and k < 20:
@@ -277,25 +306,147 @@ def our_arm(args, rank, world):
         cpu = {"value": n_tot / t_tot, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                "sample": f"{len(sub['w'])} particles (a contiguous cell run of the workload) x {k} steps of "
                          "push+sort+deposit+KMC on the full grid, single-threaded C oracle"}
+    P = res[forms[0]]
+    pk, pk_kind = peaks()
     line = {
-        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if form == itokmc.FP64 else "f32",
+        "metric": METRIC, "value": P["value"], "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": P["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if forms[0] == itokmc.FP64 else "f32",
         "data": "synthetic (seeded discharge-tree state; no dataset)",
-        "config": config_of(args, N0),
-        "push_sort_deposit_kmc_rate": core_rate,
-        "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
-        "movers_per_step": movers / args.steps, "mg_cycles": mg_cycles, "particles_per_step": counts,
-        "last_step_counters": merge_stats,
-        "roofline": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)", "achieved": ach,
-                     "peak": pk, "peak_kind": pk_kind, "unit": "GB/s", "frac": ach / pk, "traffic": None,
-                     "bytes_per_particle": 2 * R + mesh / 32},
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "config": config_of(args, N0, forms[0] == itokmc.FP64),
+        "push_sort_deposit_kmc_rate": P["push_sort_deposit_kmc_rate"],
+        "stage_ms_per_step": P["stage_ms_per_step"], "movers_per_step": P["movers_per_step"],
+        "mg_cycles": P["mg_cycles"], "mg_smoothing": P["mg_smoothing"], "particles_per_step": P["particles_per_step"],
+        "last_step_counters": P["last_step_counters"],
+        "roofline": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)",
+                     "achieved": P["transport_achieved_gbs"], "peak": pk, "peak_kind": pk_kind, "unit": "GB/s",
+                     "frac": P["transport_achieved_gbs"] / pk, "traffic": None,
+                     "bytes_per_particle": P["bytes_per_particle"]},
+        "cpu_baseline": cpu, "e2e": P.get("e2e"), "gpu_launches": P["gpu_launches"], "clocks": P["clocks"],
     }
+    if len(forms) > 1:
+        M = res[itokmc.MIXED]
+        line["mixed_form"] = {
+            "dtype": "f32 positions/push/leaps, int64 deposit, fixed-point potential with FP32 V-cycles",
+            "value": M["value"], "ms_per_step": M["ms_per_step"],
+            "push_sort_deposit_kmc_rate": M["push_sort_deposit_kmc_rate"],
+            "stage_ms_per_step": M["stage_ms_per_step"], "mg_cycles": M["mg_cycles"], "mg_smoothing": M["mg_smoothing"],
+            "particles_per_step": M["particles_per_step"], "gpu_launches": M["gpu_launches"],
+            "clocks": M["clocks"],
+            "roofline": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)",
+                         "achieved": M["transport_achieved_gbs"], "peak": pk, "unit": "GB/s",
+                         "frac": M["transport_achieved_gbs"] / pk, "bytes_per_particle": M["bytes_per_particle"]},
+            "speedup_vs_fp64": M["value"] / P["value"]}
     print(json.dumps(line), flush=True)
-    H.close()
     if dist:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ precision study
+def precision_study(args):
+    """The FP32/fixed-point form against the FP64 plain form on the same GPU:
+    the small-blob physics (1 cm, 1.5 MV/m, dt 1 ps, ppc 8, photons off) on
+    an n^3 grid, both forms stepped in lockstep from one state with the same
+    seeds (common random numbers), and per step the relative L2 differences
+    of the electron density (ne_fix) and of E.  Variant "deterministic": D = 0
+    and reactions off, which leaves only the rounding of the push and field."""
+    import torch
+    from paper_2307_01797_gb300 import itokmc, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    out = {"study": "precision", "grid": args.n, "steps": args.study_steps, "variants": {}}
+    for variant in ("full", "deterministic"):
+        ph = synth.physics_small(args.n)
+        if variant == "deterministic":
+            ph.update(D=0.0, alpha_A=0.0, eta=0.0)
+        st = synth.blob_state(ph, seed=1, sigma=5e-4, peak=1e18, zfrac=0.8)
+        N0 = len(st["w"])
+        hs = {}
+        for name, form in (("fp64", itokmc.FP64), ("mixed", itokmc.MIXED)):
+            H = itokmc.Handle(itokmc.make_config(ph, 8 * N0 + 1_000_000, seed0=1, precision=form))
+            H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+            H.itokmc_solve_field()
+            hs[name] = H
+        l2_ne, l2_E, counts = [], [], []
+        for k in range(args.study_steps):
+            for H in hs.values():
+                H.itokmc_step(1)
+            a = hs["mixed"].itokmc_read_densities(itokmc.NE_FIX).astype(np.float64)
+            b = hs["fp64"].itokmc_read_densities(itokmc.NE_FIX).astype(np.float64)
+            l2_ne.append(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)))
+            a = hs["mixed"].itokmc_read_densities(itokmc.E).ravel()
+            b = hs["fp64"].itokmc_read_densities(itokmc.E).ravel()
+            l2_E.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+            counts.append([hs["fp64"].itokmc_num_particles(), hs["mixed"].itokmc_num_particles()])
+        for H in hs.values():
+            H.close()
+        out["variants"][variant] = {"particles0": N0, "l2_ne": l2_ne, "l2_E": l2_E, "particles": counts}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ ensemble study
+def ensemble_study(args):
+    """Batched ensemble against sequential single runs on the same GPU: R
+    independent realizations (seeds 1..R) of the 1 cm, 128^3 physics with
+    photoionization, ppc 16, each seeded by a Gaussian blob (sigma 0.5 mm at
+    0.8 L) whose peak is log-uniform in [1e17, 1e19] m^-3 (uneven particle
+    counts).  The batched handle advances all R in every launch; the
+    sequential runs advance one single-realization handle per member."""
+    import torch
+    from paper_2307_01797_gb300 import itokmc, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    R, K = args.members, args.study_steps
+    ph = synth.physics_ensemble_member(args.n)
+    rng = np.random.default_rng(2024)
+    peaks = 10.0 ** rng.uniform(17.0, 19.0, R)
+    states = [synth.blob_state(ph, seed=1 + r, sigma=5e-4, peak=float(peaks[r]), zfrac=0.8) for r in range(R)]
+    counts = [len(st["w"]) for st in states]
+    out = {"study": "ensemble", "grid": args.n, "members": R, "steps": K, "particles0": counts, "forms": {}}
+    forms = [("fp64", itokmc.FP64), ("mixed", itokmc.MIXED)]
+    for name, form in forms:
+        # batched: every member in one handle
+        x = np.concatenate([st["x"] for st in states]); y = np.concatenate([st["y"] for st in states])
+        z = np.concatenate([st["z"] for st in states]); w = np.concatenate([st["w"] for st in states])
+        real = np.concatenate([np.full(c, r, np.int32) for r, c in enumerate(counts)])
+        H = itokmc.Handle(itokmc.make_config(ph, 8 * len(w) + 4_000_000, realizations=R, seed0=1, precision=form))
+        H.itokmc_set_particles(x, y, z, w, real)
+        H.itokmc_solve_field()
+        for _ in range(args.warmup):
+            H.itokmc_step(1)
+        torch.cuda.synchronize()
+        done = 0
+        t0 = time.perf_counter()
+        for _ in range(K):
+            done += H.itokmc_num_particles()
+            H.itokmc_step(1)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        H.close()
+        res = {"batched_ms_per_step": 1e3 * tb / K, "batched_particle_steps_per_s": done / tb}
+        if name == "fp64" or not args.batched_only:
+            # sequential: one member at a time
+            ts, dn = 0.0, 0
+            for r, st in enumerate(states):
+                H = itokmc.Handle(itokmc.make_config(ph, 8 * counts[r] + 1_000_000, seed0=1 + r, precision=form))
+                H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+                H.itokmc_solve_field()
+                for _ in range(args.warmup):
+                    H.itokmc_step(1)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(K):
+                    dn += H.itokmc_num_particles()
+                    H.itokmc_step(1)
+                torch.cuda.synchronize()
+                ts += time.perf_counter() - t0
+                H.close()
+            res.update({"sequential_ms_per_step": 1e3 * ts / K, "sequential_particle_steps_per_s": dn / ts,
+                        "batched_speedup": ts / tb})
+        out["forms"][name] = res
+    fp = out["forms"]["fp64"]
+    if "mixed" in out["forms"]:
+        out["mixed_batched_vs_fp64_sequential"] = fp["sequential_ms_per_step"] / out["forms"]["mixed"][
+            "batched_ms_per_step"]
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -304,7 +455,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--form", default="both", choices=["fp64", "mixed", "both"],
+                    help="both: the FP64 plain form gives the headline, the mixed form is reported beside it")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--particles", type=float, default=2e7)
     ap.add_argument("--ref-particles", type=int, default=2000000)
@@ -312,7 +464,19 @@ def main():
     ap.add_argument("--cap-factor", type=float, default=4.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default smoother counts (2, 2)")
+    ap.add_argument("--study", default=None, choices=["precision", "ensemble"],
+                    help="instead of the benchmark: the FP32-vs-FP64 precision study")
+    ap.add_argument("--study-steps", type=int, default=20)
+    ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--batched-only", action="store_true")
     args = ap.parse_args()
+    if args.study == "precision":
+        precision_study(args)
+        return
+    if args.study == "ensemble":
+        ensemble_study(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

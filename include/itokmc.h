@@ -196,6 +196,32 @@ int itokmc_run_stage(itokmc_handle* h, int32_t stage);
 /* Advances the step counter used in every Philox counter by one. */
 int itokmc_advance_counter(itokmc_handle* h);
 
+/* ---- autotuning ----------------------------------------------------------
+ * The paper fixes no smoother counts; the multigrid cycle (Sec. 4.3:
+ * V-cycles with red-black Gauss-Seidel smoothing) takes nu1 pre- and nu2
+ * post-smoothing sweeps per level.  itokmc_autotune times the field solve
+ * of the current charge (as left by itokmc_solve_field or the last step)
+ * for each candidate pair (nu1, nu2) in {1,2,3} x {1,2,3}, each from a zero
+ * potential (a solve of many cycles, which ranks the pairs by convergence
+ * per unit time), twice, and keeps the fastest pair that converges in the
+ * handle's configuration (mg_nu1, mg_nu2).  The potential and field
+ * are restored afterwards, so the run continues as without the call; only
+ * the number of V-cycles of later solves changes (the tolerance does not).
+ *   out  optional: the chosen pair, its time, and every candidate's time
+ *        (ms, -1 if it did not converge).
+ * Returns ITOKMC_OK, ITOKMC_ERR_NOCONV if no candidate converges, or
+ * ITOKMC_ERR_CUDA.  Synchronises the stream. */
+#define ITOKMC_TUNE_CANDIDATES 9
+typedef struct itokmc_tuning {
+    int32_t mg_nu1, mg_nu2;                          /* chosen pair            */
+    double ms_field;                                 /* its field-solve time   */
+    int32_t cycles;                                  /* its V-cycle count      */
+    int32_t n_tried;
+    int32_t nu_tried[ITOKMC_TUNE_CANDIDATES][2];
+    double ms_tried[ITOKMC_TUNE_CANDIDATES];         /* -1: no convergence     */
+} itokmc_tuning;
+int itokmc_autotune(itokmc_handle* h, itokmc_tuning* out);
+
 /* Copies one field (ITOKMC_NE_FIX ...) of realization r (or all
  * realizations when r = -1) into host_out of the given size in bytes.
  * ERR_ARG if bytes is too small.  Synchronises the stream. */

@@ -1,6 +1,8 @@
 // ik_api.cu -- the C ABI of libitokmc (declared in include/itokmc.h): handle
 // life cycle, device memory, state upload/readback and the step driver.
 #include <algorithm>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,7 +14,7 @@
 #include "ik_state.h"
 
 namespace ik {
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
 
 // Message of the last error raised without a handle (fixed storage: no
 // allocation on this path).
@@ -28,6 +30,9 @@ struct itokmc_handle {
     ik::Params P;
     ik::Dev d;
     cudaStream_t s = nullptr;
+    cudaStream_t sf = nullptr;    // field stream (the solve overlaps the particle stages)
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int device = 0;
     uint64_t G = 0;
     uint32_t N = 0;           // particle count (host copy)
     uint32_t cap = 0;
@@ -35,6 +40,7 @@ struct itokmc_handle {
     int field_prec = 0;
     bool poisoned = false;
     std::string err;
+    std::mutex emtx;              // err/poisoned are written by the step and field threads
     std::vector<void*> allocs;
     itokmc_stats st{};
     cudaEvent_t ev[8]{};
@@ -47,6 +53,7 @@ namespace {
 int fail(itokmc_handle* h, int code, const std::string& msg)
 {
     if (h) {
+        std::lock_guard<std::mutex> lk(h->emtx);
         h->err = msg;
         if (code == ITOKMC_ERR_CUDA || code == ITOKMC_ERR_TIMEOUT) h->poisoned = true;
     } else {
@@ -246,18 +253,19 @@ int stage_particles(itokmc_handle* h)
     return status_of_err(h, c.err);
 }
 
-int stage_field(itokmc_handle* h)
+// a5 on stream s into the field arrays E / E32 (the handle's own, or the
+// next step's when the solve overlaps the particle stages).
+int stage_field_on(itokmc_handle* h, cudaStream_t s, ik::E64* E, float4* E32, unsigned long long rho_absmax)
 {
-    IK_CHECK(h, cudaEventRecord(h->ev[6], h->s));
+    IK_CHECK(h, cudaEventRecord(h->ev[6], s));
     int cycles = 0;
     double rel = 0.0;
-    const int st = ik::field_solve(h->P, h->d, h->d.phi_F > 0 ? 2 : h->field_prec, h->cfg.mg_rtol, h->cfg.mg_nu1, h->cfg.mg_nu2,
-                                   h->rb->ctr.rho_absmax,
-                                   h->cfg.mg_max_cycles, h->s, &cycles, &rel);
+    const int st = ik::field_solve(h->P, h->d, h->d.phi_F > 0 ? 2 : h->field_prec, h->cfg.mg_rtol, h->cfg.mg_nu1,
+                                   h->cfg.mg_nu2, rho_absmax, h->cfg.mg_max_cycles, s, &cycles, &rel);
     if (st == -3) return cuda_check(h, cudaGetLastError(), "field solve");
-    ik::launch_efield(h->P, h->d, h->s);
-    IK_CHECK(h, cudaEventRecord(h->ev[7], h->s));
-    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    ik::launch_efield_to(h->P, h->d, s, E, E32);
+    IK_CHECK(h, cudaEventRecord(h->ev[7], s));
+    IK_CHECK(h, cudaStreamSynchronize(s));
     IK_CHECK(h, cudaGetLastError());
     h->st.mg_cycles = cycles;
     h->st.mg_rel_residual = rel;
@@ -267,6 +275,45 @@ int stage_field(itokmc_handle* h)
         snprintf(buf, sizeof buf, "multigrid stopped at %d cycles, relative residual %.3e", cycles, rel);
         return fail(h, ITOKMC_ERR_NOCONV, buf);
     }
+    return ITOKMC_OK;
+}
+
+int stage_field(itokmc_handle* h) { return stage_field_on(h, h->s, h->d.E, h->d.E32, h->rb->ctr.rho_absmax); }
+
+// One full step.  After the transport stage has formed rho, the field of the
+// next step is solved on the field stream by a host thread while this
+// thread runs KMC and the particle stages (they read the current field; the
+// solve writes the next one); the two fields swap at the end.
+int full_step(itokmc_handle* h)
+{
+    int rc = stage_transport(h);
+    if (rc) return rc;
+    IK_CHECK(h, cudaEventRecord(h->fork, h->s));
+    IK_CHECK(h, cudaStreamWaitEvent(h->sf, h->fork, 0));
+    const unsigned long long amax = h->rb->ctr.rho_absmax;
+    int frc = ITOKMC_OK;
+    std::string ferr;
+    std::thread field([h, amax, &frc, &ferr]() {
+        if (cudaSetDevice(h->device) != cudaSuccess) {
+            frc = ITOKMC_ERR_CUDA;
+            ferr = "field thread: cudaSetDevice";
+            return;
+        }
+        frc = stage_field_on(h, h->sf, h->d.E_next, h->d.E32_next, amax);
+        if (frc) {
+            std::lock_guard<std::mutex> lk(h->emtx);
+            ferr = h->err;
+        }
+    });
+    rc = stage_kmc(h);
+    if (!rc) rc = stage_particles(h);
+    field.join();
+    IK_CHECK(h, cudaEventRecord(h->join, h->sf));
+    IK_CHECK(h, cudaStreamWaitEvent(h->s, h->join, 0));
+    if (rc) return rc;
+    if (frc) return fail(h, frc, ferr);
+    std::swap(h->d.E, h->d.E_next);
+    std::swap(h->d.E32, h->d.E32_next);
     return ITOKMC_OK;
 }
 
@@ -385,8 +432,13 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     d.Nneg = dalloc_n<int64_t>(h, G, &rc);
     d.rho = dalloc_n<int64_t>(h, G, &rc);
     // FP64 form: FP64 field (push, KMC); mixed form: FP32 field only
-    if (d.mixed) d.E32 = dalloc_n<float4>(h, G, &rc);
-    else d.E = dalloc_n<ik::E64>(h, G, &rc);
+    if (d.mixed) {
+        d.E32 = dalloc_n<float4>(h, G, &rc);
+        d.E32_next = dalloc_n<float4>(h, G, &rc);
+    } else {
+        d.E = dalloc_n<ik::E64>(h, G, &rc);
+        d.E_next = dalloc_n<ik::E64>(h, G, &rc);
+    }
     d.fired = dalloc_n<int64_t>(h, 3 * G, &rc);
     d.stage = dalloc_n<double>(h, 3 * G, &rc);
     d.photos = dalloc_n<ik::Photo>(h, d.photo_cap, &rc);
@@ -431,6 +483,11 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
         rc = fail(h, ITOKMC_ERR_OOM, "pinned host buffer");
     for (int e = 0; e < 8 && !rc; ++e)
         if (cudaEventCreate(&h->ev[e]) != cudaSuccess) rc = fail(h, ITOKMC_ERR_CUDA, "event create");
+    if (!rc && (cudaGetDevice(&h->device) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&h->sf, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess))
+        rc = fail(h, ITOKMC_ERR_CUDA, "field stream");
     if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->s), "init sync");
     if (rc) {
         ik::set_global_error(h->err.c_str());
@@ -452,6 +509,12 @@ int itokmc_destroy(itokmc_handle* h)
         else cudaFreeAsync(p, h->s);
     }
     cudaStreamSynchronize(h->s);
+    if (h->sf) {
+        cudaStreamSynchronize(h->sf);
+        cudaStreamDestroy(h->sf);
+    }
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
     if (h->rb) cudaFreeHost(h->rb);
     if (h->d.norm_host) cudaFreeHost(h->d.norm_host);
@@ -598,6 +661,66 @@ int itokmc_run_stage(itokmc_handle* h, int32_t stage)
     }
 }
 
+int itokmc_autotune(itokmc_handle* h, itokmc_tuning* out)
+{
+    IK_GUARD(h);
+    ik::Dev& d = h->d;
+    const size_t cells = h->G;
+    double* phi0 = d.lev[0].phi;
+    // the stage buffer (3 G doubles) holds the initial potential
+    IK_CHECK(h, cudaMemcpyAsync(d.stage, phi0, cells * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    const int F0 = d.phi_F;
+    itokmc_tuning t{};
+    int best = -1;
+    double best_ms = 0.0;
+    int best_cyc = 0;
+    const int prec = d.phi_F > 0 ? 2 : h->field_prec;
+    for (int a = 1; a <= 3; ++a)
+        for (int b = 1; b <= 3; ++b) {
+            const int k = t.n_tried++;
+            t.nu_tried[k][0] = a;
+            t.nu_tried[k][1] = b;
+            double ms = -1.0;
+            int cyc = 0;
+            for (int rep = 0; rep < 2; ++rep) {
+                // from a zero potential: a solve that needs many cycles ranks
+                // the pairs by their convergence per unit time
+                IK_CHECK(h, cudaMemsetAsync(phi0, 0, cells * sizeof(double), h->s));
+                d.phi_F = F0;
+                double rel = 0.0;
+                IK_CHECK(h, cudaEventRecord(h->ev[6], h->s));
+                const int st = ik::field_solve(h->P, d, prec, h->cfg.mg_rtol, a, b, h->rb->ctr.rho_absmax,
+                                               h->cfg.mg_max_cycles, h->s, &cyc, &rel);
+                IK_CHECK(h, cudaEventRecord(h->ev[7], h->s));
+                IK_CHECK(h, cudaStreamSynchronize(h->s));
+                if (st == -3) return cuda_check(h, cudaGetLastError(), "autotune field solve");
+                if (st != 0) { ms = -1.0; break; }
+                const double m = elapsed(h, 6, 7);
+                ms = ms < 0.0 ? m : std::min(ms, m);
+            }
+            t.ms_tried[k] = ms;
+            if (ms >= 0.0 && (best < 0 || ms < best_ms)) {
+                best = k;
+                best_ms = ms;
+                best_cyc = cyc;
+            }
+        }
+    // restore the potential and the field of the initial state
+    IK_CHECK(h, cudaMemcpyAsync(phi0, d.stage, cells * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    d.phi_F = F0;
+    ik::launch_efield(h->P, d, h->s);
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    if (best < 0) return fail(h, ITOKMC_ERR_NOCONV, "autotune: no smoother pair converged");
+    h->cfg.mg_nu1 = t.nu_tried[best][0];
+    h->cfg.mg_nu2 = t.nu_tried[best][1];
+    t.mg_nu1 = h->cfg.mg_nu1;
+    t.mg_nu2 = h->cfg.mg_nu2;
+    t.ms_field = best_ms;
+    t.cycles = best_cyc;
+    if (out) *out = t;
+    return cuda_check(h, cudaGetLastError(), "autotune");
+}
+
 int itokmc_advance_counter(itokmc_handle* h)
 {
     IK_GUARD(h);
@@ -612,10 +735,7 @@ int itokmc_step(itokmc_handle* h, int32_t nsteps)
     IK_GUARD(h);
     if (nsteps < 0) return fail(h, ITOKMC_ERR_ARG, "nsteps < 0");
     for (int k = 0; k < nsteps; ++k) {
-        int rc = stage_transport(h);
-        if (!rc) rc = stage_kmc(h);
-        if (!rc) rc = stage_particles(h);
-        if (!rc) rc = stage_field(h);
+        const int rc = full_step(h);
         if (rc) return rc;
         itokmc_advance_counter(h);
     }

@@ -74,7 +74,7 @@ __device__ __forceinline__ T inv_diag(int d)
 }
 
 template <class T>
-__global__ void k_smooth(T* __restrict__ phi, const T* __restrict__ rhs, Geo G, T h2, int color)
+__global__ void k_smooth(T* __restrict__ phi, const T* __restrict__ rhs, Geo G, int color)
 {
     const uint64_t half = G.cells >> 1;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < half; t += (uint64_t)gridDim.x * blockDim.x) {
@@ -88,15 +88,17 @@ __global__ void k_smooth(T* __restrict__ phi, const T* __restrict__ rhs, Geo G, 
         const uint64_t idx = ((r * n + k) * n + j) * n + i;
         int diag;
         const T s = nbr_sum(phi, idx, n, i, j, k, diag);
-        phi[idx] = (s - h2 * rhs[idx]) * inv_diag<T>(diag);
+        phi[idx] = (s - rhs[idx]) * inv_diag<T>(diag);
     }
 }
 
-// Residual r = b - A phi at fine cells, averaged over the 8 children of each
-// coarse cell into the coarse right-hand side.
+// Residual at fine cells, averaged over the 8 children of each coarse cell
+// into the coarse right-hand side.  Every level stores h^2 b (the multigrid
+// systems are scaled by h^2), so the coarse value h_c^2 mean(r) is half the
+// sum of the children's h_f^2 r = h_f^2 b - (neighbour sum - diag phi).
 template <class T, class TC>
 __global__ void k_resid_restrict(const T* __restrict__ phi, const T* __restrict__ rhs, TC* __restrict__ rhs_c,
-                                 Geo Gc, int nf, T inv_h2)
+                                 Geo Gc, int nf)
 {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < Gc.cells; t += (uint64_t)gridDim.x * blockDim.x) {
         int r, K, J, I;
@@ -108,14 +110,39 @@ __global__ void k_resid_restrict(const T* __restrict__ phi, const T* __restrict_
             const uint64_t idx = (((uint64_t)r * nf + k) * nf + j) * nf + i;
             int diag;
             const T s = nbr_sum(phi, idx, nf, i, j, k, diag);
-            acc += rhs[idx] - (s - (T)diag * phi[idx]) * inv_h2;
+            acc += rhs[idx] - (s - (T)diag * phi[idx]);
         }
-        rhs_c[t] = (TC)(acc * (T)0.125);
+        rhs_c[t] = (TC)(acc * (T)0.5);
     }
 }
 
-// phi_f += trilinear cell-centred interpolation of the coarse correction
-// (weights 3/4, 1/4 per axis; ghosts: Neumann e, Dirichlet -e).
+// phi_f += trilinear cell-centred interpolation of the coarse correction:
+// weights 3/4, 1/4 per axis written as (3 a + b) / 4 with fused multiply-
+// adds (ghosts: Neumann e, Dirichlet -e, i.e. (3 a - a) / 4 in z).
+template <class T>
+__device__ __forceinline__ T prolong_at(const T* __restrict__ ec, int nc, int i, int j, int k)
+{
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1), K2 = K + ((k & 1) ? 1 : -1);
+    T sz = (T)1;
+    if (I2 < 0 || I2 >= nc) I2 = I;
+    if (J2 < 0 || J2 >= nc) J2 = J;
+    if (K2 < 0 || K2 >= nc) { K2 = K; sz = (T)-1; }
+    const int iz[2] = { K, K2 }, iy[2] = { J, J2 };
+    T m[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        T q[2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const T* row = ec + ((uint64_t)iz[c] * nc + iy[b]) * nc;
+            q[b] = fma((T)3, row[I], row[I2]);
+        }
+        m[c] = fma((T)3, q[0], q[1]);
+    }
+    return fma((T)3, m[0], sz * m[1]) * (T)(1.0 / 64.0);
+}
+
 template <class T>
 __global__ void k_prolong(T* __restrict__ phi_f, const T* __restrict__ e_c, Geo Gf)
 {
@@ -123,29 +150,13 @@ __global__ void k_prolong(T* __restrict__ phi_f, const T* __restrict__ e_c, Geo 
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < Gf.cells; t += (uint64_t)gridDim.x * blockDim.x) {
         int r, k, j, i;
         decode(t, Gf.log2n, r, k, j, i);
-        const int I = i >> 1, J = j >> 1, K = k >> 1;
-        const int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1), K2 = K + ((k & 1) ? 1 : -1);
-        const T* ec = e_c + (uint64_t)r * nc * nc * nc;
-        int ix[2] = { I, I2 }, iy[2] = { J, J2 }, iz[2] = { K, K2 };
-        T wx[2] = { (T)0.75, (T)0.25 }, wy[2] = { (T)0.75, (T)0.25 }, wz[2] = { (T)0.75, (T)0.25 };
-        if (I2 < 0 || I2 >= nc) { ix[1] = I; }
-        if (J2 < 0 || J2 >= nc) { iy[1] = J; }
-        if (K2 < 0 || K2 >= nc) { iz[1] = K; wz[1] = (T)-0.25; }
-        T acc = 0;
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-                    acc += wx[a] * wy[b] * wz[c] * ec[((uint64_t)iz[c] * nc + iy[b]) * nc + ix[a]];
-        phi_f[t] += acc;
+        phi_f[t] += prolong_at(e_c + (uint64_t)r * nc * nc * nc, nc, i, j, k);
     }
 }
 
 // Bottom solve: one block per realization, red-black sweeps in shared memory.
 template <class T>
-__global__ void k_bottom(T* __restrict__ phi, const T* __restrict__ rhs, int n, T h2, int sweeps)
+__global__ void k_bottom(T* __restrict__ phi, const T* __restrict__ rhs, int n, int sweeps)
 {
     extern __shared__ unsigned char smem_raw[];
     T* s = reinterpret_cast<T*>(smem_raw);
@@ -161,7 +172,7 @@ __global__ void k_bottom(T* __restrict__ phi, const T* __restrict__ rhs, int n, 
                 if (((i + j + k) & 1) != color) continue;
                 int diag;
                 const T sum = nbr_sum(s, (uint64_t)c, n, i, j, k, diag);
-                s[c] = (sum - h2 * b[c]) / (T)diag;
+                s[c] = (sum - b[c]) / (T)diag;
             }
             __syncthreads();
         }
@@ -175,7 +186,7 @@ __global__ void k_bottom(T* __restrict__ phi, const T* __restrict__ rhs, int n, 
 constexpr int NORM_TPB = 256;
 
 __global__ void __launch_bounds__(NORM_TPB) k_resid_norm(const double* __restrict__ phi, const double* __restrict__ rhs,
-                                                         float* __restrict__ r32, Geo G, double inv_h2,
+                                                         float* __restrict__ r32, Geo G,
                                                          double* __restrict__ part, int with_b, int items)
 {
     __shared__ double red[NORM_TPB / 32][2];
@@ -188,7 +199,7 @@ __global__ void __launch_bounds__(NORM_TPB) k_resid_norm(const double* __restric
         decode(t, G.log2n, r, k, j, i);
         int diag;
         const double s = nbr_sum(phi, t, G.n, i, j, k, diag);
-        const double res = rhs[t] - (s - (double)diag * phi[t]) * inv_h2;
+        const double res = rhs[t] - (s - (double)diag * phi[t]);
         if (r32) r32[t] = (float)res;
         acc = __fma_rn(res, res, acc);
         if (with_b) bacc = __fma_rn(rhs[t], rhs[t], bacc);
@@ -420,13 +431,12 @@ constexpr int COARSE_N = 16;
 struct CoarseLevels {
     int nlev;            // levels in the fused range, finest first
     int n[MAX_LEVELS];
-    double h2[MAX_LEVELS];
     void* phi[MAX_LEVELS];
     void* rhs[MAX_LEVELS];
 };
 
 template <class T>
-__device__ void blk_smooth(T* phi, const T* rhs, int n, T h2, int color)
+__device__ void blk_smooth(T* phi, const T* rhs, int n, int color)
 {
     const int half = n * n * n / 2;
     for (int t = threadIdx.x; t < half; t += blockDim.x) {
@@ -435,13 +445,13 @@ __device__ void blk_smooth(T* phi, const T* rhs, int n, T h2, int color)
         const uint64_t idx = ((uint64_t)k * n + j) * n + i;
         int diag;
         const T sum = nbr_sum(phi, idx, n, i, j, k, diag);
-        phi[idx] = (sum - h2 * rhs[idx]) / (T)diag;
+        phi[idx] = (sum - rhs[idx]) / (T)diag;
     }
     __syncthreads();
 }
 
 template <class T>
-__device__ void blk_resid_restrict(const T* phi, const T* rhs, T* rhs_c, int nf, T inv_h2)
+__device__ void blk_resid_restrict(const T* phi, const T* rhs, T* rhs_c, int nf)
 {
     const int nc = nf / 2;
     for (int t = threadIdx.x; t < nc * nc * nc; t += blockDim.x) {
@@ -452,9 +462,9 @@ __device__ void blk_resid_restrict(const T* phi, const T* rhs, T* rhs_c, int nf,
             const uint64_t idx = ((uint64_t)k * nf + j) * nf + i;
             int diag;
             const T sum = nbr_sum(phi, idx, nf, i, j, k, diag);
-            acc += rhs[idx] - (sum - (T)diag * phi[idx]) * inv_h2;
+            acc += rhs[idx] - (sum - (T)diag * phi[idx]);
         }
-        rhs_c[t] = acc * (T)0.125;
+        rhs_c[t] = acc * (T)0.5;
     }
     __syncthreads();
 }
@@ -465,20 +475,7 @@ __device__ void blk_prolong(T* phi_f, const T* e_c, int nf)
     const int nc = nf / 2;
     for (int t = threadIdx.x; t < nf * nf * nf; t += blockDim.x) {
         const int i = t % nf, j = (t / nf) % nf, k = t / (nf * nf);
-        const int I = i >> 1, J = j >> 1, K = k >> 1;
-        const int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1), K2 = K + ((k & 1) ? 1 : -1);
-        int ix[2] = { I, I2 }, iy[2] = { J, J2 }, iz[2] = { K, K2 };
-        T wz1 = (T)0.25;
-        if (I2 < 0 || I2 >= nc) ix[1] = I;
-        if (J2 < 0 || J2 >= nc) iy[1] = J;
-        if (K2 < 0 || K2 >= nc) { iz[1] = K; wz1 = (T)-0.25; }
-        const T wx[2] = { (T)0.75, (T)0.25 }, wy[2] = { (T)0.75, (T)0.25 }, wz[2] = { (T)0.75, wz1 };
-        T acc = 0;
-        for (int c = 0; c < 2; ++c)
-            for (int b = 0; b < 2; ++b)
-                for (int a = 0; a < 2; ++a)
-                    acc += wx[a] * wy[b] * wz[c] * e_c[((uint64_t)iz[c] * nc + iy[b]) * nc + ix[a]];
-        phi_f[t] += acc;
+        phi_f[t] += prolong_at(e_c, nc, i, j, k);
     }
     __syncthreads();
 }
@@ -492,23 +489,23 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseLevels C, int nu1,
     const int L = C.nlev - 1;
     for (int l = 0; l < L; ++l) {
         for (int it = 0; it < nu1; ++it) {
-            blk_smooth<T>(PHI(l), RHS(l), C.n[l], (T)C.h2[l], 0);
-            blk_smooth<T>(PHI(l), RHS(l), C.n[l], (T)C.h2[l], 1);
+            blk_smooth<T>(PHI(l), RHS(l), C.n[l], 0);
+            blk_smooth<T>(PHI(l), RHS(l), C.n[l], 1);
         }
-        blk_resid_restrict<T>(PHI(l), RHS(l), RHS(l + 1), C.n[l], (T)(1.0 / C.h2[l]));
+        blk_resid_restrict<T>(PHI(l), RHS(l), RHS(l + 1), C.n[l]);
         T* pc = PHI(l + 1);
         for (int t = threadIdx.x; t < C.n[l + 1] * C.n[l + 1] * C.n[l + 1]; t += blockDim.x) pc[t] = (T)0;
         __syncthreads();
     }
     for (int it = 0; it < bottom_sweeps; ++it) {
-        blk_smooth<T>(PHI(L), RHS(L), C.n[L], (T)C.h2[L], 0);
-        blk_smooth<T>(PHI(L), RHS(L), C.n[L], (T)C.h2[L], 1);
+        blk_smooth<T>(PHI(L), RHS(L), C.n[L], 0);
+        blk_smooth<T>(PHI(L), RHS(L), C.n[L], 1);
     }
     for (int l = L - 1; l >= 0; --l) {
         blk_prolong<T>(PHI(l), PHI(l + 1), C.n[l]);
         for (int it = 0; it < nu2; ++it) {
-            blk_smooth<T>(PHI(l), RHS(l), C.n[l], (T)C.h2[l], 1);
-            blk_smooth<T>(PHI(l), RHS(l), C.n[l], (T)C.h2[l], 0);
+            blk_smooth<T>(PHI(l), RHS(l), C.n[l], 1);
+            blk_smooth<T>(PHI(l), RHS(l), C.n[l], 0);
         }
     }
 }
@@ -531,7 +528,6 @@ void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
 {
     MGLevel& L = d.lev[l];
     const Geo G = geo(d, l, R);
-    const T h2 = (T)(L.h * L.h);
     T* phi = lphi<T>(L);
     T* rhs = lrhs<T>(L);
     if (L.n <= COARSE_N && d.nlev - l >= 2) {
@@ -540,7 +536,6 @@ void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
         for (int q = 0; q < C.nlev; ++q) {
             MGLevel& M = d.lev[l + q];
             C.n[q] = M.n;
-            C.h2[q] = M.h * M.h;
             C.phi[q] = lphi<T>(M);
             C.rhs[q] = lrhs<T>(M);
         }
@@ -552,20 +547,20 @@ void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
         const int cells = G.n * G.n * G.n;
         const size_t sm = 2 * sizeof(T) * cells;
         ++g_launches;
-        k_bottom<T><<<R, 256, sm, s>>>(phi, rhs, G.n, h2, 48);
+        k_bottom<T><<<R, 256, sm, s>>>(phi, rhs, G.n, 48);
         return;
     }
     const int tpb = 256;
     for (int it = 0; it < nu1; ++it) {
         ++g_launches;
-        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, h2, 0);
+        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, 0);
         ++g_launches;
-        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, h2, 1);
+        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, 1);
     }
     MGLevel& C = d.lev[l + 1];
     const Geo Gc = geo(d, l + 1, R);
     ++g_launches;
-    k_resid_restrict<T, T><<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(phi, rhs, lrhs<T>(C), Gc, G.n, (T)(1.0 / (L.h * L.h)));
+    k_resid_restrict<T, T><<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(phi, rhs, lrhs<T>(C), Gc, G.n);
     ++g_launches;
     k_zero<T><<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(lphi<T>(C), Gc.cells);
     vcycle<T>(d, l + 1, R, nu1, nu2, s);
@@ -573,9 +568,9 @@ void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
     k_prolong<T><<<gridsz(G.cells, tpb), tpb, 0, s>>>(phi, lphi<T>(C), G);
     for (int it = 0; it < nu2; ++it) {
         ++g_launches;
-        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, h2, 1);
+        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, 1);
         ++g_launches;
-        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, h2, 0);
+        k_smooth<T><<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, G, 0);
     }
 }
 
@@ -594,7 +589,6 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
     const int R = P.R;
     MGLevel& L0 = d.lev[0];
     const Geo G0 = geo(d, 0, R);
-    const double inv_h2 = 1.0 / (L0.h * L0.h);
     const uint64_t per_real = G0.cells / R;
     const int items = (int)(per_real / NORM_TPB < 8 ? per_real / NORM_TPB : 8);
     const int nblk = (int)(G0.cells / ((uint64_t)NORM_TPB * items));
@@ -622,14 +616,14 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
         k_rhs_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(d.rho, Bfix, G0, qscale, bc_top,
                                                          L0.h * L0.h * std::ldexp(1.0, d.phi_F));
     }
-    const float rsc = (float)(std::ldexp(1.0, -d.phi_F) * inv_h2);
+    const float rsc = (float)std::ldexp(1.0, -d.phi_F);
     const float esc = (float)std::ldexp(1.0, d.phi_F);
     for (cyc = 0; cyc <= max_cycles; ++cyc) {
         ++g_launches;
         if (fixed)
             k_resid_fixed<<<nblk, NORM_TPB, 0, s>>>(Phi, Bfix, L0.rhs32, G0, rsc, d.norm_part, cyc == 0, items);
         else
-            k_resid_norm<<<nblk, NORM_TPB, 0, s>>>(L0.phi, L0.rhs, precision == 1 ? L0.rhs32 : nullptr, G0, inv_h2,
+            k_resid_norm<<<nblk, NORM_TPB, 0, s>>>(L0.phi, L0.rhs, precision == 1 ? L0.rhs32 : nullptr, G0,
                                                    d.norm_part, cyc == 0, items);
         ++g_launches;
         k_norm_final<<<R, 256, 0, s>>>(d.norm_part, bpr, R, d.norm_out);
@@ -708,17 +702,20 @@ void launch_unpack_field(const Params& P, Dev& d, double* E3, cudaStream_t s)
     k_unpack_field<<<gridsz(G, 256), 256, 0, s>>>(d.E, d.E32, E3, G);
 }
 
-void launch_efield(const Params& P, Dev& d, cudaStream_t s)
+void launch_efield(const Params& P, Dev& d, cudaStream_t s) { launch_efield_to(P, d, s, d.E, d.E32); }
+
+// E = -grad(phi) into the given FP64 and/or FP32 field arrays.
+void launch_efield_to(const Params& P, Dev& d, cudaStream_t s, E64* E, float4* E32)
 {
     const Geo G0 = geo(d, 0, P.R);
     const double phi_top = P.E0 * (P.hi[2] - P.lo[2]);
     ++g_launches;
     if (d.phi_F > 0)
         k_efield_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(
-            reinterpret_cast<const long long*>(d.lev[0].phi), d.E, d.E32, G0,
+            reinterpret_cast<const long long*>(d.lev[0].phi), E, E32, G0,
             std::ldexp(1.0, -d.phi_F) / (2.0 * d.lev[0].h), std::llrint(std::ldexp(phi_top, d.phi_F)));
     else
-        k_efield<<<gridsz(G0.cells, 256), 256, 0, s>>>(d.lev[0].phi, d.E, d.E32, G0, d.lev[0].h, phi_top);
+        k_efield<<<gridsz(G0.cells, 256), 256, 0, s>>>(d.lev[0].phi, E, E32, G0, d.lev[0].h, phi_top);
 }
 
 // The potential as FP64 volts into out (R n^3).
@@ -755,7 +752,8 @@ std::mutex g_noalloc_mtx;
 constexpr int NOALLOC_MAX_DEV = 64;
 void* g_noalloc_ptr[NOALLOC_MAX_DEV] = {};
 
-// b = -rho/eps0 with the electrode potentials folded in (as the step does).
+// h^2 b with b = -rho/eps0 and the electrode potentials folded in (as the
+// step does).
 __global__ void k_rhs_from_rho(const int64_t* __restrict__ rho, double* __restrict__ rhs, int n, int log2n,
                                double qscale, double phi_top, double h)
 {
@@ -764,7 +762,7 @@ __global__ void k_rhs_from_rho(const int64_t* __restrict__ rho, double* __restri
         const int k = (int)(g >> (2 * log2n));
         double b = -((double)rho[g] * qscale) / 8.8541878128e-12;
         if (k == n - 1) b = b - 2.0 * phi_top / (h * h);
-        rhs[g] = b;
+        rhs[g] = b * (h * h);
     }
 }
 

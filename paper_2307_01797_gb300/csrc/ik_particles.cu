@@ -463,11 +463,11 @@ __global__ void __launch_bounds__(TPB) k_deposit_f64(Params P, const P64* __rest
 // ------------------------------------------------------------------ rho
 // rho_fixed = 2^3s (N+ - N-) - ne_fix (units q_e 2^-3s per cell), its
 // maximum modulus, and (rhs != nullptr) the FP64 multigrid right-hand side
-// b = -rho/eps0 with the electrode potentials folded in (ghost 2 phi_b -
-// phi_1 at z faces: -2 phi_b / h^2).
+// h^2 b, b = -rho/eps0 with the electrode potentials folded in (ghost
+// 2 phi_b - phi_1 at z faces: -2 phi_b / h^2).
 __global__ void k_rho(Params P, const int64_t* __restrict__ Npos, const int64_t* __restrict__ Nneg,
                       const unsigned long long* __restrict__ ne_fix, int64_t* __restrict__ rho,
-                      double* __restrict__ rhs, uint64_t G, double qscale, double bc_top,
+                      double* __restrict__ rhs, uint64_t G, double qscale, double bc_top, double h2,
                       Counters* __restrict__ ctr)
 {
     unsigned long long amax = 0;
@@ -484,7 +484,7 @@ __global__ void k_rho(Params P, const int64_t* __restrict__ Npos, const int64_t*
             const int k = (int)((g >> (2 * P.log2n)) & (uint64_t)(P.n - 1));
             double b = -((double)rf * qscale);
             if (k == P.n - 1) b = b - bc_top;
-            rhs[g] = b;
+            rhs[g] = b * h2;
         }
     }
 #pragma unroll
@@ -1801,7 +1801,7 @@ void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
     ++g_launches;
     // the fixed-point field form builds its right-hand side in the solve
     k_rho<<<grid_for(G, 256), 256, 0, s>>>(P, d.Npos, d.Nneg, d.ne_fix, d.rho, d.phi_F > 0 ? nullptr : d.lev[0].rhs,
-                                          G, qscale, bc_top, d.ctr);
+                                          G, qscale, bc_top, P.h[2] * P.h[2], d.ctr);
 }
 
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)

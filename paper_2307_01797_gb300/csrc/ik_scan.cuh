@@ -3,12 +3,13 @@
 // supplies load(g, v[C]), store(g, excl[C], v[C]) and total(tot[C]).
 // Deterministic (integer sums), no inter-block waits.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace ik {
 
-extern unsigned long long g_launches;
+extern std::atomic<unsigned long long> g_launches;
 
 constexpr int SCAN_TPB = 512;
 constexpr int SCAN_ITEMS = 8;

@@ -2,6 +2,7 @@
 // shared by the translation units of libitokmc.
 #pragma once
 #include <cstddef>
+#include <atomic>
 #include <cstdint>
 #include <cmath>
 #include <cuda_runtime.h>
@@ -123,6 +124,8 @@ struct Dev {
     uint32_t mover_cap = 0, photo_cap = 0;
     uint64_t work_cap = 0;             // merge work area, 32-byte units
     double* stage = nullptr;           // 3 G doubles: field upload/readback
+    E64* E_next = nullptr;             // field of the next step, solved while the
+    float4* E32_next = nullptr;        //   particle stages of this step still run
     bool mixed = false;                // FP32 particle form
     int phi_F = 0;                     // potential in int64 units of 2^-phi_F V (0: FP64 potential)
 };
@@ -179,13 +182,14 @@ void launch_set_particles(const Params& P, Dev& d, const double* x, const double
 int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2, unsigned long long rho_absmax,
                 int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out);
 void launch_efield(const Params& P, Dev& d, cudaStream_t s);
+void launch_efield_to(const Params& P, Dev& d, cudaStream_t s, E64* E, float4* E32);
 void launch_phi_to_double(const Params& P, Dev& d, double* out, cudaStream_t s);
 void launch_pack_field(const Params& P, Dev& d, const double* E3, cudaStream_t s);
 void launch_unpack_field(const Params& P, Dev& d, double* E3, cudaStream_t s);
 
 // Kernel launches issued by this library (all handles), for the benchmark's
 // launch count.
-extern unsigned long long g_launches;
+extern std::atomic<unsigned long long> g_launches;
 
 // Last error of a call made without a handle (itokmc_last_error(NULL)).
 extern thread_local char g_noh_err[256];

@@ -65,6 +65,17 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+TUNE_CANDIDATES = 9
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("mg_nu1", ctypes.c_int32), ("mg_nu2", ctypes.c_int32), ("ms_field", ctypes.c_double),
+        ("cycles", ctypes.c_int32), ("n_tried", ctypes.c_int32),
+        ("nu_tried", (ctypes.c_int32 * 2) * TUNE_CANDIDATES), ("ms_tried", ctypes.c_double * TUNE_CANDIDATES),
+    ]
+
+
 class ItokmcError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
@@ -107,6 +118,7 @@ def lib(build_if_missing: bool = True):
                 "itokmc_step": ([H, i32], ctypes.c_int),
                 "itokmc_run_stage": ([H, i32], ctypes.c_int),
                 "itokmc_advance_counter": ([H], ctypes.c_int),
+                "itokmc_autotune": ([H, ctypes.POINTER(Tuning)], ctypes.c_int),
                 "itokmc_read_densities": ([H, i32, i32, vp, ctypes.c_size_t], ctypes.c_int),
                 "itokmc_get_stats": ([H, ctypes.POINTER(Stats)], ctypes.c_int),
                 "itokmc_num_particles": ([H, ctypes.POINTER(i64)], ctypes.c_int),
@@ -275,6 +287,12 @@ class Handle:
 
     def itokmc_run_stage(self, stage):
         _check(lib().itokmc_run_stage(self.h, int(stage)), self.h)
+
+    def itokmc_autotune(self):
+        t = Tuning()
+        _check(lib().itokmc_autotune(self.h, ctypes.byref(t)), self.h)
+        return {"mg_nu1": t.mg_nu1, "mg_nu2": t.mg_nu2, "ms_field": t.ms_field, "cycles": t.cycles,
+                "tried": [((t.nu_tried[k][0], t.nu_tried[k][1]), t.ms_tried[k]) for k in range(t.n_tried)]}
 
     def itokmc_advance_counter(self):
         _check(lib().itokmc_advance_counter(self.h), self.h)
