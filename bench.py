@@ -449,6 +449,74 @@ def ensemble_study(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ small config (C1)
+def small_study(args):
+    """The plain FP64 configuration in full: 64^3 over a 1 cm cube, 1.5 MV/m,
+    a Gaussian blob (sigma 0.5 mm, peak 1e18 m^-3 at 0.8 L) sampled at ppc 8
+    (about 2e5 particles), photons off, dt 1 ps, Philox seed 1, 10 steps.
+    The GPU steps are timed (FP64 and mixed); the oracle runs the same 10
+    steps with its exact field solve (timed on one host core), and the GPU
+    FP64 run, fed the oracle's field before each step, is compared with it
+    particle by particle."""
+    import torch
+    import oracle
+    from oracle import poisson
+    from paper_2307_01797_gb300 import itokmc, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ph = synth.physics_small(64)
+    st = synth.blob_state(ph, seed=1, sigma=5e-4, peak=1e18, zfrac=0.8)
+    N0, K = len(st["w"]), args.study_steps
+    out = {"study": "small", "grid": 64, "particles0": N0, "steps": K, "forms": {}}
+    for name, form in (("fp64", itokmc.FP64), ("mixed", itokmc.MIXED)):
+        H = itokmc.Handle(itokmc.make_config(ph, 8 * N0 + 100000, seed0=1, precision=form))
+        H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+        H.itokmc_solve_field()
+        for _ in range(args.warmup):
+            H.itokmc_step(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = 0
+        for _ in range(K):
+            done += H.itokmc_num_particles()
+            H.itokmc_step(1)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        H.close()
+        out["forms"][name] = {"ms_per_step": 1e3 * t / K, "particle_steps_per_s": done / t}
+    # oracle chain and the GPU FP64 run on the oracle's fields
+    p0 = oracle.make_params(ph, seed=1)
+    S = oracle.canonical(p0, st)
+    n3 = ph["n"] ** 3
+    S["Npos"] = np.zeros(n3, np.int64)
+    S["Nneg"] = np.zeros(n3, np.int64)
+    ne, _ = oracle.deposit(p0, S["x"], S["y"], S["z"], S["w"], S["cell"])
+    _, E = poisson.solve(oracle.rho_fixed(p0, ne, S["Npos"], S["Nneg"]), ph)
+    H = itokmc.Handle(itokmc.make_config(ph, 8 * N0 + 100000, seed0=1, precision=itokmc.FP64))
+    H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+    H.itokmc_set_field(*E)
+    t_or, n_or, exact = 0.0, 0, 0
+    for k in range(K):
+        t0 = time.perf_counter()
+        n_or += len(S["w"])
+        S, info = oracle.step(oracle.make_params(ph, seed=1, step=k), S, E)
+        _, E = poisson.solve(info["rho_fixed"], ph)
+        t_or += time.perf_counter() - t0
+        H.itokmc_step(1)
+        G = H.itokmc_read_particles()
+        same = (len(G["w"]) == len(S["w"]) and all(np.array_equal(np.asarray(G[c]).view(np.uint64),
+                                                                    np.asarray(S[c]).view(np.uint64))
+                                                     for c in ("x", "y", "z"))
+                and np.array_equal(G["w"], S["w"]) and np.array_equal(G["cell"], S["cell"])
+                and np.array_equal(H.itokmc_read_densities(itokmc.NPOS), S["Npos"]))
+        exact += int(same)
+        H.itokmc_set_field(*E)
+    H.close()
+    out["oracle"] = {"ms_per_step": 1e3 * t_or / K, "particle_steps_per_s": n_or / t_or, "cores": 1,
+                     "scope": "full step (push, sort, deposit, KMC, products, merge, exact field solve)"}
+    out["fp64_steps_bit_exact_with_oracle"] = f"{exact}/{K}"
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,7 +533,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default smoother counts (2, 2)")
-    ap.add_argument("--study", default=None, choices=["precision", "ensemble"],
+    ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small"],
                     help="instead of the benchmark: the FP32-vs-FP64 precision study")
     ap.add_argument("--study-steps", type=int, default=20)
     ap.add_argument("--members", type=int, default=64)
@@ -476,6 +544,9 @@ def main():
         return
     if args.study == "ensemble":
         ensemble_study(args)
+        return
+    if args.study == "small":
+        small_study(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

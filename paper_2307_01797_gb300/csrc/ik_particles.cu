@@ -199,7 +199,9 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
     }
     const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = __reduce_min_sync(0xffffffffu, v[k]);
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v[k] = min(v[k], __shfl_xor_sync(0xffffffffu, v[k], d));
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) wred[wid][k] = v[k];
@@ -1082,27 +1084,30 @@ __device__ __forceinline__ int widest_axis(const typename ET<E>::K lo[3], const 
     return axis;
 }
 
-// Minimum / maximum over a group of contiguous lanes (a node's elements in
-// one chunk of 32); the result is valid at the group's last lane.
-__device__ __forceinline__ uint32_t grp_min(unsigned grp, uint32_t v, unsigned) { return __reduce_min_sync(grp, v); }
-__device__ __forceinline__ uint32_t grp_max(unsigned grp, uint32_t v, unsigned) { return __reduce_max_sync(grp, v); }
-__device__ __forceinline__ unsigned long long grp_min(unsigned grp, unsigned long long v, unsigned lane)
+// Minimum / maximum / sum over a group of contiguous lanes (a node's
+// elements in one chunk of 32; gs = the group's first lane) by an inclusive
+// segmented shuffle scan; the result is valid at the group's last lane.
+// (Shuffles measured faster than the redux and match instructions for this
+// pattern on GB300.)
+template <class V, class Op>
+__device__ __forceinline__ V grp_scan(int gs, V v, unsigned lane, Op op)
 {
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long o = __shfl_up_sync(0xffffffffu, v, d);
-        if ((int)lane >= d && ((grp >> (lane - d)) & 1u)) v = o < v ? o : v;
+        const V o = __shfl_up_sync(0xffffffffu, v, d);
+        if ((int)lane - d >= gs) v = op(o, v);
     }
     return v;
 }
-__device__ __forceinline__ unsigned long long grp_max(unsigned grp, unsigned long long v, unsigned lane)
+template <class V>
+__device__ __forceinline__ V grp_min(int gs, V v, unsigned lane)
 {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long o = __shfl_up_sync(0xffffffffu, v, d);
-        if ((int)lane >= d && ((grp >> (lane - d)) & 1u)) v = o > v ? o : v;
-    }
-    return v;
+    return grp_scan(gs, v, lane, [](V a, V b) { return a < b ? a : b; });
+}
+template <class V>
+__device__ __forceinline__ V grp_max(int gs, V v, unsigned lane)
+{
+    return grp_scan(gs, v, lane, [](V a, V b) { return a > b ? a : b; });
 }
 
 constexpr uint8_t NO_SPLIT = 0xff;
@@ -1279,23 +1284,26 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                 const uint32_t j = b0 + lane;
                 const bool ok = j < n;
                 const uint32_t d = ok ? nid[j] : 0xffffu;
-                const unsigned grp = __match_any_sync(0xffffffffu, d);
-                const bool last = (int)lane == 31 - __clz(grp);
+                // nodes are contiguous: the lane's group is its node's range
+                // within the chunk (the tail past n forms one more group)
+                const uint32_t g0 = ok ? nb[d] : n, g1 = ok ? nb[d + 1] : b0 + 32;
+                const int gs = (int)(g0 > b0 ? g0 - b0 : 0);
+                const bool last = (int)lane == (int)((g1 < b0 + 32 ? g1 : b0 + 32) - b0) - 1;
                 E e;
                 if (ok) e = cur[j];
                 else { e.x = 0; e.y = 0; e.z = 0; e.w = 0; }
-                const uint32_t wlo = __reduce_add_sync(grp, e.w & 0xffffu);
-                const uint32_t whi = __reduce_add_sync(grp, e.w >> 16);
+                const unsigned long long wsum = grp_scan(gs, (unsigned long long)e.w, lane,
+                                                         [](unsigned long long x, unsigned long long y) { return x + y; });
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     const K v = ET<E>::key(e, a);
-                    const K mn = grp_min(grp, v, lane), mx = grp_max(grp, v, lane);
+                    const K mn = grp_min(gs, v, lane), mx = grp_max(gs, v, lane);
                     if (ok && last) {
                         atomicMin(nlo + 3 * d + a, mn);
                         atomicMax(nhi + 3 * d + a, mx);
                     }
                 }
-                if (ok && last) atomicAdd(nW + d, ((unsigned long long)whi << 16) + wlo);
+                if (ok && last) atomicAdd(nW + d, wsum);
             }
             __syncwarp();
             // ---- split axis per node (NO_SPLIT below weight 2)
@@ -1335,14 +1343,12 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                 const uint32_t j = b0 + lane;
                 const bool ok = j < n;
                 const uint32_t d = ok ? nid[j] : 0xffffu;
-                const unsigned grp = __match_any_sync(0xffffffffu, d);
+                const uint32_t g0 = ok ? nb[d] : n;
+                const int gs = (int)(g0 > b0 ? g0 - b0 : 0);
                 const unsigned long long w = ok ? tmp[j].w : 0ull;
-                unsigned long long v = w;
-#pragma unroll
-                for (int k = 1; k < 32; k <<= 1) {
-                    const unsigned long long o = __shfl_up_sync(0xffffffffu, v, k);
-                    if ((int)lane >= k && ((grp >> (lane - k)) & 1u)) v += o;
-                }
+                const unsigned long long v0 = grp_scan(gs, w, lane,
+                                                       [](unsigned long long x, unsigned long long y) { return x + y; });
+                unsigned long long v = v0;
                 if (d == carry_d) v += carry;
                 if (ok && nax[d] != NO_SPLIT) {
                     const unsigned long long W = nW[d];
