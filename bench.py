@@ -526,7 +526,8 @@ def main():
     ap.add_argument("--form", default="both", choices=["fp64", "mixed", "both"],
                     help="both: the FP64 plain form gives the headline, the mixed form is reported beside it")
     ap.add_argument("--n", type=int, default=256)
-    ap.add_argument("--particles", type=float, default=2e7)
+    ap.add_argument("--particles", type=float, default=1e8,
+                    help="target superparticle count of the synthetic discharge tree (about 7e7 are placed)")
     ap.add_argument("--ref-particles", type=int, default=2000000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cap-factor", type=float, default=4.0)

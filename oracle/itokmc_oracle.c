@@ -12,9 +12,11 @@
  * Every function below follows the paper in the paper's order.  Where the
  * paper leaves a detail open (cell-centred indexing, tie-breaks, random-number
  * layout, particle boundary conditions ...) the reading adopted is stated at
- * the function.  Compile with -O2 -ffp-contract=off (no fused multiply-add,
+ * the function.  Compile with -O2 -ffp-contract=off (no implicit contraction,
  * no fast-math) so that every floating-point operation is a single IEEE-754
- * round-to-nearest operation performed in the order written.
+ * round-to-nearest operation performed in the order written; fused
+ * multiply-adds appear only as explicit fma() calls (one rounding each: the
+ * series evaluations and the interpolation sums).
  *
  * Contents
  *   Philox4x32-10 counter RNG      (Salmon et al., SC'11)
@@ -167,17 +169,17 @@ double ora_log(double x)
     double s = f / (2.0 + f);
     double z = s * s;
     double p = 1.0 / 21.0;
-    p = p * z + 1.0 / 19.0;
-    p = p * z + 1.0 / 17.0;
-    p = p * z + 1.0 / 15.0;
-    p = p * z + 1.0 / 13.0;
-    p = p * z + 1.0 / 11.0;
-    p = p * z + 1.0 / 9.0;
-    p = p * z + 1.0 / 7.0;
-    p = p * z + 1.0 / 5.0;
-    p = p * z + 1.0 / 3.0;
+    p = fma(p, z, 1.0 / 19.0);
+    p = fma(p, z, 1.0 / 17.0);
+    p = fma(p, z, 1.0 / 15.0);
+    p = fma(p, z, 1.0 / 13.0);
+    p = fma(p, z, 1.0 / 11.0);
+    p = fma(p, z, 1.0 / 9.0);
+    p = fma(p, z, 1.0 / 7.0);
+    p = fma(p, z, 1.0 / 5.0);
+    p = fma(p, z, 1.0 / 3.0);
     double two_s = 2.0 * s;
-    double lnm = two_s + two_s * (z * p);
+    double lnm = fma(two_s, z * p, two_s);
     double de = (double)e;
     return de * ORA_LN2_HI + (de * ORA_LN2_LO + lnm);
 }
@@ -190,19 +192,19 @@ double ora_exp(double x)
     double nd = rint(x * 1.44269504088896340736);   /* x / ln2 */
     double r = (x - nd * ORA_LN2_HI) - nd * ORA_LN2_LO;
     double p = 1.0 / 6227020800.0;                  /* 1/13! */
-    p = p * r + 1.0 / 479001600.0;                  /* 1/12! */
-    p = p * r + 1.0 / 39916800.0;                   /* 1/11! */
-    p = p * r + 1.0 / 3628800.0;                    /* 1/10! */
-    p = p * r + 1.0 / 362880.0;                     /* 1/9!  */
-    p = p * r + 1.0 / 40320.0;
-    p = p * r + 1.0 / 5040.0;
-    p = p * r + 1.0 / 720.0;
-    p = p * r + 1.0 / 120.0;
-    p = p * r + 1.0 / 24.0;
-    p = p * r + 1.0 / 6.0;
-    p = p * r + 0.5;
-    p = p * r + 1.0;
-    p = p * r + 1.0;
+    p = fma(p, r, 1.0 / 479001600.0);                  /* 1/12! */
+    p = fma(p, r, 1.0 / 39916800.0);                   /* 1/11! */
+    p = fma(p, r, 1.0 / 3628800.0);                    /* 1/10! */
+    p = fma(p, r, 1.0 / 362880.0);                     /* 1/9!  */
+    p = fma(p, r, 1.0 / 40320.0);
+    p = fma(p, r, 1.0 / 5040.0);
+    p = fma(p, r, 1.0 / 720.0);
+    p = fma(p, r, 1.0 / 120.0);
+    p = fma(p, r, 1.0 / 24.0);
+    p = fma(p, r, 1.0 / 6.0);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    p = fma(p, r, 1.0);
     int n = (int)nd;
     if (n > 1023) {                                 /* 2^n overflows alone */
         return (p * 2.0) * bits_to_double((uint64_t)(n - 1 + 1023) << 52);
@@ -222,24 +224,24 @@ void ora_sincos2pi(double u, double* s_out, double* c_out)
     double a = f * 1.57079632679489661923;          /* pi/2 */
     double z = a * a;
     double sp = -1.0 / 355687428096000.0;           /* -1/17! */
-    sp = sp * z + 1.0 / 1307674368000.0;            /* 1/15!  */
-    sp = sp * z - 1.0 / 6227020800.0;               /* 1/13!  */
-    sp = sp * z + 1.0 / 39916800.0;                 /* 1/11!  */
-    sp = sp * z - 1.0 / 362880.0;
-    sp = sp * z + 1.0 / 5040.0;
-    sp = sp * z - 1.0 / 120.0;
-    sp = sp * z + 1.0 / 6.0;
-    double sa = a - a * (z * sp);
+    sp = fma(sp, z, 1.0 / 1307674368000.0);            /* 1/15!  */
+    sp = fma(sp, z, -1.0 / 6227020800.0);               /* 1/13!  */
+    sp = fma(sp, z, 1.0 / 39916800.0);                 /* 1/11!  */
+    sp = fma(sp, z, -1.0 / 362880.0);
+    sp = fma(sp, z, 1.0 / 5040.0);
+    sp = fma(sp, z, -1.0 / 120.0);
+    sp = fma(sp, z, 1.0 / 6.0);
+    double sa = fma(-a, z * sp, a);
     double cp = 1.0 / 6402373705728000.0;           /* 1/18! */
-    cp = cp * z - 1.0 / 20922789888000.0;           /* 1/16! */
-    cp = cp * z + 1.0 / 87178291200.0;              /* 1/14! */
-    cp = cp * z - 1.0 / 479001600.0;                /* 1/12! */
-    cp = cp * z + 1.0 / 3628800.0;
-    cp = cp * z - 1.0 / 40320.0;
-    cp = cp * z + 1.0 / 720.0;
-    cp = cp * z - 1.0 / 24.0;
-    cp = cp * z + 0.5;
-    double ca = 1.0 - z * cp;
+    cp = fma(cp, z, -1.0 / 20922789888000.0);           /* 1/16! */
+    cp = fma(cp, z, 1.0 / 87178291200.0);              /* 1/14! */
+    cp = fma(cp, z, -1.0 / 479001600.0);                /* 1/12! */
+    cp = fma(cp, z, 1.0 / 3628800.0);
+    cp = fma(cp, z, -1.0 / 40320.0);
+    cp = fma(cp, z, 1.0 / 720.0);
+    cp = fma(cp, z, -1.0 / 24.0);
+    cp = fma(cp, z, 0.5);
+    double ca = fma(-z, cp, 1.0);
     int qi = ((int)q) & 3;
     double s, c;
     switch (qi) {
@@ -375,7 +377,7 @@ static int inside(const ora_params* p, const double X[3])
 
 /* Trilinear (CIC) interpolation of a cell-centred field at X (Sec. 4.2,     */
 /* V_p = v(X_p), Sec. 3.1).  Sum order: z outer, y, x inner; weight product  */
-/* (wx*wy)*wz.                                                               */
+/* (wx*wy)*wz, accumulated by fused multiply-add.                            */
 static double interp(const ora_params* p, const double* F, const int ia[3], const int ib[3],
                      const double f[3])
 {
@@ -387,7 +389,7 @@ static double interp(const ora_params* p, const double* F, const int ia[3], cons
     for (int c = 0; c < 2; ++c)
         for (int b = 0; b < 2; ++b)
             for (int a = 0; a < 2; ++a)
-                acc = acc + ((wx[a] * wy[b]) * wz[c]) * F[lin(p, ix[a], iy[b], iz[c])];
+                acc = fma((wx[a] * wy[b]) * wz[c], F[lin(p, ix[a], iy[b], iz[c])], acc);
     return acc;
 }
 

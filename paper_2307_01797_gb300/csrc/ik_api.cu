@@ -155,6 +155,16 @@ int ensure_work_cap(itokmc_handle* h, uint64_t need)
     return ITOKMC_OK;
 }
 
+// The field stream gets the highest priority: the solve is the longer of
+// the two concurrent branches of a step, the particle kernels fill in.
+cudaError_t create_field_stream(cudaStream_t* sf)
+{
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e != cudaSuccess) return e;
+    return cudaStreamCreateWithPriority(sf, cudaStreamNonBlocking, hi);
+}
+
 int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
 int status_of_err(itokmc_handle* h, unsigned err)
@@ -255,13 +265,14 @@ int stage_particles(itokmc_handle* h)
 
 // a5 on stream s into the field arrays E / E32 (the handle's own, or the
 // next step's when the solve overlaps the particle stages).
-int stage_field_on(itokmc_handle* h, cudaStream_t s, ik::E64* E, float4* E32, unsigned long long rho_absmax)
+int stage_field_on(itokmc_handle* h, cudaStream_t s, ik::E64* E, float4* E32, unsigned long long rho_absmax,
+                   bool extrapolate = false)
 {
     IK_CHECK(h, cudaEventRecord(h->ev[6], s));
     int cycles = 0;
     double rel = 0.0;
     const int st = ik::field_solve(h->P, h->d, h->d.phi_F > 0 ? 2 : h->field_prec, h->cfg.mg_rtol, h->cfg.mg_nu1,
-                                   h->cfg.mg_nu2, rho_absmax, h->cfg.mg_max_cycles, s, &cycles, &rel);
+                                   h->cfg.mg_nu2, rho_absmax, h->cfg.mg_max_cycles, s, &cycles, &rel, extrapolate);
     if (st == -3) return cuda_check(h, cudaGetLastError(), "field solve");
     ik::launch_efield_to(h->P, h->d, s, E, E32);
     IK_CHECK(h, cudaEventRecord(h->ev[7], s));
@@ -299,7 +310,7 @@ int full_step(itokmc_handle* h)
             ferr = "field thread: cudaSetDevice";
             return;
         }
-        frc = stage_field_on(h, h->sf, h->d.E_next, h->d.E32_next, amax);
+        frc = stage_field_on(h, h->sf, h->d.E_next, h->d.E32_next, amax, true);
         if (frc) {
             std::lock_guard<std::mutex> lk(h->emtx);
             ferr = h->err;
@@ -441,6 +452,7 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     }
     d.fired = dalloc_n<int64_t>(h, 3 * G, &rc);
     d.stage = dalloc_n<double>(h, 3 * G, &rc);
+    d.phi_prev = dalloc_n<double>(h, G, &rc);
     d.photos = dalloc_n<ik::Photo>(h, d.photo_cap, &rc);
     d.photo_sorted = dalloc_n<uint32_t>(h, d.photo_cap, &rc);
     d.photo_cnt = dalloc_n<int32_t>(h, G, &rc);
@@ -484,7 +496,7 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     for (int e = 0; e < 8 && !rc; ++e)
         if (cudaEventCreate(&h->ev[e]) != cudaSuccess) rc = fail(h, ITOKMC_ERR_CUDA, "event create");
     if (!rc && (cudaGetDevice(&h->device) != cudaSuccess ||
-                cudaStreamCreateWithFlags(&h->sf, cudaStreamNonBlocking) != cudaSuccess ||
+                create_field_stream(&h->sf) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess))
         rc = fail(h, ITOKMC_ERR_CUDA, "field stream");

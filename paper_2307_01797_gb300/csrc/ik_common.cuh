@@ -116,17 +116,17 @@ __device__ __forceinline__ double dlog(double x)
     const double s = f / (2.0 + f);
     const double z = s * s;
     double p = 1.0 / 21.0;
-    p = p * z + 1.0 / 19.0;
-    p = p * z + 1.0 / 17.0;
-    p = p * z + 1.0 / 15.0;
-    p = p * z + 1.0 / 13.0;
-    p = p * z + 1.0 / 11.0;
-    p = p * z + 1.0 / 9.0;
-    p = p * z + 1.0 / 7.0;
-    p = p * z + 1.0 / 5.0;
-    p = p * z + 1.0 / 3.0;
+    p = __fma_rn(p, z, 1.0 / 19.0);
+    p = __fma_rn(p, z, 1.0 / 17.0);
+    p = __fma_rn(p, z, 1.0 / 15.0);
+    p = __fma_rn(p, z, 1.0 / 13.0);
+    p = __fma_rn(p, z, 1.0 / 11.0);
+    p = __fma_rn(p, z, 1.0 / 9.0);
+    p = __fma_rn(p, z, 1.0 / 7.0);
+    p = __fma_rn(p, z, 1.0 / 5.0);
+    p = __fma_rn(p, z, 1.0 / 3.0);
     const double t = 2.0 * s;
-    const double lnm = t + t * (z * p);
+    const double lnm = __fma_rn(t, z * p, t);
     const double de = (double)e;
     return de * 6.93147180369123816490e-01 + (de * 1.90821492927058770002e-10 + lnm);
 }
@@ -140,19 +140,19 @@ __device__ __forceinline__ double dexp(double x)
     const double nd = rint(x * 1.44269504088896340736);
     const double r = (x - nd * 6.93147180369123816490e-01) - nd * 1.90821492927058770002e-10;
     double p = 1.0 / 6227020800.0;
-    p = p * r + 1.0 / 479001600.0;
-    p = p * r + 1.0 / 39916800.0;
-    p = p * r + 1.0 / 3628800.0;
-    p = p * r + 1.0 / 362880.0;
-    p = p * r + 1.0 / 40320.0;
-    p = p * r + 1.0 / 5040.0;
-    p = p * r + 1.0 / 720.0;
-    p = p * r + 1.0 / 120.0;
-    p = p * r + 1.0 / 24.0;
-    p = p * r + 1.0 / 6.0;
-    p = p * r + 0.5;
-    p = p * r + 1.0;
-    p = p * r + 1.0;
+    p = __fma_rn(p, r, 1.0 / 479001600.0);
+    p = __fma_rn(p, r, 1.0 / 39916800.0);
+    p = __fma_rn(p, r, 1.0 / 3628800.0);
+    p = __fma_rn(p, r, 1.0 / 362880.0);
+    p = __fma_rn(p, r, 1.0 / 40320.0);
+    p = __fma_rn(p, r, 1.0 / 5040.0);
+    p = __fma_rn(p, r, 1.0 / 720.0);
+    p = __fma_rn(p, r, 1.0 / 120.0);
+    p = __fma_rn(p, r, 1.0 / 24.0);
+    p = __fma_rn(p, r, 1.0 / 6.0);
+    p = __fma_rn(p, r, 0.5);
+    p = __fma_rn(p, r, 1.0);
+    p = __fma_rn(p, r, 1.0);
     const int n = (int)nd;
     if (n > 1023) return (p * 2.0) * __longlong_as_double((long long)(n - 1 + 1023) << 52);
     if (n < -1020) {
@@ -172,24 +172,24 @@ __device__ __forceinline__ void dsincos2pi(double u, double* so, double* co)
     const double a = f * 1.57079632679489661923;
     const double z = a * a;
     double sp = -1.0 / 355687428096000.0;
-    sp = sp * z + 1.0 / 1307674368000.0;
-    sp = sp * z - 1.0 / 6227020800.0;
-    sp = sp * z + 1.0 / 39916800.0;
-    sp = sp * z - 1.0 / 362880.0;
-    sp = sp * z + 1.0 / 5040.0;
-    sp = sp * z - 1.0 / 120.0;
-    sp = sp * z + 1.0 / 6.0;
-    const double sa = a - a * (z * sp);
+    sp = __fma_rn(sp, z, 1.0 / 1307674368000.0);
+    sp = __fma_rn(sp, z, -1.0 / 6227020800.0);
+    sp = __fma_rn(sp, z, 1.0 / 39916800.0);
+    sp = __fma_rn(sp, z, -1.0 / 362880.0);
+    sp = __fma_rn(sp, z, 1.0 / 5040.0);
+    sp = __fma_rn(sp, z, -1.0 / 120.0);
+    sp = __fma_rn(sp, z, 1.0 / 6.0);
+    const double sa = __fma_rn(-a, z * sp, a);
     double cp = 1.0 / 6402373705728000.0;
-    cp = cp * z - 1.0 / 20922789888000.0;
-    cp = cp * z + 1.0 / 87178291200.0;
-    cp = cp * z - 1.0 / 479001600.0;
-    cp = cp * z + 1.0 / 3628800.0;
-    cp = cp * z - 1.0 / 40320.0;
-    cp = cp * z + 1.0 / 720.0;
-    cp = cp * z - 1.0 / 24.0;
-    cp = cp * z + 0.5;
-    const double ca = 1.0 - z * cp;
+    cp = __fma_rn(cp, z, -1.0 / 20922789888000.0);
+    cp = __fma_rn(cp, z, 1.0 / 87178291200.0);
+    cp = __fma_rn(cp, z, -1.0 / 479001600.0);
+    cp = __fma_rn(cp, z, 1.0 / 3628800.0);
+    cp = __fma_rn(cp, z, -1.0 / 40320.0);
+    cp = __fma_rn(cp, z, 1.0 / 720.0);
+    cp = __fma_rn(cp, z, -1.0 / 24.0);
+    cp = __fma_rn(cp, z, 0.5);
+    const double ca = __fma_rn(-z, cp, 1.0);
     switch (((int)q) & 3) {
     case 0: *so = sa; *co = ca; break;
     case 1: *so = ca; *co = -sa; break;

@@ -14,6 +14,7 @@
 // (phi += V32(b - A phi) until the FP64 residual meets the tolerance).
 // Realizations are stacked (slowest index) and solved together; each has
 // its own convergence test.  Norms are reduced in a fixed order.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -361,6 +362,18 @@ __global__ void k_shift_fixed(long long* __restrict__ Phi, int sh, uint64_t cell
         Phi[t] = (Phi[t] + half) >> sh;
 }
 
+// phi <- 2 phi - prev, prev <- the old phi (with no previous potential yet:
+// prev <- phi only).
+template <class T>
+__global__ void k_extrapolate(T* __restrict__ phi, T* __restrict__ prev, uint64_t cells, bool have)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        const T v = phi[t];
+        if (have) phi[t] = (v + v) - prev[t];
+        prev[t] = v;
+    }
+}
+
 __global__ void k_phi_to_double(const long long* __restrict__ Phi, double* __restrict__ out, double sc, uint64_t cells)
 {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cells; t += (uint64_t)gridDim.x * blockDim.x)
@@ -584,7 +597,7 @@ constexpr int MAX_REAL_NORM = 4096;
 // convergence, ITOKMC_ERR_NOCONV (-6) if max_cycles is reached or the
 // potential leaves the fixed-point range.
 int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2, unsigned long long rho_absmax,
-                int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out)
+                int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out, bool extrapolate)
 {
     const int R = P.R;
     MGLevel& L0 = d.lev[0];
@@ -608,6 +621,11 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
         if (F < d.phi_F) {
             ++g_launches;
             k_shift_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(Phi, d.phi_F - F, G0.cells);
+            if (d.phi_prev && d.have_prev) {
+                ++g_launches;
+                k_shift_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(reinterpret_cast<long long*>(d.phi_prev),
+                                                                   d.phi_F - F, G0.cells);
+            }
             d.phi_F = F;
         }
         double qscale, bc_top;
@@ -616,9 +634,31 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
         k_rhs_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(d.rho, Bfix, G0, qscale, bc_top,
                                                          L0.h * L0.h * std::ldexp(1.0, d.phi_F));
     }
+    // initial guess 2 phi_k - phi_{k-1} (the previous potential is kept)
+    if (extrapolate && d.phi_prev) {
+        ++g_launches;
+        if (fixed)
+            k_extrapolate<long long><<<gridsz(G0.cells, 256), 256, 0, s>>>(
+                Phi, reinterpret_cast<long long*>(d.phi_prev), G0.cells, d.have_prev);
+        else
+            k_extrapolate<double><<<gridsz(G0.cells, 256), 256, 0, s>>>(
+                L0.phi, reinterpret_cast<double*>(d.phi_prev), G0.cells, d.have_prev);
+        d.have_prev = true;
+    }
     const float rsc = (float)std::ldexp(1.0, -d.phi_F);
     const float esc = (float)std::ldexp(1.0, d.phi_F);
+    // FP64 V-cycles: the residual norm only serves the convergence test, so
+    // it is evaluated at cycle 0 and then at the cycle the observed
+    // convergence factor predicts (refinement forms need the residual every
+    // outer iteration as the right-hand side of the correction).
+    int next_check = 0;
+    double rho_est = 0.1, prev_rel = -1.0;
+    int prev_cyc = 0;
     for (cyc = 0; cyc <= max_cycles; ++cyc) {
+        if (precision == 0 && cyc < next_check && cyc < max_cycles) {
+            vcycle<double>(d, 0, R, nu1, nu2, s);
+            continue;
+        }
         ++g_launches;
         if (fixed)
             k_resid_fixed<<<nblk, NORM_TPB, 0, s>>>(Phi, Bfix, L0.rhs32, G0, rsc, d.norm_part, cyc == 0, items);
@@ -640,6 +680,16 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
         }
         if (done) { status = 0; break; }
         if (cyc == max_cycles || !std::isfinite(worst)) break;
+        if (precision == 0) {
+            if (prev_rel > 0.0 && worst > 0.0 && cyc > prev_cyc) {
+                rho_est = std::pow(worst / prev_rel, 1.0 / (cyc - prev_cyc));
+                rho_est = std::min(0.5, std::max(0.02, rho_est));
+            }
+            prev_rel = worst;
+            prev_cyc = cyc;
+            const double need = worst > 0.0 ? std::log(rtol / worst) / std::log(rho_est) : 1.0;
+            next_check = cyc + std::max(1, (int)std::floor(need));
+        }
         if (precision >= 1) {
             ++g_launches;
             k_zero<float><<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi32, G0.cells);

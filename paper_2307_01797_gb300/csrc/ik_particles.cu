@@ -68,9 +68,9 @@ __device__ __forceinline__ void interp_f64(const Params& P, const E64* __restric
             for (int a = 0; a < 2; ++a) {
                 const double wgt = (wx[a] * wy[b]) * wz[c];
                 const E64 e = ld_e64(E + ((size_t)iz[c] * P.n + iy[b]) * P.n + ix[a]);
-                ax = ax + wgt * e.x;
-                ay = ay + wgt * e.y;
-                az = az + wgt * e.z;
+                ax = __fma_rn(wgt, e.x, ax);
+                ay = __fma_rn(wgt, e.y, ay);
+                az = __fma_rn(wgt, e.z, az);
             }
     Ep[0] = ax; Ep[1] = ay; Ep[2] = az;
 }
@@ -152,6 +152,25 @@ __device__ __forceinline__ void stencil_f64(const Params& P, const double X[3], 
         double f;
         cic_axis(X[a], P.lo[a], P.h[a], P.n, S.ia[a], S.ib[a], f);
         const long long q = (long long)floor(f * scale);
+        S.A[a][0] = one - q;
+        S.A[a][1] = q;
+    }
+}
+
+// The same stencil from precomputed quotients qd = (x - lo) / h (the push
+// needs them for the cell index too): u = qd - 1/2 as in cic_axis.
+__device__ __forceinline__ void stencil_f64_q(const Params& P, const double qd[3], Stencil& S)
+{
+    const long long one = 1ll << P.frac_bits;
+    const double scale = (double)one;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double u = qd[a] - 0.5;
+        const double fl = floor(u);
+        const int i0 = (int)fl;
+        S.ia[a] = clampi(i0, P.n);
+        S.ib[a] = clampi(i0 + 1, P.n);
+        const long long q = (long long)floor((u - fl) * scale);
         S.A[a][0] = one - q;
         S.A[a][1] = q;
     }
@@ -301,15 +320,21 @@ __global__ void __launch_bounds__(TPB) k_push_f64(
         P64 q;
         q.x = Xn[0]; q.y = Xn[1]; q.z = Xn[2]; q.w = w;
         if (inside) {
-            const int ix = cell_axis(Xn[0], P.lo[0], P.h[0], P.n);
-            const int iy = cell_axis(Xn[1], P.lo[1], P.h[1], P.n);
-            const int iz = cell_axis(Xn[2], P.lo[2], P.h[2], P.n);
-            gnew = (uint32_t)(ebase + ((size_t)iz * P.n + iy) * P.n + ix);
+            // one division per axis serves the cell index and the stencil
+            double qd[3];
+            int ic[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                qd[a] = (Xn[a] - P.lo[a]) / P.h[a];
+                const int ci = (int)floor(qd[a]);
+                ic[a] = ci > P.n - 1 ? P.n - 1 : (ci < 0 ? 0 : ci);
+            }
+            gnew = (uint32_t)(ebase + ((size_t)ic[2] * P.n + ic[1]) * P.n + ic[0]);
             alive = true;
             mover = gnew != gold;
             q.cell = gnew;
             keyB[i] = gnew | (mover ? KEY_MOVER : 0u);
-            stencil_f64(P, Xn, S);
+            stencil_f64_q(P, qd, S);
             if (mover) {
                 atomicAdd(in_cnt + gnew, 1);
                 if (gold < gnew) atomicAdd(in_before + gnew, 1);

@@ -128,6 +128,8 @@ struct Dev {
     float4* E32_next = nullptr;        //   particle stages of this step still run
     bool mixed = false;                // FP32 particle form
     int phi_F = 0;                     // potential in int64 units of 2^-phi_F V (0: FP64 potential)
+    void* phi_prev = nullptr;          // potential of the previous solve (initial-guess extrapolation)
+    bool have_prev = false;
 };
 
 // Right-hand side constants: b = -rho_fixed qscale, minus bc_top in the top
@@ -180,7 +182,7 @@ void launch_set_particles(const Params& P, Dev& d, const double* x, const double
                           uint64_t G, cudaStream_t s);
 // ik_field.cu
 int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2, unsigned long long rho_absmax,
-                int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out);
+                int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out, bool extrapolate = false);
 void launch_efield(const Params& P, Dev& d, cudaStream_t s);
 void launch_efield_to(const Params& P, Dev& d, cudaStream_t s, E64* E, float4* E32);
 void launch_phi_to_double(const Params& P, Dev& d, double* out, cudaStream_t s);
