@@ -347,12 +347,23 @@ static int64_t lin(const ora_params* p, int i, int j, int k)
 
 static int clampi(int i, int n) { return i < 0 ? 0 : (i > n - 1 ? n - 1 : i); }
 
+/* (x-lo)/h in grid units: the quotient by the reciprocal r = 1/h with one   */
+/* fused correction, q0 = d r, q = q0 + (d - q0 h) r (Markstein's step; both  */
+/* fused operations are single IEEE roundings).                             */
+static double grid_quot(const ora_params* p, int ax, double x)
+{
+    double h = cell_h(p, ax);
+    double r = 1.0 / h;
+    double d = x - p->lo[ax];
+    double q0 = d * r;
+    return fma(fma(-q0, h, d), r, q0);
+}
+
 /* CIC stencil along one axis: u = (x-lo)/h - 1/2, i0 = floor(u), f = u-i0; */
 /* weights (1-f, f) on cells (i0, i0+1), indices folded onto [0, n-1].      */
 static void cic_axis(const ora_params* p, int ax, double x, int* ia, int* ib, double* f_out)
 {
-    double h = cell_h(p, ax);
-    double u = (x - p->lo[ax]) / h - 0.5;
+    double u = grid_quot(p, ax, x) - 0.5;
     double fl = floor(u);
     int i0 = (int)fl;
     *f_out = u - fl;
@@ -363,8 +374,7 @@ static void cic_axis(const ora_params* p, int ax, double x, int* ia, int* ib, do
 /* Cell of a position known to lie in [lo, hi): floor((x-lo)/h), top-clamped. */
 static int cell_axis(const ora_params* p, int ax, double x)
 {
-    double h = cell_h(p, ax);
-    int i = (int)floor((x - p->lo[ax]) / h);
+    int i = (int)floor(grid_quot(p, ax, x));
     return i > p->n - 1 ? p->n - 1 : (i < 0 ? 0 : i);
 }
 

@@ -394,7 +394,10 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     ik::Params& P = h->P;
     P.n = n; P.n3 = n * n * n; P.R = R; P.log2n = ilog2(n);
     P.ppc = cfg->ppc; P.n_new = cfg->n_new; P.n_crit = cfg->n_crit; P.n_ssa = cfg->n_ssa; P.frac_bits = cfg->frac_bits;
-    for (int a = 0; a < 3; ++a) { P.lo[a] = cfg->lo[a]; P.hi[a] = cfg->hi[a]; P.h[a] = (cfg->hi[a] - cfg->lo[a]) / n; }
+    for (int a = 0; a < 3; ++a) {
+        P.lo[a] = cfg->lo[a]; P.hi[a] = cfg->hi[a]; P.h[a] = (cfg->hi[a] - cfg->lo[a]) / n;
+        P.rh[a] = 1.0 / P.h[a];
+    }
     P.dt = cfg->dt; P.mu = cfg->mu; P.D = cfg->D; P.alpha_A = cfg->alpha_A; P.alpha_B = cfg->alpha_B; P.eta = cfg->eta;
     P.photon_ratio = cfg->photon_ratio; P.kappa_lo = cfg->kappa_lo; P.kappa_hi = cfg->kappa_hi; P.eps = cfg->eps;
     P.sdt = sqrt((2.0 * cfg->D) * cfg->dt);

@@ -20,7 +20,7 @@ struct Params {
     int R;                  // realizations
     int log2n;
     int ppc, n_new, n_crit, n_ssa, frac_bits;
-    double lo[3], hi[3], h[3];
+    double lo[3], hi[3], h[3], rh[3];   // rh = 1/h
     double dt, mu, D, alpha_A, alpha_B, eta, photon_ratio, kappa_lo, kappa_hi, eps;
     double sdt;             // sqrt(2 D dt)
     double E0;
@@ -55,6 +55,16 @@ __device__ __forceinline__ u32x4 philox10(u32x4 c, uint32_t k0, uint32_t k1)
 
 // A draw stream (key = seed, counter = (index, step, tag<<24|sub, block));
 // words are consumed in order, a block is generated every four words.
+// (2k+1) 2^-53 for a 52-bit k, assembled from its bits with integer
+// instructions (the value is exact: 2k+1 < 2^53).
+__device__ __forceinline__ double u53(uint64_t k)
+{
+    const uint64_t m = 2ull * k + 1ull;
+    const int p = 63 - __clzll((long long)m);            // leading bit, 0..52
+    const uint64_t bits = ((uint64_t)(p - 53 + 1023) << 52) | ((m << (52 - p)) & 0x000fffffffffffffull);
+    return __longlong_as_double((long long)bits);
+}
+
 struct Stream {
     uint32_t k0, k1, c0, c1, c2, blk;
     u32x4 buf;
@@ -80,7 +90,7 @@ struct Stream {
         const uint32_t a = u32();
         const uint32_t b = u32();
         const uint64_t k = ((uint64_t)a << 20) | (uint64_t)(b >> 12);
-        return (double)(2ull * k + 1ull) * 0x1p-53;
+        return u53(k);
     }
 };
 
@@ -261,10 +271,19 @@ __device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i > n 
 
 // CIC stencil along one axis for an absolute coordinate (FP64 form):
 // u = (x - lo)/h - 1/2, i0 = floor(u), f = u - i0, indices folded to [0,n-1].
-__device__ __forceinline__ void cic_axis(double x, double lo, double h, int n, int& ia, int& ib,
+// (x-lo)/h in grid units: q0 = d r, q = q0 + (d - q0 h) r with r = 1/h (one
+// fused correction; the same operations as the specification's).
+__device__ __forceinline__ double grid_quot(double x, double lo, double h, double rh)
+{
+    const double d = x - lo;
+    const double q0 = d * rh;
+    return __fma_rn(__fma_rn(-q0, h, d), rh, q0);
+}
+
+__device__ __forceinline__ void cic_axis(double x, double lo, double h, double rh, int n, int& ia, int& ib,
                                          double& f)
 {
-    const double u = (x - lo) / h - 0.5;
+    const double u = grid_quot(x, lo, h, rh) - 0.5;
     const double fl = floor(u);
     const int i0 = (int)fl;
     f = u - fl;
@@ -273,9 +292,9 @@ __device__ __forceinline__ void cic_axis(double x, double lo, double h, int n, i
 }
 
 // Cell of a coordinate known to lie in [lo, hi): floor((x-lo)/h), clamped.
-__device__ __forceinline__ int cell_axis(double x, double lo, double h, int n)
+__device__ __forceinline__ int cell_axis(double x, double lo, double h, double rh, int n)
 {
-    const int i = (int)floor((x - lo) / h);
+    const int i = (int)floor(grid_quot(x, lo, h, rh));
     return i > n - 1 ? n - 1 : (i < 0 ? 0 : i);
 }
 

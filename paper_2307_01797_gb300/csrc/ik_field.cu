@@ -869,7 +869,10 @@ extern "C" int itokmc_field_solve_noalloc(const itokmc_config* cfg, const int64_
     Params P{};
     P.n = n; P.n3 = n * n * n; P.R = 1;
     while ((1 << P.log2n) < n) ++P.log2n;
-    for (int a = 0; a < 3; ++a) { P.lo[a] = cfg->lo[a]; P.hi[a] = cfg->hi[a]; P.h[a] = (cfg->hi[a] - cfg->lo[a]) / n; }
+    for (int a = 0; a < 3; ++a) {
+        P.lo[a] = cfg->lo[a]; P.hi[a] = cfg->hi[a]; P.h[a] = (cfg->hi[a] - cfg->lo[a]) / n;
+        P.rh[a] = 1.0 / P.h[a];
+    }
     P.E0 = cfg->E0;
     P.frac_bits = cfg->frac_bits;
     Dev d;

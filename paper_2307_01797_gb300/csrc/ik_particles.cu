@@ -56,7 +56,7 @@ __device__ __forceinline__ void interp_f64(const Params& P, const E64* __restric
     int ia[3], ib[3];
     double f[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) cic_axis(X[a], P.lo[a], P.h[a], P.n, ia[a], ib[a], f[a]);
+    for (int a = 0; a < 3; ++a) cic_axis(X[a], P.lo[a], P.h[a], P.rh[a], P.n, ia[a], ib[a], f[a]);
     const double wx[2] = { 1.0 - f[0], f[0] }, wy[2] = { 1.0 - f[1], f[1] }, wz[2] = { 1.0 - f[2], f[2] };
     const int ix[2] = { ia[0], ib[0] }, iy[2] = { ia[1], ib[1] }, iz[2] = { ia[2], ib[2] };
     double ax = 0.0, ay = 0.0, az = 0.0;
@@ -86,7 +86,7 @@ __device__ __forceinline__ void deposit_f64(const Params& P, unsigned long long*
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double f;
-        cic_axis(X[a], P.lo[a], P.h[a], P.n, ia[a], ib[a], f);
+        cic_axis(X[a], P.lo[a], P.h[a], P.rh[a], P.n, ia[a], ib[a], f);
         const long long q = (long long)floor(f * scale);
         A[a][0] = one - q;
         A[a][1] = q;
@@ -150,14 +150,14 @@ __device__ __forceinline__ void stencil_f64(const Params& P, const double X[3], 
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double f;
-        cic_axis(X[a], P.lo[a], P.h[a], P.n, S.ia[a], S.ib[a], f);
+        cic_axis(X[a], P.lo[a], P.h[a], P.rh[a], P.n, S.ia[a], S.ib[a], f);
         const long long q = (long long)floor(f * scale);
         S.A[a][0] = one - q;
         S.A[a][1] = q;
     }
 }
 
-// The same stencil from precomputed quotients qd = (x - lo) / h (the push
+// The same stencil from precomputed quotients qd = grid_quot(x) (the push
 // needs them for the cell index too): u = qd - 1/2 as in cic_axis.
 __device__ __forceinline__ void stencil_f64_q(const Params& P, const double qd[3], Stencil& S)
 {
@@ -197,13 +197,16 @@ constexpr int DEP_WIN = 2048;   // cells of the block's shared deposit window (1
 // block.  The cells the block touches usually form a small box (particles are
 // sorted by cell), so the contributions are first summed in a shared-memory
 // window over that box and flushed with one global atomic per touched cell;
-// blocks whose box is too large or spans realizations add directly.  Integer
+// blocks whose box is too large or spans realizations add directly.  The
+// window keeps each 64-bit sum as two 32-bit words updated with native 32-bit
+// shared atomics: the low word's atomic returns the old value, from which the
+// carry into the high word follows exactly.  Integer
 // sums: the result does not depend on the order.  All threads of the block
 // must call this.
 __device__ __forceinline__ void block_deposit(const Params& P, unsigned long long* __restrict__ ne, bool alive, int r,
                                               const Stencil& S, uint32_t w)
 {
-    __shared__ unsigned long long win[DEP_WIN];
+    __shared__ uint32_t wlo[DEP_WIN], whi[DEP_WIN];
     __shared__ int wred[TPB / 32][8];
     __shared__ int wfin[8];
     const int BIG = 0x7fffffff;
@@ -253,7 +256,7 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
         }
         return;
     }
-    for (int t = threadIdx.x; t < (int)V; t += TPB) win[t] = 0ull;
+    for (int t = threadIdx.x; t < (int)V; t += TPB) { wlo[t] = 0u; whi[t] = 0u; }
     __syncthreads();
     if (alive) {
 #pragma unroll
@@ -263,14 +266,19 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
                     const long long val = (long long)w * S.A[0][a] * S.A[1][b] * S.A[2][c];
-                    if (val) atomicAdd(&win[((iz[c] - lo2) * e1 + (iy[b] - lo1)) * e0 + (ix[a] - lo0)],
-                                       (unsigned long long)val);
+                    if (val) {
+                        const int k = ((iz[c] - lo2) * e1 + (iy[b] - lo1)) * e0 + (ix[a] - lo0);
+                        const uint32_t lo = (uint32_t)val;
+                        const uint32_t old = atomicAdd(&wlo[k], lo);
+                        const uint32_t hc = (uint32_t)((unsigned long long)val >> 32) + (old + lo < old ? 1u : 0u);
+                        if (hc) atomicAdd(&whi[k], hc);
+                    }
                 }
     }
     __syncthreads();
     unsigned long long* base = ne + (size_t)wfin[6] * P.n3;
     for (int t = threadIdx.x; t < (int)V; t += TPB) {
-        const unsigned long long val = win[t];
+        const unsigned long long val = ((unsigned long long)whi[t] << 32) | wlo[t];
         if (val) {
             const int x = t % e0, y = (t / e0) % e1, z = t / (e0 * e1);
             atomicAdd(base + ((size_t)(z + lo2) * P.n + (y + lo1)) * P.n + (x + lo0), val);
@@ -325,7 +333,7 @@ __global__ void __launch_bounds__(TPB) k_push_f64(
             int ic[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                qd[a] = (Xn[a] - P.lo[a]) / P.h[a];
+                qd[a] = grid_quot(Xn[a], P.lo[a], P.h[a], P.rh[a]);
                 const int ci = (int)floor(qd[a]);
                 ic[a] = ci > P.n - 1 ? P.n - 1 : (ci < 0 ? 0 : ci);
             }
@@ -893,9 +901,9 @@ __global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired
                     Ya[a] = Y0[a] + rr * dir[a];
                     inside = inside && (Ya[a] >= P.lo[a]) && (Ya[a] < P.hi[a]);
                 }
-                ix = inside ? cell_axis(Ya[0], P.lo[0], P.h[0], P.n) : 0;
-                iy = inside ? cell_axis(Ya[1], P.lo[1], P.h[1], P.n) : 0;
-                iz = inside ? cell_axis(Ya[2], P.lo[2], P.h[2], P.n) : 0;
+                ix = inside ? cell_axis(Ya[0], P.lo[0], P.h[0], P.rh[0], P.n) : 0;
+                iy = inside ? cell_axis(Ya[1], P.lo[1], P.h[1], P.rh[1], P.n) : 0;
+                iz = inside ? cell_axis(Ya[2], P.lo[2], P.h[2], P.rh[2], P.n) : 0;
             }
             if (!inside) {
                 atomicAdd(&ctr->lost[r], (unsigned long long)wj);

@@ -88,9 +88,9 @@ __global__ void k_pack(Params P, const double* __restrict__ x, const double* __r
         for (int a = 0; a < 3; ++a) ok = ok && X[a] >= P.lo[a] && X[a] < P.hi[a];
         uint32_t g = 0;
         if (ok) {
-            const int ix = cell_axis(X[0], P.lo[0], P.h[0], P.n);
-            const int iy = cell_axis(X[1], P.lo[1], P.h[1], P.n);
-            const int iz = cell_axis(X[2], P.lo[2], P.h[2], P.n);
+            const int ix = cell_axis(X[0], P.lo[0], P.h[0], P.rh[0], P.n);
+            const int iy = cell_axis(X[1], P.lo[1], P.h[1], P.rh[1], P.n);
+            const int iz = cell_axis(X[2], P.lo[2], P.h[2], P.rh[2], P.n);
             g = (uint32_t)((size_t)r * P.n3 + ((size_t)iz * P.n + iy) * P.n + ix);
         } else {
             atomicOr(&ctr->err, DERR_INTERNAL);
@@ -120,7 +120,7 @@ __global__ void k_gather32(Params P, const P64* __restrict__ in, const uint32_t*
         const double X[3] = { p.x, p.y, p.z };
         float o[3];
         for (int a = 0; a < 3; ++a) {
-            float f = (float)((X[a] - P.lo[a]) / P.h[a] - (double)id[a]);
+            float f = (float)(grid_quot(X[a], P.lo[a], P.h[a], P.rh[a]) - (double)id[a]);
             if (!(f >= 0.0f)) f = 0.0f;
             if (f >= 1.0f) f = 0x1.fffffep-1f;
             o[a] = f;
