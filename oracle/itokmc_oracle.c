@@ -884,6 +884,14 @@ static void split_node(ora_mp* P, int64_t M, ora_mp* left, int64_t* nl, ora_mp* 
     for (int64_t q = pm + 1; q < M; ++q) right[(*nr)++] = P[q];
 }
 
+/* a / b given r = 1/b: q0 = a r, q = q0 + (a - q0 b) r (one fused          */
+/* correction, as for the grid quotient).                                   */
+static double quot_r(double a, double b, double r)
+{
+    double q0 = a * r;
+    return fma(fma(-q0, b, a), r, q0);
+}
+
 /* Merge one cell's list in[0..M) into at most T leaves written to out.     */
 /* Returns the number of leaves.                                             */
 static int64_t merge_cell(const ora_mp* in, int64_t M, int T, ora_mp* out)
@@ -927,13 +935,17 @@ static int64_t merge_cell(const ora_mp* in, int64_t M, int T, ora_mp* out)
         uint64_t W = 0;
         for (int64_t q = nb[d]; q < nb[d + 1]; ++q) {
             double wd = (double)cur[q].w;
-            sx = sx + wd * cur[q].X[0];
-            sy = sy + wd * cur[q].X[1];
-            sz = sz + wd * cur[q].X[2];
+            sx = fma(wd, cur[q].X[0], sx);
+            sy = fma(wd, cur[q].X[1], sy);
+            sz = fma(wd, cur[q].X[2], sz);
             W += cur[q].w;
         }
+        /* centroid: quotients by the reciprocal of W with one fused correction */
         double Wd = (double)W;
-        out[d].X[0] = sx / Wd; out[d].X[1] = sy / Wd; out[d].X[2] = sz / Wd;
+        double rw = 1.0 / Wd;
+        out[d].X[0] = quot_r(sx, Wd, rw);
+        out[d].X[1] = quot_r(sy, Wd, rw);
+        out[d].X[2] = quot_r(sz, Wd, rw);
         out[d].w = W;
         out[d].ord = d;
     }

@@ -280,6 +280,13 @@ __device__ __forceinline__ double grid_quot(double x, double lo, double h, doubl
     return __fma_rn(__fma_rn(-q0, h, d), rh, q0);
 }
 
+// a / b given r = 1/b, with the same fused correction.
+__device__ __forceinline__ double quot_r(double a, double b, double r)
+{
+    const double q0 = a * r;
+    return __fma_rn(__fma_rn(-q0, b, a), r, q0);
+}
+
 __device__ __forceinline__ void cic_axis(double x, double lo, double h, double rh, int n, int& ia, int& ib,
                                          double& f)
 {

@@ -982,8 +982,9 @@ __host__ __device__ inline MLayout merge_layout(uint32_t cap, uint32_t T, uint32
 // Merge tiers by list capacity M + ppc (a level adds at most one element
 // per node): tier 0 and 1 in shared memory (warps per block NW0 / NW1),
 // tier 2 in the global work area.
-constexpr uint32_t MERGE_CAP0 = 128, MERGE_CAP1 = 256;
+constexpr uint32_t MERGE_CAP0_MP32 = 96, MERGE_CAP0_MP = 96, MERGE_CAP1 = 256;
 constexpr int MERGE_NW0 = 4, MERGE_NW1 = 4;
+__host__ __device__ inline uint32_t merge_cap0(int esize) { return esize == 16 ? MERGE_CAP0_MP32 : MERGE_CAP0_MP; }
 
 // Per cell: W = X_e + dN + photo weight -> min(W, ppc) leaves; photo offsets;
 // work-area units (32 B) for tier-2 cells; the tier lists.
@@ -1010,7 +1011,7 @@ struct MergeScanOp {
         v[1] = photo_cnt[g];
         const long long M = (long long)(cs[g + 1] - cs[g]) + (dN > 0 ? (dN < n_new ? dN : n_new) : 0) + photo_cnt[g];
         const long long S = M + ppc;
-        const int tier = S <= MERGE_CAP0 ? 0 : (S <= MERGE_CAP1 ? 1 : 2);
+        const int tier = S <= (long long)merge_cap0(esize) ? 0 : (S <= MERGE_CAP1 ? 1 : 2);
         v[2] = (v[0] > 0 && tier == 2)
                    ? ((long long)merge_layout((uint32_t)S, (uint32_t)ppc, (uint32_t)esize, (uint32_t)ksize).bytes + 31) / 32
                    : 0;
@@ -1523,15 +1524,16 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                     for (uint32_t q = nb[d]; q < nb[d + 1]; ++q) {
                         const E e = cur[q];
                         const double wd = (double)e.w;
-                        sx = sx + wd * e.x;
-                        sy = sy + wd * e.y;
-                        sz = sz + wd * e.z;
+                        sx = __fma_rn(wd, e.x, sx);
+                        sy = __fma_rn(wd, e.y, sy);
+                        sz = __fma_rn(wd, e.z, sz);
                         Wl += e.w;
                     }
                     if (Wl > 0xffffffffull) atomicOr(&ctr->err, DERR_OVERFLOW);
-                    const double Wd = (double)Wl;
+                    // quotients by the reciprocal of W with one fused correction
+                    const double Wd = (double)Wl, rw = 1.0 / Wd;
                     P64 o;
-                    o.x = sx / Wd; o.y = sy / Wd; o.z = sz / Wd;
+                    o.x = quot_r(sx, Wd, rw); o.y = quot_r(sy, Wd, rw); o.z = quot_r(sz, Wd, rw);
                     o.cell = (uint32_t)g;
                     o.w = (uint32_t)Wl;
                     st_p64(out + o0 + d, o);
@@ -1882,7 +1884,8 @@ void launch_merge_tiers(const Params& P, Dev& d, uint64_t G, cudaStream_t s, con
 {
     using E = typename std::conditional<MX, MP32, MP>::type;
     using K = typename EKey<E>::K;
-    const MLayout L0 = merge_layout(MERGE_CAP0, P.ppc, sizeof(E), sizeof(K));
+    const uint32_t cap0 = merge_cap0((int)sizeof(E));
+    const MLayout L0 = merge_layout(cap0, P.ppc, sizeof(E), sizeof(K));
     const MLayout L1 = merge_layout(MERGE_CAP1, P.ppc, sizeof(E), sizeof(K));
     const size_t sm0 = (size_t)L0.bytes * MERGE_NW0, sm1 = (size_t)L1.bytes * MERGE_NW1;
     static bool attr = false;
@@ -1893,7 +1896,7 @@ void launch_merge_tiers(const Params& P, Dev& d, uint64_t G, cudaStream_t s, con
     g_launches += 3;
     k_merge_lv<E, false><<<152 * 16, MERGE_NW0 * 32, sm0, s>>>(
         P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
-        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.small_list, d.list_n, 0, MERGE_CAP0, d.ctr);
+        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.small_list, d.list_n, 0, cap0, d.ctr);
     k_merge_lv<E, false><<<152 * 8, MERGE_NW1 * 32, sm1, s>>>(
         P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
         d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.mid_list, d.list_n, 1, MERGE_CAP1, d.ctr);
