@@ -945,7 +945,7 @@ __global__ void k_photo_place(const Photo* __restrict__ photos, const Counters* 
 // Per-warp scratch of the merge of one cell (all node arrays for T = ppc
 // nodes, element lists for `cap` elements): byte offsets from the base.
 struct MLayout {
-    uint32_t cur, tmp, nW, nC, keys, nlo, nhi, nA, nB, nb, nb2, npm, nsh, nid, nid2, nnd, nax, nfl, bytes;
+    uint32_t cur, tmp, nW, nW2, nC, keys, nlo, nhi, nA, nB, nb, nb2, npm, nsh, nid, nid2, nnd, nax, nfl, bytes;
 };
 __host__ __device__ inline uint32_t ml_take(uint32_t& o, uint32_t bytes)
 {
@@ -960,6 +960,7 @@ __host__ __device__ inline MLayout merge_layout(uint32_t cap, uint32_t T, uint32
     L.cur = ml_take(o, cap * esize);
     L.tmp = ml_take(o, cap * esize);
     L.nW = ml_take(o, T * 8);
+    L.nW2 = ml_take(o, (T + 1) * 8);
     L.nC = ml_take(o, T * 8);
     L.keys = ml_take(o, cap * ksize);
     L.nlo = ml_take(o, 3 * T * ksize);
@@ -1209,6 +1210,7 @@ __global__ void __launch_bounds__(128) k_merge_lv(
         E* cur = reinterpret_cast<E*>(base + L.cur);
         E* tmp = reinterpret_cast<E*>(base + L.tmp);
         unsigned long long* nW = reinterpret_cast<unsigned long long*>(base + L.nW);
+        unsigned long long* nW2 = reinterpret_cast<unsigned long long*>(base + L.nW2);
         unsigned long long* nC = reinterpret_cast<unsigned long long*>(base + L.nC);
         K* keys = reinterpret_cast<K*>(base + L.keys);
         K* nlo = reinterpret_cast<K*>(base + L.nlo);
@@ -1301,43 +1303,68 @@ __global__ void __launch_bounds__(128) k_merge_lv(
             nb[0] = 0;
             nb[1] = M;
         }
-        for (uint32_t j = lane; j < M; j += 32) nid[j] = 0;
+        // root weight; the weights of later nodes follow from the splits
+        unsigned long long wroot = 0;
+        for (uint32_t j = lane; j < M; j += 32) {
+            nid[j] = 0;
+            wroot += cur[j].w;
+        }
+#pragma unroll
+        for (int dd = 16; dd > 0; dd >>= 1) wroot += __shfl_xor_sync(0xffffffffu, wroot, dd);
+        if (lane == 0) nW[0] = wroot;
         uint32_t n = M;
         int nnodes = 1;
         __syncwarp();
 
         for (int level = 1; level < T; level *= 2) {
-            // ---- node weights and bounding boxes
-            for (int d = lane; d < nnodes; d += 32) {
-                nW[d] = 0;
+            // ---- bounding boxes: one node per lane when the nodes are small
+            // (at most 4 elements on average), else group reductions per chunk
+            if (n <= 4u * (uint32_t)nnodes) {
+                for (int d = lane; d < nnodes; d += 32) {
+                    K lo[3], hi[3];
+                    const E e0 = cur[nb[d]];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) { nlo[3 * d + a] = (K)~(K)0; nhi[3 * d + a] = (K)0; }
-            }
-            __syncwarp();
-            for (uint32_t b0 = 0; b0 < n; b0 += 32) {
-                const uint32_t j = b0 + lane;
-                const bool ok = j < n;
-                const uint32_t d = ok ? nid[j] : 0xffffu;
-                // nodes are contiguous: the lane's group is its node's range
-                // within the chunk (the tail past n forms one more group)
-                const uint32_t g0 = ok ? nb[d] : n, g1 = ok ? nb[d + 1] : b0 + 32;
-                const int gs = (int)(g0 > b0 ? g0 - b0 : 0);
-                const bool last = (int)lane == (int)((g1 < b0 + 32 ? g1 : b0 + 32) - b0) - 1;
-                E e;
-                if (ok) e = cur[j];
-                else { e.x = 0; e.y = 0; e.z = 0; e.w = 0; }
-                const unsigned long long wsum = grp_scan(gs, (unsigned long long)e.w, lane,
-                                                         [](unsigned long long x, unsigned long long y) { return x + y; });
+                    for (int a = 0; a < 3; ++a) { lo[a] = ET<E>::key(e0, a); hi[a] = lo[a]; }
+                    for (uint32_t q = nb[d] + 1; q < nb[d + 1]; ++q) {
+                        const E e = cur[q];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const K v = ET<E>::key(e, a);
-                    const K mn = grp_min(gs, v, lane), mx = grp_max(gs, v, lane);
-                    if (ok && last) {
-                        atomicMin(nlo + 3 * d + a, mn);
-                        atomicMax(nhi + 3 * d + a, mx);
+                        for (int a = 0; a < 3; ++a) {
+                            const K v = ET<E>::key(e, a);
+                            lo[a] = v < lo[a] ? v : lo[a];
+                            hi[a] = v > hi[a] ? v : hi[a];
+                        }
+                    }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) { nlo[3 * d + a] = lo[a]; nhi[3 * d + a] = hi[a]; }
+                }
+            } else {
+                for (int d = lane; d < nnodes; d += 32) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) { nlo[3 * d + a] = (K)~(K)0; nhi[3 * d + a] = (K)0; }
+                }
+                __syncwarp();
+                for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+                    const uint32_t j = b0 + lane;
+                    const bool ok = j < n;
+                    const uint32_t d = ok ? nid[j] : 0xffffu;
+                    // nodes are contiguous: the lane's group is its node's range
+                    // within the chunk (the tail past n forms one more group)
+                    const uint32_t g0 = ok ? nb[d] : n, g1 = ok ? nb[d + 1] : b0 + 32;
+                    const int gs = (int)(g0 > b0 ? g0 - b0 : 0);
+                    const bool last = (int)lane == (int)((g1 < b0 + 32 ? g1 : b0 + 32) - b0) - 1;
+                    E e;
+                    if (ok) e = cur[j];
+                    else { e.x = 0; e.y = 0; e.z = 0; e.w = 0; }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const K v = ET<E>::key(e, a);
+                        const K mn = grp_min(gs, v, lane), mx = grp_max(gs, v, lane);
+                        if (ok && last) {
+                            atomicMin(nlo + 3 * d + a, mn);
+                            atomicMax(nhi + 3 * d + a, mx);
+                        }
                     }
                 }
-                if (ok && last) atomicAdd(nW + d, wsum);
             }
             __syncwarp();
             // ---- split axis per node (NO_SPLIT below weight 2)
@@ -1433,6 +1460,17 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                     const uint32_t sh = ex_c + ie - extra, ndi = nd_c + ic - cnt;
                     nsh[d] = sh;
                     nnd[d] = (uint16_t)ndi;
+                    // weights of the children: the left one holds the elements
+                    // before the median and the median's left share
+                    const unsigned long long Wd = nW[d];
+                    if (split) {
+                        const uint32_t wm = tmp[nb[d] + pm].w;
+                        const unsigned long long wl = nC[d] - wm + (lm ? (wm == 1 ? 1ull : (unsigned long long)a) : 0ull);
+                        nW2[ndi] = wl;
+                        nW2[ndi + 1] = Wd - wl;
+                    } else {
+                        nW2[ndi] = Wd;
+                    }
                     nA[d] = a;
                     nB[d] = b;
                     nfl[d] = (uint8_t)((lm ? 1 : 0) | (rm ? 2 : 0));
@@ -1484,6 +1522,7 @@ __global__ void __launch_bounds__(128) k_merge_lv(
             nnodes = (int)nd_c;
             { uint32_t* t = nb; nb = nb2; nb2 = t; }
             { uint16_t* t = nid; nid = nid2; nid2 = t; }
+            { unsigned long long* t = nW; nW = nW2; nW2 = t; }
             __syncwarp();
         }
         // ---- leaves: weight sum, weight-averaged position (list order)
