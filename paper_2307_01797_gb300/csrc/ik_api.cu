@@ -528,6 +528,8 @@ int itokmc_destroy(itokmc_handle* h)
         cudaStreamSynchronize(h->sf);
         cudaStreamDestroy(h->sf);
     }
+    for (auto& gx : h->d.vgraph)
+        if (gx) cudaGraphExecDestroy(gx);
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);

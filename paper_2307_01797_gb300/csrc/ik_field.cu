@@ -591,6 +591,56 @@ void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
 
 constexpr int MAX_REAL_NORM = 4096;
 
+// Replays (capturing first if needed) the graph of kind k on stream s:
+// k = 0: one FP64 V-cycle; k = 1: zero the FP32 correction, two FP32
+// V-cycles.  The launches of a cycle depend only on the level pointers and
+// the smoother counts, so one capture per (nu1, nu2) serves every solve.
+// Falls back to direct launches if capture is not possible.
+void run_cycles(Dev& d, int k, int R, int nu1, int nu2, cudaStream_t s)
+{
+    auto direct = [&]() {
+        if (k == 0) {
+            vcycle<double>(d, 0, R, nu1, nu2, s);
+        } else {
+            const Geo G0 = geo(d, 0, R);
+            ++g_launches;
+            k_zero<float><<<gridsz(G0.cells, 256), 256, 0, s>>>(d.lev[0].phi32, G0.cells);
+            vcycle<float>(d, 0, R, nu1, nu2, s);
+            vcycle<float>(d, 0, R, nu1, nu2, s);
+        }
+    };
+    if (d.vgraph[k] && (d.vgraph_nu[k][0] != nu1 || d.vgraph_nu[k][1] != nu2)) {
+        cudaGraphExecDestroy(d.vgraph[k]);
+        d.vgraph[k] = nullptr;
+    }
+    if (!d.vgraph[k]) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            direct();
+            return;
+        }
+        const unsigned long long l0 = g_launches.load();
+        direct();
+        const unsigned long long nk = g_launches.load() - l0;
+        g_launches -= nk;                         // captured, not run
+        if (cudaStreamEndCapture(s, &g) != cudaSuccess || !g ||
+            cudaGraphInstantiate(&d.vgraph[k], g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            d.vgraph[k] = nullptr;
+            direct();
+            return;
+        }
+        cudaGraphDestroy(g);
+        d.vgraph_nu[k][0] = nu1;
+        d.vgraph_nu[k][1] = nu2;
+        d.vgraph_kernels[k] = nk;
+    }
+    g_launches += d.vgraph_kernels[k];
+    cudaGraphLaunch(d.vgraph[k], s);
+}
+
 // precision: 0 FP64 V-cycles; 1 FP32 V-cycles in FP64 residual refinement;
 // 2 FP32 V-cycles in fixed-point residual refinement (potential in units of
 // 2^-phi_F V, right-hand side prepared by the charge kernel).  Returns 0 on
@@ -656,7 +706,7 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
     int prev_cyc = 0;
     for (cyc = 0; cyc <= max_cycles; ++cyc) {
         if (precision == 0 && cyc < next_check && cyc < max_cycles) {
-            vcycle<double>(d, 0, R, nu1, nu2, s);
+            run_cycles(d, 0, R, nu1, nu2, s);
             continue;
         }
         ++g_launches;
@@ -691,18 +741,15 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
             next_check = cyc + std::max(1, (int)std::floor(need));
         }
         if (precision >= 1) {
-            ++g_launches;
-            k_zero<float><<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi32, G0.cells);
             // inner solve of A e = r in FP32: two V-cycles per outer residual
-            vcycle<float>(d, 0, R, nu1, nu2, s);
-            vcycle<float>(d, 0, R, nu1, nu2, s);
+            run_cycles(d, 1, R, nu1, nu2, s);
             ++g_launches;
             if (fixed)
                 k_add_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(Phi, L0.phi32, esc, G0.cells);
             else
                 k_add_correction<<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi, L0.phi32, G0.cells);
         } else {
-            vcycle<double>(d, 0, R, nu1, nu2, s);
+            run_cycles(d, 0, R, nu1, nu2, s);
         }
     }
     if (cycles_out) *cycles_out = cyc;
@@ -909,6 +956,8 @@ extern "C" int itokmc_field_solve_noalloc(const itokmc_config* cfg, const int64_
     double rel = 0.0;
     const int st = field_solve(P, d, prec, cfg->mg_rtol, cfg->mg_nu1, cfg->mg_nu2, 0ull, cfg->mg_max_cycles, s, &cycles,
                                &rel);
+    for (auto& gx : d.vgraph)
+        if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
     if (cycles_out) *cycles_out = cycles;
     if (rel_out) *rel_out = rel;
     if (st == -3) {

@@ -124,6 +124,11 @@ struct Dev {
     uint32_t mover_cap = 0, photo_cap = 0;
     uint64_t work_cap = 0;             // merge work area, 32-byte units
     double* stage = nullptr;           // 3 G doubles: field upload/readback
+    // CUDA graphs of the correction sweep (FP32: zero + two V-cycles) and of
+    // one FP64 V-cycle, captured once per smoother pair and replayed
+    cudaGraphExec_t vgraph[2] = { nullptr, nullptr };
+    int vgraph_nu[2][2] = { { 0, 0 }, { 0, 0 } };
+    unsigned long long vgraph_kernels[2] = { 0, 0 };
     E64* E_next = nullptr;             // field of the next step, solved while the
     float4* E32_next = nullptr;        //   particle stages of this step still run
     bool mixed = false;                // FP32 particle form
