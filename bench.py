@@ -167,6 +167,19 @@ def config_of(args, nparticles, fp64=True):
 
 
 # ------------------------------------------------------------------ our arm
+def aggregate_ranks(ms, processed, dist, device):
+    """Whole-job figures of a replica run: the slowest rank's time (max over
+    ranks) and the particle-steps of all ranks (sum); identity on one rank."""
+    if not dist:
+        return float(ms), float(processed)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(processed)], dtype=torch.float64, device=device)
+    dist.all_reduce(p)
+    return float(t.item()), float(p.item())
+
+
 def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e):
     """Warm up and time args.steps full steps of one form on the workload;
     returns the measurements (rank-local) and the handle's stats."""
@@ -216,16 +229,7 @@ def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e)
         dist.barrier()
     clk = clocks.stop()
     launches = H.itokmc_get_stats()["kernel_launches"] - l0
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        p = torch.tensor([float(processed)], device="cuda")
-        dist.all_reduce(p)
-        processed_all = float(p.item())
-    else:
-        processed_all = float(processed)
+    ms, processed_all = aggregate_ranks(e0.elapsed_time(e1), processed, dist, "cuda")
     # push+sort+deposit+KMC scope (stage times from CUDA events on the
     # library's stream)
     core_ms = stage["transport"] + stage["kmc"]
