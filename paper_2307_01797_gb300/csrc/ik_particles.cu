@@ -1312,6 +1312,7 @@ __global__ void __launch_bounds__(128) k_merge_lv(
 #pragma unroll
         for (int dd = 16; dd > 0; dd >>= 1) wroot += __shfl_xor_sync(0xffffffffu, wroot, dd);
         if (lane == 0) nW[0] = wroot;
+        const bool w32 = wroot < (1ull << 31);
         uint32_t n = M;
         int nnodes = 1;
         __syncwarp();
@@ -1407,8 +1408,10 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                 const uint32_t g0 = ok ? nb[d] : n;
                 const int gs = (int)(g0 > b0 ? g0 - b0 : 0);
                 const unsigned long long w = ok ? tmp[j].w : 0ull;
-                const unsigned long long v0 = grp_scan(gs, w, lane,
-                                                       [](unsigned long long x, unsigned long long y) { return x + y; });
+                // 32-bit prefix sums when the cell's weight allows (warp-uniform)
+                const unsigned long long v0 =
+                    w32 ? (unsigned long long)grp_scan(gs, (uint32_t)w, lane, [](uint32_t x, uint32_t y) { return x + y; })
+                        : grp_scan(gs, w, lane, [](unsigned long long x, unsigned long long y) { return x + y; });
                 unsigned long long v = v0;
                 if (d == carry_d) v += carry;
                 if (ok && nax[d] != NO_SPLIT) {
