@@ -500,6 +500,9 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
         if (cudaEventCreate(&h->ev[e]) != cudaSuccess) rc = fail(h, ITOKMC_ERR_CUDA, "event create");
     if (!rc && (cudaGetDevice(&h->device) != cudaSuccess ||
                 create_field_stream(&h->sf) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&d.side, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&d.side_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&d.side_join, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess))
         rc = fail(h, ITOKMC_ERR_CUDA, "field stream");
@@ -530,6 +533,12 @@ int itokmc_destroy(itokmc_handle* h)
     }
     for (auto& gx : h->d.vgraph)
         if (gx) cudaGraphExecDestroy(gx);
+    if (h->d.side) {
+        cudaStreamSynchronize(h->d.side);
+        cudaStreamDestroy(h->d.side);
+    }
+    if (h->d.side_fork) cudaEventDestroy(h->d.side_fork);
+    if (h->d.side_join) cudaEventDestroy(h->d.side_join);
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);

@@ -1936,15 +1936,26 @@ void launch_merge_tiers(const Params& P, Dev& d, uint64_t G, cudaStream_t s, con
         attr = true;
     }
     g_launches += 3;
+    // tiers 1 and 2 (few, long cells) on the side stream beside tier 0
+    cudaStream_t s12 = s;
+    if (d.side) {
+        cudaEventRecord(d.side_fork, s);
+        cudaStreamWaitEvent(d.side, d.side_fork, 0);
+        s12 = d.side;
+    }
+    k_merge_lv<E, false><<<152 * 8, MERGE_NW1 * 32, sm1, s12>>>(
+        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
+        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.mid_list, d.list_n, 1, MERGE_CAP1, d.ctr);
+    k_merge_lv<E, true><<<152 * 4, 128, 0, s12>>>(
+        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
+        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.big_list, d.list_n, 2, 0, d.ctr);
     k_merge_lv<E, false><<<152 * 16, MERGE_NW0 * 32, sm0, s>>>(
         P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
         d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.small_list, d.list_n, 0, cap0, d.ctr);
-    k_merge_lv<E, false><<<152 * 8, MERGE_NW1 * 32, sm1, s>>>(
-        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
-        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.mid_list, d.list_n, 1, MERGE_CAP1, d.ctr);
-    k_merge_lv<E, true><<<152 * 4, 128, 0, s>>>(
-        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
-        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.big_list, d.list_n, 2, 0, d.ctr);
+    if (d.side) {
+        cudaEventRecord(d.side_join, d.side);
+        cudaStreamWaitEvent(s, d.side_join, 0);
+    }
 }
 
 void launch_merges(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
