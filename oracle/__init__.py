@@ -99,6 +99,7 @@ def lib():
             L.ora_sincos2pi.argtypes = [d, pd, pd]
             L.ora_poisson_draws.argtypes = [u64, u32, u32, u32, u32, d, i64, pi64]
             L.ora_uniform_draws.argtypes = [u64, u32, u32, u32, u32, i64, pd]
+            L.ora_normal_draws.argtypes = [u64, u32, u32, u32, u32, i64, pd]
             L.ora_push.argtypes = [pp, i64, pd, pd, pd, pd, pd, pd, pd, pd, pd, pi64]
             L.ora_sort_by_cell.argtypes = [i64, i64, pi64, pi64]; L.ora_sort_by_cell.restype = i64
             L.ora_deposit.argtypes = [pp, i64, pd, pd, pd, pu32, pi64, pi64, pi64]
@@ -144,6 +145,12 @@ def sincos2pi(u: float):
 def uniform_draws(seed, index, step, tag, sub, n):
     out = np.zeros(n, dtype=np.float64)
     lib().ora_uniform_draws(seed, index, step, tag, sub, n, _P(out, ctypes.c_double))
+    return out
+
+
+def normal_draws(seed, index, step, tag, sub, n):
+    out = np.zeros(n, dtype=np.float64)
+    lib().ora_normal_draws(seed, index, step, tag, sub, n, _P(out, ctypes.c_double))
     return out
 
 

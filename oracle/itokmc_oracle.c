@@ -22,6 +22,7 @@
  *   Philox4x32-10 counter RNG      (Salmon et al., SC'11)
  *   ora_log / ora_exp / sincos2pi  (argument reduction + series, own code)
  *   Poisson sampler                (inversion; PTRS of Hoermann 1993)
+ *   normal sampler                 (ziggurat of Marsaglia & Tsang 2000)
  *   push      a1+a2  -- Sec. 4.2 (CIC interpolation), Sec. 4.3 (explicit
  *                       Euler-Maruyama, first equation), Eq. ito_kernel
  *   sort      a3     -- stable sort by cell ("spatial binning", Sec. 5.6)
@@ -334,6 +335,81 @@ void ora_uniform_draws(uint64_t seed, uint32_t index, uint32_t step, uint32_t ta
 }
 
 /* ------------------------------------------------------------------------ */
+/* Standard normals by the ziggurat method (G. Marsaglia and W. W. Tsang,   */
+/* "The ziggurat method for generating random variables", J. Stat. Softw.   */
+/* 5(8), 2000), 128 layers, base-strip parameters r = 3.442619855899 and    */
+/* v = 9.91256303526217e-3 of that paper, with a 53-bit magnitude:          */
+/* each attempt takes two words U = a 2^32 + b: layer i = U mod 128, sign  */
+/* bit 7, magnitude m = U >> 11; x = m W_i is accepted at once if m < K_i,  */
+/* else by the base-strip tail (i = 0, Marsaglia's tail method) or the      */
+/* wedge test against exp(-x^2/2).  The tables come from the paper's setup  */
+/* recurrence, evaluated with the project's own ln/exp and IEEE sqrt.       */
+/* ------------------------------------------------------------------------ */
+#define ZIG_R 3.442619855899
+#define ZIG_V 9.91256303526217e-3
+#define ZIG_M 9007199254740992.0            /* 2^53 */
+static double zig_w[128], zig_f[128];
+static uint64_t zig_k[128];
+static int zig_ready = 0;
+
+static void zig_init(void)
+{
+    double q = ZIG_V / ora_exp(-0.5 * ZIG_R * ZIG_R);
+    zig_k[0] = (uint64_t)((ZIG_R / q) * ZIG_M);
+    zig_k[1] = 0;
+    zig_w[0] = q / ZIG_M;
+    zig_w[127] = ZIG_R / ZIG_M;
+    zig_f[0] = 1.0;
+    zig_f[127] = ora_exp(-0.5 * ZIG_R * ZIG_R);
+    double d = ZIG_R, t = ZIG_R;
+    for (int i = 126; i >= 1; --i) {
+        d = sqrt(-2.0 * ora_log(ZIG_V / d + ora_exp(-0.5 * d * d)));
+        zig_k[i + 1] = (uint64_t)((d / t) * ZIG_M);
+        t = d;
+        zig_f[i] = ora_exp(-0.5 * d * d);
+        zig_w[i] = d / ZIG_M;
+    }
+    zig_ready = 1;
+}
+
+static double ora_normal(ora_stream* s)
+{
+    if (!zig_ready) zig_init();
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        uint32_t a = stream_u32(s);
+        uint32_t b = stream_u32(s);
+        uint64_t U = ((uint64_t)a << 32) | (uint64_t)b;
+        int i = (int)(U & 127u);
+        int neg = (int)((U >> 7) & 1u);
+        uint64_t m = U >> 11;
+        double x = (double)m * zig_w[i];
+        if (m < zig_k[i]) return neg ? -x : x;
+        if (i == 0) {                         /* tail beyond r */
+            double xt, y;
+            int tries = 0;
+            do {
+                xt = -ora_log(stream_uniform(s)) / ZIG_R;
+                y = -ora_log(stream_uniform(s));
+            } while (y + y < xt * xt && ++tries < 64);
+            double v = ZIG_R + xt;
+            return neg ? -v : v;
+        }
+        double u = stream_uniform(s);        /* wedge */
+        if (zig_f[i] + u * (zig_f[i - 1] - zig_f[i]) < ora_exp(-0.5 * x * x)) return neg ? -x : x;
+    }
+    return 0.0;
+}
+
+/* Exported for the pins: n normals from one stream.                        */
+void ora_normal_draws(uint64_t seed, uint32_t index, uint32_t step, uint32_t tag, uint32_t sub,
+                      int64_t n, double* out)
+{
+    ora_stream s;
+    stream_init(&s, seed, index, step, tag, sub);
+    for (int64_t i = 0; i < n; ++i) out[i] = ora_normal(&s);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Grid helpers.  Cell-centred mesh: cell i spans [lo+i h, lo+(i+1) h], its  */
 /* centre is lo+(i+1/2) h (the paper's x_i = i dx read as the centre index). */
 /* Linear index (k n + j) n + i, x fastest.                                 */
@@ -406,9 +482,9 @@ static double interp(const ora_params* p, const double* F, const int ia[3], cons
 /* ------------------------------------------------------------------------ */
 /* a1+a2: interpolate E and push (explicit Euler-Maruyama, Sec. 4.3 first   */
 /* equation; Eq. ito_kernel; V_p = sgn(Z) mu E(X_p) with sgn = -1 for       */
-/* electrons, Eq. Vk1).  Normals by Box-Muller from the stream               */
-/* (index = i, step, PUSH): pairs (u1,u2), (u3,u4); N = (r1 cos, r1 sin,     */
-/* r2 cos).  x' = (x + ((-mu) E_x) dt) + sqrt(2 D dt) N_x.  A particle with  */
+/* electrons, Eq. Vk1).  Normals N_x, N_y, N_z by the ziggurat sampler, in  */
+/* that order, from the stream (index = i, step, PUSH).                      */
+/* x' = (x + ((-mu) E_x) dt) + sqrt(2 D dt) N_x.  A particle with            */
 /* x' outside [lo, hi) on any axis leaves through the electrode / side face  */
 /* and is removed; its weight is tallied (particle boundary condition: the   */
 /* paper states removal for photons only; electrons are absorbed likewise).  */
@@ -428,13 +504,8 @@ void ora_push(const ora_params* p, int64_t np, const double* x, const double* y,
         double Ep[3] = { interp(p, Ex, ia, ib, f), interp(p, Ey, ia, ib, f), interp(p, Ez, ia, ib, f) };
         ora_stream s;
         stream_init(&s, p->seed, (uint32_t)i, p->step, TAG_PUSH, 0);
-        double u1 = stream_uniform(&s), u2 = stream_uniform(&s);
-        double u3 = stream_uniform(&s), u4 = stream_uniform(&s);
-        double r1 = sqrt(-2.0 * ora_log(u1)), r2 = sqrt(-2.0 * ora_log(u3));
-        double s1, c1, s2, c2;
-        ora_sincos2pi(u2, &s1, &c1);
-        ora_sincos2pi(u4, &s2, &c2);
-        double N[3] = { r1 * c1, r1 * s1, r2 * c2 };
+        double N[3];
+        for (int ax = 0; ax < 3; ++ax) N[ax] = ora_normal(&s);
         double Xn[3];
         for (int ax = 0; ax < 3; ++ax) Xn[ax] = (X[ax] + (nmu * Ep[ax]) * p->dt) + sdt * N[ax];
         xo[i] = Xn[0]; yo[i] = Xn[1]; zo[i] = Xn[2];

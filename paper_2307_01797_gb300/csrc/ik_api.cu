@@ -506,6 +506,7 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
                 cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess))
         rc = fail(h, ITOKMC_ERR_CUDA, "field stream");
+    if (!rc) ik::launch_zig_init(h->s);
     if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->s), "init sync");
     if (rc) {
         ik::set_global_error(h->err.c_str());

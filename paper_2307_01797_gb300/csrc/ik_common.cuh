@@ -94,12 +94,53 @@ struct Stream {
     }
 };
 
+// The stream consumed two words at a time (the word order of Stream): pair
+// k is words 2k, 2k+1; uniform() is the FP64 uniform of the next pair,
+// uniform32() the FP32 uniform of its high word.
+struct PairStream {
+    uint32_t k0, k1, c0, c1, c2, blk;
+    u32x4 buf;
+    bool hi_half;                 // next pair is (buf.z, buf.w)
+    __device__ __forceinline__ PairStream(uint64_t seed, uint32_t index, uint32_t step, uint32_t tag, uint32_t sub)
+        : k0((uint32_t)seed), k1((uint32_t)(seed >> 32)), c0(index), c1(step), c2((tag << 24) | sub), blk(0),
+          buf{ 0, 0, 0, 0 }, hi_half(false)
+    {
+        buf = philox10(u32x4{ c0, c1, c2, blk }, k0, k1);
+        ++blk;
+    }
+    __device__ __forceinline__ void pair(uint32_t& a, uint32_t& b)
+    {
+        if (hi_half) {
+            a = buf.z; b = buf.w;
+            buf = philox10(u32x4{ c0, c1, c2, blk }, k0, k1);
+            ++blk;
+        } else {
+            a = buf.x; b = buf.y;
+        }
+        hi_half = !hi_half;
+    }
+    __device__ __forceinline__ double uniform()
+    {
+        uint32_t a, b;
+        pair(a, b);
+        return u53((((uint64_t)a) << 20) | (uint64_t)(b >> 12));
+    }
+    __device__ __forceinline__ float uniform32();
+};
+
 // FP32 uniform on (0,1) from the high word of an FP64 uniform: its top 23
 // bits k give (2k+1) 2^-24 (exact in FP32), the FP64 uniform to within an
 // FP32 ulp.
 __device__ __forceinline__ float uniform_f32(uint32_t v)
 {
     return (float)(2u * (v >> 9) + 1u) * 0x1p-24f;
+}
+
+__device__ __forceinline__ float PairStream::uniform32()
+{
+    uint32_t a, b;
+    pair(a, b);
+    return uniform_f32(a);
 }
 
 // ---------------------------------------------------------------- FP64 math
@@ -247,11 +288,13 @@ static __device__ __noinline__ int64_t dpoisson(Stream& s, double mu)
         return k;
     }
     const double slam = sqrt(mu);
-    const double loglam = dlog(mu);
     const double b = 0.931 + 2.53 * slam;
     const double a = -0.059 + 0.02483 * b;
-    const double invalpha = 1.1239 + 1.1328 / (b - 3.4);
     const double vr = 0.9277 - 3.6224 / (b - 2.0);
+    // ln(mu) and 1/alpha serve only the slow test: formed on first use (the
+    // same values, so the draws are unchanged)
+    double loglam = 0.0, invalpha = 0.0;
+    bool slow_ready = false;
     for (int it = 0; it < 1000000; ++it) {
         const double U = s.uniform() - 0.5;
         const double V = s.uniform();
@@ -259,6 +302,11 @@ static __device__ __noinline__ int64_t dpoisson(Stream& s, double mu)
         const double kd = floor(((((2.0 * a) / us) + b) * U + mu) + 0.43);
         if (us >= 0.07 && V <= vr) return (int64_t)kd;
         if (kd < 0.0 || (us < 0.013 && V > us)) continue;
+        if (!slow_ready) {
+            loglam = dlog(mu);
+            invalpha = 1.1239 + 1.1328 / (b - 3.4);
+            slow_ready = true;
+        }
         const double lhs = (dlog(V) + dlog(invalpha)) - dlog((a / (us * us)) + b);
         const double rhs = ((-mu) + kd * loglam) - dlogfact((int64_t)kd);
         if (lhs <= rhs) return (int64_t)kd;

@@ -12,6 +12,7 @@
 //   particles (a7-a9): loss removal and products (Sec. 4.4, Eq. w), photons
 //     (Sec. 4.5, Eq. photon_transport), kd-tree merge/split (Sec. 4.6).
 #include <cstdio>
+#include <mutex>
 #include <type_traits>
 
 #include "ik_common.cuh"
@@ -286,6 +287,111 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
     }
 }
 
+// ------------------------------------------------------------------ normals
+// Standard normals by the ziggurat method (Marsaglia & Tsang, J. Stat.
+// Softw. 5(8), 2000), 128 layers, base strip r = 3.442619855899,
+// v = 9.91256303526217e-3, 53-bit magnitudes: an attempt takes two words
+// U = a 2^32 + b: layer i = U mod 128, sign bit 7, magnitude m = U >> 11;
+// x = m W_i is accepted at once if m < K_i, else through the tail (i = 0) or
+// the wedge test.  The tables follow the paper's setup recurrence with the
+// library's ln/exp and IEEE sqrt (computed once per device by k_zig_init).
+// The FP32 form takes the same words and the same integer decisions, and
+// its rare paths use FP32 uniforms from the high words.
+__device__ double g_zig_w[128], g_zig_f[128];
+__device__ unsigned long long g_zig_k[128];
+__device__ float g_zig_w32[128], g_zig_f32[128];
+
+constexpr double ZIG_R = 3.442619855899, ZIG_V = 9.91256303526217e-3, ZIG_M = 9007199254740992.0;
+
+__global__ void k_zig_init()
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const double q = ZIG_V / dexp(-0.5 * ZIG_R * ZIG_R);
+    g_zig_k[0] = (unsigned long long)((ZIG_R / q) * ZIG_M);
+    g_zig_k[1] = 0;
+    g_zig_w[0] = q / ZIG_M;
+    g_zig_w[127] = ZIG_R / ZIG_M;
+    g_zig_f[0] = 1.0;
+    g_zig_f[127] = dexp(-0.5 * ZIG_R * ZIG_R);
+    double d = ZIG_R, t = ZIG_R;
+    for (int i = 126; i >= 1; --i) {
+        d = sqrt(-2.0 * dlog(ZIG_V / d + dexp(-0.5 * d * d)));
+        g_zig_k[i + 1] = (unsigned long long)((d / t) * ZIG_M);
+        t = d;
+        g_zig_f[i] = dexp(-0.5 * d * d);
+        g_zig_w[i] = d / ZIG_M;
+    }
+    for (int i = 0; i < 128; ++i) {
+        g_zig_w32[i] = (float)g_zig_w[i];
+        g_zig_f32[i] = (float)g_zig_f[i];
+    }
+}
+
+// m < 2^53 as a double, assembled from its bits (exact).
+__device__ __forceinline__ double u53_exact(unsigned long long m)
+{
+    if (m == 0) return 0.0;
+    const int p = 63 - __clzll((long long)m);
+    const unsigned long long bits = ((unsigned long long)(p + 1023) << 52) | ((m << (52 - p)) & 0x000fffffffffffffull);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double znormal(PairStream& s)
+{
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        uint32_t a, b;
+        s.pair(a, b);
+        const unsigned long long U = ((unsigned long long)a << 32) | b;
+        const int i = (int)(U & 127u);
+        const bool neg = (U >> 7) & 1u;
+        const unsigned long long m = U >> 11;
+        const double x = u53_exact(m) * __ldg(g_zig_w + i);
+        if (m < __ldg(g_zig_k + i)) return neg ? -x : x;
+        if (i == 0) {
+            double xt, y;
+            int tries = 0;
+            do {
+                xt = -dlog(s.uniform()) / ZIG_R;
+                y = -dlog(s.uniform());
+            } while (y + y < xt * xt && ++tries < 64);
+            const double v = ZIG_R + xt;
+            return neg ? -v : v;
+        }
+        const double u = s.uniform();
+        const double fi = __ldg(g_zig_f + i), fm = __ldg(g_zig_f + i - 1);
+        if (fi + u * (fm - fi) < dexp(-0.5 * x * x)) return neg ? -x : x;
+    }
+    return 0.0;
+}
+
+__device__ __forceinline__ float znormal32(PairStream& s)
+{
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        uint32_t a, b;
+        s.pair(a, b);
+        const unsigned long long U = ((unsigned long long)a << 32) | b;
+        const int i = (int)(U & 127u);
+        const bool neg = (U >> 7) & 1u;
+        const unsigned long long m = U >> 11;
+        const float x = __ull2float_rn(m) * __ldg(g_zig_w32 + i);
+        if (m < __ldg(g_zig_k + i)) return neg ? -x : x;
+        if (i == 0) {
+            float xt, y;
+            int tries = 0;
+            do {
+                xt = -logf(s.uniform32()) / (float)ZIG_R;
+                y = -logf(s.uniform32());
+            } while (y + y < xt * xt && ++tries < 64);
+            const float v = (float)ZIG_R + xt;
+            return neg ? -v : v;
+        }
+        const float u = s.uniform32();
+        const float fi = __ldg(g_zig_f32 + i), fm = __ldg(g_zig_f32 + i - 1);
+        if (fi + u * (fm - fi) < expf(-0.5f * x * x)) return neg ? -x : x;
+    }
+    return 0.f;
+}
+
 // ------------------------------------------------------------------ pass 1
 __global__ void __launch_bounds__(TPB) k_push_f64(
     Params P, const P64* __restrict__ A, P64* __restrict__ B, uint32_t* __restrict__ keyB, uint32_t N,
@@ -310,13 +416,10 @@ __global__ void __launch_bounds__(TPB) k_push_f64(
         const double X[3] = { p.x, p.y, p.z };
         double Ep[3];
         interp_f64(P, E + ebase, X, Ep);
-        Stream s(seed_of(P, r), idx, P.step, TAG_PUSH, 0);
-        const double u1 = s.uniform(), u2 = s.uniform(), u3 = s.uniform(), u4 = s.uniform();
-        const double r1 = sqrt(-2.0 * dlog(u1)), r2 = sqrt(-2.0 * dlog(u3));
-        double s1, c1, s2, c2;
-        dsincos2pi(u2, &s1, &c1);
-        dsincos2pi(u4, &s2, &c2);
-        const double Nn[3] = { r1 * c1, r1 * s1, r2 * c2 };
+        PairStream s(seed_of(P, r), idx, P.step, TAG_PUSH, 0);
+        double Nn[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Nn[a] = znormal(s);
         const double nmu = -P.mu;
         double Xn[3];
         bool inside = true;
@@ -1676,18 +1779,12 @@ __global__ void __launch_bounds__(TPB) k_push_f32(
                     ey = __fmaf_rn(wgt, e.y, ey);
                     ez = __fmaf_rn(wgt, e.z, ez);
                 }
-        // the FP64 form's stream (blocks 0 and 1): uniform j takes the top 24
-        // of its 52 bits, so both forms draw common random numbers (equal to
-        // FP32 rounding) -> FP32 Box-Muller, three normals
-        const uint64_t key = seed_of(P, r);
-        const u32x4 b0 = philox10(u32x4{ idx, P.step, TAG_PUSH << 24, 0u }, (uint32_t)key, (uint32_t)(key >> 32));
-        const u32x4 b1 = philox10(u32x4{ idx, P.step, TAG_PUSH << 24, 1u }, (uint32_t)key, (uint32_t)(key >> 32));
-        const float u1 = uniform_f32(b0.x), u2 = uniform_f32(b0.z), u3 = uniform_f32(b1.x), u4 = uniform_f32(b1.z);
-        const float r1 = sqrtf(-2.0f * logf(u1)), r2 = sqrtf(-2.0f * logf(u3));
-        float s1, c1, s2, c2;
-        sincospif(2.0f * u2, &s1, &c1);
-        sincospif(2.0f * u4, &s2, &c2);
-        const float nrm[3] = { r1 * c1, r1 * s1, r2 * c2 };
+        // the FP64 form's stream and words: the same ziggurat decisions, so
+        // both forms draw common random numbers (equal to FP32 rounding)
+        PairStream zs(seed_of(P, r), idx, P.step, TAG_PUSH, 0);
+        float nrm[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nrm[a] = znormal32(zs);
         const float Ep[3] = { ex, ey, ez };
         float on[3];
         int idn[3];
@@ -1875,6 +1972,21 @@ void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
     ++g_launches;
     if (d.mixed) k_deposit_f32<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.rA32, d.cellA32, N, d.Xe, d.ne_fix);
     else k_deposit_f64<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.recA, N, d.Xe, d.ne_fix);
+}
+
+// Ziggurat tables, once per device (the same values for every handle).
+void launch_zig_init(cudaStream_t s)
+{
+    static std::mutex mtx;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mtx);
+    if (dev >= 0 && dev < 64 && done[dev]) return;
+    ++g_launches;
+    k_zig_init<<<1, 1, 0, s>>>();
+    cudaStreamSynchronize(s);
+    if (dev >= 0 && dev < 64) done[dev] = true;
 }
 
 void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)

@@ -176,6 +176,7 @@ void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
 void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s);
 void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
 void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
+void launch_zig_init(cudaStream_t s);
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
 void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
 void launch_particles_b(const Params& P, Dev& d, uint64_t G, cudaStream_t s);

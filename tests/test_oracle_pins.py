@@ -123,6 +123,26 @@ def _phys_small(n=16, **kw):
     return ph
 
 
+def test_ziggurat_normals_follow_the_standard_normal(oracle_mod):
+    """The push normals (ziggurat method, Marsaglia & Tsang 2000) are N(0, 1):
+    Kolmogorov-Smirnov against the normal CDF, the first four moments, and the
+    probability of the tail beyond the base strip r and beyond 4."""
+    from scipy import stats
+    x = oracle_mod.normal_draws(11, 5, 2, 2, 0, 400000)
+    assert stats.kstest(x, "norm").pvalue > 1e-3
+    n = len(x)
+    assert abs(x.mean()) < 5 / math.sqrt(n)
+    assert abs(x.var() - 1.0) < 5 * math.sqrt(2.0 / n)
+    assert abs(stats.skew(x)) < 5 * math.sqrt(6.0 / n)
+    assert abs(stats.kurtosis(x)) < 5 * math.sqrt(24.0 / n)
+    for t in (3.442619855899, 4.0):
+        p = 2 * stats.norm.sf(t)
+        assert abs((np.abs(x) > t).mean() - p) < 5 * math.sqrt(p / n)
+    # symmetric sign and independent successive draws
+    assert abs((x > 0).mean() - 0.5) < 5 * 0.5 / math.sqrt(n)
+    assert abs(np.corrcoef(x[:-1], x[1:])[0, 1]) < 5 / math.sqrt(n)
+
+
 def test_push_free_cloud_moments(oracle_mod):
     """Eq. ensemble_averages: <dX> = v dt, <|dX - v dt|^2> = 2 D d dt, with
     v = -mu E for electrons (Eq. Vk1, sgn = -1).  Uniform E = -E0 z."""
