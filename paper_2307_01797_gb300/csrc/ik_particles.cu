@@ -299,7 +299,7 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
 // its rare paths use FP32 uniforms from the high words.
 __device__ double g_zig_w[128], g_zig_f[128];
 __device__ unsigned long long g_zig_k[128];
-__device__ float g_zig_w32[128], g_zig_f32[128];
+__device__ float g_zig_w32[128], g_zig_f32[128];   // W_i 2^29 (for the top 24 magnitude bits), F_i
 
 constexpr double ZIG_R = 3.442619855899, ZIG_V = 9.91256303526217e-3, ZIG_M = 9007199254740992.0;
 
@@ -322,7 +322,7 @@ __global__ void k_zig_init()
         g_zig_w[i] = d / ZIG_M;
     }
     for (int i = 0; i < 128; ++i) {
-        g_zig_w32[i] = (float)g_zig_w[i];
+        g_zig_w32[i] = (float)(g_zig_w[i] * 536870912.0);   // 2^29
         g_zig_f32[i] = (float)g_zig_f[i];
     }
 }
@@ -373,7 +373,8 @@ __device__ __forceinline__ float znormal32(PairStream& s)
         const int i = (int)(U & 127u);
         const bool neg = (U >> 7) & 1u;
         const unsigned long long m = U >> 11;
-        const float x = __ull2float_rn(m) * __ldg(g_zig_w32 + i);
+        // the top 24 bits of the 53-bit magnitude: an exact 32-bit conversion
+        const float x = __uint2float_rn((uint32_t)(m >> 29)) * __ldg(g_zig_w32 + i);
         if (m < __ldg(g_zig_k + i)) return neg ? -x : x;
         if (i == 0) {
             float xt, y;
