@@ -1443,11 +1443,11 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                     for (int a = 0; a < 3; ++a) { nlo[3 * d + a] = lo[a]; nhi[3 * d + a] = hi[a]; }
                 }
             } else {
-                for (int d = lane; d < nnodes; d += 32) {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) { nlo[3 * d + a] = (K)~(K)0; nhi[3 * d + a] = (K)0; }
-                }
-                __syncwarp();
+                // a node continuing from the previous chunk takes that chunk's
+                // partial bounds (carried from its last lane); a node's bounds
+                // are stored by its last lane
+                K clo[3] = { (K)~(K)0, (K)~(K)0, (K)~(K)0 }, chi[3] = { 0, 0, 0 };
+                uint32_t cd = 0xffffffffu;
                 for (uint32_t b0 = 0; b0 < n; b0 += 32) {
                     const uint32_t j = b0 + lane;
                     const bool ok = j < n;
@@ -1456,19 +1456,27 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                     // within the chunk (the tail past n forms one more group)
                     const uint32_t g0 = ok ? nb[d] : n, g1 = ok ? nb[d + 1] : b0 + 32;
                     const int gs = (int)(g0 > b0 ? g0 - b0 : 0);
-                    const bool last = (int)lane == (int)((g1 < b0 + 32 ? g1 : b0 + 32) - b0) - 1;
+                    const bool fin = ok && g1 <= b0 + 32 && (int)lane == (int)(g1 - b0) - 1;
+                    const bool cont = d == cd;
                     E e;
                     if (ok) e = cur[j];
                     else { e.x = 0; e.y = 0; e.z = 0; e.w = 0; }
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const K v = ET<E>::key(e, a);
-                        const K mn = grp_min(gs, v, lane), mx = grp_max(gs, v, lane);
-                        if (ok && last) {
-                            atomicMin(nlo + 3 * d + a, mn);
-                            atomicMax(nhi + 3 * d + a, mx);
+                        K mn = grp_min(gs, v, lane), mx = grp_max(gs, v, lane);
+                        if (cont) {
+                            mn = clo[a] < mn ? clo[a] : mn;
+                            mx = chi[a] > mx ? chi[a] : mx;
                         }
+                        if (fin) {
+                            nlo[3 * d + a] = mn;
+                            nhi[3 * d + a] = mx;
+                        }
+                        clo[a] = __shfl_sync(0xffffffffu, mn, 31);
+                        chi[a] = __shfl_sync(0xffffffffu, mx, 31);
                     }
+                    cd = __shfl_sync(0xffffffffu, d, 31);
                 }
             }
             __syncwarp();
