@@ -1504,9 +1504,13 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                 if (nax[d] == NO_SPLIT) { tmp[j] = cur[j]; continue; }
                 const uint32_t s0 = nb[d], s1 = nb[d + 1];
                 const K kj = keys[j];
+                // one pass over the node (every lane of the node busy for the
+                // same trip count): smaller keys, and equal keys placed before
                 uint32_t rk = 0;
-                for (uint32_t k = s0; k < j; ++k) rk += keys[k] <= kj;
-                for (uint32_t k = j + 1; k < s1; ++k) rk += keys[k] < kj;
+                for (uint32_t k = s0; k < s1; ++k) {
+                    const K kk = keys[k];
+                    rk += (kk < kj) | ((kk == kj) & (k < j));
+                }
                 tmp[s0 + rk] = cur[j];
             }
             __syncwarp();
