@@ -51,13 +51,74 @@ __device__ __forceinline__ E64 ld_e64(const E64* p)
 
 // Trilinear interpolation of the cell-centred field at (x,y,z); sum order z
 // outer, y, x inner; weight (wx*wy)*wz.
+// Cell quotients qd in [1/2, 2^31) split from their bits.  For such qd the
+// stencil coordinate u = qd - 1/2 is exact (1/2 is a multiple of ulp(qd)),
+// and so are floor(u), the fraction f = u - floor(u) = F 2^-sh and
+// floor(f 2^s) = F >> (sh - s): the FP64 subtract / floor / convert
+// sequence yields the same values, and these integer steps keep the FP64
+// pipe (a small fraction of the FP32 rate on GB300) for the arithmetic
+// that rounds.  qc = floor(qd) is the cell index.
+struct QSplit {
+    int qc, i0, sh;
+    unsigned long long F;
+};
+__device__ __forceinline__ bool qsplit(double qd, QSplit& r)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(qd);
+    const int e = (int)(b >> 52);                  // biased exponent (>= 2048 when negative)
+    if (e < 1022 || e > 1053) return false;        // qd < 1/2, qd >= 2^31, negative, NaN
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = 1075 - e;                       // fraction bits of qd, 22..53
+    const unsigned long long fb = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    r.qc = (int)(m >> sh);
+    r.sh = sh;
+    if (fb >= half) { r.i0 = r.qc; r.F = fb - half; }
+    else { r.i0 = r.qc - 1; r.F = fb + half; }
+    return true;
+}
+// F 2^-sh as a double (F < 2^sh, sh <= 53: exact).
+__device__ __forceinline__ double qfrac(unsigned long long F, int sh)
+{
+    if (F == 0) return 0.0;
+    const int pb = 63 - __clzll((long long)F);
+    const unsigned long long mant = (F << (52 - pb)) & 0xfffffffffffffull;
+    return __longlong_as_double((long long)(((unsigned long long)(pb - sh + 1023) << 52) | mant));
+}
+// cic_axis with the split above (the FP64 steps for qd < 1/2).
+__device__ __forceinline__ void cic_axis_q(double x, double lo, double h, double rh, int n, int& ia, int& ib,
+                                           double& f)
+{
+    const double qd = grid_quot(x, lo, h, rh);
+    QSplit t;
+    int i0;
+    if (qsplit(qd, t)) {
+        i0 = t.i0;
+        f = qfrac(t.F, t.sh);
+    } else {
+        const double u = qd - 0.5;
+        const double fl = floor(u);
+        i0 = (int)fl;
+        f = u - fl;
+    }
+    ia = clampi(i0, n);
+    ib = clampi(i0 + 1, n);
+}
+// x >= lo and x < hi by order-preserving integer keys (-0 taken as +0; a NaN
+// fails one of the two tests, as in the FP64 comparisons).
+__device__ __forceinline__ unsigned long long dkey(double v)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    b = b == 0x8000000000000000ull ? 0ull : b;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 __device__ __forceinline__ void interp_f64(const Params& P, const E64* __restrict__ E, const double X[3],
                                            double Ep[3])
 {
     int ia[3], ib[3];
     double f[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) cic_axis(X[a], P.lo[a], P.h[a], P.rh[a], P.n, ia[a], ib[a], f[a]);
+    for (int a = 0; a < 3; ++a) cic_axis_q(X[a], P.lo[a], P.h[a], P.rh[a], P.n, ia[a], ib[a], f[a]);
     const double wx[2] = { 1.0 - f[0], f[0] }, wy[2] = { 1.0 - f[1], f[1] }, wz[2] = { 1.0 - f[2], f[2] };
     const int ix[2] = { ia[0], ib[0] }, iy[2] = { ia[1], ib[1] }, iz[2] = { ia[2], ib[2] };
     double ax = 0.0, ay = 0.0, az = 0.0;
@@ -153,25 +214,6 @@ __device__ __forceinline__ void stencil_f64(const Params& P, const double X[3], 
         double f;
         cic_axis(X[a], P.lo[a], P.h[a], P.rh[a], P.n, S.ia[a], S.ib[a], f);
         const long long q = (long long)floor(f * scale);
-        S.A[a][0] = one - q;
-        S.A[a][1] = q;
-    }
-}
-
-// The same stencil from precomputed quotients qd = grid_quot(x) (the push
-// needs them for the cell index too): u = qd - 1/2 as in cic_axis.
-__device__ __forceinline__ void stencil_f64_q(const Params& P, const double qd[3], Stencil& S)
-{
-    const long long one = 1ll << P.frac_bits;
-    const double scale = (double)one;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double u = qd[a] - 0.5;
-        const double fl = floor(u);
-        const int i0 = (int)fl;
-        S.ia[a] = clampi(i0, P.n);
-        S.ib[a] = clampi(i0 + 1, P.n);
-        const long long q = (long long)floor((u - fl) * scale);
         S.A[a][0] = one - q;
         S.A[a][1] = q;
     }
@@ -427,26 +469,43 @@ __global__ void __launch_bounds__(TPB) k_push_f64(
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             Xn[a] = (X[a] + (nmu * Ep[a]) * P.dt) + P.sdt * Nn[a];
-            inside = inside && (Xn[a] >= P.lo[a]) && (Xn[a] < P.hi[a]);
+            const unsigned long long kx = dkey(Xn[a]);
+            inside = inside && kx >= dkey(P.lo[a]) && kx < dkey(P.hi[a]);
         }
         P64 q;
         q.x = Xn[0]; q.y = Xn[1]; q.z = Xn[2]; q.w = w;
         if (inside) {
             // one division per axis serves the cell index and the stencil
-            double qd[3];
             int ic[3];
+            const long long one = 1ll << P.frac_bits;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                qd[a] = grid_quot(Xn[a], P.lo[a], P.h[a], P.rh[a]);
-                const int ci = (int)floor(qd[a]);
+                const double qd = grid_quot(Xn[a], P.lo[a], P.h[a], P.rh[a]);
+                QSplit t;
+                int ci, i0;
+                long long fq;
+                if (qsplit(qd, t)) {
+                    ci = t.qc;
+                    i0 = t.i0;
+                    fq = (long long)(t.F >> (t.sh - P.frac_bits));
+                } else {
+                    ci = (int)floor(qd);
+                    const double u = qd - 0.5;
+                    const double fl = floor(u);
+                    i0 = (int)fl;
+                    fq = (long long)floor((u - fl) * (double)one);
+                }
                 ic[a] = ci > P.n - 1 ? P.n - 1 : (ci < 0 ? 0 : ci);
+                S.ia[a] = clampi(i0, P.n);
+                S.ib[a] = clampi(i0 + 1, P.n);
+                S.A[a][0] = one - fq;
+                S.A[a][1] = fq;
             }
             gnew = (uint32_t)(ebase + ((size_t)ic[2] * P.n + ic[1]) * P.n + ic[0]);
             alive = true;
             mover = gnew != gold;
             q.cell = gnew;
             keyB[i] = gnew | (mover ? KEY_MOVER : 0u);
-            stencil_f64_q(P, qd, S);
             if (mover) {
                 atomicAdd(in_cnt + gnew, 1);
                 if (gold < gnew) atomicAdd(in_before + gnew, 1);
