@@ -205,20 +205,6 @@ struct Stencil {
     long long A[3][2];
 };
 
-__device__ __forceinline__ void stencil_f64(const Params& P, const double X[3], Stencil& S)
-{
-    const long long one = 1ll << P.frac_bits;
-    const double scale = (double)one;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double f;
-        cic_axis(X[a], P.lo[a], P.h[a], P.rh[a], P.n, S.ia[a], S.ib[a], f);
-        const long long q = (long long)floor(f * scale);
-        S.A[a][0] = one - q;
-        S.A[a][1] = q;
-    }
-}
-
 __device__ __forceinline__ void stencil_f32(const Params& P, const int id[3], const float o[3], Stencil& S)
 {
     const int one = 1 << P.frac_bits, half = one >> 1;
@@ -860,55 +846,72 @@ __device__ int kmc_cell(const Params& P, Stream& s, long long X0, const T kr[3],
     return -1;
 }
 
+// Cells with electrons listed for the KMC (one thread per listed cell keeps
+// the warps' lanes busy: the active cells are a small part of the grid);
+// the other cells fire nothing.
+__global__ void k_kmc_list(const unsigned long long* __restrict__ Xe, int64_t* __restrict__ fired, uint64_t G,
+                           uint32_t* __restrict__ list, Counters* __restrict__ ctr)
+{
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
+        if (Xe[g] > 0) {
+            list[warp_slot32(&ctr->n_kmc_cells)] = (uint32_t)g;
+        } else {
+            fired[g] = 0;
+            fired[G + g] = 0;
+            fired[2 * G + g] = 0;
+        }
+    }
+}
+
 template <class T>
 __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const E64* __restrict__ E,
                       const float4* __restrict__ E32, int64_t* __restrict__ fired, int64_t* __restrict__ Npos,
-                      int64_t* __restrict__ Nneg, uint64_t G, uint32_t* __restrict__ pc_list,
-                      Counters* __restrict__ ctr)
+                      int64_t* __restrict__ Nneg, uint64_t G, const uint32_t* __restrict__ list,
+                      uint32_t* __restrict__ pc_list, Counters* __restrict__ ctr)
 {
     unsigned long long t_ion = 0, t_att = 0, t_ph = 0, t_slots = 0;
+    const uint64_t n = ctr->n_kmc_cells;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t g0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const uint64_t gend = ((G + stride - 1) / stride) * stride;   // whole warps iterate together
-    for (uint64_t g = g0; g < gend; g += stride) {
-        if (g >= G) continue;
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t tend = ((n + stride - 1) / stride) * stride;   // whole warps iterate together
+    for (uint64_t t = t0; t < tend; t += stride) {
+        if (t >= n) continue;
+        const uint64_t g = list[t];
         long long f[3] = { 0, 0, 0 };
         const long long X0 = (long long)Xe[g];
-        if (X0 > 0) {
-            T kr[3];
-            if constexpr (sizeof(T) == 8) {
-                const E64 e = ld_e64(E + g);
-                const double Em = e.m;
-                const double ve = P.mu * Em;
-                const double alpha = (Em > 0.0) ? P.alpha_A * dexp(-(P.alpha_B / Em)) : 0.0;
-                kr[0] = alpha * ve;
-                kr[1] = P.eta * ve;
-                kr[2] = P.photon_ratio * kr[0];
-            } else {
-                const float Em = __ldg(E32 + g).w;
-                const float ve = (float)P.mu * Em;
-                const float alpha = (Em > 0.0f) ? (float)P.alpha_A * expf(-((float)P.alpha_B / Em)) : 0.0f;
-                kr[0] = alpha * ve;
-                kr[1] = (float)P.eta * ve;
-                kr[2] = (float)P.photon_ratio * kr[0];
-            }
-            const int r = real_of(P, (uint32_t)g);
-            const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
-            Stream s(seed_of(P, r), c, P.step, TAG_KMC, 0);
-            if (kmc_cell<T>(P, s, X0, kr, f) != 0) {
-                atomicOr(&ctr->err, DERR_KMC);
-                ctr->kmc_fail_cell = (unsigned)g;
-            }
-            Npos[g] += f[0];
-            Nneg[g] += f[1];
-            if (f[2] > 0) {
-                t_slots += (unsigned long long)(f[2] < P.n_new ? f[2] : P.n_new);
-                pc_list[warp_slot32(&ctr->n_photo_cells)] = (uint32_t)g;
-            }
-            t_ion += (unsigned long long)f[0];
-            t_att += (unsigned long long)f[1];
-            t_ph += (unsigned long long)f[2];
+        T kr[3];
+        if constexpr (sizeof(T) == 8) {
+            const E64 e = ld_e64(E + g);
+            const double Em = e.m;
+            const double ve = P.mu * Em;
+            const double alpha = (Em > 0.0) ? P.alpha_A * dexp(-(P.alpha_B / Em)) : 0.0;
+            kr[0] = alpha * ve;
+            kr[1] = P.eta * ve;
+            kr[2] = P.photon_ratio * kr[0];
+        } else {
+            const float Em = __ldg(E32 + g).w;
+            const float ve = (float)P.mu * Em;
+            const float alpha = (Em > 0.0f) ? (float)P.alpha_A * expf(-((float)P.alpha_B / Em)) : 0.0f;
+            kr[0] = alpha * ve;
+            kr[1] = (float)P.eta * ve;
+            kr[2] = (float)P.photon_ratio * kr[0];
         }
+        const int r = real_of(P, (uint32_t)g);
+        const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
+        Stream s(seed_of(P, r), c, P.step, TAG_KMC, 0);
+        if (kmc_cell<T>(P, s, X0, kr, f) != 0) {
+            atomicOr(&ctr->err, DERR_KMC);
+            ctr->kmc_fail_cell = (unsigned)g;
+        }
+        Npos[g] += f[0];
+        Nneg[g] += f[1];
+        if (f[2] > 0) {
+            t_slots += (unsigned long long)(f[2] < P.n_new ? f[2] : P.n_new);
+            pc_list[warp_slot32(&ctr->n_photo_cells)] = (uint32_t)g;
+        }
+        t_ion += (unsigned long long)f[0];
+        t_att += (unsigned long long)f[1];
+        t_ph += (unsigned long long)f[2];
         fired[g] = f[0];
         fired[G + g] = f[1];
         fired[2 * G + g] = f[2];
@@ -1627,13 +1630,14 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                         extra = (lm ? 1u : 0u) + (rm ? 1u : 0u) - 1u;
                     }
                 }
-                uint32_t ie = extra, ic = cnt;
+                // both prefix counts in one word (each at most 64 per chunk)
+                uint32_t pk = (cnt << 16) | extra;
 #pragma unroll
                 for (int k = 1; k < 32; k <<= 1) {
-                    const uint32_t ye = __shfl_up_sync(0xffffffffu, ie, k);
-                    const uint32_t yc = __shfl_up_sync(0xffffffffu, ic, k);
-                    if ((int)lane >= k) { ie += ye; ic += yc; }
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, pk, k);
+                    if ((int)lane >= k) pk += y;
                 }
+                const uint32_t ie = pk & 0xffffu, ic = pk >> 16;
                 if (d < nnodes) {
                     const uint32_t sh = ex_c + ie - extra, ndi = nd_c + ic - cnt;
                     nsh[d] = sh;
@@ -2073,13 +2077,15 @@ void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 {
-    ++g_launches;
+    // the merge's tier-0 list is free until the merge scan of this step
+    g_launches += 2;
+    k_kmc_list<<<grid_for(G, 256, 152 * 32), 256, 0, s>>>(d.Xe, d.fired, G, d.small_list, d.ctr);
     if (d.mixed)
         k_kmc<float><<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G,
-                                                              d.pc_list, d.ctr);
+                                                              d.small_list, d.pc_list, d.ctr);
     else
         k_kmc<double><<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G,
-                                                               d.pc_list, d.ctr);
+                                                               d.small_list, d.pc_list, d.ctr);
 }
 
 // Part a: loss removal, photons, merge scan (offsets, output count, work).

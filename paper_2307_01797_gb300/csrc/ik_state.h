@@ -61,6 +61,7 @@ struct Counters {
     unsigned long long absorbed_w;
     unsigned long long photo_slots;    // sum over cells of min(N_gamma, N_new)
     unsigned int n_photo_cells;        // photon-emitting cells listed by the KMC
+    unsigned int n_kmc_cells;          // cells with X_e > 0 listed for the KMC
     unsigned long long merge_cells, merge_elems, merge_elems2, merge_maxm;   // merge workload
     unsigned long long rho_absmax;     // max |rho_fixed| of the last deposit
     unsigned int err;                  // DERR_* bits
