@@ -50,13 +50,28 @@ __device__ __forceinline__ T nbr_sum(const T* __restrict__ phi, uint64_t idx, in
     const uint64_t sy = (uint64_t)n, sz = (uint64_t)n * n;
     T s = 0;
     diag = 0;
-    if (i > 0) { s += phi[idx - 1]; ++diag; }
+    if (i > 0) { s = phi[idx - 1]; ++diag; }     // the sum starts at the first neighbour
     if (i < n - 1) { s += phi[idx + 1]; ++diag; }
     if (j > 0) { s += phi[idx - sy]; ++diag; }
     if (j < n - 1) { s += phi[idx + sy]; ++diag; }
     if (k > 0) { s += phi[idx - sz]; ++diag; } else diag += 2;
     if (k < n - 1) { s += phi[idx + sz]; ++diag; } else diag += 2;
     return s;
+}
+
+// diag as a T without a conversion instruction.
+template <class T>
+__device__ __forceinline__ T diag_val(int d)
+{
+    switch (d) {
+    case 4: return (T)4;
+    case 5: return (T)5;
+    case 6: return (T)6;
+    case 7: return (T)7;
+    case 8: return (T)8;
+    case 9: return (T)9;
+    default: return (T)d;
+    }
 }
 
 // 1/diag for the diagonal counts 1..8 (a multiply instead of a divide).
@@ -111,7 +126,7 @@ __global__ void k_resid_restrict(const T* __restrict__ phi, const T* __restrict_
             const uint64_t idx = (((uint64_t)r * nf + k) * nf + j) * nf + i;
             int diag;
             const T s = nbr_sum(phi, idx, nf, i, j, k, diag);
-            acc += rhs[idx] - (s - (T)diag * phi[idx]);
+            acc += fma(diag_val<T>(diag), phi[idx], rhs[idx] - s);
         }
         rhs_c[t] = (TC)(acc * (T)0.5);
     }
@@ -173,7 +188,7 @@ __global__ void k_bottom(T* __restrict__ phi, const T* __restrict__ rhs, int n, 
                 if (((i + j + k) & 1) != color) continue;
                 int diag;
                 const T sum = nbr_sum(s, (uint64_t)c, n, i, j, k, diag);
-                s[c] = (sum - b[c]) / (T)diag;
+                s[c] = (sum - b[c]) * inv_diag<T>(diag);
             }
             __syncthreads();
         }
@@ -458,7 +473,7 @@ __device__ void blk_smooth(T* phi, const T* rhs, int n, int color)
         const uint64_t idx = ((uint64_t)k * n + j) * n + i;
         int diag;
         const T sum = nbr_sum(phi, idx, n, i, j, k, diag);
-        phi[idx] = (sum - rhs[idx]) / (T)diag;
+        phi[idx] = (sum - rhs[idx]) * inv_diag<T>(diag);
     }
     __syncthreads();
 }
@@ -475,7 +490,7 @@ __device__ void blk_resid_restrict(const T* phi, const T* rhs, T* rhs_c, int nf)
             const uint64_t idx = ((uint64_t)k * nf + j) * nf + i;
             int diag;
             const T sum = nbr_sum(phi, idx, nf, i, j, k, diag);
-            acc += rhs[idx] - (sum - (T)diag * phi[idx]);
+            acc += fma(diag_val<T>(diag), phi[idx], rhs[idx] - sum);
         }
         rhs_c[t] = acc * (T)0.5;
     }
