@@ -31,6 +31,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes per particle of the transport stage (push, transport scans,
+# scatter, mover kernels) in one step of the 256^3 streamer, from an ncu launch
+# list of that workload, keyed by "FP64 form": the push and the scatter each
+# read and write every record, so the stage moves about twice the
+# algorithmic bytes.
+TRANSPORT_DRAM_PER_PARTICLE = {True: 10.955e9 / 75505333, False: 7.085e9 / 75504496}
+
 METRIC = "particle-steps/s (push+sort+deposit+KMC), HBM roofline %; FP32 vs FP64 at stated err"
 
 
@@ -240,12 +247,18 @@ def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e)
     mesh = (24 + 8 + 8) if form == itokmc.FP64 else (12 + 8 + 8)
     bpp = 2 * R + mesh / 32
     ach = processed * bpp / (stage["transport"] / 1e3) / 1e9
+    # measured DRAM bytes of the same stage (dram__bytes_read.sum +
+    # dram__bytes_write.sum of its kernels in one ncu launch list of this
+    # workload at 256^3), per step at the timed mean particle count
+    tpp = TRANSPORT_DRAM_PER_PARTICLE[form == itokmc.FP64] if (args.n == 256 and args.particles == 1e8) else None
+    traffic = tpp * processed / args.steps if tpp else None
     out = {"value": processed_all / (ms / 1e3), "ms_per_step": ms / args.steps,
            "push_sort_deposit_kmc_rate": processed / (core_ms / 1e3),
            "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
            "movers_per_step": movers / args.steps, "mg_cycles": mg_cycles, "particles_per_step": counts,
            "last_step_counters": last, "gpu_launches": int(launches), "clocks": clk,
-           "transport_achieved_gbs": ach, "bytes_per_particle": bpp,
+           "transport_achieved_gbs": ach, "bytes_per_particle": bpp, "traffic": traffic,
+           "traffic_per_particle": tpp,
            "mg_smoothing": {"nu1": tune["mg_nu1"], "nu2": tune["mg_nu2"], "autotuned": True} if tune else
            {"nu1": 2, "nu2": 2, "autotuned": False}}
     if with_e2e:
@@ -324,8 +337,8 @@ def our_arm(args, rank, world):
         "last_step_counters": P["last_step_counters"],
         "roofline": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)",
                      "achieved": P["transport_achieved_gbs"], "peak": pk, "peak_kind": pk_kind, "unit": "GB/s",
-                     "frac": P["transport_achieved_gbs"] / pk, "traffic": None,
-                     "bytes_per_particle": P["bytes_per_particle"]},
+                     "frac": P["transport_achieved_gbs"] / pk, "traffic": P["traffic"],
+                     "bytes_per_particle": P["bytes_per_particle"], "traffic_per_particle": P["traffic_per_particle"]},
         "cpu_baseline": cpu, "e2e": P.get("e2e"), "gpu_launches": P["gpu_launches"], "clocks": P["clocks"],
     }
     if len(forms) > 1:
@@ -339,7 +352,8 @@ def our_arm(args, rank, world):
             "clocks": M["clocks"],
             "roofline": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)",
                          "achieved": M["transport_achieved_gbs"], "peak": pk, "unit": "GB/s",
-                         "frac": M["transport_achieved_gbs"] / pk, "bytes_per_particle": M["bytes_per_particle"]},
+                         "frac": M["transport_achieved_gbs"] / pk, "traffic": M["traffic"],
+                         "bytes_per_particle": M["bytes_per_particle"], "traffic_per_particle": M["traffic_per_particle"]},
             "speedup_vs_fp64": M["value"] / P["value"]}
     print(json.dumps(line), flush=True)
     if dist:
@@ -529,7 +543,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="both", choices=["fp64", "mixed", "both"],
                     help="both: the FP64 plain form gives the headline, the mixed form is reported beside it")
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--n", type=int, default=None,
+                    help="cells per edge (default 256; the ensemble study defaults to 128 per member)")
     ap.add_argument("--particles", type=float, default=1e8,
                     help="target superparticle count of the synthetic discharge tree (about 7e7 are placed)")
     ap.add_argument("--ref-particles", type=int, default=2000000)
@@ -544,6 +559,8 @@ def main():
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--batched-only", action="store_true")
     args = ap.parse_args()
+    if args.n is None:
+        args.n = 128 if args.study == "ensemble" else 256
     if args.study == "precision":
         precision_study(args)
         return

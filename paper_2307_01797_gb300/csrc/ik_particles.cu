@@ -1560,47 +1560,48 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                 keys[j] = a == NO_SPLIT ? (K)0 : ET<E>::key(cur[j], a);
             }
             __syncwarp();
-            // ---- stable rank sort within each node: cur -> tmp
+            // ---- stable rank sort within each node (cur -> tmp), and the
+            // weighted median: an element's rank counts the node's elements
+            // placed before it, whose weights give its inclusive prefix
+            // weight v in sorted order; the median is the element with
+            // 2 v > W >= 2 (v - w)
             for (uint32_t j = lane; j < n; j += 32) {
                 const uint32_t d = nid[j];
-                if (nax[d] == NO_SPLIT) { tmp[j] = cur[j]; continue; }
+                const E ej = cur[j];
+                if (nax[d] == NO_SPLIT) { tmp[j] = ej; continue; }
                 const uint32_t s0 = nb[d], s1 = nb[d + 1];
                 const K kj = keys[j];
                 // one pass over the node (every lane of the node busy for the
                 // same trip count): smaller keys, and equal keys placed before
                 uint32_t rk = 0;
-                for (uint32_t k = s0; k < s1; ++k) {
-                    const K kk = keys[k];
-                    rk += (kk < kj) | ((kk == kj) & (k < j));
-                }
-                tmp[s0 + rk] = cur[j];
-            }
-            __syncwarp();
-            // ---- weighted median: segmented inclusive weight scan in sorted order
-            unsigned long long carry = 0;
-            uint32_t carry_d = 0xffffffffu;
-            for (uint32_t b0 = 0; b0 < n; b0 += 32) {
-                const uint32_t j = b0 + lane;
-                const bool ok = j < n;
-                const uint32_t d = ok ? nid[j] : 0xffffu;
-                const uint32_t g0 = ok ? nb[d] : n;
-                const int gs = (int)(g0 > b0 ? g0 - b0 : 0);
-                const unsigned long long w = ok ? tmp[j].w : 0ull;
-                // 32-bit prefix sums when the cell's weight allows (warp-uniform)
-                const unsigned long long v0 =
-                    w32 ? (unsigned long long)grp_scan(gs, (uint32_t)w, lane, [](uint32_t x, uint32_t y) { return x + y; })
-                        : grp_scan(gs, w, lane, [](unsigned long long x, unsigned long long y) { return x + y; });
-                unsigned long long v = v0;
-                if (d == carry_d) v += carry;
-                if (ok && nax[d] != NO_SPLIT) {
-                    const unsigned long long W = nW[d];
-                    if (2ull * v > W && 2ull * (v - w) <= W) {
-                        npm[d] = j - nb[d];
-                        nC[d] = v;
+                unsigned long long v;
+                if (w32) {
+                    uint32_t pw = 0;
+                    for (uint32_t k = s0; k < s1; ++k) {
+                        const K kk = keys[k];
+                        const uint32_t wk = cur[k].w;
+                        const bool bf = (kk < kj) | ((kk == kj) & (k < j));
+                        rk += bf;
+                        pw += bf ? wk : 0u;
                     }
+                    v = (unsigned long long)pw + ej.w;
+                } else {
+                    unsigned long long pw = 0;
+                    for (uint32_t k = s0; k < s1; ++k) {
+                        const K kk = keys[k];
+                        const uint32_t wk = cur[k].w;
+                        const bool bf = (kk < kj) | ((kk == kj) & (k < j));
+                        rk += bf;
+                        pw += bf ? (unsigned long long)wk : 0ull;
+                    }
+                    v = pw + ej.w;
                 }
-                carry = __shfl_sync(0xffffffffu, v, 31);
-                carry_d = __shfl_sync(0xffffffffu, d, 31);
+                tmp[s0 + rk] = ej;
+                const unsigned long long W = nW[d];
+                if (2ull * v > W && 2ull * (v - ej.w) <= W) {
+                    npm[d] = rk;
+                    nC[d] = v;
+                }
             }
             __syncwarp();
             // ---- per node: median rule, child layout of the next level
