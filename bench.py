@@ -555,12 +555,15 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default smoother counts (2, 2)")
     ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small"],
                     help="instead of the benchmark: the FP32-vs-FP64 precision study")
-    ap.add_argument("--study-steps", type=int, default=20)
+    ap.add_argument("--study-steps", type=int, default=None,
+                    help="steps of a study (default: precision 20, small 10, ensemble 5)")
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--batched-only", action="store_true")
     args = ap.parse_args()
     if args.n is None:
         args.n = 128 if args.study == "ensemble" else 256
+    if args.study_steps is None:
+        args.study_steps = {"ensemble": 5, "small": 10}.get(args.study, 20)
     if args.study == "precision":
         precision_study(args)
         return
