@@ -37,6 +37,13 @@ sys.path.insert(0, ROOT)
 # read and write every record, so the stage moves about twice the
 # algorithmic bytes.
 TRANSPORT_DRAM_PER_PARTICLE = {True: 10.955e9 / 75505333, False: 7.085e9 / 75504496}
+# FP64 arithmetic of the FP64 push per particle (ncu thread-instruction counts
+# of DADD, DMUL and DFMA over a launch, divided by its particles; an FMA
+# counts as two operations) and GB300's FP64 peak: 152 SMs x 2 FP64 FMA lanes
+# per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak 304 per
+# cycle over the GPU) x 2 FLOP x 2.07 GHz.
+FP64_FLOP_PER_PARTICLE = 123.0
+FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 
 METRIC = "particle-steps/s (push+sort+deposit+KMC), HBM roofline %; FP32 vs FP64 at stated err"
 
@@ -341,6 +348,14 @@ def our_arm(args, rank, world):
                      "bytes_per_particle": P["bytes_per_particle"], "traffic_per_particle": P["traffic_per_particle"]},
         "cpu_baseline": cpu, "e2e": P.get("e2e"), "gpu_launches": P["gpu_launches"], "clocks": P["clocks"],
     }
+    if forms[0] == itokmc.FP64:
+        # the FP64 transport is bound by GB300's FP64 units, not by HBM
+        t_tr = P["stage_ms_per_step"]["transport"] / 1e3
+        ach = FP64_FLOP_PER_PARTICLE * (sum(P["particles_per_step"]) / len(P["particles_per_step"])) / t_tr / 1e12
+        line["roofline_fp64"] = {"bound": "alu", "kernel": "transport stage (push+sort+deposit), FP64 arithmetic",
+                                 "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": ach / FP64_PEAK_TFLOPS, "flop_per_particle": FP64_FLOP_PER_PARTICLE,
+                                 "peak_kind": "derived (unit counts x clock)"}
     if len(forms) > 1:
         M = res[itokmc.MIXED]
         line["mixed_form"] = {

@@ -422,7 +422,7 @@ __device__ __forceinline__ float znormal32(PairStream& s)
 }
 
 // ------------------------------------------------------------------ pass 1
-__global__ void __launch_bounds__(TPB) k_push_f64(
+__global__ void __launch_bounds__(TPB, 4) k_push_f64(
     Params P, const P64* __restrict__ A, P64* __restrict__ B, uint32_t* __restrict__ keyB, uint32_t N,
     const uint32_t* __restrict__ cell_start, const E64* __restrict__ E, int32_t* __restrict__ cnt_new,
     int32_t* __restrict__ in_cnt, int32_t* __restrict__ in_before, unsigned long long* __restrict__ Xe,
@@ -1813,7 +1813,7 @@ __device__ __forceinline__ void deposit32(const Params& P, unsigned long long* _
             }
 }
 
-__global__ void __launch_bounds__(TPB) k_push_f32(
+__global__ void __launch_bounds__(TPB, 4) k_push_f32(
     Params P, const P32* __restrict__ A, const uint32_t* __restrict__ cA, P32* __restrict__ B,
     uint32_t* __restrict__ keyB, uint32_t N, const uint32_t* __restrict__ cell_start,
     const float4* __restrict__ E32, int32_t* __restrict__ cnt_new, int32_t* __restrict__ in_cnt,
