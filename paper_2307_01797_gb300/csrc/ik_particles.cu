@@ -202,7 +202,7 @@ __device__ __forceinline__ unsigned warp_slot32(unsigned* ctr)
 // weights (2^s - a, a).
 struct Stencil {
     int ia[3], ib[3];
-    long long A[3][2];
+    uint32_t A[3][2];   // 2^s - a and a (s <= 10: a product of three fits 32 bits)
 };
 
 __device__ __forceinline__ void stencil_f32(const Params& P, const int id[3], const float o[3], Stencil& S)
@@ -250,9 +250,7 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
     }
     const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) v[k] = min(v[k], __shfl_xor_sync(0xffffffffu, v[k], d));
+    for (int k = 0; k < 8; ++k) v[k] = __reduce_min_sync(0xffffffffu, v[k]);
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) wred[wid][k] = v[k];
@@ -279,8 +277,8 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
                 for (int b = 0; b < 2; ++b)
 #pragma unroll
                     for (int a = 0; a < 2; ++a) {
-                        const long long val = (long long)w * S.A[0][a] * S.A[1][b] * S.A[2][c];
-                        if (val) atomicAdd(base + ((size_t)iz[c] * P.n + iy[b]) * P.n + ix[a], (unsigned long long)val);
+                        const unsigned long long val = (unsigned long long)w * (S.A[0][a] * S.A[1][b] * S.A[2][c]);
+                        if (val) atomicAdd(base + ((size_t)iz[c] * P.n + iy[b]) * P.n + ix[a], val);
                     }
         }
         return;
@@ -294,7 +292,7 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
             for (int b = 0; b < 2; ++b)
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
-                    const long long val = (long long)w * S.A[0][a] * S.A[1][b] * S.A[2][c];
+                    const unsigned long long val = (unsigned long long)w * (S.A[0][a] * S.A[1][b] * S.A[2][c]);
                     if (val) {
                         const int k = ((iz[c] - lo2) * e1 + (iy[b] - lo1)) * e0 + (ix[a] - lo0);
                         const uint32_t lo = (uint32_t)val;
@@ -484,8 +482,8 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f64(
                 ic[a] = ci > P.n - 1 ? P.n - 1 : (ci < 0 ? 0 : ci);
                 S.ia[a] = clampi(i0, P.n);
                 S.ib[a] = clampi(i0 + 1, P.n);
-                S.A[a][0] = one - fq;
-                S.A[a][1] = fq;
+                S.A[a][0] = (uint32_t)(one - fq);
+                S.A[a][1] = (uint32_t)fq;
             }
             gnew = (uint32_t)(ebase + ((size_t)ic[2] * P.n + ic[1]) * P.n + ic[0]);
             alive = true;
