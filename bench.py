@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 # list of that workload, keyed by "FP64 form": the push and the scatter each
 # read and write every record, so the stage moves about twice the
 # algorithmic bytes.
-TRANSPORT_DRAM_PER_PARTICLE = {True: 10.955e9 / 75505333, False: 7.085e9 / 75504496}
+TRANSPORT_DRAM_PER_PARTICLE = {True: 10.963e9 / 75505333, False: 7.080e9 / 75504496}
 # FP64 arithmetic of the FP64 push per particle (ncu thread-instruction counts
 # of DADD, DMUL and DFMA over a launch, divided by its particles; an FMA
 # counts as two operations) and GB300's FP64 peak: 152 SMs x 2 FP64 FMA lanes
