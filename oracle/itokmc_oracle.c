@@ -309,7 +309,8 @@ static int64_t ora_poisson(ora_stream* s, double mu)
         double kd = floor(((((2.0 * a) / us) + b) * U + mu) + 0.43);
         if (us >= 0.07 && V <= vr) return (int64_t)kd;
         if (kd < 0.0 || (us < 0.013 && V > us)) continue;
-        double lhs = (ora_log(V) + ora_log(invalpha)) - ora_log((a / (us * us)) + b);
+        /* the acceptance test as one logarithm (Hoermann's form) */
+        double lhs = ora_log((V * invalpha) / ((a / (us * us)) + b));
         double rhs = ((-mu) + kd * loglam) - ora_logfact((int64_t)kd);
         if (lhs <= rhs) return (int64_t)kd;
     }

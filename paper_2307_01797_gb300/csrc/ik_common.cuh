@@ -307,7 +307,8 @@ static __device__ __noinline__ int64_t dpoisson(Stream& s, double mu)
             invalpha = 1.1239 + 1.1328 / (b - 3.4);
             slow_ready = true;
         }
-        const double lhs = (dlog(V) + dlog(invalpha)) - dlog((a / (us * us)) + b);
+        // the acceptance test as one logarithm (Hoermann's form)
+        const double lhs = dlog((V * invalpha) / ((a / (us * us)) + b));
         const double rhs = ((-mu) + kd * loglam) - dlogfact((int64_t)kd);
         if (lhs <= rhs) return (int64_t)kd;
     }

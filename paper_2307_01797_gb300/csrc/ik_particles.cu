@@ -733,7 +733,7 @@ __device__ long long KT<float>::poisson(Stream& s, float mu)
         const float kd = floorf(((((2.0f * a) / us) + b) * U + mu) + 0.43f);
         if (us >= 0.07f && V <= vr) return (long long)kd;
         if (kd < 0.0f || (us < 0.013f && V > us)) continue;
-        const float lhs = (logf(V) + logf(invalpha)) - logf((a / (us * us)) + b);
+        const float lhs = logf((V * invalpha) / ((a / (us * us)) + b));
         const float rhs = ((-mu) + kd * loglam) - lgammaf(kd + 1.0f);
         if (lhs <= rhs) return (long long)kd;
     }

@@ -235,6 +235,31 @@ def test_edge_cases():
     assert e.value.code == -4
 
 
+@pytest.mark.parametrize("precision", [itokmc.FP64, itokmc.MIXED])
+def test_runaway_charge_reports_overflow(precision):
+    """A cell whose ion surplus leaves the fixed-point range of rho (2^(62-3s)
+    elementary charges, s = 10) is reported as ERR_OVERFLOW before any field
+    is computed from it; the handle stays usable once the state is valid."""
+    ph = small_phys(8, dt=1e-12)
+    H = gpu_handle(ph, 1000, precision=precision)
+    L = ph["hi"][0]
+    H.itokmc_set_particles(np.array([L / 2]), np.array([L / 2]), np.array([L / 2]), np.array([1], np.uint32))
+    n3 = ph["n"] ** 3
+    npos = np.zeros(n3, np.int64)
+    npos[n3 // 2] = 1 << 33
+    H.itokmc_set_ions(npos, np.zeros(n3, np.int64))
+    with pytest.raises(itokmc.ItokmcError) as e:
+        H.itokmc_solve_field()
+    assert e.value.code == -5
+    npos[n3 // 2] = (1 << 32) - 1          # the largest surplus the guard admits
+    H.itokmc_set_ions(npos, np.zeros(n3, np.int64))
+    H.itokmc_solve_field()
+    H.itokmc_set_ions(np.zeros(n3, np.int64), np.zeros(n3, np.int64))
+    H.itokmc_solve_field()
+    H.itokmc_step(1)
+    H.close()
+
+
 # ---------------------------------------------------------------- mixed form
 def _mixed_handle(ph, st, E, ions, seed0, cap):
     H = gpu_handle(ph, cap, seed0=seed0, precision=itokmc.MIXED)
