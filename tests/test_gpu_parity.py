@@ -102,6 +102,39 @@ def test_kmc_and_particles_bit_exact():
     assert st_["photons_absorbed_weight"] + st_["photons_lost_weight"] == int(info["n_ph"].sum())
 
 
+@pytest.mark.parametrize("ppc", [8, 32])
+def test_merge_tiers_bit_exact(ppc):
+    """Cells whose merge lists fall in each tier of the merge kernel (lists of
+    up to 96 and 256 elements in shared memory, longer ones in the global
+    work area), some with equal coordinates: the whole particles stage bit
+    for bit against the oracle."""
+    ph = small_phys(8, dt=1e-13, ppc=ppc, photon_ratio=0.0)
+    rng = np.random.default_rng(17 + ppc)
+    h = (ph["hi"][0] - ph["lo"][0]) / ph["n"]
+    cols = {k: [] for k in ("x", "y", "z", "w")}
+    for (i, j, k), m in [((1, 1, 1), 30), ((4, 4, 4), 90), ((3, 4, 5), 150), ((6, 2, 3), 400)]:
+        X = [ph["lo"][0] + (c + rng.uniform(0.05, 0.95, m)) * h for c in (i, j, k)]
+        X[0][: m // 8] = X[0][0]            # equal x: the stable order decides
+        X[2][m // 8: m // 4] = X[2][m // 8]
+        for key, v in zip(("x", "y", "z"), X):
+            cols[key].append(v)
+        cols["w"].append(rng.integers(1, 5000, m).astype(np.uint32))
+    st = {k: np.concatenate(v) for k, v in cols.items()}
+    E = synth.random_field(ph, seed=11, amp=3e6, base=4.5e6)
+    seed0, step = 7, 1
+    S = oracle_state(ph, st, seed0)
+    p = oracle.make_params(ph, seed=seed0, step=step)
+    new_state, info = oracle.step(p, S, E)
+    H = _setup(ph, st, E, None, seed0, step)
+    H.itokmc_run_stage(itokmc.STAGE_TRANSPORT)
+    H.itokmc_run_stage(itokmc.STAGE_KMC)
+    H.itokmc_run_stage(itokmc.STAGE_PARTICLES)
+    assert_particles_equal(H.itokmc_read_particles(), new_state)
+    st_ = H.itokmc_get_stats()
+    assert st_["merge_max_list"] >= 400 and st_["merge_cells"] >= 4
+    H.close()
+
+
 def _field_err(phi_g, E_g, phi_o, E_o):
     ephi = np.max(np.abs(phi_g - phi_o.ravel())) / np.max(np.abs(phi_o))
     Eo = np.stack([e.ravel() for e in E_o])
