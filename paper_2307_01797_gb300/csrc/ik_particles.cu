@@ -1320,8 +1320,9 @@ constexpr uint8_t NO_SPLIT = 0xff;
 // element with 2 C > W), a unit-weight median joins the lighter side (left
 // on ties) and a heavier one is divided ceil(W/2) - W_L : rest.  Leaves are
 // the nodes after log2(ppc) levels.  Per level the warp runs element-
-// parallel passes (bounding boxes by group reductions, a rank sort, a
-// segmented weight scan, a scatter into the next level's list) and node-
+// parallel passes (bounding boxes by group reductions carried across chunks
+// of 32, a rank sort whose loop also gives each element's prefix weight and
+// so the weighted median, a scatter into the next level's list) and node-
 // parallel passes (axis, median bookkeeping).  GLOBAL: the scratch lives in
 // the work area (cells too long for shared memory).
 template <class E, bool GLOBAL>
