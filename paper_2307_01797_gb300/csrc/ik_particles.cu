@@ -1126,7 +1126,7 @@ __host__ __device__ inline MLayout merge_layout(uint32_t cap, uint32_t T, uint32
     L.nW = ml_take(o, T * 8);
     L.nW2 = ml_take(o, (T + 1) * 8);
     L.nC = ml_take(o, T * 8);
-    L.keys = ml_take(o, cap * ksize);
+    L.keys = ml_take(o, cap * (ksize == 4 ? 8u : 16u));   // KeyW<K>
     L.nlo = ml_take(o, 3 * T * ksize);
     L.nhi = ml_take(o, 3 * T * ksize);
     L.nA = ml_take(o, T * 4);
@@ -1218,6 +1218,13 @@ struct MP {           // merge work element (FP64 form)
 
 template <class E> struct EKey { using K = unsigned long long; };
 template <> struct EKey<MP32> { using K = uint32_t; };
+
+// A sort key beside its element's weight: the rank loop reads both with one
+// vector load.
+template <class K> struct __align__(sizeof(K) == 4 ? 8 : 16) KeyW {
+    K k;
+    uint32_t w;
+};
 
 // Order-preserving integer keys of coordinates: the tree compares keys with
 // integer instructions (FP64 comparisons run at a small fraction of the FP32
@@ -1377,7 +1384,7 @@ __global__ void __launch_bounds__(128) k_merge_lv(
         unsigned long long* nW = reinterpret_cast<unsigned long long*>(base + L.nW);
         unsigned long long* nW2 = reinterpret_cast<unsigned long long*>(base + L.nW2);
         unsigned long long* nC = reinterpret_cast<unsigned long long*>(base + L.nC);
-        K* keys = reinterpret_cast<K*>(base + L.keys);
+        KeyW<K>* keys = reinterpret_cast<KeyW<K>*>(base + L.keys);
         K* nlo = reinterpret_cast<K*>(base + L.nlo);
         K* nhi = reinterpret_cast<K*>(base + L.nhi);
         uint32_t* nA = reinterpret_cast<uint32_t*>(base + L.nA);
@@ -1556,7 +1563,8 @@ __global__ void __launch_bounds__(128) k_merge_lv(
             __syncwarp();
             for (uint32_t j = lane; j < n; j += 32) {
                 const uint8_t a = nax[nid[j]];
-                keys[j] = a == NO_SPLIT ? (K)0 : ET<E>::key(cur[j], a);
+                const E e = cur[j];
+                keys[j] = KeyW<K>{ a == NO_SPLIT ? (K)0 : ET<E>::key(e, a), e.w };
             }
             __syncwarp();
             // ---- stable rank sort within each node (cur -> tmp), and the
@@ -1569,7 +1577,7 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                 const E ej = cur[j];
                 if (nax[d] == NO_SPLIT) { tmp[j] = ej; continue; }
                 const uint32_t s0 = nb[d], s1 = nb[d + 1];
-                const K kj = keys[j];
+                const K kj = keys[j].k;
                 // one pass over the node (every lane of the node busy for the
                 // same trip count): smaller keys, and equal keys placed before
                 uint32_t rk = 0;
@@ -1577,8 +1585,9 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                 if (w32) {
                     uint32_t pw = 0;
                     for (uint32_t k = s0; k < s1; ++k) {
-                        const K kk = keys[k];
-                        const uint32_t wk = cur[k].w;
+                        const KeyW<K> q = keys[k];
+                        const K kk = q.k;
+                        const uint32_t wk = q.w;
                         const bool bf = (kk < kj) | ((kk == kj) & (k < j));
                         rk += bf;
                         pw += bf ? wk : 0u;
@@ -1587,8 +1596,9 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                 } else {
                     unsigned long long pw = 0;
                     for (uint32_t k = s0; k < s1; ++k) {
-                        const K kk = keys[k];
-                        const uint32_t wk = cur[k].w;
+                        const KeyW<K> q = keys[k];
+                        const K kk = q.k;
+                        const uint32_t wk = q.w;
                         const bool bf = (kk < kj) | ((kk == kj) & (k < j));
                         rk += bf;
                         pw += bf ? (unsigned long long)wk : 0ull;
