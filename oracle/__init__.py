@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
 and by the CPU-baseline leg of ``bench.py``; never by the product package.
 It shares no code with the CUDA library.  The particle, KMC and photon steps
 are plain C (``itokmc_oracle.c``, built without FMA contraction); the field
-solve is numpy (``poisson.py``); the step composition is ``step.py``.
+solve is numpy (``poisson.py``); the step composition is ``stages.py``; the
+semi-implicit field coupling of Sec. 4.3 (variable-coefficient solve and the
+diffusive/advective substeps) is ``semi_implicit.py``.
 """
 from __future__ import annotations
 
@@ -101,6 +103,8 @@ def lib():
             L.ora_uniform_draws.argtypes = [u64, u32, u32, u32, u32, i64, pd]
             L.ora_normal_draws.argtypes = [u64, u32, u32, u32, u32, i64, pd]
             L.ora_push.argtypes = [pp, i64, pd, pd, pd, pd, pd, pd, pd, pd, pd, pi64]
+            L.ora_diffuse.argtypes = [pp, i64, pd, pd, pd, pd, pd, pd]
+            L.ora_advect.argtypes = [pp, i64, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pi64]
             L.ora_sort_by_cell.argtypes = [i64, i64, pi64, pi64]; L.ora_sort_by_cell.restype = i64
             L.ora_deposit.argtypes = [pp, i64, pd, pd, pd, pu32, pi64, pi64, pi64]
             L.ora_kmc.argtypes = [pp, pi64, pd, pd, pd, pi64, pi64, pi64]; L.ora_kmc.restype = ctypes.c_int

@@ -25,6 +25,9 @@
  *   normal sampler                 (ziggurat of Marsaglia & Tsang 2000)
  *   push      a1+a2  -- Sec. 4.2 (CIC interpolation), Sec. 4.3 (explicit
  *                       Euler-Maruyama, first equation), Eq. ito_kernel
+ *   diffuse / advect -- the semi-implicit transport of Sec. 4.3 (Eq.
+ *                       Xdagger, Eq. particle_kernel, Eq. Vk1); its field
+ *                       solve is oracle/semi_implicit.py
  *   sort      a3     -- stable sort by cell ("spatial binning", Sec. 5.6)
  *   deposit   a4     -- Sec. 4.2 CIC deposition in int64 fixed point
  *   kmc       a6     -- Sec. 3.2.3 steps 1-8 (Cao et al. hybrid, eps = inf)
@@ -509,6 +512,53 @@ void ora_push(const ora_params* p, int64_t np, const double* x, const double* y,
         for (int ax = 0; ax < 3; ++ax) N[ax] = ora_normal(&s);
         double Xn[3];
         for (int ax = 0; ax < 3; ++ax) Xn[ax] = (X[ax] + (nmu * Ep[ax]) * p->dt) + sdt * N[ax];
+        xo[i] = Xn[0]; yo[i] = Xn[1]; zo[i] = Xn[2];
+        if (inside(p, Xn))
+            cell_out[i] = lin(p, cell_axis(p, 0, Xn[0]), cell_axis(p, 1, Xn[1]), cell_axis(p, 2, Xn[2]));
+        else
+            cell_out[i] = -1;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Semi-implicit transport (Sec. 4.3, Eq. particle_kernel and Eq. Xdagger;   */
+/* Sec. 4.7 steps 2, 4 and 5).  ora_diffuse: the diffusive advance           */
+/* X+ = X + sqrt(2 D dt) N with the normals of ora_push (same stream, same   */
+/* order), no removal (the charge density rho+ of Sec. 4.7 step 3 is         */
+/* deposited at X+ with the folded stencil).  ora_advect: V = -mu E(X) with  */
+/* the new field interpolated at the position X of the start of the step     */
+/* (Eq. Vk1), X' = X+ + V dt, removal outside [lo, hi) as in ora_push.       */
+/* ------------------------------------------------------------------------ */
+void ora_diffuse(const ora_params* p, int64_t np, const double* x, const double* y, const double* z,
+                 double* xd, double* yd, double* zd)
+{
+    double sdt = sqrt((2.0 * p->D) * p->dt);
+    for (int64_t i = 0; i < np; ++i) {
+        ora_stream s;
+        stream_init(&s, p->seed, (uint32_t)i, p->step, TAG_PUSH, 0);
+        double N[3];
+        for (int ax = 0; ax < 3; ++ax) N[ax] = ora_normal(&s);
+        xd[i] = x[i] + sdt * N[0];
+        yd[i] = y[i] + sdt * N[1];
+        zd[i] = z[i] + sdt * N[2];
+    }
+}
+
+void ora_advect(const ora_params* p, int64_t np, const double* x, const double* y, const double* z,
+                const double* xd, const double* yd, const double* zd,
+                const double* Ex, const double* Ey, const double* Ez,
+                double* xo, double* yo, double* zo, int64_t* cell_out)
+{
+    double nmu = -p->mu;
+    for (int64_t i = 0; i < np; ++i) {
+        double X[3] = { x[i], y[i], z[i] };
+        int ia[3], ib[3];
+        double f[3];
+        for (int ax = 0; ax < 3; ++ax) cic_axis(p, ax, X[ax], &ia[ax], &ib[ax], &f[ax]);
+        double Ep[3] = { interp(p, Ex, ia, ib, f), interp(p, Ey, ia, ib, f), interp(p, Ez, ia, ib, f) };
+        double Xd[3] = { xd[i], yd[i], zd[i] };
+        double Xn[3];
+        for (int ax = 0; ax < 3; ++ax) Xn[ax] = Xd[ax] + (nmu * Ep[ax]) * p->dt;
         xo[i] = Xn[0]; yo[i] = Xn[1]; zo[i] = Xn[2];
         if (inside(p, Xn))
             cell_out[i] = lin(p, cell_axis(p, 0, Xn[0]), cell_axis(p, 1, Xn[1]), cell_axis(p, 2, Xn[2]));
