@@ -303,6 +303,30 @@ def test_kmc_leap_mean_and_variance_discrete_closed_form(oracle_mod):
     assert abs(finals.var() / v - 1.0) < 5 * math.sqrt(2.0 / R)
 
 
+def test_kmc_finite_eps_follows_the_yule_process(oracle_mod):
+    """Finite eps (Sec. 3.2.3 step 4, the Cao step bound): a pure birth
+    process over lambda dt = 1 is split into substeps of relative change
+    ~eps, so the final count approaches the exact Yule law, mean X0 e and
+    variance X0 e (e - 1), to a bias of order eps; one eps = inf leap has mean
+    X0 (1 + lambda dt) = 2 X0 instead."""
+    ph = _phys_small(8, dt=1e-12)
+    lam = 1.0 / ph["dt"]
+    X0, R = 2000, 400
+
+    def finals(eps):
+        p = oracle_mod.make_params(dict(ph, eps=eps), seed=21, step=0)
+        return np.array([oracle_mod.kmc_single(p, X0, lam, 0.0, 0.0, index=r)[0] for r in range(R)],
+                        dtype=np.float64)
+
+    mean_y, var_y = X0 * math.e, X0 * math.e * (math.e - 1.0)
+    f = finals(0.03)
+    se = math.sqrt(var_y / R)
+    assert 0.95 * mean_y < f.mean() < mean_y + 5 * se
+    assert abs(f.var() / var_y - 1.0) < 0.25
+    g = finals(float("inf"))
+    assert abs(g.mean() - 2 * X0) < 5 * math.sqrt(2 * X0 / R) + 1
+
+
 def test_kmc_birth_death_small_numbers_kendall(oracle_mod):
     """From one electron with A dt << 1 the hybrid runs the exact SSA/critical
     branches: mean and extinction probability of a linear birth-death process
