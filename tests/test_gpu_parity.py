@@ -102,6 +102,32 @@ def test_kmc_and_particles_bit_exact():
     assert st_["photons_absorbed_weight"] + st_["photons_lost_weight"] == int(info["n_ph"].sum())
 
 
+def test_kmc_finite_eps_bit_exact():
+    """The Cao step bound for a finite eps (substeps of bounded relative
+    change) in the FP64 KMC kernel: firings per cell bit for bit against the
+    oracle, in a case where the bound splits the step (the firings differ
+    from those of eps = inf)."""
+    ph = small_phys(16, dt=5e-11, photon_ratio=0.06, eps=0.01)
+    st = mixed_state(ph, seed=13, peak=2e19, n_random=800)
+    E = synth.random_field(ph, seed=9, amp=3e6, base=4.5e6)
+    ions = synth.random_ions(ph, seed=4)
+    seed0, step = 5, 1
+    S = oracle_state(ph, st, seed0, *ions)
+    _, info = oracle.step(oracle.make_params(ph, seed=seed0, step=step), S, E)
+    ph_inf = dict(ph, eps=float("inf"))
+    _, info_inf = oracle.step(oracle.make_params(ph_inf, seed=seed0, step=step),
+                              oracle_state(ph_inf, st, seed0, *ions), E)
+    assert not np.array_equal(info["n_ion"], info_inf["n_ion"])
+    H = _setup(ph, st, E, ions, seed0, step)
+    H.itokmc_run_stage(itokmc.STAGE_TRANSPORT)
+    H.itokmc_run_stage(itokmc.STAGE_KMC)
+    F = H.itokmc_read_densities(itokmc.FIRINGS)
+    assert np.array_equal(F[0], info["n_ion"])
+    assert np.array_equal(F[1], info["n_att"])
+    assert np.array_equal(F[2], info["n_ph"])
+    H.close()
+
+
 @pytest.mark.parametrize("ppc", [8, 32])
 def test_merge_tiers_bit_exact(ppc):
     """Cells whose merge lists fall in each tier of the merge kernel (lists of
