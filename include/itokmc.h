@@ -196,6 +196,22 @@ int itokmc_run_stage(itokmc_handle* h, int32_t stage);
 /* Advances the step counter used in every Philox counter by one. */
 int itokmc_advance_counter(itokmc_handle* h);
 
+/* Semi-implicit transport stage (Sec. 4.3, Eq. particle_kernel, Eq. Xdagger,
+ * Eq. poisson_simp, Eq. conductivity; Sec. 4.7 steps 1-5), the alternative
+ * to ITOKMC_STAGE_TRANSPORT that removes the dielectric-relaxation limit of
+ * the explicit push: conductivity sigma = q_e mu n_e from a CIC deposit of
+ * the current particles; diffusive advance X+ = X + sqrt(2 D dt) N (the
+ * push's normals); charge rho+ of the diffused particles; FP64 multigrid on
+ * div[(1 + sigma dt / eps0) grad phi] = -rho+/eps0 (face coefficient: the
+ * mean of the two cells'; boundary faces: the cell's own) to mg_rtol, E =
+ * -grad(phi) into the handle's field; advective step X' = X+ - mu E(X) dt
+ * with E at the start-of-step position X; then the stable sort, the deposit
+ * and the charge of X' as in ITOKMC_STAGE_TRANSPORT.  FP64 form only
+ * (ERR_ARG for the mixed form).  cycles_out / rel_out (may be NULL): the
+ * V-cycles taken and the final relative residual.  Errors: ERR_ARG,
+ * ERR_NOCONV, ERR_OVERFLOW, ERR_CAPACITY, ERR_CUDA. */
+int itokmc_transport_semi_implicit(itokmc_handle* h, int32_t* cycles_out, double* rel_out);
+
 /* ---- autotuning ----------------------------------------------------------
  * The paper fixes no smoother counts; the multigrid cycle (Sec. 4.3:
  * V-cycles with red-black Gauss-Seidel smoothing) takes nu1 pre- and nu2

@@ -103,11 +103,14 @@ def solve(rho_fixed, c: np.ndarray, phys: dict):
     return phi, efield(phi, h, phi_top)
 
 
-def transport(p, phys: dict, S: dict):
+def transport(p, phys: dict, S: dict, E=None):
     """Sec. 4.7 steps 1-5 for the particles of S (canonical order: x, y, z,
     w, cell; Npos, Nneg per cell).  Returns a dict with the advected
     positions (xo, yo, zo), their cells (-1: left the box), the diffused
-    positions (xd, yd, zd), sigma, rho+ and the new field (phi, E)."""
+    positions (xd, yd, zd), sigma, rho+ and the new field (phi, E).  A given
+    field E (Ex, Ey, Ez) replaces the solve in step 3 (phi is then None):
+    the substeps can be checked on their own against a field from
+    elsewhere."""
     from . import lib, _P
     from .stages import deposit, rho_fixed
     import ctypes
@@ -129,9 +132,12 @@ def transport(p, phys: dict, S: dict):
     # of them, also those diffused past a face; their X_e tally is not used)
     ne_d, _ = deposit(p, xd, yd, zd, w, np.zeros(npart, np.int64))
     rho_d = rho_fixed(p, ne_d, S["Npos"], S["Nneg"])
-    phi, E = solve(rho_d, coefficient(sigma, float(phys["dt"])), phys)
+    if E is None:
+        phi, E = solve(rho_d, coefficient(sigma, float(phys["dt"])), phys)
+    else:
+        phi = None
     # 4.-5. velocity from the new field at X^k, advective step from X+
-    Ex, Ey, Ez = (np.ascontiguousarray(e.ravel(), np.float64) for e in E)
+    Ex, Ey, Ez = (np.ascontiguousarray(np.ravel(e), np.float64) for e in E)
     xo, yo, zo = np.empty(npart), np.empty(npart), np.empty(npart)
     cell = np.empty(npart, np.int64)
     lib().ora_advect(ctypes.byref(p), npart, _P(x, pd), _P(y, pd), _P(z, pd), _P(xd, pd), _P(yd, pd),

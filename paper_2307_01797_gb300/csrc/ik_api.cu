@@ -45,6 +45,7 @@ struct itokmc_handle {
     itokmc_stats st{};
     cudaEvent_t ev[8]{};
     struct Readback { uint32_t N; uint32_t pad; ik::Counters ctr; }* rb = nullptr;  // pinned
+    double* semi_c[ik::MAX_LEVELS] = {};   // semi-implicit coefficients per level (on first use)
 };
 
 namespace {
@@ -686,6 +687,58 @@ int itokmc_run_stage(itokmc_handle* h, int32_t stage)
     case ITOKMC_STAGE_FIELD: return stage_field(h);
     default: return fail(h, ITOKMC_ERR_ARG, "unknown stage");
     }
+}
+
+int itokmc_transport_semi_implicit(itokmc_handle* h, int32_t* cycles_out, double* rel_out)
+{
+    IK_GUARD(h);
+    ik::Dev& d = h->d;
+    if (d.mixed || d.phi_F > 0)
+        return fail(h, ITOKMC_ERR_ARG, "semi-implicit transport: FP64 form only");
+    // no work of an overlapped field solve may still be in flight
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    if (h->sf) IK_CHECK(h, cudaStreamSynchronize(h->sf));
+    int rc = 0;
+    for (int l = 0; l < d.nlev && !rc; ++l)
+        if (!h->semi_c[l]) {
+            const size_t n = (size_t)d.lev[l].n;
+            h->semi_c[l] = dalloc_n<double>(h, (size_t)h->P.R * n * n * n, &rc);
+        }
+    if (rc) return rc;
+    IK_CHECK(h, cudaEventRecord(h->ev[0], h->s));
+    ik::launch_deposit_only(h->P, d, h->N, h->s);       // n_e of the start of the step
+    ik::launch_semi_coef(h->P, d, h->semi_c[0], h->s);
+    ik::launch_diffuse(h->P, d, h->N, h->s);            // X+ into recB
+    ik::launch_deposit_B(h->P, d, h->N, h->s);
+    IK_CHECK(h, cudaMemsetAsync(d.ctr, 0, sizeof(ik::Counters), h->s));
+    ik::launch_rho(h->P, d, h->G, h->s);                // rho+
+    rc = readback(h);
+    if (rc) return rc;
+    rc = status_of_err(h, h->rb->ctr.err);
+    if (rc) return rc;
+    int cycles = 0;
+    double rel = 0.0;
+    const int st = ik::field_solve_vc(h->P, d, h->semi_c, d.norm_out, d.norm_host, h->cfg.mg_rtol, h->cfg.mg_nu1,
+                                      h->cfg.mg_nu2, h->cfg.mg_max_cycles, h->s, &cycles, &rel);
+    if (cycles_out) *cycles_out = cycles;
+    if (rel_out) *rel_out = rel;
+    h->st.mg_cycles = cycles;
+    h->st.mg_rel_residual = rel;
+    if (st == -3) return cuda_check(h, cudaGetLastError(), "semi-implicit field solve");
+    if (st != 0) return fail(h, ITOKMC_ERR_NOCONV, "semi-implicit field: multigrid did not reach mg_rtol");
+    ik::launch_advect(h->P, d, h->N, h->s);
+    ik::launch_transport_finish(h->P, d, h->N, h->G, h->s);
+    ik::launch_rho(h->P, d, h->G, h->s);
+    IK_CHECK(h, cudaEventRecord(h->ev[1], h->s));
+    rc = readback(h);
+    if (rc) return rc;
+    const ik::Counters& c = h->rb->ctr;
+    h->st.n_movers = (int64_t)c.n_movers;
+    int64_t out = 0;
+    for (int r = 0; r < h->P.R; ++r) out += (int64_t)c.outflow[r];
+    h->st.outflow_weight = out;
+    h->st.ms_transport = elapsed(h, 0, 1);
+    return status_of_err(h, c.err);
 }
 
 int itokmc_autotune(itokmc_handle* h, itokmc_tuning* out)

@@ -602,6 +602,129 @@ void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
     }
 }
 
+
+// ------------------------------------------------------------------ semi-implicit
+// Variable-coefficient operator of the semi-implicit coupling (Sec. 4.3, Eq.
+// poisson_simp): div(c grad phi) with c = 1 + sigma dt / eps0 per cell; the
+// coefficient of an interior face is the mean of its two cells', a boundary
+// face takes the cell's own (Neumann sides: no flux; Dirichlet electrodes:
+// ghost 2 phi_b - phi_1).  With c = 1 it is the operator above.  The
+// systems are scaled by h^2 like the constant-coefficient ones.
+__device__ __forceinline__ double vc_nbr(const double* __restrict__ phi, const double* __restrict__ c, uint64_t idx,
+                                         int n, int i, int j, int k, double& dsum)
+{
+    const uint64_t sy = (uint64_t)n, sz = (uint64_t)n * n;
+    const double ci = c[idx];
+    double s = 0.0, d = 0.0;
+    if (i > 0) { const double cf = 0.5 * (c[idx - 1] + ci); s += cf * phi[idx - 1]; d += cf; }
+    if (i < n - 1) { const double cf = 0.5 * (ci + c[idx + 1]); s += cf * phi[idx + 1]; d += cf; }
+    if (j > 0) { const double cf = 0.5 * (c[idx - sy] + ci); s += cf * phi[idx - sy]; d += cf; }
+    if (j < n - 1) { const double cf = 0.5 * (ci + c[idx + sy]); s += cf * phi[idx + sy]; d += cf; }
+    if (k > 0) { const double cf = 0.5 * (c[idx - sz] + ci); s += cf * phi[idx - sz]; d += cf; }
+    else d += 2.0 * ci;
+    if (k < n - 1) { const double cf = 0.5 * (ci + c[idx + sz]); s += cf * phi[idx + sz]; d += cf; }
+    else d += 2.0 * ci;
+    dsum = d;
+    return s;
+}
+
+__global__ void k_smooth_vc(double* __restrict__ phi, const double* __restrict__ rhs, const double* __restrict__ c,
+                            Geo G, int color)
+{
+    const uint64_t half = G.cells >> 1;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < half; t += (uint64_t)gridDim.x * blockDim.x) {
+        const int n = G.n;
+        const int ih = (int)(t & (uint64_t)(n / 2 - 1));
+        const int j = (int)((t >> (G.log2n - 1)) & (uint64_t)(n - 1));
+        const int k = (int)((t >> (2 * G.log2n - 1)) & (uint64_t)(n - 1));
+        const uint64_t r = t >> (3 * G.log2n - 1);
+        const int i = 2 * ih + ((j + k + color) & 1);
+        const uint64_t idx = ((r * n + k) * n + j) * n + i;
+        double d;
+        const double sum = vc_nbr(phi, c, idx, n, i, j, k, d);
+        phi[idx] = (sum - rhs[idx]) / d;
+    }
+}
+
+// Residual h^2 (b - A phi) at fine cells, half the sum of 8 children into the
+// coarse right-hand side (the convention of k_resid_restrict).
+__global__ void k_resid_restrict_vc(const double* __restrict__ phi, const double* __restrict__ rhs,
+                                    const double* __restrict__ c, double* __restrict__ rhs_c, Geo Gc, int nf)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < Gc.cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        int r, K, J, I;
+        decode(t, Gc.log2n, r, K, J, I);
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q >> 2);
+            const uint64_t idx = (((uint64_t)r * nf + k) * nf + j) * nf + i;
+            double d;
+            const double sum = vc_nbr(phi, c, idx, nf, i, j, k, d);
+            acc += rhs[idx] - (sum - d * phi[idx]);
+        }
+        rhs_c[t] = acc * 0.5;
+    }
+}
+
+// Coarse coefficient: the mean of the 8 children.
+__global__ void k_coef_restrict(const double* __restrict__ cf, double* __restrict__ cc, Geo Gc, int nf)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < Gc.cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        int r, K, J, I;
+        decode(t, Gc.log2n, r, K, J, I);
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q >> 2);
+            acc += cf[(((uint64_t)r * nf + k) * nf + j) * nf + i];
+        }
+        cc[t] = acc * 0.125;
+    }
+}
+
+// Squared norms of the residual and of the right-hand side per realization
+// (atomic sums: only the convergence test reads them).
+__global__ void k_resid_norm_vc(const double* __restrict__ phi, const double* __restrict__ rhs,
+                                const double* __restrict__ c, Geo G, double* __restrict__ acc)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G.cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        int r, k, j, i;
+        decode(t, G.log2n, r, k, j, i);
+        double d;
+        const double sum = vc_nbr(phi, c, t, G.n, i, j, k, d);
+        const double res = rhs[t] - (sum - d * phi[t]);
+        atomicAdd(acc + 2 * r, res * res);
+        atomicAdd(acc + 2 * r + 1, rhs[t] * rhs[t]);
+    }
+}
+
+// h^2 b = h^2 (-rho/eps0) with the top electrode term weighted by the
+// boundary cell's coefficient.
+__global__ void k_rhs_vc(const int64_t* __restrict__ rho, const double* __restrict__ c, double* __restrict__ rhs, Geo G,
+                         double qscale, double bc_top, double h2)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G.cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        int r, k, j, i;
+        decode(t, G.log2n, r, k, j, i);
+        double b = -((double)rho[t] * qscale);
+        if (k == G.n - 1) b = b - c[t] * bc_top;
+        rhs[t] = b * h2;
+    }
+}
+
+// c = 1 + sigma dt / eps0, sigma = q_e mu n_e (Eq. conductivity) from the
+// fixed-point CIC electron count.
+__global__ void k_coef_from_ne(const unsigned long long* __restrict__ ne_fix, double* __restrict__ c, uint64_t cells,
+                               double per_cell, double qmu, double dt_eps)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        const double ne = ((double)ne_fix[t] * per_cell);
+        const double sigma = qmu * ne;
+        c[t] = 1.0 + sigma * dt_eps;
+    }
+}
+
 }  // namespace
 
 constexpr int MAX_REAL_NORM = 4096;
@@ -837,6 +960,96 @@ void launch_phi_to_double(const Params& P, Dev& d, double* out, cudaStream_t s)
     ++g_launches;
     k_phi_to_double<<<gridsz(G0.cells, 256), 256, 0, s>>>(reinterpret_cast<const long long*>(d.lev[0].phi), out,
                                                           std::ldexp(1.0, -d.phi_F), G0.cells);
+}
+
+
+// ------------------------------------------------------------------ semi-implicit solve
+// One V-cycle of the variable-coefficient system from level l (RB-GS, the
+// colour order of the constant-coefficient cycle; the coarsest level is
+// relaxed by 40 sweep pairs).
+static void vcycle_vc(const Dev& d, double* const* c, int l, int R, int nu1, int nu2, cudaStream_t s)
+{
+    const Geo G = geo(d, l, R);
+    double* phi = d.lev[l].phi;
+    const double* rhs = d.lev[l].rhs;
+    const int tpb = 256;
+    auto sweep = [&](int color) {
+        ++g_launches;
+        k_smooth_vc<<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, c[l], G, color);
+    };
+    if (l == d.nlev - 1) {
+        for (int it = 0; it < 40; ++it) { sweep(0); sweep(1); }
+        return;
+    }
+    for (int it = 0; it < nu1; ++it) { sweep(0); sweep(1); }
+    const Geo Gc = geo(d, l + 1, R);
+    g_launches += 2;
+    k_resid_restrict_vc<<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(phi, rhs, c[l], d.lev[l + 1].rhs, Gc, G.n);
+    cudaMemsetAsync(d.lev[l + 1].phi, 0, Gc.cells * sizeof(double), s);
+    vcycle_vc(d, c, l + 1, R, nu1, nu2, s);
+    k_prolong<double><<<gridsz(G.cells, tpb), tpb, 0, s>>>(phi, d.lev[l + 1].phi, G);
+    for (int it = 0; it < nu2; ++it) { sweep(1); sweep(0); }
+}
+
+// Coefficients of the semi-implicit field (Sec. 4.7 step 1) into c0 from the
+// electron deposit in d.ne_fix (the particles at the start of the step).
+void launch_semi_coef(const Params& P, Dev& d, double* c0, cudaStream_t s)
+{
+    const Geo G0 = geo(d, 0, P.R);
+    const double dV = P.h[0] * P.h[1] * P.h[2];
+    const double per_cell = std::ldexp(1.0, -3 * P.frac_bits) / dV;
+    ++g_launches;
+    k_coef_from_ne<<<gridsz(G0.cells, 256), 256, 0, s>>>(d.ne_fix, c0, G0.cells, per_cell, 1.602176634e-19 * P.mu,
+                                                          P.dt / 8.8541878128e-12);
+}
+
+// Semi-implicit field (Sec. 4.7 step 3, FP64 form): the level-0
+// coefficients in c[0] (launch_semi_coef), restricted to the coarser levels,
+// the right-hand side from d.rho (the charge of the diffused particles), FP64
+// V-cycles until ||r|| <= rtol ||b|| per realization, then E = -grad(phi) into
+// d.E.  c[l] holds one coefficient per cell of level l; acc 2 R doubles of
+// device scratch, acc_host its pinned mirror.  Returns 0, -6 (no
+// convergence) or -3 (CUDA error).
+int field_solve_vc(const Params& P, Dev& d, double* const* c, double* acc, double* acc_host, double rtol, int nu1,
+                   int nu2, int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out)
+{
+    const int R = P.R;
+    const Geo G0 = geo(d, 0, R);
+    const int tpb = 256;
+    for (int l = 0; l + 1 < d.nlev; ++l) {
+        const Geo Gc = geo(d, l + 1, R);
+        ++g_launches;
+        k_coef_restrict<<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(c[l], c[l + 1], Gc, d.lev[l].n);
+    }
+    double qscale, bc_top;
+    rhs_consts(P, qscale, bc_top);
+    ++g_launches;
+    k_rhs_vc<<<gridsz(G0.cells, tpb), tpb, 0, s>>>(d.rho, c[0], d.lev[0].rhs, G0, qscale, bc_top,
+                                                    P.h[2] * P.h[2]);
+    int cyc = 0, status = -6;
+    double worst = 0.0;
+    for (cyc = 0; cyc <= max_cycles; ++cyc) {
+        cudaMemsetAsync(acc, 0, 2 * R * sizeof(double), s);
+        ++g_launches;
+        k_resid_norm_vc<<<gridsz(G0.cells, tpb), tpb, 0, s>>>(d.lev[0].phi, d.lev[0].rhs, c[0], G0, acc);
+        cudaMemcpyAsync(acc_host, acc, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
+        worst = 0.0;
+        bool done = true;
+        for (int r = 0; r < R; ++r) {
+            const double rn = std::sqrt(acc_host[2 * r]), bn = std::sqrt(acc_host[2 * r + 1]);
+            const double rel = bn > 0.0 ? rn / bn : rn;
+            if (rel > worst || !(rel == rel)) worst = rel;
+            if (!(rn <= rtol * bn)) done = false;
+        }
+        if (done) { status = 0; break; }
+        if (cyc == max_cycles || !std::isfinite(worst)) break;
+        vcycle_vc(d, c, 0, R, nu1, nu2, s);
+    }
+    if (cycles_out) *cycles_out = cyc;
+    if (rel_out) *rel_out = worst;
+    launch_efield_to(P, d, s, d.E, d.E32);
+    return status;
 }
 
 }  // namespace ik

@@ -515,6 +515,102 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f64(
     if (threadIdx.x == 0) blk_stay[blockIdx.x] = (uint32_t)nstay;
 }
 
+// The advective substep of the semi-implicit transport (Sec. 4.3, Eq.
+// particle_kernel), otherwise the FP64 push: B holds the diffused positions
+// X+ on entry; the field (of the end of the step) is interpolated at the
+// positions X of A and the particle moves from X+ by V dt, no normals drawn.
+__global__ void __launch_bounds__(TPB, 4) k_advect_f64(
+    Params P, const P64* __restrict__ A, P64* __restrict__ B, uint32_t* __restrict__ keyB, uint32_t N,
+    const uint32_t* __restrict__ cell_start, const E64* __restrict__ E, int32_t* __restrict__ cnt_new,
+    int32_t* __restrict__ in_cnt, int32_t* __restrict__ in_before, unsigned long long* __restrict__ Xe,
+    unsigned long long* __restrict__ ne_fix, Mover* __restrict__ movers, uint32_t mover_cap,
+    Counters* __restrict__ ctr, uint32_t* __restrict__ blk_stay)
+{
+    const uint32_t i = blockIdx.x * TPB + threadIdx.x;
+    bool alive = false, mover = false;
+    uint32_t gnew = 0, w = 0;
+    int rr = 0;
+    Stencil S;
+    if (i < N) {
+        const P64 p = ld_p64(A + i);
+        const uint32_t gold = p.cell;
+        const int r = real_of(P, gold);
+        rr = r;
+        const size_t ebase = (size_t)r * P.n3;
+        w = p.w;
+        const double X[3] = { p.x, p.y, p.z };
+        double Ep[3];
+        interp_f64(P, E + ebase, X, Ep);
+        const P64 pd = ld_p64(B + i);
+        const double Xd[3] = { pd.x, pd.y, pd.z };
+        const double nmu = -P.mu;
+        double Xn[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Xn[a] = Xd[a] + (nmu * Ep[a]) * P.dt;
+            const unsigned long long kx = dkey(Xn[a]);
+            inside = inside && kx >= dkey(P.lo[a]) && kx < dkey(P.hi[a]);
+        }
+        P64 q;
+        q.x = Xn[0]; q.y = Xn[1]; q.z = Xn[2]; q.w = w;
+        if (inside) {
+            // one division per axis serves the cell index and the stencil
+            int ic[3];
+            const long long one = 1ll << P.frac_bits;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double qd = grid_quot(Xn[a], P.lo[a], P.h[a], P.rh[a]);
+                QSplit t;
+                int ci, i0;
+                long long fq;
+                if (qsplit(qd, t)) {
+                    ci = t.qc;
+                    i0 = t.i0;
+                    fq = (long long)(t.F >> (t.sh - P.frac_bits));
+                } else {
+                    ci = (int)floor(qd);
+                    const double u = qd - 0.5;
+                    const double fl = floor(u);
+                    i0 = (int)fl;
+                    fq = (long long)floor((u - fl) * (double)one);
+                }
+                ic[a] = ci > P.n - 1 ? P.n - 1 : (ci < 0 ? 0 : ci);
+                S.ia[a] = clampi(i0, P.n);
+                S.ib[a] = clampi(i0 + 1, P.n);
+                S.A[a][0] = (uint32_t)(one - fq);
+                S.A[a][1] = (uint32_t)fq;
+            }
+            gnew = (uint32_t)(ebase + ((size_t)ic[2] * P.n + ic[1]) * P.n + ic[0]);
+            alive = true;
+            mover = gnew != gold;
+            q.cell = gnew;
+            keyB[i] = gnew | (mover ? KEY_MOVER : 0u);
+            if (mover) {
+                atomicAdd(in_cnt + gnew, 1);
+                if (gold < gnew) atomicAdd(in_before + gnew, 1);
+                const unsigned long long slot = warp_slot(&ctr->n_movers);
+                if (slot < mover_cap) movers[slot] = Mover{ gnew, i };
+                else atomicOr(&ctr->err, DERR_CAPACITY);
+            }
+        } else {
+            q.cell = gold;
+            keyB[i] = KEY_DEAD;
+            atomicAdd(&ctr->outflow[r], (unsigned long long)w);
+        }
+        st_p64(B + i, q);
+    }
+    block_deposit(P, ne_fix, alive, rr, S, w);
+    unsigned long long v = alive ? (unsigned long long)w : 0ull;
+    unsigned c = alive ? 1u : 0u;
+    if (warp_run_sum(gnew, alive, v, c)) {
+        atomicAdd(cnt_new + gnew, (int)c);
+        atomicAdd(Xe + gnew, v);
+    }
+    const int nstay = __syncthreads_count(alive && !mover);
+    if (threadIdx.x == 0) blk_stay[blockIdx.x] = (uint32_t)nstay;
+}
+
 // Exclusive scan over the pass-1 blocks of their stayer counts.
 struct BlockScanOp {
     const uint32_t* blk;
@@ -2019,6 +2115,62 @@ void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
     else
         k_push_f64<<<nblk, TPB, 0, s>>>(P, d.recA, d.recB, d.keyB, N, d.cell_start, d.E, d.cnt_new, d.in_cnt,
                                          d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr, d.blk_stay);
+}
+
+// Semi-implicit transport (FP64 form), Sec. 4.7 steps 2 and 5: the
+// diffusive substep X+ = X + sqrt(2 D dt) N into recB (the push's normals:
+// the same stream and order), and the advective substep from X+ with the
+// field of d.E, which also counts, keys and deposits like the push.
+__global__ void __launch_bounds__(TPB) k_diffuse_f64(Params P, const P64* __restrict__ A, P64* __restrict__ B,
+                                                     uint32_t N, const uint32_t* __restrict__ cell_start)
+{
+    const uint32_t i = blockIdx.x * TPB + threadIdx.x;
+    if (i >= N) return;
+    P64 p = ld_p64(A + i);
+    const int r = real_of(P, p.cell);
+    const uint32_t idx = i - cell_start[(size_t)r * P.n3];
+    PairStream s(seed_of(P, r), idx, P.step, TAG_PUSH, 0);
+    double Nn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Nn[a] = znormal(s);
+    p.x = p.x + P.sdt * Nn[0];
+    p.y = p.y + P.sdt * Nn[1];
+    p.z = p.z + P.sdt * Nn[2];
+    st_p64(B + i, p);
+}
+
+void launch_diffuse(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
+{
+    if (N == 0) return;
+    ++g_launches;
+    k_diffuse_f64<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.recA, d.recB, N, d.cell_start);
+}
+
+// Deposit (ne_fix, X_e) of the records of recB (the diffused positions).
+void launch_deposit_B(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
+{
+    const uint64_t G = (uint64_t)P.R * P.n3;
+    cudaMemsetAsync(d.Xe, 0, G * sizeof(unsigned long long), s);
+    cudaMemsetAsync(d.ne_fix, 0, G * sizeof(unsigned long long), s);
+    if (N == 0) return;
+    ++g_launches;
+    k_deposit_f64<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.recB, N, d.Xe, d.ne_fix);
+}
+
+void launch_advect(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
+{
+    const uint64_t G = (uint64_t)P.R * P.n3;
+    cudaMemsetAsync(d.cnt_new, 0, G * sizeof(int32_t), s);
+    cudaMemsetAsync(d.in_cnt, 0, G * sizeof(int32_t), s);
+    cudaMemsetAsync(d.in_before, 0, G * sizeof(int32_t), s);
+    cudaMemsetAsync(d.Xe, 0, G * sizeof(unsigned long long), s);
+    cudaMemsetAsync(d.ne_fix, 0, G * sizeof(unsigned long long), s);
+    cudaMemsetAsync(d.ctr, 0, sizeof(Counters), s);
+    if (N == 0) return;
+    ++g_launches;
+    k_advect_f64<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.recA, d.recB, d.keyB, N, d.cell_start, d.E,
+                                                          d.cnt_new, d.in_cnt, d.in_before, d.Xe, d.ne_fix,
+                                                          d.movers, d.mover_cap, d.ctr, d.blk_stay);
 }
 
 void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s)

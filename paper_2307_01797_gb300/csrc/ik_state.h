@@ -181,6 +181,9 @@ void launch_zig_init(cudaStream_t s);
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
 void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
 void launch_particles_b(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
+void launch_diffuse(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
+void launch_deposit_B(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
+void launch_advect(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
 // ik_sort.cu
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
                       uint32_t n, int key_bits, cudaStream_t s, long long* blk_scratch,
@@ -194,6 +197,9 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
                 int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out, bool extrapolate = false);
 void launch_efield(const Params& P, Dev& d, cudaStream_t s);
 void launch_efield_to(const Params& P, Dev& d, cudaStream_t s, E64* E, float4* E32);
+void launch_semi_coef(const Params& P, Dev& d, double* c0, cudaStream_t s);
+int field_solve_vc(const Params& P, Dev& d, double* const* c, double* acc, double* acc_host, double rtol, int nu1,
+                   int nu2, int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out);
 void launch_phi_to_double(const Params& P, Dev& d, double* out, cudaStream_t s);
 void launch_pack_field(const Params& P, Dev& d, const double* E3, cudaStream_t s);
 void launch_unpack_field(const Params& P, Dev& d, double* E3, cudaStream_t s);

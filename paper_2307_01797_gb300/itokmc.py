@@ -118,6 +118,8 @@ def lib(build_if_missing: bool = True):
                 "itokmc_step": ([H, i32], ctypes.c_int),
                 "itokmc_run_stage": ([H, i32], ctypes.c_int),
                 "itokmc_advance_counter": ([H], ctypes.c_int),
+                "itokmc_transport_semi_implicit": ([H, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
+                                                   ctypes.c_int),
                 "itokmc_autotune": ([H, ctypes.POINTER(Tuning)], ctypes.c_int),
                 "itokmc_read_densities": ([H, i32, i32, vp, ctypes.c_size_t], ctypes.c_int),
                 "itokmc_get_stats": ([H, ctypes.POINTER(Stats)], ctypes.c_int),
@@ -296,6 +298,13 @@ class Handle:
 
     def itokmc_advance_counter(self):
         _check(lib().itokmc_advance_counter(self.h), self.h)
+
+    def itokmc_transport_semi_implicit(self):
+        """The semi-implicit transport stage; returns (V-cycles, relative residual)."""
+        cyc = ctypes.c_int32()
+        rel = ctypes.c_double()
+        _check(lib().itokmc_transport_semi_implicit(self.h, ctypes.byref(cyc), ctypes.byref(rel)), self.h)
+        return cyc.value, rel.value
 
     def itokmc_read_densities(self, which, realization=0):
         cells = self.n ** 3 * (self.R if realization < 0 else 1)

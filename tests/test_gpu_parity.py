@@ -102,6 +102,38 @@ def test_kmc_and_particles_bit_exact():
     assert st_["photons_absorbed_weight"] + st_["photons_lost_weight"] == int(info["n_ph"].sum())
 
 
+@pytest.mark.parametrize("dt", [5e-12, 5e-11])
+def test_semi_implicit_transport_against_oracle(dt):
+    """The semi-implicit transport stage (Sec. 4.3, Sec. 4.7 steps 1-5): the
+    field of the variable-coefficient solve within the field tolerance of the
+    oracle's direct solve; with that field, the diffusive and advective
+    substeps, the sort and the deposit bit for bit like the oracle's."""
+    from oracle import semi_implicit as si
+    ph = small_phys(16, dt=dt)
+    st = mixed_state(ph, seed=21, peak=2e19, n_random=1500)
+    E0 = synth.random_field(ph, seed=5, amp=4e6)
+    ions = synth.random_ions(ph, seed=6)
+    seed0, step = 33, 2
+    S = oracle_state(ph, st, seed0, *ions)
+    p = oracle.make_params(ph, seed=seed0, step=step)
+    ref = si.transport(p, ph, S)
+    H = _setup(ph, st, E0, ions, seed0, step)
+    cycles, rel = H.itokmc_transport_semi_implicit()
+    assert 0 < cycles < 40 and rel <= 1e-10
+    Eg = H.itokmc_read_densities(itokmc.E).reshape(3, -1)
+    Eo = np.stack([e.ravel() for e in ref["E"]])
+    assert np.max(np.abs(Eg - Eo)) <= E_TOL * np.max(np.abs(Eo))
+    assert np.max(si.coefficient(ref["sigma"], dt)) > 1.0
+    r = si.transport(p, ph, S, E=tuple(Eg))
+    perm = oracle.sort_by_cell(r["cell"], ph["n"] ** 3)
+    T = dict(x=r["xo"][perm], y=r["yo"][perm], z=r["zo"][perm], w=S["w"][perm].copy(), cell=r["cell"][perm])
+    assert_particles_equal(H.itokmc_read_particles(), T)
+    ne, Xe = oracle.deposit(p, T["x"], T["y"], T["z"], T["w"], T["cell"])
+    assert np.array_equal(H.itokmc_read_densities(itokmc.NE_FIX), ne)
+    assert np.array_equal(H.itokmc_read_densities(itokmc.XE), Xe)
+    H.close()
+
+
 def test_kmc_finite_eps_bit_exact():
     """The Cao step bound for a finite eps (substeps of bounded relative
     change) in the FP64 KMC kernel: firings per cell bit for bit against the
