@@ -483,6 +483,51 @@ def ensemble_study(args):
 
 
 # ------------------------------------------------------------------ small config (C1)
+def semi_study(args):
+    """The semi-implicit transport stage (Sec. 4.3, Sec. 4.7 steps 1-5) on the
+    benchmark workload, FP64 form, against the explicit transport stage plus
+    the field solve it replaces: the time of each and the V-cycles of the
+    variable-coefficient solve (stage calls, each ending in a host
+    synchronisation)."""
+    import torch
+    from paper_2307_01797_gb300 import itokmc
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ph, st, ions = workload(args)
+    N0 = len(st["w"])
+    H = itokmc.Handle(itokmc.make_config(ph, int(N0 * args.cap_factor) + 20_000_000, seed0=1,
+                                         precision=itokmc.FP64))
+    H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+    H.itokmc_set_ions(*ions)
+    H.itokmc_solve_field()
+    K = args.study_steps
+    out = {"study": "semi", "grid": args.n, "particles": N0, "steps": K}
+    for mode in ("explicit", "semi"):
+        for _ in range(max(1, args.warmup)):
+            if mode == "semi":
+                H.itokmc_transport_semi_implicit()
+            else:
+                H.itokmc_run_stage(itokmc.STAGE_TRANSPORT)
+                H.itokmc_run_stage(itokmc.STAGE_FIELD)
+            H.itokmc_advance_counter()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cyc = []
+        for _ in range(K):
+            if mode == "semi":
+                cyc.append(H.itokmc_transport_semi_implicit()[0])
+            else:
+                H.itokmc_run_stage(itokmc.STAGE_TRANSPORT)
+                H.itokmc_run_stage(itokmc.STAGE_FIELD)
+                cyc.append(H.itokmc_get_stats()["mg_cycles"])
+            H.itokmc_advance_counter()
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0) / K
+        out[mode] = {"ms_per_transport_and_field": ms, "mg_cycles": cyc,
+                     "particle_steps_per_s": H.itokmc_num_particles() / (ms / 1e3)}
+    H.close()
+    print(json.dumps(out), flush=True)
+
+
 def small_study(args):
     """The plain FP64 configuration in full: 64^3 over a 1 cm cube, 1.5 MV/m,
     a Gaussian blob (sigma 0.5 mm, peak 1e18 m^-3 at 0.8 L) sampled at ppc 8
@@ -568,7 +613,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default smoother counts (2, 2)")
-    ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small"],
+    ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small", "semi"],
                     help="instead of the benchmark: the FP32-vs-FP64 precision study")
     ap.add_argument("--study-steps", type=int, default=None,
                     help="steps of a study (default: precision 20, small 10, ensemble 5)")
@@ -578,7 +623,7 @@ def main():
     if args.n is None:
         args.n = 128 if args.study == "ensemble" else 256
     if args.study_steps is None:
-        args.study_steps = {"ensemble": 5, "small": 10}.get(args.study, 20)
+        args.study_steps = {"ensemble": 5, "small": 10, "semi": 3}.get(args.study, 20)
     if args.study == "precision":
         precision_study(args)
         return
@@ -587,6 +632,9 @@ def main():
         return
     if args.study == "small":
         small_study(args)
+        return
+    if args.study == "semi":
+        semi_study(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

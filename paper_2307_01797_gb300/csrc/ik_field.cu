@@ -684,18 +684,38 @@ __global__ void k_coef_restrict(const double* __restrict__ cf, double* __restric
 }
 
 // Squared norms of the residual and of the right-hand side per realization
-// (atomic sums: only the convergence test reads them).
-__global__ void k_resid_norm_vc(const double* __restrict__ phi, const double* __restrict__ rhs,
-                                const double* __restrict__ c, Geo G, double* __restrict__ acc)
+// (blockIdx.y): block sums, one atomic add per block (only the convergence
+// test reads them).  256 threads per block.
+__global__ void __launch_bounds__(256) k_resid_norm_vc(const double* __restrict__ phi, const double* __restrict__ rhs,
+                                                       const double* __restrict__ c, Geo G, double* __restrict__ acc)
 {
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G.cells; t += (uint64_t)gridDim.x * blockDim.x) {
-        int r, k, j, i;
-        decode(t, G.log2n, r, k, j, i);
+    const uint64_t r = blockIdx.y;
+    const uint64_t per = (uint64_t)G.n * G.n * G.n;
+    double s0 = 0.0, s1 = 0.0;
+    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < per; u += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t t = r * per + u;
+        int rr, k, j, i;
+        decode(t, G.log2n, rr, k, j, i);
         double d;
         const double sum = vc_nbr(phi, c, t, G.n, i, j, k, d);
         const double res = rhs[t] - (sum - d * phi[t]);
-        atomicAdd(acc + 2 * r, res * res);
-        atomicAdd(acc + 2 * r + 1, rhs[t] * rhs[t]);
+        s0 += res * res;
+        s1 += rhs[t] * rhs[t];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    __shared__ double w0[8], w1[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { w0[wid] = s0; w1[wid] = s1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += w0[q]; b += w1[q]; }
+        atomicAdd(acc + 2 * r, a);
+        atomicAdd(acc + 2 * r + 1, b);
     }
 }
 
@@ -1031,7 +1051,9 @@ int field_solve_vc(const Params& P, Dev& d, double* const* c, double* acc, doubl
     for (cyc = 0; cyc <= max_cycles; ++cyc) {
         cudaMemsetAsync(acc, 0, 2 * R * sizeof(double), s);
         ++g_launches;
-        k_resid_norm_vc<<<gridsz(G0.cells, tpb), tpb, 0, s>>>(d.lev[0].phi, d.lev[0].rhs, c[0], G0, acc);
+        const uint64_t per = G0.cells / (uint64_t)R;
+        const dim3 ng((unsigned)gridsz(per, tpb), (unsigned)R);
+        k_resid_norm_vc<<<ng, tpb, 0, s>>>(d.lev[0].phi, d.lev[0].rhs, c[0], G0, acc);
         cudaMemcpyAsync(acc_host, acc, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
         worst = 0.0;
