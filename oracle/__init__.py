@@ -118,6 +118,8 @@ def lib():
             L.ora_merge_list.restype = i64
             L.ora_photon_samples.argtypes = [pp, i32, i32, i32, i64, pd, pd, pd, pd]
             L.ora_cells.argtypes = [pp, i64, pd, pd, pd, pi64]
+            L.ora_grid_axis.argtypes = [pp, i32, i64, pd, pd, pi64, pi64, pi64, pd, pi64]
+            L.ora_interp_points.argtypes = [pp, pd, i64, pd, pd, pd, pd]
             _lib = L
     return _lib
 
@@ -185,6 +187,32 @@ def cells(params: Params, x, y, z):
     out = np.empty(len(x), np.int64)
     lib().ora_cells(ctypes.byref(params), len(x), _P(x, ctypes.c_double), _P(y, ctypes.c_double),
                     _P(z, ctypes.c_double), _P(out, ctypes.c_int64))
+    return out
+
+
+def grid_axis(params: Params, ax: int, x):
+    """Grid arithmetic of one axis at coordinates x: dict(q, cell, ia, ib, f, a)
+    (quotient (x-lo)/h, cell, folded CIC indices, CIC fraction, fixed-point
+    deposit weight floor(f 2^s))."""
+    x = np.ascontiguousarray(x, np.float64)
+    n = len(x)
+    q = np.empty(n); f = np.empty(n)
+    cell = np.empty(n, np.int64); ia = np.empty(n, np.int64); ib = np.empty(n, np.int64); a = np.empty(n, np.int64)
+    lib().ora_grid_axis(ctypes.byref(params), int(ax), n, _P(x, ctypes.c_double), _P(q, ctypes.c_double),
+                        _P(cell, ctypes.c_int64), _P(ia, ctypes.c_int64), _P(ib, ctypes.c_int64),
+                        _P(f, ctypes.c_double), _P(a, ctypes.c_int64))
+    return dict(q=q, cell=cell, ia=ia, ib=ib, f=f, a=a)
+
+
+def interp_points(params: Params, F, x, y, z):
+    """CIC interpolation of the cell-centred scalar field F (n^3, x fastest)
+    at the points (x, y, z), as the push interpolates each component of E."""
+    F = np.ascontiguousarray(F, np.float64).ravel()
+    x = np.ascontiguousarray(x, np.float64); y = np.ascontiguousarray(y, np.float64)
+    z = np.ascontiguousarray(z, np.float64)
+    out = np.empty(len(x))
+    lib().ora_interp_points(ctypes.byref(params), _P(F, ctypes.c_double), len(x), _P(x, ctypes.c_double),
+                            _P(y, ctypes.c_double), _P(z, ctypes.c_double), _P(out, ctypes.c_double))
     return out
 
 

@@ -1147,3 +1147,37 @@ void ora_cells(const ora_params* p, int64_t np, const double* x, const double* y
         cell[i] = inside(p, X) ? lin(p, cell_axis(p, 0, X[0]), cell_axis(p, 1, X[1]), cell_axis(p, 2, X[2])) : -1;
     }
 }
+
+/* Exported for the pins of the grid arithmetic (no step calls it): for each */
+/* coordinate x on axis ax, the quotient q = (x-lo)/h as grid_quot forms it, */
+/* the cell of cell_axis, the folded CIC indices (ia, ib) and fraction f of  */
+/* cic_axis, and the deposit's fixed-point weight a = floor(f 2^s).          */
+void ora_grid_axis(const ora_params* p, int32_t ax, int64_t np, const double* x, double* q, int64_t* cell,
+                   int64_t* ia, int64_t* ib, double* f, int64_t* a)
+{
+    double scale = (double)((int64_t)1 << p->frac_bits);
+    for (int64_t i = 0; i < np; ++i) {
+        int ja, jb;
+        double fv;
+        q[i] = grid_quot(p, ax, x[i]);
+        cell[i] = cell_axis(p, ax, x[i]);
+        cic_axis(p, ax, x[i], &ja, &jb, &fv);
+        ia[i] = ja; ib[i] = jb; f[i] = fv;
+        a[i] = (int64_t)floor(fv * scale);
+    }
+}
+
+/* Exported for the pins of the interpolation (no step calls it): the CIC    */
+/* interpolation of one cell-centred scalar field F at each point, exactly   */
+/* as ora_push interpolates each component of E.                             */
+void ora_interp_points(const ora_params* p, const double* F, int64_t np, const double* x, const double* y,
+                       const double* z, double* out)
+{
+    for (int64_t i = 0; i < np; ++i) {
+        double X[3] = { x[i], y[i], z[i] };
+        int ia[3], ib[3];
+        double f[3];
+        for (int ax = 0; ax < 3; ++ax) cic_axis(p, ax, X[ax], &ia[ax], &ib[ax], &f[ax]);
+        out[i] = interp(p, F, ia, ib, f);
+    }
+}
