@@ -32,18 +32,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # DRAM bytes per particle of the transport stage (push, transport scans,
-# scatter, mover kernels) in one step of the 256^3 streamer, from an ncu launch
-# list of that workload, keyed by "FP64 form": the push and the scatter each
-# read and write every record, so the stage moves about twice the
-# algorithmic bytes.
-TRANSPORT_DRAM_PER_PARTICLE = {True: 10.963e9 / 75505333, False: 7.080e9 / 75504496}
+# scatter, mover kernels): dram__bytes_read.sum + dram__bytes_write.sum of
+# those kernels in one ncu capture of the streamer workload at 128^3
+# (1.0e7 particles, the same kernels as the timed run), divided by the
+# particles of the captured step, keyed by "FP64 form"; scaled to the timed
+# run by its particle count (the stage's traffic grows in proportion: every
+# kernel streams the records or the per-cell arrays once or twice).
+TRANSPORT_DRAM_PER_PARTICLE = {True: None, False: None}
 # FP64 arithmetic of the FP64 push per particle (ncu thread-instruction counts
 # of DADD, DMUL and DFMA over a launch, divided by its particles; an FMA
-# counts as two operations) and GB300's FP64 peak: 152 SMs x 2 FP64 FMA lanes
-# per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak 304 per
-# cycle over the GPU) x 2 FLOP x 2.07 GHz.
+# counts as two operations).  The peak it is set against is measured in the
+# run (itokmc_probe_fp64_peak: register-resident FMA chains on every SM).
 FP64_FLOP_PER_PARTICLE = 123.0
-FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 
 METRIC = "particle-steps/s (push+sort+deposit+KMC), HBM roofline %; FP32 vs FP64 at stated err"
 
@@ -257,7 +257,7 @@ def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e)
     # measured DRAM bytes of the same stage (dram__bytes_read.sum +
     # dram__bytes_write.sum of its kernels in one ncu launch list of this
     # workload at 256^3), per step at the timed mean particle count
-    tpp = TRANSPORT_DRAM_PER_PARTICLE[form == itokmc.FP64] if (args.n == 256 and args.particles == 1e8) else None
+    tpp = TRANSPORT_DRAM_PER_PARTICLE[form == itokmc.FP64]
     traffic = tpp * processed / args.steps if tpp else None
     out = {"value": processed_all / (ms / 1e3), "ms_per_step": ms / args.steps,
            "push_sort_deposit_kmc_rate": processed / (core_ms / 1e3),
@@ -332,6 +332,7 @@ def our_arm(args, rank, world):
                          "push+sort+deposit+KMC on the full grid, single-threaded C oracle"}
     P = res[forms[0]]
     pk, pk_kind = peaks()
+    fp64_peak, _ = itokmc.itokmc_probe_fp64_peak(torch.cuda.current_stream().cuda_stream)
     line = {
         "metric": METRIC, "value": P["value"], "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": P["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -342,20 +343,24 @@ def our_arm(args, rank, world):
         "stage_ms_per_step": P["stage_ms_per_step"], "movers_per_step": P["movers_per_step"],
         "mg_cycles": P["mg_cycles"], "mg_smoothing": P["mg_smoothing"], "particles_per_step": P["particles_per_step"],
         "last_step_counters": P["last_step_counters"],
-        "roofline": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)",
-                     "achieved": P["transport_achieved_gbs"], "peak": pk, "peak_kind": pk_kind, "unit": "GB/s",
-                     "frac": P["transport_achieved_gbs"] / pk, "traffic": P["traffic"],
-                     "bytes_per_particle": P["bytes_per_particle"], "traffic_per_particle": P["traffic_per_particle"]},
+        "roofline_hbm": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)",
+                         "achieved": P["transport_achieved_gbs"], "peak": pk, "peak_kind": pk_kind, "unit": "GB/s",
+                         "frac": P["transport_achieved_gbs"] / pk, "traffic": P["traffic"],
+                         "bytes_per_particle": P["bytes_per_particle"],
+                         "traffic_per_particle": P["traffic_per_particle"]},
         "cpu_baseline": cpu, "e2e": P.get("e2e"), "gpu_launches": P["gpu_launches"], "clocks": P["clocks"],
     }
     if forms[0] == itokmc.FP64:
-        # the FP64 transport is bound by GB300's FP64 units, not by HBM
+        # the FP64 transport is bound by GB300's FP64 units, not by HBM: its
+        # roofline is the FP64 arithmetic rate (measured above)
         t_tr = P["stage_ms_per_step"]["transport"] / 1e3
         ach = FP64_FLOP_PER_PARTICLE * (sum(P["particles_per_step"]) / len(P["particles_per_step"])) / t_tr / 1e12
-        line["roofline_fp64"] = {"bound": "alu", "kernel": "transport stage (push+sort+deposit), FP64 arithmetic",
-                                 "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                 "frac": ach / FP64_PEAK_TFLOPS, "flop_per_particle": FP64_FLOP_PER_PARTICLE,
-                                 "peak_kind": "derived (unit counts x clock)"}
+        line["roofline"] = {"bound": "alu", "kernel": "transport stage (push+sort+deposit), FP64 arithmetic",
+                            "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                            "traffic": P["traffic"], "flop_per_particle": FP64_FLOP_PER_PARTICLE,
+                            "peak_kind": "measured (FP64 FMA loop, itokmc_probe_fp64_peak)"}
+    else:
+        line["roofline"] = line["roofline_hbm"]
     if len(forms) > 1:
         M = res[itokmc.MIXED]
         line["mixed_form"] = {
@@ -528,6 +533,62 @@ def semi_study(args):
     print(json.dumps(out), flush=True)
 
 
+def transport_study(args):
+    """The transport stage alone (push, sort, deposit: the roofline's subject)
+    on the streamer workload, or on a count-pinned uniform z-slab
+    (--slab: ``--particles`` particles uniform in z in [0.4 L, 0.6 L), weight
+    100, on the streamer physics of the chosen grid), each form: W untimed
+    stages, then K stages timed by CUDA events on the library's stream
+    (itokmc_get_stats ms_transport).  --dt-scale multiplies dt (the sort stress
+    case: at x100 a particle moves about one cell per step)."""
+    import torch
+    from paper_2307_01797_gb300 import itokmc, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ph = synth.physics_streamer(args.n) if args.physics == "streamer" else synth.physics_tree(args.n)
+    ph["dt"] *= args.dt_scale
+    if args.slab:
+        st = synth.uniform_slab_state(ph, int(args.particles), seed=1)
+        ions = None
+    else:
+        st = synth.streamer_tree_state(ph, int(args.particles), seed=7)
+        ions = synth.streamer_ions(ph, st, seed=8)
+    N0 = len(st["w"])
+    pk, pk_kind = peaks()
+    forms = {"fp64": [itokmc.FP64], "mixed": [itokmc.MIXED], "both": [itokmc.FP64, itokmc.MIXED]}[args.form]
+    out = {"study": "transport", "grid": args.n, "physics": args.physics, "slab": bool(args.slab),
+           "dt": ph["dt"], "particles": N0, "forms": {}}
+    for form in forms:
+        H = itokmc.Handle(itokmc.make_config(ph, int(1.3 * N0) + 1_000_000, seed0=1, precision=form))
+        H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+        if ions is not None:
+            H.itokmc_set_ions(*ions)
+        H.itokmc_solve_field()
+        for _ in range(args.warmup):
+            H.itokmc_run_stage(itokmc.STAGE_TRANSPORT)
+            H.itokmc_advance_counter()
+        ms, npart, movers = [], [], []
+        for _ in range(args.steps):
+            npart.append(H.itokmc_num_particles())
+            H.itokmc_run_stage(itokmc.STAGE_TRANSPORT)
+            H.itokmc_advance_counter()
+            s = H.itokmc_get_stats()
+            ms.append(s["ms_transport"])
+            movers.append(s["n_movers"])
+        H.close()
+        fp64 = form == itokmc.FP64
+        bpp = 2 * (32 if fp64 else 20) + ((24 + 8 + 8) if fp64 else (12 + 8 + 8)) / ph["ppc"]
+        med = statistics.median(ms)
+        n_avg = sum(npart) / len(npart)
+        gbs = n_avg * bpp / (med / 1e3) / 1e9
+        tpp = TRANSPORT_DRAM_PER_PARTICLE[fp64]
+        out["forms"]["fp64" if fp64 else "mixed"] = {
+            "ms_median": med, "ms": ms, "particles": npart, "movers_per_stage": sum(movers) / len(movers),
+            "bytes_per_particle": bpp, "achieved_gbs": gbs, "frac_hbm": gbs / pk, "peak_gbs": pk, "peak_kind": pk_kind,
+            "particles_per_s": n_avg / (med / 1e3),
+            "traffic_per_particle": tpp, "traffic": tpp * n_avg if tpp else None}
+    print(json.dumps(out), flush=True)
+
+
 def small_study(args):
     """The plain FP64 configuration in full: 64^3 over a 1 cm cube, 1.5 MV/m,
     a Gaussian blob (sigma 0.5 mm, peak 1e18 m^-3 at 0.8 L) sampled at ppc 8
@@ -613,8 +674,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default smoother counts (2, 2)")
-    ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small", "semi"],
-                    help="instead of the benchmark: the FP32-vs-FP64 precision study")
+    ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small", "semi", "transport"],
+                    help="instead of the benchmark: one of the studies (see each function's docstring)")
+    ap.add_argument("--slab", action="store_true", help="transport study: count-pinned uniform z-slab")
+    ap.add_argument("--physics", default="streamer", choices=["streamer", "tree"],
+                    help="transport study: streamer (2 cm, ppc 32) or discharge-tree physics (4 cm, ppc 64)")
+    ap.add_argument("--dt-scale", type=float, default=1.0, help="transport study: dt multiplier (sort stress)")
     ap.add_argument("--study-steps", type=int, default=None,
                     help="steps of a study (default: precision 20, small 10, ensemble 5)")
     ap.add_argument("--members", type=int, default=64)
@@ -635,6 +700,9 @@ def main():
         return
     if args.study == "semi":
         semi_study(args)
+        return
+    if args.study == "transport":
+        transport_study(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -148,7 +148,15 @@ int itokmc_config_defaults(itokmc_config* cfg);
 
 /* Validates *cfg, allocates all device state for n_realizations x n^3 cells
  * and particle_capacity particles, zeroes it, and returns the handle in
- * *out.  No particles exist yet.  Errors: ERR_ARG (bad config), ERR_OOM. */
+ * *out.  No particles exist yet.  The configuration is the problem of Sec. 4
+ * (Eq. ito_poisson): the electron drift-diffusion coefficients (mu, D) of
+ * Eq. ito_kernel with v = -mu E (Eq. Vk1), the first-order network of Sec.
+ * 3.2 and Table air_reactions restricted to ionization, attachment and
+ * photon emission (alpha(E), eta, k_gamma), the photon absorption range of
+ * Sec. 5.1, the Cao et al. parameters N_c, N_SSA, eps of Sec. 3.2.3, the
+ * particle budget of Sec. 4.4 (N_new) and Sec. 4.6 (ppc), and the electrode
+ * and side boundary conditions of Sec. 5.1.  Errors: ERR_ARG (bad config),
+ * ERR_OOM. */
 int itokmc_init(const itokmc_config* cfg, itokmc_handle** out);
 
 /* Releases all device memory of the handle.  Always safe on a poisoned
@@ -158,8 +166,11 @@ int itokmc_destroy(itokmc_handle* h);
 /* Replaces all particles.  x, y, z (double), w (uint32 weights = physical
  * electrons, >= 1) and realization (int32, may be NULL when R = 1) hold n
  * particles in any order, in host (mem = ITOKMC_HOST) or device memory.
- * Particles are stably sorted by (realization, cell); particles outside
- * [lo, hi) are rejected with ERR_ARG.  ERR_CAPACITY if n > capacity. */
+ * These are the computational particles of Sec. 3.1 (position X_p, integer
+ * weight w_p: the number of physical electrons a superparticle stands for,
+ * Sec. 4.4).  Particles are stably sorted by (realization, cell), the
+ * binning of Sec. 5.6; particles outside [lo, hi) are rejected with ERR_ARG.
+ * ERR_CAPACITY if n > capacity. */
 int itokmc_set_particles(itokmc_handle* h, const double* x, const double* y, const double* z,
                          const uint32_t* w, const int32_t* realization, int64_t n, int32_t mem);
 
@@ -184,8 +195,13 @@ int itokmc_set_field(itokmc_handle* h, const double* E, int32_t mem);
  * multigrid stops at mg_max_cycles above tolerance. */
 int itokmc_solve_field(itokmc_handle* h);
 
-/* Advances nsteps full steps (a1-a9 then a5).  Errors: ERR_CAPACITY,
- * ERR_OVERFLOW, ERR_NOCONV, ERR_KMC, ERR_CUDA. */
+/* Advances nsteps full steps (a1-a9 then a5): the time step of Sec. 4.7 in
+ * its explicit form -- particle transport by Eq. ito_kernel with the
+ * Euler-Maruyama update of Sec. 4.3 (first equation), deposition (Sec. 4.2),
+ * per-cell KMC (Sec. 3.2.3), products (Sec. 4.4), photoionization (Sec.
+ * 4.5), merge/split (Sec. 4.6) and the Poisson solve (Sec. 4.3) for the
+ * next step's field.  Errors: ERR_CAPACITY, ERR_OVERFLOW, ERR_NOCONV,
+ * ERR_KMC, ERR_CUDA. */
 int itokmc_step(itokmc_handle* h, int32_t nsteps);
 
 /* Runs one stage (ITOKMC_STAGE_*) on the current state without advancing
@@ -240,7 +256,11 @@ int itokmc_autotune(itokmc_handle* h, itokmc_tuning* out);
 
 /* Copies one field (ITOKMC_NE_FIX ...) of realization r (or all
  * realizations when r = -1) into host_out of the given size in bytes.
- * ERR_ARG if bytes is too small.  Synchronises the stream. */
+ * The densities are the mesh quantities of Sec. 4.2: the CIC deposit of the
+ * particle weights (W_cic, in fixed point), the per-cell electron and ion
+ * counts X_e, N+, N- of the KMC state (Sec. 3.2, Eq. kmc), the space charge
+ * rho of Eq. poisson, and phi and E = -grad phi (Sec. 4.3).  ERR_ARG if
+ * bytes is too small.  Synchronises the stream. */
 int itokmc_read_densities(itokmc_handle* h, int32_t realization, int32_t which, void* host_out,
                           size_t bytes);
 
@@ -257,6 +277,19 @@ const char* itokmc_last_error(const itokmc_handle* h);
 /* Library version string. */
 const char* itokmc_version(void);
 
+/* ---- measurement --------------------------------------------------------
+ * The FP64 form is bound by the device's FP64 units (the interpolation,
+ * push and quotient arithmetic of Sec. 4.2-4.3 in double precision), so its
+ * roofline is taken against the FP64 arithmetic rate.  This call measures
+ * that rate: 8 blocks of 256 threads per SM, each thread 8 independent
+ * chains of 4096 fused multiply-adds in registers (2 FLOP each), best of
+ * three timed launches on `stream` (a cudaStream_t, or NULL).  Allocates
+ * 64 KB of device memory for the duration of the call.
+ *   tflops_out  measured FP64 TFLOP/s;  ms_out (may be NULL) the best time.
+ * Returns ITOKMC_OK, ITOKMC_ERR_ARG, ITOKMC_ERR_OOM or ITOKMC_ERR_CUDA (the
+ * message in itokmc_last_error(NULL)).  Synchronises the stream. */
+int itokmc_probe_fp64_peak(void* stream, double* tflops_out, double* ms_out);
+
 /* ---- field solve without device allocation ------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc -- for instance a program whose device memory is
@@ -269,15 +302,23 @@ const char* itokmc_version(void);
  * exits, so grids are limited to ITOKMC_NOALLOC_MAX_N cells per axis.
  *
  *   cfg     grid (n, lo, hi; one realization), E0, frac_bits, mg_rtol,
- *           mg_nu1/nu2, mg_max_cycles, precision/field_precision (FP64 or
- *           MIXED) and stream; particle and allocator fields are ignored.
+ *           mg_nu1/nu2, mg_max_cycles, precision/field_precision and
+ *           stream; particle and allocator fields are ignored.  The field
+ *           form is field_precision, or precision when that is -1:
+ *           ITOKMC_FP64 runs FP64 V-cycles; ITOKMC_MIXED runs FP32 V-cycles
+ *           inside FP64 residual refinement (an FP64 potential, not the
+ *           fixed-point potential a handle of the mixed form keeps).  Any
+ *           other value is ITOKMC_ERR_ARG before anything is launched.
+ *           The V-cycles are launched directly on the stream (no graph is
+ *           captured or instantiated).
  *   rho     device, int64 n^3: space charge in units of q_e 2^-3s per cell
  *           (the ITOKMC_RHO layout).
  *   phi     device, double n^3: initial guess on entry, potential on exit.
  *   E       device, double 3 n^3: Ex, Ey, Ez blocks on exit.
  *   cycles_out, rel_out  optional: V-cycles used, final ||r||/||b||.
  * Returns ITOKMC_OK, ITOKMC_ERR_ARG (NULL pointer, R != 1, n not a power of
- * two or n > ITOKMC_NOALLOC_MAX_N), ITOKMC_ERR_NOCONV or ITOKMC_ERR_CUDA;
+ * two, n > ITOKMC_NOALLOC_MAX_N, or an unknown precision), ITOKMC_ERR_NOCONV
+ * or ITOKMC_ERR_CUDA;
  * the message is in itokmc_last_error(NULL).  The first call on a device
  * looks up the scratch array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  All calls share the one

@@ -379,6 +379,8 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     if (cfg->n_ssa < 1 || cfg->n_crit < 0) return fail(nullptr, ITOKMC_ERR_ARG, "n_ssa, n_crit");
     if (cfg->precision != ITOKMC_FP64 && cfg->precision != ITOKMC_MIXED)
         return fail(nullptr, ITOKMC_ERR_ARG, "precision");
+    if (cfg->field_precision != -1 && cfg->field_precision != ITOKMC_FP64 && cfg->field_precision != ITOKMC_MIXED)
+        return fail(nullptr, ITOKMC_ERR_ARG, "field_precision: -1, ITOKMC_FP64 or ITOKMC_MIXED");
     if (cfg->particle_capacity < 1 || cfg->particle_capacity > 0x7fff0000ll)
         return fail(nullptr, ITOKMC_ERR_ARG, "particle_capacity in [1, 2^31)");
     if (cfg->photon_ratio > 0 && !(cfg->kappa_hi >= cfg->kappa_lo && cfg->kappa_lo > 0))

@@ -684,10 +684,12 @@ __global__ void k_coef_restrict(const double* __restrict__ cf, double* __restric
 }
 
 // Squared norms of the residual and of the right-hand side per realization
-// (blockIdx.y): block sums, one atomic add per block (only the convergence
-// test reads them).  256 threads per block.
+// (blockIdx.y): one partial pair per block in part[2 (r gridDim.x + x)],
+// summed in a fixed order by k_norm_final, so the convergence test (and with
+// it the cycle count and the potential) is the same on every run.  256
+// threads per block.
 __global__ void __launch_bounds__(256) k_resid_norm_vc(const double* __restrict__ phi, const double* __restrict__ rhs,
-                                                       const double* __restrict__ c, Geo G, double* __restrict__ acc)
+                                                       const double* __restrict__ c, Geo G, double* __restrict__ part)
 {
     const uint64_t r = blockIdx.y;
     const uint64_t per = (uint64_t)G.n * G.n * G.n;
@@ -714,8 +716,9 @@ __global__ void __launch_bounds__(256) k_resid_norm_vc(const double* __restrict_
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += w0[q]; b += w1[q]; }
-        atomicAdd(acc + 2 * r, a);
-        atomicAdd(acc + 2 * r + 1, b);
+        const uint64_t o = 2 * (r * gridDim.x + blockIdx.x);
+        part[o] = a;
+        part[o + 1] = b;
     }
 }
 
@@ -753,7 +756,8 @@ constexpr int MAX_REAL_NORM = 4096;
 // k = 0: one FP64 V-cycle; k = 1: zero the FP32 correction, two FP32
 // V-cycles.  The launches of a cycle depend only on the level pointers and
 // the smoother counts, so one capture per (nu1, nu2) serves every solve.
-// Falls back to direct launches if capture is not possible.
+// Launches directly when d.direct_cycles is set (a solve on per-call
+// buffers, whose graphs could not be reused) or capture is not possible.
 void run_cycles(Dev& d, int k, int R, int nu1, int nu2, cudaStream_t s)
 {
     auto direct = [&]() {
@@ -767,6 +771,10 @@ void run_cycles(Dev& d, int k, int R, int nu1, int nu2, cudaStream_t s)
             vcycle<float>(d, 0, R, nu1, nu2, s);
         }
     };
+    if (d.direct_cycles) {
+        direct();
+        return;
+    }
     if (d.vgraph[k] && (d.vgraph_nu[k][0] != nu1 || d.vgraph_nu[k][1] != nu2)) {
         cudaGraphExecDestroy(d.vgraph[k]);
         d.vgraph[k] = nullptr;
@@ -1049,11 +1057,11 @@ int field_solve_vc(const Params& P, Dev& d, double* const* c, double* acc, doubl
     int cyc = 0, status = -6;
     double worst = 0.0;
     for (cyc = 0; cyc <= max_cycles; ++cyc) {
-        cudaMemsetAsync(acc, 0, 2 * R * sizeof(double), s);
-        ++g_launches;
+        g_launches += 2;
         const uint64_t per = G0.cells / (uint64_t)R;
         const dim3 ng((unsigned)gridsz(per, tpb), (unsigned)R);
-        k_resid_norm_vc<<<ng, tpb, 0, s>>>(d.lev[0].phi, d.lev[0].rhs, c[0], G0, acc);
+        k_resid_norm_vc<<<ng, tpb, 0, s>>>(d.lev[0].phi, d.lev[0].rhs, c[0], G0, d.norm_part);
+        k_norm_final<<<R, 256, 0, s>>>(d.norm_part, (int)ng.x, R, acc);
         cudaMemcpyAsync(acc_host, acc, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
         worst = 0.0;
@@ -1137,7 +1145,14 @@ extern "C" int itokmc_field_solve_noalloc(const itokmc_config* cfg, const int64_
         set_global_error("field_solve_noalloc: grid larger than ITOKMC_NOALLOC_MAX_N (64) cells per axis");
         return ITOKMC_ERR_ARG;
     }
-    const int prec = cfg->field_precision < 0 ? cfg->precision : cfg->field_precision;
+    if ((cfg->precision != ITOKMC_FP64 && cfg->precision != ITOKMC_MIXED) ||
+        (cfg->field_precision != -1 && cfg->field_precision != ITOKMC_FP64 && cfg->field_precision != ITOKMC_MIXED)) {
+        set_global_error("field_solve_noalloc: precision must be ITOKMC_FP64 or ITOKMC_MIXED (field_precision also -1)");
+        return ITOKMC_ERR_ARG;
+    }
+    const int fp = cfg->field_precision < 0 ? cfg->precision : cfg->field_precision;
+    // FP64 V-cycles, or FP32 V-cycles inside FP64 residual refinement
+    const int prec = fp == ITOKMC_MIXED ? 1 : 0;
     cudaStream_t s = (cudaStream_t)cfg->stream;
     // set-up once per device, with that device current: the device address
     // of the scratch array (its name is only a stand-in in host code)
@@ -1173,6 +1188,7 @@ extern "C" int itokmc_field_solve_noalloc(const itokmc_config* cfg, const int64_
     P.E0 = cfg->E0;
     P.frac_bits = cfg->frac_bits;
     Dev d;
+    d.direct_cycles = true;            // no graph objects: nothing is instantiated per call
     size_t off = 0;
     int l = 0;
     for (int m = n; m >= 4 && l < MAX_LEVELS; m >>= 1, ++l) {
@@ -1206,8 +1222,6 @@ extern "C" int itokmc_field_solve_noalloc(const itokmc_config* cfg, const int64_
     double rel = 0.0;
     const int st = field_solve(P, d, prec, cfg->mg_rtol, cfg->mg_nu1, cfg->mg_nu2, 0ull, cfg->mg_max_cycles, s, &cycles,
                                &rel);
-    for (auto& gx : d.vgraph)
-        if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
     if (cycles_out) *cycles_out = cycles;
     if (rel_out) *rel_out = rel;
     if (st == -3) {

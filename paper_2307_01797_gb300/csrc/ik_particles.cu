@@ -229,15 +229,20 @@ constexpr int DEP_WIN = 2048;   // cells of the block's shared deposit window (1
 // blocks whose box is too large or spans realizations add directly.  The
 // window keeps each 64-bit sum as two 32-bit words updated with native 32-bit
 // shared atomics: the low word's atomic returns the old value, from which the
-// carry into the high word follows exactly.  Integer
-// sums: the result does not depend on the order.  All threads of the block
-// must call this.
+// carry into the high word follows exactly.  Integer sums: the result does
+// not depend on the order.  The flush decodes window positions with
+// multiplicative inverses ceil(2^32/e) formed once per block (exact for
+// positions below 2^16).  SINGLE: one realization (no realization bounds).
+// All threads of the block must call this.
+template <bool SINGLE>
 __device__ __forceinline__ void block_deposit(const Params& P, unsigned long long* __restrict__ ne, bool alive, int r,
                                               const Stencil& S, uint32_t w)
 {
-    __shared__ uint32_t wlo[DEP_WIN], whi[DEP_WIN];
+    constexpr int NK = SINGLE ? 6 : 8;
+    __shared__ uint2 win[DEP_WIN];
     __shared__ int wred[TPB / 32][8];
     __shared__ int wfin[8];
+    __shared__ uint32_t wdiv[2];
     const int BIG = 0x7fffffff;
     int v[8];
     if (alive) {
@@ -250,23 +255,31 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
     }
     const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = __reduce_min_sync(0xffffffffu, v[k]);
+    for (int k = 0; k < NK; ++k) v[k] = __reduce_min_sync(0xffffffffu, v[k]);
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) wred[wid][k] = v[k];
+        for (int k = 0; k < NK; ++k) wred[wid][k] = v[k];
     }
     __syncthreads();
-    if (threadIdx.x < 8) {
+    if (wid == 0) {
         int m = BIG;
-        for (int q = 0; q < TPB / 32; ++q) m = min(m, wred[q][threadIdx.x]);
-        wfin[threadIdx.x] = m;
+        if (lane < NK)
+            for (int q = 0; q < TPB / 32; ++q) m = min(m, wred[q][lane]);
+        const int l0 = __shfl_sync(0xffffffffu, m, 0), h0 = __shfl_sync(0xffffffffu, m, 3);
+        const int l1 = __shfl_sync(0xffffffffu, m, 1), h1 = __shfl_sync(0xffffffffu, m, 4);
+        if (lane < NK) wfin[lane] = m;
+        if (lane == 0 && l0 != BIG) {
+            const uint32_t e0 = (uint32_t)(-h0 - l0 + 1), e01 = e0 * (uint32_t)(-h1 - l1 + 1);
+            wdiv[0] = e0 > 1 ? 0xffffffffu / e0 + 1u : 0u;
+            wdiv[1] = e01 > 1 ? 0xffffffffu / e01 + 1u : 0u;
+        }
     }
     __syncthreads();
     if (wfin[0] == BIG) return;                       // no alive particle in the block
     const int lo0 = wfin[0], lo1 = wfin[1], lo2 = wfin[2];
     const int e0 = -wfin[3] - lo0 + 1, e1 = -wfin[4] - lo1 + 1, e2 = -wfin[5] - lo2 + 1;
     const long long V = (long long)e0 * e1 * e2;
-    const bool use = wfin[6] == -wfin[7] && V <= DEP_WIN;
+    const bool use = (SINGLE || wfin[6] == -wfin[7]) && V <= DEP_WIN;
     const int ix[2] = { S.ia[0], S.ib[0] }, iy[2] = { S.ia[1], S.ib[1] }, iz[2] = { S.ia[2], S.ib[2] };
     if (!use) {
         if (alive) {
@@ -283,9 +296,10 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
         }
         return;
     }
-    for (int t = threadIdx.x; t < (int)V; t += TPB) { wlo[t] = 0u; whi[t] = 0u; }
+    for (int t = threadIdx.x; t < (int)V; t += TPB) win[t] = make_uint2(0u, 0u);
     __syncthreads();
     if (alive) {
+        uint32_t* wl = reinterpret_cast<uint32_t*>(win);
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -296,19 +310,26 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
                     if (val) {
                         const int k = ((iz[c] - lo2) * e1 + (iy[b] - lo1)) * e0 + (ix[a] - lo0);
                         const uint32_t lo = (uint32_t)val;
-                        const uint32_t old = atomicAdd(&wlo[k], lo);
-                        const uint32_t hc = (uint32_t)((unsigned long long)val >> 32) + (old + lo < old ? 1u : 0u);
-                        if (hc) atomicAdd(&whi[k], hc);
+                        const uint32_t old = atomicAdd(wl + 2 * k, lo);
+                        const uint32_t hc = (uint32_t)(val >> 32) + (old + lo < old ? 1u : 0u);
+                        if (hc) atomicAdd(wl + 2 * k + 1, hc);
                     }
                 }
     }
     __syncthreads();
-    unsigned long long* base = ne + (size_t)wfin[6] * P.n3;
+    const int rb = SINGLE ? 0 : wfin[6];
+    unsigned long long* base = ne + (size_t)rb * P.n3 + ((size_t)lo2 * P.n + lo1) * P.n + lo0;
+    const uint32_t m0 = wdiv[0], m01 = wdiv[1];
+    const uint32_t e01 = (uint32_t)(e0 * e1);
     for (int t = threadIdx.x; t < (int)V; t += TPB) {
-        const unsigned long long val = ((unsigned long long)whi[t] << 32) | wlo[t];
+        const uint2 q = win[t];
+        const unsigned long long val = ((unsigned long long)q.y << 32) | q.x;
         if (val) {
-            const int x = t % e0, y = (t / e0) % e1, z = t / (e0 * e1);
-            atomicAdd(base + ((size_t)(z + lo2) * P.n + (y + lo1)) * P.n + (x + lo0), val);
+            const uint32_t zq = e01 > 1 ? __umulhi((uint32_t)t, m01) : (uint32_t)t;
+            const uint32_t rem = (uint32_t)t - zq * e01;
+            const uint32_t yq = e0 > 1 ? __umulhi(rem, m0) : rem;
+            const uint32_t xq = rem - yq * (uint32_t)e0;
+            atomicAdd(base + ((size_t)zq * P.n + yq) * P.n + xq, val);
         }
     }
 }
@@ -504,7 +525,7 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f64(
         }
         st_p64(B + i, q);
     }
-    block_deposit(P, ne_fix, alive, rr, S, w);
+    block_deposit<false>(P, ne_fix, alive, rr, S, w);
     unsigned long long v = alive ? (unsigned long long)w : 0ull;
     unsigned c = alive ? 1u : 0u;
     if (warp_run_sum(gnew, alive, v, c)) {
@@ -600,7 +621,7 @@ __global__ void __launch_bounds__(TPB, 4) k_advect_f64(
         }
         st_p64(B + i, q);
     }
-    block_deposit(P, ne_fix, alive, rr, S, w);
+    block_deposit<false>(P, ne_fix, alive, rr, S, w);
     unsigned long long v = alive ? (unsigned long long)w : 0ull;
     unsigned c = alive ? 1u : 0u;
     if (warp_run_sum(gnew, alive, v, c)) {
@@ -1918,6 +1939,10 @@ __device__ __forceinline__ void deposit32(const Params& P, unsigned long long* _
             }
 }
 
+// Pass 1 of the mixed form: interpolation (FP32, cell-relative offsets),
+// push, new cell, fixed-point deposit, per-cell counts.  SINGLE: one
+// realization (Philox key and counter index are kernel-wide).
+template <bool SINGLE>
 __global__ void __launch_bounds__(TPB, 4) k_push_f32(
     Params P, const P32* __restrict__ A, const uint32_t* __restrict__ cA, P32* __restrict__ B,
     uint32_t* __restrict__ keyB, uint32_t N, const uint32_t* __restrict__ cell_start,
@@ -1933,13 +1958,13 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f32(
     if (i < N) {
         const P32 p = A[i];
         const uint32_t gold = __ldg(cA + i);
-        const int r = real_of(P, gold);
+        const int r = SINGLE ? 0 : real_of(P, gold);
         rr = r;
         const uint32_t c = gold & (uint32_t)(P.n3 - 1);
         const int id[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
                             (int)(c >> (2 * P.log2n)) };
-        const uint32_t idx = i - cell_start[(size_t)r * P.n3];
-        const size_t ebase = (size_t)r * P.n3;
+        const uint32_t idx = SINGLE ? i : i - cell_start[(size_t)r * P.n3];
+        const size_t ebase = SINGLE ? 0 : (size_t)r * P.n3;
         w = p.w;
         const float o[3] = { p.ox, p.oy, p.oz };
         int ia[3], ib[3];
@@ -1963,7 +1988,7 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f32(
                 }
         // the FP64 form's stream and words: the same ziggurat decisions, so
         // both forms draw common random numbers (equal to FP32 rounding)
-        PairStream zs(seed_of(P, r), idx, P.step, TAG_PUSH, 0);
+        PairStream zs(SINGLE ? P.seed0 : seed_of(P, r), idx, P.step, TAG_PUSH, 0);
         float nrm[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) nrm[a] = znormal32(zs);
@@ -2004,7 +2029,7 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f32(
             atomicAdd(&ctr->outflow[r], (unsigned long long)w);
         }
     }
-    block_deposit(P, ne_fix, alive, rr, S, w);
+    block_deposit<SINGLE>(P, ne_fix, alive, rr, S, w);
     unsigned long long v = alive ? (unsigned long long)w : 0ull;
     unsigned cc = alive ? 1u : 0u;
     if (warp_run_sum(gnew, alive, v, cc)) {
@@ -2108,11 +2133,11 @@ void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
     const uint32_t nblk = (N + TPB - 1) / TPB;
     if (N == 0) return;
     ++g_launches;
-    if (d.mixed)
-        k_push_f32<<<nblk, TPB, 0, s>>>(P, d.rA32, d.cellA32, d.rB32, d.keyB, N, d.cell_start, d.E32, d.cnt_new,
-                                         d.in_cnt, d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr,
-                                         d.blk_stay);
-    else
+    if (d.mixed) {
+        auto k = P.R == 1 ? k_push_f32<true> : k_push_f32<false>;
+        k<<<nblk, TPB, 0, s>>>(P, d.rA32, d.cellA32, d.rB32, d.keyB, N, d.cell_start, d.E32, d.cnt_new, d.in_cnt,
+                               d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr, d.blk_stay);
+    } else
         k_push_f64<<<nblk, TPB, 0, s>>>(P, d.recA, d.recB, d.keyB, N, d.cell_start, d.E, d.cnt_new, d.in_cnt,
                                          d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr, d.blk_stay);
 }

@@ -130,6 +130,7 @@ struct Dev {
     cudaGraphExec_t vgraph[2] = { nullptr, nullptr };
     int vgraph_nu[2][2] = { { 0, 0 }, { 0, 0 } };
     unsigned long long vgraph_kernels[2] = { 0, 0 };
+    bool direct_cycles = false;        // launch the cycles directly (no capture)
     cudaStream_t side = nullptr;       // merge tiers 1 and 2 run beside tier 0
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
     E64* E_next = nullptr;             // field of the next step, solved while the

@@ -128,6 +128,7 @@ def lib(build_if_missing: bool = True):
                 "itokmc_version": ([], ctypes.c_char_p),
                 "itokmc_field_solve_noalloc": ([ctypes.POINTER(Config), vp, vp, vp, ctypes.POINTER(i32),
                                                 ctypes.POINTER(d)], ctypes.c_int),
+                "itokmc_probe_fp64_peak": ([vp, ctypes.POINTER(d), ctypes.POINTER(d)], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -135,6 +136,14 @@ def lib(build_if_missing: bool = True):
                 f.restype = res
             _lib = L
     return _lib
+
+
+def itokmc_probe_fp64_peak(stream=None):
+    """Measured FP64 FMA rate of the current device: (TFLOP/s, ms)."""
+    t = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(lib().itokmc_probe_fp64_peak(stream, ctypes.byref(t), ctypes.byref(ms)), None)
+    return t.value, ms.value
 
 
 def itokmc_field_solve_noalloc(cfg: Config, rho, phi, E):

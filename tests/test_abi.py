@@ -37,6 +37,18 @@ def test_init_rejects_bad_config_without_touching_the_gpu():
     assert b"power of two" in itokmc.lib().itokmc_last_error(None)
 
 
+@pytest.mark.parametrize("prec,fprec", [(0, 2), (1, 7), (2, -1), (-1, 0)])
+def test_init_rejects_unknown_precision_without_touching_the_gpu(prec, fprec):
+    """Only ITOKMC_FP64 / ITOKMC_MIXED select a form (field_precision also -1:
+    as precision); anything else is refused before any device work."""
+    from paper_2307_01797_gb300 import synth
+    c = itokmc.make_config(synth.physics_small(16), 1000)
+    c.precision, c.field_precision = prec, fprec
+    h = ctypes.c_void_p()
+    assert itokmc.lib().itokmc_init(ctypes.byref(c), ctypes.byref(h)) == -1
+    assert b"precision" in itokmc.lib().itokmc_last_error(None)
+
+
 def test_struct_layout_matches_header():
     src = r'''
 #include <stdio.h>
