@@ -120,6 +120,9 @@ def lib():
             L.ora_cells.argtypes = [pp, i64, pd, pd, pd, pi64]
             L.ora_grid_axis.argtypes = [pp, i32, i64, pd, pd, pi64, pi64, pi64, pd, pi64]
             L.ora_interp_points.argtypes = [pp, pd, i64, pd, pd, pd, pd]
+            pi32 = ctypes.POINTER(i32)
+            L.ora_seed_blobs.argtypes = [pp, i32, pd, pd, pd, pi32, i32, pd, pd, pd, pu32, pi64, pi64, i64]
+            L.ora_seed_blobs.restype = i64
             _lib = L
     return _lib
 
@@ -214,6 +217,28 @@ def interp_points(params: Params, F, x, y, z):
     lib().ora_interp_points(ctypes.byref(params), _P(F, ctypes.c_double), len(x), _P(x, ctypes.c_double),
                             _P(y, ctypes.c_double), _P(z, ctypes.c_double), _P(out, ctypes.c_double))
     return out
+
+
+def seed_blobs(params: Params, blobs, real: int = 0, cap: int = 50_000_000):
+    """Initial electrons of one realization from Gaussian blobs, each blob a
+    dict(center=(x, y, z), sigma, peak, realization=-1): dict(x, y, z, w,
+    cell) in canonical order and counts (electrons per cell)."""
+    nb = len(blobs)
+    C = np.ascontiguousarray([b["center"] for b in blobs], np.float64).reshape(-1)
+    S = np.ascontiguousarray([b["sigma"] for b in blobs], np.float64)
+    A = np.ascontiguousarray([b["peak"] for b in blobs], np.float64)
+    Rb = np.ascontiguousarray([b.get("realization", -1) for b in blobs], np.int32)
+    n3 = params.n ** 3
+    cap = int(min(cap, n3 * params.ppc))
+    x = np.empty(cap); y = np.empty(cap); z = np.empty(cap)
+    w = np.empty(cap, np.uint32); cell = np.empty(cap, np.int64); counts = np.zeros(n3, np.int64)
+    np_ = lib().ora_seed_blobs(ctypes.byref(params), nb, _P(C, ctypes.c_double), _P(S, ctypes.c_double),
+                               _P(A, ctypes.c_double), Rb.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(real),
+                               _P(x, ctypes.c_double), _P(y, ctypes.c_double), _P(z, ctypes.c_double),
+                               _P(w, ctypes.c_uint32), _P(cell, ctypes.c_int64), _P(counts, ctypes.c_int64), cap)
+    if np_ < 0:
+        raise RuntimeError("seed_blobs: " + ("capacity" if np_ == -1 else "weight overflow"))
+    return dict(x=x[:np_], y=y[:np_], z=z[:np_], w=w[:np_], cell=cell[:np_]), counts
 
 
 def canonical(params: Params, st: dict) -> dict:

@@ -1181,3 +1181,63 @@ void ora_interp_points(const ora_params* p, const double* F, int64_t np, const d
         out[i] = interp(p, F, ia, ib, f);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Initial electrons from Gaussian seeds (the initial conditions of Sec.    */
+/* 5.1: electrons, or electron-ion pairs, seeded as Gaussian blobs).  The   */
+/* density at the centre x_c of cell c is n(x_c) = sum_b A_b exp(-|x_c -    */
+/* c_b|^2 / (2 s_b^2)) (squared distance summed x, y, z); the cell receives */
+/* N_c ~ Poisson(n(x_c) dV) electrons, drawn from the stream (index = c,     */
+/* step, INIT, sub 0) with the tau-leap's sampler, carried by m =           */
+/* min(N_c, ppc) superparticles with the weight rule of Eq. w (N_c div m,   */
+/* the remainder on the first), each uniform in the cell: three FP64        */
+/* uniforms from the stream (c, step, INIT, 1 + slot), x = lo + (i + u) h.  */
+/* Blob b seeds the realization real_b (or every one when real_b < 0); the  */
+/* oracle seeds one realization, `real`.  Particles are written in          */
+/* canonical order (cell, slot); counts[c] = N_c.  Returns the particle     */
+/* count, or -1 if cap is exceeded, -2 if a weight exceeds 2^32 - 1.        */
+/* ------------------------------------------------------------------------ */
+int64_t ora_seed_blobs(const ora_params* p, int32_t nb, const double* centers, const double* sigma,
+                       const double* peak, const int32_t* real_of_blob, int32_t real,
+                       double* x, double* y, double* z, uint32_t* w, int64_t* cell, int64_t* counts, int64_t cap)
+{
+    int64_t ncell = (int64_t)p->n * p->n * p->n;
+    double h[3] = { cell_h(p, 0), cell_h(p, 1), cell_h(p, 2) };
+    double dV = (h[0] * h[1]) * h[2];
+    int64_t np = 0;
+    for (int64_t c = 0; c < ncell; ++c) {
+        int ijk[3] = { (int)(c % p->n), (int)((c / p->n) % p->n), (int)(c / ((int64_t)p->n * p->n)) };
+        double xc[3];
+        for (int ax = 0; ax < 3; ++ax) xc[ax] = p->lo[ax] + ((double)ijk[ax] + 0.5) * h[ax];
+        double dens = 0.0;
+        for (int32_t b = 0; b < nb; ++b) {
+            if (real_of_blob[b] >= 0 && real_of_blob[b] != real) continue;
+            double d0 = xc[0] - centers[3 * b], d1 = xc[1] - centers[3 * b + 1], d2 = xc[2] - centers[3 * b + 2];
+            double r2 = (d0 * d0 + d1 * d1) + d2 * d2;
+            dens = dens + peak[b] * ora_exp(-r2 / (2.0 * sigma[b] * sigma[b]));
+        }
+        ora_stream s;
+        stream_init(&s, p->seed, (uint32_t)c, p->step, TAG_INIT, 0);
+        int64_t N = ora_poisson(&s, dens * dV);
+        counts[c] = N;
+        if (N <= 0) continue;
+        int64_t m = N < p->ppc ? N : p->ppc;
+        int64_t wq = N / m, rem = N % m;
+        if (wq + rem > 0xffffffffll) return -2;
+        for (int64_t j = 0; j < m; ++j) {
+            if (np >= cap) return -1;
+            ora_stream t;
+            stream_init(&t, p->seed, (uint32_t)c, p->step, TAG_INIT, (uint32_t)(1 + j));
+            double P[3];
+            for (int ax = 0; ax < 3; ++ax) {
+                double u = stream_uniform(&t);
+                P[ax] = p->lo[ax] + ((double)ijk[ax] + u) * h[ax];
+            }
+            x[np] = P[0]; y[np] = P[1]; z[np] = P[2];
+            w[np] = (uint32_t)(wq + (j == 0 ? rem : 0));
+            cell[np] = c;
+            np += 1;
+        }
+    }
+    return np;
+}
