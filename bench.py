@@ -38,7 +38,10 @@ sys.path.insert(0, ROOT)
 # particles of the captured step, keyed by "FP64 form"; scaled to the timed
 # run by its particle count (the stage's traffic grows in proportion: every
 # kernel streams the records or the per-cell arrays once or twice).
-TRANSPORT_DRAM_PER_PARTICLE = {True: None, False: None}
+# Captured: FP64 1.398 GB, mixed 0.856 GB for 9.97e6 particles (the
+# cudaMemsetAsync zeroing of five per-cell arrays, about 6 B per particle
+# at this density, is not a kernel and is not in the figure).
+TRANSPORT_DRAM_PER_PARTICLE = {True: 140.2, False: 85.8}
 # FP64 arithmetic of the FP64 push per particle (ncu thread-instruction counts
 # of DADD, DMUL and DFMA over a launch, divided by its particles; an FMA
 # counts as two operations).  The peak it is set against is measured in the
@@ -589,6 +592,64 @@ def transport_study(args):
     print(json.dumps(out), flush=True)
 
 
+def tree_study(args):
+    """The discharge-tree configuration: 512^3 cells over a 4 cm cube, 1.8 MV/m,
+    dt 5 ps, ppc 64, photoionization on; four Gaussian electron seeds (sigma
+    0.3 mm, peak 5e18 m^-3) at (L/2 +- 5 mm, L/2 +- 5 mm, 0.9 L) sampled on
+    the device (itokmc_init with blobs); the mixed form (FP32 particles,
+    fixed-point potential with FP32 V-cycles); K full steps after W, with the
+    particle count per step and the transport stage's HBM roofline."""
+    import torch
+    from paper_2307_01797_gb300 import itokmc, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ph = synth.physics_tree(args.n)
+    L = ph["hi"][0] - ph["lo"][0]
+    blobs = [dict(center=(L / 2 + sx * 5e-3, L / 2 + sy * 5e-3, 0.9 * L), sigma=3e-4, peak=5e18)
+             for sx in (-1, 1) for sy in (-1, 1)]
+    form = {"fp64": itokmc.FP64, "mixed": itokmc.MIXED}[args.form if args.form != "both" else "mixed"]
+    cfg = itokmc.make_config(ph, int(args.particles), seed0=1, precision=form)
+    arr = itokmc.blob_array(blobs)
+    cfg.blobs = itokmc.ctypes.cast(arr, itokmc.ctypes.c_void_p)
+    cfg.n_blobs = len(blobs)
+    t0 = time.perf_counter()
+    H = itokmc.Handle(cfg)
+    torch.cuda.synchronize()
+    t_init = time.perf_counter() - t0
+    N0 = H.itokmc_num_particles()
+    tune = H.itokmc_autotune()
+    for _ in range(args.warmup):
+        H.itokmc_step(1)
+    pk, pk_kind = peaks()
+    counts, ms, tr, mg = [], [], [], []
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        counts.append(H.itokmc_num_particles())
+        H.itokmc_step(1)
+        s = H.itokmc_get_stats()
+        tr.append(s["ms_transport"])
+        mg.append(s["mg_cycles"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tot = e0.elapsed_time(e1)
+    H.close()
+    fp64 = form == itokmc.FP64
+    bpp = 2 * (32 if fp64 else 20) + ((24 + 8 + 8) if fp64 else (12 + 8 + 8)) / ph["ppc"]
+    n_avg = sum(counts) / len(counts)
+    gbs = n_avg * bpp / (statistics.median(tr) / 1e3) / 1e9
+    out = {"study": "tree", "grid": args.n, "form": "fp64" if fp64 else "mixed", "init_s": t_init,
+           "particles0": N0, "particles_per_step": counts, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": tot / args.steps, "particle_steps_per_s": sum(counts) / (tot / 1e3),
+           "steps_per_s": args.steps / (tot / 1e3), "transport_ms": tr, "mg_cycles": mg,
+           "mg_smoothing": [tune["mg_nu1"], tune["mg_nu2"]],
+           "roofline": {"bound": "hbm", "kernel": "transport stage (push+sort+deposit)", "achieved": gbs,
+                        "peak": pk, "peak_kind": pk_kind, "unit": "GB/s", "frac": gbs / pk,
+                        "bytes_per_particle": bpp}}
+    print(json.dumps(out), flush=True)
+
+
 def small_study(args):
     """The plain FP64 configuration in full: 64^3 over a 1 cm cube, 1.5 MV/m,
     a Gaussian blob (sigma 0.5 mm, peak 1e18 m^-3 at 0.8 L) sampled at ppc 8
@@ -674,7 +735,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default smoother counts (2, 2)")
-    ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small", "semi", "transport"],
+    ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small", "semi", "transport", "tree"],
                     help="instead of the benchmark: one of the studies (see each function's docstring)")
     ap.add_argument("--slab", action="store_true", help="transport study: count-pinned uniform z-slab")
     ap.add_argument("--physics", default="streamer", choices=["streamer", "tree"],
@@ -686,7 +747,7 @@ def main():
     ap.add_argument("--batched-only", action="store_true")
     args = ap.parse_args()
     if args.n is None:
-        args.n = 128 if args.study == "ensemble" else 256
+        args.n = {"ensemble": 128, "tree": 512}.get(args.study, 256)
     if args.study_steps is None:
         args.study_steps = {"ensemble": 5, "small": 10, "semi": 3}.get(args.study, 20)
     if args.study == "precision":
@@ -703,6 +764,9 @@ def main():
         return
     if args.study == "transport":
         transport_study(args)
+        return
+    if args.study == "tree":
+        tree_study(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

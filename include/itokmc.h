@@ -90,6 +90,19 @@ extern "C" {
 #define ITOKMC_STAGE_PARTICLES 2  /* a7-a9: products, photons, merge/split  */
 #define ITOKMC_STAGE_FIELD 3      /* a5 from the rho of the last a4          */
 
+/* ---- initial seeds ------------------------------------------------------
+ * A Gaussian seed of electrons (the initial conditions of Sec. 5.1): density
+ * peak exp(-|x - center|^2 / (2 sigma^2)) per m^3.  realization: the
+ * realization it seeds, or -1 for every realization. */
+typedef struct itokmc_seed_blob {
+    double center[3];          /* m                                          */
+    double sigma;              /* m, > 0                                     */
+    double peak;               /* electrons per m^3 at the centre, >= 0      */
+    int32_t realization;       /* -1: all realizations                       */
+    int32_t pad;
+} itokmc_seed_blob;
+#define ITOKMC_SEED_NEUTRAL 1  /* seed electron-ion pairs: N+ += N_c per cell */
+
 typedef void* (*itokmc_alloc_fn)(size_t bytes, void* ctx);   /* device memory */
 typedef void (*itokmc_free_fn)(void* ptr, void* ctx);
 
@@ -121,6 +134,9 @@ typedef struct itokmc_config {
     itokmc_alloc_fn alloc;     /* device allocator, or NULL: cudaMallocAsync */
     itokmc_free_fn free_fn;    /* matching free                              */
     void* alloc_ctx;           /* passed to alloc/free_fn                    */
+    const itokmc_seed_blob* blobs; /* initial seeds sampled by itokmc_init   */
+    int32_t n_blobs;           /* 0: no seeding (particles set by the caller)*/
+    int32_t seed_flags;        /* 0 or ITOKMC_SEED_NEUTRAL                   */
 } itokmc_config;
 
 typedef struct itokmc_stats {
@@ -155,8 +171,12 @@ int itokmc_config_defaults(itokmc_config* cfg);
  * photon emission (alpha(E), eta, k_gamma), the photon absorption range of
  * Sec. 5.1, the Cao et al. parameters N_c, N_SSA, eps of Sec. 3.2.3, the
  * particle budget of Sec. 4.4 (N_new) and Sec. 4.6 (ppc), and the electrode
- * and side boundary conditions of Sec. 5.1.  Errors: ERR_ARG (bad config),
- * ERR_OOM. */
+ * and side boundary conditions of Sec. 5.1.  With n_blobs > 0 the initial
+ * electrons are then sampled on the device from cfg->blobs
+ * (itokmc_seed_blobs, with cfg->seed_flags), deposited, and the initial
+ * field is solved (itokmc_solve_field); cfg->blobs is read during the call
+ * only.  Errors: ERR_ARG (bad config or blobs), ERR_OOM, and those of
+ * itokmc_seed_blobs and itokmc_solve_field. */
 int itokmc_init(const itokmc_config* cfg, itokmc_handle** out);
 
 /* Releases all device memory of the handle.  Always safe on a poisoned
@@ -182,6 +202,22 @@ int itokmc_set_particles(itokmc_handle* h, const double* x, const double* y, con
 int itokmc_read_particles(itokmc_handle* h, double* x, double* y, double* z, uint32_t* w,
                           int32_t* realization, int64_t* cell, int64_t cap, int64_t* n_out,
                           int32_t mem);
+
+/* Replaces all particles by initial electrons sampled on the device from
+ * Gaussian seeds (Sec. 5.1).  Per cell c of realization r: the density at
+ * the cell centre n(x_c) = sum of the blobs that seed r; N_c ~ Poisson(n(x_c)
+ * dV), drawn from the Philox stream (key seed0 + r, index c, the step
+ * counter, tag INIT, sub 0) with the tau-leap's sampler (inversion below mean
+ * 10, PTRS above); m = min(N_c, ppc) superparticles with the weight rule of
+ * Eq. w (N_c div m, the remainder on the first); slot j uniform in the cell
+ * from the stream (c, step, INIT, 1 + j): x = lo + (i + u) h from FP64
+ * uniforms (the mixed form keeps the FP32 offsets from the high words of
+ * the same uniforms).  Particles come out in canonical order (cell, slot).
+ * flags: ITOKMC_SEED_NEUTRAL also adds N_c to the cell's positive ions.  The
+ * field is not solved (call itokmc_solve_field).  Errors: ERR_ARG (NULL
+ * blobs with n_blobs > 0, sigma <= 0, peak < 0, realization < -1, unknown
+ * flags), ERR_CAPACITY, ERR_OVERFLOW (a weight above 2^32 - 1), ERR_CUDA. */
+int itokmc_seed_blobs(itokmc_handle* h, const itokmc_seed_blob* blobs, int32_t n_blobs, int32_t flags);
 
 /* Sets the ion counts (int64, R n^3 each; host or device). */
 int itokmc_set_ions(itokmc_handle* h, const int64_t* npos, const int64_t* nneg, int32_t mem);
@@ -227,6 +263,31 @@ int itokmc_advance_counter(itokmc_handle* h);
  * V-cycles taken and the final relative residual.  Errors: ERR_ARG,
  * ERR_NOCONV, ERR_OVERFLOW, ERR_CAPACITY, ERR_CUDA. */
 int itokmc_transport_semi_implicit(itokmc_handle* h, int32_t* cycles_out, double* rel_out);
+
+/* ---- checkpoints ----------------------------------------------------------
+ * The paper's runs write checkpoint files from which a run restarts (Sec.
+ * 5.6).  itokmc_save writes, at a step boundary, everything the next step
+ * reads: the configuration it belongs to, the step counter and the smoother
+ * counts in use, the particles in canonical order with the per-cell offsets,
+ * the ion counts N+ and N-, the field E of the next step, the potential and
+ * the previous potential (the next solve starts from their extrapolation),
+ * the fixed-point exponent of the mixed potential, and the densities of the
+ * last deposit (NE_FIX, XE, RHO, FIRINGS).  Every random draw is a Philox
+ * counter of (seed, index, step, tag), so a handle that loads the file
+ * continues bit for bit as the run that wrote it would have.
+ *   itokmc_save  path: file to create or overwrite (host I/O, about
+ *                R n^3 (128 + 8 FP64 | 56 mixed) bytes plus 32 (FP64) or
+ *                20 (mixed) bytes per particle).  Synchronises the stream.
+ *   itokmc_load  into a handle created with the same configuration (grid,
+ *                realizations, form, physics, seed0, mg_rtol; the stream,
+ *                allocator and a capacity of at least the saved particle
+ *                count may differ).  Replaces the handle's state and sets its
+ *                step counter and smoother counts from the file.
+ * Errors: ERR_ARG (NULL path, unreadable or foreign file, another
+ * configuration: the message names the first differing field),
+ * ERR_CAPACITY (load: too many particles), ERR_CUDA. */
+int itokmc_save(itokmc_handle* h, const char* path);
+int itokmc_load(itokmc_handle* h, const char* path);
 
 /* ---- autotuning ----------------------------------------------------------
  * The paper fixes no smoother counts; the multigrid cycle (Sec. 4.3:

@@ -12,6 +12,7 @@
 #include "../../include/itokmc.h"
 #include "ik_common.cuh"
 #include "ik_state.h"
+#include "ik_handle.h"
 
 namespace ik {
 std::atomic<unsigned long long> g_launches{0};
@@ -331,6 +332,19 @@ int full_step(itokmc_handle* h)
 
 }  // namespace
 
+namespace ik {
+int handle_view(itokmc_handle* h, HandleView* v)
+{
+    IK_GUARD(h);
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    if (h->sf) IK_CHECK(h, cudaStreamSynchronize(h->sf));
+    *v = HandleView{ &h->cfg, &h->P, &h->d, h->s, &h->N, h->cap, &h->step, h->G, h->field_prec };
+    return ITOKMC_OK;
+}
+int handle_fail(itokmc_handle* h, int code, const char* msg) { return fail(h, code, msg); }
+int handle_solve_field(itokmc_handle* h) { return itokmc_solve_field(h); }
+}  // namespace ik
+
 extern "C" {
 
 int itokmc_config_defaults(itokmc_config* c)
@@ -387,6 +401,8 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
         return fail(nullptr, ITOKMC_ERR_ARG, "kappa range");
     if (!(cfg->alloc == nullptr) != !(cfg->free_fn == nullptr))
         return fail(nullptr, ITOKMC_ERR_ARG, "alloc and free_fn must be given together");
+    if (cfg->n_blobs < 0 || (cfg->n_blobs > 0 && !cfg->blobs))
+        return fail(nullptr, ITOKMC_ERR_ARG, "n_blobs >= 0 with a blob array");
 
     itokmc_handle* h = new itokmc_handle();
     h->cfg = *cfg;
@@ -516,7 +532,18 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
         itokmc_destroy(h);
         return rc;
     }
-    // linear potential as the first guess of the first solve
+    // initial seeds from the configuration: sample, deposit, initial field
+    if (cfg->n_blobs > 0) {
+        rc = itokmc_seed_blobs(h, cfg->blobs, cfg->n_blobs, cfg->seed_flags);
+        if (!rc) rc = itokmc_solve_field(h);
+        if (rc) {
+            ik::set_global_error(h->err.c_str());
+            itokmc_destroy(h);
+            return rc;
+        }
+    }
+    h->cfg.blobs = nullptr;           // read during init only
+    h->cfg.n_blobs = 0;
     *out = h;
     return ITOKMC_OK;
 }
@@ -870,6 +897,7 @@ int itokmc_get_stats(itokmc_handle* h, itokmc_stats* st)
     if (!st) return ITOKMC_ERR_ARG;
     IK_CHECK(h, cudaStreamSynchronize(h->s));
     h->st.n_particles = h->N;
+    h->st.step = h->step;
     h->st.kernel_launches = (int64_t)ik::g_launches;
     *st = h->st;
     return ITOKMC_OK;

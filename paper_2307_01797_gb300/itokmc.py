@@ -45,7 +45,29 @@ class Config(ctypes.Structure):
         ("mg_max_cycles", ctypes.c_int32), ("field_precision", ctypes.c_int32),
         ("particle_capacity", ctypes.c_int64), ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+        ("blobs", ctypes.c_void_p), ("n_blobs", ctypes.c_int32), ("seed_flags", ctypes.c_int32),
     ]
+
+
+class SeedBlob(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_double * 3), ("sigma", ctypes.c_double), ("peak", ctypes.c_double),
+                ("realization", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+SEED_NEUTRAL = 1
+
+
+def blob_array(blobs):
+    """A ctypes array of itokmc_seed_blob from dicts (center, sigma, peak,
+    realization=-1)."""
+    arr = (SeedBlob * max(1, len(blobs)))()
+    for i, b in enumerate(blobs):
+        for a in range(3):
+            arr[i].center[a] = float(b["center"][a])
+        arr[i].sigma = float(b["sigma"])
+        arr[i].peak = float(b["peak"])
+        arr[i].realization = int(b.get("realization", -1))
+    return arr
 
 
 class Stats(ctypes.Structure):
@@ -129,6 +151,9 @@ def lib(build_if_missing: bool = True):
                 "itokmc_field_solve_noalloc": ([ctypes.POINTER(Config), vp, vp, vp, ctypes.POINTER(i32),
                                                 ctypes.POINTER(d)], ctypes.c_int),
                 "itokmc_probe_fp64_peak": ([vp, ctypes.POINTER(d), ctypes.POINTER(d)], ctypes.c_int),
+                "itokmc_seed_blobs": ([H, ctypes.POINTER(SeedBlob), i32, i32], ctypes.c_int),
+                "itokmc_save": ([H, ctypes.c_char_p], ctypes.c_int),
+                "itokmc_load": ([H, ctypes.c_char_p], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -322,6 +347,16 @@ class Handle:
         out = np.empty(blocks * cells, dtype=dt)
         _check(lib().itokmc_read_densities(self.h, int(realization), int(which), _ptr(out), out.nbytes), self.h)
         return out.reshape(blocks, cells) if blocks > 1 else out
+
+    def itokmc_seed_blobs(self, blobs, flags=0):
+        arr = blob_array(blobs)
+        _check(lib().itokmc_seed_blobs(self.h, arr, len(blobs), int(flags)), self.h)
+
+    def itokmc_save(self, path):
+        _check(lib().itokmc_save(self.h, os.fsencode(path)), self.h)
+
+    def itokmc_load(self, path):
+        _check(lib().itokmc_load(self.h, os.fsencode(path)), self.h)
 
     def itokmc_get_stats(self):
         st = Stats()

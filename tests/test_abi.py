@@ -55,9 +55,10 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "itokmc.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(itokmc_config), offsetof(itokmc_config, particle_capacity),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(itokmc_config), offsetof(itokmc_config, particle_capacity),
          offsetof(itokmc_config, alloc_ctx), offsetof(itokmc_config, field_precision),
-         sizeof(itokmc_stats), offsetof(itokmc_stats, ms_field));
+         sizeof(itokmc_stats), offsetof(itokmc_stats, ms_field), offsetof(itokmc_config, blobs),
+         offsetof(itokmc_config, seed_flags), sizeof(itokmc_seed_blob), offsetof(itokmc_seed_blob, realization));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -67,8 +68,10 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.join(build.ROOT, "include"), c, "-o", exe], check=True)
         got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     C, S = itokmc.Config, itokmc.Stats
+    B = itokmc.SeedBlob
     assert got == [ctypes.sizeof(C), C.particle_capacity.offset, C.alloc_ctx.offset, C.field_precision.offset,
-                   ctypes.sizeof(S), S.ms_field.offset]
+                   ctypes.sizeof(S), S.ms_field.offset, C.blobs.offset, C.seed_flags.offset, ctypes.sizeof(B),
+                   B.realization.offset]
 
 
 def test_oracle_and_library_share_no_source():
