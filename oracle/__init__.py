@@ -123,6 +123,8 @@ def lib():
             pi32 = ctypes.POINTER(i32)
             L.ora_seed_blobs.argtypes = [pp, i32, pd, pd, pd, pi32, i32, pd, pd, pd, pu32, pi64, pi64, i64]
             L.ora_seed_blobs.restype = i64
+            L.ora_kmc0d.argtypes = [pp, d, i64, i32, i32, pi64]
+            L.ora_kmc0d.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -239,6 +241,17 @@ def seed_blobs(params: Params, blobs, real: int = 0, cap: int = 50_000_000):
     if np_ < 0:
         raise RuntimeError("seed_blobs: " + ("capacity" if np_ == -1 else "weight overflow"))
     return dict(x=x[:np_], y=y[:np_], z=z[:np_], w=w[:np_], cell=cell[:np_]), counts
+
+
+def kmc0d(params: Params, E_mag: float, X0: int, n_real: int, n_steps: int):
+    """0-D KMC ensemble (Sec. 3.2.4): int64 (n_real, n_steps + 1) electron
+    counts; realization m, step k draw from the stream (seed, m, k, KMC)."""
+    X = np.zeros((int(n_real), int(n_steps) + 1), np.int64)
+    st = lib().ora_kmc0d(ctypes.byref(params), float(E_mag), int(X0), int(n_real), int(n_steps),
+                         _P(X, ctypes.c_int64))
+    if st != 0:
+        raise RuntimeError("kmc0d: iteration guard")
+    return X
 
 
 def canonical(params: Params, st: dict) -> dict:

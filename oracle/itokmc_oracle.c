@@ -1241,3 +1241,34 @@ int64_t ora_seed_blobs(const ora_params* p, int32_t nb, const double* centers, c
     }
     return np;
 }
+
+/* ------------------------------------------------------------------------ */
+/* 0-D KMC ensembles (Sec. 3.2.4): n_real independent single cells, each    */
+/* starting from X0 electrons in the field magnitude E_mag (rates as in the  */
+/* spatial step: the field (0, 0, -E_mag)), advanced n_steps steps of dt,   */
+/* realization m, step k drawing from the stream (key seed, index m, step   */
+/* k, KMC).  X[m (n_steps + 1) + k] = electrons after k steps.  Returns 0,  */
+/* or -1 if some cell hit the iteration guard.                               */
+/* ------------------------------------------------------------------------ */
+int ora_kmc0d(const ora_params* p, double E_mag, int64_t X0, int32_t n_real, int32_t n_steps, int64_t* X)
+{
+    double kr[3];
+    rates_at(p, 0.0, 0.0, -E_mag, kr);
+    int status = 0;
+    for (int32_t m = 0; m < n_real; ++m) {
+        int64_t x = X0;
+        int64_t* out = X + (int64_t)m * (n_steps + 1);
+        out[0] = x;
+        for (int32_t k = 0; k < n_steps; ++k) {
+            int64_t fired[3] = { 0, 0, 0 };
+            if (x > 0) {
+                ora_stream s;
+                stream_init(&s, p->seed, (uint32_t)m, (uint32_t)k, TAG_KMC, 0);
+                if (kmc_cell(p, &s, x, kr, fired) != 0) status = -1;
+            }
+            x += fired[0] - fired[1];
+            out[k + 1] = x;
+        }
+    }
+    return status;
+}

@@ -657,3 +657,28 @@ def test_kmc_rates_breakdown_field(oracle_mod):
             a, b = ion[sl].sum(), att[sl].sum()
             assert abs(a / b - ratio) < 6 * ratio * math.sqrt(1 / a + 1 / b)
         assert ph_.sum() == 0
+
+
+def test_kmc0d_ensemble_mean_follows_the_rate_equation(oracle_mod):
+    """0-D ensembles (Sec. 3.2.4): with every reaction non-critical the
+    tau-leap mean after K steps is X0 (1 + (k_ion - k_att) dt)^K exactly
+    (the discrete rate equation), so the ensemble mean must lie within the
+    sampling error of it; at a field below breakdown the count decays."""
+    ph = synth.physics_small(8)
+    p = oracle_mod.make_params(ph, seed=4)
+    E = 5e6
+    ve = ph["mu"] * E
+    ka = ph["alpha_A"] * math.exp(-ph["alpha_B"] / E) * ve
+    kb = ph["eta"] * ve
+    K, X0 = 50, 2000
+    X = oracle_mod.kmc0d(p, E, X0, 2000, K)
+    mean = X0 * (1 + (ka - kb) * ph["dt"]) ** K
+    assert abs(X[:, -1].mean() - mean) < 5 * X[:, -1].std() / math.sqrt(X.shape[0])
+    assert np.all(X[:, 0] == X0)
+    # below breakdown, A dt < 1: the exact SSA path, mean X0 exp((k_ion - k_att) t)
+    E2 = 2e6
+    ka2 = ph["alpha_A"] * math.exp(-ph["alpha_B"] / E2) * ph["mu"] * E2
+    kb2 = ph["eta"] * ph["mu"] * E2
+    Y = oracle_mod.kmc0d(p, E2, 200, 4000, 200)
+    mean2 = 200 * math.exp((ka2 - kb2) * 200 * ph["dt"])
+    assert mean2 < 200 and abs(Y[:, -1].mean() - mean2) < 5 * Y[:, -1].std() / math.sqrt(Y.shape[0])
