@@ -425,34 +425,64 @@ def precision_study(args):
 
 
 # ------------------------------------------------------------------ ensemble study
+def ensemble_partition(R, world, rank):
+    """Members [first, first + count) of an R-member ensemble that rank
+    `rank` of `world` advances: contiguous blocks, the first R mod world ranks
+    one member more.  A rank's handle takes seed0 + first as its Philox base,
+    so its local realization r draws with key seed0 + first + r, the global
+    member's own key."""
+    base, extra = divmod(int(R), int(world))
+    count = base + (1 if rank < extra else 0)
+    first = rank * base + min(rank, extra)
+    return first, count
+
+
+def ensemble_members(R, rng_seed=2024):
+    """Peaks of the R seed blobs, log-uniform in [1e17, 1e19] m^-3 (member r's
+    peak does not depend on how the ensemble is split)."""
+    rng = np.random.default_rng(rng_seed)
+    return [float(p) for p in 10.0 ** rng.uniform(17.0, 19.0, int(R))]
+
+
 def ensemble_study(args):
     """Batched ensemble against sequential single runs on the same GPU: R
-    independent realizations (seeds 1..R) of the 1 cm, 128^3 physics with
-    photoionization, ppc 16, each seeded by a Gaussian blob (sigma 0.5 mm at
-    0.8 L) whose peak is log-uniform in [1e17, 1e19] m^-3 (uneven particle
-    counts).  The batched handle advances all R in every launch; the
-    sequential runs advance one single-realization handle per member."""
+    independent realizations (member r: Philox key 1 + r) of the 1 cm, 128^3
+    physics with photoionization, ppc 16, each seeded on the device from a
+    Gaussian blob (sigma 0.5 mm at (L/2, L/2, 0.8 L)) whose peak is
+    log-uniform in [1e17, 1e19] m^-3 (uneven particle counts).  The batched
+    handle advances all of a rank's members in every launch; the sequential
+    runs advance one single-realization handle per member.  Under torchrun
+    the members are split R/N per rank (ensemble_partition): no collective
+    on the data path, the slowest rank's time and every rank's particle-steps
+    make the whole-job figures."""
     import torch
     from paper_2307_01797_gb300 import itokmc, synth
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     R, K = args.members, args.study_steps
+    first, Rl = ensemble_partition(R, world, rank)
+    peaks = ensemble_members(R)[first:first + Rl]
     ph = synth.physics_ensemble_member(args.n)
-    rng = np.random.default_rng(2024)
-    peaks = 10.0 ** rng.uniform(17.0, 19.0, R)
-    states = [synth.blob_state(ph, seed=1 + r, sigma=5e-4, peak=float(peaks[r]), zfrac=0.8) for r in range(R)]
-    counts = [len(st["w"]) for st in states]
-    out = {"study": "ensemble", "grid": args.n, "members": R, "steps": K, "particles0": counts, "forms": {}}
-    forms = [("fp64", itokmc.FP64), ("mixed", itokmc.MIXED)]
-    for name, form in forms:
-        # batched: every member in one handle
-        x = np.concatenate([st["x"] for st in states]); y = np.concatenate([st["y"] for st in states])
-        z = np.concatenate([st["z"] for st in states]); w = np.concatenate([st["w"] for st in states])
-        real = np.concatenate([np.full(c, r, np.int32) for r, c in enumerate(counts)])
-        H = itokmc.Handle(itokmc.make_config(ph, 8 * len(w) + 4_000_000, realizations=R, seed0=1, precision=form))
-        H.itokmc_set_particles(x, y, z, w, real)
-        H.itokmc_solve_field()
+    L = ph["hi"][0] - ph["lo"][0]
+    center = (L / 2, L / 2, 0.8 * L)
+
+    def handle(form, blobs, R_, seed0, cap):
+        cfg = itokmc.make_config(ph, cap, realizations=R_, seed0=seed0, precision=form)
+        arr = itokmc.blob_array(blobs)
+        cfg.blobs = itokmc.ctypes.cast(arr, itokmc.ctypes.c_void_p)
+        cfg.n_blobs = len(blobs)
+        return itokmc.Handle(cfg)
+
+    def timed(H):
         for _ in range(args.warmup):
             H.itokmc_step(1)
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
         done = 0
         t0 = time.perf_counter()
@@ -460,26 +490,28 @@ def ensemble_study(args):
             done += H.itokmc_num_particles()
             H.itokmc_step(1)
         torch.cuda.synchronize()
-        tb = time.perf_counter() - t0
+        return time.perf_counter() - t0, done
+
+    out = {"study": "ensemble", "grid": args.n, "members": R, "steps": K, "ranks": world,
+           "members_per_rank": [ensemble_partition(R, world, q)[1] for q in range(world)], "forms": {}}
+    for name, form in (("fp64", itokmc.FP64), ("mixed", itokmc.MIXED)):
+        blobs = [dict(center=center, sigma=5e-4, peak=peaks[r], realization=r) for r in range(Rl)]
+        H = handle(form, blobs, Rl, 1 + first, 4_000_000 * Rl + 4_000_000)
+        counts0 = H.itokmc_num_particles()
+        tb, done = timed(H)
         H.close()
-        res = {"batched_ms_per_step": 1e3 * tb / K, "batched_particle_steps_per_s": done / tb}
+        tb, done = aggregate_ranks(tb, done, dist, "cuda")
+        res = {"particles0": counts0, "batched_ms_per_step": 1e3 * tb / K, "batched_particle_steps_per_s": done / tb}
         if name == "fp64" or not args.batched_only:
-            # sequential: one member at a time
             ts, dn = 0.0, 0
-            for r, st in enumerate(states):
-                H = itokmc.Handle(itokmc.make_config(ph, 8 * counts[r] + 1_000_000, seed0=1 + r, precision=form))
-                H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
-                H.itokmc_solve_field()
-                for _ in range(args.warmup):
-                    H.itokmc_step(1)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                for _ in range(K):
-                    dn += H.itokmc_num_particles()
-                    H.itokmc_step(1)
-                torch.cuda.synchronize()
-                ts += time.perf_counter() - t0
+            for r in range(Rl):
+                H = handle(form, [dict(center=center, sigma=5e-4, peak=peaks[r], realization=0)], 1, 1 + first + r,
+                           8_000_000 + 1_000_000)
+                t, d = timed(H)
+                ts += t
+                dn += d
                 H.close()
+            ts, dn = aggregate_ranks(ts, dn, dist, "cuda")
             res.update({"sequential_ms_per_step": 1e3 * ts / K, "sequential_particle_steps_per_s": dn / ts,
                         "batched_speedup": ts / tb})
         out["forms"][name] = res
@@ -487,7 +519,10 @@ def ensemble_study(args):
     if "mixed" in out["forms"]:
         out["mixed_batched_vs_fp64_sequential"] = fp["sequential_ms_per_step"] / out["forms"]["mixed"][
             "batched_ms_per_step"]
-    print(json.dumps(out), flush=True)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 # ------------------------------------------------------------------ small config (C1)
@@ -650,6 +685,53 @@ def tree_study(args):
     print(json.dumps(out), flush=True)
 
 
+def kmc0d_study(args):
+    """0-D KMC ensembles against the reaction rate equation (Sec. 3.2.4,
+    Fig. AvalancheAttachment, with the configuration's alpha(E) and eta):
+    --members realizations of a single cell, X0 electrons, K steps of 1 ps at
+    several field magnitudes, in both forms on the GPU (itokmc_kmc0d into
+    device memory, timed with CUDA events) and a sample on the oracle (one
+    host core).  Reports realization-steps/s and, per field, the ensemble
+    mean and variance at the last step beside the rate equation's
+    X0 exp((k_ion - k_att) t)."""
+    import torch
+    import oracle
+    from paper_2307_01797_gb300 import itokmc, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ph = synth.physics_small(8)
+    M, K, X0 = args.members, args.study_steps, 100
+    out = {"study": "kmc0d", "realizations": M, "steps": K, "X0": X0, "dt": ph["dt"], "fields": {}}
+    stream = torch.cuda.current_stream()
+    for E in (2.0e6, 3.54e6, 5.0e6):
+        ve = ph["mu"] * E
+        ka = ph["alpha_A"] * math.exp(-ph["alpha_B"] / E) * ve
+        kb = ph["eta"] * ve
+        rec = {"k_ion": ka, "k_att": kb, "rre_mean": X0 * math.exp((ka - kb) * K * ph["dt"])}
+        for name, form in (("fp64", itokmc.FP64), ("mixed", itokmc.MIXED)):
+            cfg = itokmc.make_config(ph, 1, seed0=1, precision=form, stream=stream.cuda_stream)
+            X = torch.empty((M, K + 1), dtype=torch.int64, device="cuda")
+            for _ in range(max(1, args.warmup)):
+                itokmc._check(itokmc.lib().itokmc_kmc0d(itokmc.ctypes.byref(cfg), E, X0, M, K, X.data_ptr(),
+                                                        itokmc.DEVICE))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            itokmc._check(itokmc.lib().itokmc_kmc0d(itokmc.ctypes.byref(cfg), E, X0, M, K, X.data_ptr(),
+                                                    itokmc.DEVICE))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            last = X[:, -1].double()
+            rec[name] = {"ms": ms, "realization_steps_per_s": M * K / (ms / 1e3), "mean": float(last.mean()),
+                         "var": float(last.var()), "extinct": float((X[:, -1] == 0).double().mean())}
+        m_or = max(1, min(M, 2000))
+        t0 = time.perf_counter()
+        oracle.kmc0d(oracle.make_params(ph, seed=1), E, X0, m_or, K)
+        t = time.perf_counter() - t0
+        rec["oracle"] = {"realizations": m_or, "s": t, "realization_steps_per_s": m_or * K / t, "cores": 1}
+        out["fields"][f"{E:.3g}"] = rec
+    print(json.dumps(out), flush=True)
+
+
 def small_study(args):
     """The plain FP64 configuration in full: 64^3 over a 1 cm cube, 1.5 MV/m,
     a Gaussian blob (sigma 0.5 mm, peak 1e18 m^-3 at 0.8 L) sampled at ppc 8
@@ -735,7 +817,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default smoother counts (2, 2)")
-    ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small", "semi", "transport", "tree"],
+    ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small", "semi", "transport", "tree", "kmc0d"],
                     help="instead of the benchmark: one of the studies (see each function's docstring)")
     ap.add_argument("--slab", action="store_true", help="transport study: count-pinned uniform z-slab")
     ap.add_argument("--physics", default="streamer", choices=["streamer", "tree"],
@@ -749,7 +831,7 @@ def main():
     if args.n is None:
         args.n = {"ensemble": 128, "tree": 512}.get(args.study, 256)
     if args.study_steps is None:
-        args.study_steps = {"ensemble": 5, "small": 10, "semi": 3}.get(args.study, 20)
+        args.study_steps = {"ensemble": 5, "small": 10, "semi": 3, "kmc0d": 500}.get(args.study, 20)
     if args.study == "precision":
         precision_study(args)
         return
@@ -767,6 +849,9 @@ def main():
         return
     if args.study == "tree":
         tree_study(args)
+        return
+    if args.study == "kmc0d":
+        kmc0d_study(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

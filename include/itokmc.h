@@ -264,6 +264,28 @@ int itokmc_advance_counter(itokmc_handle* h);
  * ERR_NOCONV, ERR_OVERFLOW, ERR_CAPACITY, ERR_CUDA. */
 int itokmc_transport_semi_implicit(itokmc_handle* h, int32_t* cycles_out, double* rel_out);
 
+/* ---- 0-D KMC ensembles ------------------------------------------------------
+ * The paper compares KMC with the reaction rate equation on a single
+ * well-mixed cell (Sec. 3.2.4, Fig. AvalancheAttachment): thousands of
+ * independent realizations of the electron count under ionization,
+ * attachment and photon emission at a fixed field.  itokmc_kmc0d advances
+ * n_real such realizations on the device, one thread each, with the per-cell
+ * KMC of the spatial step (Sec. 3.2.3, Cao et al. hybrid; cfg's n_crit,
+ * n_ssa, eps, dt) and the rates of the field magnitude E_mag (V/m): k_ion =
+ * alpha(E) mu E, k_att = eta mu E, k_ph = photon_ratio k_ion, in FP64
+ * (cfg->precision = ITOKMC_FP64) or FP32 (ITOKMC_MIXED).  Realization m,
+ * step k draws from the Philox stream (key seed0, index m, step k, tag KMC).
+ *   X  int64 n_real x (n_steps + 1), row m = realization m: the electrons
+ *      after k = 0 .. n_steps steps (X[m][0] = X0); host (mem =
+ *      ITOKMC_HOST) or device (ITOKMC_DEVICE) memory of the caller.
+ * Grid, particle and allocator fields of cfg are ignored; cfg->stream is
+ * used.  Allocates a small counter block (and, for host output, a device
+ * copy of X) for the call.  Returns ITOKMC_OK, ITOKMC_ERR_ARG, ITOKMC_ERR_OOM,
+ * ITOKMC_ERR_KMC (a realization hit the iteration guard) or ITOKMC_ERR_CUDA;
+ * the message is in itokmc_last_error(NULL).  Synchronises the stream. */
+int itokmc_kmc0d(const itokmc_config* cfg, double E_mag, int64_t X0, int32_t n_real, int32_t n_steps, int64_t* X,
+                 int32_t mem);
+
 /* ---- checkpoints ----------------------------------------------------------
  * The paper's runs write checkpoint files from which a run restarts (Sec.
  * 5.6).  itokmc_save writes, at a step boundary, everything the next step

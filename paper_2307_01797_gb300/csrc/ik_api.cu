@@ -169,6 +169,26 @@ cudaError_t create_field_stream(cudaStream_t* sf)
 
 int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
+// Kernel parameters of a configuration (grid of n^3 cells per realization).
+void fill_params(const itokmc_config* cfg, ik::Params& P)
+{
+    const int n = cfg->n[0];
+    P.n = n; P.n3 = n * n * n; P.R = cfg->n_realizations; P.log2n = ilog2(n);
+    P.ppc = cfg->ppc; P.n_new = cfg->n_new; P.n_crit = cfg->n_crit; P.n_ssa = cfg->n_ssa; P.frac_bits = cfg->frac_bits;
+    for (int a = 0; a < 3; ++a) {
+        P.lo[a] = cfg->lo[a]; P.hi[a] = cfg->hi[a]; P.h[a] = (cfg->hi[a] - cfg->lo[a]) / n;
+        P.rh[a] = 1.0 / P.h[a];
+    }
+    P.dt = cfg->dt; P.mu = cfg->mu; P.D = cfg->D; P.alpha_A = cfg->alpha_A; P.alpha_B = cfg->alpha_B; P.eta = cfg->eta;
+    P.photon_ratio = cfg->photon_ratio; P.kappa_lo = cfg->kappa_lo; P.kappa_hi = cfg->kappa_hi; P.eps = cfg->eps;
+    P.sdt = sqrt((2.0 * cfg->D) * cfg->dt);
+    P.E0 = cfg->E0;
+    P.seed0 = cfg->seed0;
+    P.step = 0;
+    P.f_drift = (float)(-cfg->mu * cfg->dt / P.h[0]);
+    P.f_diff = (float)(P.sdt / P.h[0]);
+}
+
 int status_of_err(itokmc_handle* h, unsigned err)
 {
     if (!err) return ITOKMC_OK;
@@ -411,20 +431,7 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     h->cap = (uint32_t)cfg->particle_capacity;
     h->field_prec = cfg->field_precision < 0 ? cfg->precision : cfg->field_precision;
     ik::Params& P = h->P;
-    P.n = n; P.n3 = n * n * n; P.R = R; P.log2n = ilog2(n);
-    P.ppc = cfg->ppc; P.n_new = cfg->n_new; P.n_crit = cfg->n_crit; P.n_ssa = cfg->n_ssa; P.frac_bits = cfg->frac_bits;
-    for (int a = 0; a < 3; ++a) {
-        P.lo[a] = cfg->lo[a]; P.hi[a] = cfg->hi[a]; P.h[a] = (cfg->hi[a] - cfg->lo[a]) / n;
-        P.rh[a] = 1.0 / P.h[a];
-    }
-    P.dt = cfg->dt; P.mu = cfg->mu; P.D = cfg->D; P.alpha_A = cfg->alpha_A; P.alpha_B = cfg->alpha_B; P.eta = cfg->eta;
-    P.photon_ratio = cfg->photon_ratio; P.kappa_lo = cfg->kappa_lo; P.kappa_hi = cfg->kappa_hi; P.eps = cfg->eps;
-    P.sdt = sqrt((2.0 * cfg->D) * cfg->dt);
-    P.E0 = cfg->E0;
-    P.seed0 = cfg->seed0;
-    P.step = 0;
-    P.f_drift = (float)(-cfg->mu * cfg->dt / P.h[0]);
-    P.f_diff = (float)(P.sdt / P.h[0]);
+    fill_params(cfg, P);
 
     int rc = 0;
     ik::Dev& d = h->d;
@@ -909,6 +916,54 @@ int itokmc_num_particles(itokmc_handle* h, int64_t* n_out)
     if (!n_out) return ITOKMC_ERR_ARG;
     IK_CHECK(h, cudaStreamSynchronize(h->s));
     *n_out = h->N;
+    return ITOKMC_OK;
+}
+
+int itokmc_kmc0d(const itokmc_config* cfg, double E_mag, int64_t X0, int32_t n_real, int32_t n_steps, int64_t* X,
+                 int32_t mem)
+{
+    if (!cfg || !X) return fail(nullptr, ITOKMC_ERR_ARG, "kmc0d: NULL argument");
+    if (n_real < 1 || n_steps < 0 || X0 < 0 || !(E_mag >= 0.0) || !(cfg->dt > 0.0) || cfg->mu < 0.0 ||
+        cfg->n_ssa < 1 || cfg->n_crit < 0 || (mem != ITOKMC_HOST && mem != ITOKMC_DEVICE))
+        return fail(nullptr, ITOKMC_ERR_ARG, "kmc0d: n_real >= 1, n_steps >= 0, X0 >= 0, E >= 0, dt > 0, mu >= 0");
+    if (cfg->precision != ITOKMC_FP64 && cfg->precision != ITOKMC_MIXED)
+        return fail(nullptr, ITOKMC_ERR_ARG, "kmc0d: precision");
+    itokmc_config c = *cfg;
+    c.n[0] = c.n[1] = c.n[2] = 8;                      // no grid: any valid size for the parameters
+    for (int a = 0; a < 3; ++a) { c.lo[a] = 0.0; c.hi[a] = 1.0; }
+    c.n_realizations = 1;
+    ik::Params P{};
+    fill_params(&c, P);
+    cudaStream_t s = (cudaStream_t)cfg->stream;
+    const size_t bytes = (size_t)n_real * (size_t)(n_steps + 1) * sizeof(long long);
+    long long* dX = reinterpret_cast<long long*>(X);
+    ik::Counters* ctr = nullptr;
+    bool own = false;
+    if (cudaMalloc(reinterpret_cast<void**>(&ctr), sizeof(ik::Counters)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, ITOKMC_ERR_OOM, "kmc0d: counters");
+    }
+    if (mem == ITOKMC_HOST) {
+        if (cudaMalloc(reinterpret_cast<void**>(&dX), bytes) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(ctr);
+            return fail(nullptr, ITOKMC_ERR_OOM, "kmc0d: trajectories");
+        }
+        own = true;
+    }
+    cudaMemsetAsync(ctr, 0, sizeof(ik::Counters), s);
+    ik::launch_kmc0d(P, cfg->precision == ITOKMC_MIXED, E_mag, (long long)X0, (uint32_t)n_real, n_steps, dX, ctr, s);
+    unsigned err = 0;
+    cudaMemcpyAsync(&err, &ctr->err, sizeof err, cudaMemcpyDeviceToHost, s);
+    if (own) cudaMemcpyAsync(X, dX, bytes, cudaMemcpyDeviceToHost, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (own) cudaFree(dX);
+    cudaFree(ctr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, ITOKMC_ERR_CUDA, std::string("kmc0d: ") + cudaGetErrorString(e));
+    }
+    if (err) return fail(nullptr, ITOKMC_ERR_KMC, "kmc0d: KMC iteration guard hit");
     return ITOKMC_OK;
 }
 

@@ -1037,6 +1037,48 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
     warp_add(&ctr->photo_slots, t_slots);
 }
 
+// ------------------------------------------------------------------ 0-D KMC
+// Independent single-cell realizations (Sec. 3.2.4): realization m starts
+// from X0 electrons and advances nsteps steps of dt with the rates of the
+// field magnitude Em (k_ion = alpha(Em) mu Em, k_att = eta mu Em, k_ph =
+// photon_ratio k_ion), each step the per-cell KMC of the spatial model drawn
+// from the stream (key seed0, index m, step k, KMC).  X[m (nsteps + 1) + k]
+// holds the electrons after k steps.
+template <class T>
+__global__ void k_kmc0d(Params P, double Em, long long X0, uint32_t nreal, int nsteps, long long* __restrict__ X,
+                        Counters* __restrict__ ctr)
+{
+    T kr[3];
+    if constexpr (sizeof(T) == 8) {
+        const double ve = P.mu * Em;
+        const double alpha = (Em > 0.0) ? P.alpha_A * dexp(-(P.alpha_B / Em)) : 0.0;
+        kr[0] = alpha * ve;
+        kr[1] = P.eta * ve;
+        kr[2] = P.photon_ratio * kr[0];
+    } else {
+        const float Ef = (float)Em;
+        const float ve = (float)P.mu * Ef;
+        const float alpha = (Ef > 0.0f) ? (float)P.alpha_A * expf(-((float)P.alpha_B / Ef)) : 0.0f;
+        kr[0] = alpha * ve;
+        kr[1] = (float)P.eta * ve;
+        kr[2] = (float)P.photon_ratio * kr[0];
+    }
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < nreal; m += gridDim.x * blockDim.x) {
+        long long x = X0;
+        long long* out = X + (size_t)m * (nsteps + 1);
+        out[0] = x;
+        for (int k = 0; k < nsteps; ++k) {
+            long long f[3] = { 0, 0, 0 };
+            if (x > 0) {
+                Stream s(P.seed0, m, (uint32_t)k, TAG_KMC, 0);
+                if (kmc_cell<T>(P, s, x, kr, f) != 0) atomicOr(&ctr->err, DERR_KMC);
+            }
+            x += f[0] - f[1];
+            out[k + 1] = x;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ loss
 // Systematic integer removal of L = -dN electrons from the cell's particles
 // in canonical order: particle p loses floor((C_p L + R)/W) -
@@ -2260,6 +2302,15 @@ void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
     // the fixed-point field form builds its right-hand side in the solve
     k_rho<<<grid_for(G, 256), 256, 0, s>>>(P, d.Npos, d.Nneg, d.ne_fix, d.rho, d.phi_F > 0 ? nullptr : d.lev[0].rhs,
                                           G, qscale, bc_top, P.h[2] * P.h[2], d.ctr);
+}
+
+void launch_kmc0d(const Params& P, bool mixed, double Em, long long X0, uint32_t nreal, int nsteps, long long* X,
+                  Counters* ctr, cudaStream_t s)
+{
+    ++g_launches;
+    const int blocks = grid_for(nreal, 128, 152 * 64);
+    if (mixed) k_kmc0d<float><<<blocks, 128, 0, s>>>(P, Em, X0, nreal, nsteps, X, ctr);
+    else k_kmc0d<double><<<blocks, 128, 0, s>>>(P, Em, X0, nreal, nsteps, X, ctr);
 }
 
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)

@@ -152,6 +152,7 @@ def lib(build_if_missing: bool = True):
                                                 ctypes.POINTER(d)], ctypes.c_int),
                 "itokmc_probe_fp64_peak": ([vp, ctypes.POINTER(d), ctypes.POINTER(d)], ctypes.c_int),
                 "itokmc_seed_blobs": ([H, ctypes.POINTER(SeedBlob), i32, i32], ctypes.c_int),
+                "itokmc_kmc0d": ([ctypes.POINTER(Config), d, i64, i32, i32, vp, i32], ctypes.c_int),
                 "itokmc_save": ([H, ctypes.c_char_p], ctypes.c_int),
                 "itokmc_load": ([H, ctypes.c_char_p], ctypes.c_int),
             }
@@ -161,6 +162,13 @@ def lib(build_if_missing: bool = True):
                 f.restype = res
             _lib = L
     return _lib
+
+
+def itokmc_kmc0d(cfg: Config, E_mag: float, X0: int, n_real: int, n_steps: int):
+    """0-D KMC ensemble: int64 array (n_real, n_steps + 1) of electron counts."""
+    X = np.empty((int(n_real), int(n_steps) + 1), np.int64)
+    _check(lib().itokmc_kmc0d(ctypes.byref(cfg), float(E_mag), int(X0), int(n_real), int(n_steps), _ptr(X), HOST))
+    return X
 
 
 def itokmc_probe_fp64_peak(stream=None):
