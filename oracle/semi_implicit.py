@@ -144,3 +144,17 @@ def transport(p, phys: dict, S: dict, E=None):
                      _P(zd, pd), _P(Ex, pd), _P(Ey, pd), _P(Ez, pd), _P(xo, pd), _P(yo, pd), _P(zo, pd),
                      _P(cell, ctypes.c_int64))
     return dict(xo=xo, yo=yo, zo=zo, cell=cell, xd=xd, yd=yd, zd=zd, sigma=sigma, rho=rho_d, phi=phi, E=E)
+
+
+def step(p, phys: dict, S: dict, E=None):
+    """One semi-implicit time step (Sec. 4.7): the transport of Sec. 4.7 steps
+    1-5 (``transport``; a given field E replaces its solve), then the sort,
+    the deposit, KMC in the field of the end of the step, products, photons
+    and the merge/split, as the explicit step does after its push.  Returns
+    (new_state, info); info also holds the transport's results under
+    "transport"."""
+    from .stages import after_transport
+    T = transport(p, phys, S, E=E)
+    new, info = after_transport(p, S, T["xo"], T["yo"], T["zo"], T["cell"], T["E"])
+    info["transport"] = T
+    return new, info

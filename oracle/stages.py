@@ -142,8 +142,16 @@ def step(p: Params, state: dict, E):
     Npos, Nneg (int64 n^3).  Returns (new_state, info) where info holds the
     intermediate results: sorted particles, ne_fix, Xe, rho_fixed (for the
     next field solve), firings, outflow and lost-photon weights."""
-    ncell = p.n ** 3
     xo, yo, zo, cnew = push(p, state["x"], state["y"], state["z"], E)
+    return after_transport(p, state, xo, yo, zo, cnew, E)
+
+
+def after_transport(p: Params, state: dict, xo, yo, zo, cnew, E):
+    """The rest of a step once the particles of ``state`` have moved to
+    (xo, yo, zo) in cells cnew (-1: left the box): the stable sort, the
+    deposit and charge, KMC with the field E, products, photons and the
+    merge/split.  Returns (new_state, info) as ``step``."""
+    ncell = p.n ** 3
     w0 = np.asarray(state["w"], np.uint32)
     outflow = int(w0[cnew < 0].astype(np.int64).sum())
     perm = sort_by_cell(cnew, ncell)

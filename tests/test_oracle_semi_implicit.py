@@ -199,3 +199,29 @@ def test_velocity_is_taken_at_the_start_of_step_position(oracle_mod):
     tol = 4 * np.finfo(np.float64).eps * np.max(np.abs(S["z"]))
     assert np.max(np.abs(got - at_xk)) <= tol
     assert np.max(np.abs(got - at_xd)) > 100 * tol
+
+
+def test_semi_implicit_full_step_conserves_charge(oracle_mod):
+    """Whole semi-implicit steps (transport, KMC, products, photons,
+    merge/split): the net charge sum(N+ - N-) - sum(w) changes only by the
+    electrons absorbed at the faces (a lost photon creates nothing), every
+    count stays non-negative and every cell ends with at most ppc
+    particles."""
+    from oracle import semi_implicit as si
+    ph = _phys(16, dt=5e-12, photon_ratio=0.06)
+    st = synth.blob_state(ph, seed=3, sigma=1.2e-3, peak=5e18, zfrac=0.5)
+    p = oracle_mod.make_params(ph, seed=8, step=0)
+    S = oracle_mod.canonical(p, st)
+    n3 = ph["n"] ** 3
+    S["Npos"] = np.zeros(n3, np.int64)
+    S["Nneg"] = np.zeros(n3, np.int64)
+    q0 = int(S["Npos"].sum() - S["Nneg"].sum()) - int(S["w"].astype(np.int64).sum())
+    for k in range(2):
+        p = oracle_mod.make_params(ph, seed=8, step=k)
+        S, info = si.step(p, ph, S)
+        q1 = int(S["Npos"].sum() - S["Nneg"].sum()) - int(S["w"].astype(np.int64).sum())
+        assert q1 - q0 == info["outflow"], (q1 - q0, info["outflow"])
+        q0 = q1
+        assert np.all(S["Npos"] >= 0) and np.all(S["Nneg"] >= 0) and np.all(S["w"] > 0)
+        assert np.bincount(S["cell"], minlength=n3).max() <= ph["ppc"]
+        assert info["n_ion"].sum() > 0
