@@ -471,8 +471,10 @@ def ensemble_study(args):
     L = ph["hi"][0] - ph["lo"][0]
     center = (L / 2, L / 2, 0.8 * L)
 
+    coupling = itokmc.SEMI_IMPLICIT if args.coupling == "semi" else itokmc.EXPLICIT
+
     def handle(form, blobs, R_, seed0, cap):
-        cfg = itokmc.make_config(ph, cap, realizations=R_, seed0=seed0, precision=form)
+        cfg = itokmc.make_config(ph, cap, realizations=R_, seed0=seed0, precision=form, coupling=coupling)
         arr = itokmc.blob_array(blobs)
         cfg.blobs = itokmc.ctypes.cast(arr, itokmc.ctypes.c_void_p)
         cfg.n_blobs = len(blobs)
@@ -492,16 +494,20 @@ def ensemble_study(args):
         torch.cuda.synchronize()
         return time.perf_counter() - t0, done
 
-    out = {"study": "ensemble", "grid": args.n, "members": R, "steps": K, "ranks": world,
+    out = {"study": "ensemble", "grid": args.n, "members": R, "steps": K, "ranks": world, "coupling": args.coupling,
            "members_per_rank": [ensemble_partition(R, world, q)[1] for q in range(world)], "forms": {}}
-    for name, form in (("fp64", itokmc.FP64), ("mixed", itokmc.MIXED)):
+    # the semi-implicit step exists in the FP64 form
+    forms = (("fp64", itokmc.FP64),) if args.coupling == "semi" else (("fp64", itokmc.FP64), ("mixed", itokmc.MIXED))
+    for name, form in forms:
         blobs = [dict(center=center, sigma=5e-4, peak=peaks[r], realization=r) for r in range(Rl)]
         H = handle(form, blobs, Rl, 1 + first, 4_000_000 * Rl + 4_000_000)
         counts0 = H.itokmc_num_particles()
         tb, done = timed(H)
+        counts_end = H.itokmc_num_particles()
         H.close()
         tb, done = aggregate_ranks(tb, done, dist, "cuda")
-        res = {"particles0": counts0, "batched_ms_per_step": 1e3 * tb / K, "batched_particle_steps_per_s": done / tb}
+        res = {"particles0": counts0, "particles_end": counts_end, "batched_ms_per_step": 1e3 * tb / K,
+               "batched_particle_steps_per_s": done / tb}
         if name == "fp64" or not args.batched_only:
             ts, dn = 0.0, 0
             for r in range(Rl):
@@ -568,6 +574,29 @@ def semi_study(args):
         out[mode] = {"ms_per_transport_and_field": ms, "mg_cycles": cyc,
                      "particle_steps_per_s": H.itokmc_num_particles() / (ms / 1e3)}
     H.close()
+    # whole steps of each coupling (the explicit step overlaps its field
+    # solve with KMC and merge; the semi-implicit one solves inside its
+    # transport stage), from the same state
+    for mode, coupling in (("explicit", itokmc.EXPLICIT), ("semi", itokmc.SEMI_IMPLICIT)):
+        H = itokmc.Handle(itokmc.make_config(ph, int(N0 * args.cap_factor) + 20_000_000, seed0=1,
+                                             precision=itokmc.FP64, coupling=coupling))
+        H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+        H.itokmc_set_ions(*ions)
+        H.itokmc_solve_field()
+        for _ in range(max(1, args.warmup)):
+            H.itokmc_step(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = 0
+        for _ in range(K):
+            done += H.itokmc_num_particles()
+            H.itokmc_step(1)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        s_ = H.itokmc_get_stats()
+        out[mode]["full_step"] = {"ms_per_step": 1e3 * t / K, "particle_steps_per_s": done / t,
+                                  "ms_transport_last": s_["ms_transport"], "ms_particles_last": s_["ms_particles"]}
+        H.close()
     print(json.dumps(out), flush=True)
 
 
@@ -823,6 +852,8 @@ def main():
     ap.add_argument("--physics", default="streamer", choices=["streamer", "tree"],
                     help="transport study: streamer (2 cm, ppc 32) or discharge-tree physics (4 cm, ppc 64)")
     ap.add_argument("--dt-scale", type=float, default=1.0, help="transport study: dt multiplier (sort stress)")
+    ap.add_argument("--coupling", default="explicit", choices=["explicit", "semi"],
+                    help="ensemble study: explicit or semi-implicit field coupling (FP64 form)")
     ap.add_argument("--study-steps", type=int, default=None,
                     help="steps of a study (default: precision 20, small 10, ensemble 5)")
     ap.add_argument("--members", type=int, default=64)

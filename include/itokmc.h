@@ -67,6 +67,12 @@ extern "C" {
                         /* fixed-point deposit, FP32 V-cycles inside FP64   */
                         /* residual iterative refinement                    */
 
+/* ---- field coupling of a step (itokmc_config.coupling) ----------------- */
+#define ITOKMC_EXPLICIT 0       /* Euler-Maruyama push with the field of the  */
+                                /* start of the step (Sec. 4.3, first form)   */
+#define ITOKMC_SEMI_IMPLICIT 1  /* the paper's semi-implicit step (Sec. 4.3, */
+                                /* Sec. 4.7 steps 1-5; FP64 form)             */
+
 /* ---- memory kinds for host/device pointers ----------------------------- */
 #define ITOKMC_HOST 0
 #define ITOKMC_DEVICE 1
@@ -137,6 +143,8 @@ typedef struct itokmc_config {
     const itokmc_seed_blob* blobs; /* initial seeds sampled by itokmc_init   */
     int32_t n_blobs;           /* 0: no seeding (particles set by the caller)*/
     int32_t seed_flags;        /* 0 or ITOKMC_SEED_NEUTRAL                   */
+    int32_t coupling;          /* ITOKMC_EXPLICIT or ITOKMC_SEMI_IMPLICIT     */
+    int32_t pad0;
 } itokmc_config;
 
 typedef struct itokmc_stats {
@@ -231,12 +239,17 @@ int itokmc_set_field(itokmc_handle* h, const double* E, int32_t mem);
  * multigrid stops at mg_max_cycles above tolerance. */
 int itokmc_solve_field(itokmc_handle* h);
 
-/* Advances nsteps full steps (a1-a9 then a5): the time step of Sec. 4.7 in
- * its explicit form -- particle transport by Eq. ito_kernel with the
- * Euler-Maruyama update of Sec. 4.3 (first equation), deposition (Sec. 4.2),
- * per-cell KMC (Sec. 3.2.3), products (Sec. 4.4), photoionization (Sec.
- * 4.5), merge/split (Sec. 4.6) and the Poisson solve (Sec. 4.3) for the
- * next step's field.  Errors: ERR_CAPACITY, ERR_OVERFLOW, ERR_NOCONV,
+/* Advances nsteps full steps.  With coupling = ITOKMC_EXPLICIT (a1-a9 then
+ * a5): particle transport by Eq. ito_kernel with the Euler-Maruyama update
+ * of Sec. 4.3 (first equation) in the field of the start of the step,
+ * deposition (Sec. 4.2), per-cell KMC (Sec. 3.2.3), products (Sec. 4.4),
+ * photoionization (Sec. 4.5), merge/split (Sec. 4.6) and the Poisson solve
+ * (Sec. 4.3) for the next step's field, overlapped with a6-a9.  With
+ * ITOKMC_SEMI_IMPLICIT the time step of Sec. 4.7: the semi-implicit
+ * transport stage of itokmc_transport_semi_implicit (conductivity, diffusive
+ * substep, variable-coefficient solve for the field of the end of the step,
+ * advective substep, sort, deposit) and then a6-a9 with that field; no
+ * solve follows the step.  Errors: ERR_CAPACITY, ERR_OVERFLOW, ERR_NOCONV,
  * ERR_KMC, ERR_CUDA. */
 int itokmc_step(itokmc_handle* h, int32_t nsteps);
 

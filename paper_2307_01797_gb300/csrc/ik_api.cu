@@ -46,7 +46,6 @@ struct itokmc_handle {
     itokmc_stats st{};
     cudaEvent_t ev[8]{};
     struct Readback { uint32_t N; uint32_t pad; ik::Counters ctr; }* rb = nullptr;  // pinned
-    double* semi_c[ik::MAX_LEVELS] = {};   // semi-implicit coefficients per level (on first use)
 };
 
 namespace {
@@ -313,6 +312,67 @@ int stage_field_on(itokmc_handle* h, cudaStream_t s, ik::E64* E, float4* E32, un
 
 int stage_field(itokmc_handle* h) { return stage_field_on(h, h->s, h->d.E, h->d.E32, h->rb->ctr.rho_absmax); }
 
+// The semi-implicit transport stage (Sec. 4.3, Sec. 4.7 steps 1-5): the
+// conductivity of the start of the step, the diffusive substep, the charge of
+// the diffused particles, the variable-coefficient solve for the field of
+// the end of the step (into d.E), the advective substep, sort and deposit.
+int stage_semi_transport(itokmc_handle* h, int32_t* cycles_out, double* rel_out)
+{
+    ik::Dev& d = h->d;
+    if (d.mixed || d.phi_F > 0)
+        return fail(h, ITOKMC_ERR_ARG, "semi-implicit transport: FP64 form only");
+    // no work of an overlapped field solve may still be in flight
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    if (h->sf) IK_CHECK(h, cudaStreamSynchronize(h->sf));
+    int rc = 0;
+    for (int l = 0; l < d.nlev && !rc; ++l)
+        if (!d.vc[l].c) {
+            const size_t cells = (size_t)h->P.R * d.lev[l].n * d.lev[l].n * d.lev[l].n;
+            ik::VCLevel& V = d.vc[l];
+            V.c = dalloc_n<double>(h, cells, &rc);
+            V.fx = dalloc_n<double>(h, cells, &rc);
+            V.fy = dalloc_n<double>(h, cells, &rc);
+            V.fz = dalloc_n<double>(h, cells, &rc);
+            V.dg = dalloc_n<double>(h, cells, &rc);
+            V.idg = dalloc_n<double>(h, cells, &rc);
+        }
+    if (rc) return rc;
+    IK_CHECK(h, cudaEventRecord(h->ev[0], h->s));
+    ik::launch_deposit_only(h->P, d, h->N, h->s);       // n_e of the start of the step
+    ik::launch_semi_coef(h->P, d, d.vc[0].c, h->s);
+    ik::launch_diffuse(h->P, d, h->N, h->s);            // X+ into recB
+    ik::launch_deposit_B(h->P, d, h->N, h->s);
+    IK_CHECK(h, cudaMemsetAsync(d.ctr, 0, sizeof(ik::Counters), h->s));
+    ik::launch_rho(h->P, d, h->G, h->s);                // rho+
+    rc = readback(h);
+    if (rc) return rc;
+    rc = status_of_err(h, h->rb->ctr.err);
+    if (rc) return rc;
+    int cycles = 0;
+    double rel = 0.0;
+    const int st = ik::field_solve_vc(h->P, d, d.norm_out, d.norm_host, h->cfg.mg_rtol, h->cfg.mg_nu1, h->cfg.mg_nu2,
+                                      h->cfg.mg_max_cycles, h->s, &cycles, &rel);
+    if (cycles_out) *cycles_out = cycles;
+    if (rel_out) *rel_out = rel;
+    h->st.mg_cycles = cycles;
+    h->st.mg_rel_residual = rel;
+    if (st == -3) return cuda_check(h, cudaGetLastError(), "semi-implicit field solve");
+    if (st != 0) return fail(h, ITOKMC_ERR_NOCONV, "semi-implicit field: multigrid did not reach mg_rtol");
+    ik::launch_advect(h->P, d, h->N, h->s);
+    ik::launch_transport_finish(h->P, d, h->N, h->G, h->s);
+    ik::launch_rho(h->P, d, h->G, h->s);
+    IK_CHECK(h, cudaEventRecord(h->ev[1], h->s));
+    rc = readback(h);
+    if (rc) return rc;
+    const ik::Counters& c = h->rb->ctr;
+    h->st.n_movers = (int64_t)c.n_movers;
+    int64_t out = 0;
+    for (int r = 0; r < h->P.R; ++r) out += (int64_t)c.outflow[r];
+    h->st.outflow_weight = out;
+    h->st.ms_transport = elapsed(h, 0, 1);
+    return status_of_err(h, c.err);
+}
+
 // One full step.  After the transport stage has formed rho, the field of the
 // next step is solved on the field stream by a host thread while this
 // thread runs KMC and the particle stages (they read the current field; the
@@ -348,6 +408,18 @@ int full_step(itokmc_handle* h)
     std::swap(h->d.E, h->d.E_next);
     std::swap(h->d.E32, h->d.E32_next);
     return ITOKMC_OK;
+}
+
+// One semi-implicit step (Sec. 4.7): the semi-implicit transport stage
+// solves the field of the end of the step, with which KMC and the particle
+// stages then run; nothing overlaps (the next step's field is solved inside
+// the next transport stage).
+int semi_step(itokmc_handle* h)
+{
+    int rc = stage_semi_transport(h, nullptr, nullptr);
+    if (!rc) rc = stage_kmc(h);
+    if (!rc) rc = stage_particles(h);
+    return rc;
 }
 
 }  // namespace
@@ -423,6 +495,11 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
         return fail(nullptr, ITOKMC_ERR_ARG, "alloc and free_fn must be given together");
     if (cfg->n_blobs < 0 || (cfg->n_blobs > 0 && !cfg->blobs))
         return fail(nullptr, ITOKMC_ERR_ARG, "n_blobs >= 0 with a blob array");
+    if (cfg->coupling != ITOKMC_EXPLICIT && cfg->coupling != ITOKMC_SEMI_IMPLICIT)
+        return fail(nullptr, ITOKMC_ERR_ARG, "coupling: ITOKMC_EXPLICIT or ITOKMC_SEMI_IMPLICIT");
+    if (cfg->coupling == ITOKMC_SEMI_IMPLICIT &&
+        (cfg->precision != ITOKMC_FP64 || (cfg->field_precision != -1 && cfg->field_precision != ITOKMC_FP64)))
+        return fail(nullptr, ITOKMC_ERR_ARG, "semi-implicit coupling: FP64 form only");
 
     itokmc_handle* h = new itokmc_handle();
     h->cfg = *cfg;
@@ -728,53 +805,7 @@ int itokmc_run_stage(itokmc_handle* h, int32_t stage)
 int itokmc_transport_semi_implicit(itokmc_handle* h, int32_t* cycles_out, double* rel_out)
 {
     IK_GUARD(h);
-    ik::Dev& d = h->d;
-    if (d.mixed || d.phi_F > 0)
-        return fail(h, ITOKMC_ERR_ARG, "semi-implicit transport: FP64 form only");
-    // no work of an overlapped field solve may still be in flight
-    IK_CHECK(h, cudaStreamSynchronize(h->s));
-    if (h->sf) IK_CHECK(h, cudaStreamSynchronize(h->sf));
-    int rc = 0;
-    for (int l = 0; l < d.nlev && !rc; ++l)
-        if (!h->semi_c[l]) {
-            const size_t n = (size_t)d.lev[l].n;
-            h->semi_c[l] = dalloc_n<double>(h, (size_t)h->P.R * n * n * n, &rc);
-        }
-    if (rc) return rc;
-    IK_CHECK(h, cudaEventRecord(h->ev[0], h->s));
-    ik::launch_deposit_only(h->P, d, h->N, h->s);       // n_e of the start of the step
-    ik::launch_semi_coef(h->P, d, h->semi_c[0], h->s);
-    ik::launch_diffuse(h->P, d, h->N, h->s);            // X+ into recB
-    ik::launch_deposit_B(h->P, d, h->N, h->s);
-    IK_CHECK(h, cudaMemsetAsync(d.ctr, 0, sizeof(ik::Counters), h->s));
-    ik::launch_rho(h->P, d, h->G, h->s);                // rho+
-    rc = readback(h);
-    if (rc) return rc;
-    rc = status_of_err(h, h->rb->ctr.err);
-    if (rc) return rc;
-    int cycles = 0;
-    double rel = 0.0;
-    const int st = ik::field_solve_vc(h->P, d, h->semi_c, d.norm_out, d.norm_host, h->cfg.mg_rtol, h->cfg.mg_nu1,
-                                      h->cfg.mg_nu2, h->cfg.mg_max_cycles, h->s, &cycles, &rel);
-    if (cycles_out) *cycles_out = cycles;
-    if (rel_out) *rel_out = rel;
-    h->st.mg_cycles = cycles;
-    h->st.mg_rel_residual = rel;
-    if (st == -3) return cuda_check(h, cudaGetLastError(), "semi-implicit field solve");
-    if (st != 0) return fail(h, ITOKMC_ERR_NOCONV, "semi-implicit field: multigrid did not reach mg_rtol");
-    ik::launch_advect(h->P, d, h->N, h->s);
-    ik::launch_transport_finish(h->P, d, h->N, h->G, h->s);
-    ik::launch_rho(h->P, d, h->G, h->s);
-    IK_CHECK(h, cudaEventRecord(h->ev[1], h->s));
-    rc = readback(h);
-    if (rc) return rc;
-    const ik::Counters& c = h->rb->ctr;
-    h->st.n_movers = (int64_t)c.n_movers;
-    int64_t out = 0;
-    for (int r = 0; r < h->P.R; ++r) out += (int64_t)c.outflow[r];
-    h->st.outflow_weight = out;
-    h->st.ms_transport = elapsed(h, 0, 1);
-    return status_of_err(h, c.err);
+    return stage_semi_transport(h, cycles_out, rel_out);
 }
 
 int itokmc_autotune(itokmc_handle* h, itokmc_tuning* out)
@@ -851,7 +882,7 @@ int itokmc_step(itokmc_handle* h, int32_t nsteps)
     IK_GUARD(h);
     if (nsteps < 0) return fail(h, ITOKMC_ERR_ARG, "nsteps < 0");
     for (int k = 0; k < nsteps; ++k) {
-        const int rc = full_step(h);
+        const int rc = h->cfg.coupling == ITOKMC_SEMI_IMPLICIT ? semi_step(h) : full_step(h);
         if (rc) return rc;
         itokmc_advance_counter(h);
     }

@@ -608,28 +608,58 @@ void vcycle(Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
 // poisson_simp): div(c grad phi) with c = 1 + sigma dt / eps0 per cell; the
 // coefficient of an interior face is the mean of its two cells', a boundary
 // face takes the cell's own (Neumann sides: no flux; Dirichlet electrodes:
-// ghost 2 phi_b - phi_1).  With c = 1 it is the operator above.  The
-// systems are scaled by h^2 like the constant-coefficient ones.
-__device__ __forceinline__ double vc_nbr(const double* __restrict__ phi, const double* __restrict__ c, uint64_t idx,
-                                         int n, int i, int j, int k, double& dsum)
+// ghost 2 phi_b - phi_1, i.e. 2 c on the diagonal).  With c = 1 it is the
+// operator above.  The systems are scaled by h^2 like the constant-
+// coefficient ones.  Per level the face coefficients (fx, fy, fz: the +x,
+// +y, +z face of each cell, 0 on the boundary), the diagonal and its
+// inverse are formed once per solve (k_vc_faces), so a smoothing update is
+// six fused multiply-adds and one multiply.
+__global__ void k_vc_faces(const double* __restrict__ c, double* __restrict__ fx, double* __restrict__ fy,
+                           double* __restrict__ fz, double* __restrict__ dg, double* __restrict__ idg, Geo G)
+{
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < G.cells; t += (uint64_t)gridDim.x * blockDim.x) {
+        int r, k, j, i;
+        decode(t, G.log2n, r, k, j, i);
+        const int n = G.n;
+        const uint64_t sy = (uint64_t)n, sz = (uint64_t)n * n;
+        const double ci = c[t];
+        const double xm = i > 0 ? 0.5 * (c[t - 1] + ci) : 0.0, xp = i < n - 1 ? 0.5 * (ci + c[t + 1]) : 0.0;
+        const double ym = j > 0 ? 0.5 * (c[t - sy] + ci) : 0.0, yp = j < n - 1 ? 0.5 * (ci + c[t + sy]) : 0.0;
+        const double zm = k > 0 ? 0.5 * (c[t - sz] + ci) : 2.0 * ci, zp = k < n - 1 ? 0.5 * (ci + c[t + sz]) : 2.0 * ci;
+        fx[t] = xp;
+        fy[t] = yp;
+        fz[t] = k < n - 1 ? zp : 0.0;
+        const double d = ((((xm + xp) + ym) + yp) + zm) + zp;
+        dg[t] = d;
+        idg[t] = 1.0 / d;
+    }
+}
+
+// Off-diagonal sum of the variable-coefficient operator at (k, j, i).
+__device__ __forceinline__ double vcf_sum(const double* __restrict__ phi, const double* __restrict__ fx,
+                                          const double* __restrict__ fy, const double* __restrict__ fz, uint64_t idx,
+                                          int n, int i, int j, int k)
 {
     const uint64_t sy = (uint64_t)n, sz = (uint64_t)n * n;
-    const double ci = c[idx];
-    double s = 0.0, d = 0.0;
-    if (i > 0) { const double cf = 0.5 * (c[idx - 1] + ci); s += cf * phi[idx - 1]; d += cf; }
-    if (i < n - 1) { const double cf = 0.5 * (ci + c[idx + 1]); s += cf * phi[idx + 1]; d += cf; }
-    if (j > 0) { const double cf = 0.5 * (c[idx - sy] + ci); s += cf * phi[idx - sy]; d += cf; }
-    if (j < n - 1) { const double cf = 0.5 * (ci + c[idx + sy]); s += cf * phi[idx + sy]; d += cf; }
-    if (k > 0) { const double cf = 0.5 * (c[idx - sz] + ci); s += cf * phi[idx - sz]; d += cf; }
-    else d += 2.0 * ci;
-    if (k < n - 1) { const double cf = 0.5 * (ci + c[idx + sz]); s += cf * phi[idx + sz]; d += cf; }
-    else d += 2.0 * ci;
-    dsum = d;
+    double s = 0.0;
+    if (i > 0) s = __fma_rn(fx[idx - 1], phi[idx - 1], s);
+    if (i < n - 1) s = __fma_rn(fx[idx], phi[idx + 1], s);
+    if (j > 0) s = __fma_rn(fy[idx - sy], phi[idx - sy], s);
+    if (j < n - 1) s = __fma_rn(fy[idx], phi[idx + sy], s);
+    if (k > 0) s = __fma_rn(fz[idx - sz], phi[idx - sz], s);
+    if (k < n - 1) s = __fma_rn(fz[idx], phi[idx + sz], s);
     return s;
 }
 
-__global__ void k_smooth_vc(double* __restrict__ phi, const double* __restrict__ rhs, const double* __restrict__ c,
-                            Geo G, int color)
+struct VCArrays {        // one level's operator (kernel argument)
+    const double* fx;
+    const double* fy;
+    const double* fz;
+    const double* dg;
+    const double* idg;
+};
+
+__global__ void k_smooth_vc(double* __restrict__ phi, const double* __restrict__ rhs, VCArrays A, Geo G, int color)
 {
     const uint64_t half = G.cells >> 1;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < half; t += (uint64_t)gridDim.x * blockDim.x) {
@@ -640,16 +670,15 @@ __global__ void k_smooth_vc(double* __restrict__ phi, const double* __restrict__
         const uint64_t r = t >> (3 * G.log2n - 1);
         const int i = 2 * ih + ((j + k + color) & 1);
         const uint64_t idx = ((r * n + k) * n + j) * n + i;
-        double d;
-        const double sum = vc_nbr(phi, c, idx, n, i, j, k, d);
-        phi[idx] = (sum - rhs[idx]) / d;
+        const double sum = vcf_sum(phi, A.fx, A.fy, A.fz, idx, n, i, j, k);
+        phi[idx] = (sum - rhs[idx]) * A.idg[idx];
     }
 }
 
 // Residual h^2 (b - A phi) at fine cells, half the sum of 8 children into the
 // coarse right-hand side (the convention of k_resid_restrict).
-__global__ void k_resid_restrict_vc(const double* __restrict__ phi, const double* __restrict__ rhs,
-                                    const double* __restrict__ c, double* __restrict__ rhs_c, Geo Gc, int nf)
+__global__ void k_resid_restrict_vc(const double* __restrict__ phi, const double* __restrict__ rhs, VCArrays A,
+                                    double* __restrict__ rhs_c, Geo Gc, int nf)
 {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < Gc.cells; t += (uint64_t)gridDim.x * blockDim.x) {
         int r, K, J, I;
@@ -659,9 +688,8 @@ __global__ void k_resid_restrict_vc(const double* __restrict__ phi, const double
         for (int q = 0; q < 8; ++q) {
             const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q >> 2);
             const uint64_t idx = (((uint64_t)r * nf + k) * nf + j) * nf + i;
-            double d;
-            const double sum = vc_nbr(phi, c, idx, nf, i, j, k, d);
-            acc += rhs[idx] - (sum - d * phi[idx]);
+            const double sum = vcf_sum(phi, A.fx, A.fy, A.fz, idx, nf, i, j, k);
+            acc += rhs[idx] - __fma_rn(-A.dg[idx], phi[idx], sum);
         }
         rhs_c[t] = acc * 0.5;
     }
@@ -683,13 +711,89 @@ __global__ void k_coef_restrict(const double* __restrict__ cf, double* __restric
     }
 }
 
+// The coarse end of the variable-coefficient V-cycle (levels of at most 16^3
+// cells) in one launch, one block per realization (as k_vcycle_coarse).
+struct CoarseVC {
+    int nlev;
+    int n[MAX_LEVELS];
+    double* phi[MAX_LEVELS];
+    double* rhs[MAX_LEVELS];
+    VCArrays A[MAX_LEVELS];
+};
+
+__device__ void blk_smooth_vc(double* phi, const double* rhs, const VCArrays& A, uint64_t off, int n, int color)
+{
+    const int half = n * n * n / 2;
+    for (int t = threadIdx.x; t < half; t += blockDim.x) {
+        const int ih = t % (n / 2), j = (t / (n / 2)) % n, k = t / (n * n / 2);
+        const int i = 2 * ih + ((j + k + color) & 1);
+        const uint64_t idx = ((uint64_t)k * n + j) * n + i;
+        const double sum = vcf_sum(phi, A.fx + off, A.fy + off, A.fz + off, idx, n, i, j, k);
+        phi[idx] = (sum - rhs[idx]) * A.idg[off + idx];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(512) k_vcycle_coarse_vc(CoarseVC C, int nu1, int nu2, int bottom_sweeps)
+{
+    const uint64_t r = blockIdx.x;
+    auto cells = [&](int l) { return (uint64_t)C.n[l] * C.n[l] * C.n[l]; };
+    const int L = C.nlev - 1;
+    for (int l = 0; l < L; ++l) {
+        const uint64_t off = r * cells(l);
+        double* phi = C.phi[l] + off;
+        const double* rhs = C.rhs[l] + off;
+        for (int it = 0; it < nu1; ++it) {
+            blk_smooth_vc(phi, rhs, C.A[l], off, C.n[l], 0);
+            blk_smooth_vc(phi, rhs, C.A[l], off, C.n[l], 1);
+        }
+        const int nf = C.n[l], nc = nf / 2;
+        const uint64_t offc = r * cells(l + 1);
+        for (int t = threadIdx.x; t < nc * nc * nc; t += blockDim.x) {
+            const int I = t % nc, J = (t / nc) % nc, K = t / (nc * nc);
+            double acc = 0.0;
+            for (int q = 0; q < 8; ++q) {
+                const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q >> 2);
+                const uint64_t idx = ((uint64_t)k * nf + j) * nf + i;
+                const double sum = vcf_sum(phi, C.A[l].fx + off, C.A[l].fy + off, C.A[l].fz + off, idx, nf, i, j, k);
+                acc += rhs[idx] - __fma_rn(-C.A[l].dg[off + idx], phi[idx], sum);
+            }
+            C.rhs[l + 1][offc + t] = acc * 0.5;
+            C.phi[l + 1][offc + t] = 0.0;
+        }
+        __syncthreads();
+    }
+    {
+        const uint64_t off = r * cells(L);
+        for (int it = 0; it < bottom_sweeps; ++it) {
+            blk_smooth_vc(C.phi[L] + off, C.rhs[L] + off, C.A[L], off, C.n[L], 0);
+            blk_smooth_vc(C.phi[L] + off, C.rhs[L] + off, C.A[L], off, C.n[L], 1);
+        }
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        const uint64_t off = r * cells(l);
+        double* phi = C.phi[l] + off;
+        const double* ec = C.phi[l + 1] + r * cells(l + 1);
+        const int nf = C.n[l];
+        for (int t = threadIdx.x; t < nf * nf * nf; t += blockDim.x) {
+            const int i = t % nf, j = (t / nf) % nf, k = t / (nf * nf);
+            phi[t] += prolong_at(ec, nf / 2, i, j, k);
+        }
+        __syncthreads();
+        for (int it = 0; it < nu2; ++it) {
+            blk_smooth_vc(phi, C.rhs[l] + off, C.A[l], off, nf, 1);
+            blk_smooth_vc(phi, C.rhs[l] + off, C.A[l], off, nf, 0);
+        }
+    }
+}
+
 // Squared norms of the residual and of the right-hand side per realization
 // (blockIdx.y): one partial pair per block in part[2 (r gridDim.x + x)],
 // summed in a fixed order by k_norm_final, so the convergence test (and with
 // it the cycle count and the potential) is the same on every run.  256
 // threads per block.
 __global__ void __launch_bounds__(256) k_resid_norm_vc(const double* __restrict__ phi, const double* __restrict__ rhs,
-                                                       const double* __restrict__ c, Geo G, double* __restrict__ part)
+                                                       VCArrays A, Geo G, double* __restrict__ part)
 {
     const uint64_t r = blockIdx.y;
     const uint64_t per = (uint64_t)G.n * G.n * G.n;
@@ -698,9 +802,8 @@ __global__ void __launch_bounds__(256) k_resid_norm_vc(const double* __restrict_
         const uint64_t t = r * per + u;
         int rr, k, j, i;
         decode(t, G.log2n, rr, k, j, i);
-        double d;
-        const double sum = vc_nbr(phi, c, t, G.n, i, j, k, d);
-        const double res = rhs[t] - (sum - d * phi[t]);
+        const double sum = vcf_sum(phi, A.fx, A.fy, A.fz, t, G.n, i, j, k);
+        const double res = rhs[t] - __fma_rn(-A.dg[t], phi[t], sum);
         s0 += res * res;
         s1 += rhs[t] * rhs[t];
     }
@@ -992,31 +1095,86 @@ void launch_phi_to_double(const Params& P, Dev& d, double* out, cudaStream_t s)
 
 
 // ------------------------------------------------------------------ semi-implicit solve
+VCArrays vc_arrays(const Dev& d, int l)
+{
+    const VCLevel& V = d.vc[l];
+    return VCArrays{ V.fx, V.fy, V.fz, V.dg, V.idg };
+}
+
 // One V-cycle of the variable-coefficient system from level l (RB-GS, the
-// colour order of the constant-coefficient cycle; the coarsest level is
-// relaxed by 40 sweep pairs).
-static void vcycle_vc(const Dev& d, double* const* c, int l, int R, int nu1, int nu2, cudaStream_t s)
+// colour order of the constant-coefficient cycle); levels of at most 16^3
+// cells run in the fused coarse kernel, whose coarsest level is relaxed by
+// 48 sweep pairs.
+static void vcycle_vc(const Dev& d, int l, int R, int nu1, int nu2, cudaStream_t s)
 {
     const Geo G = geo(d, l, R);
     double* phi = d.lev[l].phi;
     const double* rhs = d.lev[l].rhs;
     const int tpb = 256;
-    auto sweep = [&](int color) {
+    if (G.n <= COARSE_N && d.nlev - l >= 2) {
+        CoarseVC C{};
+        C.nlev = d.nlev - l;
+        for (int q = 0; q < C.nlev; ++q) {
+            C.n[q] = d.lev[l + q].n;
+            C.phi[q] = d.lev[l + q].phi;
+            C.rhs[q] = d.lev[l + q].rhs;
+            C.A[q] = vc_arrays(d, l + q);
+        }
         ++g_launches;
-        k_smooth_vc<<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, c[l], G, color);
-    };
-    if (l == d.nlev - 1) {
-        for (int it = 0; it < 40; ++it) { sweep(0); sweep(1); }
+        k_vcycle_coarse_vc<<<R, 512, 0, s>>>(C, nu1, nu2, 48);
         return;
     }
+    const VCArrays A = vc_arrays(d, l);
+    auto sweep = [&](int color) {
+        ++g_launches;
+        k_smooth_vc<<<gridsz(G.cells / 2, tpb), tpb, 0, s>>>(phi, rhs, A, G, color);
+    };
     for (int it = 0; it < nu1; ++it) { sweep(0); sweep(1); }
     const Geo Gc = geo(d, l + 1, R);
-    g_launches += 2;
-    k_resid_restrict_vc<<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(phi, rhs, c[l], d.lev[l + 1].rhs, Gc, G.n);
-    cudaMemsetAsync(d.lev[l + 1].phi, 0, Gc.cells * sizeof(double), s);
-    vcycle_vc(d, c, l + 1, R, nu1, nu2, s);
+    g_launches += 3;
+    k_resid_restrict_vc<<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(phi, rhs, A, d.lev[l + 1].rhs, Gc, G.n);
+    k_zero<double><<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(d.lev[l + 1].phi, Gc.cells);
+    vcycle_vc(d, l + 1, R, nu1, nu2, s);
     k_prolong<double><<<gridsz(G.cells, tpb), tpb, 0, s>>>(phi, d.lev[l + 1].phi, G);
     for (int it = 0; it < nu2; ++it) { sweep(1); sweep(0); }
+}
+
+// One variable-coefficient V-cycle from the graph of kind 2 (captured once
+// per smoother pair: the operator arrays keep their addresses).
+static void run_cycle_vc(Dev& d, int R, int nu1, int nu2, cudaStream_t s)
+{
+    const int k = 2;
+    if (d.direct_cycles) { vcycle_vc(d, 0, R, nu1, nu2, s); return; }
+    if (d.vgraph[k] && (d.vgraph_nu[k][0] != nu1 || d.vgraph_nu[k][1] != nu2)) {
+        cudaGraphExecDestroy(d.vgraph[k]);
+        d.vgraph[k] = nullptr;
+    }
+    if (!d.vgraph[k]) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            vcycle_vc(d, 0, R, nu1, nu2, s);
+            return;
+        }
+        const unsigned long long l0 = g_launches.load();
+        vcycle_vc(d, 0, R, nu1, nu2, s);
+        const unsigned long long nk = g_launches.load() - l0;
+        g_launches -= nk;
+        if (cudaStreamEndCapture(s, &g) != cudaSuccess || !g ||
+            cudaGraphInstantiate(&d.vgraph[k], g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            d.vgraph[k] = nullptr;
+            vcycle_vc(d, 0, R, nu1, nu2, s);
+            return;
+        }
+        cudaGraphDestroy(g);
+        d.vgraph_nu[k][0] = nu1;
+        d.vgraph_nu[k][1] = nu2;
+        d.vgraph_kernels[k] = nk;
+    }
+    g_launches += d.vgraph_kernels[k];
+    cudaGraphLaunch(d.vgraph[k], s);
 }
 
 // Coefficients of the semi-implicit field (Sec. 4.7 step 1) into c0 from the
@@ -1032,14 +1190,14 @@ void launch_semi_coef(const Params& P, Dev& d, double* c0, cudaStream_t s)
 }
 
 // Semi-implicit field (Sec. 4.7 step 3, FP64 form): the level-0
-// coefficients in c[0] (launch_semi_coef), restricted to the coarser levels,
-// the right-hand side from d.rho (the charge of the diffused particles), FP64
-// V-cycles until ||r|| <= rtol ||b|| per realization, then E = -grad(phi) into
-// d.E.  c[l] holds one coefficient per cell of level l; acc 2 R doubles of
-// device scratch, acc_host its pinned mirror.  Returns 0, -6 (no
+// coefficients in d.vc[0].c (launch_semi_coef), restricted to the coarser
+// levels, each level's face coefficients and diagonal, the right-hand side
+// from d.rho (the charge of the diffused particles), FP64 V-cycles until
+// ||r|| <= rtol ||b|| per realization, then E = -grad(phi) into d.E.  acc 2 R
+// doubles of device scratch, acc_host its pinned mirror.  Returns 0, -6 (no
 // convergence) or -3 (CUDA error).
-int field_solve_vc(const Params& P, Dev& d, double* const* c, double* acc, double* acc_host, double rtol, int nu1,
-                   int nu2, int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out)
+int field_solve_vc(const Params& P, Dev& d, double* acc, double* acc_host, double rtol, int nu1, int nu2,
+                   int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out)
 {
     const int R = P.R;
     const Geo G0 = geo(d, 0, R);
@@ -1047,20 +1205,27 @@ int field_solve_vc(const Params& P, Dev& d, double* const* c, double* acc, doubl
     for (int l = 0; l + 1 < d.nlev; ++l) {
         const Geo Gc = geo(d, l + 1, R);
         ++g_launches;
-        k_coef_restrict<<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(c[l], c[l + 1], Gc, d.lev[l].n);
+        k_coef_restrict<<<gridsz(Gc.cells, tpb), tpb, 0, s>>>(d.vc[l].c, d.vc[l + 1].c, Gc, d.lev[l].n);
+    }
+    for (int l = 0; l < d.nlev; ++l) {
+        const Geo G = geo(d, l, R);
+        const VCLevel& V = d.vc[l];
+        ++g_launches;
+        k_vc_faces<<<gridsz(G.cells, tpb), tpb, 0, s>>>(V.c, V.fx, V.fy, V.fz, V.dg, V.idg, G);
     }
     double qscale, bc_top;
     rhs_consts(P, qscale, bc_top);
     ++g_launches;
-    k_rhs_vc<<<gridsz(G0.cells, tpb), tpb, 0, s>>>(d.rho, c[0], d.lev[0].rhs, G0, qscale, bc_top,
+    k_rhs_vc<<<gridsz(G0.cells, tpb), tpb, 0, s>>>(d.rho, d.vc[0].c, d.lev[0].rhs, G0, qscale, bc_top,
                                                     P.h[2] * P.h[2]);
+    const VCArrays A0 = vc_arrays(d, 0);
     int cyc = 0, status = -6;
     double worst = 0.0;
     for (cyc = 0; cyc <= max_cycles; ++cyc) {
         g_launches += 2;
         const uint64_t per = G0.cells / (uint64_t)R;
         const dim3 ng((unsigned)gridsz(per, tpb), (unsigned)R);
-        k_resid_norm_vc<<<ng, tpb, 0, s>>>(d.lev[0].phi, d.lev[0].rhs, c[0], G0, d.norm_part);
+        k_resid_norm_vc<<<ng, tpb, 0, s>>>(d.lev[0].phi, d.lev[0].rhs, A0, G0, d.norm_part);
         k_norm_final<<<R, 256, 0, s>>>(d.norm_part, (int)ng.x, R, acc);
         cudaMemcpyAsync(acc_host, acc, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
@@ -1074,7 +1239,7 @@ int field_solve_vc(const Params& P, Dev& d, double* const* c, double* acc, doubl
         }
         if (done) { status = 0; break; }
         if (cyc == max_cycles || !std::isfinite(worst)) break;
-        vcycle_vc(d, c, 0, R, nu1, nu2, s);
+        run_cycle_vc(d, R, nu1, nu2, s);
     }
     if (cycles_out) *cycles_out = cyc;
     if (rel_out) *rel_out = worst;

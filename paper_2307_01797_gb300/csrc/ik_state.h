@@ -70,6 +70,15 @@ struct Counters {
     unsigned long long lost[MAX_R];
 };
 
+// Variable-coefficient operator of one level (semi-implicit field): the cell
+// coefficient c, the coefficients of the +x, +y, +z faces of each cell (0
+// where the face is on the boundary), the diagonal and its inverse.
+struct VCLevel {
+    double* c = nullptr;
+    double* fx = nullptr;  double* fy = nullptr;  double* fz = nullptr;
+    double* dg = nullptr;  double* idg = nullptr;
+};
+
 struct MGLevel {
     int n;                 // cells per axis on this level
     double h;              // cell size
@@ -127,9 +136,10 @@ struct Dev {
     double* stage = nullptr;           // 3 G doubles: field upload/readback
     // CUDA graphs of the correction sweep (FP32: zero + two V-cycles) and of
     // one FP64 V-cycle, captured once per smoother pair and replayed
-    cudaGraphExec_t vgraph[2] = { nullptr, nullptr };
-    int vgraph_nu[2][2] = { { 0, 0 }, { 0, 0 } };
-    unsigned long long vgraph_kernels[2] = { 0, 0 };
+    cudaGraphExec_t vgraph[3] = { nullptr, nullptr, nullptr };
+    int vgraph_nu[3][2] = { { 0, 0 }, { 0, 0 }, { 0, 0 } };
+    unsigned long long vgraph_kernels[3] = { 0, 0, 0 };
+    VCLevel vc[MAX_LEVELS];            // semi-implicit operator per level (allocated on first use)
     bool direct_cycles = false;        // launch the cycles directly (no capture)
     cudaStream_t side = nullptr;       // merge tiers 1 and 2 run beside tier 0
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
@@ -201,8 +211,8 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
 void launch_efield(const Params& P, Dev& d, cudaStream_t s);
 void launch_efield_to(const Params& P, Dev& d, cudaStream_t s, E64* E, float4* E32);
 void launch_semi_coef(const Params& P, Dev& d, double* c0, cudaStream_t s);
-int field_solve_vc(const Params& P, Dev& d, double* const* c, double* acc, double* acc_host, double rtol, int nu1,
-                   int nu2, int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out);
+int field_solve_vc(const Params& P, Dev& d, double* acc, double* acc_host, double rtol, int nu1, int nu2,
+                   int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out);
 void launch_phi_to_double(const Params& P, Dev& d, double* out, cudaStream_t s);
 void launch_pack_field(const Params& P, Dev& d, const double* E3, cudaStream_t s);
 void launch_unpack_field(const Params& P, Dev& d, double* E3, cudaStream_t s);

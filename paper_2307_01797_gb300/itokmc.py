@@ -22,6 +22,7 @@ ITOKMC_OK = 0
 ERR_NAMES = {-1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_CAPACITY", -5: "ERR_OVERFLOW",
              -6: "ERR_NOCONV", -7: "ERR_TIMEOUT", -8: "ERR_POISONED", -9: "ERR_KMC"}
 FP64, MIXED = 0, 1
+EXPLICIT, SEMI_IMPLICIT = 0, 1
 HOST, DEVICE = 0, 1
 NE_FIX, XE, NPOS, NNEG, PHI, E, RHO, FIRINGS = range(8)
 STAGE_TRANSPORT, STAGE_KMC, STAGE_PARTICLES, STAGE_FIELD = range(4)
@@ -46,6 +47,7 @@ class Config(ctypes.Structure):
         ("particle_capacity", ctypes.c_int64), ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
         ("blobs", ctypes.c_void_p), ("n_blobs", ctypes.c_int32), ("seed_flags", ctypes.c_int32),
+        ("coupling", ctypes.c_int32), ("pad0", ctypes.c_int32),
     ]
 
 

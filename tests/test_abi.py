@@ -49,6 +49,17 @@ def test_init_rejects_unknown_precision_without_touching_the_gpu(prec, fprec):
     assert b"precision" in itokmc.lib().itokmc_last_error(None)
 
 
+@pytest.mark.parametrize("prec,coupling", [(1, 1), (0, 2), (0, -1)])
+def test_init_rejects_unsupported_coupling_without_touching_the_gpu(prec, coupling):
+    """The semi-implicit step exists in the FP64 form; unknown couplings are refused."""
+    from paper_2307_01797_gb300 import synth
+    c = itokmc.make_config(synth.physics_small(16), 1000, precision=prec)
+    c.coupling = coupling
+    h = ctypes.c_void_p()
+    assert itokmc.lib().itokmc_init(ctypes.byref(c), ctypes.byref(h)) == -1
+    assert b"coupling" in itokmc.lib().itokmc_last_error(None)
+
+
 def test_struct_layout_matches_header():
     src = r'''
 #include <stdio.h>
@@ -58,7 +69,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(itokmc_config), offsetof(itokmc_config, particle_capacity),
          offsetof(itokmc_config, alloc_ctx), offsetof(itokmc_config, field_precision),
          sizeof(itokmc_stats), offsetof(itokmc_stats, ms_field), offsetof(itokmc_config, blobs),
-         offsetof(itokmc_config, seed_flags), sizeof(itokmc_seed_blob), offsetof(itokmc_seed_blob, realization));
+         offsetof(itokmc_config, coupling), sizeof(itokmc_seed_blob), offsetof(itokmc_seed_blob, realization));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -70,7 +81,7 @@ int main(void) {
     C, S = itokmc.Config, itokmc.Stats
     B = itokmc.SeedBlob
     assert got == [ctypes.sizeof(C), C.particle_capacity.offset, C.alloc_ctx.offset, C.field_precision.offset,
-                   ctypes.sizeof(S), S.ms_field.offset, C.blobs.offset, C.seed_flags.offset, ctypes.sizeof(B),
+                   ctypes.sizeof(S), S.ms_field.offset, C.blobs.offset, C.coupling.offset, ctypes.sizeof(B),
                    B.realization.offset]
 
 
