@@ -449,7 +449,10 @@ def ensemble_study(args):
     independent realizations (member r: Philox key 1 + r) of the 1 cm, 128^3
     physics with photoionization, ppc 16, each seeded on the device from a
     Gaussian blob (sigma 0.5 mm at (L/2, L/2, 0.8 L)) whose peak is
-    log-uniform in [1e17, 1e19] m^-3 (uneven particle counts).  The batched
+    log-uniform in [1e17, 1e19] m^-3 (uneven particle counts), as
+    electron-ion pairs (--electron-seeds: electrons only, whose space charge
+    drives an avalanche that leaves the fixed-point range within a few
+    steps).  The batched
     handle advances all of a rank's members in every launch; the sequential
     runs advance one single-realization handle per member.  Under torchrun
     the members are split R/N per rank (ensemble_partition): no collective
@@ -478,6 +481,7 @@ def ensemble_study(args):
         arr = itokmc.blob_array(blobs)
         cfg.blobs = itokmc.ctypes.cast(arr, itokmc.ctypes.c_void_p)
         cfg.n_blobs = len(blobs)
+        cfg.seed_flags = 0 if args.electron_seeds else itokmc.SEED_NEUTRAL
         return itokmc.Handle(cfg)
 
     def timed(H):
@@ -495,12 +499,14 @@ def ensemble_study(args):
         return time.perf_counter() - t0, done
 
     out = {"study": "ensemble", "grid": args.n, "members": R, "steps": K, "ranks": world, "coupling": args.coupling,
+           "seeds": "electrons" if args.electron_seeds else "electron-ion pairs",
            "members_per_rank": [ensemble_partition(R, world, q)[1] for q in range(world)], "forms": {}}
     # the semi-implicit step exists in the FP64 form
     forms = (("fp64", itokmc.FP64),) if args.coupling == "semi" else (("fp64", itokmc.FP64), ("mixed", itokmc.MIXED))
     for name, form in forms:
         blobs = [dict(center=center, sigma=5e-4, peak=peaks[r], realization=r) for r in range(Rl)]
         H = handle(form, blobs, Rl, 1 + first, 4_000_000 * Rl + 4_000_000)
+        assert H.itokmc_num_particles() > 0
         counts0 = H.itokmc_num_particles()
         tb, done = timed(H)
         counts_end = H.itokmc_num_particles()
@@ -852,6 +858,8 @@ def main():
     ap.add_argument("--physics", default="streamer", choices=["streamer", "tree"],
                     help="transport study: streamer (2 cm, ppc 32) or discharge-tree physics (4 cm, ppc 64)")
     ap.add_argument("--dt-scale", type=float, default=1.0, help="transport study: dt multiplier (sort stress)")
+    ap.add_argument("--electron-seeds", action="store_true",
+                    help="ensemble study: seed electrons only (default: electron-ion pairs)")
     ap.add_argument("--coupling", default="explicit", choices=["explicit", "semi"],
                     help="ensemble study: explicit or semi-implicit field coupling (FP64 form)")
     ap.add_argument("--study-steps", type=int, default=None,
