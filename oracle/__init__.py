@@ -26,16 +26,34 @@ _lib = None
 TAG_INIT, TAG_PUSH, TAG_KMC, TAG_PRODUCT, TAG_PHOTON = 1, 2, 3, 4, 5
 
 
+_OMP_PATH = os.path.join(_HERE, "_build", "liboracle_omp.so")
+_use_omp = False
+
+
 def build(force: bool = False) -> str:
-    """Compile the C oracle with gcc (no FMA contraction, no fast-math)."""
+    """Compile the C oracle with gcc (no FMA contraction, no fast-math), once
+    plain and once with OpenMP (the same arithmetic spread over threads)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
+    for path, extra in ((_LIB_PATH, []), (_OMP_PATH, ["-fopenmp"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+            tmp = path + f".{os.getpid()}.tmp"
+            cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", *extra,
+                   "-shared", "-o", tmp, _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, path)
     return _LIB_PATH
+
+
+def use_openmp(on: bool = True, threads: int | None = None) -> None:
+    """Route the oracle's calls to the OpenMP build (threads: OMP_NUM_THREADS,
+    default every core this process may run on) or back to the plain one."""
+    global _lib, _use_omp
+    with _lock:
+        if bool(on) != _use_omp:
+            _lib = None
+        _use_omp = bool(on)
+        if on:
+            os.environ["OMP_NUM_THREADS"] = str(threads or len(os.sched_getaffinity(0)))
 
 
 class Params(ctypes.Structure):
@@ -89,7 +107,7 @@ def lib():
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_LIB_PATH)
+            L = ctypes.CDLL(_OMP_PATH if _use_omp else _LIB_PATH)
             d, i64, u32, u64, i32 = (ctypes.c_double, ctypes.c_int64, ctypes.c_uint32,
                                      ctypes.c_uint64, ctypes.c_int32)
             pd, pi64, pu32, pu64 = (ctypes.POINTER(d), ctypes.POINTER(i64), ctypes.POINTER(u32),

@@ -35,6 +35,12 @@
  *   photons   a8     -- Sec. 4.5, Eq. photon_transport; Sec. 5.1 kappa(f)
  *   merge     a9     -- Sec. 4.6, Eq. weight_median
  * The field solve (a5) is oracle/poisson.py (numpy, exact separable solve).
+ *
+ * Built twice: plain (one thread) and with -fopenmp (the CPU baseline on
+ * all host cores).  The OpenMP pragmas only spread the independent
+ * iterations of the particle and cell loops over threads (each particle and
+ * each cell draws from its own Philox stream; integer sums are atomic), so
+ * both builds compute the same values; a build without -fopenmp ignores them.
  */
 #include <math.h>
 #include <stdint.h>
@@ -500,6 +506,8 @@ void ora_push(const ora_params* p, int64_t np, const double* x, const double* y,
 {
     double sdt = sqrt((2.0 * p->D) * p->dt);
     double nmu = -p->mu;
+    if (!zig_ready) zig_init();
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < np; ++i) {
         double X[3] = { x[i], y[i], z[i] };
         int ia[3], ib[3];
@@ -598,6 +606,7 @@ void ora_deposit(const ora_params* p, int64_t np, const double* x, const double*
     int s = p->frac_bits;
     int64_t one = (int64_t)1 << s;
     double scale = (double)one;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < np; ++i) {
         double X[3] = { x[i], y[i], z[i] };
         int ia[3], ib[3];
@@ -612,8 +621,12 @@ void ora_deposit(const ora_params* p, int64_t np, const double* x, const double*
         int ix[2] = { ia[0], ib[0] }, iy[2] = { ia[1], ib[1] }, iz[2] = { ia[2], ib[2] };
         for (int c = 0; c < 2; ++c)
             for (int b = 0; b < 2; ++b)
-                for (int a = 0; a < 2; ++a)
-                    ne_fix[lin(p, ix[a], iy[b], iz[c])] += (int64_t)w[i] * A[0][a] * A[1][b] * A[2][c];
+                for (int a = 0; a < 2; ++a) {
+                    int64_t v = (int64_t)w[i] * A[0][a] * A[1][b] * A[2][c];
+#pragma omp atomic
+                    ne_fix[lin(p, ix[a], iy[b], iz[c])] += v;
+                }
+#pragma omp atomic
         Xe[cell[i]] += (int64_t)w[i];
     }
 }
@@ -766,6 +779,7 @@ int ora_kmc(const ora_params* p, const int64_t* Xe, const double* Ex, const doub
 {
     int64_t ncell = (int64_t)p->n * p->n * p->n;
     int status = 0;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(min : status)
     for (int64_t c = 0; c < ncell; ++c) {
         n_ion[c] = n_att[c] = n_ph[c] = 0;
         if (Xe[c] <= 0) continue;
