@@ -436,7 +436,47 @@ def precision_study(args):
         for H in hs.values():
             H.close()
         out["variants"][variant] = {"particles0": N0, "l2_ne": l2_ne, "l2_E": l2_E, "particles": counts}
+    out["variants"]["ensemble"] = precision_ensemble(itokmc, synth, args.members if args.members != 64 else 16,
+                                                     args.study_steps)
     print(json.dumps(out), flush=True)
+
+
+def precision_ensemble(itokmc, synth, R, K):
+    """The mixed form's statistical tolerance: R realizations (keys 1..R) of
+    the small-blob physics on its 64^3 grid in one handle per form, common
+    random numbers, K steps; per step the relative difference of the
+    ensemble-mean electron count, its standard error, and the relative L2
+    differences of the ensemble-mean density and field."""
+    ph = synth.physics_small(64)
+    st = synth.blob_state(ph, seed=1, sigma=5e-4, peak=1e18, zfrac=0.8)
+    N0 = len(st["w"])
+    n3 = ph["n"] ** 3
+    rep = {k: np.tile(np.asarray(st[k]), R) for k in ("x", "y", "z", "w")}
+    real = np.repeat(np.arange(R, dtype=np.int32), N0)
+    hs = {}
+    for name, form in (("fp64", itokmc.FP64), ("mixed", itokmc.MIXED)):
+        H = itokmc.Handle(itokmc.make_config(ph, 8 * R * N0 + 1_000_000, realizations=R, seed0=1, precision=form))
+        H.itokmc_set_particles(rep["x"], rep["y"], rep["z"], rep["w"], real)
+        H.itokmc_solve_field()
+        hs[name] = H
+    rel_total, sem, l2_ne, l2_E = [], [], [], []
+    for k in range(K):
+        for H in hs.values():
+            H.itokmc_step(1)
+        ne = {m: H.itokmc_read_densities(itokmc.NE_FIX, realization=-1).reshape(R, n3).astype(np.float64)
+              for m, H in hs.items()}
+        tot = {m: v.sum(axis=1) for m, v in ne.items()}
+        rel_total.append(float(abs(tot["mixed"].mean() - tot["fp64"].mean()) / tot["fp64"].mean()))
+        sem.append(float(tot["fp64"].std(ddof=1) / np.sqrt(R) / tot["fp64"].mean()))
+        a, b = ne["mixed"].mean(axis=0), ne["fp64"].mean(axis=0)
+        l2_ne.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+        Ea = hs["mixed"].itokmc_read_densities(itokmc.E, realization=-1).reshape(3, R, n3).mean(axis=1)
+        Eb = hs["fp64"].itokmc_read_densities(itokmc.E, realization=-1).reshape(3, R, n3).mean(axis=1)
+        l2_E.append(float(np.linalg.norm(Ea - Eb) / np.linalg.norm(Eb)))
+    for H in hs.values():
+        H.close()
+    return {"realizations": R, "grid": 64, "particles0": N0, "rel_diff_mean_electrons": rel_total,
+            "rel_std_error_mean_electrons": sem, "l2_mean_ne": l2_ne, "l2_mean_E": l2_E}
 
 
 # ------------------------------------------------------------------ ensemble study

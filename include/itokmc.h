@@ -144,7 +144,11 @@ typedef struct itokmc_config {
     int32_t n_blobs;           /* 0: no seeding (particles set by the caller)*/
     int32_t seed_flags;        /* 0 or ITOKMC_SEED_NEUTRAL                   */
     int32_t coupling;          /* ITOKMC_EXPLICIT or ITOKMC_SEMI_IMPLICIT     */
-    int32_t pad0;
+    int32_t dt_adapt;          /* 0: every step dt; 1: adaptive, dt the largest */
+    double dt_min;             /* smallest adaptive step (s)                  */
+    double cfl;                /* drift / diffusion bound (cells per step)    */
+    double drt_factor;         /* dt <= drt eps0/sigma_max (explicit; 0: off) */
+    double ion_factor;         /* k_ion(|E|max) dt <= ion_factor (0: off)     */
 } itokmc_config;
 
 typedef struct itokmc_stats {
@@ -161,6 +165,7 @@ typedef struct itokmc_stats {
     double ms_transport, ms_kmc, ms_particles, ms_field; /* last step (events)*/
     int64_t kernel_launches;   /* kernels launched by the library so far     */
     int64_t merge_cells, merge_elements, merge_elements_sq, merge_max_list; /* last a9 */
+    double dt_last;            /* step size of the last step (s)             */
 } itokmc_stats;
 
 typedef struct itokmc_handle itokmc_handle;
@@ -239,7 +244,21 @@ int itokmc_set_field(itokmc_handle* h, const double* E, int32_t mem);
  * multigrid stops at mg_max_cycles above tolerance. */
 int itokmc_solve_field(itokmc_handle* h);
 
-/* Advances nsteps full steps.  With coupling = ITOKMC_EXPLICIT (a1-a9 then
+/* Adaptive step size (dt_adapt = 1).  The paper runs fixed steps and names
+ * CFL- or physics-based dynamic time stepping as the way to use its
+ * adjustable-accuracy chemistry (Sec. 4.7).  Before each step the step size
+ * becomes dt 2^-j, j the smallest >= 0 for which it satisfies every active
+ * bound, from the field that pushes the particles (its largest |E|) and the
+ * densest cell of the last deposit: mu |E|max dt <= cfl h and 2 D dt <=
+ * (cfl h)^2 (cfl > 0); dt <= drt_factor eps0 / (q_e mu n_max) with the
+ * explicit coupling (drt_factor > 0; the dielectric relaxation time);
+ * alpha(|E|max) mu |E|max dt <= ion_factor (ion_factor > 0).  It never goes
+ * below the largest such step not under dt_min.  Power-of-two steps make the
+ * choice depend only on which side of each bound the candidate falls.  The
+ * Philox counters keep using the step index; itokmc_get_stats reports the
+ * size of the last step.
+ *
+ * Advances nsteps full steps.  With coupling = ITOKMC_EXPLICIT (a1-a9 then
  * a5): particle transport by Eq. ito_kernel with the Euler-Maruyama update
  * of Sec. 4.3 (first equation) in the field of the start of the step,
  * deposition (Sec. 4.2), per-cell KMC (Sec. 3.2.3), products (Sec. 4.4),

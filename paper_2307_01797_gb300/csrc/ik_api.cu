@@ -410,6 +410,49 @@ int full_step(itokmc_handle* h)
     return ITOKMC_OK;
 }
 
+// The adaptive step size (dt_adapt): dt 2^-j, j the smallest >= 0 with the
+// step under every active bound, from the largest |E| of the field that
+// pushes the particles and the densest cell of the last deposit; never
+// below the largest such step not under dt_min.  Sets the step-dependent
+// kernel constants.
+int choose_step(itokmc_handle* h)
+{
+    ik::Params& P = h->P;
+    const itokmc_config& c = h->cfg;
+    double dt = c.dt;
+    if (c.dt_adapt) {
+        unsigned long long* m = reinterpret_cast<unsigned long long*>(h->d.norm_out);   // 2 words of scratch
+        ik::launch_step_maxima(P, h->d, m, h->s);
+        unsigned long long hm[2] = { 0, 0 };
+        IK_CHECK(h, cudaMemcpyAsync(hm, m, sizeof hm, cudaMemcpyDeviceToHost, h->s));
+        IK_CHECK(h, cudaStreamSynchronize(h->s));
+        double Emax;
+        std::memcpy(&Emax, &hm[0], sizeof Emax);
+        const double hcell = P.h[0];
+        double b = INFINITY;
+        if (c.cfl > 0.0 && c.mu * Emax > 0.0) b = std::min(b, c.cfl * hcell / (c.mu * Emax));
+        if (c.cfl > 0.0 && c.D > 0.0) b = std::min(b, (c.cfl * hcell) * (c.cfl * hcell) / (2.0 * c.D));
+        if (c.coupling == ITOKMC_EXPLICIT && c.drt_factor > 0.0 && hm[1] > 0) {
+            const double dV = (hcell * hcell) * hcell;
+            const double nmax = (double)hm[1] * std::ldexp(1.0, -3 * P.frac_bits) / dV;
+            b = std::min(b, c.drt_factor * 8.8541878128e-12 / (1.602176634e-19 * c.mu * nmax));
+        }
+        if (c.ion_factor > 0.0 && Emax > 0.0) {
+            const double k = c.alpha_A * std::exp(-c.alpha_B / Emax) * (c.mu * Emax);
+            if (k > 0.0) b = std::min(b, c.ion_factor / k);
+        }
+        int j = 0;
+        while (j < 62 && std::ldexp(c.dt, -j) > b && std::ldexp(c.dt, -(j + 1)) >= c.dt_min) ++j;
+        dt = std::ldexp(c.dt, -j);
+    }
+    P.dt = dt;
+    P.sdt = sqrt((2.0 * c.D) * dt);
+    P.f_drift = (float)(-c.mu * dt / P.h[0]);
+    P.f_diff = (float)(P.sdt / P.h[0]);
+    h->st.dt_last = dt;
+    return ITOKMC_OK;
+}
+
 // One semi-implicit step (Sec. 4.7): the semi-implicit transport stage
 // solves the field of the end of the step, with which KMC and the particle
 // stages then run; nothing overlaps (the next step's field is solved inside
@@ -495,6 +538,10 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
         return fail(nullptr, ITOKMC_ERR_ARG, "alloc and free_fn must be given together");
     if (cfg->n_blobs < 0 || (cfg->n_blobs > 0 && !cfg->blobs))
         return fail(nullptr, ITOKMC_ERR_ARG, "n_blobs >= 0 with a blob array");
+    if (cfg->dt_adapt != 0 && cfg->dt_adapt != 1) return fail(nullptr, ITOKMC_ERR_ARG, "dt_adapt: 0 or 1");
+    if (cfg->dt_adapt && !(cfg->dt_min > 0.0 && cfg->dt_min <= cfg->dt && cfg->cfl >= 0.0 && cfg->drt_factor >= 0.0 &&
+                           cfg->ion_factor >= 0.0))
+        return fail(nullptr, ITOKMC_ERR_ARG, "adaptive step: 0 < dt_min <= dt, cfl, drt_factor, ion_factor >= 0");
     if (cfg->coupling != ITOKMC_EXPLICIT && cfg->coupling != ITOKMC_SEMI_IMPLICIT)
         return fail(nullptr, ITOKMC_ERR_ARG, "coupling: ITOKMC_EXPLICIT or ITOKMC_SEMI_IMPLICIT");
     if (cfg->coupling == ITOKMC_SEMI_IMPLICIT &&
@@ -509,6 +556,7 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     h->field_prec = cfg->field_precision < 0 ? cfg->precision : cfg->field_precision;
     ik::Params& P = h->P;
     fill_params(cfg, P);
+    h->st.dt_last = cfg->dt;
 
     int rc = 0;
     ik::Dev& d = h->d;
@@ -882,7 +930,8 @@ int itokmc_step(itokmc_handle* h, int32_t nsteps)
     IK_GUARD(h);
     if (nsteps < 0) return fail(h, ITOKMC_ERR_ARG, "nsteps < 0");
     for (int k = 0; k < nsteps; ++k) {
-        const int rc = h->cfg.coupling == ITOKMC_SEMI_IMPLICIT ? semi_step(h) : full_step(h);
+        int rc = h->cfg.dt_adapt ? choose_step(h) : ITOKMC_OK;
+        if (!rc) rc = h->cfg.coupling == ITOKMC_SEMI_IMPLICIT ? semi_step(h) : full_step(h);
         if (rc) return rc;
         itokmc_advance_counter(h);
     }

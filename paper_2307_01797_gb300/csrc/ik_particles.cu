@@ -2304,6 +2304,41 @@ void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
                                           G, qscale, bc_top, P.h[2] * P.h[2], d.ctr);
 }
 
+// Largest |E| (FP64 field, or the FP32 copy of the mixed form) and largest
+// fixed-point electron density over all cells, into m[0], m[1] (zeroed by
+// the caller): the inputs of the adaptive step size.  Non-negative doubles
+// order like their bit patterns, so an integer maximum serves both.
+__global__ void k_step_maxima(const E64* __restrict__ E, const float4* __restrict__ E32,
+                              const unsigned long long* __restrict__ ne, uint64_t G, unsigned long long* __restrict__ m)
+{
+    unsigned long long em = 0, nm = 0;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
+        const double e = E ? E[g].m : (double)__ldg(E32 + g).w;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(e > 0.0 ? e : 0.0);
+        em = b > em ? b : em;
+        const unsigned long long v = ne[g];
+        nm = v > nm ? v : nm;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, em, d), b = __shfl_xor_sync(0xffffffffu, nm, d);
+        em = a > em ? a : em;
+        nm = b > nm ? b : nm;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(m, em);
+        atomicMax(m + 1, nm);
+    }
+}
+
+void launch_step_maxima(const Params& P, Dev& d, unsigned long long* m, cudaStream_t s)
+{
+    const uint64_t G = (uint64_t)P.R * P.n3;
+    cudaMemsetAsync(m, 0, 2 * sizeof(unsigned long long), s);
+    ++g_launches;
+    k_step_maxima<<<grid_for(G, 256), 256, 0, s>>>(d.mixed ? nullptr : d.E, d.mixed ? d.E32 : nullptr, d.ne_fix, G, m);
+}
+
 void launch_kmc0d(const Params& P, bool mixed, double Em, long long X0, uint32_t nreal, int nsteps, long long* X,
                   Counters* ctr, cudaStream_t s)
 {

@@ -190,6 +190,7 @@ void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
 void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
 void launch_zig_init(cudaStream_t s);
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
+void launch_step_maxima(const Params& P, Dev& d, unsigned long long* m, cudaStream_t s);
 void launch_kmc0d(const Params& P, bool mixed, double Em, long long X0, uint32_t nreal, int nsteps, long long* X,
                   Counters* ctr, cudaStream_t s);
 void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s);

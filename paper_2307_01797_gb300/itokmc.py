@@ -47,7 +47,8 @@ class Config(ctypes.Structure):
         ("particle_capacity", ctypes.c_int64), ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
         ("blobs", ctypes.c_void_p), ("n_blobs", ctypes.c_int32), ("seed_flags", ctypes.c_int32),
-        ("coupling", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("coupling", ctypes.c_int32), ("dt_adapt", ctypes.c_int32), ("dt_min", ctypes.c_double),
+        ("cfl", ctypes.c_double), ("drt_factor", ctypes.c_double), ("ion_factor", ctypes.c_double),
     ]
 
 
@@ -82,7 +83,7 @@ class Stats(ctypes.Structure):
         ("mg_rel_residual", ctypes.c_double), ("ms_transport", ctypes.c_double), ("ms_kmc", ctypes.c_double),
         ("ms_particles", ctypes.c_double), ("ms_field", ctypes.c_double),
         ("kernel_launches", ctypes.c_int64), ("merge_cells", ctypes.c_int64), ("merge_elements", ctypes.c_int64),
-        ("merge_elements_sq", ctypes.c_int64), ("merge_max_list", ctypes.c_int64),
+        ("merge_elements_sq", ctypes.c_int64), ("merge_max_list", ctypes.c_int64), ("dt_last", ctypes.c_double),
     ]
 
     def as_dict(self):
