@@ -66,7 +66,7 @@ class Params(ctypes.Structure):
         ("alpha_A", ctypes.c_double), ("alpha_B", ctypes.c_double), ("eta", ctypes.c_double),
         ("photon_ratio", ctypes.c_double), ("kappa_lo", ctypes.c_double), ("kappa_hi", ctypes.c_double),
         ("eps", ctypes.c_double), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint32),
-        ("pad", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32), ("beta_ep", ctypes.c_double), ("beta_np", ctypes.c_double),
     ]
 
 
@@ -93,6 +93,8 @@ def make_params(phys: dict, seed: int, step: int = 0) -> Params:
     p.kappa_lo = float(phys.get("kappa_lo", 520.0))
     p.kappa_hi = float(phys.get("kappa_hi", 3.0e4))
     p.eps = float(phys.get("eps", float("inf")))
+    p.beta_ep = float(phys.get("beta_ep", 0.0))
+    p.beta_np = float(phys.get("beta_np", 0.0))
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     p.step = int(step) & 0xFFFFFFFF
     return p
@@ -125,10 +127,12 @@ def lib():
             L.ora_advect.argtypes = [pp, i64, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pi64]
             L.ora_sort_by_cell.argtypes = [i64, i64, pi64, pi64]; L.ora_sort_by_cell.restype = i64
             L.ora_deposit.argtypes = [pp, i64, pd, pd, pd, pu32, pi64, pi64, pi64]
-            L.ora_kmc.argtypes = [pp, pi64, pd, pd, pd, pi64, pi64, pi64]; L.ora_kmc.restype = ctypes.c_int
+            L.ora_kmc.argtypes = [pp, pi64, pi64, pi64, pd, pd, pd, pi64, pi64, pi64, pi64, pi64]
+            L.ora_kmc.restype = ctypes.c_int
             L.ora_kmc_single.argtypes = [pp, i64, d, d, d, u32, pi64]; L.ora_kmc_single.restype = i64
+            L.ora_kmc_network.argtypes = [pp, pi64, pd, u32, pi64, pi64]; L.ora_kmc_network.restype = ctypes.c_int
             L.ora_products_photons.argtypes = [pp, i64, pd, pd, pd, pu32, pi64, pi64, pi64, pi64, pi64,
-                                               pi64, pi64, pd, pd, pd, pu32, pi64, i64, pi64]
+                                               pi64, pi64, pi64, pi64, pd, pd, pd, pu32, pi64, i64, pi64]
             L.ora_products_photons.restype = i64
             L.ora_merge.argtypes = [pp, pd, pd, pd, pu32, pi64, pd, pd, pd, pu32, pi64, i64]
             L.ora_merge.restype = i64
@@ -194,6 +198,21 @@ def kmc_single(params: Params, X0: int, k_ion: float, k_att: float, k_ph: float,
     X = lib().ora_kmc_single(ctypes.byref(params), int(X0), float(k_ion), float(k_att), float(k_ph),
                              int(index), _P(fired, ctypes.c_int64))
     return int(X), fired
+
+
+def kmc_network(params: Params, X0, kr, index: int):
+    """One cell of the five-reaction network (Sec. 5.1): counts X0 = (X_e,
+    X_+, X_-), frequencies kr = (k_alpha, k_eta, k_gamma, k_ep, k_np), stream
+    (index, params.step, KMC).  Returns (X[3], fired[5])."""
+    X0 = np.ascontiguousarray(X0, dtype=np.int64)
+    kr = np.ascontiguousarray(kr, dtype=np.float64)
+    assert X0.shape == (3,) and kr.shape == (5,)
+    X = np.zeros(3, np.int64)
+    fired = np.zeros(5, np.int64)
+    if lib().ora_kmc_network(ctypes.byref(params), _P(X0, ctypes.c_int64), _P(kr, ctypes.c_double),
+                             int(index), _P(X, ctypes.c_int64), _P(fired, ctypes.c_int64)) != 0:
+        raise RuntimeError("kmc_network: iteration guard")
+    return X, fired
 
 
 def photon_samples(params: Params, i: int, j: int, k: int, m: int):

@@ -67,6 +67,8 @@ typedef struct {
     uint64_t seed;        /* Philox key of this realization                 */
     uint32_t step;        /* step counter k (part of every Philox counter)  */
     uint32_t pad;
+    double beta_ep;       /* electron-ion recombination coefficient m^3/s   */
+    double beta_np;       /* ion-ion recombination coefficient m^3/s        */
 } ora_params;
 
 enum { TAG_INIT = 1, TAG_PUSH = 2, TAG_KMC = 3, TAG_PRODUCT = 4, TAG_PHOTON = 5 };
@@ -633,60 +635,89 @@ void ora_deposit(const ora_params* p, int64_t np, const double* x, const double*
 
 /* ------------------------------------------------------------------------ */
 /* a6: per-cell KMC, Sec. 3.2.3 steps 1-8 (Cao, Gillespie, Petzold 2005,     */
-/* 2006) for the first-order network of Table air_reactions restricted to    */
-/*   r=0 ionization  e -> 2e + M+   a0 = k_alpha X   nu_e = +1               */
-/*   r=1 attachment  e -> M-        a1 = k_eta X     nu_e = -1               */
-/*   r=2 photon      e -> e + gamma a2 = k_gamma X   nu_e =  0               */
+/* 2006) for the network of Table air_reactions.  State (X_e, X_+, X_-) =    */
+/* electrons, positive and negative ions of the cell; reactions             */
+/*   r=0 ionization     e -> 2e + M+    a0 = k_alpha X_e       nu = (+1,+1, 0) */
+/*   r=1 attachment     e -> M-         a1 = k_eta X_e         nu = (-1, 0,+1) */
+/*   r=2 photon         e -> e + gamma  a2 = k_gamma X_e       nu = ( 0, 0, 0) */
+/*   r=3 e-ion recomb.  e + M+ -> 0     a3 = k_ep X_e X_+      nu = (-1,-1, 0) */
+/*   r=4 ion-ion recomb M- + M+ -> 0    a4 = k_np X_+ X_-      nu = ( 0,-1,-1) */
 /* with k_alpha = alpha(|E|) mu |E|, k_eta = eta mu |E|, k_gamma =           */
-/* photon_ratio k_alpha (Sec. 5.1 structure).  Readings: critical set =     */
-/* reactions within N_c firings of exhausting a reactant (only attachment,   */
-/* when X < N_c); dt_c = -ln(u)/A_c; dt_nc from the eps formula (infinite    */
-/* for eps = inf); the SSA switch (A dtau <= 1, dtau = min(dt - tau, dt_nc)) */
-/* is tested before the critical time is drawn, as in the cited Cao et al.   */
-/* (2006) procedure -- testing it after a critical draw that did not fire    */
-/* would count critical firings twice; a rejected substep sets dt_nc =       */
-/* dtau/2 and redoes step 5 with fresh draws (the critical time is kept);    */
-/* the SSA branch runs at most N_SSA events and advances tau by the full     */
-/* dtau if the next event falls beyond it, else by the time of the last      */
-/* event.  Draws come from the stream (index = cell, step, KMC).             */
-/* Outputs per cell: firings of each reaction.                               */
+/* photon_ratio k_alpha (Sec. 5.1 structure) and k_ep = beta_ep / dV,        */
+/* k_np = beta_np / dV (Sec. 5.1, dV = the cell volume); with beta = 0 the   */
+/* last two never fire and the network is the first-order one.  Readings:   */
+/* a reaction with a positive propensity is critical when it is within N_c  */
+/* firings of exhausting a reactant (attachment: X_e < N_c; e-ion           */
+/* recombination: min(X_e, X_+) < N_c; ion-ion: min(X_+, X_-) < N_c);       */
+/* dt_c = -ln(u)/A_c; dt_nc from the eps formula over the reactant species  */
+/* of the non-critical reactions, g_i = 2 for a species that is a reactant  */
+/* of a second-order reaction with a positive coefficient (distinct         */
+/* reactants, Cao et al. 2006), else 1 (infinite for eps = inf); the SSA    */
+/* switch (A dtau <= 1, dtau = min(dt - tau, dt_nc)) is tested before the   */
+/* critical time is drawn, as in the cited Cao et al. (2006) procedure --   */
+/* testing it after a critical draw that did not fire would count critical  */
+/* firings twice; a substep that leaves any count negative is rejected,     */
+/* dt_nc = dtau/2 and step 5 is redone with fresh draws (the critical time  */
+/* is kept); the SSA branch runs at most N_SSA events and advances tau by   */
+/* the full dtau if the next event falls beyond it, else by the time of the */
+/* last event.  Draws come from the stream (index = cell, step, KMC).       */
+/* Outputs per cell: firings of each reaction.                              */
 /* ------------------------------------------------------------------------ */
-static int kmc_cell(const ora_params* p, ora_stream* s, int64_t X0, double kr[3],
-                    int64_t fired[3])
+static const int kmc_nu[5][3] = { { +1, +1, 0 }, { -1, 0, +1 }, { 0, 0, 0 }, { -1, -1, 0 }, { 0, -1, -1 } };
+
+static void kmc_props(const double kr[5], const int64_t X[3], double a[5])
 {
-    static const int nu[3] = { +1, -1, 0 };
-    int64_t X = X0;
+    double xe = (double)X[0], xp = (double)X[1], xm = (double)X[2];
+    a[0] = kr[0] * xe;
+    a[1] = kr[1] * xe;
+    a[2] = kr[2] * xe;
+    a[3] = (kr[3] * xe) * xp;
+    a[4] = (kr[4] * xp) * xm;
+}
+
+static int kmc_cell(const ora_params* p, ora_stream* s, const int64_t X0[3], const double kr[5],
+                    int64_t fired[5])
+{
+    int64_t X[3] = { X0[0], X0[1], X0[2] };
     double dt = p->dt;
     double tau = 0.0;
-    fired[0] = fired[1] = fired[2] = 0;
+    /* g_i: 2 for a reactant of a second-order reaction present in the network */
+    double g[3] = { kr[3] > 0.0 ? 2.0 : 1.0, (kr[3] > 0.0 || kr[4] > 0.0) ? 2.0 : 1.0, kr[4] > 0.0 ? 2.0 : 1.0 };
+    for (int r = 0; r < 5; ++r) fired[r] = 0;
     for (int guard = 0; guard < 100000; ++guard) {
         if (!(tau < dt)) return 0;
-        double xd = (double)X;
-        double a[3] = { kr[0] * xd, kr[1] * xd, kr[2] * xd };
-        double A = (a[0] + a[1]) + a[2];
+        double a[5];
+        kmc_props(kr, X, a);
+        double A = (((a[0] + a[1]) + a[2]) + a[3]) + a[4];
         if (!(A > 0.0)) return 0;
-        /* step 1: partition (only attachment can exhaust its reactant) */
-        int crit[3] = { 0, X < (int64_t)p->n_crit, 0 };
+        /* step 1: partition by the firings left before a reactant runs out */
+        int64_t L3 = X[0] < X[1] ? X[0] : X[1], L4 = X[1] < X[2] ? X[1] : X[2];
+        int crit[5] = { 0, a[1] > 0.0 && X[0] < (int64_t)p->n_crit, 0, a[3] > 0.0 && L3 < (int64_t)p->n_crit,
+                        a[4] > 0.0 && L4 < (int64_t)p->n_crit };
         /* step 2 */
         double Ac = 0.0;
-        for (int r = 0; r < 3; ++r) if (crit[r]) Ac = Ac + a[r];
+        for (int r = 0; r < 5; ++r) if (crit[r]) Ac = Ac + a[r];
         /* step 4: non-critical step bound from eps (infinite for eps = inf) */
         double dtnc = INFINITY;
         if (!isinf(p->eps)) {
-            double xi = 0.0, sig2 = 0.0;
-            int any = 0;
-            for (int r = 0; r < 3; ++r) {
-                if (crit[r]) continue;
-                any = 1;
-                xi = xi + (double)nu[r] * a[r];
-                sig2 = sig2 + (double)(nu[r] * nu[r]) * a[r];
-            }
-            if (any) {
-                double num = p->eps * xd;
+            /* reactant species of the non-critical reactions: the electrons */
+            /* (ionization is never critical), the ions through the          */
+            /* recombinations present in the network (beta > 0)             */
+            int reactant[3] = { 1, (!crit[3] && kr[3] > 0.0) || (!crit[4] && kr[4] > 0.0), !crit[4] && kr[4] > 0.0 };
+            for (int i = 0; i < 3; ++i) {
+                if (!reactant[i]) continue;
+                double xi = 0.0, sig2 = 0.0;
+                for (int r = 0; r < 5; ++r) {
+                    if (crit[r]) continue;
+                    xi = xi + (double)kmc_nu[r][i] * a[r];
+                    sig2 = sig2 + (double)(kmc_nu[r][i] * kmc_nu[r][i]) * a[r];
+                }
+                double num = (p->eps * (double)X[i]) / g[i];
                 if (num < 1.0) num = 1.0;
                 double t1 = (xi != 0.0) ? num / fabs(xi) : INFINITY;
                 double t2 = (sig2 != 0.0) ? (num * num) / sig2 : INFINITY;
-                dtnc = t1 < t2 ? t1 : t2;
+                double ti = t1 < t2 ? t1 : t2;
+                if (ti < dtnc) dtnc = ti;
             }
         }
         /* step 3 is drawn lazily (only when a leap is taken) and kept across */
@@ -695,31 +726,31 @@ static int kmc_cell(const ora_params* p, ora_stream* s, int64_t X0, double kr[3]
         for (int rej = 0; rej < 10000; ++rej) {
             double rem = dt - tau;
             double dtau = dtnc < rem ? dtnc : rem;
-            int64_t k[3] = { 0, 0, 0 };
+            int64_t k[5] = { 0, 0, 0, 0, 0 };
             double adv;
             if (A * dtau <= 1.0) {
                 /* step 6b exception, checked before the critical draw as in  */
                 /* Cao et al. (2006): SSA on the whole network, at most N_SSA */
                 /* events within dtau; tau advances by dtau if the next event */
                 /* falls beyond it, else by the time of the last event.       */
-                int64_t Xs = X;
+                int64_t Xs[3] = { X[0], X[1], X[2] };
                 double t = 0.0;
                 for (int ev = 0; ev < p->n_ssa; ++ev) {
-                    double xs = (double)Xs;
-                    double as[3] = { kr[0] * xs, kr[1] * xs, kr[2] * xs };
-                    double As = (as[0] + as[1]) + as[2];
+                    double as[5];
+                    kmc_props(kr, Xs, as);
+                    double As = (((as[0] + as[1]) + as[2]) + as[3]) + as[4];
                     if (!(As > 0.0)) { t = dtau; break; }
                     double dte = (-ora_log(stream_uniform(s))) / As;
                     if (t + dte > dtau) { t = dtau; break; }
                     t = t + dte;
                     double target = stream_uniform(s) * As, cum = 0.0;
-                    int j = 2;
-                    for (int r = 0; r < 3; ++r) {
+                    int j = (as[3] > 0.0 || as[4] > 0.0) ? (as[4] > 0.0 ? 4 : 3) : 2;
+                    for (int r = 0; r < 5; ++r) {
                         cum = cum + as[r];
                         if (cum > target) { j = r; break; }
                     }
                     k[j] += 1;
-                    Xs += nu[j];
+                    for (int i = 0; i < 3; ++i) Xs[i] += kmc_nu[j][i];
                 }
                 adv = t;
             } else {
@@ -731,7 +762,7 @@ static int kmc_cell(const ora_params* p, ora_stream* s, int64_t X0, double kr[3]
                     dtau = dtc;
                     double target = stream_uniform(s) * Ac, cum = 0.0;
                     int rc = -1, last = -1;
-                    for (int r = 0; r < 3; ++r) {
+                    for (int r = 0; r < 5; ++r) {
                         if (!crit[r]) continue;
                         last = r;
                         cum = cum + a[r];
@@ -741,18 +772,20 @@ static int kmc_cell(const ora_params* p, ora_stream* s, int64_t X0, double kr[3]
                     k[rc] += 1;
                 }
                 /* step 6a/6b: non-critical tau-leap over dtau (Eq. tau_leaping) */
-                for (int r = 0; r < 3; ++r)
+                for (int r = 0; r < 5; ++r)
                     if (!crit[r]) k[r] += ora_poisson(s, a[r] * dtau);
                 adv = dtau;
             }
-            int64_t Xn = X + k[0] - k[1];
-            if (Xn < 0) {                 /* step 7a: reject, halve, redo step 5 */
+            int64_t Xn[3];
+            for (int i = 0; i < 3; ++i)
+                Xn[i] = X[i] + kmc_nu[0][i] * k[0] + kmc_nu[1][i] * k[1] + kmc_nu[3][i] * k[3] + kmc_nu[4][i] * k[4];
+            if (Xn[0] < 0 || Xn[1] < 0 || Xn[2] < 0) {   /* step 7a: reject, halve, redo step 5 */
                 dtnc = dtau * 0.5;
                 continue;
             }
             /* step 7b: accept */
-            X = Xn;
-            fired[0] += k[0]; fired[1] += k[1]; fired[2] += k[2];
+            for (int i = 0; i < 3; ++i) X[i] = Xn[i];
+            for (int r = 0; r < 5; ++r) fired[r] += k[r];
             if (adv >= rem) tau = dt; else tau = tau + adv;
             goto next_substep;
         }
@@ -773,23 +806,44 @@ static void rates_at(const ora_params* p, double ex, double ey, double ez, doubl
     kr[2] = p->photon_ratio * kr[0];
 }
 
-/* Returns 0, or -1 if some cell did not finish (iteration guard). */
-int ora_kmc(const ora_params* p, const int64_t* Xe, const double* Ex, const double* Ey,
-            const double* Ez, int64_t* n_ion, int64_t* n_att, int64_t* n_ph)
+/* Recombination frequencies per pair: k = beta / dV (Sec. 5.1). */
+static void recomb_rates(const ora_params* p, double* k_ep, double* k_np)
+{
+    double dV = (cell_h(p, 0) * cell_h(p, 1)) * cell_h(p, 2);
+    *k_ep = p->beta_ep / dV;
+    *k_np = p->beta_np / dV;
+}
+
+/* Npos, Nneg: the ion counts at the start of the chemistry (NULL: none);  */
+/* n_ep, n_np: recombination firings (NULL: not wanted).  A cell runs when  */
+/* it has electrons, or ions of both signs with ion-ion recombination on.  */
+/* Returns 0, or -1 if some cell did not finish (iteration guard).          */
+int ora_kmc(const ora_params* p, const int64_t* Xe, const int64_t* Npos, const int64_t* Nneg,
+            const double* Ex, const double* Ey, const double* Ez, int64_t* n_ion, int64_t* n_att,
+            int64_t* n_ph, int64_t* n_ep, int64_t* n_np)
 {
     int64_t ncell = (int64_t)p->n * p->n * p->n;
     int status = 0;
+    double k_ep, k_np;
+    recomb_rates(p, &k_ep, &k_np);
 #pragma omp parallel for schedule(dynamic, 4096) reduction(min : status)
     for (int64_t c = 0; c < ncell; ++c) {
         n_ion[c] = n_att[c] = n_ph[c] = 0;
-        if (Xe[c] <= 0) continue;
-        double kr[3];
+        if (n_ep) n_ep[c] = 0;
+        if (n_np) n_np[c] = 0;
+        int64_t X[3] = { Xe[c], Npos ? Npos[c] : 0, Nneg ? Nneg[c] : 0 };
+        if (X[0] <= 0 && !(k_np > 0.0 && X[1] > 0 && X[2] > 0)) continue;
+        double kr[5];
         rates_at(p, Ex[c], Ey[c], Ez[c], kr);
+        kr[3] = k_ep;
+        kr[4] = k_np;
         ora_stream s;
         stream_init(&s, p->seed, (uint32_t)c, p->step, TAG_KMC, 0);
-        int64_t fired[3];
-        if (kmc_cell(p, &s, Xe[c], kr, fired) != 0) status = -1;
+        int64_t fired[5];
+        if (kmc_cell(p, &s, X, kr, fired) != 0) status = -1;
         n_ion[c] = fired[0]; n_att[c] = fired[1]; n_ph[c] = fired[2];
+        if (n_ep) n_ep[c] = fired[3];
+        if (n_np) n_np[c] = fired[4];
     }
     return status;
 }
@@ -799,11 +853,29 @@ int ora_kmc(const ora_params* p, const int64_t* Xe, const double* Ex, const doub
 int64_t ora_kmc_single(const ora_params* p, int64_t X0, double k_ion, double k_att, double k_ph,
                        uint32_t index, int64_t* fired)
 {
-    double kr[3] = { k_ion, k_att, k_ph };
+    double kr[5] = { k_ion, k_att, k_ph, 0.0, 0.0 };
+    int64_t X[3] = { X0, 0, 0 }, f[5];
+    ora_stream s;
+    stream_init(&s, p->seed, index, p->step, TAG_KMC, 0);
+    if (kmc_cell(p, &s, X, kr, f) != 0) return -1;
+    fired[0] = f[0]; fired[1] = f[1]; fired[2] = f[2];
+    return X0 + fired[0] - fired[1];
+}
+
+/* Exported for the oracle's pins: one cell of the whole network (counts   */
+/* X0 = (X_e, X_+, X_-), frequencies kr[5]) on stream (index, step, KMC);   */
+/* the final counts in X[3], firings in fired[5].  Returns 0 or -1 (guard). */
+int ora_kmc_network(const ora_params* p, const int64_t* X0, const double* kr, uint32_t index,
+                    int64_t* X, int64_t* fired)
+{
     ora_stream s;
     stream_init(&s, p->seed, index, p->step, TAG_KMC, 0);
     if (kmc_cell(p, &s, X0, kr, fired) != 0) return -1;
-    return X0 + fired[0] - fired[1];
+    for (int i = 0; i < 3; ++i) {
+        X[i] = X0[i];
+        for (int r = 0; r < 5; ++r) X[i] += kmc_nu[r][i] * fired[r];
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -884,7 +956,8 @@ void ora_photon_samples(const ora_params* p, int32_t i, int32_t j, int32_t k, in
 int64_t ora_products_photons(const ora_params* p, int64_t np, const double* x, const double* y,
                              const double* z, uint32_t* w, const int64_t* cell_start,
                              const int64_t* Xe, const int64_t* n_ion, const int64_t* n_att,
-                             const int64_t* n_ph, int64_t* Npos, int64_t* Nneg,
+                             const int64_t* n_ph, const int64_t* n_ep, const int64_t* n_np,
+                             int64_t* Npos, int64_t* Nneg,
                              double* nx, double* ny, double* nz, uint32_t* nw, int64_t* ncell_new,
                              int64_t cap_new, int64_t* lost_photon_weight)
 {
@@ -897,9 +970,10 @@ int64_t ora_products_photons(const ora_params* p, int64_t np, const double* x, c
     for (int64_t c = 0; c < ncell; ++c) {
         int ci = (int)(c % p->n), cj = (int)((c / p->n) % p->n), ck = (int)(c / ((int64_t)p->n * p->n));
         int ijk[3] = { ci, cj, ck };
-        int64_t dN = n_ion[c] - n_att[c];
-        Npos[c] += n_ion[c];
-        Nneg[c] += n_att[c];
+        int64_t ep = n_ep ? n_ep[c] : 0, npr = n_np ? n_np[c] : 0;
+        int64_t dN = n_ion[c] - n_att[c] - ep;
+        Npos[c] += n_ion[c] - ep - npr;
+        Nneg[c] += n_att[c] - npr;
         if (dN > 0) {
             int64_t m = dN < p->n_new ? dN : p->n_new;
             int64_t wq = dN / m, rem = dN % m;
@@ -1266,19 +1340,21 @@ int64_t ora_seed_blobs(const ora_params* p, int32_t nb, const double* centers, c
 /* ------------------------------------------------------------------------ */
 int ora_kmc0d(const ora_params* p, double E_mag, int64_t X0, int32_t n_real, int32_t n_steps, int64_t* X)
 {
-    double kr[3];
+    double kr[5];
     rates_at(p, 0.0, 0.0, -E_mag, kr);
+    kr[3] = kr[4] = 0.0;              /* the first-order network (no ion counts tracked) */
     int status = 0;
     for (int32_t m = 0; m < n_real; ++m) {
         int64_t x = X0;
         int64_t* out = X + (int64_t)m * (n_steps + 1);
         out[0] = x;
         for (int32_t k = 0; k < n_steps; ++k) {
-            int64_t fired[3] = { 0, 0, 0 };
+            int64_t fired[5] = { 0, 0, 0, 0, 0 };
             if (x > 0) {
+                int64_t X[3] = { x, 0, 0 };
                 ora_stream s;
                 stream_init(&s, p->seed, (uint32_t)m, (uint32_t)k, TAG_KMC, 0);
-                if (kmc_cell(p, &s, x, kr, fired) != 0) status = -1;
+                if (kmc_cell(p, &s, X, kr, fired) != 0) status = -1;
             }
             x += fired[0] - fired[1];
             out[k + 1] = x;

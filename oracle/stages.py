@@ -63,18 +63,25 @@ def deposit(p: Params, x, y, z, w, cell):
     return ne, Xe
 
 
-def kmc(p: Params, Xe, E):
-    """a6.  Returns (n_ion, n_att, n_ph) firings per cell."""
+def kmc(p: Params, Xe, E, Npos=None, Nneg=None):
+    """a6.  Returns the firings per cell (n_ion, n_att, n_ph, n_ep, n_np):
+    ionization, attachment, photon emission, electron-ion and ion-ion
+    recombination (the last two zero unless p.beta_ep / p.beta_np > 0, which
+    need the ion counts Npos, Nneg at the start of the chemistry)."""
     ncell = p.n ** 3
     Xe = np.ascontiguousarray(Xe, dtype=np.int64)
     Ex, Ey, Ez = (_d(np.asarray(e).ravel()) for e in E)
-    a, b, c = (np.zeros(ncell, dtype=np.int64) for _ in range(3))
-    st = lib().ora_kmc(ctypes.byref(p), _P(Xe, ctypes.c_int64), _P(Ex, ctypes.c_double),
-                       _P(Ey, ctypes.c_double), _P(Ez, ctypes.c_double), _P(a, ctypes.c_int64),
-                       _P(b, ctypes.c_int64), _P(c, ctypes.c_int64))
+    a, b, c, d, e = (np.zeros(ncell, dtype=np.int64) for _ in range(5))
+    zero = np.zeros(ncell, dtype=np.int64)
+    Np = np.ascontiguousarray(Npos if Npos is not None else zero, dtype=np.int64)
+    Nn = np.ascontiguousarray(Nneg if Nneg is not None else zero, dtype=np.int64)
+    st = lib().ora_kmc(ctypes.byref(p), _P(Xe, ctypes.c_int64), _P(Np, ctypes.c_int64), _P(Nn, ctypes.c_int64),
+                       _P(Ex, ctypes.c_double), _P(Ey, ctypes.c_double), _P(Ez, ctypes.c_double),
+                       _P(a, ctypes.c_int64), _P(b, ctypes.c_int64), _P(c, ctypes.c_int64),
+                       _P(d, ctypes.c_int64), _P(e, ctypes.c_int64))
     if st != 0:
         raise RuntimeError("oracle KMC iteration guard hit")
-    return a, b, c
+    return a, b, c, d, e
 
 
 def cell_start_of(cell, ncell):
@@ -86,7 +93,10 @@ def products_photons(p: Params, x, y, z, w, cell, Xe, fired, Npos, Nneg):
     Returns (new particle arrays (x, y, z, w, cell), lost photon weight)."""
     ncell = p.n ** 3
     cs = cell_start_of(cell, ncell)
-    n_ion, n_att, n_ph = (np.ascontiguousarray(f, dtype=np.int64) for f in fired)
+    n_ion, n_att, n_ph = (np.ascontiguousarray(f, dtype=np.int64) for f in fired[:3])
+    zero = np.zeros(ncell, dtype=np.int64)
+    n_ep = np.ascontiguousarray(fired[3], dtype=np.int64) if len(fired) > 3 else zero
+    n_np = np.ascontiguousarray(fired[4], dtype=np.int64) if len(fired) > 4 else zero
     cap = int(np.minimum(n_ion + n_ph, 2 * p.n_new).sum()) + 16
     nx, ny, nz = np.empty(cap), np.empty(cap), np.empty(cap)
     nw = np.empty(cap, dtype=np.uint32)
@@ -100,6 +110,7 @@ def products_photons(p: Params, x, y, z, w, cell, Xe, fired, Npos, Nneg):
                                    _P(z, ctypes.c_double), _P(w, ctypes.c_uint32), _P(cs, ctypes.c_int64),
                                    _P(Xe, ctypes.c_int64), _P(n_ion, ctypes.c_int64),
                                    _P(n_att, ctypes.c_int64), _P(n_ph, ctypes.c_int64),
+                                   _P(n_ep, ctypes.c_int64), _P(n_np, ctypes.c_int64),
                                    _P(Npos, ctypes.c_int64), _P(Nneg, ctypes.c_int64),
                                    _P(nx, ctypes.c_double), _P(ny, ctypes.c_double), _P(nz, ctypes.c_double),
                                    _P(nw, ctypes.c_uint32), _P(nc, ctypes.c_int64), cap, ctypes.byref(lost))
@@ -160,7 +171,7 @@ def after_transport(p: Params, state: dict, xo, yo, zo, cnew, E):
     Npos = np.array(state["Npos"], dtype=np.int64, copy=True)
     Nneg = np.array(state["Nneg"], dtype=np.int64, copy=True)
     rho = rho_fixed(p, ne, Npos, Nneg)
-    fired = kmc(p, Xe, E)
+    fired = kmc(p, Xe, E, Npos, Nneg)
     sorted_state = dict(x=sx.copy(), y=sy.copy(), z=sz.copy(), w=sw.copy(), cell=sc.copy())
     new, lost = products_photons(p, sx, sy, sz, sw, sc, Xe, fired, Npos, Nneg)
     ax = np.concatenate([sx, new[0]]); ay = np.concatenate([sy, new[1]])
@@ -170,6 +181,6 @@ def after_transport(p: Params, state: dict, xo, yo, zo, cnew, E):
     mx, my, mz, mw, mc = merge(p, ax[order], ay[order], az[order], aw[order], ac[order])
     new_state = dict(x=mx, y=my, z=mz, w=mw, cell=mc, Npos=Npos, Nneg=Nneg)
     info = dict(sorted=sorted_state, ne_fix=ne, Xe=Xe, rho_fixed=rho, n_ion=fired[0], n_att=fired[1],
-                n_ph=fired[2], outflow=outflow, lost_photon=lost, weights_after_loss=sw,
-                new_particles=new)
+                n_ph=fired[2], n_ep=fired[3], n_np=fired[4], outflow=outflow, lost_photon=lost,
+                weights_after_loss=sw, new_particles=new)
     return new_state, info

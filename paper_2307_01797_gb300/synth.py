@@ -40,6 +40,21 @@ def _base(n, L, E0, dt, ppc, photons):
     )
 
 
+def with_recombination(phys, T=300.0):
+    """A copy of ``phys`` with the air recombination coefficients of Sec. 5.1:
+    beta_ep = 1.138e-11 T_e^-0.7 m^3/s and beta_np = 2e-13 (300/T)^0.5 m^3/s,
+    T the gas temperature in K.  The transport here has a constant mobility
+    and diffusion coefficient, so the electron temperature is the one of the
+    Einstein relation, k_B T_e = e D / mu (in K: T_e = (D / mu) e / k_B), and
+    the coefficients are constants."""
+    e_over_kB = 1.602176634e-19 / 1.380649e-23
+    Te = (phys["D"] / phys["mu"]) * e_over_kB
+    out = dict(phys)
+    out["beta_ep"] = 1.138e-11 * Te ** -0.7
+    out["beta_np"] = 2e-13 * (300.0 / T) ** 0.5
+    return out
+
+
 def physics_small(n=64):
     """64^3, 1 cm, 1.5 MV/m, dt = 1 ps, ppc = 8, photons off."""
     return _base(n, 0.01, 1.5e6, 1e-12, 8, False)

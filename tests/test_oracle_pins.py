@@ -652,7 +652,7 @@ def test_kmc_rates_breakdown_field(oracle_mod):
         half = n ** 3 // 2
         E[0][:half] = scale * Eb            # field along x in one half ...
         E[2][half:] = -scale * Eb           # ... along -z in the other
-        ion, att, ph_ = oracle_mod.kmc(p, Xe, E)
+        ion, att, ph_ = oracle_mod.kmc(p, Xe, E)[:3]
         for sl in (slice(0, half), slice(half, None)):
             a, b = ion[sl].sum(), att[sl].sum()
             assert abs(a / b - ratio) < 6 * ratio * math.sqrt(1 / a + 1 / b)
