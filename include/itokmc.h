@@ -87,8 +87,9 @@ extern "C" {
 #define ITOKMC_E 5        /* double 3 n^3: Ex block, Ey block, Ez block V/m */
 #define ITOKMC_RHO 6      /* int64 n^3: space charge 2^3s (N+ - N-) - ne_fix*/
                           /* in units of q_e 2^-3s, as of the last a4       */
-#define ITOKMC_FIRINGS 7  /* int64 3 n^3: ionizations, attachments, photon  */
-                          /* emissions of the last a6 (blocks of n^3)       */
+#define ITOKMC_FIRINGS 7  /* int64 5 n^3: ionizations, attachments, photon  */
+                          /* emissions, e-ion and ion-ion recombinations of */
+                          /* the last a6 (blocks of n^3)                    */
 
 /* ---- stages runnable one at a time (itokmc_run_stage) ------------------ */
 #define ITOKMC_STAGE_TRANSPORT 0  /* a1-a4: push, sort, deposit, X_e, rho   */
@@ -149,6 +150,9 @@ typedef struct itokmc_config {
     double cfl;                /* drift / diffusion bound (cells per step)    */
     double drt_factor;         /* dt <= drt eps0/sigma_max (explicit; 0: off) */
     double ion_factor;         /* k_ion(|E|max) dt <= ion_factor (0: off)     */
+    double beta_ep, beta_np;   /* recombination coefficients (m^3/s), Sec. 5.1:
+                                  k_ep = beta_ep / dV, k_np = beta_np / dV;
+                                  0 (the defaults): the reaction is off       */
 } itokmc_config;
 
 typedef struct itokmc_stats {
@@ -166,6 +170,7 @@ typedef struct itokmc_stats {
     int64_t kernel_launches;   /* kernels launched by the library so far     */
     int64_t merge_cells, merge_elements, merge_elements_sq, merge_max_list; /* last a9 */
     double dt_last;            /* step size of the last step (s)             */
+    int64_t recombinations_ep, recombinations_np; /* last a6                */
 } itokmc_stats;
 
 typedef struct itokmc_handle itokmc_handle;
@@ -179,9 +184,14 @@ int itokmc_config_defaults(itokmc_config* cfg);
  * and particle_capacity particles, zeroes it, and returns the handle in
  * *out.  No particles exist yet.  The configuration is the problem of Sec. 4
  * (Eq. ito_poisson): the electron drift-diffusion coefficients (mu, D) of
- * Eq. ito_kernel with v = -mu E (Eq. Vk1), the first-order network of Sec.
- * 3.2 and Table air_reactions restricted to ionization, attachment and
- * photon emission (alpha(E), eta, k_gamma), the photon absorption range of
+ * Eq. ito_kernel with v = -mu E (Eq. Vk1), the reaction network of Sec.
+ * 3.2 and Table air_reactions over the counts (X_e, X_+, X_-): ionization,
+ * attachment and photon emission (alpha(E), eta, k_gamma) and, with
+ * beta_ep / beta_np > 0, electron-ion and ion-ion recombination
+ * (propensities k_ep X_e X_+ and k_np X_+ X_-, k = beta / dV, Sec. 5.1;
+ * cells with ions of both signs but no electrons then run the KMC too; the
+ * field dependence of beta_ep through T_e is the caller's: it is one
+ * constant here), the photon absorption range of
  * Sec. 5.1, the Cao et al. parameters N_c, N_SSA, eps of Sec. 3.2.3, the
  * particle budget of Sec. 4.4 (N_new) and Sec. 4.6 (ppc), and the electrode
  * and side boundary conditions of Sec. 5.1.  With n_blobs > 0 the initial

@@ -181,6 +181,9 @@ void fill_params(const itokmc_config* cfg, ik::Params& P)
     P.dt = cfg->dt; P.mu = cfg->mu; P.D = cfg->D; P.alpha_A = cfg->alpha_A; P.alpha_B = cfg->alpha_B; P.eta = cfg->eta;
     P.photon_ratio = cfg->photon_ratio; P.kappa_lo = cfg->kappa_lo; P.kappa_hi = cfg->kappa_hi; P.eps = cfg->eps;
     P.sdt = sqrt((2.0 * cfg->D) * cfg->dt);
+    const double dV = (P.h[0] * P.h[1]) * P.h[2];
+    P.k_ep = cfg->beta_ep / dV;
+    P.k_np = cfg->beta_np / dV;
     P.E0 = cfg->E0;
     P.seed0 = cfg->seed0;
     P.step = 0;
@@ -269,6 +272,8 @@ int stage_particles(itokmc_handle* h)
     h->st.ionizations = (int64_t)c.ion;
     h->st.attachments = (int64_t)c.att;
     h->st.photon_emissions = (int64_t)c.phot;
+    h->st.recombinations_ep = (int64_t)c.rec_ep;
+    h->st.recombinations_np = (int64_t)c.rec_np;
     h->st.photons_absorbed_weight = (int64_t)c.absorbed_w;
     int64_t lost = 0;
     for (int r = 0; r < h->P.R; ++r) lost += (int64_t)c.lost[r];
@@ -542,6 +547,8 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     if (cfg->dt_adapt && !(cfg->dt_min > 0.0 && cfg->dt_min <= cfg->dt && cfg->cfl >= 0.0 && cfg->drt_factor >= 0.0 &&
                            cfg->ion_factor >= 0.0))
         return fail(nullptr, ITOKMC_ERR_ARG, "adaptive step: 0 < dt_min <= dt, cfl, drt_factor, ion_factor >= 0");
+    if (!(cfg->beta_ep >= 0.0 && cfg->beta_np >= 0.0 && std::isfinite(cfg->beta_ep) && std::isfinite(cfg->beta_np)))
+        return fail(nullptr, ITOKMC_ERR_ARG, "recombination coefficients: finite, >= 0");
     if (cfg->coupling != ITOKMC_EXPLICIT && cfg->coupling != ITOKMC_SEMI_IMPLICIT)
         return fail(nullptr, ITOKMC_ERR_ARG, "coupling: ITOKMC_EXPLICIT or ITOKMC_SEMI_IMPLICIT");
     if (cfg->coupling == ITOKMC_SEMI_IMPLICIT &&
@@ -604,7 +611,7 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
         d.E = dalloc_n<ik::E64>(h, G, &rc);
         d.E_next = dalloc_n<ik::E64>(h, G, &rc);
     }
-    d.fired = dalloc_n<int64_t>(h, 3 * G, &rc);
+    d.fired = dalloc_n<int64_t>(h, 5 * G, &rc);
     d.stage = dalloc_n<double>(h, 3 * G, &rc);
     d.phi_prev = dalloc_n<double>(h, G, &rc);
     d.photos = dalloc_n<ik::Photo>(h, d.photo_cap, &rc);
@@ -966,7 +973,7 @@ int itokmc_read_densities(itokmc_handle* h, int32_t r, int32_t which, void* host
     case ITOKMC_E:
         ik::launch_unpack_field(h->P, h->d, h->d.stage, h->s);
         src = h->d.stage; blocks = 3; break;
-    case ITOKMC_FIRINGS: src = h->d.fired; blocks = 3; break;
+    case ITOKMC_FIRINGS: src = h->d.fired; blocks = 5; break;
     default: return fail(h, ITOKMC_ERR_ARG, "unknown field");
     }
     if (bytes < blocks * cnt * 8) return fail(h, ITOKMC_ERR_ARG, "output buffer too small");

@@ -22,7 +22,7 @@
 
 namespace {
 
-constexpr char MAGIC[8] = { 'I', 'T', 'O', 'K', 'M', 'C', 'K', '1' };
+constexpr char MAGIC[8] = { 'I', 'T', 'O', 'K', 'M', 'C', 'K', '2' };
 
 // The part of the configuration a checkpoint is bound to (the physics, the
 // grid and the form; not the allocator, the stream or the capacity).
@@ -35,6 +35,7 @@ struct CkptHeader {
     int32_t mg_nu1, mg_nu2, phi_F, have_prev;
     uint32_t N, pad1;
     uint64_t G;
+    double beta_ep, beta_np;
 };
 
 CkptHeader header_of(const ik::HandleView& v)
@@ -54,6 +55,7 @@ CkptHeader header_of(const ik::HandleView& v)
     H.phi_F = v.d->phi_F; H.have_prev = v.d->have_prev ? 1 : 0;
     H.N = *v.N;
     H.G = v.G;
+    H.beta_ep = c.beta_ep; H.beta_np = c.beta_np;
     return H;
 }
 
@@ -65,6 +67,7 @@ const char* mismatch(const CkptHeader& a, const CkptHeader& b)
     IK_SAME(n_new); IK_SAME(n_crit); IK_SAME(n_ssa); IK_SAME(lo); IK_SAME(hi); IK_SAME(dt); IK_SAME(mu);
     IK_SAME(D); IK_SAME(alpha_A); IK_SAME(alpha_B); IK_SAME(eta); IK_SAME(E0); IK_SAME(photon_ratio);
     IK_SAME(kappa_lo); IK_SAME(kappa_hi); IK_SAME(eps); IK_SAME(mg_rtol); IK_SAME(seed0); IK_SAME(G);
+    IK_SAME(beta_ep); IK_SAME(beta_np);
 #undef IK_SAME
     return "";
 }
@@ -96,7 +99,7 @@ std::vector<Blob> blobs_of(const ik::HandleView& v, uint32_t N)
     b.push_back({ d.ne_fix, G * sizeof(unsigned long long) });
     b.push_back({ d.Xe, G * sizeof(unsigned long long) });
     b.push_back({ d.rho, G * sizeof(int64_t) });
-    b.push_back({ d.fired, 3 * G * sizeof(int64_t) });
+    b.push_back({ d.fired, 5 * G * sizeof(int64_t) });
     return b;
 }
 

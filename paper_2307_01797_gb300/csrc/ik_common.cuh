@@ -23,6 +23,7 @@ struct Params {
     double lo[3], hi[3], h[3], rh[3];   // rh = 1/h
     double dt, mu, D, alpha_A, alpha_B, eta, photon_ratio, kappa_lo, kappa_hi, eps;
     double sdt;             // sqrt(2 D dt)
+    double k_ep, k_np;      // recombination frequencies per pair, beta / dV (1/s)
     double E0;
     uint64_t seed0;
     uint32_t step;

@@ -857,40 +857,81 @@ __device__ long long KT<float>::poisson(Stream& s, float mu)
     return -1;
 }
 
+// Per-cell hybrid tau-leap/SSA of Cao et al. (2006), Sec. 3.2.3, over the
+// counts X = (X_e, X_+, X_-) and the five reactions of Sec. 5.1's air table:
+//   r=0 ionization      a = k_alpha X_e        nu = (+1, +1,  0)
+//   r=1 attachment      a = k_eta X_e          nu = (-1,  0, +1)
+//   r=2 photon emission a = k_gamma X_e        nu = ( 0,  0,  0)
+//   r=3 e-ion recomb.   a = k_ep X_e X_+       nu = (-1, -1,  0)
+//   r=4 ion-ion recomb. a = k_np X_+ X_-       nu = ( 0, -1, -1)
+// A reaction is critical when it is within N_c firings of exhausting a
+// reactant; the non-critical step bound takes eps X_i / g_i over the
+// reactant species of the non-critical reactions, g_i = 2 for a reactant of
+// a second-order reaction with a positive coefficient; the SSA switch
+// (A dtau <= 1) is tested before the critical time is drawn; a substep that
+// leaves a count negative is redone with half the step.  Sums are taken in
+// reaction order and each operation rounds once (-fmad=false), so the FP64
+// form is one fixed evaluation of these steps.
+__device__ __forceinline__ int kmc_nu(int r, int i)
+{
+    // compile-time after unrolling: the stoichiometry table above
+    return i == 0 ? (r == 0) - (r == 1) - (r == 3) : (i == 1 ? (r == 0) - (r == 3) - (r == 4) : (r == 1) - (r == 4));
+}
+
 template <class T>
-__device__ int kmc_cell(const Params& P, Stream& s, long long X0, const T kr[3], long long fired[3])
+__device__ __forceinline__ void kmc_props(const T kr[5], const long long X[3], T a[5])
+{
+    const T xe = (T)X[0], xp = (T)X[1], xm = (T)X[2];
+    a[0] = kr[0] * xe;
+    a[1] = kr[1] * xe;
+    a[2] = kr[2] * xe;
+    a[3] = (kr[3] * xe) * xp;
+    a[4] = (kr[4] * xp) * xm;
+}
+
+template <class T>
+__device__ int kmc_cell(const Params& P, Stream& s, const long long X0[3], const T kr[5], long long fired[5])
 {
     using K = KT<T>;
-    const int nu[3] = { +1, -1, 0 };
-    long long X = X0;
+    long long X[3] = { X0[0], X0[1], X0[2] };
     const T dt = (T)P.dt;
+    const long long nc = (long long)P.n_crit;
     T tau = (T)0;
-    fired[0] = fired[1] = fired[2] = 0;
+    const bool g2[3] = { kr[3] > (T)0, kr[3] > (T)0 || kr[4] > (T)0, kr[4] > (T)0 };
+#pragma unroll
+    for (int r = 0; r < 5; ++r) fired[r] = 0;
     for (int guard = 0; guard < 100000; ++guard) {
         if (!(tau < dt)) return 0;
-        const T xd = (T)X;
-        const T a[3] = { kr[0] * xd, kr[1] * xd, kr[2] * xd };
-        const T A = (a[0] + a[1]) + a[2];
+        T a[5];
+        kmc_props<T>(kr, X, a);
+        const T A = (((a[0] + a[1]) + a[2]) + a[3]) + a[4];
         if (!(A > (T)0)) return 0;
-        const bool crit[3] = { false, X < (long long)P.n_crit, false };
+        const long long L3 = X[0] < X[1] ? X[0] : X[1], L4 = X[1] < X[2] ? X[1] : X[2];
+        const bool crit[5] = { false, a[1] > (T)0 && X[0] < nc, false, a[3] > (T)0 && L3 < nc, a[4] > (T)0 && L4 < nc };
         T Ac = (T)0;
-        for (int r = 0; r < 3; ++r) if (crit[r]) Ac = Ac + a[r];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) if (crit[r]) Ac = Ac + a[r];
         T dtnc = K::inf();
         if (!isinf(P.eps)) {
-            T xi = (T)0, sig2 = (T)0;
-            bool any = false;
-            for (int r = 0; r < 3; ++r) {
-                if (crit[r]) continue;
-                any = true;
-                xi = xi + (T)nu[r] * a[r];
-                sig2 = sig2 + (T)(nu[r] * nu[r]) * a[r];
-            }
-            if (any) {
-                T num = (T)P.eps * xd;
+            const bool reactant[3] = { true, (!crit[3] && kr[3] > (T)0) || (!crit[4] && kr[4] > (T)0),
+                                       !crit[4] && kr[4] > (T)0 };
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (!reactant[i]) continue;
+                T xi = (T)0, sig2 = (T)0;
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    if (crit[r]) continue;
+                    xi = xi + (T)kmc_nu(r, i) * a[r];
+                    sig2 = sig2 + (T)(kmc_nu(r, i) * kmc_nu(r, i)) * a[r];
+                }
+                T num = (T)P.eps * (T)X[i];
+                if (g2[i]) num = num * (T)0.5;          // num / g_i, exact for g_i = 2
                 if (num < (T)1) num = (T)1;
                 const T t1 = (xi != (T)0) ? num / (xi < (T)0 ? -xi : xi) : K::inf();
                 const T t2 = (sig2 != (T)0) ? (num * num) / sig2 : K::inf();
-                dtnc = t1 < t2 ? t1 : t2;
+                const T ti = t1 < t2 ? t1 : t2;
+                if (ti < dtnc) dtnc = ti;
             }
         }
         T dtc = (T)-1;
@@ -898,28 +939,32 @@ __device__ int kmc_cell(const Params& P, Stream& s, long long X0, const T kr[3],
         for (int rej = 0; rej < 10000 && !accepted; ++rej) {
             const T rem = dt - tau;
             T dtau = dtnc < rem ? dtnc : rem;
-            long long k[3] = { 0, 0, 0 };
+            long long k[5] = { 0, 0, 0, 0, 0 };
             T adv;
             if (A * dtau <= (T)1) {
-                long long Xs = X;
+                long long Xs[3] = { X[0], X[1], X[2] };
                 T t = (T)0;
                 for (int ev = 0; ev < P.n_ssa; ++ev) {
-                    const T xs = (T)Xs;
-                    const T as[3] = { kr[0] * xs, kr[1] * xs, kr[2] * xs };
-                    const T As = (as[0] + as[1]) + as[2];
+                    T as[5];
+                    kmc_props<T>(kr, Xs, as);
+                    const T As = (((as[0] + as[1]) + as[2]) + as[3]) + as[4];
                     if (!(As > (T)0)) { t = dtau; break; }
                     const T dte = (-K::lg(K::uni(s))) / As;
                     if (t + dte > dtau) { t = dtau; break; }
                     t = t + dte;
                     const T target = K::uni(s) * As;
                     T cum = (T)0;
-                    int j = 2;
-                    for (int r = 0; r < 3; ++r) {
+                    int j = (as[3] > (T)0 || as[4] > (T)0) ? (as[4] > (T)0 ? 4 : 3) : 2;
+#pragma unroll
+                    for (int r = 0; r < 5; ++r) {
                         cum = cum + as[r];
                         if (cum > target) { j = r; break; }
                     }
-                    k[j] += 1;
-                    Xs += nu[j];
+#pragma unroll
+                    for (int r = 0; r < 5; ++r) k[r] += (j == r);
+                    Xs[0] += (j == 0) - (j == 1) - (j == 3);
+                    Xs[1] += (j == 0) - (j == 3) - (j == 4);
+                    Xs[2] += (j == 1) - (j == 4);
                 }
                 adv = t;
             } else {
@@ -929,16 +974,19 @@ __device__ int kmc_cell(const Params& P, Stream& s, long long X0, const T kr[3],
                     const T target = K::uni(s) * Ac;
                     T cum = (T)0;
                     int rc = -1, last = -1;
-                    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                    for (int r = 0; r < 5; ++r) {
                         if (!crit[r]) continue;
                         last = r;
                         cum = cum + a[r];
                         if (cum > target) { rc = r; break; }
                     }
                     if (rc < 0) rc = last;
-                    k[rc] += 1;
+#pragma unroll
+                    for (int r = 0; r < 5; ++r) k[r] += (rc == r);
                 }
-                for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
                     if (crit[r]) continue;
                     const long long kk = K::poisson(s, a[r] * dtau);
                     if (kk < 0) return -1;
@@ -946,13 +994,16 @@ __device__ int kmc_cell(const Params& P, Stream& s, long long X0, const T kr[3],
                 }
                 adv = dtau;
             }
-            const long long Xn = X + k[0] - k[1];
-            if (Xn < 0) {
+            const long long Xn0 = X[0] + k[0] - k[1] - k[3];
+            const long long Xn1 = X[1] + k[0] - k[3] - k[4];
+            const long long Xn2 = X[2] + k[1] - k[4];
+            if (Xn0 < 0 || Xn1 < 0 || Xn2 < 0) {
                 dtnc = dtau * (T)0.5;
                 continue;
             }
-            X = Xn;
-            fired[0] += k[0]; fired[1] += k[1]; fired[2] += k[2];
+            X[0] = Xn0; X[1] = Xn1; X[2] = Xn2;
+#pragma unroll
+            for (int r = 0; r < 5; ++r) fired[r] += k[r];
             if (adv >= rem) tau = dt; else tau = tau + adv;
             accepted = true;
         }
@@ -961,19 +1012,38 @@ __device__ int kmc_cell(const Params& P, Stream& s, long long X0, const T kr[3],
     return -1;
 }
 
-// Cells with electrons listed for the KMC (one thread per listed cell keeps
-// the warps' lanes busy: the active cells are a small part of the grid);
-// the other cells fire nothing.
-__global__ void k_kmc_list(const unsigned long long* __restrict__ Xe, int64_t* __restrict__ fired, uint64_t G,
+// Net electron gain of cell g from its firings: ionizations - attachments -
+// e-ion recombinations (the last block is read only when k_ep > 0; it stays
+// zero otherwise).
+__device__ __forceinline__ long long net_gain(const int64_t* __restrict__ fired, uint64_t G, uint64_t g, bool rec_ep)
+{
+    long long dN = fired[g] - fired[G + g];
+    if (rec_ep) dN -= fired[3 * G + g];
+    return dN;
+}
+
+// Cells with electrons -- or, with ion-ion recombination on, ions of both
+// signs -- listed for the KMC (one thread per listed cell keeps the warps'
+// lanes busy: the active cells are a small part of the grid); the other
+// cells fire nothing.  The recombination blocks of the firings are touched
+// only when their reaction is on.
+__global__ void k_kmc_list(Params P, const unsigned long long* __restrict__ Xe, const int64_t* __restrict__ Npos,
+                           const int64_t* __restrict__ Nneg, int64_t* __restrict__ fired, uint64_t G,
                            uint32_t* __restrict__ list, Counters* __restrict__ ctr)
 {
+    const bool rec = P.k_ep > 0.0 || P.k_np > 0.0;
+    const bool ion_only = P.k_np > 0.0;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
-        if (Xe[g] > 0) {
+        if (Xe[g] > 0 || (ion_only && Npos[g] > 0 && Nneg[g] > 0)) {
             list[warp_slot32(&ctr->n_kmc_cells)] = (uint32_t)g;
         } else {
             fired[g] = 0;
             fired[G + g] = 0;
             fired[2 * G + g] = 0;
+            if (rec) {
+                fired[3 * G + g] = 0;
+                fired[4 * G + g] = 0;
+            }
         }
     }
 }
@@ -984,7 +1054,8 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
                       int64_t* __restrict__ Nneg, uint64_t G, const uint32_t* __restrict__ list,
                       uint32_t* __restrict__ pc_list, Counters* __restrict__ ctr)
 {
-    unsigned long long t_ion = 0, t_att = 0, t_ph = 0, t_slots = 0;
+    unsigned long long t_ion = 0, t_att = 0, t_ph = 0, t_ep = 0, t_np = 0, t_slots = 0;
+    const bool rec = P.k_ep > 0.0 || P.k_np > 0.0;
     const uint64_t n = ctr->n_kmc_cells;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -992,9 +1063,11 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
     for (uint64_t t = t0; t < tend; t += stride) {
         if (t >= n) continue;
         const uint64_t g = list[t];
-        long long f[3] = { 0, 0, 0 };
-        const long long X0 = (long long)Xe[g];
-        T kr[3];
+        long long f[5] = { 0, 0, 0, 0, 0 };
+        const long long X0[3] = { (long long)Xe[g], rec ? (long long)Npos[g] : 0, rec ? (long long)Nneg[g] : 0 };
+        T kr[5];
+        kr[3] = (T)P.k_ep;
+        kr[4] = (T)P.k_np;
         if constexpr (sizeof(T) == 8) {
             const E64 e = ld_e64(E + g);
             const double Em = e.m;
@@ -1018,8 +1091,8 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
             atomicOr(&ctr->err, DERR_KMC);
             ctr->kmc_fail_cell = (unsigned)g;
         }
-        Npos[g] += f[0];
-        Nneg[g] += f[1];
+        Npos[g] += (f[0] - f[3]) - f[4];
+        Nneg[g] += f[1] - f[4];
         if (f[2] > 0) {
             t_slots += (unsigned long long)(f[2] < P.n_new ? f[2] : P.n_new);
             pc_list[warp_slot32(&ctr->n_photo_cells)] = (uint32_t)g;
@@ -1027,13 +1100,21 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
         t_ion += (unsigned long long)f[0];
         t_att += (unsigned long long)f[1];
         t_ph += (unsigned long long)f[2];
+        t_ep += (unsigned long long)f[3];
+        t_np += (unsigned long long)f[4];
         fired[g] = f[0];
         fired[G + g] = f[1];
         fired[2 * G + g] = f[2];
+        if (rec) {
+            fired[3 * G + g] = f[3];
+            fired[4 * G + g] = f[4];
+        }
     }
     warp_add(&ctr->ion, t_ion);
     warp_add(&ctr->att, t_att);
     warp_add(&ctr->phot, t_ph);
+    warp_add(&ctr->rec_ep, t_ep);
+    warp_add(&ctr->rec_np, t_np);
     warp_add(&ctr->photo_slots, t_slots);
 }
 
@@ -1043,12 +1124,14 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
 // field magnitude Em (k_ion = alpha(Em) mu Em, k_att = eta mu Em, k_ph =
 // photon_ratio k_ion), each step the per-cell KMC of the spatial model drawn
 // from the stream (key seed0, index m, step k, KMC).  X[m (nsteps + 1) + k]
-// holds the electrons after k steps.
+// holds the electrons after k steps.  The ensembles track no ion counts:
+// the network is the first-order one (no recombination).
 template <class T>
 __global__ void k_kmc0d(Params P, double Em, long long X0, uint32_t nreal, int nsteps, long long* __restrict__ X,
                         Counters* __restrict__ ctr)
 {
-    T kr[3];
+    T kr[5];
+    kr[3] = kr[4] = (T)0;
     if constexpr (sizeof(T) == 8) {
         const double ve = P.mu * Em;
         const double alpha = (Em > 0.0) ? P.alpha_A * dexp(-(P.alpha_B / Em)) : 0.0;
@@ -1068,10 +1151,11 @@ __global__ void k_kmc0d(Params P, double Em, long long X0, uint32_t nreal, int n
         long long* out = X + (size_t)m * (nsteps + 1);
         out[0] = x;
         for (int k = 0; k < nsteps; ++k) {
-            long long f[3] = { 0, 0, 0 };
+            long long f[5] = { 0, 0, 0, 0, 0 };
             if (x > 0) {
+                const long long X3[3] = { x, 0, 0 };
                 Stream s(P.seed0, m, (uint32_t)k, TAG_KMC, 0);
-                if (kmc_cell<T>(P, s, x, kr, f) != 0) atomicOr(&ctr->err, DERR_KMC);
+                if (kmc_cell<T>(P, s, X3, kr, f) != 0) atomicOr(&ctr->err, DERR_KMC);
             }
             x += f[0] - f[1];
             out[k + 1] = x;
@@ -1086,8 +1170,9 @@ __global__ void k_kmc0d(Params P, double Em, long long X0, uint32_t nreal, int n
 __global__ void k_loss(Params P, uint32_t* __restrict__ wbase, int wstride, const uint32_t* __restrict__ cs,
                        const unsigned long long* __restrict__ Xe, const int64_t* __restrict__ fired, uint64_t G)
 {
+    const bool rec_ep = P.k_ep > 0.0;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
-        const long long dN = fired[g] - fired[G + g];
+        const long long dN = net_gain(fired, G, g, rec_ep);
         if (dN >= 0) continue;
         const unsigned long long L = (unsigned long long)(-dN);
         const unsigned long long W = Xe[g];
@@ -1327,9 +1412,10 @@ struct MergeScanOp {
     uint32_t* list_n;         // [3]: lengths
     uint64_t G;
     int ppc, n_new, esize, ksize;
+    bool rec_ep;
     __device__ void load(uint64_t g, long long v[6]) const
     {
-        const long long dN = fired[g] - fired[G + g];
+        const long long dN = net_gain(fired, G, g, rec_ep);
         const long long W = (long long)Xe[g] + dN + (long long)photo_w[g];
         v[0] = W < ppc ? W : ppc;
         v[1] = photo_cnt[g];
@@ -1512,7 +1598,7 @@ __global__ void __launch_bounds__(128) k_merge_lv(
         const uint64_t g = list[li];
         const int r = real_of(P, (uint32_t)g);
         const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
-        const long long dN = fired[g] - fired[G + g];
+        const long long dN = net_gain(fired, G, g, P.k_ep > 0.0);
         const uint32_t e0 = cs[g], e1 = cs[g + 1];
         const uint32_t mprod = dN > 0 ? (uint32_t)(dN < P.n_new ? dN : P.n_new) : 0u;
         const uint32_t p0 = photo_off[g], np = photo_off[g + 1] - p0;
@@ -2352,7 +2438,7 @@ void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 {
     // the merge's tier-0 list is free until the merge scan of this step
     g_launches += 2;
-    k_kmc_list<<<grid_for(G, 256, 152 * 32), 256, 0, s>>>(d.Xe, d.fired, G, d.small_list, d.ctr);
+    k_kmc_list<<<grid_for(G, 256, 152 * 32), 256, 0, s>>>(P, d.Xe, d.Npos, d.Nneg, d.fired, G, d.small_list, d.ctr);
     if (d.mixed)
         k_kmc<float><<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G,
                                                               d.small_list, d.pc_list, d.ctr);
@@ -2378,7 +2464,7 @@ void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
     }
     MergeScanOp op{ d.Xe, d.fired, d.photo_w, d.photo_cnt, d.cell_start, d.out_start, d.photo_off, d.work_off,
                     d.small_list, d.mid_list, d.big_list, d.list_n, G, P.ppc, P.n_new,
-                    d.mixed ? (int)sizeof(MP32) : (int)sizeof(MP), d.mixed ? 4 : 8 };
+                    d.mixed ? (int)sizeof(MP32) : (int)sizeof(MP), d.mixed ? 4 : 8, P.k_ep > 0.0 };
     run_scan<6>(op, G, d.scan_blk, s);
 }
 

@@ -181,7 +181,7 @@ int seed_blobs(itokmc_handle* h, const itokmc_seed_blob* blobs, int nb, int flag
         k_seed_write<false><<<grid_of(G), 256, 0, s>>>(P, cnt, d.cell_start, v.cap, d.recA, nullptr, nullptr, d.Npos,
                                                        flags & ITOKMC_SEED_NEUTRAL, G);
     // the firing counts were borrowed: no reaction has fired yet
-    cudaMemsetAsync(d.fired, 0, 3 * G * sizeof(int64_t), s);
+    cudaMemsetAsync(d.fired, 0, 5 * G * sizeof(int64_t), s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return handle_fail(h, ITOKMC_ERR_CUDA, "seed_blobs: write pass");
     *v.N = total;

@@ -58,6 +58,7 @@ struct Counters {
     unsigned long long n_photo;
     unsigned long long n_new;          // product + photo particles
     unsigned long long ion, att, phot; // firings
+    unsigned long long rec_ep, rec_np; // recombination firings
     unsigned long long absorbed_w;
     unsigned long long photo_slots;    // sum over cells of min(N_gamma, N_new)
     unsigned int n_photo_cells;        // photon-emitting cells listed by the KMC
@@ -106,7 +107,7 @@ struct Dev {
     int64_t* Npos = nullptr;  int64_t* Nneg = nullptr;  int64_t* rho = nullptr;
     E64* E = nullptr;  float4* E32 = nullptr;
     // chemistry
-    int64_t* fired = nullptr;          // 3 G: ion, att, photon
+    int64_t* fired = nullptr;          // 5 G: ion, att, photon, e-ion and ion-ion recombination
     // photons
     Photo* photos = nullptr;  uint32_t* photo_sorted = nullptr;
     int32_t* photo_cnt = nullptr;  int32_t* photo_cursor = nullptr;

@@ -49,6 +49,7 @@ class Config(ctypes.Structure):
         ("blobs", ctypes.c_void_p), ("n_blobs", ctypes.c_int32), ("seed_flags", ctypes.c_int32),
         ("coupling", ctypes.c_int32), ("dt_adapt", ctypes.c_int32), ("dt_min", ctypes.c_double),
         ("cfl", ctypes.c_double), ("drt_factor", ctypes.c_double), ("ion_factor", ctypes.c_double),
+        ("beta_ep", ctypes.c_double), ("beta_np", ctypes.c_double),
     ]
 
 
@@ -84,6 +85,7 @@ class Stats(ctypes.Structure):
         ("ms_particles", ctypes.c_double), ("ms_field", ctypes.c_double),
         ("kernel_launches", ctypes.c_int64), ("merge_cells", ctypes.c_int64), ("merge_elements", ctypes.c_int64),
         ("merge_elements_sq", ctypes.c_int64), ("merge_max_list", ctypes.c_int64), ("dt_last", ctypes.c_double),
+        ("recombinations_ep", ctypes.c_int64), ("recombinations_np", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -245,7 +247,8 @@ def make_config(phys: dict, capacity: int, realizations: int = 1, seed0: int = 1
         c.hi[a] = float(phys["hi"][a])
     c.dt = float(phys["dt"])
     c.seed0 = int(seed0)
-    for k in ("mu", "D", "alpha_A", "alpha_B", "eta", "E0", "photon_ratio", "kappa_lo", "kappa_hi"):
+    for k in ("mu", "D", "alpha_A", "alpha_B", "eta", "E0", "photon_ratio", "kappa_lo", "kappa_hi",
+              "beta_ep", "beta_np"):
         setattr(c, k, float(phys.get(k, getattr(c, k))))
     c.eps = float(phys.get("eps", math.inf))
     for k in ("ppc", "n_new", "n_crit", "n_ssa", "frac_bits"):
@@ -353,7 +356,7 @@ class Handle:
 
     def itokmc_read_densities(self, which, realization=0):
         cells = self.n ** 3 * (self.R if realization < 0 else 1)
-        blocks = 3 if which in (E, FIRINGS) else 1
+        blocks = {E: 3, FIRINGS: 5}.get(which, 1)
         dt = np.float64 if which in (PHI, E) else np.int64
         out = np.empty(blocks * cells, dtype=dt)
         _check(lib().itokmc_read_densities(self.h, int(realization), int(which), _ptr(out), out.nbytes), self.h)
