@@ -65,6 +65,8 @@ def peaks():
 def workload(args):
     from paper_2307_01797_gb300 import synth
     ph = synth.physics_streamer(args.n)
+    if getattr(args, "recombination", False):
+        ph = synth.with_recombination(ph)
     st = synth.streamer_tree_state(ph, int(args.particles), seed=7)
     ions = synth.streamer_ions(ph, st, seed=8)
     return ph, st, ions
@@ -185,6 +187,8 @@ def config_of(args, nparticles, fp64=True):
                         f"photoionization on, synthetic 4-channel discharge tree",
             "grid": args.n, "particles": int(nparticles), "ppc": 32,
             "form": "fp64 plain" if fp64 else "mixed (fp32 + fixed point)",
+            "chemistry": ("ionization, attachment, photon emission, e-ion and ion-ion recombination (air)"
+                          if getattr(args, "recombination", False) else "ionization, attachment, photon emission"),
             "l2": "inputs > L2 (particle records of several GB; no flush)"}
 
 
@@ -243,7 +247,8 @@ def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e)
         movers += s["n_movers"]
         mg_cycles.append(s["mg_cycles"])
         last = {k: s[k] for k in ("merge_cells", "merge_elements", "merge_elements_sq", "merge_max_list",
-                                  "n_new_particles", "photon_emissions", "ionizations", "attachments",
+                                  "n_new_particles", "photon_emissions", "ionizations", "attachments", "recombinations_ep",
+                                  "recombinations_np",
                                   "mg_rel_residual")}
     e1.record(stream)
     torch.cuda.synchronize()
@@ -907,6 +912,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default smoother counts (2, 2)")
+    ap.add_argument("--recombination", action="store_true",
+                    help="add the air recombination coefficients to the chemistry (five reactions)")
     ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small", "semi", "transport", "tree", "kmc0d"],
                     help="instead of the benchmark: one of the studies (see each function's docstring)")
     ap.add_argument("--slab", action="store_true", help="transport study: count-pinned uniform z-slab")

@@ -284,7 +284,13 @@ int itokmc_step(itokmc_handle* h, int32_t nsteps);
 
 /* Runs one stage (ITOKMC_STAGE_*) on the current state without advancing
  * the step counter; a full step is TRANSPORT, KMC, PARTICLES, FIELD and then
- * the counter advance (itokmc_advance_counter). */
+ * the counter advance (itokmc_advance_counter).  Order: TRANSPORT (or
+ * itokmc_transport_semi_implicit) and FIELD may run at any time; KMC needs a
+ * transport of the current particles and may be repeated on it (each run
+ * applies its firings to the ion counts again); PARTICLES needs a KMC after
+ * the last transport and changes the particles, so the next KMC needs a new
+ * transport.  Setting, seeding or loading particles restarts the order.
+ * Errors: ERR_ARG (unknown stage or out of order), and those of the stage. */
 int itokmc_run_stage(itokmc_handle* h, int32_t stage);
 
 /* Advances the step counter used in every Philox counter by one. */

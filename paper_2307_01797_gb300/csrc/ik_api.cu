@@ -39,6 +39,7 @@ struct itokmc_handle {
     uint32_t cap = 0;
     int64_t step = 0;
     int field_prec = 0;
+    int stage = 0;                // stage order, see checked_stage
     bool poisoned = false;
     std::string err;
     std::mutex emtx;              // err/poisoned are written by the step and field threads
@@ -219,7 +220,7 @@ float elapsed(itokmc_handle* h, int a, int b)
     return ms;
 }
 
-int stage_transport(itokmc_handle* h)
+int transport_body(itokmc_handle* h)
 {
     IK_CHECK(h, cudaEventRecord(h->ev[0], h->s));
     ik::launch_transport(h->P, h->d, h->N, h->s);
@@ -237,7 +238,7 @@ int stage_transport(itokmc_handle* h)
     return status_of_err(h, c.err);
 }
 
-int stage_kmc(itokmc_handle* h)
+int kmc_body(itokmc_handle* h)
 {
     IK_CHECK(h, cudaEventRecord(h->ev[2], h->s));
     ik::launch_kmc(h->P, h->d, h->G, h->s);
@@ -245,7 +246,7 @@ int stage_kmc(itokmc_handle* h)
     return cuda_check(h, cudaGetLastError(), "kmc launch");
 }
 
-int stage_particles(itokmc_handle* h)
+int particles_body(itokmc_handle* h)
 {
     IK_CHECK(h, cudaEventRecord(h->ev[4], h->s));
     // the photon list must hold every superphoton this step can emit
@@ -321,7 +322,7 @@ int stage_field(itokmc_handle* h) { return stage_field_on(h, h->s, h->d.E, h->d.
 // conductivity of the start of the step, the diffusive substep, the charge of
 // the diffused particles, the variable-coefficient solve for the field of
 // the end of the step (into d.E), the advective substep, sort and deposit.
-int stage_semi_transport(itokmc_handle* h, int32_t* cycles_out, double* rel_out)
+int semi_transport_body(itokmc_handle* h, int32_t* cycles_out, double* rel_out)
 {
     ik::Dev& d = h->d;
     if (d.mixed || d.phi_F > 0)
@@ -382,6 +383,46 @@ int stage_semi_transport(itokmc_handle* h, int32_t* cycles_out, double* rel_out)
 // next step is solved on the field stream by a host thread while this
 // thread runs KMC and the particle stages (they read the current field; the
 // solve writes the next one); the two fields swap at the end.
+// Stage order.  The KMC reads X_e of the last deposit, the particles stage
+// the firings of the last KMC and the cell offsets of the last transport, so
+// each stage runs only on the state the stages before it produced from the
+// current particles: a transport (either coupling) may run at any time; the
+// KMC after a transport, and again on the same transported state; the
+// particles stage once after a KMC, after which the particles have changed
+// and the next KMC needs a new transport.  h->stage is 0 (no deposit of the
+// current particles), 1 (transported) or 2 (KMC done); replacing the
+// particles (set, seed, load) returns it to 0.
+int stage_transport(itokmc_handle* h)
+{
+    h->stage = 0;
+    const int rc = transport_body(h);
+    if (!rc) h->stage = 1;
+    return rc;
+}
+
+int stage_semi_transport(itokmc_handle* h, int32_t* cycles_out, double* rel_out)
+{
+    h->stage = 0;
+    const int rc = semi_transport_body(h, cycles_out, rel_out);
+    if (!rc) h->stage = 1;
+    return rc;
+}
+
+int stage_kmc(itokmc_handle* h)
+{
+    if (h->stage < 1) return fail(h, ITOKMC_ERR_ARG, "stage order: the KMC needs a transport stage first");
+    const int rc = kmc_body(h);
+    h->stage = rc ? 0 : 2;
+    return rc;
+}
+
+int stage_particles(itokmc_handle* h)
+{
+    if (h->stage != 2) return fail(h, ITOKMC_ERR_ARG, "stage order: the particles stage needs a KMC after a transport");
+    h->stage = 0;
+    return particles_body(h);
+}
+
 int full_step(itokmc_handle* h)
 {
     int rc = stage_transport(h);
@@ -478,7 +519,7 @@ int handle_view(itokmc_handle* h, HandleView* v)
     IK_GUARD(h);
     IK_CHECK(h, cudaStreamSynchronize(h->s));
     if (h->sf) IK_CHECK(h, cudaStreamSynchronize(h->sf));
-    *v = HandleView{ &h->cfg, &h->P, &h->d, h->s, &h->N, h->cap, &h->step, h->G, h->field_prec };
+    *v = HandleView{ &h->cfg, &h->P, &h->d, h->s, &h->N, h->cap, &h->step, h->G, h->field_prec, &h->stage };
     return ITOKMC_OK;
 }
 int handle_fail(itokmc_handle* h, int code, const char* msg) { return fail(h, code, msg); }
@@ -723,6 +764,7 @@ int itokmc_set_particles(itokmc_handle* h, const double* x, const double* y, con
                          const int32_t* realization, int64_t n, int32_t mem)
 {
     IK_GUARD(h);
+    h->stage = 0;
     if (n < 0 || (n > 0 && (!x || !y || !z || !w))) return fail(h, ITOKMC_ERR_ARG, "bad particle arrays");
     if (n > (int64_t)h->cap) return fail(h, ITOKMC_ERR_CAPACITY, "more particles than particle_capacity");
     if (h->P.R > 1 && n > 0 && !realization) return fail(h, ITOKMC_ERR_ARG, "realization array required when R > 1");
@@ -982,6 +1024,12 @@ int itokmc_read_densities(itokmc_handle* h, int32_t r, int32_t which, void* host
                                     static_cast<const char*>(src) + (b * h->G + off) * 8, cnt * 8,
                                     cudaMemcpyDeviceToHost, h->s));
     IK_CHECK(h, cudaStreamSynchronize(h->s));
+    if (which == ITOKMC_FIRINGS && h->P.k_ep > 0.0) {
+        // the device keeps the electrons lost (attachments + e-ion
+        // recombinations) in block 1, the form its consumers read
+        int64_t* f = static_cast<int64_t*>(host_out);
+        for (size_t i = 0; i < cnt; ++i) f[cnt + i] -= f[3 * cnt + i];
+    }
     return cuda_check(h, cudaGetLastError(), "read_densities");
 }
 

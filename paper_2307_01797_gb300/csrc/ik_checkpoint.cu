@@ -140,6 +140,7 @@ extern "C" int itokmc_load(itokmc_handle* h, const char* path)
     ik::HandleView v;
     int rc = ik::handle_view(h, &v);
     if (rc) return rc;
+    *v.stage = 0;                                 // a checkpoint is a step boundary
     if (!path) return ik::handle_fail(h, ITOKMC_ERR_ARG, "load: NULL path");
     FILE* f = std::fopen(path, "rb");
     if (!f) return ik::handle_fail(h, ITOKMC_ERR_ARG, (std::string("load: cannot open ") + path).c_str());

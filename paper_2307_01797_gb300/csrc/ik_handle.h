@@ -20,6 +20,8 @@ struct HandleView {
     int64_t* step;        // step counter
     uint64_t G;           // cells of all realizations
     int field_prec;
+    int* stage;           // stage order: 0 particles not deposited since they
+                          // last changed, 1 transported, 2 KMC done
 };
 
 // Fills *v after waiting for the handle's streams (nothing of a step may be

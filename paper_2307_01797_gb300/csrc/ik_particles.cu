@@ -878,49 +878,71 @@ __device__ __forceinline__ int kmc_nu(int r, int i)
     return i == 0 ? (r == 0) - (r == 1) - (r == 3) : (i == 1 ? (r == 0) - (r == 3) - (r == 4) : (r == 1) - (r == 4));
 }
 
-template <class T>
+// REC = false compiles the first-order network alone (reactions 0-2, only
+// X_e enters): the same results as REC = true with k_ep = k_np = 0, whose
+// extra terms are exact zeros, without their cost.
+template <class T, bool REC>
 __device__ __forceinline__ void kmc_props(const T kr[5], const long long X[3], T a[5])
 {
-    const T xe = (T)X[0], xp = (T)X[1], xm = (T)X[2];
+    const T xe = (T)X[0];
     a[0] = kr[0] * xe;
     a[1] = kr[1] * xe;
     a[2] = kr[2] * xe;
-    a[3] = (kr[3] * xe) * xp;
-    a[4] = (kr[4] * xp) * xm;
+    if constexpr (REC) {
+        const T xp = (T)X[1], xm = (T)X[2];
+        a[3] = (kr[3] * xe) * xp;
+        a[4] = (kr[4] * xp) * xm;
+    } else {
+        a[3] = a[4] = (T)0;
+    }
 }
 
-template <class T>
+template <class T, bool REC>
+__device__ T kmc_total(const T a[5])
+{
+    const T A = (a[0] + a[1]) + a[2];
+    if constexpr (REC) return (A + a[3]) + a[4];
+    return A;
+}
+
+template <class T, bool REC>
 __device__ int kmc_cell(const Params& P, Stream& s, const long long X0[3], const T kr[5], long long fired[5])
 {
     using K = KT<T>;
+    constexpr int NR = REC ? 5 : 3;          // reactions that can fire
+    constexpr int NS = REC ? 3 : 1;          // species that enter a propensity
     long long X[3] = { X0[0], X0[1], X0[2] };
     const T dt = (T)P.dt;
     const long long nc = (long long)P.n_crit;
     T tau = (T)0;
-    const bool g2[3] = { kr[3] > (T)0, kr[3] > (T)0 || kr[4] > (T)0, kr[4] > (T)0 };
+    const bool g2[3] = { REC && kr[3] > (T)0, REC && (kr[3] > (T)0 || kr[4] > (T)0), REC && kr[4] > (T)0 };
 #pragma unroll
     for (int r = 0; r < 5; ++r) fired[r] = 0;
     for (int guard = 0; guard < 100000; ++guard) {
         if (!(tau < dt)) return 0;
         T a[5];
-        kmc_props<T>(kr, X, a);
-        const T A = (((a[0] + a[1]) + a[2]) + a[3]) + a[4];
+        kmc_props<T, REC>(kr, X, a);
+        const T A = kmc_total<T, REC>(a);
         if (!(A > (T)0)) return 0;
-        const long long L3 = X[0] < X[1] ? X[0] : X[1], L4 = X[1] < X[2] ? X[1] : X[2];
-        const bool crit[5] = { false, a[1] > (T)0 && X[0] < nc, false, a[3] > (T)0 && L3 < nc, a[4] > (T)0 && L4 < nc };
+        bool crit[5] = { false, a[1] > (T)0 && X[0] < nc, false, false, false };
+        if constexpr (REC) {
+            const long long L3 = X[0] < X[1] ? X[0] : X[1], L4 = X[1] < X[2] ? X[1] : X[2];
+            crit[3] = a[3] > (T)0 && L3 < nc;
+            crit[4] = a[4] > (T)0 && L4 < nc;
+        }
         T Ac = (T)0;
 #pragma unroll
-        for (int r = 0; r < 5; ++r) if (crit[r]) Ac = Ac + a[r];
+        for (int r = 0; r < NR; ++r) if (crit[r]) Ac = Ac + a[r];
         T dtnc = K::inf();
         if (!isinf(P.eps)) {
-            const bool reactant[3] = { true, (!crit[3] && kr[3] > (T)0) || (!crit[4] && kr[4] > (T)0),
-                                       !crit[4] && kr[4] > (T)0 };
+            const bool reactant[3] = { true, REC && ((!crit[3] && kr[3] > (T)0) || (!crit[4] && kr[4] > (T)0)),
+                                       REC && !crit[4] && kr[4] > (T)0 };
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
+            for (int i = 0; i < NS; ++i) {
                 if (!reactant[i]) continue;
                 T xi = (T)0, sig2 = (T)0;
 #pragma unroll
-                for (int r = 0; r < 5; ++r) {
+                for (int r = 0; r < NR; ++r) {
                     if (crit[r]) continue;
                     xi = xi + (T)kmc_nu(r, i) * a[r];
                     sig2 = sig2 + (T)(kmc_nu(r, i) * kmc_nu(r, i)) * a[r];
@@ -946,25 +968,27 @@ __device__ int kmc_cell(const Params& P, Stream& s, const long long X0[3], const
                 T t = (T)0;
                 for (int ev = 0; ev < P.n_ssa; ++ev) {
                     T as[5];
-                    kmc_props<T>(kr, Xs, as);
-                    const T As = (((as[0] + as[1]) + as[2]) + as[3]) + as[4];
+                    kmc_props<T, REC>(kr, Xs, as);
+                    const T As = kmc_total<T, REC>(as);
                     if (!(As > (T)0)) { t = dtau; break; }
                     const T dte = (-K::lg(K::uni(s))) / As;
                     if (t + dte > dtau) { t = dtau; break; }
                     t = t + dte;
                     const T target = K::uni(s) * As;
                     T cum = (T)0;
-                    int j = (as[3] > (T)0 || as[4] > (T)0) ? (as[4] > (T)0 ? 4 : 3) : 2;
+                    int j = (REC && (as[3] > (T)0 || as[4] > (T)0)) ? (as[4] > (T)0 ? 4 : 3) : 2;
 #pragma unroll
-                    for (int r = 0; r < 5; ++r) {
+                    for (int r = 0; r < NR; ++r) {
                         cum = cum + as[r];
                         if (cum > target) { j = r; break; }
                     }
 #pragma unroll
-                    for (int r = 0; r < 5; ++r) k[r] += (j == r);
+                    for (int r = 0; r < NR; ++r) k[r] += (j == r);
                     Xs[0] += (j == 0) - (j == 1) - (j == 3);
-                    Xs[1] += (j == 0) - (j == 3) - (j == 4);
-                    Xs[2] += (j == 1) - (j == 4);
+                    if constexpr (REC) {
+                        Xs[1] += (j == 0) - (j == 3) - (j == 4);
+                        Xs[2] += (j == 1) - (j == 4);
+                    }
                 }
                 adv = t;
             } else {
@@ -975,7 +999,7 @@ __device__ int kmc_cell(const Params& P, Stream& s, const long long X0[3], const
                     T cum = (T)0;
                     int rc = -1, last = -1;
 #pragma unroll
-                    for (int r = 0; r < 5; ++r) {
+                    for (int r = 0; r < NR; ++r) {
                         if (!crit[r]) continue;
                         last = r;
                         cum = cum + a[r];
@@ -983,10 +1007,10 @@ __device__ int kmc_cell(const Params& P, Stream& s, const long long X0[3], const
                     }
                     if (rc < 0) rc = last;
 #pragma unroll
-                    for (int r = 0; r < 5; ++r) k[r] += (rc == r);
+                    for (int r = 0; r < NR; ++r) k[r] += (rc == r);
                 }
 #pragma unroll
-                for (int r = 0; r < 5; ++r) {
+                for (int r = 0; r < NR; ++r) {
                     if (crit[r]) continue;
                     const long long kk = K::poisson(s, a[r] * dtau);
                     if (kk < 0) return -1;
@@ -995,31 +1019,28 @@ __device__ int kmc_cell(const Params& P, Stream& s, const long long X0[3], const
                 adv = dtau;
             }
             const long long Xn0 = X[0] + k[0] - k[1] - k[3];
-            const long long Xn1 = X[1] + k[0] - k[3] - k[4];
-            const long long Xn2 = X[2] + k[1] - k[4];
-            if (Xn0 < 0 || Xn1 < 0 || Xn2 < 0) {
+            if (Xn0 < 0) {
                 dtnc = dtau * (T)0.5;
                 continue;
             }
-            X[0] = Xn0; X[1] = Xn1; X[2] = Xn2;
+            if constexpr (REC) {
+                const long long Xn1 = X[1] + k[0] - k[3] - k[4];
+                const long long Xn2 = X[2] + k[1] - k[4];
+                if (Xn1 < 0 || Xn2 < 0) {
+                    dtnc = dtau * (T)0.5;
+                    continue;
+                }
+                X[1] = Xn1; X[2] = Xn2;
+            }
+            X[0] = Xn0;
 #pragma unroll
-            for (int r = 0; r < 5; ++r) fired[r] += k[r];
+            for (int r = 0; r < NR; ++r) fired[r] += k[r];
             if (adv >= rem) tau = dt; else tau = tau + adv;
             accepted = true;
         }
         if (!accepted) return -1;
     }
     return -1;
-}
-
-// Net electron gain of cell g from its firings: ionizations - attachments -
-// e-ion recombinations (the last block is read only when k_ep > 0; it stays
-// zero otherwise).
-__device__ __forceinline__ long long net_gain(const int64_t* __restrict__ fired, uint64_t G, uint64_t g, bool rec_ep)
-{
-    long long dN = fired[g] - fired[G + g];
-    if (rec_ep) dN -= fired[3 * G + g];
-    return dN;
 }
 
 // Cells with electrons -- or, with ion-ion recombination on, ions of both
@@ -1048,14 +1069,15 @@ __global__ void k_kmc_list(Params P, const unsigned long long* __restrict__ Xe, 
     }
 }
 
-template <class T>
-__global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const E64* __restrict__ E,
+// Residency: four blocks of 128 threads per SM in the FP64 form and with
+// recombination (<= 128 registers), five in the FP32 first-order form.
+template <class T, bool REC>
+__global__ void __launch_bounds__(128, (sizeof(T) == 8 || REC) ? 4 : 5) k_kmc(Params P, const unsigned long long* __restrict__ Xe, const E64* __restrict__ E,
                       const float4* __restrict__ E32, int64_t* __restrict__ fired, int64_t* __restrict__ Npos,
                       int64_t* __restrict__ Nneg, uint64_t G, const uint32_t* __restrict__ list,
                       uint32_t* __restrict__ pc_list, Counters* __restrict__ ctr)
 {
     unsigned long long t_ion = 0, t_att = 0, t_ph = 0, t_ep = 0, t_np = 0, t_slots = 0;
-    const bool rec = P.k_ep > 0.0 || P.k_np > 0.0;
     const uint64_t n = ctr->n_kmc_cells;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -1064,7 +1086,7 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
         if (t >= n) continue;
         const uint64_t g = list[t];
         long long f[5] = { 0, 0, 0, 0, 0 };
-        const long long X0[3] = { (long long)Xe[g], rec ? (long long)Npos[g] : 0, rec ? (long long)Nneg[g] : 0 };
+        const long long X0[3] = { (long long)Xe[g], REC ? (long long)Npos[g] : 0, REC ? (long long)Nneg[g] : 0 };
         T kr[5];
         kr[3] = (T)P.k_ep;
         kr[4] = (T)P.k_np;
@@ -1087,7 +1109,7 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
         const int r = real_of(P, (uint32_t)g);
         const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
         Stream s(seed_of(P, r), c, P.step, TAG_KMC, 0);
-        if (kmc_cell<T>(P, s, X0, kr, f) != 0) {
+        if (kmc_cell<T, REC>(P, s, X0, kr, f) != 0) {
             atomicOr(&ctr->err, DERR_KMC);
             ctr->kmc_fail_cell = (unsigned)g;
         }
@@ -1103,9 +1125,9 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
         t_ep += (unsigned long long)f[3];
         t_np += (unsigned long long)f[4];
         fired[g] = f[0];
-        fired[G + g] = f[1];
+        fired[G + g] = REC ? f[1] + f[3] : f[1];      // electrons lost: attachments + e-ion recombinations
         fired[2 * G + g] = f[2];
-        if (rec) {
+        if constexpr (REC) {
             fired[3 * G + g] = f[3];
             fired[4 * G + g] = f[4];
         }
@@ -1113,8 +1135,10 @@ __global__ void k_kmc(Params P, const unsigned long long* __restrict__ Xe, const
     warp_add(&ctr->ion, t_ion);
     warp_add(&ctr->att, t_att);
     warp_add(&ctr->phot, t_ph);
-    warp_add(&ctr->rec_ep, t_ep);
-    warp_add(&ctr->rec_np, t_np);
+    if constexpr (REC) {
+        warp_add(&ctr->rec_ep, t_ep);
+        warp_add(&ctr->rec_np, t_np);
+    }
     warp_add(&ctr->photo_slots, t_slots);
 }
 
@@ -1155,7 +1179,7 @@ __global__ void k_kmc0d(Params P, double Em, long long X0, uint32_t nreal, int n
             if (x > 0) {
                 const long long X3[3] = { x, 0, 0 };
                 Stream s(P.seed0, m, (uint32_t)k, TAG_KMC, 0);
-                if (kmc_cell<T>(P, s, X3, kr, f) != 0) atomicOr(&ctr->err, DERR_KMC);
+                if (kmc_cell<T, false>(P, s, X3, kr, f) != 0) atomicOr(&ctr->err, DERR_KMC);
             }
             x += f[0] - f[1];
             out[k + 1] = x;
@@ -1170,9 +1194,8 @@ __global__ void k_kmc0d(Params P, double Em, long long X0, uint32_t nreal, int n
 __global__ void k_loss(Params P, uint32_t* __restrict__ wbase, int wstride, const uint32_t* __restrict__ cs,
                        const unsigned long long* __restrict__ Xe, const int64_t* __restrict__ fired, uint64_t G)
 {
-    const bool rec_ep = P.k_ep > 0.0;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
-        const long long dN = net_gain(fired, G, g, rec_ep);
+        const long long dN = fired[g] - fired[G + g];
         if (dN >= 0) continue;
         const unsigned long long L = (unsigned long long)(-dN);
         const unsigned long long W = Xe[g];
@@ -1412,10 +1435,9 @@ struct MergeScanOp {
     uint32_t* list_n;         // [3]: lengths
     uint64_t G;
     int ppc, n_new, esize, ksize;
-    bool rec_ep;
     __device__ void load(uint64_t g, long long v[6]) const
     {
-        const long long dN = net_gain(fired, G, g, rec_ep);
+        const long long dN = fired[g] - fired[G + g];
         const long long W = (long long)Xe[g] + dN + (long long)photo_w[g];
         v[0] = W < ppc ? W : ppc;
         v[1] = photo_cnt[g];
@@ -1598,7 +1620,7 @@ __global__ void __launch_bounds__(128) k_merge_lv(
         const uint64_t g = list[li];
         const int r = real_of(P, (uint32_t)g);
         const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
-        const long long dN = net_gain(fired, G, g, P.k_ep > 0.0);
+        const long long dN = fired[g] - fired[G + g];
         const uint32_t e0 = cs[g], e1 = cs[g + 1];
         const uint32_t mprod = dN > 0 ? (uint32_t)(dN < P.n_new ? dN : P.n_new) : 0u;
         const uint32_t p0 = photo_off[g], np = photo_off[g + 1] - p0;
@@ -2436,15 +2458,30 @@ void launch_kmc0d(const Params& P, bool mixed, double Em, long long X0, uint32_t
 
 void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 {
+    // The stage's own counters start from zero on every call (firing totals,
+    // photon slots, the photon-cell and KMC-cell list lengths, and the
+    // absorbed photon weight the particles stage adds after it): a KMC stage
+    // run again without a transport stage between must not append to the
+    // lists of the previous run, whose lengths are bounded by G only per call.
+    static_assert(offsetof(Counters, n_kmc_cells) > offsetof(Counters, ion), "counter layout");
+    cudaMemsetAsync(reinterpret_cast<char*>(d.ctr) + offsetof(Counters, ion), 0,
+                    offsetof(Counters, n_kmc_cells) + sizeof(unsigned int) - offsetof(Counters, ion), s);
     // the merge's tier-0 list is free until the merge scan of this step
     g_launches += 2;
     k_kmc_list<<<grid_for(G, 256, 152 * 32), 256, 0, s>>>(P, d.Xe, d.Npos, d.Nneg, d.fired, G, d.small_list, d.ctr);
-    if (d.mixed)
-        k_kmc<float><<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G,
-                                                              d.small_list, d.pc_list, d.ctr);
-    else
-        k_kmc<double><<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G,
-                                                               d.small_list, d.pc_list, d.ctr);
+    const int nb = grid_for(G, 128, 152 * 64);
+    const bool rec = P.k_ep > 0.0 || P.k_np > 0.0;
+    if (d.mixed) {
+        if (rec) k_kmc<float, true><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G, d.small_list,
+                                                       d.pc_list, d.ctr);
+        else k_kmc<float, false><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G, d.small_list,
+                                                    d.pc_list, d.ctr);
+    } else {
+        if (rec) k_kmc<double, true><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G, d.small_list,
+                                                        d.pc_list, d.ctr);
+        else k_kmc<double, false><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G, d.small_list,
+                                                     d.pc_list, d.ctr);
+    }
 }
 
 // Part a: loss removal, photons, merge scan (offsets, output count, work).
@@ -2464,7 +2501,7 @@ void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
     }
     MergeScanOp op{ d.Xe, d.fired, d.photo_w, d.photo_cnt, d.cell_start, d.out_start, d.photo_off, d.work_off,
                     d.small_list, d.mid_list, d.big_list, d.list_n, G, P.ppc, P.n_new,
-                    d.mixed ? (int)sizeof(MP32) : (int)sizeof(MP), d.mixed ? 4 : 8, P.k_ep > 0.0 };
+                    d.mixed ? (int)sizeof(MP32) : (int)sizeof(MP), d.mixed ? 4 : 8 };
     run_scan<6>(op, G, d.scan_blk, s);
 }
 

@@ -140,6 +140,7 @@ int seed_blobs(itokmc_handle* h, const itokmc_seed_blob* blobs, int nb, int flag
     HandleView v;
     int rc = handle_view(h, &v);
     if (rc) return rc;
+    *v.stage = 0;
     Dev& d = *v.d;
     const Params& P = *v.P;
     const uint64_t G = v.G;

@@ -107,7 +107,8 @@ struct Dev {
     int64_t* Npos = nullptr;  int64_t* Nneg = nullptr;  int64_t* rho = nullptr;
     E64* E = nullptr;  float4* E32 = nullptr;
     // chemistry
-    int64_t* fired = nullptr;          // 5 G: ion, att, photon, e-ion and ion-ion recombination
+    int64_t* fired = nullptr;          // 5 G: ionizations, electrons lost (attachments + e-ion
+                                       // recombinations), photons, e-ion and ion-ion recombinations
     // photons
     Photo* photos = nullptr;  uint32_t* photo_sorted = nullptr;
     int32_t* photo_cnt = nullptr;  int32_t* photo_cursor = nullptr;

@@ -102,6 +102,62 @@ def test_kmc_and_particles_bit_exact():
     assert st_["photons_absorbed_weight"] + st_["photons_lost_weight"] == int(info["n_ph"].sum())
 
 
+def test_kmc_stage_rerun_starts_its_cell_lists_afresh():
+    """The KMC stage run four times on one transported state: every run lists
+    the active cells from zero (the lists hold at most one entry per cell per
+    run), gives the oracle's firings, and adds its ions once; the statistics
+    of the particles stage count one run's reactions."""
+    ph = small_phys(16, dt=5e-12, photon_ratio=0.06)
+    st = mixed_state(ph, seed=3, peak=2e19, n_random=800)
+    E = synth.random_field(ph, seed=9, amp=3e6, base=4.5e6)
+    ions = synth.random_ions(ph, seed=4)
+    seed0, step = 5, 2
+    S = oracle_state(ph, st, seed0, *ions)
+    _, info = oracle.step(oracle.make_params(ph, seed=seed0, step=step), S, E)
+    H = _setup(ph, st, E, ions, seed0, step)
+    H.itokmc_run_stage(itokmc.STAGE_TRANSPORT)
+    Np0 = H.itokmc_read_densities(itokmc.NPOS)
+    Nn0 = H.itokmc_read_densities(itokmc.NNEG)
+    runs = 4
+    for _ in range(runs):
+        H.itokmc_run_stage(itokmc.STAGE_KMC)
+        F = H.itokmc_read_densities(itokmc.FIRINGS)
+        assert np.array_equal(F[0], info["n_ion"]) and np.array_equal(F[1], info["n_att"])
+        assert np.array_equal(F[2], info["n_ph"])
+    assert np.array_equal(H.itokmc_read_densities(itokmc.NPOS), Np0 + runs * info["n_ion"])
+    assert np.array_equal(H.itokmc_read_densities(itokmc.NNEG), Nn0 + runs * info["n_att"])
+    H.itokmc_run_stage(itokmc.STAGE_PARTICLES)
+    s = H.itokmc_get_stats()
+    assert s["ionizations"] == int(info["n_ion"].sum()) and s["attachments"] == int(info["n_att"].sum())
+    H.close()
+
+
+def test_stages_out_of_order_are_refused():
+    """The KMC before any transport, the particles stage without a KMC after
+    the last transport, and a KMC after the particles stage are refused on
+    the host (ERR_ARG, nothing launched); the handle stays usable and the
+    stages in order then run."""
+    ph = small_phys(16, dt=5e-12)
+    st = mixed_state(ph, seed=3, n_random=500)
+    H = _setup(ph, st, synth.random_field(ph, seed=9, amp=3e6), synth.random_ions(ph, seed=4), 5)
+    with pytest.raises(itokmc.ItokmcError, match="stage order"):
+        H.itokmc_run_stage(itokmc.STAGE_KMC)
+    H.itokmc_run_stage(itokmc.STAGE_TRANSPORT)
+    with pytest.raises(itokmc.ItokmcError, match="stage order"):
+        H.itokmc_run_stage(itokmc.STAGE_PARTICLES)
+    H.itokmc_run_stage(itokmc.STAGE_KMC)
+    H.itokmc_run_stage(itokmc.STAGE_PARTICLES)
+    with pytest.raises(itokmc.ItokmcError, match="stage order"):
+        H.itokmc_run_stage(itokmc.STAGE_PARTICLES)
+    with pytest.raises(itokmc.ItokmcError, match="stage order"):
+        H.itokmc_run_stage(itokmc.STAGE_KMC)
+    H.itokmc_run_stage(itokmc.STAGE_FIELD)
+    H.itokmc_advance_counter()
+    H.itokmc_step(1)
+    assert H.itokmc_get_stats()["n_particles"] > 0
+    H.close()
+
+
 @pytest.mark.parametrize("dt", [5e-12, 5e-11])
 def test_semi_implicit_transport_against_oracle(dt):
     """The semi-implicit transport stage (Sec. 4.3, Sec. 4.7 steps 1-5): the
