@@ -325,7 +325,10 @@ __device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i > n 
 // fused correction; the same operations as the specification's).
 __device__ __forceinline__ double grid_quot(double x, double lo, double h, double rh)
 {
-    const double d = x - lo;
+    // x - 0 is x itself (also for -0): a domain corner at 0 (uniform across
+    // the launch) needs no subtraction on the FP64 pipe
+    double d = x;
+    if (__double_as_longlong(lo) != 0) d = x - lo;
     const double q0 = d * rh;
     return __fma_rn(__fma_rn(-q0, h, d), rh, q0);
 }

@@ -84,9 +84,11 @@ __device__ __forceinline__ double qfrac(unsigned long long F, int sh)
     const unsigned long long mant = (F << (52 - pb)) & 0xfffffffffffffull;
     return __longlong_as_double((long long)(((unsigned long long)(pb - sh + 1023) << 52) | mant));
 }
-// cic_axis with the split above (the FP64 steps for qd < 1/2).
+// cic_axis with the split above (the FP64 steps for qd < 1/2); g = 1 - f,
+// exact: 2^sh - F is at most 2^sh, so (2^sh - F) 2^-sh is the same double
+// as the FP64 subtraction 1 - f.
 __device__ __forceinline__ void cic_axis_q(double x, double lo, double h, double rh, int n, int& ia, int& ib,
-                                           double& f)
+                                           double& f, double& g)
 {
     const double qd = grid_quot(x, lo, h, rh);
     QSplit t;
@@ -94,11 +96,13 @@ __device__ __forceinline__ void cic_axis_q(double x, double lo, double h, double
     if (qsplit(qd, t)) {
         i0 = t.i0;
         f = qfrac(t.F, t.sh);
+        g = t.F == 0 ? 1.0 : qfrac((1ull << t.sh) - t.F, t.sh);
     } else {
         const double u = qd - 0.5;
         const double fl = floor(u);
         i0 = (int)fl;
         f = u - fl;
+        g = 1.0 - f;
     }
     ia = clampi(i0, n);
     ib = clampi(i0 + 1, n);
@@ -116,10 +120,10 @@ __device__ __forceinline__ void interp_f64(const Params& P, const E64* __restric
                                            double Ep[3])
 {
     int ia[3], ib[3];
-    double f[3];
+    double f[3], g[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) cic_axis_q(X[a], P.lo[a], P.h[a], P.rh[a], P.n, ia[a], ib[a], f[a]);
-    const double wx[2] = { 1.0 - f[0], f[0] }, wy[2] = { 1.0 - f[1], f[1] }, wz[2] = { 1.0 - f[2], f[2] };
+    for (int a = 0; a < 3; ++a) cic_axis_q(X[a], P.lo[a], P.h[a], P.rh[a], P.n, ia[a], ib[a], f[a], g[a]);
+    const double wx[2] = { g[0], f[0] }, wy[2] = { g[1], f[1] }, wz[2] = { g[2], f[2] };
     const int ix[2] = { ia[0], ib[0] }, iy[2] = { ia[1], ib[1] }, iz[2] = { ia[2], ib[2] };
     double ax = 0.0, ay = 0.0, az = 0.0;
 #pragma unroll
@@ -393,7 +397,7 @@ __device__ __forceinline__ double znormal(PairStream& s)
         const bool neg = (U >> 7) & 1u;
         const unsigned long long m = U >> 11;
         const double x = u53_exact(m) * __ldg(g_zig_w + i);
-        if (m < __ldg(g_zig_k + i)) return neg ? -x : x;
+        if (m < __ldg(g_zig_k + i)) return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));
         if (i == 0) {
             double xt, y;
             int tries = 0;

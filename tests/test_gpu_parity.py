@@ -218,15 +218,16 @@ def test_kmc_finite_eps_bit_exact():
 
 @pytest.mark.parametrize("ppc", [8, 32])
 def test_merge_tiers_bit_exact(ppc):
-    """Cells whose merge lists fall in each tier of the merge kernel (lists of
-    up to 96 and 256 elements in shared memory, longer ones in the global
-    work area), some with equal coordinates: the whole particles stage bit
-    for bit against the oracle."""
+    """Cells whose merge lists fall in each tier of the merge kernel (list plus
+    leaves up to 96 and 256 elements in shared memory, longer ones in the
+    global work area), some with equal coordinates: the whole particles stage
+    bit for bit against the oracle."""
     ph = small_phys(8, dt=1e-13, ppc=ppc, photon_ratio=0.0)
     rng = np.random.default_rng(17 + ppc)
     h = (ph["hi"][0] - ph["lo"][0]) / ph["n"]
     cols = {k: [] for k in ("x", "y", "z", "w")}
-    for (i, j, k), m in [((1, 1, 1), 30), ((4, 4, 4), 90), ((3, 4, 5), 150), ((6, 2, 3), 400)]:
+    for (i, j, k), m in [((1, 1, 1), 30), ((2, 5, 6), 20), ((5, 1, 2), 50), ((0, 6, 1), 70), ((4, 4, 4), 90),
+                         ((3, 4, 5), 150), ((6, 2, 3), 400)]:
         X = [ph["lo"][0] + (c + rng.uniform(0.05, 0.95, m)) * h for c in (i, j, k)]
         X[0][: m // 8] = X[0][0]            # equal x: the stable order decides
         X[2][m // 8: m // 4] = X[2][m // 8]
