@@ -2008,9 +2008,9 @@ __global__ void __launch_bounds__(128) k_merge_lv(
                         for (uint32_t q = q0; q < q1; ++q) {
                             const E e = cur[q];
                             const float wf = (float)e.w;
-                            sx = sx + wf * e.x;
-                            sy = sy + wf * e.y;
-                            sz = sz + wf * e.z;
+                            sx = __fmaf_rn(wf, e.x, sx);
+                            sy = __fmaf_rn(wf, e.y, sy);
+                            sz = __fmaf_rn(wf, e.z, sz);
                             Wl += e.w;
                         }
                         if (Wl > 0xffffffffull) atomicOr(&ctr->err, DERR_OVERFLOW);
