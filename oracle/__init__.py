@@ -67,6 +67,7 @@ class Params(ctypes.Structure):
         ("photon_ratio", ctypes.c_double), ("kappa_lo", ctypes.c_double), ("kappa_hi", ctypes.c_double),
         ("eps", ctypes.c_double), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint32),
         ("pad", ctypes.c_uint32), ("beta_ep", ctypes.c_double), ("beta_np", ctypes.c_double),
+        ("mu_ion", ctypes.c_double), ("D_ion", ctypes.c_double),
     ]
 
 
@@ -95,6 +96,8 @@ def make_params(phys: dict, seed: int, step: int = 0) -> Params:
     p.eps = float(phys.get("eps", float("inf")))
     p.beta_ep = float(phys.get("beta_ep", 0.0))
     p.beta_np = float(phys.get("beta_np", 0.0))
+    p.mu_ion = float(phys.get("mu_ion", 0.0))
+    p.D_ion = float(phys.get("D_ion", 0.0))
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     p.step = int(step) & 0xFFFFFFFF
     return p
@@ -131,8 +134,15 @@ def lib():
             L.ora_kmc.restype = ctypes.c_int
             L.ora_kmc_single.argtypes = [pp, i64, d, d, d, u32, pi64]; L.ora_kmc_single.restype = i64
             L.ora_kmc_network.argtypes = [pp, pi64, pd, u32, pi64, pi64]; L.ora_kmc_network.restype = ctypes.c_int
+            pi32 = ctypes.POINTER(ctypes.c_int32)
             L.ora_products_photons.argtypes = [pp, i64, pd, pd, pd, pu32, pi64, pi64, pi64, pi64, pi64,
-                                               pi64, pi64, pi64, pi64, pd, pd, pd, pu32, pi64, i64, pi64]
+                                               pi64, pi64, pi64, pi64, pd, pd, pd, pu32, pi64, i64, pi64,
+                                               pi64, pi32, pi32]
+            L.ora_push_species.argtypes = [pp, ctypes.c_int32, i64, pd, pd, pd, pd, pd, pd, pd, pd, pd, pi64]
+            L.ora_push_species.restype = None
+            L.ora_species_products.argtypes = [pp, ctypes.c_int32, pi64, pi64, pi64, pu32, pd, pd, pd, pu32, pi64,
+                                               pi64, pi32, pi32, i64]
+            L.ora_species_products.restype = i64
             L.ora_products_photons.restype = i64
             L.ora_merge.argtypes = [pp, pd, pd, pd, pu32, pi64, pd, pd, pd, pu32, pi64, i64]
             L.ora_merge.restype = i64
@@ -313,6 +323,7 @@ def merge_list(x, y, z, w, T):
 
 
 from . import stages  # noqa: E402  (stage wrappers and the step composition)
-from .stages import (push, sort_by_cell, deposit, kmc, products_photons, merge, step,  # noqa: E402,F401
+from .stages import (push, sort_by_cell, deposit, kmc, products_photons, merge, step, push_species,  # noqa: E402,F401
+                     species_products, step_mobile,  # noqa: E402,F401
                      rho_fixed)
 from .poisson import solve as solve_field  # noqa: E402,F401

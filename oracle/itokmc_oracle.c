@@ -69,9 +69,12 @@ typedef struct {
     uint32_t pad;
     double beta_ep;       /* electron-ion recombination coefficient m^3/s   */
     double beta_np;       /* ion-ion recombination coefficient m^3/s        */
+    double mu_ion;        /* ion mobility m^2/Vs (mobile ions)              */
+    double D_ion;         /* ion diffusion coefficient m^2/s (mobile ions)  */
 } ora_params;
 
-enum { TAG_INIT = 1, TAG_PUSH = 2, TAG_KMC = 3, TAG_PRODUCT = 4, TAG_PHOTON = 5 };
+enum { TAG_INIT = 1, TAG_PUSH = 2, TAG_KMC = 3, TAG_PRODUCT = 4, TAG_PHOTON = 5,
+       TAG_PUSH_POS = 6, TAG_PUSH_NEG = 7, TAG_PRODUCT_POS = 8, TAG_PRODUCT_NEG = 9 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as  */
@@ -502,12 +505,16 @@ static double interp(const ora_params* p, const double* F, const int ia[3], cons
 /* paper states removal for photons only; electrons are absorbed likewise).  */
 /* cell_out[i] = new linear cell, or -1 if removed.                          */
 /* ------------------------------------------------------------------------ */
-void ora_push(const ora_params* p, int64_t np, const double* x, const double* y, const double* z,
-              const double* Ex, const double* Ey, const double* Ez,
-              double* xo, double* yo, double* zo, int64_t* cell_out)
+/* The push of one species (Eq. ito_kernel with V = sgn(Z_s) mu_s E, Eq.     */
+/* Vk1): cmu = sgn(Z_s) mu_s (electrons -mu, positive ions +mu_ion, negative */
+/* ions -mu_ion), diffusion D_s, normals from the stream (i, step, tag).     */
+static void push_species(const ora_params* p, double cmu, double D, uint32_t tag, int64_t np,
+                         const double* x, const double* y, const double* z, const double* Ex,
+                         const double* Ey, const double* Ez, double* xo, double* yo, double* zo,
+                         int64_t* cell_out)
 {
-    double sdt = sqrt((2.0 * p->D) * p->dt);
-    double nmu = -p->mu;
+    double sdt = sqrt((2.0 * D) * p->dt);
+    double nmu = cmu;
     if (!zig_ready) zig_init();
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < np; ++i) {
@@ -517,7 +524,7 @@ void ora_push(const ora_params* p, int64_t np, const double* x, const double* y,
         for (int ax = 0; ax < 3; ++ax) cic_axis(p, ax, X[ax], &ia[ax], &ib[ax], &f[ax]);
         double Ep[3] = { interp(p, Ex, ia, ib, f), interp(p, Ey, ia, ib, f), interp(p, Ez, ia, ib, f) };
         ora_stream s;
-        stream_init(&s, p->seed, (uint32_t)i, p->step, TAG_PUSH, 0);
+        stream_init(&s, p->seed, (uint32_t)i, p->step, tag, 0);
         double N[3];
         for (int ax = 0; ax < 3; ++ax) N[ax] = ora_normal(&s);
         double Xn[3];
@@ -528,6 +535,31 @@ void ora_push(const ora_params* p, int64_t np, const double* x, const double* y,
         else
             cell_out[i] = -1;
     }
+}
+
+/* Species 0 electrons, 1 positive ions, 2 negative ions. */
+static void species_transport(const ora_params* p, int species, double* cmu, double* D, uint32_t* tag)
+{
+    if (species == 1) { *cmu = p->mu_ion; *D = p->D_ion; *tag = TAG_PUSH_POS; }
+    else if (species == 2) { *cmu = -p->mu_ion; *D = p->D_ion; *tag = TAG_PUSH_NEG; }
+    else { *cmu = -p->mu; *D = p->D; *tag = TAG_PUSH; }
+}
+
+void ora_push(const ora_params* p, int64_t np, const double* x, const double* y, const double* z,
+              const double* Ex, const double* Ey, const double* Ez,
+              double* xo, double* yo, double* zo, int64_t* cell_out)
+{
+    push_species(p, -p->mu, p->D, TAG_PUSH, np, x, y, z, Ex, Ey, Ez, xo, yo, zo, cell_out);
+}
+
+void ora_push_species(const ora_params* p, int32_t species, int64_t np, const double* x, const double* y,
+                      const double* z, const double* Ex, const double* Ey, const double* Ez, double* xo,
+                      double* yo, double* zo, int64_t* cell_out)
+{
+    double cmu, D;
+    uint32_t tag;
+    species_transport(p, species, &cmu, &D, &tag);
+    push_species(p, cmu, D, tag, np, x, y, z, Ex, Ey, Ez, xo, yo, zo, cell_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -959,7 +991,8 @@ int64_t ora_products_photons(const ora_params* p, int64_t np, const double* x, c
                              const int64_t* n_ph, const int64_t* n_ep, const int64_t* n_np,
                              int64_t* Npos, int64_t* Nneg,
                              double* nx, double* ny, double* nz, uint32_t* nw, int64_t* ncell_new,
-                             int64_t cap_new, int64_t* lost_photon_weight)
+                             int64_t cap_new, int64_t* lost_photon_weight, int64_t* nsrc, int32_t* nkind,
+                             int32_t* nslot)
 {
     (void)np; (void)x; (void)y; (void)z;
     int64_t ncell = (int64_t)p->n * p->n * p->n;
@@ -987,6 +1020,7 @@ int64_t ora_products_photons(const ora_params* p, int64_t np, const double* x, c
                 }
                 int rc = plist_push(&L, P[0], P[1], P[2], (uint64_t)(wq + (j == 0 ? rem : 0)), c);
                 if (rc) return rc;
+                if (nsrc) { nsrc[L.n - 1] = c; nkind[L.n - 1] = 0; nslot[L.n - 1] = (int32_t)j; }
             }
         } else if (dN < 0) {
             uint64_t Ls = (uint64_t)(-dN);
@@ -1017,6 +1051,7 @@ int64_t ora_products_photons(const ora_params* p, int64_t np, const double* x, c
                     Npos[dc] += wj;
                     int rc = plist_push(&L, Ya[0], Ya[1], Ya[2], (uint64_t)wj, dc);
                     if (rc) return rc;
+                    if (nsrc) { nsrc[L.n - 1] = c; nkind[L.n - 1] = 1; nslot[L.n - 1] = (int32_t)j; }
                 } else {
                     lost += wj;
                 }
@@ -1024,6 +1059,62 @@ int64_t ora_products_photons(const ora_params* p, int64_t np, const double* x, c
         }
     }
     *lost_photon_weight = lost;
+    return L.n;
+}
+
+/* Mobile ions: the gain or loss dN of one ion species per cell (positive    */
+/* ions n_ion - n_ep - n_np, negative ions n_att - n_np), with the electron  */
+/* products' rules of Sec. 4.4 and the species' stream tag: a gain gives     */
+/* m = min(dN, N_new) particles of weight dN div m (remainder on the first)  */
+/* uniform in the cell, stream (c, step, tag, j); a loss is removed from the */
+/* cell's ion particles by systematic integer sampling against X (the NGP    */
+/* ion count of the last deposit), stream (c, step, tag, N_new).  The new    */
+/* particles' source cell, kind (0) and slot go to nsrc / nkind / nslot.     */
+/* Returns their count, -1 (capacity) or -2 (weight overflow).              */
+int64_t ora_species_products(const ora_params* p, int32_t species, const int64_t* cell_start,
+                             const int64_t* X, const int64_t* dNs, uint32_t* w, double* nx, double* ny,
+                             double* nz, uint32_t* nw, int64_t* ncell_new, int64_t* nsrc, int32_t* nkind,
+                             int32_t* nslot, int64_t cap_new)
+{
+    int64_t ncell = (int64_t)p->n * p->n * p->n;
+    uint32_t tag = species == 2 ? TAG_PRODUCT_NEG : TAG_PRODUCT_POS;
+    ora_plist L = { nx, ny, nz, nw, ncell_new, 0, cap_new };
+    double h[3] = { cell_h(p, 0), cell_h(p, 1), cell_h(p, 2) };
+    for (int64_t c = 0; c < ncell; ++c) {
+        int ijk[3] = { (int)(c % p->n), (int)((c / p->n) % p->n), (int)(c / ((int64_t)p->n * p->n)) };
+        int64_t dN = dNs[c];
+        if (dN > 0) {
+            int64_t m = dN < p->n_new ? dN : p->n_new;
+            int64_t wq = dN / m, rem = dN % m;
+            for (int64_t j = 0; j < m; ++j) {
+                ora_stream s;
+                stream_init(&s, p->seed, (uint32_t)c, p->step, tag, (uint32_t)j);
+                double P[3];
+                for (int ax = 0; ax < 3; ++ax) {
+                    double u = stream_uniform(&s);
+                    P[ax] = p->lo[ax] + ((double)ijk[ax] + u) * h[ax];
+                }
+                int rc = plist_push(&L, P[0], P[1], P[2], (uint64_t)(wq + (j == 0 ? rem : 0)), c);
+                if (rc) return rc;
+                nsrc[L.n - 1] = c; nkind[L.n - 1] = 0; nslot[L.n - 1] = (int32_t)j;
+            }
+        } else if (dN < 0) {
+            uint64_t Ls = (uint64_t)(-dN);
+            uint64_t W = (uint64_t)X[c];
+            if (Ls > W) return -3;
+            ora_stream s;
+            stream_init(&s, p->seed, (uint32_t)c, p->step, tag, (uint32_t)p->n_new);
+            uint32_t a = stream_u32(&s), b = stream_u32(&s);
+            uint64_t R = (((uint64_t)a << 32) | b) % W;
+            unsigned __int128 C = 0;
+            for (int64_t q = cell_start[c]; q < cell_start[c + 1]; ++q) {
+                unsigned __int128 before = (C * Ls + R) / W;
+                C += w[q];
+                unsigned __int128 after = (C * Ls + R) / W;
+                w[q] = (uint32_t)(w[q] - (uint64_t)(after - before));
+            }
+        }
+    }
     return L.n;
 }
 

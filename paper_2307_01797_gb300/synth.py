@@ -55,6 +55,39 @@ def with_recombination(phys, T=300.0):
     return out
 
 
+def with_mobile_ions(phys, mu_ion=2e-4, T=300.0):
+    """A copy of ``phys`` with mobile ions (the ions as Ito particles, Sec.
+    4.3 Eq. particle_kernel with sgn(Z_s)): ion mobility mu_ion in m^2/Vs
+    (the paper gives none; 2e-4 is the order of N2+/O2- in air at 1 bar) and
+    the ions' diffusion coefficient from the Einstein relation at the gas
+    temperature T, D = mu k_B T / e."""
+    out = dict(phys)
+    out["mu_ion"] = float(mu_ion)
+    out["D_ion"] = float(mu_ion) * (1.380649e-23 * T / 1.602176634e-19)
+    return out
+
+
+def ion_particles(phys, seed, n_per_cell=2, mean=40, frac=0.4, cells=None):
+    """Ion superparticles (x, y, z, w, sorted by cell) on a random fraction of
+    the cells: n_per_cell particles uniform in each chosen cell sharing a
+    Poisson(mean) count (cells drawing 0 hold none)."""
+    n = phys["n"]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if cells is None:
+        cells = np.flatnonzero(rng.random(n ** 3) < frac)
+    N = rng.poisson(mean, len(cells)).astype(np.int64)
+    keep = N > 0
+    cells, N = cells[keep], N[keep]
+    m = np.minimum(N, n_per_cell)
+    reps, w = _split_counts(N, m)
+    c = cells[reps]
+    h = cell_size(phys)
+    lo = phys["lo"]
+    ijk = np.stack([c % n, (c // n) % n, c // (n * n)], axis=1)
+    X = [lo[a] + (ijk[:, a] + rng.random(len(c))) * h for a in range(3)]
+    return dict(x=X[0], y=X[1], z=X[2], w=w.astype(np.uint32))
+
+
 def physics_small(n=64):
     """64^3, 1 cm, 1.5 MV/m, dt = 1 ps, ppc = 8, photons off."""
     return _base(n, 0.01, 1.5e6, 1e-12, 8, False)
