@@ -153,6 +153,11 @@ typedef struct itokmc_config {
     double beta_ep, beta_np;   /* recombination coefficients (m^3/s), Sec. 5.1:
                                   k_ep = beta_ep / dV, k_np = beta_np / dV;
                                   0 (the defaults): the reaction is off       */
+    int32_t mobile_ions;       /* 0: ions as per-cell counts; 1: positive and
+                                  negative ions as Ito particles (explicit
+                                  coupling only)                             */
+    int32_t pad_ions;
+    double mu_ion, D_ion;      /* ion mobility (m^2/Vs), diffusion (m^2/s)   */
 } itokmc_config;
 
 typedef struct itokmc_stats {
@@ -171,6 +176,8 @@ typedef struct itokmc_stats {
     int64_t merge_cells, merge_elements, merge_elements_sq, merge_max_list; /* last a9 */
     double dt_last;            /* step size of the last step (s)             */
     int64_t recombinations_ep, recombinations_np; /* last a6                */
+    int64_t outflow_ion_pos, outflow_ion_neg;     /* ion weight absorbed at the
+                                                     faces, last step (mobile) */
 } itokmc_stats;
 
 typedef struct itokmc_handle itokmc_handle;
@@ -217,10 +224,21 @@ int itokmc_destroy(itokmc_handle* h);
 int itokmc_set_particles(itokmc_handle* h, const double* x, const double* y, const double* z,
                          const uint32_t* w, const int32_t* realization, int64_t n, int32_t mem);
 
+/* As itokmc_set_particles, with the species of each particle (int32, NULL:
+ * all electrons): 0 electrons, 1 positive ions, 2 negative ions (the ions as
+ * Ito particles, Sec. 4.3 Eq. particle_kernel with sgn(Z_s); species 1 and 2
+ * need mobile_ions = 1, else ERR_ARG).  Each species of each realization
+ * is a particle block b = species R + realization with its own cells;
+ * particles are sorted by (block, cell). */
+int itokmc_set_particles_species(itokmc_handle* h, const double* x, const double* y, const double* z,
+                                 const uint32_t* w, const int32_t* realization, const int32_t* species,
+                                 int64_t n, int32_t mem);
+
 /* Copies the particles (canonical order: by realization, cell, then the
  * order of the last sort/merge) into caller buffers of capacity cap.  Any
  * pointer may be NULL.  cell receives the linear cell index within the
- * realization.  *n_out receives the particle count; ERR_CAPACITY if it
+ * realization; realization receives the particle block (with mobile ions,
+ * species R + realization: blocks of electrons, positive, negative ions).  *n_out receives the particle count; ERR_CAPACITY if it
  * exceeds cap (nothing copied).  Synchronises the stream. */
 int itokmc_read_particles(itokmc_handle* h, double* x, double* y, double* z, uint32_t* w,
                           int32_t* realization, int64_t* cell, int64_t cap, int64_t* n_out,
@@ -242,7 +260,9 @@ int itokmc_read_particles(itokmc_handle* h, double* x, double* y, double* z, uin
  * flags), ERR_CAPACITY, ERR_OVERFLOW (a weight above 2^32 - 1), ERR_CUDA. */
 int itokmc_seed_blobs(itokmc_handle* h, const itokmc_seed_blob* blobs, int32_t n_blobs, int32_t flags);
 
-/* Sets the ion counts (int64, R n^3 each; host or device). */
+/* Sets the ion counts (int64, R n^3 each; host or device).  ERR_ARG with
+ * mobile ions (the ions are particles then; the counts read back by
+ * itokmc_read_densities are their NGP counts). */
 int itokmc_set_ions(itokmc_handle* h, const int64_t* npos, const int64_t* nneg, int32_t mem);
 
 /* Sets E directly (double, three blocks Ex, Ey, Ez of R n^3 each), bypassing

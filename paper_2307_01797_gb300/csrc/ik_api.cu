@@ -34,7 +34,8 @@ struct itokmc_handle {
     cudaStream_t sf = nullptr;    // field stream (the solve overlaps the particle stages)
     cudaEvent_t fork = nullptr, join = nullptr;
     int device = 0;
-    uint64_t G = 0;
+    uint64_t G = 0;           // cells of all realizations (field, KMC)
+    uint64_t Gp = 0;          // particle cells: G per species block (S G)
     uint32_t N = 0;           // particle count (host copy)
     uint32_t cap = 0;
     int64_t step = 0;
@@ -169,27 +170,49 @@ cudaError_t create_field_stream(cudaStream_t* sf)
 
 int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
+// The step-size dependent constants: sqrt(2 D dt) and the FP32 form's
+// drift and diffusion in cell units, for the electrons and (per species)
+// for every particle block.
+void set_step_consts(const itokmc_config* cfg, ik::Params& P, double dt)
+{
+    P.dt = dt;
+    P.sdt = sqrt((2.0 * cfg->D) * dt);
+    P.f_drift = (float)(-cfg->mu * dt / P.h[0]);
+    P.f_diff = (float)(P.sdt / P.h[0]);
+    const double sdt_ion = sqrt((2.0 * cfg->D_ion) * dt);
+    const double cmu[3] = { -cfg->mu, cfg->mu_ion, -cfg->mu_ion };
+    for (int s = 0; s < 3; ++s) {
+        P.cmu_sp[s] = cmu[s];
+        P.sdt_sp[s] = s == 0 ? P.sdt : sdt_ion;
+        P.f_drift_sp[s] = s == 0 ? P.f_drift : (float)(cmu[s] * dt / P.h[0]);
+        P.f_diff_sp[s] = (float)(P.sdt_sp[s] / P.h[0]);
+    }
+}
+
 // Kernel parameters of a configuration (grid of n^3 cells per realization).
 void fill_params(const itokmc_config* cfg, ik::Params& P)
 {
     const int n = cfg->n[0];
     P.n = n; P.n3 = n * n * n; P.R = cfg->n_realizations; P.log2n = ilog2(n);
+    P.S = cfg->mobile_ions ? 3 : 1;
+    P.B = P.S * P.R;
+    const uint32_t push_tags[3] = { ik::TAG_PUSH, ik::TAG_PUSH_POS, ik::TAG_PUSH_NEG };
+    const uint32_t prod_tags[3] = { ik::TAG_PRODUCT, ik::TAG_PRODUCT_POS, ik::TAG_PRODUCT_NEG };
+    for (int s = 0; s < 3; ++s) { P.push_tag_sp[s] = push_tags[s]; P.prod_tag_sp[s] = prod_tags[s]; }
     P.ppc = cfg->ppc; P.n_new = cfg->n_new; P.n_crit = cfg->n_crit; P.n_ssa = cfg->n_ssa; P.frac_bits = cfg->frac_bits;
     for (int a = 0; a < 3; ++a) {
         P.lo[a] = cfg->lo[a]; P.hi[a] = cfg->hi[a]; P.h[a] = (cfg->hi[a] - cfg->lo[a]) / n;
         P.rh[a] = 1.0 / P.h[a];
     }
-    P.dt = cfg->dt; P.mu = cfg->mu; P.D = cfg->D; P.alpha_A = cfg->alpha_A; P.alpha_B = cfg->alpha_B; P.eta = cfg->eta;
+    P.mu = cfg->mu; P.D = cfg->D; P.alpha_A = cfg->alpha_A; P.alpha_B = cfg->alpha_B; P.eta = cfg->eta;
     P.photon_ratio = cfg->photon_ratio; P.kappa_lo = cfg->kappa_lo; P.kappa_hi = cfg->kappa_hi; P.eps = cfg->eps;
-    P.sdt = sqrt((2.0 * cfg->D) * cfg->dt);
+    set_step_consts(cfg, P, cfg->dt);
     const double dV = (P.h[0] * P.h[1]) * P.h[2];
     P.k_ep = cfg->beta_ep / dV;
     P.k_np = cfg->beta_np / dV;
     P.E0 = cfg->E0;
     P.seed0 = cfg->seed0;
     P.step = 0;
-    P.f_drift = (float)(-cfg->mu * cfg->dt / P.h[0]);
-    P.f_diff = (float)(P.sdt / P.h[0]);
 }
 
 int status_of_err(itokmc_handle* h, unsigned err)
@@ -205,7 +228,7 @@ int status_of_err(itokmc_handle* h, unsigned err)
 // Copies N (from cell_start[G]) and the counters to the pinned mirror and waits.
 int readback(itokmc_handle* h)
 {
-    IK_CHECK(h, cudaMemcpyAsync(&h->rb->N, h->d.cell_start + h->G, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->s));
+    IK_CHECK(h, cudaMemcpyAsync(&h->rb->N, h->d.cell_start + h->Gp, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->s));
     IK_CHECK(h, cudaMemcpyAsync(&h->rb->ctr, h->d.ctr, sizeof(ik::Counters), cudaMemcpyDeviceToHost, h->s));
     IK_CHECK(h, cudaStreamSynchronize(h->s));
     IK_CHECK(h, cudaGetLastError());
@@ -224,16 +247,19 @@ int transport_body(itokmc_handle* h)
 {
     IK_CHECK(h, cudaEventRecord(h->ev[0], h->s));
     ik::launch_transport(h->P, h->d, h->N, h->s);
-    ik::launch_transport_finish(h->P, h->d, h->N, h->G, h->s);
+    ik::launch_transport_finish(h->P, h->d, h->N, h->Gp, h->s);
     ik::launch_rho(h->P, h->d, h->G, h->s);
     IK_CHECK(h, cudaEventRecord(h->ev[1], h->s));
     int rc = readback(h);
     if (rc) return rc;
     const ik::Counters& c = h->rb->ctr;
     h->st.n_movers = (int64_t)c.n_movers;
-    int64_t out = 0;
-    for (int r = 0; r < h->P.R; ++r) out += (int64_t)c.outflow[r];
-    h->st.outflow_weight = out;
+    // absorbed weight per particle block: electrons, then the ion species
+    int64_t out[3] = { 0, 0, 0 };
+    for (int b = 0; b < h->P.B; ++b) out[ik::species_of(h->P, b)] += (int64_t)c.outflow[b];
+    h->st.outflow_weight = out[0];
+    h->st.outflow_ion_pos = out[1];
+    h->st.outflow_ion_neg = out[2];
     h->st.ms_transport = elapsed(h, 0, 1);
     return status_of_err(h, c.err);
 }
@@ -258,8 +284,8 @@ int particles_body(itokmc_handle* h)
     // output count and merge work size are known after the merge scan
     uint64_t tail[2];
     uint32_t outn = 0;
-    IK_CHECK(h, cudaMemcpyAsync(&tail[0], h->d.work_off + h->G, sizeof(uint64_t), cudaMemcpyDeviceToHost, h->s));
-    IK_CHECK(h, cudaMemcpyAsync(&outn, h->d.out_start + h->G, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->s));
+    IK_CHECK(h, cudaMemcpyAsync(&tail[0], h->d.work_off + h->Gp, sizeof(uint64_t), cudaMemcpyDeviceToHost, h->s));
+    IK_CHECK(h, cudaMemcpyAsync(&outn, h->d.out_start + h->Gp, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->s));
     IK_CHECK(h, cudaStreamSynchronize(h->s));
     (void)tail[1];
     if (outn > h->cap) return fail(h, ITOKMC_ERR_CAPACITY, "particle capacity exceeded by the merge output");
@@ -324,6 +350,7 @@ int stage_field(itokmc_handle* h) { return stage_field_on(h, h->s, h->d.E, h->d.
 // the end of the step (into d.E), the advective substep, sort and deposit.
 int semi_transport_body(itokmc_handle* h, int32_t* cycles_out, double* rel_out)
 {
+    if (h->P.S != 1) return fail(h, ITOKMC_ERR_ARG, "semi-implicit transport: ions as per-cell counts only");
     ik::Dev& d = h->d;
     if (d.mixed || d.phi_F > 0)
         return fail(h, ITOKMC_ERR_ARG, "semi-implicit transport: FP64 form only");
@@ -365,16 +392,19 @@ int semi_transport_body(itokmc_handle* h, int32_t* cycles_out, double* rel_out)
     if (st == -3) return cuda_check(h, cudaGetLastError(), "semi-implicit field solve");
     if (st != 0) return fail(h, ITOKMC_ERR_NOCONV, "semi-implicit field: multigrid did not reach mg_rtol");
     ik::launch_advect(h->P, d, h->N, h->s);
-    ik::launch_transport_finish(h->P, d, h->N, h->G, h->s);
+    ik::launch_transport_finish(h->P, d, h->N, h->Gp, h->s);
     ik::launch_rho(h->P, d, h->G, h->s);
     IK_CHECK(h, cudaEventRecord(h->ev[1], h->s));
     rc = readback(h);
     if (rc) return rc;
     const ik::Counters& c = h->rb->ctr;
     h->st.n_movers = (int64_t)c.n_movers;
-    int64_t out = 0;
-    for (int r = 0; r < h->P.R; ++r) out += (int64_t)c.outflow[r];
-    h->st.outflow_weight = out;
+    // absorbed weight per particle block: electrons, then the ion species
+    int64_t out[3] = { 0, 0, 0 };
+    for (int b = 0; b < h->P.B; ++b) out[ik::species_of(h->P, b)] += (int64_t)c.outflow[b];
+    h->st.outflow_weight = out[0];
+    h->st.outflow_ion_pos = out[1];
+    h->st.outflow_ion_neg = out[2];
     h->st.ms_transport = elapsed(h, 0, 1);
     return status_of_err(h, c.err);
 }
@@ -491,10 +521,7 @@ int choose_step(itokmc_handle* h)
         while (j < 62 && std::ldexp(c.dt, -j) > b && std::ldexp(c.dt, -(j + 1)) >= c.dt_min) ++j;
         dt = std::ldexp(c.dt, -j);
     }
-    P.dt = dt;
-    P.sdt = sqrt((2.0 * c.D) * dt);
-    P.f_drift = (float)(-c.mu * dt / P.h[0]);
-    P.f_diff = (float)(P.sdt / P.h[0]);
+    set_step_consts(&c, P, dt);
     h->st.dt_last = dt;
     return ITOKMC_OK;
 }
@@ -519,7 +546,7 @@ int handle_view(itokmc_handle* h, HandleView* v)
     IK_GUARD(h);
     IK_CHECK(h, cudaStreamSynchronize(h->s));
     if (h->sf) IK_CHECK(h, cudaStreamSynchronize(h->sf));
-    *v = HandleView{ &h->cfg, &h->P, &h->d, h->s, &h->N, h->cap, &h->step, h->G, h->field_prec, &h->stage };
+    *v = HandleView{ &h->cfg, &h->P, &h->d, h->s, &h->N, h->cap, &h->step, h->G, h->field_prec, h->Gp, &h->stage };
     return ITOKMC_OK;
 }
 int handle_fail(itokmc_handle* h, int code, const char* msg) { return fail(h, code, msg); }
@@ -590,6 +617,13 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
         return fail(nullptr, ITOKMC_ERR_ARG, "adaptive step: 0 < dt_min <= dt, cfl, drt_factor, ion_factor >= 0");
     if (!(cfg->beta_ep >= 0.0 && cfg->beta_np >= 0.0 && std::isfinite(cfg->beta_ep) && std::isfinite(cfg->beta_np)))
         return fail(nullptr, ITOKMC_ERR_ARG, "recombination coefficients: finite, >= 0");
+    if (cfg->mobile_ions != 0 && cfg->mobile_ions != 1) return fail(nullptr, ITOKMC_ERR_ARG, "mobile_ions: 0 or 1");
+    if (cfg->mobile_ions && !(cfg->mu_ion >= 0.0 && cfg->D_ion >= 0.0 && std::isfinite(cfg->mu_ion) &&
+                              std::isfinite(cfg->D_ion)))
+        return fail(nullptr, ITOKMC_ERR_ARG, "mobile ions: finite mu_ion, D_ion >= 0");
+    if (cfg->mobile_ions && cfg->coupling != ITOKMC_EXPLICIT)
+        return fail(nullptr, ITOKMC_ERR_ARG, "mobile ions: explicit coupling only");
+    if (cfg->mobile_ions && 3 * R > ik::MAX_R) return fail(nullptr, ITOKMC_ERR_ARG, "mobile ions: 3 R particle blocks > MAX_R");
     if (cfg->coupling != ITOKMC_EXPLICIT && cfg->coupling != ITOKMC_SEMI_IMPLICIT)
         return fail(nullptr, ITOKMC_ERR_ARG, "coupling: ITOKMC_EXPLICIT or ITOKMC_SEMI_IMPLICIT");
     if (cfg->coupling == ITOKMC_SEMI_IMPLICIT &&
@@ -604,6 +638,8 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     h->field_prec = cfg->field_precision < 0 ? cfg->precision : cfg->field_precision;
     ik::Params& P = h->P;
     fill_params(cfg, P);
+    h->Gp = G * (uint64_t)P.S;
+    const uint64_t Gp = h->Gp;
     h->st.dt_last = cfg->dt;
 
     int rc = 0;
@@ -625,22 +661,24 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
         d.recB = dalloc_n<ik::P64>(h, cap, &rc);
     }
     d.keyB = dalloc_n<uint32_t>(h, cap, &rc);
-    d.cell_start = dalloc_n<uint32_t>(h, G + 1, &rc);
-    d.cell_start_B = dalloc_n<uint32_t>(h, G + 1, &rc);
-    d.out_start = dalloc_n<uint32_t>(h, G + 1, &rc);
-    d.cnt_new = dalloc_n<int32_t>(h, G, &rc);
-    d.in_cnt = dalloc_n<int32_t>(h, G, &rc);
-    d.in_before = dalloc_n<int32_t>(h, G, &rc);
-    d.cursor = dalloc_n<int32_t>(h, G, &rc);
-    d.delta = dalloc_n<int64_t>(h, G, &rc);
-    d.in_off = dalloc_n<uint32_t>(h, G + 1, &rc);
+    // particle-cell arrays: one block of n^3 per species and realization
+    d.cell_start = dalloc_n<uint32_t>(h, Gp + 1, &rc);
+    d.cell_start_B = dalloc_n<uint32_t>(h, Gp + 1, &rc);
+    d.out_start = dalloc_n<uint32_t>(h, Gp + 1, &rc);
+    d.cnt_new = dalloc_n<int32_t>(h, Gp, &rc);
+    d.in_cnt = dalloc_n<int32_t>(h, Gp, &rc);
+    d.in_before = dalloc_n<int32_t>(h, Gp, &rc);
+    d.cursor = dalloc_n<int32_t>(h, Gp, &rc);
+    d.delta = dalloc_n<int64_t>(h, Gp, &rc);
+    d.in_off = dalloc_n<uint32_t>(h, Gp + 1, &rc);
     const size_t nblk = (cap + ik::TPB - 1) / ik::TPB + 1;
     d.blk_stay = dalloc_n<uint32_t>(h, nblk, &rc);
     d.blk_prefix = dalloc_n<uint32_t>(h, nblk, &rc);
     d.movers = dalloc_n<ik::Mover>(h, cap, &rc);
     d.mover_sorted = dalloc_n<uint32_t>(h, cap, &rc);
-    d.ne_fix = dalloc_n<unsigned long long>(h, G, &rc);
-    d.Xe = dalloc_n<unsigned long long>(h, G, &rc);
+    d.ne_fix = dalloc_n<unsigned long long>(h, Gp, &rc);
+    d.Xe = dalloc_n<unsigned long long>(h, Gp, &rc);
+    d.gain = dalloc_n<int64_t>(h, Gp, &rc);
     d.Npos = dalloc_n<int64_t>(h, G, &rc);
     d.Nneg = dalloc_n<int64_t>(h, G, &rc);
     d.rho = dalloc_n<int64_t>(h, G, &rc);
@@ -660,15 +698,15 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     d.photo_cnt = dalloc_n<int32_t>(h, G, &rc);
     d.photo_cursor = dalloc_n<int32_t>(h, G, &rc);
     d.photo_w = dalloc_n<unsigned long long>(h, G, &rc);
-    d.photo_off = dalloc_n<uint32_t>(h, G + 1, &rc);
-    d.work_off = dalloc_n<uint64_t>(h, G + 1, &rc);
-    d.small_list = dalloc_n<uint32_t>(h, G, &rc);
-    d.mid_list = dalloc_n<uint32_t>(h, G, &rc);
-    d.big_list = dalloc_n<uint32_t>(h, G, &rc);
+    d.photo_off = dalloc_n<uint32_t>(h, Gp + 1, &rc);
+    d.work_off = dalloc_n<uint64_t>(h, Gp + 1, &rc);
+    d.small_list = dalloc_n<uint32_t>(h, Gp, &rc);
+    d.mid_list = dalloc_n<uint32_t>(h, Gp, &rc);
+    d.big_list = dalloc_n<uint32_t>(h, Gp, &rc);
     d.list_n = dalloc_n<uint32_t>(h, 4, &rc);
     d.pc_list = dalloc_n<uint32_t>(h, G, &rc);
     set_work(h, reinterpret_cast<unsigned char*>(dalloc(h, d.work_cap * 32, &rc)), d.work_cap);
-    const size_t se = 2 * std::max(std::max(ik::scan_scratch_elems(G, 6), ik::scan_scratch_elems(nblk, 3)),
+    const size_t se = 2 * std::max(std::max(ik::scan_scratch_elems(Gp, 6), ik::scan_scratch_elems(nblk, 3)),
                                    ik::radix_scratch_elems(h->cap));
     d.scan_blk = dalloc_n<long long>(h, se, &rc);
     d.scan_blk_elems = se;
@@ -763,6 +801,13 @@ int itokmc_destroy(itokmc_handle* h)
 int itokmc_set_particles(itokmc_handle* h, const double* x, const double* y, const double* z, const uint32_t* w,
                          const int32_t* realization, int64_t n, int32_t mem)
 {
+    return itokmc_set_particles_species(h, x, y, z, w, realization, nullptr, n, mem);
+}
+
+int itokmc_set_particles_species(itokmc_handle* h, const double* x, const double* y, const double* z,
+                                 const uint32_t* w, const int32_t* realization, const int32_t* species, int64_t n,
+                                 int32_t mem)
+{
     IK_GUARD(h);
     h->stage = 0;
     if (n < 0 || (n > 0 && (!x || !y || !z || !w))) return fail(h, ITOKMC_ERR_ARG, "bad particle arrays");
@@ -784,14 +829,17 @@ int itokmc_set_particles(itokmc_handle* h, const double* x, const double* y, con
         IK_CHECK(h, cudaMemcpyAsync(dw, w, n * sizeof(uint32_t), k, h->s));
         if (dr) IK_CHECK(h, cudaMemcpyAsync(dr, realization, n * sizeof(int32_t), k, h->s));
     }
-    ik::launch_set_particles(h->P, h->d, dx, dy, dz, dw, dr, (uint32_t)n, h->G, h->s);
+    // the species (mobile ions) in the push keys' buffer, free until the next push
+    int32_t* dsp = (species && n > 0) ? reinterpret_cast<int32_t*>(h->d.keyB) : nullptr;
+    if (dsp) IK_CHECK(h, cudaMemcpyAsync(dsp, species, n * sizeof(int32_t), k, h->s));
+    ik::launch_set_particles(h->P, h->d, dx, dy, dz, dw, dr, dsp, (uint32_t)n, h->Gp, h->s);
     int rc = readback(h);
     if (rc) return rc;
     if (h->rb->ctr.err) {
         h->N = 0;
-        cudaMemsetAsync(h->d.cell_start, 0, (h->G + 1) * sizeof(uint32_t), h->s);
+        cudaMemsetAsync(h->d.cell_start, 0, (h->Gp + 1) * sizeof(uint32_t), h->s);
         cudaStreamSynchronize(h->s);
-        return fail(h, ITOKMC_ERR_ARG, "particle outside the domain, zero weight or bad realization");
+        return fail(h, ITOKMC_ERR_ARG, "particle outside the domain, zero weight, bad realization or species");
     }
     h->N = (uint32_t)n;
     h->st.n_particles = n;
@@ -850,6 +898,8 @@ int itokmc_read_particles(itokmc_handle* h, double* x, double* y, double* z, uin
 int itokmc_set_ions(itokmc_handle* h, const int64_t* npos, const int64_t* nneg, int32_t mem)
 {
     IK_GUARD(h);
+    if (h->P.S != 1)
+        return fail(h, ITOKMC_ERR_ARG, "mobile ions are particles: set them with itokmc_set_particles_species");
     const cudaMemcpyKind k = mem == ITOKMC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     if (npos) IK_CHECK(h, cudaMemcpyAsync(h->d.Npos, npos, h->G * sizeof(int64_t), k, h->s));
     if (nneg) IK_CHECK(h, cudaMemcpyAsync(h->d.Nneg, nneg, h->G * sizeof(int64_t), k, h->s));
@@ -1001,8 +1051,9 @@ int itokmc_read_densities(itokmc_handle* h, int32_t r, int32_t which, void* host
     switch (which) {
     case ITOKMC_NE_FIX: src = h->d.ne_fix; break;
     case ITOKMC_XE: src = h->d.Xe; break;
-    case ITOKMC_NPOS: src = h->d.Npos; break;
-    case ITOKMC_NNEG: src = h->d.Nneg; break;
+    // mobile ions: the NGP counts of the ion blocks' last deposit
+    case ITOKMC_NPOS: src = h->P.S == 3 ? static_cast<const void*>(h->d.Xe + h->G) : h->d.Npos; break;
+    case ITOKMC_NNEG: src = h->P.S == 3 ? static_cast<const void*>(h->d.Xe + 2 * h->G) : h->d.Nneg; break;
     case ITOKMC_PHI:
         if (h->d.phi_F > 0) {
             ik::launch_phi_to_double(h->P, h->d, h->d.stage, h->s);
@@ -1024,12 +1075,6 @@ int itokmc_read_densities(itokmc_handle* h, int32_t r, int32_t which, void* host
                                     static_cast<const char*>(src) + (b * h->G + off) * 8, cnt * 8,
                                     cudaMemcpyDeviceToHost, h->s));
     IK_CHECK(h, cudaStreamSynchronize(h->s));
-    if (which == ITOKMC_FIRINGS && h->P.k_ep > 0.0) {
-        // the device keeps the electrons lost (attachments + e-ion
-        // recombinations) in block 1, the form its consumers read
-        int64_t* f = static_cast<int64_t*>(host_out);
-        for (size_t i = 0; i < cnt; ++i) f[cnt + i] -= f[3 * cnt + i];
-    }
     return cuda_check(h, cudaGetLastError(), "read_densities");
 }
 

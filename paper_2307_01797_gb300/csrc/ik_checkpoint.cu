@@ -22,7 +22,7 @@
 
 namespace {
 
-constexpr char MAGIC[8] = { 'I', 'T', 'O', 'K', 'M', 'C', 'K', '2' };
+constexpr char MAGIC[8] = { 'I', 'T', 'O', 'K', 'M', 'C', 'K', '3' };
 
 // The part of the configuration a checkpoint is bound to (the physics, the
 // grid and the form; not the allocator, the stream or the capacity).
@@ -36,6 +36,8 @@ struct CkptHeader {
     uint32_t N, pad1;
     uint64_t G;
     double beta_ep, beta_np;
+    int32_t mobile_ions, pad2;
+    double mu_ion, D_ion;
 };
 
 CkptHeader header_of(const ik::HandleView& v)
@@ -56,6 +58,7 @@ CkptHeader header_of(const ik::HandleView& v)
     H.N = *v.N;
     H.G = v.G;
     H.beta_ep = c.beta_ep; H.beta_np = c.beta_np;
+    H.mobile_ions = c.mobile_ions; H.mu_ion = c.mu_ion; H.D_ion = c.D_ion;
     return H;
 }
 
@@ -67,7 +70,7 @@ const char* mismatch(const CkptHeader& a, const CkptHeader& b)
     IK_SAME(n_new); IK_SAME(n_crit); IK_SAME(n_ssa); IK_SAME(lo); IK_SAME(hi); IK_SAME(dt); IK_SAME(mu);
     IK_SAME(D); IK_SAME(alpha_A); IK_SAME(alpha_B); IK_SAME(eta); IK_SAME(E0); IK_SAME(photon_ratio);
     IK_SAME(kappa_lo); IK_SAME(kappa_hi); IK_SAME(eps); IK_SAME(mg_rtol); IK_SAME(seed0); IK_SAME(G);
-    IK_SAME(beta_ep); IK_SAME(beta_np);
+    IK_SAME(beta_ep); IK_SAME(beta_np); IK_SAME(mobile_ions); IK_SAME(mu_ion); IK_SAME(D_ion);
 #undef IK_SAME
     return "";
 }
@@ -81,7 +84,7 @@ struct Blob {
 std::vector<Blob> blobs_of(const ik::HandleView& v, uint32_t N)
 {
     ik::Dev& d = *v.d;
-    const size_t G = v.G;
+    const size_t G = v.G, Gp = v.Gp;
     std::vector<Blob> b;
     if (d.mixed) {
         b.push_back({ d.rA32, (size_t)N * sizeof(ik::P32) });
@@ -91,15 +94,16 @@ std::vector<Blob> blobs_of(const ik::HandleView& v, uint32_t N)
         b.push_back({ d.recA, (size_t)N * sizeof(ik::P64) });
         b.push_back({ d.E, G * sizeof(ik::E64) });
     }
-    b.push_back({ d.cell_start, (G + 1) * sizeof(uint32_t) });
+    b.push_back({ d.cell_start, (Gp + 1) * sizeof(uint32_t) });
     b.push_back({ d.Npos, G * sizeof(int64_t) });
     b.push_back({ d.Nneg, G * sizeof(int64_t) });
     b.push_back({ d.lev[0].phi, G * sizeof(double) });     // FP64 potential, or the int64 fixed-point one
     b.push_back({ d.phi_prev, G * sizeof(double) });
-    b.push_back({ d.ne_fix, G * sizeof(unsigned long long) });
-    b.push_back({ d.Xe, G * sizeof(unsigned long long) });
+    b.push_back({ d.ne_fix, Gp * sizeof(unsigned long long) });
+    b.push_back({ d.Xe, Gp * sizeof(unsigned long long) });
     b.push_back({ d.rho, G * sizeof(int64_t) });
     b.push_back({ d.fired, 5 * G * sizeof(int64_t) });
+    b.push_back({ d.gain, Gp * sizeof(int64_t) });
     return b;
 }
 

@@ -18,6 +18,8 @@ namespace ik {
 struct Params {
     int n, n3;              // cells per axis, cells per realization
     int R;                  // realizations
+    int S;                  // particle species blocks: 1 (electrons), or 3 with mobile ions
+    int B;                  // particle blocks S R: block b holds species b / R of realization b % R
     int log2n;
     int ppc, n_new, n_crit, n_ssa, frac_bits;
     double lo[3], hi[3], h[3], rh[3];   // rh = 1/h
@@ -30,9 +32,18 @@ struct Params {
     // FP32 form constants (cell units)
     float f_drift;          // -mu dt / h   (multiplies E in V/m)
     float f_diff;           // sqrt(2 D dt) / h
+    // per species (electrons, positive ions, negative ions): drift
+    // coefficient sgn(Z) mu (V = cmu E), sqrt(2 D dt), the FP32 form's
+    // cmu dt / h and sqrt(2 D dt) / h, and the push and product stream tags
+    double cmu_sp[3], sdt_sp[3];
+    float f_drift_sp[3], f_diff_sp[3];
+    uint32_t push_tag_sp[3], prod_tag_sp[3];
 };
 
-enum : uint32_t { TAG_INIT = 1u, TAG_PUSH = 2u, TAG_KMC = 3u, TAG_PRODUCT = 4u, TAG_PHOTON = 5u };
+enum : uint32_t {
+    TAG_INIT = 1u, TAG_PUSH = 2u, TAG_KMC = 3u, TAG_PRODUCT = 4u, TAG_PHOTON = 5u,
+    TAG_PUSH_POS = 6u, TAG_PUSH_NEG = 7u, TAG_PRODUCT_POS = 8u, TAG_PRODUCT_NEG = 9u
+};
 
 // Device error word bits (OR-ed by kernels, read by the host after a stage).
 enum : uint32_t {
@@ -359,6 +370,10 @@ __device__ __forceinline__ int cell_axis(double x, double lo, double h, double r
 }
 
 __device__ __forceinline__ uint64_t seed_of(const Params& P, int r) { return P.seed0 + (uint64_t)r; }
+// Particle block b: species b / R, realization b % R (at most three species:
+// two comparisons instead of a division).
+__host__ __device__ __forceinline__ int species_of(const Params& P, int b) { return (b >= P.R) + (b >= 2 * P.R); }
+__host__ __device__ __forceinline__ int phys_of(const Params& P, int b) { return b - species_of(P, b) * P.R; }
 
 // ---------------------------------------------------------------- warp helpers
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

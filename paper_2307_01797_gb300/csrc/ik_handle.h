@@ -20,6 +20,7 @@ struct HandleView {
     int64_t* step;        // step counter
     uint64_t G;           // cells of all realizations
     int field_prec;
+    uint64_t Gp;          // particle cells (G per species block)
     int* stage;           // stage order: 0 particles not deposited since they
                           // last changed, 1 transported, 2 KMC done
 };

@@ -460,24 +460,25 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f64(
     if (i < N) {
         const P64 p = ld_p64(A + i);
         const uint32_t gold = p.cell;
-        const int r = real_of(P, gold);
+        const int r = real_of(P, gold);              // particle block: species r / R, realization r % R
         rr = r;
+        const int sp = species_of(P, r), rp = phys_of(P, r);
         const uint32_t idx = i - cell_start[(size_t)r * P.n3];
         const size_t ebase = (size_t)r * P.n3;
         w = p.w;
         const double X[3] = { p.x, p.y, p.z };
         double Ep[3];
-        interp_f64(P, E + ebase, X, Ep);
-        PairStream s(seed_of(P, r), idx, P.step, TAG_PUSH, 0);
+        interp_f64(P, E + (size_t)rp * P.n3, X, Ep);
+        PairStream s(seed_of(P, rp), idx, P.step, P.push_tag_sp[sp], 0);
         double Nn[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) Nn[a] = znormal(s);
-        const double nmu = -P.mu;
+        const double nmu = P.cmu_sp[sp], sdt = P.sdt_sp[sp];   // electrons: -mu, sqrt(2 D dt)
         double Xn[3];
         bool inside = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            Xn[a] = (X[a] + (nmu * Ep[a]) * P.dt) + P.sdt * Nn[a];
+            Xn[a] = (X[a] + (nmu * Ep[a]) * P.dt) + sdt * Nn[a];
             const unsigned long long kx = dkey(Xn[a]);
             inside = inside && kx >= dkey(P.lo[a]) && kx < dkey(P.hi[a]);
         }
@@ -774,12 +775,21 @@ __global__ void k_rho(Params P, const int64_t* __restrict__ Npos, const int64_t*
                       Counters* __restrict__ ctr)
 {
     unsigned long long amax = 0;
+    const bool mobile = P.S == 3;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
-        const long long dq = Npos[g] - Nneg[g];
         const unsigned long long ne = ne_fix[g];
-        const long long lim = 1ll << (62 - 3 * P.frac_bits);
-        if (dq >= lim || dq <= -lim || ne >= (1ull << 62)) atomicOr(&ctr->err, DERR_OVERFLOW);
-        const long long rf = dq * (1ll << (3 * P.frac_bits)) - (long long)ne;
+        long long rf;
+        if (mobile) {
+            // mobile ions: the CIC densities of the ion blocks, same units
+            const unsigned long long np_ = ne_fix[G + g], nn_ = ne_fix[2 * G + g];
+            if (ne >= (1ull << 62) || np_ >= (1ull << 62) || nn_ >= (1ull << 62)) atomicOr(&ctr->err, DERR_OVERFLOW);
+            rf = ((long long)np_ - (long long)nn_) - (long long)ne;
+        } else {
+            const long long dq = Npos[g] - Nneg[g];
+            const long long lim = 1ll << (62 - 3 * P.frac_bits);
+            if (dq >= lim || dq <= -lim || ne >= (1ull << 62)) atomicOr(&ctr->err, DERR_OVERFLOW);
+            rf = dq * (1ll << (3 * P.frac_bits)) - (long long)ne;
+        }
         rho[g] = rf;
         const unsigned long long a = (unsigned long long)(rf < 0 ? -rf : rf);
         amax = a > amax ? a : amax;
@@ -1052,14 +1062,31 @@ __device__ int kmc_cell(const Params& P, Stream& s, const long long X0[3], const
 // lanes busy: the active cells are a small part of the grid); the other
 // cells fire nothing.  The recombination blocks of the firings are touched
 // only when their reaction is on.
+// The ion counts of cell g: the NGP counts of the ion blocks' last deposit
+// (mobile ions), else the per-cell counts.
+__device__ __forceinline__ void ion_counts(const Params& P, const unsigned long long* __restrict__ Xe,
+                                           const int64_t* __restrict__ Npos, const int64_t* __restrict__ Nneg,
+                                           uint64_t G, uint64_t g, long long& xp, long long& xm)
+{
+    if (P.S == 3) { xp = (long long)Xe[G + g]; xm = (long long)Xe[2 * G + g]; }
+    else { xp = (long long)Npos[g]; xm = (long long)Nneg[g]; }
+}
+
 __global__ void k_kmc_list(Params P, const unsigned long long* __restrict__ Xe, const int64_t* __restrict__ Npos,
-                           const int64_t* __restrict__ Nneg, int64_t* __restrict__ fired, uint64_t G,
-                           uint32_t* __restrict__ list, Counters* __restrict__ ctr)
+                           const int64_t* __restrict__ Nneg, int64_t* __restrict__ fired,
+                           int64_t* __restrict__ gain, uint64_t G, uint32_t* __restrict__ list,
+                           Counters* __restrict__ ctr)
 {
     const bool rec = P.k_ep > 0.0 || P.k_np > 0.0;
     const bool ion_only = P.k_np > 0.0;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
-        if (Xe[g] > 0 || (ion_only && Npos[g] > 0 && Nneg[g] > 0)) {
+        bool run = Xe[g] > 0;
+        if (!run && ion_only) {
+            long long xp, xm;
+            ion_counts(P, Xe, Npos, Nneg, G, g, xp, xm);
+            run = xp > 0 && xm > 0;
+        }
+        if (run) {
             list[warp_slot32(&ctr->n_kmc_cells)] = (uint32_t)g;
         } else {
             fired[g] = 0;
@@ -1069,6 +1096,7 @@ __global__ void k_kmc_list(Params P, const unsigned long long* __restrict__ Xe, 
                 fired[3 * G + g] = 0;
                 fired[4 * G + g] = 0;
             }
+            for (int s = 0; s < P.S; ++s) gain[(uint64_t)s * G + g] = 0;
         }
     }
 }
@@ -1077,8 +1105,8 @@ __global__ void k_kmc_list(Params P, const unsigned long long* __restrict__ Xe, 
 // recombination (<= 128 registers), five in the FP32 first-order form.
 template <class T, bool REC>
 __global__ void __launch_bounds__(128, (sizeof(T) == 8 || REC) ? 4 : 5) k_kmc(Params P, const unsigned long long* __restrict__ Xe, const E64* __restrict__ E,
-                      const float4* __restrict__ E32, int64_t* __restrict__ fired, int64_t* __restrict__ Npos,
-                      int64_t* __restrict__ Nneg, uint64_t G, const uint32_t* __restrict__ list,
+                      const float4* __restrict__ E32, int64_t* __restrict__ fired, int64_t* __restrict__ gain,
+                      int64_t* __restrict__ Npos, int64_t* __restrict__ Nneg, uint64_t G, const uint32_t* __restrict__ list,
                       uint32_t* __restrict__ pc_list, Counters* __restrict__ ctr)
 {
     unsigned long long t_ion = 0, t_att = 0, t_ph = 0, t_ep = 0, t_np = 0, t_slots = 0;
@@ -1090,7 +1118,9 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 8 || REC) ? 4 : 5) k_kmc(Pa
         if (t >= n) continue;
         const uint64_t g = list[t];
         long long f[5] = { 0, 0, 0, 0, 0 };
-        const long long X0[3] = { (long long)Xe[g], REC ? (long long)Npos[g] : 0, REC ? (long long)Nneg[g] : 0 };
+        long long xp = 0, xm = 0;
+        if constexpr (REC) ion_counts(P, Xe, Npos, Nneg, G, g, xp, xm);
+        const long long X0[3] = { (long long)Xe[g], xp, xm };
         T kr[5];
         kr[3] = (T)P.k_ep;
         kr[4] = (T)P.k_np;
@@ -1117,8 +1147,16 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 8 || REC) ? 4 : 5) k_kmc(Pa
             atomicOr(&ctr->err, DERR_KMC);
             ctr->kmc_fail_cell = (unsigned)g;
         }
-        Npos[g] += (f[0] - f[3]) - f[4];
-        Nneg[g] += f[1] - f[4];
+        // net gains of the cell's particle species (Sec. 4.4); the per-cell
+        // ion counts when the ions are not particles
+        gain[g] = (f[0] - f[1]) - f[3];
+        if (P.S == 3) {
+            gain[G + g] = (f[0] - f[3]) - f[4];
+            gain[2 * G + g] = f[1] - f[4];
+        } else {
+            Npos[g] += (f[0] - f[3]) - f[4];
+            Nneg[g] += f[1] - f[4];
+        }
         if (f[2] > 0) {
             t_slots += (unsigned long long)(f[2] < P.n_new ? f[2] : P.n_new);
             pc_list[warp_slot32(&ctr->n_photo_cells)] = (uint32_t)g;
@@ -1129,7 +1167,7 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 8 || REC) ? 4 : 5) k_kmc(Pa
         t_ep += (unsigned long long)f[3];
         t_np += (unsigned long long)f[4];
         fired[g] = f[0];
-        fired[G + g] = REC ? f[1] + f[3] : f[1];      // electrons lost: attachments + e-ion recombinations
+        fired[G + g] = f[1];
         fired[2 * G + g] = f[2];
         if constexpr (REC) {
             fired[3 * G + g] = f[3];
@@ -1195,17 +1233,19 @@ __global__ void k_kmc0d(Params P, double Em, long long X0, uint32_t nreal, int n
 // Systematic integer removal of L = -dN electrons from the cell's particles
 // in canonical order: particle p loses floor((C_p L + R)/W) -
 // floor((C_{p-1} L + R)/W), R = (64-bit draw) mod W.
+// Gp particle cells: each block's species loses from its own particles,
+// against its own NGP count, with its own stream tag.
 __global__ void k_loss(Params P, uint32_t* __restrict__ wbase, int wstride, const uint32_t* __restrict__ cs,
-                       const unsigned long long* __restrict__ Xe, const int64_t* __restrict__ fired, uint64_t G)
+                       const unsigned long long* __restrict__ Xe, const int64_t* __restrict__ gain, uint64_t G)
 {
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < G; g += (uint64_t)gridDim.x * blockDim.x) {
-        const long long dN = fired[g] - fired[G + g];
+        const long long dN = gain[g];
         if (dN >= 0) continue;
         const unsigned long long L = (unsigned long long)(-dN);
         const unsigned long long W = Xe[g];
-        const int r = real_of(P, (uint32_t)g);
+        const int blk = real_of(P, (uint32_t)g);
         const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
-        Stream s(seed_of(P, r), c, P.step, TAG_PRODUCT, (uint32_t)P.n_new);
+        Stream s(seed_of(P, phys_of(P, blk)), c, P.step, P.prod_tag_sp[species_of(P, blk)], (uint32_t)P.n_new);
         const uint32_t a = s.u32(), b = s.u32();
         const unsigned long long R = (((unsigned long long)a << 32) | b) % W;
         if (W < (1ull << 32)) {
@@ -1346,7 +1386,7 @@ __global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired
             }
             if (wj > 0xffffffffll) atomicOr(&ctr->err, DERR_OVERFLOW);
             const uint32_t gd = (uint32_t)((size_t)r * P.n3 + ((size_t)iz * P.n + iy) * P.n + ix);
-            atomicAdd((unsigned long long*)(Npos + gd), (unsigned long long)wj);
+            if (P.S == 1) atomicAdd((unsigned long long*)(Npos + gd), (unsigned long long)wj);
             atomicAdd(photo_cnt + gd, 1);
             atomicAdd(photo_w + gd, (unsigned long long)wj);
             t_abs += (unsigned long long)wj;
@@ -1422,11 +1462,14 @@ constexpr uint32_t MERGE_CAP0_MP32 = 96, MERGE_CAP0_MP = 96, MERGE_CAP1 = 256;
 constexpr int MERGE_NW0 = 4, MERGE_NW1 = 4;
 __host__ __device__ inline uint32_t merge_cap0(int esize) { return esize == 16 ? MERGE_CAP0_MP32 : MERGE_CAP0_MP; }
 
-// Per cell: W = X_e + dN + photo weight -> min(W, ppc) leaves; photo offsets;
-// work-area units (32 B) for tier-2 cells; the tier lists.
+// Per particle cell: W = X + dN + photo weight -> min(W, ppc) leaves; photo
+// offsets; work-area units (32 B) for tier-2 cells; the tier lists.  The
+// photons of physical cell c are the electron block's photoelectrons and the
+// positive-ion block's photo-ions (mobile ions); the photo offsets count
+// them once, over the electron blocks.
 struct MergeScanOp {
     const unsigned long long* Xe;
-    const int64_t* fired;
+    const int64_t* gain;
     const unsigned long long* photo_w;
     const int32_t* photo_cnt;
     const uint32_t* cs;
@@ -1437,15 +1480,18 @@ struct MergeScanOp {
     uint32_t* mid_list;       // ... tier 1
     uint32_t* big_list;       // ... tier 2
     uint32_t* list_n;         // [3]: lengths
-    uint64_t G;
+    uint64_t G;               // particle cells
+    uint64_t Gphys;           // physical cells (one block per realization)
     int ppc, n_new, esize, ksize;
     __device__ void load(uint64_t g, long long v[6]) const
     {
-        const long long dN = fired[g] - fired[G + g];
-        const long long W = (long long)Xe[g] + dN + (long long)photo_w[g];
+        const long long dN = gain[g];
+        const uint64_t sp = (uint64_t)(g >= Gphys) + (uint64_t)(g >= 2 * Gphys), gph = g - sp * Gphys;
+        const long long pw = sp <= 1 ? (long long)photo_w[gph] : 0, pc = sp <= 1 ? photo_cnt[gph] : 0;
+        const long long W = (long long)Xe[g] + dN + pw;
         v[0] = W < ppc ? W : ppc;
-        v[1] = photo_cnt[g];
-        const long long M = (long long)(cs[g + 1] - cs[g]) + (dN > 0 ? (dN < n_new ? dN : n_new) : 0) + photo_cnt[g];
+        v[1] = sp == 0 ? pc : 0;
+        const long long M = (long long)(cs[g + 1] - cs[g]) + (dN > 0 ? (dN < n_new ? dN : n_new) : 0) + pc;
         const long long S = M + ppc;
         const int tier = S <= (long long)merge_cap0(esize) ? 0 : (S <= MERGE_CAP1 ? 1 : 2);
         v[2] = (v[0] > 0 && tier == 2)
@@ -1603,13 +1649,16 @@ constexpr uint8_t NO_SPLIT = 0xff;
 // so the weighted median, a scatter into the next level's list) and node-
 // parallel passes (axis, median bookkeeping).  GLOBAL: the scratch lives in
 // the work area (cells too long for shared memory).
+// Residency the registers are sized for: four blocks for the global tier,
+// seven (mixed form, whose shared scratch allows eight) or five (FP64 form,
+// held to five by its shared scratch) for the shared-memory tiers.
 template <class E, bool GLOBAL>
-__global__ void __launch_bounds__(128) k_merge_lv(
+__global__ void __launch_bounds__(128, GLOBAL ? 4 : (std::is_same<E, MP32>::value ? 7 : 5)) k_merge_lv(
     Params P, const P64* __restrict__ A, const P32* __restrict__ A32, const uint32_t* __restrict__ cs,
-    const int64_t* __restrict__ fired, const Photo* __restrict__ photos, const uint32_t* __restrict__ photo_sorted,
+    const int64_t* __restrict__ gain, const Photo* __restrict__ photos, const uint32_t* __restrict__ photo_sorted,
     const uint32_t* __restrict__ photo_off, const uint32_t* __restrict__ out_start,
     const uint64_t* __restrict__ work_off, unsigned char* __restrict__ work, uint64_t work_cap,
-    P64* __restrict__ out, P32* __restrict__ out32, uint32_t* __restrict__ cout, uint64_t G, uint32_t cap,
+    P64* __restrict__ out, P32* __restrict__ out32, uint32_t* __restrict__ cout, uint64_t Gphys, uint32_t cap,
     uint32_t photo_cap, const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_n, int tier,
     uint32_t CAP, Counters* __restrict__ ctr)
 {
@@ -1621,13 +1670,17 @@ __global__ void __launch_bounds__(128) k_merge_lv(
     const uint32_t ncells = list_n[tier];
     unsigned long long t_cells = 0, t_el = 0, t_sq = 0, t_max = 0;
     for (uint32_t li = blockIdx.x * nw + wid; li < ncells; li += gridDim.x * nw) {
-        const uint64_t g = list[li];
-        const int r = real_of(P, (uint32_t)g);
+        const uint64_t g = list[li];                  // particle cell
+        const int b = real_of(P, (uint32_t)g);
+        const int sp = species_of(P, b), r = phys_of(P, b);
         const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
-        const long long dN = fired[g] - fired[G + g];
+        const long long dN = gain[g];
         const uint32_t e0 = cs[g], e1 = cs[g + 1];
         const uint32_t mprod = dN > 0 ? (uint32_t)(dN < P.n_new ? dN : P.n_new) : 0u;
-        const uint32_t p0 = photo_off[g], np = photo_off[g + 1] - p0;
+        // the photons absorbed in this cell: photoelectrons of the electron
+        // block and, with mobile ions, photo-ions of the positive-ion block
+        const uint64_t ge = g - (uint64_t)sp * Gphys;
+        const uint32_t p0 = sp <= 1 ? photo_off[ge] : 0u, np = sp <= 1 ? photo_off[ge + 1] - p0 : 0u;
         const uint32_t Mmax = (e1 - e0) + mprod + np;
         if ((uint64_t)p0 + np > photo_cap || out_start[g + 1] > cap) {
             if (lane == 0) atomicOr(&ctr->err, DERR_CAPACITY);
@@ -1716,7 +1769,7 @@ __global__ void __launch_bounds__(128) k_merge_lv(
             const int ijk[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
                                  (int)(c >> (2 * P.log2n)) };
             for (uint32_t j = lane; j < mprod; j += 32) {
-                Stream st(seed_of(P, r), c, P.step, TAG_PRODUCT, j);
+                Stream st(seed_of(P, r), c, P.step, P.prod_tag_sp[sp], j);
                 E e;
                 if constexpr (MX) {
                     // FP32 uniforms from the high words of the FP64 ones
@@ -2112,13 +2165,15 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f32(
     if (i < N) {
         const P32 p = A[i];
         const uint32_t gold = __ldg(cA + i);
-        const int r = SINGLE ? 0 : real_of(P, gold);
+        const int r = SINGLE ? 0 : real_of(P, gold);      // particle block
         rr = r;
+        const int sp = SINGLE ? 0 : species_of(P, r), rp = SINGLE ? 0 : phys_of(P, r);
         const uint32_t c = gold & (uint32_t)(P.n3 - 1);
         const int id[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
                             (int)(c >> (2 * P.log2n)) };
         const uint32_t idx = SINGLE ? i : i - cell_start[(size_t)r * P.n3];
         const size_t ebase = SINGLE ? 0 : (size_t)r * P.n3;
+        const size_t fbase = SINGLE ? 0 : (size_t)rp * P.n3;
         w = p.w;
         const float o[3] = { p.ox, p.oy, p.oz };
         int ia[3], ib[3];
@@ -2135,14 +2190,14 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f32(
 #pragma unroll
                 for (int ax = 0; ax < 2; ++ax) {
                     const float wgt = __fmul_rn(__fmul_rn(wx[ax], wy[by]), wz[cz]);
-                    const float4 e = __ldg(E32 + ebase + ((size_t)iz[cz] * P.n + iy[by]) * P.n + ix[ax]);
+                    const float4 e = __ldg(E32 + fbase + ((size_t)iz[cz] * P.n + iy[by]) * P.n + ix[ax]);
                     ex = __fmaf_rn(wgt, e.x, ex);
                     ey = __fmaf_rn(wgt, e.y, ey);
                     ez = __fmaf_rn(wgt, e.z, ez);
                 }
         // the FP64 form's stream and words: the same ziggurat decisions, so
         // both forms draw common random numbers (equal to FP32 rounding)
-        PairStream zs(SINGLE ? P.seed0 : seed_of(P, r), idx, P.step, TAG_PUSH, 0);
+        PairStream zs(SINGLE ? P.seed0 : seed_of(P, rp), idx, P.step, SINGLE ? TAG_PUSH : P.push_tag_sp[sp], 0);
         float nrm[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) nrm[a] = znormal32(zs);
@@ -2152,7 +2207,7 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f32(
         bool inside = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float d = __fmaf_rn(P.f_drift, Ep[a], P.f_diff * nrm[a]);
+            const float d = __fmaf_rn(P.f_drift_sp[sp], Ep[a], P.f_diff_sp[sp] * nrm[a]);
             float x = o[a] + d;
             const float fl = floorf(x);
             x -= fl;
@@ -2277,7 +2332,7 @@ size_t scan_scratch_elems(uint64_t G, int C) { return (size_t)(scan_nblk(G) + 1)
 // ---------------------------------------------------------------- launchers
 void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
 {
-    const uint64_t G = (uint64_t)P.R * P.n3;
+    const uint64_t G = (uint64_t)P.B * P.n3;     // particle cells
     cudaMemsetAsync(d.cnt_new, 0, G * sizeof(int32_t), s);
     cudaMemsetAsync(d.in_cnt, 0, G * sizeof(int32_t), s);
     cudaMemsetAsync(d.in_before, 0, G * sizeof(int32_t), s);
@@ -2288,7 +2343,7 @@ void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
     if (N == 0) return;
     ++g_launches;
     if (d.mixed) {
-        auto k = P.R == 1 ? k_push_f32<true> : k_push_f32<false>;
+        auto k = P.B == 1 ? k_push_f32<true> : k_push_f32<false>;
         k<<<nblk, TPB, 0, s>>>(P, d.rA32, d.cellA32, d.rB32, d.keyB, N, d.cell_start, d.E32, d.cnt_new, d.in_cnt,
                                d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr, d.blk_stay);
     } else
@@ -2328,7 +2383,7 @@ void launch_diffuse(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
 // Deposit (ne_fix, X_e) of the records of recB (the diffused positions).
 void launch_deposit_B(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
 {
-    const uint64_t G = (uint64_t)P.R * P.n3;
+    const uint64_t G = (uint64_t)P.B * P.n3;
     cudaMemsetAsync(d.Xe, 0, G * sizeof(unsigned long long), s);
     cudaMemsetAsync(d.ne_fix, 0, G * sizeof(unsigned long long), s);
     if (N == 0) return;
@@ -2338,7 +2393,7 @@ void launch_deposit_B(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
 
 void launch_advect(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
 {
-    const uint64_t G = (uint64_t)P.R * P.n3;
+    const uint64_t G = (uint64_t)P.B * P.n3;
     cudaMemsetAsync(d.cnt_new, 0, G * sizeof(int32_t), s);
     cudaMemsetAsync(d.in_cnt, 0, G * sizeof(int32_t), s);
     cudaMemsetAsync(d.in_before, 0, G * sizeof(int32_t), s);
@@ -2382,7 +2437,7 @@ void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cu
 
 void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
 {
-    const uint64_t G = (uint64_t)P.R * P.n3;
+    const uint64_t G = (uint64_t)P.B * P.n3;
     cudaMemsetAsync(d.Xe, 0, G * sizeof(unsigned long long), s);
     cudaMemsetAsync(d.ne_fix, 0, G * sizeof(unsigned long long), s);
     if (N == 0) return;
@@ -2472,41 +2527,45 @@ void launch_kmc(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
                     offsetof(Counters, n_kmc_cells) + sizeof(unsigned int) - offsetof(Counters, ion), s);
     // the merge's tier-0 list is free until the merge scan of this step
     g_launches += 2;
-    k_kmc_list<<<grid_for(G, 256, 152 * 32), 256, 0, s>>>(P, d.Xe, d.Npos, d.Nneg, d.fired, G, d.small_list, d.ctr);
+    k_kmc_list<<<grid_for(G, 256, 152 * 32), 256, 0, s>>>(P, d.Xe, d.Npos, d.Nneg, d.fired, d.gain, G, d.small_list,
+                                                          d.ctr);
     const int nb = grid_for(G, 128, 152 * 64);
     const bool rec = P.k_ep > 0.0 || P.k_np > 0.0;
     if (d.mixed) {
-        if (rec) k_kmc<float, true><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G, d.small_list,
+        if (rec) k_kmc<float, true><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.gain, d.Npos, d.Nneg, G, d.small_list,
                                                        d.pc_list, d.ctr);
-        else k_kmc<float, false><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G, d.small_list,
+        else k_kmc<float, false><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.gain, d.Npos, d.Nneg, G, d.small_list,
                                                     d.pc_list, d.ctr);
     } else {
-        if (rec) k_kmc<double, true><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G, d.small_list,
+        if (rec) k_kmc<double, true><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.gain, d.Npos, d.Nneg, G, d.small_list,
                                                         d.pc_list, d.ctr);
-        else k_kmc<double, false><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.Npos, d.Nneg, G, d.small_list,
+        else k_kmc<double, false><<<nb, 128, 0, s>>>(P, d.Xe, d.E, d.E32, d.fired, d.gain, d.Npos, d.Nneg, G, d.small_list,
                                                      d.pc_list, d.ctr);
     }
 }
 
 // Part a: loss removal, photons, merge scan (offsets, output count, work).
+// G: physical cells (photons); the loss and the merge scan run over the
+// particle cells of every species block.
 void launch_particles_a(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
 {
+    const uint64_t Gp = (uint64_t)P.B * P.n3;
     cudaMemsetAsync(d.photo_cnt, 0, G * sizeof(int32_t), s);
     cudaMemsetAsync(d.photo_cursor, 0, G * sizeof(int32_t), s);
     cudaMemsetAsync(d.photo_w, 0, G * sizeof(unsigned long long), s);
     uint32_t* wbase = d.mixed ? reinterpret_cast<uint32_t*>(d.rA32) + 3 : reinterpret_cast<uint32_t*>(d.recA) + 7;
     const int wstride = d.mixed ? 4 : 8;
     ++g_launches;
-    k_loss<<<grid_for(G, 128, 152 * 64), 128, 0, s>>>(P, wbase, wstride, d.cell_start, d.Xe, d.fired, G);
+    k_loss<<<grid_for(Gp, 128, 152 * 64), 128, 0, s>>>(P, wbase, wstride, d.cell_start, d.Xe, d.gain, Gp);
     if (P.photon_ratio > 0.0) {
         ++g_launches;
         k_photons<<<152 * 16, 256, 0, s>>>(P, d.mixed ? 1 : 0, d.fired, G, d.pc_list, d.photos, d.photo_cap,
                                             d.photo_cnt, d.photo_w, d.Npos, d.ctr);
     }
-    MergeScanOp op{ d.Xe, d.fired, d.photo_w, d.photo_cnt, d.cell_start, d.out_start, d.photo_off, d.work_off,
-                    d.small_list, d.mid_list, d.big_list, d.list_n, G, P.ppc, P.n_new,
+    MergeScanOp op{ d.Xe, d.gain, d.photo_w, d.photo_cnt, d.cell_start, d.out_start, d.photo_off, d.work_off,
+                    d.small_list, d.mid_list, d.big_list, d.list_n, Gp, G, P.ppc, P.n_new,
                     d.mixed ? (int)sizeof(MP32) : (int)sizeof(MP), d.mixed ? 4 : 8 };
-    run_scan<6>(op, G, d.scan_blk, s);
+    run_scan<6>(op, Gp, d.scan_blk, s);
 }
 
 
@@ -2534,14 +2593,14 @@ void launch_merge_tiers(const Params& P, Dev& d, uint64_t G, cudaStream_t s, con
         s12 = d.side;
     }
     k_merge_lv<E, false><<<152 * 8, MERGE_NW1 * 32, sm1, s12>>>(
-        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
-        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.mid_list, d.list_n, 1, MERGE_CAP1, d.ctr);
+        P, A, A32, d.cell_start, d.gain, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
+        d.work_cap, out, out32, cout, (uint64_t)P.R * P.n3, d.mover_cap, d.photo_cap, d.mid_list, d.list_n, 1, MERGE_CAP1, d.ctr);
     k_merge_lv<E, true><<<152 * 4, 128, 0, s12>>>(
-        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
-        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.big_list, d.list_n, 2, 0, d.ctr);
+        P, A, A32, d.cell_start, d.gain, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
+        d.work_cap, out, out32, cout, (uint64_t)P.R * P.n3, d.mover_cap, d.photo_cap, d.big_list, d.list_n, 2, 0, d.ctr);
     k_merge_lv<E, false><<<152 * 16, MERGE_NW0 * 32, sm0, s>>>(
-        P, A, A32, d.cell_start, d.fired, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
-        d.work_cap, out, out32, cout, G, d.mover_cap, d.photo_cap, d.small_list, d.list_n, 0, cap0, d.ctr);
+        P, A, A32, d.cell_start, d.gain, d.photos, d.photo_sorted, d.photo_off, d.out_start, d.work_off, d.work,
+        d.work_cap, out, out32, cout, (uint64_t)P.R * P.n3, d.mover_cap, d.photo_cap, d.small_list, d.list_n, 0, cap0, d.ctr);
     if (d.side) {
         cudaEventRecord(d.side_join, d.side);
         cudaStreamWaitEvent(s, d.side_join, 0);
@@ -2569,7 +2628,7 @@ void launch_particles_b(const Params& P, Dev& d, uint64_t G, cudaStream_t s)
         k_photo_place<<<grid_for(d.photo_cap, 256, 1024), 256, 0, s>>>(d.photos, d.ctr, d.photo_cap, d.photo_off,
                                                                       d.photo_cursor, d.photo_sorted);
     }
-    launch_merges(P, d, G, s);
+    launch_merges(P, d, (uint64_t)P.B * P.n3, s);
     uint32_t* u = d.cell_start; d.cell_start = d.out_start; d.out_start = u;
 }
 

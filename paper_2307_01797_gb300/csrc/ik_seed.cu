@@ -131,6 +131,31 @@ __global__ void k_seed_write(Params P, const int64_t* __restrict__ cnt, const ui
 
 int grid_of(uint64_t n) { const uint64_t b = (n + 255) / 256; return (int)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b)); }
 
+// Mobile ions: the ion blocks' cell offsets after the electrons' (G cells),
+// and with pairs a positive ion at every seed electron's position and weight
+// (records [N, 2N) copy [0, N), their cells shifted by the G cells of the
+// electron blocks).
+__global__ void k_seed_ions(const uint32_t* __restrict__ cs_e, uint32_t* __restrict__ cs, uint32_t N, uint64_t G,
+                            int pairs, P64* __restrict__ rec, P32* __restrict__ rec32, uint32_t* __restrict__ cell32)
+{
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, st = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = t0; g <= G; g += st) {
+        cs[G + g] = pairs ? N + cs_e[g] : N;
+        cs[2 * G + g] = pairs ? 2 * N : N;
+    }
+    if (!pairs) return;
+    for (uint64_t i = t0; i < N; i += st) {
+        if (rec) {
+            P64 p = rec[i];
+            p.cell = (uint32_t)(p.cell + G);
+            rec[N + i] = p;
+        } else {
+            rec32[N + i] = rec32[i];
+            cell32[N + i] = (uint32_t)(cell32[i] + G);
+        }
+    }
+}
+
 }  // namespace
 
 // Seeds the particles of every realization (pass 1, scan, pass 2); the
@@ -173,19 +198,32 @@ int seed_blobs(itokmc_handle* h, const itokmc_seed_blob* blobs, int nb, int flag
         return handle_fail(h, ITOKMC_ERR_CUDA, "seed_blobs: count pass");
     if (err & DERR_OVERFLOW) return handle_fail(h, ITOKMC_ERR_OVERFLOW, "seed_blobs: a weight exceeds 2^32 - 1");
     if (err) return handle_fail(h, ITOKMC_ERR_KMC, "seed_blobs: Poisson sampler gave up");
-    if (total > v.cap) return handle_fail(h, ITOKMC_ERR_CAPACITY, "seed_blobs: more particles than particle_capacity");
+    const bool mobile = P.S == 3, pairs = mobile && (flags & ITOKMC_SEED_NEUTRAL);
+    if ((uint64_t)total * (pairs ? 2u : 1u) > v.cap)
+        return handle_fail(h, ITOKMC_ERR_CAPACITY, "seed_blobs: more particles than particle_capacity");
+    // the count model adds the pairs' ions to the positive-ion counts
+    const int neutral_counts = (flags & ITOKMC_SEED_NEUTRAL) && !mobile;
     g_launches += 1;
     if (d.mixed)
         k_seed_write<true><<<grid_of(G), 256, 0, s>>>(P, cnt, d.cell_start, v.cap, nullptr, d.rA32, d.cellA32, d.Npos,
-                                                      flags & ITOKMC_SEED_NEUTRAL, G);
+                                                      neutral_counts, G);
     else
         k_seed_write<false><<<grid_of(G), 256, 0, s>>>(P, cnt, d.cell_start, v.cap, d.recA, nullptr, nullptr, d.Npos,
-                                                       flags & ITOKMC_SEED_NEUTRAL, G);
+                                                       neutral_counts, G);
+    if (mobile) {
+        g_launches += 1;
+        // cs_e: the electron offsets [0, G]; the ion blocks' offsets go after
+        // them in the same array (a copy of [0, G] is not needed: each thread
+        // reads cs[g] before any thread writes index G + g' >= G, except g = G,
+        // whose value N both writes keep)
+        k_seed_ions<<<grid_of(G + 1), 256, 0, s>>>(d.cell_start, d.cell_start, total, G, pairs ? 1 : 0,
+                                                    d.mixed ? nullptr : d.recA, d.rA32, d.cellA32);
+    }
     // the firing counts were borrowed: no reaction has fired yet
     cudaMemsetAsync(d.fired, 0, 5 * G * sizeof(int64_t), s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return handle_fail(h, ITOKMC_ERR_CUDA, "seed_blobs: write pass");
-    *v.N = total;
+    *v.N = total * (pairs ? 2u : 1u);
     return ITOKMC_OK;
 }
 

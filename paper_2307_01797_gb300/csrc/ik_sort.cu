@@ -78,13 +78,15 @@ __global__ void __launch_bounds__(RS_TPB) k_rs_scatter(const uint32_t* __restric
 // Pack SoA input into records, compute global cells, validate.
 __global__ void k_pack(Params P, const double* __restrict__ x, const double* __restrict__ y,
                        const double* __restrict__ z, const uint32_t* __restrict__ w,
-                       const int32_t* __restrict__ real, uint32_t n, P64* __restrict__ out,
-                       uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, Counters* __restrict__ ctr)
+                       const int32_t* __restrict__ real, const int32_t* __restrict__ species, uint32_t n,
+                       P64* __restrict__ out, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                       Counters* __restrict__ ctr)
 {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double X[3] = { x[i], y[i], z[i] };
-        const int r = real ? real[i] : 0;
-        bool ok = r >= 0 && r < P.R && w[i] > 0;
+        const int r0 = real ? real[i] : 0, sp = species ? species[i] : 0;
+        bool ok = r0 >= 0 && r0 < P.R && sp >= 0 && sp < P.S && w[i] > 0;
+        const int r = sp * P.R + r0;             // particle block
         for (int a = 0; a < 3; ++a) ok = ok && X[a] >= P.lo[a] && X[a] < P.hi[a];
         uint32_t g = 0;
         if (ok) {
@@ -191,7 +193,8 @@ size_t radix_scratch_elems(uint32_t cap)
 // x, y, z, w, real are device pointers (already staged).  `tmp64` holds n
 // FP64 records during the sort.
 void launch_set_particles(const Params& P, Dev& d, const double* x, const double* y, const double* z,
-                          const uint32_t* w, const int32_t* real, uint32_t n, uint64_t G, cudaStream_t s)
+                          const uint32_t* w, const int32_t* real, const int32_t* species, uint32_t n, uint64_t G,
+                          cudaStream_t s)
 {
     uint32_t* keys = d.sort_tmp;
     uint32_t* vals = keys + d.mover_cap;
@@ -201,7 +204,7 @@ void launch_set_particles(const Params& P, Dev& d, const double* x, const double
     if (n > 0) {
         ++g_launches;
         P64* tmp64 = d.mixed ? reinterpret_cast<P64*>(d.work) + n : d.recB;   // staging sits at the start
-        k_pack<<<gsz(n, 256), 256, 0, s>>>(P, x, y, z, w, real, n, tmp64, keys, vals, d.ctr);
+        k_pack<<<gsz(n, 256), 256, 0, s>>>(P, x, y, z, w, real, species, n, tmp64, keys, vals, d.ctr);
         int bits = 1;
         while (bits < 32 && (1ull << bits) < G) ++bits;
         radix_sort_pairs(keys, vals, kt, vt, n, bits, s, d.scan_blk, 0);

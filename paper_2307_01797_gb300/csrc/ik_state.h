@@ -107,8 +107,9 @@ struct Dev {
     int64_t* Npos = nullptr;  int64_t* Nneg = nullptr;  int64_t* rho = nullptr;
     E64* E = nullptr;  float4* E32 = nullptr;
     // chemistry
-    int64_t* fired = nullptr;          // 5 G: ionizations, electrons lost (attachments + e-ion
-                                       // recombinations), photons, e-ion and ion-ion recombinations
+    int64_t* fired = nullptr;          // 5 G: ionizations, attachments, photons, e-ion and ion-ion
+                                       // recombinations of the last KMC
+    int64_t* gain = nullptr;           // Gp: net gain of each particle cell's species in the last KMC
     // photons
     Photo* photos = nullptr;  uint32_t* photo_sorted = nullptr;
     int32_t* photo_cnt = nullptr;  int32_t* photo_cursor = nullptr;
@@ -206,8 +207,8 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32
                       size_t blk_scratch_elems);
 size_t radix_scratch_elems(uint32_t cap);
 void launch_set_particles(const Params& P, Dev& d, const double* x, const double* y,
-                          const double* z, const uint32_t* w, const int32_t* real, uint32_t n,
-                          uint64_t G, cudaStream_t s);
+                          const double* z, const uint32_t* w, const int32_t* real, const int32_t* species,
+                          uint32_t n, uint64_t G, cudaStream_t s);
 // ik_field.cu
 int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2, unsigned long long rho_absmax,
                 int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out, bool extrapolate = false);

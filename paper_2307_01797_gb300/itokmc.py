@@ -50,6 +50,8 @@ class Config(ctypes.Structure):
         ("coupling", ctypes.c_int32), ("dt_adapt", ctypes.c_int32), ("dt_min", ctypes.c_double),
         ("cfl", ctypes.c_double), ("drt_factor", ctypes.c_double), ("ion_factor", ctypes.c_double),
         ("beta_ep", ctypes.c_double), ("beta_np", ctypes.c_double),
+        ("mobile_ions", ctypes.c_int32), ("pad_ions", ctypes.c_int32), ("mu_ion", ctypes.c_double),
+        ("D_ion", ctypes.c_double),
     ]
 
 
@@ -86,6 +88,7 @@ class Stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_int64), ("merge_cells", ctypes.c_int64), ("merge_elements", ctypes.c_int64),
         ("merge_elements_sq", ctypes.c_int64), ("merge_max_list", ctypes.c_int64), ("dt_last", ctypes.c_double),
         ("recombinations_ep", ctypes.c_int64), ("recombinations_np", ctypes.c_int64),
+        ("outflow_ion_pos", ctypes.c_int64), ("outflow_ion_neg", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -138,6 +141,7 @@ def lib(build_if_missing: bool = True):
                 "itokmc_init": ([ctypes.POINTER(Config), ctypes.POINTER(H)], ctypes.c_int),
                 "itokmc_destroy": ([H], ctypes.c_int),
                 "itokmc_set_particles": ([H, vp, vp, vp, vp, vp, i64, i32], ctypes.c_int),
+                "itokmc_set_particles_species": ([H, vp, vp, vp, vp, vp, vp, i64, i32], ctypes.c_int),
                 "itokmc_read_particles": ([H, vp, vp, vp, vp, vp, vp, i64, ctypes.POINTER(i64), i32], ctypes.c_int),
                 "itokmc_set_ions": ([H, vp, vp, i32], ctypes.c_int),
                 "itokmc_set_field": ([H, vp, i32], ctypes.c_int),
@@ -248,8 +252,9 @@ def make_config(phys: dict, capacity: int, realizations: int = 1, seed0: int = 1
     c.dt = float(phys["dt"])
     c.seed0 = int(seed0)
     for k in ("mu", "D", "alpha_A", "alpha_B", "eta", "E0", "photon_ratio", "kappa_lo", "kappa_hi",
-              "beta_ep", "beta_np"):
+              "beta_ep", "beta_np", "mu_ion", "D_ion"):
         setattr(c, k, float(phys.get(k, getattr(c, k))))
+    c.mobile_ions = int(bool(phys.get("mobile_ions", False)))
     c.eps = float(phys.get("eps", math.inf))
     for k in ("ppc", "n_new", "n_crit", "n_ssa", "frac_bits"):
         if k in phys:
@@ -309,6 +314,17 @@ class Handle:
         _check(lib().itokmc_set_particles(self.h, _ptr(x), _ptr(y), _ptr(z), _ptr(w), _ptr(realization), n, mem),
                self.h)
 
+    def itokmc_set_particles_species(self, x, y, z, w, species, realization=None, mem=HOST):
+        n = len(w)
+        if mem == HOST:
+            x = np.ascontiguousarray(x, np.float64); y = np.ascontiguousarray(y, np.float64)
+            z = np.ascontiguousarray(z, np.float64); w = np.ascontiguousarray(w, np.uint32)
+            species = np.ascontiguousarray(species, np.int32)
+            if realization is not None:
+                realization = np.ascontiguousarray(realization, np.int32)
+        _check(lib().itokmc_set_particles_species(self.h, _ptr(x), _ptr(y), _ptr(z), _ptr(w), _ptr(realization),
+                                                  _ptr(species), n, mem), self.h)
+
     def itokmc_read_particles(self):
         n = ctypes.c_int64()
         lib().itokmc_num_particles(self.h, ctypes.byref(n))
@@ -319,7 +335,8 @@ class Handle:
         c = np.empty(N, np.int64)
         _check(lib().itokmc_read_particles(self.h, _ptr(x), _ptr(y), _ptr(z), _ptr(w), _ptr(r), _ptr(c), N,
                                            ctypes.byref(n), HOST), self.h)
-        return dict(x=x, y=y, z=z, w=w, realization=r, cell=c)
+        # the particle block b: species b // R, realization b % R
+        return dict(x=x, y=y, z=z, w=w, realization=r % self.R, species=r // self.R, cell=c)
 
     def itokmc_set_ions(self, npos, nneg):
         npos = np.ascontiguousarray(npos, np.int64); nneg = np.ascontiguousarray(nneg, np.int64)
