@@ -67,6 +67,9 @@ def workload(args):
     ph = synth.physics_streamer(args.n)
     if getattr(args, "recombination", False):
         ph = synth.with_recombination(ph)
+    if getattr(args, "mobile_ions", False):
+        ph = synth.with_mobile_ions(ph)
+        ph["mobile_ions"] = True
     st = synth.streamer_tree_state(ph, int(args.particles), seed=7)
     ions = synth.streamer_ions(ph, st, seed=8)
     return ph, st, ions
@@ -189,6 +192,8 @@ def config_of(args, nparticles, fp64=True):
             "form": "fp64 plain" if fp64 else "mixed (fp32 + fixed point)",
             "chemistry": ("ionization, attachment, photon emission, e-ion and ion-ion recombination (air)"
                           if getattr(args, "recombination", False) else "ionization, attachment, photon emission"),
+            "ions": ("Ito particles (mu_ion 2e-4 m^2/Vs, D from the Einstein relation)"
+                     if getattr(args, "mobile_ions", False) else "per-cell counts"),
             "l2": "inputs > L2 (particle records of several GB; no flush)"}
 
 
@@ -210,13 +215,24 @@ def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e)
     """Warm up and time args.steps full steps of one form on the workload;
     returns the measurements (rank-local) and the handle's stats."""
     import torch
+    from paper_2307_01797_gb300 import synth
     N0 = len(st["w"])
+    mobile = bool(ph.get("mobile_ions", False))
+    if mobile:
+        # the ion counts as ion superparticles (the merge brings every species
+        # to ppc per occupied cell within a step)
+        ip = synth.ions_from_counts(ph, ions[0], seed=9, per_cell=ph["ppc"])
+        N0 += len(ip["w"])
     # photoelectrons landing in empty cells are split up to ppc particles each,
     # so the count grows from step to step
     cap = int(N0 * args.cap_factor) + 20_000_000
     H = itokmc.Handle(itokmc.make_config(ph, cap, seed0=1 + rank, precision=form))
-    H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
-    H.itokmc_set_ions(*ions)
+    if mobile:
+        sp = np.concatenate([np.zeros(len(st["w"]), np.int32), np.ones(len(ip["w"]), np.int32)])
+        H.itokmc_set_particles_species(*(np.concatenate([st[k], ip[k]]) for k in ("x", "y", "z", "w")), sp)
+    else:
+        H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+        H.itokmc_set_ions(*ions)
     H.itokmc_solve_field()
     tune = None if args.no_tune else H.itokmc_autotune()
     for _ in range(args.warmup):
@@ -914,6 +930,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default smoother counts (2, 2)")
     ap.add_argument("--recombination", action="store_true",
                     help="add the air recombination coefficients to the chemistry (five reactions)")
+    ap.add_argument("--mobile-ions", action="store_true",
+                    help="the ions as Ito particles beside the electrons (all-particle model)")
     ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small", "semi", "transport", "tree", "kmc0d"],
                     help="instead of the benchmark: one of the studies (see each function's docstring)")
     ap.add_argument("--slab", action="store_true", help="transport study: count-pinned uniform z-slab")
@@ -956,6 +974,11 @@ def main():
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.mobile_ions:
+        # a study of the all-particle model, not the headline: device-timed
+        # steps only (the end-to-end leg and the CPU leg use electrons only)
+        args.no_e2e = True
+        args.no_cpu_baseline = True
     if args.impl == "reference":
         reference_arm(args, rank, world)
     else:

@@ -88,6 +88,24 @@ def ion_particles(phys, seed, n_per_cell=2, mean=40, frac=0.4, cells=None):
     return dict(x=X[0], y=X[1], z=X[2], w=w.astype(np.uint32))
 
 
+def ions_from_counts(phys, N, seed, per_cell=8):
+    """Ion superparticles from per-cell counts N (int64 n^3): in each cell
+    with N > 0, m = min(N, per_cell) particles uniform in the cell sharing N
+    (near-equal integer weights).  Returns dict(x, y, z, w) sorted by cell."""
+    n = phys["n"]
+    N = np.asarray(N, np.int64)
+    cells = np.flatnonzero(N > 0)
+    m = np.minimum(N[cells], per_cell)
+    reps, w = _split_counts(N[cells], m)
+    c = cells[reps]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = cell_size(phys)
+    lo = phys["lo"]
+    ijk = np.stack([c % n, (c // n) % n, c // (n * n)], axis=1)
+    X = [lo[a] + (ijk[:, a] + rng.random(len(c))) * h for a in range(3)]
+    return dict(x=X[0], y=X[1], z=X[2], w=w.astype(np.uint32))
+
+
 def physics_small(n=64):
     """64^3, 1 cm, 1.5 MV/m, dt = 1 ps, ppc = 8, photons off."""
     return _base(n, 0.01, 1.5e6, 1e-12, 8, False)
