@@ -553,7 +553,8 @@ def ensemble_study(args):
     coupling = itokmc.SEMI_IMPLICIT if args.coupling == "semi" else itokmc.EXPLICIT
 
     def handle(form, blobs, R_, seed0, cap):
-        cfg = itokmc.make_config(ph, cap, realizations=R_, seed0=seed0, precision=form, coupling=coupling)
+        cfg = itokmc.make_config(ph, cap, realizations=R_, seed0=seed0, precision=form, coupling=coupling,
+                                 graph_step=1 if args.graph else 0)
         arr = itokmc.blob_array(blobs)
         cfg.blobs = itokmc.ctypes.cast(arr, itokmc.ctypes.c_void_p)
         cfg.n_blobs = len(blobs)
@@ -861,21 +862,27 @@ def small_study(args):
     N0, K = len(st["w"]), args.study_steps
     out = {"study": "small", "grid": 64, "particles0": N0, "steps": K, "forms": {}}
     for name, form in (("fp64", itokmc.FP64), ("mixed", itokmc.MIXED)):
-        H = itokmc.Handle(itokmc.make_config(ph, 8 * N0 + 100000, seed0=1, precision=form))
-        H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
-        H.itokmc_solve_field()
-        for _ in range(args.warmup):
-            H.itokmc_step(1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        done = 0
-        for _ in range(K):
-            done += H.itokmc_num_particles()
-            H.itokmc_step(1)
-        torch.cuda.synchronize()
-        t = time.perf_counter() - t0
-        H.close()
-        out["forms"][name] = {"ms_per_step": 1e3 * t / K, "particle_steps_per_s": done / t}
+        for graph in (0, 1):
+            H = itokmc.Handle(itokmc.make_config(ph, 8 * N0 + 100000, seed0=1, precision=form, graph_step=graph))
+            H.itokmc_set_particles(st["x"], st["y"], st["z"], st["w"])
+            H.itokmc_solve_field()
+            # the swapped device buffers cycle with period six: eight warm-up
+            # steps capture every graph a replayed run uses (both variants
+            # get the same warm-up)
+            for _ in range(max(args.warmup, 8)):
+                H.itokmc_step(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            done = 0
+            for _ in range(K):
+                done += H.itokmc_num_particles()
+                H.itokmc_step(1)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            gs = H.itokmc_get_stats()["graph_steps"]
+            H.close()
+            out["forms"][name + ("_graph" if graph else "")] = {
+                "ms_per_step": 1e3 * t / K, "particle_steps_per_s": done / t, "graph_steps": gs}
     # oracle chain and the GPU FP64 run on the oracle's fields
     p0 = oracle.make_params(ph, seed=1)
     S = oracle.canonical(p0, st)
@@ -930,6 +937,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default smoother counts (2, 2)")
     ap.add_argument("--recombination", action="store_true",
                     help="add the air recombination coefficients to the chemistry (five reactions)")
+    ap.add_argument("--graph", action="store_true",
+                    help="ensemble study: replay steps from captured CUDA graphs (graph_step = 1)")
     ap.add_argument("--mobile-ions", action="store_true",
                     help="the ions as Ito particles beside the electrons (all-particle model)")
     ap.add_argument("--study", default=None, choices=["precision", "ensemble", "small", "semi", "transport", "tree", "kmc0d"],

@@ -158,6 +158,8 @@ typedef struct itokmc_config {
                                   coupling only)                             */
     int32_t pad_ions;
     double mu_ion, D_ion;      /* ion mobility (m^2/Vs), diffusion (m^2/s)   */
+    int32_t graph_step;        /* 1: replay steps from captured CUDA graphs  */
+    int32_t pad_graph;         /* (explicit coupling, fixed dt; see below)   */
 } itokmc_config;
 
 typedef struct itokmc_stats {
@@ -178,6 +180,7 @@ typedef struct itokmc_stats {
     int64_t recombinations_ep, recombinations_np; /* last a6                */
     int64_t outflow_ion_pos, outflow_ion_neg;     /* ion weight absorbed at the
                                                      faces, last step (mobile) */
+    int64_t graph_steps;       /* steps replayed from captured graphs so far */
 } itokmc_stats;
 
 typedef struct itokmc_handle itokmc_handle;
@@ -273,6 +276,18 @@ int itokmc_set_field(itokmc_handle* h, const double* E, int32_t mem);
  * them and the current ions: the initial field of a run.  ERR_NOCONV if the
  * multigrid stops at mg_max_cycles above tolerance. */
 int itokmc_solve_field(itokmc_handle* h);
+
+/* Graph-replayed steps (graph_step = 1): with the explicit coupling and a
+ * fixed step size, once a host-driven step has measured the field solve's
+ * cycle count and the buffers' use, every further step with headroom in
+ * those buffers is one launch of a captured CUDA graph (cached per state of
+ * the swapped device buffers): the particle count and the step counter are
+ * read on the device, the field runs that many cycles beside the KMC and
+ * particle stages, and after the step the host checks the error word, the
+ * residual and the fixed-point scale (a field short of the tolerance is
+ * solved further on the host; its next replays run more cycles).  Results
+ * equal the host-driven step's for the same field; the stage timings of
+ * replayed steps read 0. */
 
 /* Adaptive step size (dt_adapt = 1).  The paper runs fixed steps and names
  * CFL- or physics-based dynamic time stepping as the way to use its

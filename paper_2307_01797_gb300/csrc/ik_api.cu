@@ -36,6 +36,17 @@ struct itokmc_handle {
     int device = 0;
     uint64_t G = 0;           // cells of all realizations (field, KMC)
     uint64_t Gp = 0;          // particle cells: G per species block (S G)
+    // graph-replayed steps: capture stream, cached graphs keyed by the device
+    // state they start from, the cycle count of their field solve, and the
+    // last step's buffer use (the headroom a replay needs)
+    cudaStream_t scap = nullptr;
+    struct GraphEntry;
+    std::vector<GraphEntry*> graphs;
+    int graph_cycles = 0;
+    uint32_t graph_nbound = 0;  // particle-count bound the next replay's grids cover
+    uint64_t last_photo_slots = 0, last_work = 0;
+    unsigned long long last_rho_absmax = 0;
+    int steps_done = 0;
     uint32_t N = 0;           // particle count (host copy)
     uint32_t cap = 0;
     int64_t step = 0;
@@ -47,7 +58,7 @@ struct itokmc_handle {
     std::vector<void*> allocs;
     itokmc_stats st{};
     cudaEvent_t ev[8]{};
-    struct Readback { uint32_t N; uint32_t pad; ik::Counters ctr; }* rb = nullptr;  // pinned
+    struct Readback { uint32_t N; uint32_t step; uint64_t work_need; ik::Counters ctr; }* rb = nullptr;  // pinned
 };
 
 namespace {
@@ -213,6 +224,7 @@ void fill_params(const itokmc_config* cfg, ik::Params& P)
     P.E0 = cfg->E0;
     P.seed0 = cfg->seed0;
     P.step = 0;
+    P.step_dev = nullptr;
 }
 
 int status_of_err(itokmc_handle* h, unsigned err)
@@ -289,6 +301,8 @@ int particles_body(itokmc_handle* h)
     IK_CHECK(h, cudaStreamSynchronize(h->s));
     (void)tail[1];
     if (outn > h->cap) return fail(h, ITOKMC_ERR_CAPACITY, "particle capacity exceeded by the merge output");
+    h->last_photo_slots = h->rb->ctr.photo_slots;
+    h->last_work = tail[0];
     rc = ensure_work_cap(h, tail[0]);
     if (rc) return rc;
     ik::launch_particles_b(h->P, h->d, h->G, h->s);
@@ -453,6 +467,224 @@ int stage_particles(itokmc_handle* h)
     return particles_body(h);
 }
 
+
+// ---------------------------------------------------------------- graph steps
+// A whole explicit step (transport, deposit and charge, the field solve on
+// its own stream beside KMC, products, photons and merge) captured once as a
+// CUDA graph and replayed: one launch per step, no host synchronisation
+// inside it.  The particle count is read on the device (grids cover the
+// capacity), the step counter from device memory, the field solve runs a
+// fixed number of cycles (the count the last host-driven solve needed) and
+// leaves its residual norms for a check after the step.  The device buffers
+// a step swaps (offsets, records, field) cycle with a short period, so a
+// graph is cached per starting state, with the state it leaves.
+struct DevState {
+    uint32_t *cell_start, *cell_start_B, *out_start, *cellA32, *cellB32, *photo_sorted;
+    ik::P64 *recA, *recB;
+    ik::P32 *rA32, *rB32;
+    ik::E64 *E, *E_next;
+    float4 *E32, *E32_next;
+    ik::Photo* photos;
+    unsigned char* work;
+    uint64_t work_cap, work_bytes;
+    uint32_t photo_cap;
+    int phi_F;
+    bool have_prev;
+};
+
+DevState snapshot(const ik::Dev& d)
+{
+    DevState x;
+    std::memset(&x, 0, sizeof x);
+    x.cell_start = d.cell_start; x.cell_start_B = d.cell_start_B; x.out_start = d.out_start;
+    x.cellA32 = d.cellA32; x.cellB32 = d.cellB32; x.photo_sorted = d.photo_sorted;
+    x.recA = d.recA; x.recB = d.recB; x.rA32 = d.rA32; x.rB32 = d.rB32;
+    x.E = d.E; x.E_next = d.E_next; x.E32 = d.E32; x.E32_next = d.E32_next;
+    x.photos = d.photos; x.work = d.work; x.work_cap = d.work_cap; x.work_bytes = d.work_bytes;
+    x.photo_cap = d.photo_cap; x.phi_F = d.phi_F; x.have_prev = d.have_prev;
+    return x;
+}
+
+void apply(ik::Dev& d, const DevState& x)
+{
+    d.cell_start = x.cell_start; d.cell_start_B = x.cell_start_B; d.out_start = x.out_start;
+    d.cellA32 = x.cellA32; d.cellB32 = x.cellB32; d.photo_sorted = x.photo_sorted;
+    d.recA = x.recA; d.recB = x.recB; d.rA32 = x.rA32; d.rB32 = x.rB32;
+    d.E = x.E; d.E_next = x.E_next; d.E32 = x.E32; d.E32_next = x.E32_next;
+    d.photos = x.photos; d.work = x.work; d.work_cap = x.work_cap; d.work_bytes = x.work_bytes;
+    d.photo_cap = x.photo_cap; d.phi_F = x.phi_F; d.have_prev = x.have_prev;
+}
+
+bool same(const DevState& a, const DevState& b) { return std::memcmp(&a, &b, sizeof a) == 0; }
+
+}  // namespace
+
+struct itokmc_handle::GraphEntry {
+    DevState before, after;
+    int cycles;
+    uint32_t nbound;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+void drop_graphs(itokmc_handle* h)
+{
+    for (auto* e : h->graphs) {
+        if (e->exec) cudaGraphExecDestroy(e->exec);
+        delete e;
+    }
+    h->graphs.clear();
+}
+
+// The launches of one step, issued on the capture stream (no waits).
+void graph_launches(itokmc_handle* h, int prec)
+{
+    ik::Dev& d = h->d;
+    ik::Params& P = h->P;
+    cudaStream_t s = h->scap;
+    const uint32_t* Ndev = d.cell_start + h->Gp;          // the count before the step
+    cudaMemcpyAsync(d.step_dev, &h->rb->step, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    ik::launch_transport(P, d, h->graph_nbound, s, Ndev);
+    ik::launch_transport_finish(P, d, h->graph_nbound, h->Gp, s, Ndev);
+    ik::launch_rho(P, d, h->G, s);
+    cudaEventRecord(h->fork, s);
+    cudaStreamWaitEvent(h->sf, h->fork, 0);
+    ik::field_solve_fixed(P, d, prec, h->cfg.mg_nu1, h->cfg.mg_nu2, h->graph_cycles, h->sf);
+    ik::launch_efield_to(P, d, h->sf, d.E_next, d.E32_next);
+    ik::launch_kmc(P, d, h->G, s);
+    ik::launch_particles_a(P, d, h->G, s);
+    ik::launch_particles_b(P, d, h->G, s);
+    cudaEventRecord(h->join, h->sf);
+    cudaStreamWaitEvent(s, h->join, 0);
+    cudaMemcpyAsync(&h->rb->ctr, d.ctr, sizeof(ik::Counters), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&h->rb->N, d.cell_start + h->Gp, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&h->rb->work_need, d.work_off + h->Gp, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(d.norm_host, d.norm_out, 2 * (size_t)P.R * sizeof(double), cudaMemcpyDeviceToHost, s);
+    std::swap(d.E, d.E_next);
+    std::swap(d.E32, d.E32_next);
+}
+
+// Whether the next step may be a replayed one: explicit coupling at a fixed
+// step size, at a step boundary, after a host-driven step has measured the
+// field's cycle count and the buffers' use, with headroom in every buffer a
+// step can fill (particles at most 2/3 of the capacity, photon slots and
+// merge work at most half their buffers, and a fixed-point potential scale
+// that holds for four times the last charge).
+bool graph_eligible(itokmc_handle* h)
+{
+    const itokmc_config& c = h->cfg;
+    if (!c.graph_step || c.dt_adapt || c.coupling != ITOKMC_EXPLICIT || h->stage != 0) return false;
+    if (h->steps_done < 1 || h->graph_cycles < 1 || h->graph_cycles > c.mg_max_cycles) return false;
+    if ((uint64_t)h->N * 3 > (uint64_t)h->cap * 2 || h->N == 0) return false;
+    // the transport grids cover the next power of two of the count (at most
+    // twice the work of exact grids; a count beyond it is a new graph)
+    uint64_t nb = 256;
+    while (nb < h->N) nb <<= 1;
+    h->graph_nbound = (uint32_t)std::min<uint64_t>(nb, h->cap);
+    // photon and merge-work buffers grow here, between steps, to twice the
+    // last use (a new buffer is a new starting state: its own graph)
+    if (ensure_photo_cap(h, 2 * h->last_photo_slots + 1024) || ensure_work_cap(h, 2 * h->last_work + 1024)) return false;
+    // the fixed-point potential's scale: lowered here, if need be, to one that
+    // holds for four times the last charge (the host-driven solve lowers it
+    // the same way when the charge requires)
+    if (h->d.phi_F > 0)
+        ik::lower_phi_scale(h->P, h->d, ik::phi_fixed_bits(ik::phi_bound(h->P, 4 * h->last_rho_absmax + 1)), h->s);
+    return h->d.have_prev;
+}
+
+int graph_step(itokmc_handle* h)
+{
+    ik::Dev& d = h->d;
+    const int prec = d.phi_F > 0 ? 2 : h->field_prec;
+    const DevState cur = snapshot(d);
+    itokmc_handle::GraphEntry* e = nullptr;
+    for (auto* x : h->graphs)
+        if (x->cycles == h->graph_cycles && x->nbound == h->graph_nbound && same(x->before, cur)) { e = x; break; }
+    h->rb->step = (uint32_t)h->step;
+    if (!e) {
+        if (h->graphs.size() >= 12) drop_graphs(h);
+        IK_CHECK(h, cudaStreamSynchronize(h->s));
+        const bool dc = d.direct_cycles;
+        d.direct_cycles = true;                  // V-cycles as plain launches inside the capture
+        h->P.step_dev = d.step_dev;
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(h->scap, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            graph_launches(h, prec);
+            ce = cudaStreamEndCapture(h->scap, &g);
+        }
+        h->P.step_dev = nullptr;
+        d.direct_cycles = dc;
+        const DevState after = snapshot(d);
+        apply(d, cur);
+        cudaGraphExec_t ex = nullptr;
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&ex, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return cuda_check(h, ce, "step graph capture");
+        e = new itokmc_handle::GraphEntry{ cur, after, h->graph_cycles, h->graph_nbound, ex };
+        h->graphs.push_back(e);
+    }
+    IK_CHECK(h, cudaGraphLaunch(e->exec, h->s));
+    ++h->st.graph_steps;
+    apply(d, e->after);
+    IK_CHECK(h, cudaStreamSynchronize(h->s));
+    IK_CHECK(h, cudaGetLastError());
+    // the step's results and checks
+    const ik::Counters& c = h->rb->ctr;
+    h->N = h->rb->N;
+    h->stage = 0;
+    h->last_photo_slots = c.photo_slots;
+    h->last_work = h->rb->work_need;
+    h->last_rho_absmax = c.rho_absmax;
+    h->st.n_movers = (int64_t)c.n_movers;
+    int64_t out[3] = { 0, 0, 0 };
+    for (int b = 0; b < h->P.B; ++b) out[ik::species_of(h->P, b)] += (int64_t)c.outflow[b];
+    h->st.outflow_weight = out[0];
+    h->st.outflow_ion_pos = out[1];
+    h->st.outflow_ion_neg = out[2];
+    h->st.ionizations = (int64_t)c.ion;
+    h->st.attachments = (int64_t)c.att;
+    h->st.photon_emissions = (int64_t)c.phot;
+    h->st.recombinations_ep = (int64_t)c.rec_ep;
+    h->st.recombinations_np = (int64_t)c.rec_np;
+    h->st.photons_absorbed_weight = (int64_t)c.absorbed_w;
+    int64_t lost = 0;
+    for (int r = 0; r < h->P.R; ++r) lost += (int64_t)c.lost[r];
+    h->st.photons_lost_weight = lost;
+    h->st.n_new_particles = (int64_t)c.n_photo;
+    h->st.kmc_status = (c.err & ik::DERR_KMC) ? ITOKMC_ERR_KMC : 0;
+    h->st.merge_cells = (int64_t)c.merge_cells;
+    h->st.merge_elements = (int64_t)c.merge_elems;
+    h->st.merge_elements_sq = (int64_t)c.merge_elems2;
+    h->st.merge_max_list = (int64_t)c.merge_maxm;
+    h->st.ms_transport = h->st.ms_kmc = h->st.ms_particles = h->st.ms_field = 0.0;
+    if (c.err) return status_of_err(h, c.err);
+    if (h->N > h->cap) return fail(h, ITOKMC_ERR_CAPACITY, "particle capacity exceeded by the merge output");
+    int rc = ensure_work_cap(h, h->last_work);
+    if (!rc) rc = ensure_photo_cap(h, h->last_photo_slots);
+    if (rc) return rc;
+    // the field: tolerance reached and the fixed-point scale still valid, else
+    // the host-driven solve continues from the replayed one
+    double worst = 0.0;
+    bool done = true;
+    for (int r = 0; r < h->P.R; ++r) {
+        const double rn = std::sqrt(d.norm_host[2 * r]), bn = std::sqrt(d.norm_host[2 * r + 1]);
+        const double rel = bn > 0.0 ? rn / bn : rn;
+        if (rel > worst || !(rel == rel)) worst = rel;
+        if (!(rn <= h->cfg.mg_rtol * bn)) done = false;
+    }
+    const bool scale_ok = d.phi_F == 0 || ik::phi_fixed_bits(ik::phi_bound(h->P, c.rho_absmax)) >= d.phi_F;
+    h->st.mg_cycles = h->graph_cycles;
+    h->st.mg_rel_residual = worst;
+    if (!done || !scale_ok) {
+        rc = stage_field_on(h, h->s, d.E, d.E32, c.rho_absmax, false);
+        if (rc) return rc;
+        h->graph_cycles = std::max(h->graph_cycles, h->st.mg_cycles + h->graph_cycles);
+    }
+    return ITOKMC_OK;
+}
+
 int full_step(itokmc_handle* h)
 {
     int rc = stage_transport(h);
@@ -483,6 +715,8 @@ int full_step(itokmc_handle* h)
     if (frc) return fail(h, frc, ferr);
     std::swap(h->d.E, h->d.E_next);
     std::swap(h->d.E32, h->d.E32_next);
+    h->graph_cycles = h->st.mg_cycles;
+    h->last_rho_absmax = amax;
     return ITOKMC_OK;
 }
 
@@ -679,6 +913,7 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
     d.ne_fix = dalloc_n<unsigned long long>(h, Gp, &rc);
     d.Xe = dalloc_n<unsigned long long>(h, Gp, &rc);
     d.gain = dalloc_n<int64_t>(h, Gp, &rc);
+    d.step_dev = dalloc_n<uint32_t>(h, 1, &rc);
     d.Npos = dalloc_n<int64_t>(h, G, &rc);
     d.Nneg = dalloc_n<int64_t>(h, G, &rc);
     d.rho = dalloc_n<int64_t>(h, G, &rc);
@@ -741,7 +976,8 @@ int itokmc_init(const itokmc_config* cfg, itokmc_handle** out)
                 cudaEventCreateWithFlags(&d.side_fork, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&d.side_join, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess))
+                cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&h->scap, cudaStreamNonBlocking) != cudaSuccess))
         rc = fail(h, ITOKMC_ERR_CUDA, "field stream");
     if (!rc) ik::launch_zig_init(h->s);
     if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->s), "init sync");
@@ -782,6 +1018,8 @@ int itokmc_destroy(itokmc_handle* h)
     }
     for (auto& gx : h->d.vgraph)
         if (gx) cudaGraphExecDestroy(gx);
+    drop_graphs(h);
+    if (h->scap) cudaStreamDestroy(h->scap);
     if (h->d.side) {
         cudaStreamSynchronize(h->d.side);
         cudaStreamDestroy(h->d.side);
@@ -1030,8 +1268,10 @@ int itokmc_step(itokmc_handle* h, int32_t nsteps)
     if (nsteps < 0) return fail(h, ITOKMC_ERR_ARG, "nsteps < 0");
     for (int k = 0; k < nsteps; ++k) {
         int rc = h->cfg.dt_adapt ? choose_step(h) : ITOKMC_OK;
-        if (!rc) rc = h->cfg.coupling == ITOKMC_SEMI_IMPLICIT ? semi_step(h) : full_step(h);
+        if (!rc) rc = h->cfg.coupling == ITOKMC_SEMI_IMPLICIT ? semi_step(h)
+                                                                : (graph_eligible(h) ? graph_step(h) : full_step(h));
         if (rc) return rc;
+        ++h->steps_done;
         itokmc_advance_counter(h);
     }
     h->st.n_particles = h->N;

@@ -29,6 +29,9 @@ struct Params {
     double E0;
     uint64_t seed0;
     uint32_t step;
+    // graph-replayed steps read the step counter from device memory (the
+    // last node of a step advances it); otherwise null and step is used
+    const uint32_t* step_dev;
     // FP32 form constants (cell units)
     float f_drift;          // -mu dt / h   (multiplies E in V/m)
     float f_diff;           // sqrt(2 D dt) / h
@@ -370,6 +373,9 @@ __device__ __forceinline__ int cell_axis(double x, double lo, double h, double r
 }
 
 __device__ __forceinline__ uint64_t seed_of(const Params& P, int r) { return P.seed0 + (uint64_t)r; }
+// The step counter of the Philox streams.
+__device__ __forceinline__ uint32_t step_of(const Params& P) { return P.step_dev ? *P.step_dev : P.step; }
+
 // Particle block b: species b / R, realization b % R (at most three species:
 // two comparisons instead of a division).
 __host__ __device__ __forceinline__ int species_of(const Params& P, int b) { return (b >= P.R) + (b >= 2 * P.R); }

@@ -915,6 +915,23 @@ void run_cycles(Dev& d, int k, int R, int nu1, int nu2, cudaStream_t s)
 // 2^-phi_F V, right-hand side prepared by the charge kernel).  Returns 0 on
 // convergence, ITOKMC_ERR_NOCONV (-6) if max_cycles is reached or the
 // potential leaves the fixed-point range.
+// Lowers the fixed-point potential's scale to F bits (F < d.phi_F): the
+// potential and the kept previous one shifted right by the difference.
+void lower_phi_scale(const Params& P, Dev& d, int F, cudaStream_t s)
+{
+    if (F >= d.phi_F) return;
+    const Geo G0 = geo(d, 0, P.R);
+    ++g_launches;
+    k_shift_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(reinterpret_cast<long long*>(d.lev[0].phi), d.phi_F - F,
+                                                       G0.cells);
+    if (d.phi_prev && d.have_prev) {
+        ++g_launches;
+        k_shift_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(reinterpret_cast<long long*>(d.phi_prev), d.phi_F - F,
+                                                           G0.cells);
+    }
+    d.phi_F = F;
+}
+
 int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, int nu2, unsigned long long rho_absmax,
                 int max_cycles, cudaStream_t s, int* cycles_out, double* rel_out, bool extrapolate)
 {
@@ -936,17 +953,7 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
     long long* Bfix = reinterpret_cast<long long*>(L0.rhs);
     if (fixed) {
         // scale from a bound on |phi| (lowered only: the warm start is shifted)
-        const int F = phi_fixed_bits(phi_bound(P, rho_absmax));
-        if (F < d.phi_F) {
-            ++g_launches;
-            k_shift_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(Phi, d.phi_F - F, G0.cells);
-            if (d.phi_prev && d.have_prev) {
-                ++g_launches;
-                k_shift_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(reinterpret_cast<long long*>(d.phi_prev),
-                                                                   d.phi_F - F, G0.cells);
-            }
-            d.phi_F = F;
-        }
+        lower_phi_scale(P, d, phi_fixed_bits(phi_bound(P, rho_absmax)), s);
         double qscale, bc_top;
         rhs_consts(P, qscale, bc_top);
         ++g_launches;
@@ -1024,6 +1031,70 @@ int field_solve(const Params& P, Dev& d, int precision, double rtol, int nu1, in
     if (cycles_out) *cycles_out = cyc;
     if (rel_out) *rel_out = worst;
     return status;
+}
+
+// The solve of field_solve with a fixed number of cycles and no host
+// synchronisation, for steps replayed from a captured graph: the same
+// launches (the fixed-point scale is kept: a step that needs a lower one is
+// solved again by field_solve afterwards), then the residual and right-hand
+// side norms of every realization in d.norm_out, which the host checks after
+// the step.  cycles: V-cycles (FP64), or outer corrections of two FP32
+// V-cycles each (refinement forms).
+void field_solve_fixed(const Params& P, Dev& d, int precision, int nu1, int nu2, int cycles, cudaStream_t s)
+{
+    const int R = P.R;
+    MGLevel& L0 = d.lev[0];
+    const Geo G0 = geo(d, 0, R);
+    const uint64_t per_real = G0.cells / R;
+    const int items = (int)(per_real / NORM_TPB < 8 ? per_real / NORM_TPB : 8);
+    const int nblk = (int)(G0.cells / ((uint64_t)NORM_TPB * items));
+    const int bpr = nblk / R;
+    const bool fixed = precision == 2;
+    long long* Phi = reinterpret_cast<long long*>(L0.phi);
+    long long* Bfix = reinterpret_cast<long long*>(L0.rhs);
+    if (fixed) {
+        double qscale, bc_top;
+        rhs_consts(P, qscale, bc_top);
+        ++g_launches;
+        k_rhs_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(d.rho, Bfix, G0, qscale, bc_top,
+                                                         L0.h * L0.h * std::ldexp(1.0, d.phi_F));
+    }
+    if (d.phi_prev) {
+        ++g_launches;
+        if (fixed)
+            k_extrapolate<long long><<<gridsz(G0.cells, 256), 256, 0, s>>>(
+                Phi, reinterpret_cast<long long*>(d.phi_prev), G0.cells, d.have_prev);
+        else
+            k_extrapolate<double><<<gridsz(G0.cells, 256), 256, 0, s>>>(
+                L0.phi, reinterpret_cast<double*>(d.phi_prev), G0.cells, d.have_prev);
+        d.have_prev = true;
+    }
+    const float rsc = (float)std::ldexp(1.0, -d.phi_F);
+    const float esc = (float)std::ldexp(1.0, d.phi_F);
+    auto resid = [&](bool first) {
+        ++g_launches;
+        if (fixed)
+            k_resid_fixed<<<nblk, NORM_TPB, 0, s>>>(Phi, Bfix, L0.rhs32, G0, rsc, d.norm_part, first, items);
+        else
+            k_resid_norm<<<nblk, NORM_TPB, 0, s>>>(L0.phi, L0.rhs, precision == 1 ? L0.rhs32 : nullptr, G0,
+                                                   d.norm_part, first, items);
+    };
+    for (int c = 0; c < cycles; ++c) {
+        if (precision == 0) {
+            run_cycles(d, 0, R, nu1, nu2, s);
+            continue;
+        }
+        resid(false);
+        run_cycles(d, 1, R, nu1, nu2, s);
+        ++g_launches;
+        if (fixed)
+            k_add_fixed<<<gridsz(G0.cells, 256), 256, 0, s>>>(Phi, L0.phi32, esc, G0.cells);
+        else
+            k_add_correction<<<gridsz(G0.cells, 256), 256, 0, s>>>(L0.phi, L0.phi32, G0.cells);
+    }
+    resid(true);
+    ++g_launches;
+    k_norm_final<<<R, 256, 0, s>>>(d.norm_part, bpr, R, d.norm_out);
 }
 
 __global__ void k_pack_field(const double* __restrict__ E3, E64* __restrict__ E, float4* __restrict__ E32, uint64_t G)

@@ -450,8 +450,9 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f64(
     const uint32_t* __restrict__ cell_start, const E64* __restrict__ E, int32_t* __restrict__ cnt_new,
     int32_t* __restrict__ in_cnt, int32_t* __restrict__ in_before, unsigned long long* __restrict__ Xe,
     unsigned long long* __restrict__ ne_fix, Mover* __restrict__ movers, uint32_t mover_cap,
-    Counters* __restrict__ ctr, uint32_t* __restrict__ blk_stay)
+    Counters* __restrict__ ctr, uint32_t* __restrict__ blk_stay, const uint32_t* __restrict__ Ndev)
 {
+    if (Ndev) N = *Ndev;                          // graph-replayed steps: the count of the current step
     const uint32_t i = blockIdx.x * TPB + threadIdx.x;
     bool alive = false, mover = false;
     uint32_t gnew = 0, w = 0;
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f64(
         const double X[3] = { p.x, p.y, p.z };
         double Ep[3];
         interp_f64(P, E + (size_t)rp * P.n3, X, Ep);
-        PairStream s(seed_of(P, rp), idx, P.step, P.push_tag_sp[sp], 0);
+        PairStream s(seed_of(P, rp), idx, step_of(P), P.push_tag_sp[sp], 0);
         double Nn[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) Nn[a] = znormal(s);
@@ -696,8 +697,9 @@ __global__ void __launch_bounds__(TPB) k_scatter_f64(const P64* __restrict__ B, 
                                                      const uint32_t* __restrict__ keyB, uint32_t N,
                                                      const uint32_t* __restrict__ blk_prefix,
                                                      const int64_t* __restrict__ delta, uint32_t cap,
-                                                     Counters* __restrict__ ctr)
+                                                     Counters* __restrict__ ctr, const uint32_t* __restrict__ Ndev)
 {
+    if (Ndev) N = *Ndev;
     const uint32_t i = blockIdx.x * TPB + threadIdx.x;
     uint32_t k = KEY_DEAD;
     if (i < N) k = keyB[i];
@@ -1142,7 +1144,7 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 8 || REC) ? 4 : 5) k_kmc(Pa
         }
         const int r = real_of(P, (uint32_t)g);
         const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
-        Stream s(seed_of(P, r), c, P.step, TAG_KMC, 0);
+        Stream s(seed_of(P, r), c, step_of(P), TAG_KMC, 0);
         if (kmc_cell<T, REC>(P, s, X0, kr, f) != 0) {
             atomicOr(&ctr->err, DERR_KMC);
             ctr->kmc_fail_cell = (unsigned)g;
@@ -1245,7 +1247,7 @@ __global__ void k_loss(Params P, uint32_t* __restrict__ wbase, int wstride, cons
         const unsigned long long W = Xe[g];
         const int blk = real_of(P, (uint32_t)g);
         const uint32_t c = (uint32_t)(g & (uint64_t)(P.n3 - 1));
-        Stream s(seed_of(P, phys_of(P, blk)), c, P.step, P.prod_tag_sp[species_of(P, blk)], (uint32_t)P.n_new);
+        Stream s(seed_of(P, phys_of(P, blk)), c, step_of(P), P.prod_tag_sp[species_of(P, blk)], (uint32_t)P.n_new);
         const uint32_t a = s.u32(), b = s.u32();
         const unsigned long long R = (((unsigned long long)a << 32) | b) % W;
         if (W < (1ull << 32)) {
@@ -1294,7 +1296,7 @@ __device__ __forceinline__ void photon_sample(const Params& P, uint64_t seed, ui
                                               const int ijk[3], double lnK, double Y0[3], double& r,
                                               double dir[3])
 {
-    Stream s(seed, c, P.step, TAG_PHOTON, j);
+    Stream s(seed, c, step_of(P), TAG_PHOTON, j);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double u = s.uniform();
@@ -1339,7 +1341,7 @@ __global__ void k_photons(Params P, int mixed, const int64_t* __restrict__ fired
             if (mixed) {
                 // FP32 in cell units from the source cell's corner; the same
                 // draws as the FP64 form (top 23 bits of each uniform)
-                Stream st(seed, c, P.step, TAG_PHOTON, (uint32_t)j);
+                Stream st(seed, c, step_of(P), TAG_PHOTON, (uint32_t)j);
                 float Yc[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
@@ -1769,7 +1771,7 @@ __global__ void __launch_bounds__(128, GLOBAL ? 4 : (std::is_same<E, MP32>::valu
             const int ijk[3] = { (int)(c & (uint32_t)(P.n - 1)), (int)((c >> P.log2n) & (uint32_t)(P.n - 1)),
                                  (int)(c >> (2 * P.log2n)) };
             for (uint32_t j = lane; j < mprod; j += 32) {
-                Stream st(seed_of(P, r), c, P.step, P.prod_tag_sp[sp], j);
+                Stream st(seed_of(P, r), c, step_of(P), P.prod_tag_sp[sp], j);
                 E e;
                 if constexpr (MX) {
                     // FP32 uniforms from the high words of the FP64 ones
@@ -2155,8 +2157,10 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f32(
     uint32_t* __restrict__ keyB, uint32_t N, const uint32_t* __restrict__ cell_start,
     const float4* __restrict__ E32, int32_t* __restrict__ cnt_new, int32_t* __restrict__ in_cnt,
     int32_t* __restrict__ in_before, unsigned long long* __restrict__ Xe, unsigned long long* __restrict__ ne_fix,
-    Mover* __restrict__ movers, uint32_t mover_cap, Counters* __restrict__ ctr, uint32_t* __restrict__ blk_stay)
+    Mover* __restrict__ movers, uint32_t mover_cap, Counters* __restrict__ ctr, uint32_t* __restrict__ blk_stay,
+    const uint32_t* __restrict__ Ndev)
 {
+    if (Ndev) N = *Ndev;
     const uint32_t i = blockIdx.x * TPB + threadIdx.x;
     bool alive = false, mover = false;
     uint32_t gnew = 0, w = 0;
@@ -2197,7 +2201,7 @@ __global__ void __launch_bounds__(TPB, 4) k_push_f32(
                 }
         // the FP64 form's stream and words: the same ziggurat decisions, so
         // both forms draw common random numbers (equal to FP32 rounding)
-        PairStream zs(SINGLE ? P.seed0 : seed_of(P, rp), idx, P.step, SINGLE ? TAG_PUSH : P.push_tag_sp[sp], 0);
+        PairStream zs(SINGLE ? P.seed0 : seed_of(P, rp), idx, step_of(P), SINGLE ? TAG_PUSH : P.push_tag_sp[sp], 0);
         float nrm[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) nrm[a] = znormal32(zs);
@@ -2253,8 +2257,9 @@ __global__ void __launch_bounds__(TPB) k_scatter_f32(const P32* __restrict__ B, 
                                                      uint32_t* __restrict__ cA, const uint32_t* __restrict__ keyB,
                                                      uint32_t N, const uint32_t* __restrict__ blk_prefix,
                                                      const int64_t* __restrict__ delta, uint32_t cap,
-                                                     Counters* __restrict__ ctr)
+                                                     Counters* __restrict__ ctr, const uint32_t* __restrict__ Ndev)
 {
+    if (Ndev) N = *Ndev;
     const uint32_t i = blockIdx.x * TPB + threadIdx.x;
     uint32_t k = KEY_DEAD;
     if (i < N) k = keyB[i];
@@ -2330,7 +2335,9 @@ int grid_for(uint64_t n, int tpb, int maxb = 152 * 16)
 size_t scan_scratch_elems(uint64_t G, int C) { return (size_t)(scan_nblk(G) + 1) * C + C; }
 
 // ---------------------------------------------------------------- launchers
-void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
+// Ndev (graph-replayed steps): the particle count is read on the device and
+// N is a bound on it that sizes the grids; otherwise N is the count.
+void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s, const uint32_t* Ndev)
 {
     const uint64_t G = (uint64_t)P.B * P.n3;     // particle cells
     cudaMemsetAsync(d.cnt_new, 0, G * sizeof(int32_t), s);
@@ -2345,10 +2352,11 @@ void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
     if (d.mixed) {
         auto k = P.B == 1 ? k_push_f32<true> : k_push_f32<false>;
         k<<<nblk, TPB, 0, s>>>(P, d.rA32, d.cellA32, d.rB32, d.keyB, N, d.cell_start, d.E32, d.cnt_new, d.in_cnt,
-                               d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr, d.blk_stay);
+                               d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr, d.blk_stay, Ndev);
     } else
         k_push_f64<<<nblk, TPB, 0, s>>>(P, d.recA, d.recB, d.keyB, N, d.cell_start, d.E, d.cnt_new, d.in_cnt,
-                                         d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr, d.blk_stay);
+                                         d.in_before, d.Xe, d.ne_fix, d.movers, d.mover_cap, d.ctr, d.blk_stay,
+                                         Ndev);
 }
 
 // Semi-implicit transport (FP64 form), Sec. 4.7 steps 2 and 5: the
@@ -2363,7 +2371,7 @@ __global__ void __launch_bounds__(TPB) k_diffuse_f64(Params P, const P64* __rest
     P64 p = ld_p64(A + i);
     const int r = real_of(P, p.cell);
     const uint32_t idx = i - cell_start[(size_t)r * P.n3];
-    PairStream s(seed_of(P, r), idx, P.step, TAG_PUSH, 0);
+    PairStream s(seed_of(P, r), idx, step_of(P), TAG_PUSH, 0);
     double Nn[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) Nn[a] = znormal(s);
@@ -2407,7 +2415,7 @@ void launch_advect(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
                                                           d.movers, d.mover_cap, d.ctr, d.blk_stay);
 }
 
-void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s)
+void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s, const uint32_t* Ndev)
 {
     TransportScanOp op{ d.cnt_new, d.in_cnt, d.in_before, d.cell_start_B, d.delta, d.in_off, G };
     run_scan<3>(op, G, d.scan_blk, s);
@@ -2419,14 +2427,14 @@ void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cu
         g_launches += 3;
         if (d.mixed) {
             k_scatter_f32<<<nblk, TPB, 0, s>>>(d.rB32, d.rA32, d.cellA32, d.keyB, N, d.blk_prefix, d.delta,
-                                               d.mover_cap, d.ctr);
+                                               d.mover_cap, d.ctr, Ndev);
             k_mover_place<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.in_off, d.cursor, d.mover_sorted);
             k_mover_write_f32<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.mover_sorted, d.in_off, d.in_cnt,
                                                  d.in_before, d.cnt_new, d.cell_start_B, d.cursor, d.rB32, d.rA32,
                                                  d.cellA32);
         } else {
             k_scatter_f64<<<nblk, TPB, 0, s>>>(d.recB, d.recA, d.keyB, N, d.blk_prefix, d.delta, d.mover_cap,
-                                               d.ctr);
+                                               d.ctr, Ndev);
             k_mover_place<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.in_off, d.cursor, d.mover_sorted);
             k_mover_write_f64<<<mg, 256, 0, s>>>(d.movers, d.ctr, d.mover_cap, d.mover_sorted, d.in_off, d.in_cnt,
                                                  d.in_before, d.cnt_new, d.cell_start_B, d.cursor, d.recB, d.recA);

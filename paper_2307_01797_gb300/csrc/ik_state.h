@@ -110,6 +110,7 @@ struct Dev {
     int64_t* fired = nullptr;          // 5 G: ionizations, attachments, photons, e-ion and ion-ion
                                        // recombinations of the last KMC
     int64_t* gain = nullptr;           // Gp: net gain of each particle cell's species in the last KMC
+    uint32_t* step_dev = nullptr;      // the step counter of graph-replayed steps
     // photons
     Photo* photos = nullptr;  uint32_t* photo_sorted = nullptr;
     int32_t* photo_cnt = nullptr;  int32_t* photo_cursor = nullptr;
@@ -187,8 +188,11 @@ inline double phi_bound(const Params& P, unsigned long long rho_absmax)
 
 // ------------------------------------------------------------- launchers
 // ik_particles.cu
-void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
-void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s);
+void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s, const uint32_t* Ndev = nullptr);
+void field_solve_fixed(const Params& P, Dev& d, int precision, int nu1, int nu2, int cycles, cudaStream_t s);
+void lower_phi_scale(const Params& P, Dev& d, int F, cudaStream_t s);
+void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s,
+                             const uint32_t* Ndev = nullptr);
 void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s);
 void launch_rho(const Params& P, Dev& d, uint64_t G, cudaStream_t s);
 void launch_zig_init(cudaStream_t s);

@@ -51,7 +51,7 @@ class Config(ctypes.Structure):
         ("cfl", ctypes.c_double), ("drt_factor", ctypes.c_double), ("ion_factor", ctypes.c_double),
         ("beta_ep", ctypes.c_double), ("beta_np", ctypes.c_double),
         ("mobile_ions", ctypes.c_int32), ("pad_ions", ctypes.c_int32), ("mu_ion", ctypes.c_double),
-        ("D_ion", ctypes.c_double),
+        ("D_ion", ctypes.c_double), ("graph_step", ctypes.c_int32), ("pad_graph", ctypes.c_int32),
     ]
 
 
@@ -88,7 +88,7 @@ class Stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_int64), ("merge_cells", ctypes.c_int64), ("merge_elements", ctypes.c_int64),
         ("merge_elements_sq", ctypes.c_int64), ("merge_max_list", ctypes.c_int64), ("dt_last", ctypes.c_double),
         ("recombinations_ep", ctypes.c_int64), ("recombinations_np", ctypes.c_int64),
-        ("outflow_ion_pos", ctypes.c_int64), ("outflow_ion_neg", ctypes.c_int64),
+        ("outflow_ion_pos", ctypes.c_int64), ("outflow_ion_neg", ctypes.c_int64), ("graph_steps", ctypes.c_int64),
     ]
 
     def as_dict(self):

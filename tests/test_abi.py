@@ -66,12 +66,13 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "itokmc.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(itokmc_config), offsetof(itokmc_config, particle_capacity),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(itokmc_config), offsetof(itokmc_config, particle_capacity),
          offsetof(itokmc_config, alloc_ctx), offsetof(itokmc_config, field_precision),
          sizeof(itokmc_stats), offsetof(itokmc_stats, ms_field), offsetof(itokmc_config, blobs),
          offsetof(itokmc_config, ion_factor), sizeof(itokmc_seed_blob), offsetof(itokmc_seed_blob, realization),
          offsetof(itokmc_stats, dt_last), offsetof(itokmc_config, beta_np), offsetof(itokmc_stats, recombinations_np),
-         offsetof(itokmc_config, D_ion), offsetof(itokmc_stats, outflow_ion_neg));
+         offsetof(itokmc_config, D_ion), offsetof(itokmc_stats, outflow_ion_neg), offsetof(itokmc_config, graph_step),
+         offsetof(itokmc_stats, graph_steps));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -85,7 +86,7 @@ int main(void) {
     assert got == [ctypes.sizeof(C), C.particle_capacity.offset, C.alloc_ctx.offset, C.field_precision.offset,
                    ctypes.sizeof(S), S.ms_field.offset, C.blobs.offset, C.ion_factor.offset, ctypes.sizeof(B),
                    B.realization.offset, S.dt_last.offset, C.beta_np.offset, S.recombinations_np.offset,
-                   C.D_ion.offset, S.outflow_ion_neg.offset]
+                   C.D_ion.offset, S.outflow_ion_neg.offset, C.graph_step.offset, S.graph_steps.offset]
 
 
 def test_oracle_and_library_share_no_source():
