@@ -587,10 +587,11 @@ def ensemble_study(args):
         counts0 = H.itokmc_num_particles()
         tb, done = timed(H)
         counts_end = H.itokmc_num_particles()
+        graph_steps = H.itokmc_get_stats()["graph_steps"]
         H.close()
         tb, done = aggregate_ranks(tb, done, dist, "cuda")
         res = {"particles0": counts0, "particles_end": counts_end, "batched_ms_per_step": 1e3 * tb / K,
-               "batched_particle_steps_per_s": done / tb}
+               "batched_particle_steps_per_s": done / tb, "graph_steps": graph_steps}
         if name == "fp64" or not args.batched_only:
             ts, dn = 0.0, 0
             for r in range(Rl):
