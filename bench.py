@@ -295,7 +295,9 @@ def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e)
            "last_step_counters": last, "gpu_launches": int(launches), "clocks": clk,
            "transport_achieved_gbs": ach, "bytes_per_particle": bpp, "traffic": traffic,
            "traffic_per_particle": tpp,
-           "mg_smoothing": {"nu1": tune["mg_nu1"], "nu2": tune["mg_nu2"], "autotuned": True} if tune else
+           "mg_smoothing": {"nu1": tune["mg_nu1"], "nu2": tune["mg_nu2"], "autotuned": True,
+                            "deposit_window": tune["dep_win"],
+                            "deposit_window_ms": {str(w): round(ms, 4) for w, ms in tune["dep_tried"]}} if tune else
            {"nu1": 2, "nu2": 2, "autotuned": False}}
     if with_e2e:
         # e2e through the public API: the state uploaded from pinned host

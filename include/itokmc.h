@@ -60,6 +60,7 @@ extern "C" {
 #define ITOKMC_ERR_TIMEOUT (-7)    /* a bounded device wait gave up         */
 #define ITOKMC_ERR_POISONED (-8)   /* handle unusable after an earlier error */
 #define ITOKMC_ERR_KMC (-9)        /* KMC iteration guard hit in some cell  */
+#define ITOKMC_ERR_INTERNAL (-10)  /* a self-check of the library failed     */
 
 /* ---- precision forms --------------------------------------------------- */
 #define ITOKMC_FP64 0   /* FP64 positions/push/KMC, FP64 multigrid (parity) */
@@ -405,11 +406,17 @@ int itokmc_load(itokmc_handle* h, const char* path);
  * handle's configuration (mg_nu1, mg_nu2).  The potential and field
  * are restored afterwards, so the run continues as without the call; only
  * the number of V-cycles of later solves changes (the tolerance does not).
+ * Then, with particles present, it times the push kernel of the current
+ * particles (the transport's first kernel; its trial writes only what the
+ * next transport writes again) for each deposit window in {0, 256, 512,
+ * 1024, 2048} cells (three launches each, the fastest kept) and keeps the
+ * fastest window.
  *   out  optional: the chosen pair, its time, and every candidate's time
  *        (ms, -1 if it did not converge).
  * Returns ITOKMC_OK, ITOKMC_ERR_NOCONV if no candidate converges, or
  * ITOKMC_ERR_CUDA.  Synchronises the stream. */
 #define ITOKMC_TUNE_CANDIDATES 9
+#define ITOKMC_TUNE_DEPOSIT 5
 typedef struct itokmc_tuning {
     int32_t mg_nu1, mg_nu2;                          /* chosen pair            */
     double ms_field;                                 /* its field-solve time   */
@@ -417,6 +424,13 @@ typedef struct itokmc_tuning {
     int32_t n_tried;
     int32_t nu_tried[ITOKMC_TUNE_CANDIDATES][2];
     double ms_tried[ITOKMC_TUNE_CANDIDATES];         /* -1: no convergence     */
+    /* the push's deposit tile: the largest cell box a block of the push
+     * deposits through its shared window (0: global atomics only); the
+     * deposit is an integer sum, so the choice changes no result */
+    int32_t dep_win;                                 /* chosen window (cells)  */
+    int32_t n_dep_tried;
+    int32_t dep_tried[ITOKMC_TUNE_DEPOSIT];          /* 0, 256, 512, 1024, 2048 */
+    double ms_dep_tried[ITOKMC_TUNE_DEPOSIT];        /* push ms, -1: not timed  */
 } itokmc_tuning;
 int itokmc_autotune(itokmc_handle* h, itokmc_tuning* out);
 

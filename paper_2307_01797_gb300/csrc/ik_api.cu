@@ -211,6 +211,7 @@ void fill_params(const itokmc_config* cfg, ik::Params& P)
     const uint32_t prod_tags[3] = { ik::TAG_PRODUCT, ik::TAG_PRODUCT_POS, ik::TAG_PRODUCT_NEG };
     for (int s = 0; s < 3; ++s) { P.push_tag_sp[s] = push_tags[s]; P.prod_tag_sp[s] = prod_tags[s]; }
     P.ppc = cfg->ppc; P.n_new = cfg->n_new; P.n_crit = cfg->n_crit; P.n_ssa = cfg->n_ssa; P.frac_bits = cfg->frac_bits;
+    P.dep_win = ik::DEP_WIN_MAX;
     for (int a = 0; a < 3; ++a) {
         P.lo[a] = cfg->lo[a]; P.hi[a] = cfg->hi[a]; P.h[a] = (cfg->hi[a] - cfg->lo[a]) / n;
         P.rh[a] = 1.0 / P.h[a];
@@ -1249,6 +1250,41 @@ int itokmc_autotune(itokmc_handle* h, itokmc_tuning* out)
     t.mg_nu2 = h->cfg.mg_nu2;
     t.ms_field = best_ms;
     t.cycles = best_cyc;
+    // the push's deposit window: trial pushes of the current particles; the
+    // last deposit (ne_fix, X) is kept in the merge work area meanwhile
+    t.dep_win = h->P.dep_win;
+    t.n_dep_tried = 0;
+    const size_t dep_bytes = h->Gp * sizeof(unsigned long long);
+    if (h->N > 0 && d.work_bytes >= 3 * dep_bytes + 16) {
+        IK_CHECK(h, cudaMemcpyAsync(d.work, d.ne_fix, dep_bytes, cudaMemcpyDeviceToDevice, h->s));
+        IK_CHECK(h, cudaMemcpyAsync(d.work + dep_bytes, d.Xe, dep_bytes, cudaMemcpyDeviceToDevice, h->s));
+        // every trial's deposit must equal the first one's (integer sums)
+        unsigned long long* first = reinterpret_cast<unsigned long long*>(d.work + 2 * dep_bytes);
+        unsigned int* differs = reinterpret_cast<unsigned int*>(d.work + 3 * dep_bytes);
+        IK_CHECK(h, cudaMemsetAsync(differs, 0, sizeof(unsigned int), h->s));
+        const int cand[ITOKMC_TUNE_DEPOSIT] = { 0, 256, 512, 1024, ik::DEP_WIN_MAX };
+        float best_push = -1.f;
+        int best_win = h->P.dep_win;
+        for (int k = 0; k < ITOKMC_TUNE_DEPOSIT; ++k) {
+            h->P.dep_win = cand[k];
+            const float ms = ik::time_push(h->P, d, h->N, h->s, 3);
+            if (k == 0) IK_CHECK(h, cudaMemcpyAsync(first, d.ne_fix, dep_bytes, cudaMemcpyDeviceToDevice, h->s));
+            else ik::launch_diff_flag(first, d.ne_fix, h->Gp, differs, h->s);
+            t.dep_tried[k] = cand[k];
+            t.ms_dep_tried[k] = ms;
+            ++t.n_dep_tried;
+            if (ms >= 0.f && (best_push < 0.f || ms < best_push)) { best_push = ms; best_win = cand[k]; }
+        }
+        h->P.dep_win = best_win;
+        t.dep_win = best_win;
+        unsigned int diff = 0;
+        IK_CHECK(h, cudaMemcpyAsync(&diff, differs, sizeof diff, cudaMemcpyDeviceToHost, h->s));
+        IK_CHECK(h, cudaMemcpyAsync(d.ne_fix, d.work, dep_bytes, cudaMemcpyDeviceToDevice, h->s));
+        IK_CHECK(h, cudaMemcpyAsync(d.Xe, d.work + dep_bytes, dep_bytes, cudaMemcpyDeviceToDevice, h->s));
+        IK_CHECK(h, cudaStreamSynchronize(h->s));
+        drop_graphs(h);                      // the kernels' parameters changed
+        if (diff) return fail(h, ITOKMC_ERR_INTERNAL, "autotune: deposit windows gave different densities");
+    }
     if (out) *out = t;
     return cuda_check(h, cudaGetLastError(), "autotune");
 }

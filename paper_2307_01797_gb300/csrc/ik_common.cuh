@@ -22,6 +22,7 @@ struct Params {
     int B;                  // particle blocks S R: block b holds species b / R of realization b % R
     int log2n;
     int ppc, n_new, n_crit, n_ssa, frac_bits;
+    int dep_win;            // largest shared deposit window (cells) a push block uses, <= DEP_WIN_MAX
     double lo[3], hi[3], h[3], rh[3];   // rh = 1/h
     double dt, mu, D, alpha_A, alpha_B, eta, photon_ratio, kappa_lo, kappa_hi, eps;
     double sdt;             // sqrt(2 D dt)
@@ -42,6 +43,8 @@ struct Params {
     float f_drift_sp[3], f_diff_sp[3];
     uint32_t push_tag_sp[3], prod_tag_sp[3];
 };
+
+constexpr int DEP_WIN_MAX = 2048;   // cells of the push's shared deposit window (16 KB)
 
 enum : uint32_t {
     TAG_INIT = 1u, TAG_PUSH = 2u, TAG_KMC = 3u, TAG_PRODUCT = 4u, TAG_PHOTON = 5u,

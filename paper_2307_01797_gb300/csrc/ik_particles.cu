@@ -224,7 +224,7 @@ __device__ __forceinline__ void stencil_f32(const Params& P, const int id[3], co
     }
 }
 
-constexpr int DEP_WIN = 2048;   // cells of the block's shared deposit window (16 KB)
+constexpr int DEP_WIN = DEP_WIN_MAX;
 
 // Deposits the 8 fixed-point CIC contributions of every alive particle of the
 // block.  The cells the block touches usually form a small box (particles are
@@ -283,7 +283,7 @@ __device__ __forceinline__ void block_deposit(const Params& P, unsigned long lon
     const int lo0 = wfin[0], lo1 = wfin[1], lo2 = wfin[2];
     const int e0 = -wfin[3] - lo0 + 1, e1 = -wfin[4] - lo1 + 1, e2 = -wfin[5] - lo2 + 1;
     const long long V = (long long)e0 * e1 * e2;
-    const bool use = (SINGLE || wfin[6] == -wfin[7]) && V <= DEP_WIN;
+    const bool use = (SINGLE || wfin[6] == -wfin[7]) && V <= P.dep_win;
     const int ix[2] = { S.ia[0], S.ib[0] }, iy[2] = { S.ia[1], S.ib[1] }, iz[2] = { S.ia[2], S.ib[2] };
     if (!use) {
         if (alive) {
@@ -2452,6 +2452,47 @@ void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s)
     ++g_launches;
     if (d.mixed) k_deposit_f32<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.rA32, d.cellA32, N, d.Xe, d.ne_fix);
     else k_deposit_f64<<<(N + TPB - 1) / TPB, TPB, 0, s>>>(P, d.recA, N, d.Xe, d.ne_fix);
+}
+
+// Time of the push kernel alone (ms per launch, median of reps) with the
+// current parameters: it reads the records and writes only what the next
+// transport stage writes again first (the autotuner's deposit-window trial).
+float time_push(const Params& P, Dev& d, uint32_t N, cudaStream_t s, int reps)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = -1.f;
+    for (int k = 0; k < reps; ++k) {
+        cudaEventRecord(a, s);
+        launch_transport(P, d, N, s);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (best < 0.f || ms < best) best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+// Sets *flag if a and b differ anywhere (the autotuner's check that every
+// deposit window gives the same integer densities).
+__global__ void k_diff_flag(const unsigned long long* __restrict__ a, const unsigned long long* __restrict__ b,
+                            uint64_t n, unsigned int* __restrict__ flag)
+{
+    bool diff = false;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        diff |= a[i] != b[i];
+    if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+void launch_diff_flag(const unsigned long long* a, const unsigned long long* b, uint64_t n, unsigned int* flag,
+                      cudaStream_t s)
+{
+    ++g_launches;
+    k_diff_flag<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(a, b, n, flag);
 }
 
 // Ziggurat tables, once per device (the same values for every handle).

@@ -191,6 +191,9 @@ inline double phi_bound(const Params& P, unsigned long long rho_absmax)
 void launch_transport(const Params& P, Dev& d, uint32_t N, cudaStream_t s, const uint32_t* Ndev = nullptr);
 void field_solve_fixed(const Params& P, Dev& d, int precision, int nu1, int nu2, int cycles, cudaStream_t s);
 void lower_phi_scale(const Params& P, Dev& d, int F, cudaStream_t s);
+float time_push(const Params& P, Dev& d, uint32_t N, cudaStream_t s, int reps);
+void launch_diff_flag(const unsigned long long* a, const unsigned long long* b, uint64_t n, unsigned int* flag,
+                      cudaStream_t s);
 void launch_transport_finish(const Params& P, Dev& d, uint32_t N, uint64_t G, cudaStream_t s,
                              const uint32_t* Ndev = nullptr);
 void launch_deposit_only(const Params& P, Dev& d, uint32_t N, cudaStream_t s);

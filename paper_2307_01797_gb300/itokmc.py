@@ -20,7 +20,7 @@ from . import build as _build
 
 ITOKMC_OK = 0
 ERR_NAMES = {-1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_CAPACITY", -5: "ERR_OVERFLOW",
-             -6: "ERR_NOCONV", -7: "ERR_TIMEOUT", -8: "ERR_POISONED", -9: "ERR_KMC"}
+             -6: "ERR_NOCONV", -7: "ERR_TIMEOUT", -8: "ERR_POISONED", -9: "ERR_KMC", -10: "ERR_INTERNAL"}
 FP64, MIXED = 0, 1
 EXPLICIT, SEMI_IMPLICIT = 0, 1
 HOST, DEVICE = 0, 1
@@ -96,6 +96,7 @@ class Stats(ctypes.Structure):
 
 
 TUNE_CANDIDATES = 9
+TUNE_DEPOSIT = 5
 
 
 class Tuning(ctypes.Structure):
@@ -103,6 +104,8 @@ class Tuning(ctypes.Structure):
         ("mg_nu1", ctypes.c_int32), ("mg_nu2", ctypes.c_int32), ("ms_field", ctypes.c_double),
         ("cycles", ctypes.c_int32), ("n_tried", ctypes.c_int32),
         ("nu_tried", (ctypes.c_int32 * 2) * TUNE_CANDIDATES), ("ms_tried", ctypes.c_double * TUNE_CANDIDATES),
+        ("dep_win", ctypes.c_int32), ("n_dep_tried", ctypes.c_int32), ("dep_tried", ctypes.c_int32 * TUNE_DEPOSIT),
+        ("ms_dep_tried", ctypes.c_double * TUNE_DEPOSIT),
     ]
 
 
@@ -359,7 +362,9 @@ class Handle:
         t = Tuning()
         _check(lib().itokmc_autotune(self.h, ctypes.byref(t)), self.h)
         return {"mg_nu1": t.mg_nu1, "mg_nu2": t.mg_nu2, "ms_field": t.ms_field, "cycles": t.cycles,
-                "tried": [((t.nu_tried[k][0], t.nu_tried[k][1]), t.ms_tried[k]) for k in range(t.n_tried)]}
+                "tried": [((t.nu_tried[k][0], t.nu_tried[k][1]), t.ms_tried[k]) for k in range(t.n_tried)],
+                "dep_win": t.dep_win,
+                "dep_tried": [(t.dep_tried[k], t.ms_dep_tried[k]) for k in range(t.n_dep_tried)]}
 
     def itokmc_advance_counter(self):
         _check(lib().itokmc_advance_counter(self.h), self.h)

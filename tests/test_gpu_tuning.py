@@ -1,6 +1,7 @@
-"""The smoother-count autotuner (itokmc_autotune): it must pick a converging
-pair, leave the state as it found it (potential and field), and later steps
-must still match a handle that never tuned, up to the field tolerance."""
+"""The autotuner (itokmc_autotune): it must pick a converging smoother pair
+and a deposit window, leave the state as it found it (potential, field, the
+last deposit), and later steps must still match a handle that never tuned,
+up to the field tolerance."""
 import numpy as np
 import pytest
 
@@ -31,6 +32,13 @@ def test_autotune_restores_state_and_keeps_results(precision):
     assert any(ms >= 0 for _, ms in t["tried"])
     assert np.array_equal(hs[0].itokmc_read_densities(itokmc.PHI), phi0)
     assert np.array_equal(hs[0].itokmc_read_densities(itokmc.E), E0)
+    # the deposit window: every candidate timed (the tuner checks that all
+    # give the same densities), the chosen one among them, the last deposit
+    # restored
+    assert [w for w, _ in t["dep_tried"]] == [0, 256, 512, 1024, 2048]
+    assert all(ms > 0 for _, ms in t["dep_tried"]) and t["dep_win"] in (0, 256, 512, 1024, 2048)
+    for which in (itokmc.NE_FIX, itokmc.XE):
+        assert np.array_equal(hs[0].itokmc_read_densities(which), hs[1].itokmc_read_densities(which))
     for H in hs:
         H.itokmc_step(2)
     # the particle path before the next solve is identical; the field differs
