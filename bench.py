@@ -34,20 +34,20 @@ sys.path.insert(0, ROOT)
 
 # DRAM bytes per particle of the transport stage (push, transport scans,
 # scatter, mover kernels): dram__bytes_read.sum + dram__bytes_write.sum of
-# those kernels in one ncu capture of the streamer workload at 128^3
-# (1.0e7 particles, the same kernels as the timed run), divided by the
-# particles of the captured step, keyed by "FP64 form"; scaled to the timed
-# run by its particle count (the stage's traffic grows in proportion: every
-# kernel streams the records or the per-cell arrays once or twice).
-# Captured: FP64 1.398 GB, mixed 0.856 GB for 9.97e6 particles (the
-# cudaMemsetAsync zeroing of five per-cell arrays, about 6 B per particle
-# at this density, is not a kernel and is not in the figure).
-TRANSPORT_DRAM_PER_PARTICLE = {True: 140.2, False: 85.8}
+# those kernels over every launch of the streamer workload at 256^3 (one ncu
+# launch list of this bench: set-up, one warm-up step and two timed steps,
+# 2.161e8 particle pushes), divided by the particles pushed, keyed by "FP64
+# form"; multiplied by the timed run's particle count (every kernel of the
+# stage streams the records or the per-cell arrays once or twice).
+# Captured: FP64 32.99 GB, mixed 21.36 GB.  The cudaMemsetAsync zeroing of
+# the per-cell count arrays is not a kernel and is not in the figure.
+TRANSPORT_DRAM_PER_PARTICLE = {True: 152.6, False: 98.8}
 # FP64 arithmetic of the FP64 push per particle (ncu thread-instruction counts
 # of DADD, DMUL and DFMA over a launch, divided by its particles; an FMA
-# counts as two operations).  The peak it is set against is measured in the
-# run (itokmc_probe_fp64_peak: register-resident FMA chains on every SM).
-FP64_FLOP_PER_PARTICLE = 123.0
+# counts as two operations: 12.4 + 30.6 + 2 x 37.1).  The peak it is set
+# against is measured in the run (itokmc_probe_fp64_peak: register-resident
+# FMA chains on every SM).
+FP64_FLOP_PER_PARTICLE = 117.3
 
 METRIC = "particle-steps/s (push+sort+deposit+KMC), HBM roofline %; FP32 vs FP64 at stated err"
 
