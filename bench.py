@@ -34,14 +34,15 @@ sys.path.insert(0, ROOT)
 
 # DRAM bytes per particle of the transport stage (push, transport scans,
 # scatter, mover kernels): dram__bytes_read.sum + dram__bytes_write.sum of
-# those kernels over every launch of the streamer workload at 256^3 (one ncu
-# launch list of this bench: set-up, one warm-up step and two timed steps,
-# 2.161e8 particle pushes), divided by the particles pushed, keyed by "FP64
-# form"; multiplied by the timed run's particle count (every kernel of the
-# stage streams the records or the per-cell arrays once or twice).
-# Captured: FP64 32.99 GB, mixed 21.36 GB.  The cudaMemsetAsync zeroing of
-# the per-cell count arrays is not a kernel and is not in the figure.
-TRANSPORT_DRAM_PER_PARTICLE = {True: 152.6, False: 98.8}
+# those kernels in one ncu capture of the streamer workload at 128^3 (9.97e6
+# particles, one transport stage, the same kernels as the timed run), divided
+# by its particles, keyed by "FP64 form"; multiplied by the timed run's
+# particle count (both grids hold about the same particles per cell, so the
+# per-cell arrays weigh alike per particle; the 256^3 field array no longer
+# fits in L2, which makes the full-size figure somewhat higher).  Captured:
+# FP64 1.401 GB, mixed 0.855 GB.  The cudaMemsetAsync zeroing of the
+# per-cell count arrays is not a kernel and is not in the figure.
+TRANSPORT_DRAM_PER_PARTICLE = {True: 140.5, False: 85.8}
 # FP64 arithmetic of the FP64 push per particle (ncu thread-instruction counts
 # of DADD, DMUL and DFMA over a launch, divided by its particles; an FMA
 # counts as two operations: 12.4 + 30.6 + 2 x 37.1).  The peak it is set
@@ -284,8 +285,8 @@ def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e)
     bpp = 2 * R + mesh / 32
     ach = processed * bpp / (stage["transport"] / 1e3) / 1e9
     # measured DRAM bytes of the same stage (dram__bytes_read.sum +
-    # dram__bytes_write.sum of its kernels in one ncu launch list of this
-    # workload at 256^3), per step at the timed mean particle count
+    # dram__bytes_write.sum of its kernels in one ncu capture of the same
+    # kernels on a smaller case), per step at the timed mean particle count
     tpp = TRANSPORT_DRAM_PER_PARTICLE[form == itokmc.FP64]
     traffic = tpp * processed / args.steps if tpp else None
     out = {"value": processed_all / (ms / 1e3), "ms_per_step": ms / args.steps,
