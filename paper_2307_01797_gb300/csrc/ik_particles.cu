@@ -1711,8 +1711,6 @@ __global__ void __launch_bounds__(128, GLOBAL ? 4 : (std::is_same<E, MP32>::valu
         unsigned long long* nW2 = reinterpret_cast<unsigned long long*>(base + L.nW2);
         unsigned long long* nC = reinterpret_cast<unsigned long long*>(base + L.nC);
         KeyW<K>* keys = reinterpret_cast<KeyW<K>*>(base + L.keys);
-        K* nlo = reinterpret_cast<K*>(base + L.nlo);
-        K* nhi = reinterpret_cast<K*>(base + L.nhi);
         uint32_t* nA = reinterpret_cast<uint32_t*>(base + L.nA);
         uint32_t* nB = reinterpret_cast<uint32_t*>(base + L.nB);
         uint32_t* nb = reinterpret_cast<uint32_t*>(base + L.nb);
@@ -1816,8 +1814,11 @@ __global__ void __launch_bounds__(128, GLOBAL ? 4 : (std::is_same<E, MP32>::valu
         __syncwarp();
 
         for (int level = 1; level < T; level *= 2) {
-            // ---- bounding boxes: one node per lane when the nodes are small
-            // (at most 4 elements on average), else group reductions per chunk
+            // ---- bounding boxes and the split axis of every node (NO_SPLIT
+            // below weight 2), taken where a node's box is complete: one node
+            // per lane when the nodes are small (at most 4 elements on
+            // average), else group reductions per chunk
+            bool any_split = false;
             if (n <= 4u * (uint32_t)nnodes) {
                 for (int d = lane; d < nnodes; d += 32) {
                     K lo[3], hi[3];
@@ -1833,13 +1834,14 @@ __global__ void __launch_bounds__(128, GLOBAL ? 4 : (std::is_same<E, MP32>::valu
                             hi[a] = v > hi[a] ? v : hi[a];
                         }
                     }
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) { nlo[3 * d + a] = lo[a]; nhi[3 * d + a] = hi[a]; }
+                    const bool sp = nW[d] >= 2;
+                    nax[d] = sp ? (uint8_t)widest_axis<E>(lo, hi) : NO_SPLIT;
+                    any_split |= sp;
                 }
             } else {
                 // a node continuing from the previous chunk takes that chunk's
-                // partial bounds (carried from its last lane); a node's bounds
-                // are stored by its last lane
+                // partial bounds (carried from its last lane); a node's axis
+                // is taken by its last lane
                 K clo[3] = { (K)~(K)0, (K)~(K)0, (K)~(K)0 }, chi[3] = { 0, 0, 0 };
                 uint32_t cd = 0xffffffffu;
                 for (uint32_t b0 = 0; b0 < n; b0 += 32) {
@@ -1855,6 +1857,7 @@ __global__ void __launch_bounds__(128, GLOBAL ? 4 : (std::is_same<E, MP32>::valu
                     E e;
                     if (ok) e = cur[j];
                     else { e.x = 0; e.y = 0; e.z = 0; e.w = 0; }
+                    K lo[3], hi[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const K v = ET<E>::key(e, a);
@@ -1863,26 +1866,18 @@ __global__ void __launch_bounds__(128, GLOBAL ? 4 : (std::is_same<E, MP32>::valu
                             mn = clo[a] < mn ? clo[a] : mn;
                             mx = chi[a] > mx ? chi[a] : mx;
                         }
-                        if (fin) {
-                            nlo[3 * d + a] = mn;
-                            nhi[3 * d + a] = mx;
-                        }
+                        lo[a] = mn;
+                        hi[a] = mx;
                         clo[a] = __shfl_sync(0xffffffffu, mn, 31);
                         chi[a] = __shfl_sync(0xffffffffu, mx, 31);
                     }
+                    if (fin) {
+                        const bool sp = nW[d] >= 2;
+                        nax[d] = sp ? (uint8_t)widest_axis<E>(lo, hi) : NO_SPLIT;
+                        any_split |= sp;
+                    }
                     cd = __shfl_sync(0xffffffffu, d, 31);
                 }
-            }
-            __syncwarp();
-            // ---- split axis per node (NO_SPLIT below weight 2)
-            bool any_split = false;
-            for (int d = lane; d < nnodes; d += 32) {
-                K lo[3], hi[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) { lo[a] = nlo[3 * d + a]; hi[a] = nhi[3 * d + a]; }
-                const bool sp = nW[d] >= 2;
-                nax[d] = sp ? (uint8_t)widest_axis<E>(lo, hi) : NO_SPLIT;
-                any_split |= sp;
             }
             // no node of weight >= 2: this and all further levels keep the list
             if (!__any_sync(0xffffffffu, any_split)) break;
