@@ -301,9 +301,12 @@ def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e)
                             "deposit_window_ms": {str(w): round(ms, 4) for w, ms in tune["dep_tried"]}} if tune else
            {"nu1": 2, "nu2": 2, "autotuned": False}}
     if with_e2e:
-        # e2e through the public API: the state uploaded from pinned host
-        # memory, one step, the electron density read back, every step
+        # e2e through the public API: the state (electron particles and ion
+        # counts) uploaded from pinned host memory, one step, the electron
+        # density read back, every step; each step starts from the same
+        # state, so none drifts from the workload
         pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in st.items()}
+        pin_ions = [torch.from_numpy(np.ascontiguousarray(v, dtype=np.int64)).pin_memory() for v in ions]
         ne_host = torch.empty(args.n ** 3, dtype=torch.int64).pin_memory()
         K2 = max(1, min(args.steps, 5))
         torch.cuda.synchronize()
@@ -312,13 +315,15 @@ def run_form(args, itokmc, form, ph, st, ions, rank, world, dist, dev, with_e2e)
         lib = itokmc.lib()
         for _ in range(K2):
             H.itokmc_set_particles(pin["x"], pin["y"], pin["z"], pin["w"], mem=itokmc.HOST)
+            H.itokmc_set_ions(*pin_ions)
             done += N0
             H.itokmc_step(1)
             itokmc._check(lib.itokmc_read_densities(H.h, 0, itokmc.NE_FIX, itokmc._ptr(ne_host),
                                                     ne_host.numel() * 8), H.h)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        out["e2e"] = {"value": done / te, "unit": "particle-steps/s", "h2d_bytes_per_step": N0 * (3 * 8 + 4),
+        out["e2e"] = {"value": done / te, "unit": "particle-steps/s",
+                      "h2d_bytes_per_step": N0 * (3 * 8 + 4) + 2 * args.n ** 3 * 8,
                       "d2h_bytes_per_step": args.n ** 3 * 8, "steps": K2}
     E = None
     if rank == 0 and not args.no_cpu_baseline and form == itokmc.FP64:
