@@ -1422,7 +1422,7 @@ __global__ void k_photo_place(const Photo* __restrict__ photos, const Counters* 
 // Per-warp scratch of the merge of one cell (all node arrays for T = ppc
 // nodes, element lists for `cap` elements): byte offsets from the base.
 struct MLayout {
-    uint32_t cur, tmp, nW, nW2, nC, keys, nlo, nhi, nA, nB, nb, nb2, npm, nsh, nid, nid2, nnd, nax, nfl, bytes;
+    uint32_t cur, tmp, nW, nW2, nC, keys, nA, nB, nb, nb2, npm, nsh, nid, nid2, nnd, nax, nfl, bytes;
 };
 __host__ __device__ inline uint32_t ml_take(uint32_t& o, uint32_t bytes)
 {
@@ -1440,8 +1440,6 @@ __host__ __device__ inline MLayout merge_layout(uint32_t cap, uint32_t T, uint32
     L.nW2 = ml_take(o, (T + 1) * 8);
     L.nC = ml_take(o, T * 8);
     L.keys = ml_take(o, cap * (ksize == 4 ? 8u : 16u));   // KeyW<K>
-    L.nlo = ml_take(o, 3 * T * ksize);
-    L.nhi = ml_take(o, 3 * T * ksize);
     L.nA = ml_take(o, T * 4);
     L.nB = ml_take(o, T * 4);
     L.nb = ml_take(o, (T + 1) * 4);
