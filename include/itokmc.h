@@ -64,9 +64,11 @@ extern "C" {
 
 /* ---- precision forms --------------------------------------------------- */
 #define ITOKMC_FP64 0   /* FP64 positions/push/KMC, FP64 multigrid (parity) */
-#define ITOKMC_MIXED 1  /* FP32 cell-relative positions and push, int64     */
-                        /* fixed-point deposit, FP32 V-cycles inside FP64   */
-                        /* residual iterative refinement                    */
+#define ITOKMC_MIXED 1  /* FP32 cell-relative positions, push and KMC,      */
+                        /* int64 fixed-point deposit; the potential held in */
+                        /* int64 fixed point, its residual formed exactly   */
+                        /* and corrected by FP32 V-cycles until the FP64    */
+                        /* tolerance holds; E evaluated in FP32             */
 
 /* ---- field coupling of a step (itokmc_config.coupling) ----------------- */
 #define ITOKMC_EXPLICIT 0       /* Euler-Maruyama push with the field of the  */
@@ -84,8 +86,10 @@ extern "C" {
 #define ITOKMC_XE 1       /* int64 n^3: electrons per cell (NGP), last a4   */
 #define ITOKMC_NPOS 2     /* int64 n^3: positive-ion count per cell         */
 #define ITOKMC_NNEG 3     /* int64 n^3: negative-ion count per cell         */
-#define ITOKMC_PHI 4      /* double n^3: potential, V                       */
+#define ITOKMC_PHI 4      /* double n^3: potential, V (mixed form: its int64 */
+                          /* fixed-point potential, converted)              */
 #define ITOKMC_E 5        /* double 3 n^3: Ex block, Ey block, Ez block V/m */
+                          /* (mixed form: the FP32 values the push uses)    */
 #define ITOKMC_RHO 6      /* int64 n^3: space charge 2^3s (N+ - N-) - ne_fix*/
                           /* in units of q_e 2^-3s, as of the last a4       */
 #define ITOKMC_FIRINGS 7  /* int64 5 n^3: ionizations, attachments, photon  */
