@@ -4,8 +4,9 @@ photoionization on, dt 5 ps), built by the bench's own recipe and run in the
 bench's launch configuration (the same capacity, seed and autotuned tiles,
 host-driven ``itokmc_step``).
 
-FP64 form: one full step against the oracle's step fed the same field, bit
-for bit on every output the step leaves (sorted particles after the merge,
+FP64 form (plain and with the recombination reactions): one full step
+against the oracle's step fed the same field, bit for bit on every output
+the step leaves (sorted particles after the merge,
 the deposited densities, X_e, the space charge, the firings of all cells,
 the ion counts, the outflow), and the field the step solves within 1e-5 of
 the exact solve of the same charge.  The oracle runs whole (push, deposit
@@ -87,8 +88,18 @@ def _align_by_cell(cg, ct, n3):
     return ig, ig - sg[c] + st[c]
 
 
-def test_full_size_fp64_step_bit_exact(workload):
+@pytest.mark.parametrize("recombination", [False, True])
+def test_full_size_fp64_step_bit_exact(workload, recombination):
+    """One FP64 step of the bench workload, plain and with the air
+    recombination coefficients (the bench's --recombination: five reactions,
+    second-order propensities)."""
     ph, st, ions, S, cap = workload
+    if recombination:
+        # negative ions as well (an eighth of the positive ones) so that both
+        # recombination reactions fire in the first step
+        ph = synth.with_recombination(ph)
+        ions = (ions[0], np.asarray(ions[0], np.int64) // 8)
+        S = dict(S, Nneg=ions[1].copy())
     n3 = ph["n"] ** 3
     p = oracle.make_params(ph, seed=SEED0, step=0)
     H = _handle(ph, st, ions, cap, itokmc.FP64)
@@ -101,6 +112,8 @@ def test_full_size_fp64_step_bit_exact(workload):
     H.itokmc_step(1)
     new, info = oracle.step(p, S, E)
     assert info["n_ion"].sum() > 0 and info["n_ph"].sum() > 0 and len(info["new_particles"][0]) > 0
+    if recombination:
+        assert info["n_ep"].sum() > 0 and info["n_np"].sum() > 0
     for which, ref in ((itokmc.NE_FIX, info["ne_fix"]), (itokmc.XE, info["Xe"]), (itokmc.RHO, info["rho_fixed"])):
         assert np.array_equal(H.itokmc_read_densities(which), ref), which
     F = H.itokmc_read_densities(itokmc.FIRINGS)
