@@ -6,10 +6,10 @@ host-driven ``itokmc_step``).
 
 FP64 form (plain and with the recombination reactions): one full step
 against the oracle's step fed the same field, bit for bit on every output
-the step leaves (sorted particles after the merge,
-the deposited densities, X_e, the space charge, the firings of all cells,
-the ion counts, the outflow), and the field the step solves within 1e-5 of
-the exact solve of the same charge.  The oracle runs whole (push, deposit
+the step leaves (sorted particles after the merge, the deposited densities,
+X_e, the space charge, the firings of all cells, the ion counts, the
+outflow), and the field the step solves within 1e-5 of the exact solve of
+the same charge.  The oracle runs whole (push, deposit
 and KMC on all host cores through its OpenMP build, the rest single
 threaded), so nothing is sampled.
 
